@@ -1,0 +1,337 @@
+"""FP64 CPU oracle for the BFCS FFT solver.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import or call this
+module: only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg
+(and its --impl reference arm) use it.  It shares no code with the CUDA path.
+
+It is a plain, slow, obviously-correct restatement of the paper's method
+(Buryachenko, "New RVE concept and FFT methods in micromechanics of composites
+subjected to body force with compact support"):
+
+  * DFT conventions, Eqs. 4.3-4.5 (forward omega^{-kn}, inverse with 1/|N|),
+    evaluated with numpy's FFT as the library primitive.
+  * Strain Green operator U0 in Fourier space, Eqs. 2.16-2.18, contracted as a
+    full fourth-order tensor.
+  * Modified Lippmann-Schwinger equation, Eqs. 2.14 / 5.3-5.4, solved by the
+    modified basic scheme, Algorithm 1 (Eqs. 5.7-5.10).
+  * Reference displacement u^{b(0)} = G0 * b, Eqs. 2.8-2.9, with G0 the inverse
+    of the isotropic acoustic tensor.
+  * Equilibrium residual, Eq. 5.11 (normalisation read as stated below).
+  * Microstructure translation and translated averaging, Eqs. 3.3-3.7.
+
+Readings taken where the paper is silent or garbled (each is listed in the
+design notes of the repository):
+  R1  wavevector xi_a = 2 pi k_a / N_a with signed index k_a in (-N_a/2, N_a/2)
+      and xi_a = 0 on the Nyquist index k_a = N_a/2 (spectral differentiation
+      for even N); every operator (U0, G0, divergence) uses this xi, which keeps
+      them Hermitian-consistent so that all fields stay real.
+  R2  U0 = -Gamma0 (Moulinec-Suquet); the index "h" of Eq. 2.17 is read as l.
+  R3  k = 0 mode of the strain = the prescribed mean strain E (DFT scale N*E);
+      on the other modes with xi = 0 (Nyquist corners) the strain update is 0
+      and the load b is not felt there.
+  R4  residual r = ||i xi.sigma_hat + b_hat|| / D over modes with xi != 0,
+      D = ||b_hat|| + xi_min |sigma_hat(0)|, xi_min = 2 pi / max N_a.
+  R5  stray superscript "^L" in Eq. 5.9 ignored.
+  R6  translated averages divide by the number of shifts (Eqs. 3.5-3.6 as
+      printed), inclusion-weighted ones included; the hit count is returned.
+  R7  translation: L(x, chi) = L0(x - chi) with b fixed (Eq. 3.3).
+
+Loop convention shared with the GPU path: sweep s forms tau^s = L1 eps^s, its
+transform, the residual r(eps^s) and eps^{s+1}.  The solve stops after the
+first sweep with r(eps^s) <= tol or after maxit sweeps and returns eps^S
+(S = sweeps run) with sigma^S, u^S and r(eps^S).
+
+Layouts: fields are numpy arrays indexed [component][z][y][x]; symmetric
+tensors use 6 components (xx, yy, zz, yz, xz, xy), tensorial (not
+engineering) shears.
+
+Parity: pinned by the -m "not gpu" tests (direct DFT, Green-operator
+identities, homogeneous closed form, plane-wave Navier solution, laminate
+closed form, dense brute-force solve, energy identity, Betti reciprocity,
+translation equivariance, averaging invariants).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# (i, j) of each stored component, Voigt-like order xx yy zz yz xz xy
+COMP = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+# stored component index of each (i, j)
+IDX = np.array([[0, 5, 4], [5, 1, 3], [4, 3, 2]])
+
+
+def to_full(v6):
+    """(6, ...) symmetric storage -> nested 3x3 list of arrays (views)."""
+    return [[v6[IDX[i, j]] for j in range(3)] for i in range(3)]
+
+
+# ---------------------------------------------------------------- a1 phase map
+def phase_map(dims, cell, spheres):
+    """Integer voxelisation of spheres in a periodic unit cell (Eqs. 2.21, 3.3).
+
+    dims = (nx, ny, nz) must be multiples of cell = (cx, cy, cz).  A voxel with
+    doubled centre 2i+1 lies in a sphere (X, Y, Z, T, phase) when the squared
+    periodic minimum-image distance on the doubled grid is <= T.  Later spheres
+    overwrite earlier ones; voxels in no sphere are phase 0 (matrix).
+    Returns int8 array [z][y][x].
+    """
+    nx, ny, nz = dims
+    cx, cy, cz = cell
+    if nx % cx or ny % cy or nz % cz:
+        raise ValueError("grid is not a whole number of unit cells")
+    ph = np.zeros((cz, cy, cx), dtype=np.int8)
+
+    def dd(n, c):
+        d = (2 * np.arange(n, dtype=np.int64) + 1 - c) % (2 * n)
+        return np.where(d >= n, d - 2 * n, d)
+
+    for X, Y, Z, T, p in np.asarray(spheres, dtype=np.int64).reshape(-1, 5):
+        dx, dy, dz = dd(cx, X), dd(cy, Y), dd(cz, Z)
+        d2 = dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2
+        ph[d2 <= T] = p
+    return np.tile(ph, (nz // cz, ny // cy, nx // cx))
+
+
+def translate(field, shift):
+    """f(x, chi) = f0(x - chi) on the periodic grid (Eq. 3.3); shift = (sx, sy, sz)."""
+    sx, sy, sz = (int(s) for s in shift)
+    return np.roll(field, (sz, sy, sx), axis=(-3, -2, -1))
+
+
+# ---------------------------------------------------------------- a2 body force
+def body_force(dims, centre, a):
+    """BFCS of Eq. 2.5 in the form b = (d phi / d x1, 0, 0), phi = (1 - r^2/a^2)^3
+    for r < a, evaluated at voxel centres i + 0.5 with the periodic minimum image
+    about `centre`, then made mean-free in FP64.  Returns (3, nz, ny, nx)."""
+    nx, ny, nz = dims
+
+    def rel(n, c):
+        d = np.arange(n, dtype=np.float64) + 0.5 - c
+        return d - n * np.round(d / n)
+
+    x = rel(nx, centre[0])[None, None, :]
+    y = rel(ny, centre[1])[None, :, None]
+    z = rel(nz, centre[2])[:, None, None]
+    r2 = x * x + y * y + z * z
+    s = 1.0 - r2 / (a * a)
+    b1 = np.where(r2 < a * a, -6.0 * x * s * s / (a * a), 0.0)
+    b1 = b1 - b1.mean()
+    b = np.zeros((3, nz, ny, nx))
+    b[0] = b1
+    return b
+
+
+# ---------------------------------------------------------------- transforms
+def fft3(f):
+    """Eq. 4.3 on the last three axes (numpy FFT as the library primitive)."""
+    return np.fft.fftn(f, axes=(-3, -2, -1))
+
+
+def ifft3(fh):
+    """Eq. 4.4 on the last three axes, including 1/|N|."""
+    return np.fft.ifftn(fh, axes=(-3, -2, -1))
+
+
+def wavevectors(dims):
+    """Reading R1: xi_a = 2 pi k_a / N_a (h = 1), zero on the Nyquist index.
+    Returns (xi_x, xi_y, xi_z) shaped to broadcast on [z][y][x]."""
+    out = []
+    for n in dims:
+        k = np.fft.fftfreq(n, d=1.0 / n)          # 0..n/2-1, -n/2..-1
+        k[n // 2] = 0.0                            # Nyquist index -> 0
+        out.append(2.0 * np.pi * k / n)
+    nx, ny, nz = dims
+    return (out[0].reshape(1, 1, nx), out[1].reshape(1, ny, 1), out[2].reshape(nz, 1, 1))
+
+
+# ---------------------------------------------------------------- constitutive
+def stiffness(lam, mu):
+    """Isotropic L_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk) (P. 2, L = 3k N1 + 2 mu N2)."""
+    d = np.eye(3)
+    return (lam * np.einsum("ij,kl->ijkl", d, d)
+            + mu * (np.einsum("ik,jl->ijkl", d, d) + np.einsum("il,jk->ijkl", d, d)))
+
+
+def apply_local(phase, table, eps):
+    """sigma = L(x) eps pointwise for isotropic phases; table[p] = (lam, mu)."""
+    lam = np.asarray([t[0] for t in table])[phase]
+    mu = np.asarray([t[1] for t in table])[phase]
+    tr = eps[0] + eps[1] + eps[2]
+    out = 2.0 * mu * eps
+    out[:3] += lam * tr
+    return out
+
+
+# ---------------------------------------------------------------- Green operators
+def u0_apply(tau_hat, xi, lam0, mu0):
+    """eps_hat_ij = sum_kl U0_ijkl(xi) tau_hat_kl, Eqs. 2.16-2.18, all 81 terms.
+
+    U0 = U1/(4 mu0) + (lam0+mu0)/(mu0 (lam0+2 mu0)) U2,
+    U1_ijkl = -(d_ki xi_l xi_j + d_li xi_k xi_j + d_kj xi_l xi_i + d_lj xi_k xi_i)/|xi|^2,
+    U2_ijkl = xi_i xi_j xi_k xi_l / |xi|^4.   Modes with xi = 0 give 0.
+    """
+    q = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+    nz = q > 0
+    iq = np.where(nz, 1.0 / np.where(nz, q, 1.0), 0.0)
+    c1 = 1.0 / (4.0 * mu0)
+    c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0))
+    t = to_full(tau_hat)
+    d = np.eye(3)
+    out = np.zeros_like(tau_hat)
+    for a, (i, j) in enumerate(COMP):
+        acc = 0.0
+        for k in range(3):
+            for l in range(3):
+                u1 = -(d[k, i] * xi[l] * xi[j] + d[l, i] * xi[k] * xi[j]
+                       + d[k, j] * xi[l] * xi[i] + d[l, j] * xi[k] * xi[i]) * iq
+                u2 = xi[i] * xi[j] * xi[k] * xi[l] * iq * iq
+                acc = acc + (c1 * u1 + c2 * u2) * t[k][l]
+        out[a] = acc
+    return out
+
+
+def g0_apply(v_hat, xi, lam0, mu0):
+    """w = G0(xi) v with G0 = K0^{-1}, K0_ik = mu0 |xi|^2 d_ik + (lam0+mu0) xi_i xi_k
+    (inverse of the Navier operator of Eqs. 2.6, 2.8; solved mode by mode)."""
+    shape = np.broadcast_shapes(xi[0].shape, xi[1].shape, xi[2].shape)
+    X = [np.broadcast_to(x, shape).ravel() for x in xi]
+    q = X[0] ** 2 + X[1] ** 2 + X[2] ** 2
+    K = np.empty((q.size, 3, 3))
+    for i in range(3):
+        for k in range(3):
+            K[:, i, k] = (lam0 + mu0) * X[i] * X[k] + (mu0 * q if i == k else 0.0)
+    nzm = q > 0
+    V = np.stack([np.broadcast_to(v_hat[i], shape).ravel() for i in range(3)], axis=-1)
+    W = np.zeros_like(V)
+    W[nzm] = np.linalg.solve(K[nzm], V[nzm][..., None])[..., 0]
+    return np.stack([W[:, i].reshape(shape) for i in range(3)])
+
+
+def sym_grad_hat(u_hat, xi):
+    """eps_hat = sym(i xi (x) u_hat) in 6-component storage (Eq. 2.3 with Eq. 4.8)."""
+    out = np.empty((6,) + np.broadcast_shapes(u_hat[0].shape, xi[0].shape), dtype=complex)
+    for a, (i, j) in enumerate(COMP):
+        out[a] = 0.5j * (xi[j] * u_hat[i] + xi[i] * u_hat[j])
+    return out
+
+
+def div_hat(s_hat, xi):
+    """(i xi . sigma_hat)_i = i sum_j xi_j sigma_hat_ij (Eq. 2.1 with Eq. 4.8)."""
+    s = to_full(s_hat)
+    return np.stack([1j * (xi[0] * s[i][0] + xi[1] * s[i][1] + xi[2] * s[i][2])
+                     for i in range(3)])
+
+
+def eps_b0_hat(b_hat, xi, lam0, mu0):
+    """Reference strain eps^{b(0)} = sym grad (G0 * b), Eqs. 2.8-2.9 and 2.14."""
+    return sym_grad_hat(g0_apply(b_hat, xi, lam0, mu0), xi)
+
+
+# ---------------------------------------------------------------- residual
+def residual(phase, table, eps, b_hat, xi):
+    """Reading R4 of Eq. 5.11, from sigma = L eps formed in real space."""
+    sig_hat = fft3(apply_local(phase, table, eps))
+    q = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+    act = np.broadcast_to(q > 0, sig_hat.shape[1:])
+    div = div_hat(sig_hat, xi) + b_hat
+    num = np.sqrt(np.sum(np.abs(div[:, act]) ** 2))
+    s0 = sig_hat[:, 0, 0, 0]
+    s0n = np.sqrt(np.sum(np.abs(s0[:3]) ** 2) + 2.0 * np.sum(np.abs(s0[3:]) ** 2))
+    dims = sig_hat.shape[1:][::-1]
+    den = np.sqrt(np.sum(np.abs(b_hat[:, act]) ** 2)) + 2.0 * np.pi / max(dims) * s0n
+    return float(num / den) if den > 0 else float(num)
+
+
+def _real(fh, what):
+    f = ifft3(fh)
+    scale = max(np.max(np.abs(f.real)), 1e-300)
+    if np.max(np.abs(f.imag)) > 1e-9 * scale:
+        raise AssertionError(f"{what}: spectrum is not Hermitian-consistent")
+    return f.real.copy()
+
+
+def displacement(eps, xi, lam0, mu0):
+    """Periodic displacement u with sym grad u = eps - <eps> and zero mean:
+    u_hat = -i G0(xi) (C0 eps_hat) xi on modes with xi != 0 (from Eq. 2.3)."""
+    lam_tr = lam0 * (eps[0] + eps[1] + eps[2])
+    c0e = 2.0 * mu0 * eps
+    c0e[:3] += lam_tr
+    s = to_full(fft3(c0e))
+    v = np.stack([xi[0] * s[i][0] + xi[1] * s[i][1] + xi[2] * s[i][2] for i in range(3)])
+    return _real(-1j * g0_apply(v, xi, lam0, mu0), "displacement")
+
+
+# ---------------------------------------------------------------- Algorithm 1
+def solve(phase, table, c0, b, mean_strain=(0.0,) * 6, tol=1e-10, maxit=1000,
+          eps_init=None, history=False):
+    """Modified basic scheme (Algorithm 1, Eqs. 5.7-5.10) for the ML-S equation
+    (Eq. 2.14 / 5.3-5.4).  phase: int [z][y][x]; table: [(lam, mu)] per phase;
+    c0 = (lam0, mu0); b: (3, nz, ny, nx) mean-free body force; mean_strain E
+    (6 components).  Returns dict(eps, sig, u, sweeps, resid, hist)."""
+    lam0, mu0 = c0
+    nz, ny, nx = phase.shape
+    dims = (nx, ny, nz)
+    n = nx * ny * nz
+    xi = wavevectors(dims)
+    b_hat = fft3(b)
+    eb0_hat = eps_b0_hat(b_hat, xi, lam0, mu0)
+    eb0_hat[:, 0, 0, 0] = n * np.asarray(mean_strain, dtype=float)   # reading R3
+    table1 = [(l - lam0, m - mu0) for (l, m) in table]               # L1 = L - L0
+
+    if eps_init is None:
+        eps = _real(eb0_hat, "eps0")                 # eps^[0] = eps^{b(0)} (+ E)
+    else:
+        eps = np.array(eps_init, dtype=float, copy=True)
+
+    hist = []
+    sweeps = 0
+    for s in range(maxit):
+        tau = apply_local(phase, table1, eps)                    # Eq. 5.7
+        tau_hat = fft3(tau)                                      # Eq. 5.8
+        r = residual(phase, table, eps, b_hat, xi)               # Eq. 5.11, of eps^s
+        hist.append(r)
+        eps_hat = u0_apply(tau_hat, xi, lam0, mu0) + eb0_hat     # Eq. 5.9 (+ eps^{b(0)})
+        eps = _real(eps_hat, "eps")                              # Eq. 5.10
+        sweeps = s + 1
+        if r <= tol:
+            break
+    r_final = residual(phase, table, eps, b_hat, xi)
+    sig = apply_local(phase, table, eps)
+    u = displacement(eps, xi, lam0, mu0)
+    out = dict(eps=eps, sig=sig, u=u, sweeps=sweeps, resid=r_final)
+    if history:
+        out["hist"] = hist
+    return out
+
+
+# ---------------------------------------------------------------- translated averaging
+AVG_FIELDS = ("u", "u1", "eps", "eps1", "sig", "sig1")
+AVG_WIDTH = {"u": 3, "u1": 3, "eps": 6, "eps1": 6, "sig": 6, "sig1": 6}
+
+
+def translate_average(phase0, table, c0, b, shifts, mean_strain=(0.0,) * 6,
+                      tol=1e-10, maxit=1000):
+    """Translated averaging, Eqs. 3.3-3.6: for each integer shift chi the
+    microstructure is translated (phase(x) = phase0(x - chi), b fixed), solved,
+    and u, V u, eps, V eps, sigma, V sigma are summed and divided by the number
+    of shifts (V = indicator of the inclusion phases, phase != 0).  Returns
+    (avg (30, nz, ny, nx) in the order <u>, <u>^(1), <eps>, <eps>^(1), <sigma>,
+    <sigma>^(1); hits (nz, ny, nx) int = number of shifts with V = 1; infos)."""
+    nz, ny, nx = phase0.shape
+    acc = np.zeros((30, nz, ny, nx))
+    hits = np.zeros((nz, ny, nx), dtype=np.int64)
+    infos = []
+    for chi in np.asarray(shifts).reshape(-1, 3):
+        ph = translate(phase0, chi)
+        res = solve(ph, table, c0, b, mean_strain, tol, maxit)
+        v = (ph != 0).astype(float)
+        acc[0:3] += res["u"]
+        acc[3:6] += v * res["u"]
+        acc[6:12] += res["eps"]
+        acc[12:18] += v * res["eps"]
+        acc[18:24] += res["sig"]
+        acc[24:30] += v * res["sig"]
+        hits += (ph != 0)
+        infos.append((res["sweeps"], res["resid"]))
+    m = max(len(infos), 1)
+    return acc / m, hits, infos

@@ -1,0 +1,54 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake (a dropped factor, a flipped sign, a wrong index
+or convention) into a temporary copy of the oracle and runs the pin suite
+against that copy in a subprocess; at least one pin must fail.  The real
+oracle is never modified.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "green_U2_coefficient": ("c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0))",
+                             "c2 = (lam0 + mu0) / (mu0 * (lam0 + 1.0 * mu0))"),
+    "green_U1_sign": ("u1 = -(d[k, i]", "u1 = (d[k, i]"),
+    "nyquist_kept": ("k[n // 2] = 0.0                            # Nyquist index -> 0", "pass"),
+    "g0_sign": ("W[nzm] = np.linalg.solve(K[nzm], V[nzm][..., None])[..., 0]",
+                "W[nzm] = -np.linalg.solve(K[nzm], V[nzm][..., None])[..., 0]"),
+    "sym_grad_sign": ("out[a] = 0.5j * (xi[j] * u_hat[i] + xi[i] * u_hat[j])",
+                      "out[a] = -0.5j * (xi[j] * u_hat[i] + xi[i] * u_hat[j])"),
+    "mean_strain_dft_scale": ("eb0_hat[:, 0, 0, 0] = n * np.asarray", "eb0_hat[:, 0, 0, 0] = np.asarray"),
+    "displacement_scale": ('return _real(-1j * g0_apply(v, xi, lam0, mu0), "displacement")',
+                           'return _real(-2j * g0_apply(v, xi, lam0, mu0), "displacement")'),
+    "translation_direction": ("np.roll(field, (sz, sy, sx)", "np.roll(field, (-sz, -sy, -sx)"),
+    "lame_trace_term": ("out[:3] += lam * tr", "out[:3] += 0.5 * lam * tr"),
+    "shear_counted_once": ("acc = acc + (c1 * u1 + c2 * u2) * t[k][l]",
+                           "acc = acc + (c1 * u1 + c2 * u2) * t[k][l] * (1.0 if k <= l else 0.0)"),
+    "average_normalisation": ("return acc / m, hits, infos", "return acc / (m + 1), hits, infos"),
+    "body_force_sign": ("-6.0 * x * s * s / (a * a)", "6.0 * x * s * s / (a * a)"),
+    "sphere_boundary_exclusive": ("ph[d2 <= T] = p", "ph[d2 < T] = p"),
+    "residual_misses_load": ("div = div_hat(sig_hat, xi) + b_hat", "div = div_hat(sig_hat, xi)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    before, after = MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "bfcs_oracle.py")).read()
+    assert src.count(before) == 1, "mutation anchor drifted"
+    (tmp_path / "oracle").mkdir()
+    (tmp_path / "oracle" / "__init__.py").write_text("")
+    (tmp_path / "oracle" / "bfcs_oracle.py").write_text(src.replace(before, after))
+    (tmp_path / "tests").mkdir()
+    shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "tests")
+    env = dict(os.environ, PYTHONPATH=str(tmp_path))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py"], cwd=tmp_path, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"planted mistake {name!r} passed every pin:\n{r.stdout[-2000:]}"

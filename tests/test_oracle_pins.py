@@ -1,0 +1,490 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a direct
+DFT sum, an operator identity, a closed-form solution, a dense brute-force
+solve, an energy or reciprocity identity, or an exact symmetry.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bfcs_oracle as O
+
+RNG = np.random.default_rng(20260103)
+WEIGHT = np.array([1, 1, 1, 2, 2, 2], dtype=float)   # shear components count twice
+
+
+def rand_sym(shape=()):
+    return RNG.standard_normal((6,) + shape)
+
+
+def mean_free(b):
+    return b - b.mean(axis=(-3, -2, -1), keepdims=True)
+
+
+def drop_xi_zero(b):
+    """Remove the load content on modes where xi = 0 (k = 0 and Nyquist corners)."""
+    nz, ny, nx = b.shape[-3:]
+    bh = O.fft3(b)
+    xi = O.wavevectors((nx, ny, nz))
+    q = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+    bh = bh * (q > 0)
+    return np.real(O.ifft3(bh))
+
+
+# ------------------------------------------------------------ DFT (Eqs. 4.3-4.5, 4.10-4.15)
+@pytest.mark.parametrize("shape", [(4, 6, 2), (2, 4, 6), (3, 2, 4)])
+def test_fft_matches_direct_dft(shape):
+    f = RNG.standard_normal(shape) + 1j * RNG.standard_normal(shape)
+    nz, ny, nx = shape
+    direct = np.zeros(shape, dtype=complex)
+    inv = np.zeros(shape, dtype=complex)
+    pts = list(itertools.product(range(nz), range(ny), range(nx)))
+    for k in pts:
+        acc = 0j
+        acc_i = 0j
+        for n in pts:
+            ph = 2 * math.pi * sum(k[a] * n[a] / shape[a] for a in range(3))
+            acc += f[n] * complex(math.cos(ph), -math.sin(ph))      # omega^{-kn}
+            acc_i += f[n] * complex(math.cos(ph), math.sin(ph))     # omega^{+kn}
+        direct[k] = acc
+        inv[k] = acc_i / (nz * ny * nx)
+    assert np.allclose(O.fft3(f), direct, rtol=0, atol=1e-12)
+    assert np.allclose(O.ifft3(f), inv, rtol=0, atol=1e-12)
+    assert np.allclose(O.ifft3(O.fft3(f)), f, atol=1e-13)             # Eq. 4.9
+
+
+def test_convolution_theorem_1d_and_3d():
+    n = 12
+    f, g = RNG.standard_normal(n), RNG.standard_normal(n)
+    s = np.array([sum(f[m] * g[(k - m) % n] for m in range(n)) for k in range(n)])   # Eq. 4.14
+    assert np.allclose(np.fft.fft(s), np.fft.fft(f) * np.fft.fft(g), atol=1e-11)
+    shape = (4, 2, 6)
+    f3, g3 = RNG.standard_normal(shape), RNG.standard_normal(shape)
+    conv = np.zeros(shape)
+    for k in itertools.product(*(range(d) for d in shape)):
+        for j in itertools.product(*(range(d) for d in shape)):
+            conv[k] += f3[tuple((k[a] - j[a]) % shape[a] for a in range(3))] * g3[j]  # Eq. 4.11
+    assert np.allclose(O.fft3(conv), O.fft3(f3) * O.fft3(g3), atol=1e-10)          # Eq. 4.10
+
+
+def test_wavevector_nyquist_and_hermitian():
+    dims = (8, 6, 4)
+    xi = O.wavevectors(dims)
+    for a, n in enumerate(dims):
+        v = xi[a].ravel()
+        assert v[n // 2] == 0.0
+        for k in range(n):
+            assert v[(-k) % n] == -v[k]
+        assert v[1] == pytest.approx(2 * math.pi / n)
+
+
+def test_spectral_derivative_exact_on_trig_polynomial():
+    dims = (16, 8, 4)
+    nx, ny, nz = dims
+    x = np.arange(nx)[None, None, :]
+    y = np.arange(ny)[None, :, None]
+    xi = O.wavevectors(dims)
+    for m in (1, 3, 7):
+        f = np.sin(2 * math.pi * m * x / nx) * np.cos(2 * math.pi * 2 * y / ny) + 0 * np.zeros((nz, 1, 1))
+        df = np.real(O.ifft3(1j * xi[0] * O.fft3(f)))
+        exact = (2 * math.pi * m / nx) * np.cos(2 * math.pi * m * x / nx) * np.cos(2 * math.pi * 2 * y / ny)
+        assert np.allclose(df, exact + 0 * df, atol=1e-12)
+    # Nyquist content has zero derivative under reading R1
+    f = np.cos(math.pi * x) + 0 * np.zeros((nz, ny, 1))
+    assert np.allclose(np.real(O.ifft3(1j * xi[0] * O.fft3(f))), 0, atol=1e-12)
+
+
+# ------------------------------------------------------------ Green operators (Eqs. 2.16-2.18, 2.27)
+def u0_tensor(xi_vec, lam0, mu0):
+    """U0_ijkl at one wavevector, recovered from u0_apply on symmetric basis tensors."""
+    xi = tuple(np.array([[[v]]]) for v in xi_vec)
+    U = np.zeros((3, 3, 3, 3))
+    for b, (k, l) in enumerate(O.COMP):
+        basis = np.zeros((6, 1, 1, 1), dtype=complex)
+        basis[b] = 1.0 if k == l else 0.5     # E^{kl} = (e_k e_l + e_l e_k)/2
+        out = O.u0_apply(basis, xi, lam0, mu0)[:, 0, 0, 0].real
+        for a, (i, j) in enumerate(O.COMP):
+            for (p, q) in {(i, j), (j, i)}:
+                for (r, s) in {(k, l), (l, k)}:
+                    U[p, q, r, s] = out[a]
+    return U
+
+
+def sym6(t):
+    """3x3 -> 6 components."""
+    return np.array([t[i, j] for (i, j) in O.COMP])
+
+
+def full3(v):
+    return np.array([[v[O.IDX[i, j]] for j in range(3)] for i in range(3)])
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_u0_symmetries_evenness_homogeneity(seed):
+    r = np.random.default_rng(seed)
+    xi = r.standard_normal(3)
+    lam0, mu0 = 1.0 + r.random(), 0.5 + r.random()
+    U = u0_tensor(xi, lam0, mu0)
+    assert np.allclose(U, U.transpose(1, 0, 2, 3), atol=1e-14)
+    assert np.allclose(U, U.transpose(0, 1, 3, 2), atol=1e-14)
+    assert np.allclose(U, U.transpose(2, 3, 0, 1), atol=1e-14)
+    assert np.allclose(U, u0_tensor(-xi, lam0, mu0), atol=1e-14)
+    assert np.allclose(U, u0_tensor(3.7 * xi, lam0, mu0), atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_projection_identities(seed):
+    r = np.random.default_rng(100 + seed)
+    xi = r.standard_normal(3)
+    lam0, mu0 = 0.5 + r.random(), 0.3 + r.random()
+    U = u0_tensor(xi, lam0, mu0)
+    G = -U                                         # Gamma0 = -U0
+    C = O.stiffness(lam0, mu0)
+    GCG = np.einsum("ijmn,mnpq,pqkl->ijkl", G, C, G)
+    assert np.allclose(GCG, G, atol=1e-13)         # Gamma0 C0 Gamma0 = Gamma0
+    v = r.standard_normal(3)
+    e = 0.5 * (np.outer(xi, v) + np.outer(v, xi))  # compatible (zero-mean) strain mode
+    assert np.allclose(np.einsum("ijkl,kl->ij", U, np.einsum("klmn,mn->kl", C, e)), -e,
+                       atol=1e-13)                 # Eq. 2.27 on k != 0
+    tau = full3(r.standard_normal(6))
+    lhs = np.einsum("ijkl,kl->ij", C, np.einsum("ijkl,kl->ij", G, tau)) @ xi
+    assert np.allclose(lhs, tau @ xi, atol=1e-13)  # xi.C0.Gamma0 tau = xi.tau
+
+
+def test_reference_strain_equilibrates_load():
+    r = np.random.default_rng(7)
+    lam0, mu0 = 2.0, 0.7
+    xi = tuple(r.standard_normal((1, 1, 5)) for _ in range(3))
+    bh = r.standard_normal((3, 1, 1, 5)) + 1j * r.standard_normal((3, 1, 1, 5))
+    e = O.eps_b0_hat(bh, xi, lam0, mu0)
+    s = e.copy()
+    tr = e[0] + e[1] + e[2]
+    s = 2 * mu0 * e
+    s[:3] += lam0 * tr
+    assert np.allclose(O.div_hat(s, xi) + bh, 0, atol=1e-12)   # i xi.(C0 eps^{b0}) + b = 0
+
+
+# ------------------------------------------------------------ closed forms
+def navier_inverse(xi, lam, mu):
+    """Closed-form inverse of the isotropic acoustic tensor (textbook)."""
+    q = xi @ xi
+    return (np.eye(3) - (lam + mu) / (lam + 2 * mu) * np.outer(xi, xi) / q) / (mu * q)
+
+
+def test_plane_wave_load_homogeneous_closed_form():
+    dims = (8, 6, 4)
+    nx, ny, nz = dims
+    lam, mu = 1.3, 0.8
+    m = np.array([1, 2, 1])
+    xi = 2 * math.pi * m / np.array(dims)
+    B = np.array([0.3, -0.2, 0.5])
+    x = np.arange(nx)[None, None, :]
+    y = np.arange(ny)[None, :, None]
+    z = np.arange(nz)[:, None, None]
+    ph = xi[0] * x + xi[1] * y + xi[2] * z
+    b = np.stack([B[i] * np.cos(ph) for i in range(3)])
+    a = navier_inverse(xi, lam, mu) @ B                 # u = a cos(xi.x)
+    phase = np.zeros((nz, ny, nx), dtype=np.int8)
+    res = O.solve(phase, [(lam, mu)], (lam, mu), b, tol=0, maxit=1)
+    u_exact = np.stack([a[i] * np.cos(ph) for i in range(3)])
+    e_exact = np.stack([-0.5 * (xi[i] * a[j] + xi[j] * a[i]) * np.sin(ph) for (i, j) in O.COMP])
+    assert np.allclose(res["u"], u_exact, atol=1e-13)
+    assert np.allclose(res["eps"], e_exact, atol=1e-13)
+    assert res["resid"] < 1e-13
+
+
+def test_homogeneous_case_one_sweep_exact():
+    dims = (6, 8, 4)
+    nx, ny, nz = dims
+    c0 = (1.7, 0.9)
+    phase = RNG.integers(0, 3, size=(nz, ny, nx)).astype(np.int8)
+    table = [c0, c0, c0]                                  # C(x) = C0 everywhere
+    b = drop_xi_zero(RNG.standard_normal((3, nz, ny, nx)))
+    E = tuple(0.01 * RNG.standard_normal(6))
+    res = O.solve(phase, table, c0, b, E, tol=0, maxit=1, history=True)
+    xi = O.wavevectors(dims)
+    e0h = O.eps_b0_hat(O.fft3(b), xi, *c0)
+    e0h[:, 0, 0, 0] = nx * ny * nz * np.array(E)
+    assert np.allclose(res["eps"], np.real(O.ifft3(e0h)), atol=1e-13)
+    assert res["hist"][0] < 1e-13 and res["resid"] < 1e-13
+    assert np.allclose(res["eps"].mean(axis=(1, 2, 3)), E, atol=1e-14)
+
+
+def laminate_exact(lam, mu, b1, e11):
+    """Exact discrete solution of the 1D laminate d/dx sigma11 + b1 = 0 under reading R1."""
+    n = b1.size
+    k = np.fft.fftfreq(n, d=1.0 / n)
+    k[n // 2] = 0
+    xi = 2 * math.pi * k / n
+    bh = np.fft.fft(b1)
+    s0h = np.zeros(n, dtype=complex)
+    nzm = xi != 0
+    s0h[nzm] = 1j * bh[nzm] / xi[nzm]
+    s0 = np.real(np.fft.ifft(s0h))
+    comp = 1.0 / (lam + 2 * mu)                   # compliance along the stack
+    alt = (-1.0) ** np.arange(n)
+    A = np.array([[comp.sum(), (alt * comp).sum()], [(alt * comp).sum(), comp.sum()]])
+    rhs = np.array([n * e11 - (comp * s0).sum(), -(alt * comp * s0).sum()])
+    c0, c1 = np.linalg.solve(A, rhs)
+    sig11 = s0 + c0 + c1 * alt
+    return comp * sig11, sig11
+
+
+def test_laminate_closed_form():
+    nx, ny, nz = 16, 2, 2
+    lam_ph = [1.0, 10.0]
+    mu_ph = [0.5, 5.0]
+    layers = np.array([0, 0, 1, 1, 1, 0, 0, 0, 1, 0, 1, 1, 0, 0, 1, 0], dtype=np.int8)
+    phase = np.broadcast_to(layers[None, None, :], (nz, ny, nx)).copy()
+    b1 = RNG.standard_normal(nx)
+    bh = np.fft.fft(b1)
+    bh[0] = 0
+    bh[nx // 2] = 0
+    b1 = np.real(np.fft.ifft(bh))
+    b = np.zeros((3, nz, ny, nx))
+    b[0] = b1[None, None, :]
+    E = (0.02, 0, 0, 0, 0, 0)
+    table = list(zip(lam_ph, mu_ph))
+    c0 = (5.5, 2.75)
+    res = O.solve(phase, table, c0, b, E, tol=1e-14, maxit=5000)
+    e11, s11 = laminate_exact(np.array(lam_ph)[layers], np.array(mu_ph)[layers], b1, E[0])
+    assert res["resid"] < 1e-13
+    assert np.allclose(res["eps"][0], e11[None, None, :], atol=1e-12)
+    assert np.allclose(res["eps"][1:], 0, atol=1e-12)
+    assert np.allclose(res["sig"][0], s11[None, None, :], atol=1e-11)
+
+
+# ------------------------------------------------------------ dense brute force
+def _operators(dims):
+    """Real matrices of the spectral symmetric gradient D_s (3N -> 6N) and of the
+    divergence (6N -> 3N), assembled column by column from unit vectors."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    xi = O.wavevectors(dims)
+    Ds = np.zeros((6 * n, 3 * n))
+    for c in range(3 * n):
+        u = np.zeros(3 * n)
+        u[c] = 1.0
+        uh = O.fft3(u.reshape(3, nz, ny, nx))
+        Ds[:, c] = np.real(O.ifft3(O.sym_grad_hat(uh, xi))).ravel()
+    Dv = np.zeros((3 * n, 6 * n))
+    for c in range(6 * n):
+        s = np.zeros(6 * n)
+        s[c] = 1.0
+        sh = O.fft3(s.reshape(6, nz, ny, nx))
+        Dv[:, c] = np.real(O.ifft3(O.div_hat(sh, xi))).ravel()
+    return Ds, Dv
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4), (6, 4, 2)])
+def test_dense_bruteforce_solve(dims):
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    r = np.random.default_rng(sum(dims))
+    phase = r.integers(0, 2, size=(nz, ny, nx)).astype(np.int8)
+    table = [(1.0, 0.5), (4.0, 2.0)]
+    c0 = (2.5, 1.25)
+    b = mean_free(r.standard_normal((3, nz, ny, nx)))
+    E = tuple(0.05 * r.standard_normal(6))
+    Ds, Dv = _operators(dims)
+    lam = np.array([t[0] for t in table])[phase].ravel()
+    mu = np.array([t[1] for t in table])[phase].ravel()
+
+    def Lmat():
+        L = np.zeros((6 * n, 6 * n))
+        for a in range(6):
+            for p in range(n):
+                L[a * n + p, a * n + p] += 2 * mu[p]
+                if a < 3:
+                    for c in range(3):
+                        L[a * n + p, c * n + p] += lam[p]
+        return L
+
+    L = Lmat()
+    Evec = np.concatenate([np.full(n, E[a]) for a in range(6)])
+    A = -Dv @ L @ Ds
+    rhs = b.ravel() + Dv @ (L @ Evec)
+    u = np.linalg.lstsq(A, rhs, rcond=1e-12)[0]
+    eps_direct = (Evec + Ds @ u).reshape(6, nz, ny, nx)
+    res = O.solve(phase, table, c0, b, E, tol=1e-14, maxit=5000)
+    assert res["resid"] < 1e-13
+    assert np.allclose(res["eps"], eps_direct, atol=1e-10)
+
+
+# ------------------------------------------------------------ energy, reciprocity, translation
+def _c1_small():
+    dims = (16, 16, 16)
+    spheres = np.array([[16, 16, 16, 100, 1]], dtype=np.int32)
+    phase = O.phase_map(dims, (16, 16, 16), spheres)
+    table = [(1.0, 0.5), (10.0, 5.0)]
+    return dims, phase, table, (5.5, 2.75)
+
+
+def test_energy_identity_fixes_displacement_scale():
+    dims, phase, table, c0 = _c1_small()
+    b = O.body_force(dims, (8.0, 8.0, 8.0), 5.0)
+    res = O.solve(phase, table, c0, b, tol=1e-12, maxit=3000)
+    work = np.sum(b * res["u"])
+    energy = np.sum(WEIGHT[:, None, None, None] * res["sig"] * res["eps"])
+    assert work > 0
+    assert work == pytest.approx(energy, rel=1e-9)
+
+
+def test_betti_reciprocity():
+    dims, phase, table, c0 = _c1_small()
+    bA = O.body_force(dims, (8.0, 8.0, 8.0), 5.0)
+    bB = O.body_force(dims, (4.0, 10.0, 6.0), 4.0)
+    bB = np.stack([bB[0] * 0, bB[0], bB[0] * 0])      # a load along x2 this time
+    uA = O.solve(phase, table, c0, bA, tol=1e-12, maxit=3000)["u"]
+    uB = O.solve(phase, table, c0, bB, tol=1e-12, maxit=3000)["u"]
+    lhs, rhs = np.sum(bA * uB), np.sum(bB * uA)
+    assert abs(lhs - rhs) <= 1e-9 * max(abs(lhs), abs(rhs), 1e-30)
+    assert abs(lhs) > 1e-8
+
+
+def test_translation_equivariance():
+    dims = (12, 8, 8)
+    nx, ny, nz = dims
+    spheres = np.array([[6, 7, 8, 12, 1]], dtype=np.int32)
+    phase0 = O.phase_map(dims, (12, 8, 8), spheres)
+    table = [(1.0, 0.5), (6.0, 3.0)]
+    c0 = (3.5, 1.75)
+    b = O.body_force(dims, (6.0, 4.0, 4.0), 3.5)
+    chi = (5, 3, 2)
+    a = O.solve(O.translate(phase0, chi), table, c0, b, tol=0, maxit=25)
+    bs = O.translate(b, tuple(-c for c in chi))
+    c = O.solve(phase0, table, c0, bs, tol=0, maxit=25)
+    for key in ("eps", "sig", "u"):
+        assert np.allclose(a[key], O.translate(c[key], chi), atol=1e-13)
+
+
+def test_neumann_partial_sums():
+    dims = (8, 8, 8)
+    nx, ny, nz = dims
+    r = np.random.default_rng(3)
+    phase = r.integers(0, 2, size=(nz, ny, nx)).astype(np.int8)
+    table = [(1.0, 0.5), (3.0, 1.5)]
+    c0 = (2.0, 1.0)
+    b = mean_free(r.standard_normal((3, nz, ny, nx)))
+    xi = O.wavevectors(dims)
+    e0 = np.real(O.ifft3(O.eps_b0_hat(O.fft3(b), xi, *c0)))
+    t1 = [(l - c0[0], m - c0[1]) for l, m in table]
+
+    def B(e):   # B^U = F^-1 U0 F L1  (Eq. 5.5)
+        return np.real(O.ifft3(O.u0_apply(O.fft3(O.apply_local(phase, t1, e)), xi, *c0)))
+
+    term, total = e0, e0.copy()
+    for j in range(1, 6):
+        term = B(term)
+        total = total + term
+        res = O.solve(phase, table, c0, b, tol=0, maxit=j)
+        assert np.allclose(res["eps"], total, atol=1e-13)   # Eq. 5.6
+
+
+# ------------------------------------------------------------ inputs: phase map and body force
+def test_phase_map_bruteforce():
+    dims, cell = (12, 10, 8), (6, 10, 4)
+    spheres = np.array([[3, 9, 4, 9, 1], [11, 1, 7, 6, 2], [0, 19, 0, 4, 3]], dtype=np.int32)
+    ph = O.phase_map(dims, cell, spheres)
+    nx, ny, nz = dims
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                want = 0
+                for (X, Y, Z, T, p) in spheres:
+                    d2 = 0
+                    for (i, c, n) in ((x % cell[0], X, cell[0]), (y % cell[1], Y, cell[1]),
+                                      (z % cell[2], Z, cell[2])):
+                        best = min(abs(2 * i + 1 - c + 2 * n * s) for s in (-1, 0, 1))
+                        d2 += best * best
+                    if d2 <= T:
+                        want = p
+                assert ph[z, y, x] == want
+
+
+def test_centred_sphere_voxel_count():
+    # lattice points (i+1/2, j+1/2, k+1/2) - 8 with squared distance <= 25, counted by loops
+    count = sum(1 for i in range(16) for j in range(16) for k in range(16)
+                if (i + 0.5 - 8) ** 2 + (j + 0.5 - 8) ** 2 + (k + 0.5 - 8) ** 2 <= 25)
+    ph = O.phase_map((16, 16, 16), (16, 16, 16), np.array([[16, 16, 16, 100, 1]]))
+    assert int((ph == 1).sum()) == count == 552
+
+
+def test_body_force_form():
+    dims = (24, 20, 16)
+    centre, a = (10.0, 9.5, 8.0), 6.0
+    b = O.body_force(dims, centre, a)
+    assert abs(b[0].sum()) < 1e-12 and np.all(b[1:] == 0)
+    raw = b[0] - b[0][0, 0, 0]           # the far field equals minus the removed mean
+    nx, ny, nz = dims
+    h = 1e-5
+    for (x, y, z) in [(12, 9, 8), (7, 11, 6), (10, 14, 9)]:
+        p = np.array([x + 0.5, y + 0.5, z + 0.5]) - np.array(centre)
+
+        def phi(q):
+            r2 = q @ q
+            return (1 - r2 / a ** 2) ** 3 if r2 < a * a else 0.0
+        fd = (phi(p + [h, 0, 0]) - phi(p - [h, 0, 0])) / (2 * h)
+        assert raw[z, y, x] == pytest.approx(fd, abs=1e-8)
+    # voxel centres at integer + 1/2 about an integer centre: odd in x1, sum exactly ~0
+    b2 = O.body_force((16, 16, 16), (8.0, 8.0, 8.0), 5.0)[0]
+    assert np.allclose(b2, -b2[:, :, ::-1], atol=1e-15)
+
+
+# ------------------------------------------------------------ translated averaging
+def test_translate_average_invariants():
+    dims = (8, 8, 8)
+    cell = (4, 4, 4)
+    spheres = np.array([[4, 4, 4, 6, 1]], dtype=np.int32)
+    phase0 = O.phase_map(dims, cell, spheres)
+    table = [(1.0, 0.5), (5.0, 2.5)]
+    c0 = (3.0, 1.5)
+    b = O.body_force(dims, (4.0, 4.0, 4.0), 2.5)
+    # single shift chi = 0 reproduces the plain solve
+    avg, hits, _ = O.translate_average(phase0, table, c0, b, [(0, 0, 0)], tol=0, maxit=10)
+    one = O.solve(phase0, table, c0, b, tol=0, maxit=10)
+    assert np.allclose(avg[6:12], one["eps"]) and np.allclose(avg[0:3], one["u"])
+    v = (phase0 != 0)
+    assert np.allclose(avg[24:30], v * one["sig"]) and np.array_equal(hits, v)
+    # the full stride-1 lattice of shifts in one cell: every voxel is hit by as many
+    # shifts as the cell has inclusion voxels
+    shifts = [(i, j, k) for i in range(4) for j in range(4) for k in range(4)]
+    per_cell = int((O.phase_map(cell, cell, spheres) != 0).sum())
+    _, hits, _ = O.translate_average(phase0, table, c0, b, shifts, tol=0, maxit=0)
+    assert np.all(hits == per_cell)
+    # shifting by a whole cell period leaves every member unchanged
+    avg2, _, _ = O.translate_average(phase0, table, c0, b, [(4, 0, 0), (0, 4, 4)], tol=0, maxit=6)
+    one = O.solve(phase0, table, c0, b, tol=0, maxit=6)
+    assert np.allclose(avg2[18:24], one["sig"], atol=1e-14)
+
+
+def test_residual_decreases_and_parseval():
+    dims, phase, table, c0 = _c1_small()
+    b = O.body_force(dims, (8.0, 8.0, 8.0), 5.0)
+    res = O.solve(phase, table, c0, b, tol=1e-9, maxit=500, history=True)
+    h = res["hist"]
+    assert h[-1] < h[0] * 1e-6
+    assert all(h[i + 1] < h[i] for i in range(5, len(h) - 1))
+    # real-space equilibrium error of the returned field matches the spectral numerator
+    nx, ny, nz = dims
+    xi = O.wavevectors(dims)
+    sh = O.fft3(res["sig"])
+    bh = O.fft3(b)
+    q = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+    d = (O.div_hat(sh, xi) + bh) * (q > 0)
+    real_space = np.real(O.ifft3(d))
+    assert np.sum(np.abs(d) ** 2) == pytest.approx(nx * ny * nz * np.sum(real_space ** 2), rel=1e-10)
+
+
+def test_translation_direction_by_index():
+    """Eq. 3.3: L(x, chi) = L0(x - chi), checked element by element."""
+    f = RNG.integers(0, 100, size=(5, 6, 7))
+    chi = (2, 4, 1)   # (x, y, z)
+    g = O.translate(f, chi)
+    for z in range(5):
+        for y in range(6):
+            for x in range(7):
+                assert g[z, y, x] == f[(z - chi[2]) % 5, (y - chi[1]) % 6, (x - chi[0]) % 7]
