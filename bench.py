@@ -1,0 +1,387 @@
+"""Benchmark of the BFCS FFT solver on GB300.
+
+Workload (the metric's configuration): one plain FP32 solve on a 256^3 grid
+= 8^3 unit cells of 32^3 with seeded random non-overlapping spheres (vf 0.25,
+radii 4-6 voxels), Young contrast 10 (nu 0.2/0.3), BFCS b1 = d phi/d x1 with
+a = 24 voxels, residual 1e-6.  A step is one whole pass of the hot path on
+that input: phase-map voxelisation, body-force field, the transform of the
+load, Algorithm-1 sweeps until the residual drops below 1e-6, and the
+finalisation (strain, stress, displacement, residual of the returned field).
+
+Metric: voxel-iterations per second = N_voxels x sweeps / time (higher is
+better); the same line reports solves/s, the live roofline of the dominant
+kernel (the fused z/Green pass), the end-to-end number through host buffers,
+clocks, and the FP64 CPU oracle timed on a bounded sample as the baseline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch under torchrun; each rank solves its own seeded replica
+(independent problems, no collective on the data path: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iter/s"
+UNIT = "voxel-iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid edge (256 for the benchmarked workload)")
+    ap.add_argument("--contrast", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args, rank):
+    from paper_2601_00822_gb300 import workloads as W
+    cell = 32 if args.n >= 64 else 16
+    p = W.config_c2(contrast=args.contrast, seed=1 + rank, n=args.n, cell=cell,
+                    bf_radius=24.0 * args.n / 256.0)
+    return p
+
+
+def config_dict(p, args, world):
+    return {
+        "workload": f"plain FP32 single solve {args.n}^3 = {(args.n // p.cell[0])}^3 cells of {p.cell[0]}^3, "
+                    f"RSA spheres vf 0.25 r 4-6, Young contrast {int(args.contrast)}, BFCS a="
+                    f"{p.bf_radius:g}, residual {p.tol:g}",
+        "grid": list(p.dims), "contrast": args.contrast, "tol": p.tol, "seed": p.extra["seed"],
+        "precision": "fp32 sweeps, fp64 residual sums",
+        "l2": "inputs larger than L2 (the 6-component spectrum is 0.43 GB at 256^3; no flush needed)",
+        "parallelism": f"replicas x{world} (independent seeded problems per GPU)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def green_algorithmic_bytes(dims, elem=8):
+    """Compulsory bytes of one fused z/Green launch: read the 6-component x,y-transformed
+    spectrum, write it back, read b_hat (3) and d_prev (3), write d (3) - over the
+    nz*ny*(nx/2+1) stored modes, complex64 each."""
+    nx, ny, nz = dims
+    modes = nz * ny * (nx // 2 + 1)
+    return (6 + 6 + 3 + 3 + 3) * elem * modes
+
+
+def traffic_record(dims):
+    """dram bytes per launch of the Green pass from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "zgreen_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for name in rec.get("sources", []):
+        with open(os.path.join(ROOT, name), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("source_sha256"):
+        return None
+    nx, ny, nz = dims
+    scale = (nz * ny * (nx // 2 + 1)) / float(rec["modes"])
+    return rec["dram_bytes_per_launch"] * scale
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+def oracle_sample(p, sweeps=1):
+    """Time `sweeps` Algorithm-1 sweeps of the FP64 oracle on the same workload (its
+    setup untimed); returns (voxel-iter/s, seconds, cores)."""
+    import numpy as np
+    from oracle import bfcs_oracle as O
+    ph = O.phase_map(p.dims, p.cell, p.spheres)
+    b = O.body_force(p.dims, p.bf_centre, p.bf_radius)
+    t0 = time.perf_counter()
+    O.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=sweeps)
+    t = time.perf_counter() - t0 - t_setup
+    n = int(np.prod(p.dims))
+    return n * sweeps / max(t, 1e-9), t, 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload(args, 0)
+    import numpy as np
+    from oracle import bfcs_oracle as O
+    ph = O.phase_map(p.dims, p.cell, p.spheres)
+    b = O.body_force(p.dims, p.bf_centre, p.bf_radius)
+    t0 = time.perf_counter()
+    O.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=0)
+    t_setup = time.perf_counter() - t0
+    n = int(np.prod(p.dims))
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=1)
+        t = time.perf_counter() - t0 - t_setup
+        if k >= args.warmup:
+            times.append(t)
+    per = sum(times) / len(times)
+    value = n / per
+    sample = (f"one Algorithm-1 sweep of the {args.n}^3 workload per step (oracle setup untimed), "
+              f"FP64 numpy/scipy single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(p, args, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_00822_gb300 import api
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = workload(args, rank)
+    nx, ny, nz = p.dims
+    nvox = nx * ny * nz
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    plan = api.Plan(p.dims, "fp32")
+    stream = plan.stream
+    eps = torch.empty((6, nz, ny, nx), dtype=torch.float32, device=dev)
+    sig = torch.empty_like(eps)
+    u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev)
+
+    def step():
+        ph = api.voxelize(p.dims, p.cell, p.spheres, device=dev)
+        b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp32", device=dev)
+        _, _, _, info = plan.solve(ph, p.phases, p.c0, b, tol=p.tol, maxit=p.maxit, eps_out=eps,
+                                   sig_out=sig, u_out=u)
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    plan.profile(3)                         # event-time every fused z/Green launch
+    launches0 = api.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    sweeps = 0
+    infos = []
+    for _ in range(args.steps):
+        info = step()
+        infos.append(info)
+        sweeps += info.iters
+    e1.record(stream)
+    barrier()
+    clocks.stop()
+    launches = api.kernel_launches() - launches0
+    g_launches, g_ms = plan.profile_read()
+    plan.profile(0)
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms / 1e3, float(nvox) * sweeps, float(args.steps)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tot = t[1:].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        secs, vox_iters, solves = tmax.item(), tot[0].item(), tot[1].item()
+    else:
+        secs, vox_iters, solves = t[0].item(), t[1].item(), t[2].item()
+    value = vox_iters / secs
+
+    # per-kernel durations of one sweep (untimed extra solve, events around each kind)
+    kern = {}
+    for kind, name in ((1, "x_pass_polarization"), (2, "y_passes"), (3, "z_green_pass")):
+        plan.profile(kind)
+        step()
+        n_l, t_l = plan.profile_read()
+        kern[name] = {"launches": n_l, "avg_ms": t_l / max(n_l, 1)}
+    plan.profile(0)
+
+    # end to end through host buffers: H2D phase + b from pinned memory, solve, D2H strain
+    e2e = None
+    if not args.no_e2e:
+        ph_d = api.voxelize(p.dims, p.cell, p.spheres, device=dev)
+        b_d = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp32", device=dev)
+        ph_h = ph_d.cpu().pin_memory()
+        b_h = b_d.cpu().pin_memory()
+        eps_h = torch.empty(eps.shape, dtype=eps.dtype).pin_memory()
+        ph_in = torch.empty_like(ph_d)
+        b_in = torch.empty_like(b_d)
+
+        def e2e_step():
+            ph_in.copy_(ph_h, non_blocking=True)
+            b_in.copy_(b_h, non_blocking=True)
+            _, _, _, info = plan.solve(ph_in, p.phases, p.c0, b_in, tol=p.tol, maxit=p.maxit, eps_out=eps,
+                                       sig_out=sig, u_out=u)
+            eps_h.copy_(eps, non_blocking=True)
+            return info
+
+        for _ in range(1):
+            e2e_step()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        esweeps = 0
+        for _ in range(args.steps):
+            esweeps += e2e_step().iters
+        f1.record(stream)
+        barrier()
+        esecs = torch.tensor([f0.elapsed_time(f1) / 1e3], dtype=torch.float64, device=dev)
+        evox = torch.tensor([float(nvox) * esweeps], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(esecs, op=dist.ReduceOp.MAX)
+            dist.all_reduce(evox, op=dist.ReduceOp.SUM)
+        e2e = {"value": evox.item() / esecs.item(), "unit": UNIT,
+               "h2d_bytes_per_step": int(ph_h.numel() * ph_h.element_size() + b_h.numel() * b_h.element_size()),
+               "d2h_bytes_per_step": int(eps_h.numel() * eps_h.element_size())}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, peak_kind = peaks()
+    g_avg_ms = g_ms / max(g_launches, 1)
+    alg = green_algorithmic_bytes(p.dims)
+    achieved = alg / (g_avg_ms / 1e3) / 1e9
+    traffic = traffic_record(p.dims)
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, tcpu, cores = oracle_sample(p, sweeps=1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one Algorithm-1 sweep of the same {args.n}^3 problem (oracle setup untimed), "
+                         f"{tcpu:.1f} s, FP64 numpy/scipy single thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(p, args, world),
+        "solves_per_s": solves / secs,
+        "sweeps_per_solve": sweeps / args.steps,
+        "final_resid": infos[-1].resid,
+        "roofline": {"bound": "hbm", "kernel": "fused z/Green pass (k_zgreen<float,256>)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg, "avg_launch_ms": g_avg_ms,
+                     "launches_timed": g_launches},
+        "kernels_ms_per_launch": kern,
+        "bytes_per_voxel_iter_design": 230.6,
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

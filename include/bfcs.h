@@ -1,0 +1,212 @@
+/*
+ * bfcs.h - C ABI of the GB300 (sm_103a) FFT solver for periodic linear-elastic
+ * composites loaded by a body force with compact support (BFCS).
+ *
+ * Method: V. A. Buryachenko, "New RVE concept and FFT methods in micromechanics
+ * of composites subjected to body force with compact support".  The solver runs
+ * the modified basic scheme (Algorithm 1, Eqs. 5.7-5.10) for the modified
+ * Lippmann-Schwinger equation (Eq. 2.14, Fourier form Eqs. 5.3-5.4) and the
+ * translated averaging of Eqs. 3.3-3.7.
+ *
+ * Conventions shared by every call
+ *  - Grid: nx, ny, nz even (Eq. 4.1); each in {4,6,8,12,16,24,32,48,64,96,128,
+ *    192,256}.  Voxel (x, y, z) has linear index x + nx*(y + ny*z); h = 1.
+ *  - Symmetric tensors: 6 components in the order xx, yy, zz, yz, xz, xy, with
+ *    tensorial (not engineering) shears, stored component-major (SoA): component
+ *    c of voxel v at [c*N + v], N = nx*ny*nz.  Vectors: 3 components, same way.
+ *  - Phase maps: int8 per voxel, phase id 0 = matrix, ids >= 1 = inclusions
+ *    (the indicator V of Eqs. 3.5-3.6 is phase != 0).
+ *  - Memory: "dev" arguments are device pointers (for example torch tensor
+ *    data_ptr()), "host" arguments host pointers.  The caller owns every buffer
+ *    it passes; a plan owns its workspace.  Element types of real fields follow
+ *    the plan precision: float for BFCS_FP32, double for BFCS_FP64.
+ *  - Streams: all device work of a plan is ordered on the plan's stream.  The
+ *    solve calls return when their results are written (they wait on the stream
+ *    with a bounded host-side wait; an expired wait returns BFCS_ERR_TIMEOUT).
+ *  - Status: 0 = OK, > 0 = completed with a warning, < 0 = error (see below).
+ *    On error the output buffers are unspecified.
+ *  - Wavevector (where the paper writes F(grad f) = i k f_hat, Eq. 4.8):
+ *    xi_a = 2 pi k_a / N_a with signed k_a, and xi_a = 0 on the Nyquist index
+ *    k_a = N_a/2 (spectral differentiation for even N).  Modes with xi = 0 other
+ *    than k = 0 carry neither strain fluctuation nor load.
+ */
+#ifndef BFCS_H
+#define BFCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes */
+#define BFCS_OK 0
+#define BFCS_NOT_CONVERGED 1          /* maxit reached; result of the last sweep written */
+#define BFCS_ERR_INVALID_ARG (-1)     /* bad size, pointer, phase id, tolerance, C0 ... */
+#define BFCS_ERR_NONZERO_MEAN (-2)    /* body force not self-equilibrated (Eq. 2.5) */
+#define BFCS_ERR_OOM (-3)             /* workspace allocation failed */
+#define BFCS_ERR_CUDA (-4)            /* a CUDA runtime call failed */
+#define BFCS_ERR_TIMEOUT (-5)         /* bounded wait on the stream expired */
+#define BFCS_ERR_DIVERGED (-6)        /* NaN/Inf residual */
+#define BFCS_ERR_UNSUPPORTED (-7)     /* feature not available in this build */
+
+/* ---- plan flags */
+#define BFCS_FP32 0                   /* FP32 fields and FFTs, FP64 residual sums */
+#define BFCS_FP64 1                   /* FP64 throughout */
+
+#define BFCS_MAX_PHASES 16
+
+typedef struct bfcs_plan_s* bfcs_plan;
+
+/* Isotropic phase, L = 3k N1 + 2 mu N2 written with Lame constants (Sec. 2). */
+typedef struct { double lambda, mu; } bfcs_lame;
+
+typedef struct {
+  int iters;            /* sweeps run (each sweep = Eqs. 5.7-5.10 once) */
+  int status;           /* same value the call returned for this solve */
+  double resid;         /* residual (Eq. 5.11 reading below) of the returned strain, FP64 */
+  double resid_prev;    /* residual of the iterate that triggered the stop */
+  int precision_path;   /* 0 = FP32 sweeps, 1 = FP64 sweeps */
+  int pad;
+  double ms;            /* host wall time of the call, milliseconds */
+} bfcs_info;
+
+/* One member of a batched solve (see bfcs_solve for field meanings). */
+typedef struct {
+  const int8_t* phase;          /* dev, N */
+  const void* b;                /* dev, 3 x N */
+  double E[6];                  /* prescribed mean strain */
+  int shift[3];                 /* microstructure translation chi (Eq. 3.3) */
+  const void* eps_init;         /* dev 6 x N or NULL */
+  void* eps_out;                /* dev 6 x N */
+  void* sig_out;                /* dev 6 x N or NULL */
+  void* u_out;                  /* dev 3 x N or NULL */
+} bfcs_problem;
+
+/*
+ * bfcs_plan_create - workspace and precision for solves on an nx*ny*nz grid.
+ *  out:       receives the plan handle (host).
+ *  nx,ny,nz:  grid (BFUC of Eq. 2.7 / Sec. 4 unit cell), even, supported sizes.
+ *  max_batch: >= 1; members of bfcs_solve_batched are run in groups of at most
+ *             this many.
+ *  flags:     BFCS_FP32 or BFCS_FP64.
+ *  stream:    cudaStream_t to order work on (NULL = legacy default stream).
+ * Allocates about (6 + 3 + 3) * nz*ny*(nx/2+4) complex values of workspace.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int flags, void* stream);
+int bfcs_plan_destroy(bfcs_plan plan);
+
+/*
+ * bfcs_voxelize - phase map of spheres in a periodic unit cell (Eqs. 2.21, 3.3).
+ *  spheres: host, nsph rows of 5 int32 (X, Y, Z, T, phase): doubled centre in
+ *           cell coordinates and T = floor((2R)^2).  A voxel with doubled centre
+ *           (2i+1, 2j+1, 2k+1) (cell coordinates) is inside when its squared
+ *           periodic minimum-image distance on the doubled grid is <= T; the
+ *           last containing sphere wins; otherwise phase 0.
+ *  cell:    cx, cy, cz dividing nx, ny, nz; the cell is tiled over the grid.
+ *  phase_out: dev, N int8.  Integer arithmetic only (bit-exact).
+ */
+int bfcs_voxelize(int nx, int ny, int nz, int cx, int cy, int cz, int nsph, const int32_t* spheres,
+                  int8_t* phase_out, void* stream);
+
+/*
+ * bfcs_body_force - BFCS field of Eq. 2.5 in the form b = (d phi/d x1, 0, 0),
+ * phi = (1 - r^2/a^2)^3 for r < a, at voxel centres i + 0.5 with the periodic
+ * minimum image about (cx, cy, cz), made mean-free in FP64.
+ *  b_out: dev, 3 x N, float (precision = BFCS_FP32) or double (BFCS_FP64).
+ */
+int bfcs_body_force(int nx, int ny, int nz, double cx, double cy, double cz, double a, int precision,
+                    void* b_out, void* stream);
+
+/*
+ * bfcs_solve - modified basic scheme, Algorithm 1 (Eqs. 5.7-5.10).
+ *  phase:   dev, N int8 phase ids in [0, nphases).
+ *  phases:  host, nphases (1..16) isotropic phases, phase id = index.
+ *  C0:      isotropic reference medium L0 (Eqs. 2.16-2.18); mu0 > 0, lambda0+2mu0 > 0.
+ *  b:       dev, 3 x N body force, mean-free (Eq. 2.5), else BFCS_ERR_NONZERO_MEAN.
+ *  E:       host, 6: prescribed mean strain; sets the k = 0 mode (Eq. 5.4 with
+ *           the classical term of Eq. 2.24).
+ *  tol:     stop once the residual r(eps^s) <= tol (tol = 0: run maxit sweeps).
+ *  maxit:   >= 0 sweeps at most.
+ *  eps_init: dev 6 x N warm start or NULL (NULL: eps^0 = eps^{b(0)} + E).
+ *  eps_out: dev 6 x N, the returned strain eps^S (S = sweeps run).
+ *  sig_out: dev 6 x N or NULL, sigma^S = L(x) eps^S.
+ *  u_out:   dev 3 x N or NULL, the periodic displacement with sym grad u =
+ *           eps^S - <eps^S> and zero mean (Eqs. 2.9-2.10).
+ *  info:    host, filled on return (may be NULL).
+ * Sweep s forms tau^s = (L - L0) eps^s, its transform, the residual r(eps^s)
+ * and eps^{s+1}; the call stops after the first sweep with r(eps^s) <= tol.
+ * Residual (reading of Eq. 5.11): r = ||i xi.sigma_hat + b_hat|| / D over modes
+ * with xi != 0, D = ||b_hat|| + (2 pi / max N_a) |sigma_hat(0)|.  With a warm
+ * start r(eps^0) is not evaluated (reported as +inf).
+ * Returns OK, NOT_CONVERGED, INVALID_ARG, NONZERO_MEAN, CUDA, TIMEOUT, DIVERGED.
+ */
+int bfcs_solve(bfcs_plan plan, const int8_t* phase, int nphases, const bfcs_lame* phases, bfcs_lame C0,
+               const void* b, const double E[6], double tol, int maxit, const void* eps_init,
+               void* eps_out, void* sig_out, void* u_out, bfcs_info* info);
+
+/*
+ * bfcs_solve_batched - `batch` independent solves sharing the plan's grid,
+ * phases, C0, tol and maxit; member m reads its phase map translated by
+ * problems[m].shift (phase(x) = phase0(x - chi), Eq. 3.3).
+ *  problems: host array of `batch` members; infos: host array (may be NULL).
+ * Returns the most severe member status.
+ */
+int bfcs_solve_batched(bfcs_plan plan, int batch, const bfcs_problem* problems, int nphases,
+                       const bfcs_lame* phases, bfcs_lame C0, double tol, int maxit, bfcs_info* infos);
+
+/*
+ * bfcs_translate_average - translated averaging (Eqs. 3.3-3.6) and the
+ * dataset record of Eq. 3.7: for each integer shift chi_m (host, 3*nshift int32,
+ * (x, y, z)) the microstructure phase(x) = phase0(x - chi_m) is solved with b
+ * fixed, and the fields are summed in FP64 and divided by nshift:
+ *  avg_out: dev, 30 x N double: <u> (3), <u>^(1) (3), <eps> (6), <eps>^(1) (6),
+ *           <sigma> (6), <sigma>^(1) (6); ^(1) = weighted by the inclusion
+ *           indicator V(x, chi) and still divided by nshift (Eqs. 3.5-3.6).
+ *  hits_out: dev, N int32 or NULL: number of shifts with V(x, chi) = 1.
+ *  infos: host, nshift entries or NULL.
+ */
+int bfcs_translate_average(bfcs_plan plan, const int8_t* phase, int nphases, const bfcs_lame* phases,
+                           bfcs_lame C0, const void* b, const double E[6], int nshift,
+                           const int32_t* shifts, double tol, int maxit, double* avg_out,
+                           int32_t* hits_out, bfcs_info* infos);
+
+/*
+ * bfcs_surrogate_infer - learned warm start / surrogate (3D U-net, BF16).
+ * Not available in this build: returns BFCS_ERR_UNSUPPORTED.
+ */
+int bfcs_surrogate_infer(bfcs_plan plan, const void* weights, const void* b, const int8_t* phase,
+                         int nphases, const bfcs_lame* phases, void* eps_pred);
+
+/*
+ * bfcs_fft3d - the solver's 3D real transform on its own (Eqs. 4.3-4.4):
+ *  direction -1: real (ncomp x N) -> half spectrum (ncomp x nz x ny x (nx/2+1)
+ *  complex, unnormalised, Eq. 4.3); +1: half spectrum -> real with the 1/|N| of
+ *  Eq. 4.4 NOT applied (multiply by 1/N yourself).  ncomp in 1..6.
+ */
+int bfcs_fft3d(bfcs_plan plan, int direction, int ncomp, const void* in, void* out);
+
+/* Measurement hooks.
+ * bfcs_kernel_launches: number of kernels this library has launched in the
+ *   process so far (every launch, including sweeps skipped on device after
+ *   convergence).
+ * bfcs_profile_kernel: kind 0 = off, 1 = x pass, 2 = y passes, 3 = fused
+ *   z/Green pass.  While on, every launch of that kind inside an executed sweep
+ *   of a solve on this plan is bracketed by CUDA events on the plan's stream.
+ * bfcs_profile_read: launches timed and their summed duration (ms) since the
+ *   last read; resets the totals.  Both return a status. */
+long long bfcs_kernel_launches(void);
+int bfcs_profile_kernel(bfcs_plan plan, int kind);
+int bfcs_profile_read(bfcs_plan plan, long long* launches, double* total_ms);
+
+/* Residual history of the last solve on the plan: copies min(cap, iters)
+ * values r(eps^s) into hist (host); returns the count or a negative status. */
+int bfcs_last_history(bfcs_plan plan, double* hist, int cap);
+
+const char* bfcs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFCS_H */

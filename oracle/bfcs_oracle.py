@@ -9,7 +9,7 @@ It is a plain, slow, obviously-correct restatement of the paper's method
 subjected to body force with compact support"):
 
   * DFT conventions, Eqs. 4.3-4.5 (forward omega^{-kn}, inverse with 1/|N|),
-    evaluated with numpy's FFT as the library primitive.
+    evaluated with scipy's FFT (single thread) as the library primitive.
   * Strain Green operator U0 in Fourier space, Eqs. 2.16-2.18, contracted as a
     full fourth-order tensor.
   * Modified Lippmann-Schwinger equation, Eqs. 2.14 / 5.3-5.4, solved by the
@@ -53,6 +53,7 @@ translation equivariance, averaging invariants).
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft as sfft
 
 # (i, j) of each stored component, Voigt-like order xx yy zz yz xz xy
 COMP = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
@@ -123,13 +124,13 @@ def body_force(dims, centre, a):
 
 # ---------------------------------------------------------------- transforms
 def fft3(f):
-    """Eq. 4.3 on the last three axes (numpy FFT as the library primitive)."""
-    return np.fft.fftn(f, axes=(-3, -2, -1))
+    """Eq. 4.3 on the last three axes (library FFT as the primitive)."""
+    return sfft.fftn(f, axes=(-3, -2, -1))
 
 
 def ifft3(fh):
     """Eq. 4.4 on the last three axes, including 1/|N|."""
-    return np.fft.ifftn(fh, axes=(-3, -2, -1))
+    return sfft.ifftn(fh, axes=(-3, -2, -1))
 
 
 def wavevectors(dims):
@@ -169,10 +170,13 @@ def u0_apply(tau_hat, xi, lam0, mu0):
     U0 = U1/(4 mu0) + (lam0+mu0)/(mu0 (lam0+2 mu0)) U2,
     U1_ijkl = -(d_ki xi_l xi_j + d_li xi_k xi_j + d_kj xi_l xi_i + d_lj xi_k xi_i)/|xi|^2,
     U2_ijkl = xi_i xi_j xi_k xi_l / |xi|^4.   Modes with xi = 0 give 0.
+    With P_ab = xi_a xi_b / |xi|^2 this reads U1_ijkl = -(d_ki P_lj + d_li P_kj
+    + d_kj P_li + d_lj P_ki) and U2_ijkl = P_ij P_kl.
     """
     q = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
     nz = q > 0
     iq = np.where(nz, 1.0 / np.where(nz, q, 1.0), 0.0)
+    P = [[xi[a] * xi[b] * iq for b in range(3)] for a in range(3)]
     c1 = 1.0 / (4.0 * mu0)
     c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0))
     t = to_full(tau_hat)
@@ -182,29 +186,28 @@ def u0_apply(tau_hat, xi, lam0, mu0):
         acc = 0.0
         for k in range(3):
             for l in range(3):
-                u1 = -(d[k, i] * xi[l] * xi[j] + d[l, i] * xi[k] * xi[j]
-                       + d[k, j] * xi[l] * xi[i] + d[l, j] * xi[k] * xi[i]) * iq
-                u2 = xi[i] * xi[j] * xi[k] * xi[l] * iq * iq
+                u1 = 0.0
+                for (delta, pp) in ((d[k, i], P[l][j]), (d[l, i], P[k][j]),
+                                    (d[k, j], P[l][i]), (d[l, j], P[k][i])):
+                    if delta:
+                        u1 = u1 - delta * pp
+                u2 = P[i][j] * P[k][l]
                 acc = acc + (c1 * u1 + c2 * u2) * t[k][l]
         out[a] = acc
     return out
 
 
 def g0_apply(v_hat, xi, lam0, mu0):
-    """w = G0(xi) v with G0 = K0^{-1}, K0_ik = mu0 |xi|^2 d_ik + (lam0+mu0) xi_i xi_k
-    (inverse of the Navier operator of Eqs. 2.6, 2.8; solved mode by mode)."""
-    shape = np.broadcast_shapes(xi[0].shape, xi[1].shape, xi[2].shape)
-    X = [np.broadcast_to(x, shape).ravel() for x in xi]
-    q = X[0] ** 2 + X[1] ** 2 + X[2] ** 2
-    K = np.empty((q.size, 3, 3))
-    for i in range(3):
-        for k in range(3):
-            K[:, i, k] = (lam0 + mu0) * X[i] * X[k] + (mu0 * q if i == k else 0.0)
-    nzm = q > 0
-    V = np.stack([np.broadcast_to(v_hat[i], shape).ravel() for i in range(3)], axis=-1)
-    W = np.zeros_like(V)
-    W[nzm] = np.linalg.solve(K[nzm], V[nzm][..., None])[..., 0]
-    return np.stack([W[:, i].reshape(shape) for i in range(3)])
+    """w = G0(xi) v, G0 = K0^{-1} the inverse of the isotropic acoustic tensor
+    K0_ik = mu0 |xi|^2 d_ik + (lam0+mu0) xi_i xi_k of the Navier operator
+    (Eqs. 2.6, 2.8): G0 = [d_ik - (lam0+mu0)/(lam0+2 mu0) xi_i xi_k/|xi|^2]/(mu0 |xi|^2).
+    Modes with xi = 0 give 0."""
+    q = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+    nz = q > 0
+    iq = np.where(nz, 1.0 / np.where(nz, q, 1.0), 0.0)
+    c = (lam0 + mu0) / (lam0 + 2.0 * mu0)
+    xv = xi[0] * v_hat[0] + xi[1] * v_hat[1] + xi[2] * v_hat[2]
+    return np.stack([(v_hat[i] - c * xi[i] * xv * iq) * iq / mu0 for i in range(3)])
 
 
 def sym_grad_hat(u_hat, xi):

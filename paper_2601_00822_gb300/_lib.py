@@ -1,0 +1,111 @@
+"""ctypes loader of libbfcs.so with the C-ABI signatures of include/bfcs.h.
+
+The library is built in-tree on first use (paper_2601_00822_gb300/_build).
+There is no fallback: if the library cannot be built or loaded, load() raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_LOCK = threading.Lock()
+_LIB = None
+
+OK = 0
+NOT_CONVERGED = 1
+ERR_INVALID_ARG = -1
+ERR_NONZERO_MEAN = -2
+ERR_OOM = -3
+ERR_CUDA = -4
+ERR_TIMEOUT = -5
+ERR_DIVERGED = -6
+ERR_UNSUPPORTED = -7
+FP32 = 0
+FP64 = 1
+
+# every symbol declared in include/bfcs.h
+EXPORTS = (
+    "bfcs_plan_create", "bfcs_plan_destroy", "bfcs_voxelize", "bfcs_body_force", "bfcs_solve",
+    "bfcs_solve_batched", "bfcs_translate_average", "bfcs_surrogate_infer", "bfcs_fft3d",
+    "bfcs_last_history", "bfcs_status_string", "bfcs_kernel_launches", "bfcs_profile_kernel",
+    "bfcs_profile_read",
+)
+
+
+class Lame(C.Structure):
+    _fields_ = [("lam", C.c_double), ("mu", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("resid", C.c_double),
+                ("resid_prev", C.c_double), ("precision_path", C.c_int), ("pad", C.c_int),
+                ("ms", C.c_double)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("phase", C.c_void_p), ("b", C.c_void_p), ("E", C.c_double * 6),
+                ("shift", C.c_int * 3), ("eps_init", C.c_void_p), ("eps_out", C.c_void_p),
+                ("sig_out", C.c_void_p), ("u_out", C.c_void_p)]
+
+
+def _declare(lib):
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    lib.bfcs_plan_create.argtypes = [C.POINTER(vp), i, i, i, i, i, vp]
+    lib.bfcs_plan_destroy.argtypes = [vp]
+    lib.bfcs_voxelize.argtypes = [i, i, i, i, i, i, i, vp, vp, vp]
+    lib.bfcs_body_force.argtypes = [i, i, i, d, d, d, d, i, vp, vp]
+    lib.bfcs_solve.argtypes = [vp, vp, i, C.POINTER(Lame), Lame, vp, C.POINTER(d), d, i, vp, vp, vp,
+                               vp, C.POINTER(Info)]
+    lib.bfcs_solve_batched.argtypes = [vp, i, C.POINTER(Problem), i, C.POINTER(Lame), Lame, d, i,
+                                       C.POINTER(Info)]
+    lib.bfcs_translate_average.argtypes = [vp, vp, i, C.POINTER(Lame), Lame, vp, C.POINTER(d), i, vp,
+                                           d, i, vp, vp, C.POINTER(Info)]
+    lib.bfcs_surrogate_infer.argtypes = [vp, vp, vp, vp, i, C.POINTER(Lame), vp]
+    lib.bfcs_fft3d.argtypes = [vp, i, i, vp, vp]
+    lib.bfcs_last_history.argtypes = [vp, C.POINTER(d), i]
+    lib.bfcs_kernel_launches.argtypes = []
+    lib.bfcs_profile_kernel.argtypes = [vp, i]
+    lib.bfcs_profile_read.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(d)]
+    lib.bfcs_status_string.argtypes = [i]
+    lib.bfcs_status_string.restype = C.c_char_p
+    for name in EXPORTS:
+        if name != "bfcs_status_string":
+            getattr(lib, name).restype = C.c_int
+    lib.bfcs_kernel_launches.restype = C.c_longlong
+    return lib
+
+
+def library_path(build: bool = True) -> str:
+    from . import build as _build
+    if build:
+        return _build.build()
+    return _build.LIB_PATH
+
+
+def load(build: bool = True):
+    """Build (if needed) and dlopen libbfcs.so; raises if anything is missing."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = library_path(build)
+            if not os.path.exists(path):
+                raise RuntimeError(f"libbfcs.so not found at {path}; run the build first")
+            _LIB = _declare(C.CDLL(path, mode=C.RTLD_GLOBAL))
+        return _LIB
+
+
+def status_string(code: int) -> str:
+    return load().bfcs_status_string(code).decode()
+
+
+class BfcsError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: status {code} ({status_string(code)})")
+
+
+def check(code: int, what: str, allow=(OK,)) -> int:
+    if code not in allow:
+        raise BfcsError(code, what)
+    return code

@@ -1,0 +1,225 @@
+"""Thin Python binding of the C ABI (include/bfcs.h).
+
+Only argument marshalling lives here: torch tensors supply device memory and
+the current CUDA stream; every step of the solver runs in libbfcs.so.
+Field tensors are contiguous, shaped (components, nz, ny, nx), float32 for
+'fp32' plans and float64 for 'fp64' plans.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check_tensor(t, shape, dtype, what):
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{what}: need a contiguous CUDA tensor {tuple(shape)} {dtype}, got "
+                         f"{tuple(t.shape)} {t.dtype} on {t.device}")
+
+
+def _lames(phases):
+    arr = (_lib.Lame * len(phases))()
+    for i, (lam, mu) in enumerate(phases):
+        arr[i].lam, arr[i].mu = float(lam), float(mu)
+    return arr
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    status: int
+    resid: float
+    resid_prev: float
+    precision_path: int
+    ms: float
+
+    @staticmethod
+    def of(info: _lib.Info) -> "SolveInfo":
+        return SolveInfo(info.iters, info.status, info.resid, info.resid_prev, info.precision_path,
+                         info.ms)
+
+
+def kernel_launches() -> int:
+    """bfcs_kernel_launches: kernels launched by the library so far in this process."""
+    return int(_lib.load().bfcs_kernel_launches())
+
+
+def voxelize(dims, cell, spheres, device="cuda", stream=None) -> torch.Tensor:
+    """bfcs_voxelize: int8 phase map (nz, ny, nx) of spheres (n, 5) int32 in a periodic cell."""
+    lib = _lib.load()
+    nx, ny, nz = dims
+    sph = np.ascontiguousarray(np.asarray(spheres, dtype=np.int32).reshape(-1, 5))
+    out = torch.empty((nz, ny, nx), dtype=torch.int8, device=device)
+    _lib.check(lib.bfcs_voxelize(nx, ny, nz, cell[0], cell[1], cell[2], sph.shape[0],
+                                 sph.ctypes.data_as(C.c_void_p), _ptr(out), _stream_ptr(stream)),
+               "bfcs_voxelize")
+    return out
+
+
+def body_force(dims, centre, a, precision="fp32", device="cuda", stream=None) -> torch.Tensor:
+    """bfcs_body_force: mean-free BFCS field (3, nz, ny, nx)."""
+    lib = _lib.load()
+    nx, ny, nz = dims
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out = torch.empty((3, nz, ny, nx), dtype=dt, device=device)
+    flag = _lib.FP64 if precision == "fp64" else _lib.FP32
+    _lib.check(lib.bfcs_body_force(nx, ny, nz, float(centre[0]), float(centre[1]), float(centre[2]),
+                                   float(a), flag, _ptr(out), _stream_ptr(stream)), "bfcs_body_force")
+    return out
+
+
+class Plan:
+    """bfcs_plan_create / bfcs_plan_destroy with the solver calls as methods."""
+
+    def __init__(self, dims, precision="fp32", max_batch=1, stream=None):
+        self.lib = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        flag = _lib.FP64 if precision == "fp64" else _lib.FP32
+        nx, ny, nz = self.dims
+        _lib.check(self.lib.bfcs_plan_create(C.byref(h), nx, ny, nz, int(max_batch), flag,
+                                             _stream_ptr(self.stream)), "bfcs_plan_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.bfcs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _shape(self, ncomp):
+        nx, ny, nz = self.dims
+        return (ncomp, nz, ny, nx)
+
+    def _alloc(self, ncomp):
+        return torch.empty(self._shape(ncomp), dtype=self.dtype, device="cuda")
+
+    def solve(self, phase, phases, c0, b, E=(0.0,) * 6, tol=1e-6, maxit=10000, eps_init=None,
+              eps_out=None, sig_out=None, u_out=None, want_sig=True, want_u=True,
+              allow=(_lib.OK, _lib.NOT_CONVERGED)):
+        """bfcs_solve; returns (eps, sig or None, u or None, SolveInfo)."""
+        nx, ny, nz = self.dims
+        _check_tensor(phase, (nz, ny, nx), torch.int8, "phase")
+        _check_tensor(b, self._shape(3), self.dtype, "b")
+        _check_tensor(eps_init, self._shape(6), self.dtype, "eps_init")
+        eps_out = eps_out if eps_out is not None else self._alloc(6)
+        if sig_out is None and want_sig:
+            sig_out = self._alloc(6)
+        if u_out is None and want_u:
+            u_out = self._alloc(3)
+        for t, n, w in ((eps_out, 6, "eps_out"), (sig_out, 6, "sig_out"), (u_out, 3, "u_out")):
+            _check_tensor(t, self._shape(n), self.dtype, w)
+        lam = _lames(phases)
+        e = (C.c_double * 6)(*[float(v) for v in E])
+        info = _lib.Info()
+        code = self.lib.bfcs_solve(self.handle, _ptr(phase), len(phases), lam, _lib.Lame(*c0), _ptr(b), e,
+                                   float(tol), int(maxit), _ptr(eps_init), _ptr(eps_out), _ptr(sig_out),
+                                   _ptr(u_out), C.byref(info))
+        _lib.check(code, "bfcs_solve", allow)
+        return eps_out, sig_out, u_out, SolveInfo.of(info)
+
+    def solve_batched(self, members, phases, c0, tol=1e-6, maxit=10000,
+                      allow=(_lib.OK, _lib.NOT_CONVERGED)):
+        """bfcs_solve_batched; members: list of dicts with phase, b, E, shift, eps_init,
+        eps_out, sig_out, u_out (outputs allocated when missing). Returns (members, infos)."""
+        n = len(members)
+        arr = (_lib.Problem * n)()
+        for m, mem in enumerate(members):
+            mem.setdefault("eps_out", self._alloc(6))
+            for key, comp in (("sig_out", 6), ("u_out", 3)):
+                if key not in mem:
+                    mem[key] = self._alloc(comp)
+            arr[m].phase = mem["phase"].data_ptr()
+            arr[m].b = mem["b"].data_ptr()
+            arr[m].E = (C.c_double * 6)(*[float(v) for v in mem.get("E", (0.0,) * 6)])
+            arr[m].shift = (C.c_int * 3)(*[int(v) for v in mem.get("shift", (0, 0, 0))])
+            arr[m].eps_init = mem["eps_init"].data_ptr() if mem.get("eps_init") is not None else None
+            arr[m].eps_out = mem["eps_out"].data_ptr()
+            arr[m].sig_out = mem["sig_out"].data_ptr() if mem["sig_out"] is not None else None
+            arr[m].u_out = mem["u_out"].data_ptr() if mem["u_out"] is not None else None
+        infos = (_lib.Info * max(n, 1))()
+        code = self.lib.bfcs_solve_batched(self.handle, n, arr, len(phases), _lames(phases),
+                                           _lib.Lame(*c0), float(tol), int(maxit), infos)
+        _lib.check(code, "bfcs_solve_batched", allow)
+        return members, [SolveInfo.of(infos[m]) for m in range(n)]
+
+    def translate_average(self, phase, phases, c0, b, shifts, E=(0.0,) * 6, tol=1e-6, maxit=10000,
+                          allow=(_lib.OK, _lib.NOT_CONVERGED)):
+        """bfcs_translate_average; returns (avg (30, nz, ny, nx) float64, hits int32, infos)."""
+        nx, ny, nz = self.dims
+        sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.int32).reshape(-1, 3))
+        avg = torch.empty((30, nz, ny, nx), dtype=torch.float64, device="cuda")
+        hits = torch.empty((nz, ny, nx), dtype=torch.int32, device="cuda")
+        infos = (_lib.Info * sh.shape[0])()
+        e = (C.c_double * 6)(*[float(v) for v in E])
+        code = self.lib.bfcs_translate_average(self.handle, _ptr(phase), len(phases), _lames(phases),
+                                               _lib.Lame(*c0), _ptr(b), e, sh.shape[0],
+                                               sh.ctypes.data_as(C.c_void_p), float(tol), int(maxit),
+                                               _ptr(avg), _ptr(hits), infos)
+        _lib.check(code, "bfcs_translate_average", allow)
+        return avg, hits, [SolveInfo.of(infos[m]) for m in range(sh.shape[0])]
+
+    def fft3d(self, x, direction=-1):
+        """bfcs_fft3d: forward real (c, nz, ny, nx) -> complex (c, nz, ny, nx/2+1) or back
+        (inverse without the 1/N factor)."""
+        nx, ny, nz = self.dims
+        if direction < 0:
+            c = x.shape[0]
+            _check_tensor(x, self._shape(c), self.dtype, "x")
+            cdt = torch.complex128 if self.dtype == torch.float64 else torch.complex64
+            out = torch.empty((c, nz, ny, nx // 2 + 1), dtype=cdt, device="cuda")
+        else:
+            c = x.shape[0]
+            out = self._alloc(c)
+        _lib.check(self.lib.bfcs_fft3d(self.handle, int(direction), int(c), _ptr(x), _ptr(out)),
+                   "bfcs_fft3d")
+        return out
+
+    def profile(self, kind):
+        """bfcs_profile_kernel: 0 off, 1 x pass, 2 y passes, 3 fused z/Green pass."""
+        _lib.check(self.lib.bfcs_profile_kernel(self.handle, int(kind)), "bfcs_profile_kernel")
+
+    def profile_read(self):
+        """bfcs_profile_read: (launches timed, summed milliseconds) since the last read."""
+        n = C.c_longlong()
+        ms = C.c_double()
+        _lib.check(self.lib.bfcs_profile_read(self.handle, C.byref(n), C.byref(ms)), "bfcs_profile_read")
+        return n.value, ms.value
+
+    def history(self, cap=1 << 16):
+        """bfcs_last_history: residuals r(eps^s) of the last solve."""
+        buf = (C.c_double * cap)()
+        n = self.lib.bfcs_last_history(self.handle, buf, cap)
+        if n < 0:
+            raise _lib.BfcsError(n, "bfcs_last_history")
+        return np.array(buf[:n])

@@ -1,0 +1,226 @@
+// Shared device building blocks of the BFCS solver: complex arithmetic,
+// register-resident small DFTs and the shared-memory four-step line FFT.
+//
+// Transform convention (Eqs. 4.3-4.5 of the paper): forward uses
+// omega^{-kn} = exp(-2 pi i kn/N), inverse exp(+2 pi i kn/N); the 1/|N| of the
+// inverse (Eq. 4.4) is folded into the Green-operator pass, so every transform
+// here is unnormalised.  `dir` is -1 for forward, +1 for inverse.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bfcs {
+
+template <typename R> struct alignas(2 * sizeof(R)) C2 { R x, y; };
+
+template <typename R> __host__ __device__ __forceinline__ C2<R> mk(R a, R b) { C2<R> c; c.x = a; c.y = b; return c; }
+template <typename R> __device__ __forceinline__ C2<R> operator+(C2<R> a, C2<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ C2<R> operator-(C2<R> a, C2<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R> __device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R> __device__ __forceinline__ C2<R> conjg(C2<R> a) { return mk<R>(a.x, -a.y); }
+template <typename R> __device__ __forceinline__ C2<R> scale(C2<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+// multiply by dir * i, dir = +-1
+template <typename R, int DIR> __device__ __forceinline__ C2<R> mul_di(C2<R> a) {
+  return DIR > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x);
+}
+
+// cos(2 pi j / 48), exact quarter-wave table extended by symmetry; every radix
+// used below divides 48, so these are all the constants the register DFTs need.
+__host__ __device__ constexpr double q48(int j) {
+  return j == 0 ? 1.0 : j == 1 ? 0.9914448613738104 : j == 2 ? 0.9659258262890683
+       : j == 3 ? 0.9238795325112867 : j == 4 ? 0.8660254037844386 : j == 5 ? 0.7933533402912352
+       : j == 6 ? 0.7071067811865476 : j == 7 ? 0.6087614290087207 : j == 8 ? 0.5
+       : j == 9 ? 0.3826834323650898 : j == 10 ? 0.25881904510252074 : j == 11 ? 0.1305261922200516
+       : 0.0;
+}
+__host__ __device__ constexpr double cos48(int j) {
+  return (j % 48 + 48) % 48 <= 12 ? q48((j % 48 + 48) % 48)
+       : (j % 48 + 48) % 48 <= 24 ? -q48(24 - (j % 48 + 48) % 48)
+       : (j % 48 + 48) % 48 <= 36 ? -q48((j % 48 + 48) % 48 - 24)
+       : q48(48 - (j % 48 + 48) % 48);
+}
+__host__ __device__ constexpr double sin48(int j) { return cos48(j - 12); }
+
+// ------------------------------------------------------------------ register DFTs
+// X[k] = sum_n x[n] exp(DIR 2 pi i n k / RADIX), in place, natural order.
+template <typename R, int RADIX, int DIR> struct Dft;
+
+template <typename R, int DIR> struct Dft<R, 1, DIR> {
+  static __device__ __forceinline__ void run(C2<R>*) {}
+};
+template <typename R, int DIR> struct Dft<R, 2, DIR> {
+  static __device__ __forceinline__ void run(C2<R>* x) {
+    C2<R> a = x[0], b = x[1];
+    x[0] = a + b; x[1] = a - b;
+  }
+};
+template <typename R, int DIR> struct Dft<R, 3, DIR> {
+  static __device__ __forceinline__ void run(C2<R>* x) {
+    const R h = R(0.8660254037844386);   // sin(2 pi / 3)
+    C2<R> t1 = x[1] + x[2];
+    C2<R> t2 = x[0] - scale(t1, R(0.5));
+    C2<R> t3 = mul_di<R, DIR>(scale(x[1] - x[2], h));
+    x[0] = x[0] + t1; x[1] = t2 + t3; x[2] = t2 - t3;
+  }
+};
+template <typename R, int DIR> struct Dft<R, 4, DIR> {
+  static __device__ __forceinline__ void run(C2<R>* x) {
+    C2<R> a = x[0] + x[2], b = x[0] - x[2], c = x[1] + x[3];
+    C2<R> d = mul_di<R, DIR>(x[1] - x[3]);
+    x[0] = a + c; x[2] = a - c; x[1] = b + d; x[3] = b - d;
+  }
+};
+
+// composite radix A*B by the four-step rule with constant twiddles:
+// n = B n1 + n2, k = k1 + A k2
+template <int RADIX> struct Split;
+template <> struct Split<6> { static constexpr int A = 3, B = 2; };
+template <> struct Split<8> { static constexpr int A = 4, B = 2; };
+template <> struct Split<12> { static constexpr int A = 4, B = 3; };
+template <> struct Split<16> { static constexpr int A = 4, B = 4; };
+
+template <typename R, int RADIX, int DIR> struct Dft {
+  static __device__ __forceinline__ void run(C2<R>* x) {
+    constexpr int A = Split<RADIX>::A, B = Split<RADIX>::B;
+    C2<R> u[B][A];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) u[n2][n1] = x[B * n1 + n2];
+      Dft<R, A, DIR>::run(u[n2]);
+#pragma unroll
+      for (int k1 = 1; k1 < A; ++k1) {
+        if (n2 * k1 == 0) continue;
+        constexpr int S = 48 / RADIX;
+        const C2<R> w = mk<R>(R(cos48(S * n2 * k1)), R(DIR * sin48(S * n2 * k1)));
+        u[n2][k1] = cmul(u[n2][k1], w);
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      C2<R> v[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) v[n2] = u[n2][k1];
+      Dft<R, B, DIR>::run(v);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) x[k1 + A * k2] = v[k2];
+    }
+  }
+};
+
+// ------------------------------------------------------------------ line FFT factorisation
+// L = R1 * R2, both register radices.  Supported lengths are the even
+// 2^a 3^b up to 256 listed here.
+template <int L> struct Fac;
+template <> struct Fac<4> { static constexpr int R1 = 2, R2 = 2; };
+template <> struct Fac<6> { static constexpr int R1 = 3, R2 = 2; };
+template <> struct Fac<8> { static constexpr int R1 = 4, R2 = 2; };
+template <> struct Fac<12> { static constexpr int R1 = 4, R2 = 3; };
+template <> struct Fac<16> { static constexpr int R1 = 4, R2 = 4; };
+template <> struct Fac<24> { static constexpr int R1 = 8, R2 = 3; };
+template <> struct Fac<32> { static constexpr int R1 = 8, R2 = 4; };
+template <> struct Fac<48> { static constexpr int R1 = 8, R2 = 6; };
+template <> struct Fac<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct Fac<96> { static constexpr int R1 = 16, R2 = 6; };
+template <> struct Fac<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct Fac<192> { static constexpr int R1 = 16, R2 = 12; };
+template <> struct Fac<256> { static constexpr int R1 = 16, R2 = 16; };
+
+template <int L> struct LineInfo {
+  static constexpr int R1 = Fac<L>::R1, R2 = Fac<L>::R2;
+  static constexpr int RMAX = R1 > R2 ? R1 : R2;
+};
+
+// Shared-memory four-step FFT over NCOL independent lines of length L stored
+// column-wise: element n of line f at s[n * NCOL + f].  Needs at least
+// NCOL * RMAX threads (one task per thread per stage so it can run in place);
+// extra threads idle.  tw[j] = exp(-2 pi i j / L) (forward sign).
+// Stage 1 (thread (f, n2)): DFT_R1 over n1 of x[R2 n1 + n2], twiddle W_L^{n2 k1}.
+// Stage 2 (thread (f, k1)): DFT_R2 over n2, output X[k1 + R1 k2].
+// Begins and ends with __syncthreads().
+template <typename R, int L, int DIR>
+__device__ __forceinline__ void fft_cols(C2<R>* s, int ncol, const C2<R>* __restrict__ tw) {
+  constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
+  const int tid = threadIdx.x;
+  __syncthreads();
+  {
+    const int f = tid % ncol, n2 = tid / ncol;
+    const bool act = n2 < R2;
+    C2<R> x[R1];
+    if (act) {
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) x[n1] = s[(R2 * n1 + n2) * ncol + f];
+      Dft<R, R1, DIR>::run(x);
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) {
+        C2<R> w = tw[(n2 * k1) % L];
+        if (DIR > 0) w.y = -w.y;
+        x[k1] = cmul(x[k1], w);
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) s[(n2 * R1 + k1) * ncol + f] = x[k1];
+    }
+  }
+  __syncthreads();
+  {
+    const int f = tid % ncol, k1 = tid / ncol;
+    const bool act = k1 < R1;
+    C2<R> y[R2];
+    if (act) {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + k1) * ncol + f];
+      Dft<R, R2, DIR>::run(y);
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) s[(k1 + R1 * k2) * ncol + f] = y[k2];
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ problem descriptors
+constexpr int kMaxPhases = 16;
+
+template <typename R> struct PhaseTab {
+  R lam[kMaxPhases], mu[kMaxPhases];     // L(x)
+  R lam1[kMaxPhases], mu1[kMaxPhases];   // L1(x) = L(x) - L0
+};
+
+// Half-spectrum geometry: [comp][z][y][kx], kx in [0, nx/2], row pitch p.
+struct Geo {
+  int nx, ny, nz;
+  int mx;           // nx/2 + 1 stored columns
+  int p;            // row pitch (complex elements)
+  long long cs;     // component stride of the spectrum (nz*ny*p)
+  long long n;      // voxel count nx*ny*nz (component stride of real fields)
+};
+
+// Signed wavevector component of index k on an axis of length n (reading: zero
+// on the Nyquist index), in units of 2 pi / n.
+__device__ __forceinline__ int signed_k(int k, int n) {
+  return (2 * k == n) ? 0 : (2 * k < n ? k : k - n);
+}
+
+// Residual bookkeeping written by the Green pass, reduced in FP64.
+struct ResidSlot { double num; double pad; };
+
+// Device-side iteration state of one solve.
+struct IterState {
+  int done;          // 1 once r <= tol (further sweeps become no-ops)
+  int iters;         // sweeps executed
+  int diverged;      // NaN/Inf seen
+  int pad;
+  double resid_last;
+  double bden;       // sqrt(sum |b_hat|^2) over modes with xi != 0
+  double resid_final;
+  double tau0[6];    // k = 0 mode of tau (unnormalised), current sweep
+};
+
+}  // namespace bfcs

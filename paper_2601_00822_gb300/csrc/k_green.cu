@@ -1,0 +1,208 @@
+// Fused z pass of a sweep: forward FFT along z of the six polarization
+// components, the Green-operator apply of the modified Lippmann-Schwinger
+// equation in Fourier space (Eqs. 5.4, 5.9 with U0 of Eqs. 2.16-2.18 and the
+// reference strain of Eqs. 2.8-2.9), the equilibrium residual partial sums
+// (Eq. 5.11) and the inverse FFT along z, on one tile held in shared memory.
+//
+// Per mode k with xi != 0, using d = tau_hat . xi:
+//   w = d - i b_hat,  v = G0(xi) w,  G0 = [I - c xi xi/|xi|^2] / (mu0 |xi|^2),
+//   c = (lam0 + mu0)/(lam0 + 2 mu0),
+//   eps_hat^{s+1} = -sym(xi (x) v)   (= U0 tau_hat + sym(i xi (x) G0 b_hat))
+// because U0 tau = -sym(xi (x) G0 (tau xi)) is the factored form of Eq. 2.16.
+// The residual numerator of eps^s is |i xi . sigma_hat + b_hat| = |d^s - d^{s-1}|,
+// since eps^s = -Gamma0 tau^{s-1} + eps^{b(0)} and xi.C0.Gamma0 tau = xi.tau.
+// The displacement consistent with eps^{s+1} is u_hat = i v (Eq. 2.9-2.10).
+// Modes with xi = 0: eps_hat = N E at k = 0 (prescribed mean strain), else 0.
+#include "kernels.h"
+
+#ifndef BFCS_R
+#define BFCS_R float
+#endif
+
+namespace bfcs {
+
+constexpr int kGreenT = 4;   // kx columns per block; 6 components -> 24 line columns
+
+template <int L> struct GCfg {
+  static constexpr int NCOL = 6 * kGreenT;
+  static constexpr int THREADS = NCOL * LineInfo<L>::RMAX;
+};
+
+template <typename R>
+__device__ __forceinline__ void g0_apply(const C2<R> g[3], const R xi[3], R q, R mu0, R c,
+                                         C2<R> v[3]) {
+  const C2<R> xg = scale(g[0], xi[0]) + scale(g[1], xi[1]) + scale(g[2], xi[2]);
+  const R iq = R(1) / q;
+  const R a = iq / mu0;
+  const R b = c * iq;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = scale(g[i] - scale(xg, b * xi[i]), a);
+}
+
+template <typename R, int L>
+__global__ void __launch_bounds__(GCfg<L>::THREADS) k_zgreen(GArgs<R> a) {
+  if (a.done != nullptr && *a.done) return;
+  constexpr int T = kGreenT;
+  constexpr int NCOL = GCfg<L>::NCOL;
+  extern __shared__ unsigned char smem_raw[];
+  C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);
+  __shared__ double red[32];
+
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int nx = a.g.nx, ny = a.g.ny, mx = a.g.mx, p = a.g.p;
+  const long long cs = a.g.cs;
+  const int ky = blockIdx.y;
+  const int col0 = blockIdx.x * T;
+  const long long zs = (long long)ny * p;          // z stride
+  const long long rowbase = (long long)ky * p;
+  const int mode = a.mode;
+
+  // ---- load the six component tiles and transform forward along z
+  if (mode != GM_INIT) {
+    for (int idx = tid; idx < NCOL * L; idx += nthr) {
+      const int col = idx % T, c = (idx / T) % 6, n = idx / NCOL;
+      const int kx = col0 + col;
+      s[n * NCOL + c * T + col] =
+          kx < mx ? a.spec[c * cs + n * zs + rowbase + kx] : mk<R>(0, 0);
+    }
+    fft_cols<R, L, -1>(s, NCOL, a.tw);
+  }
+
+  // ---- Green operators per mode
+  const R two_pi = R(6.283185307179586);
+  const R fx = two_pi / R(nx), fy = two_pi / R(ny), fz = two_pi / R(L);
+  const R mu0 = a.mu0, c0 = (a.lam0 + a.mu0) / (a.lam0 + R(2) * a.mu0);
+  const R inv_n = a.inv_n;
+  double acc = 0.0;
+  for (int idx = tid; idx < T * L; idx += nthr) {
+    const int col = idx % T, n = idx / T;
+    const int kx = col0 + col;
+    C2<R>* m = s + n * NCOL + col;                  // component c at m[c * T]
+    if (kx >= mx) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) m[c * T] = mk<R>(0, 0);
+      continue;
+    }
+    const long long gi = n * zs + rowbase + kx;     // index in a 3-component spectrum
+    R xi[3];
+    xi[0] = fx * R(signed_k(kx, nx));
+    xi[1] = fy * R(signed_k(ky, ny));
+    xi[2] = fz * R(signed_k(n, L));
+    const R q = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    const R wgt = (kx == 0 || 2 * kx == nx) ? R(1) : R(2);
+
+    if (q == R(0)) {
+      const bool k0 = (kx == 0 && ky == 0 && n == 0);
+      if (k0 && mode != GM_INIT && a.st != nullptr) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.st->tau0[c] = (double)m[c * T].x;
+      }
+      if (mode == GM_SWEEP || mode == GM_INIT) {
+        a.dprev[gi] = mk<R>(0, 0); a.dprev[cs + gi] = mk<R>(0, 0); a.dprev[2 * cs + gi] = mk<R>(0, 0);
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        m[c * T] = (mode != GM_FINAL && k0) ? mk<R>(a.E[c], R(0)) : mk<R>(0, 0);
+      continue;
+    }
+
+    C2<R> d[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+    if (mode != GM_INIT) {
+      // d_i = tau_hat_ij xi_j (xx yy zz yz xz xy)
+      const C2<R> t0 = m[0], t1 = m[T], t2 = m[2 * T], t3 = m[3 * T], t4 = m[4 * T], t5 = m[5 * T];
+      d[0] = scale(t0, xi[0]) + scale(t5, xi[1]) + scale(t4, xi[2]);
+      d[1] = scale(t5, xi[0]) + scale(t1, xi[1]) + scale(t3, xi[2]);
+      d[2] = scale(t4, xi[0]) + scale(t3, xi[1]) + scale(t2, xi[2]);
+      C2<R> dp[3] = {a.dprev[gi], a.dprev[cs + gi], a.dprev[2 * cs + gi]};
+      double r2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double ex = (double)d[i].x - (double)dp[i].x, ey = (double)d[i].y - (double)dp[i].y;
+        r2 += ex * ex + ey * ey;
+      }
+      acc += (double)wgt * r2;
+      if (mode == GM_FINAL) { d[0] = dp[0]; d[1] = dp[1]; d[2] = dp[2]; }
+    }
+    if (mode == GM_SWEEP || mode == GM_INIT) {
+      a.dprev[gi] = d[0]; a.dprev[cs + gi] = d[1]; a.dprev[2 * cs + gi] = d[2];
+    }
+    // w = d - i b_hat
+    C2<R> w[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const C2<R> bh = a.bhat[i * cs + gi];
+      w[i] = mk<R>(d[i].x + bh.y, d[i].y - bh.x);
+    }
+    C2<R> v[3];
+    g0_apply<R>(w, xi, q, mu0, c0, v);
+    if (mode == GM_FINAL) {
+      // u_hat = i v, scaled for the unnormalised inverse transforms
+#pragma unroll
+      for (int i = 0; i < 3; ++i) m[i * T] = mk<R>(-v[i].y * inv_n, v[i].x * inv_n);
+#pragma unroll
+      for (int c = 3; c < 6; ++c) m[c * T] = mk<R>(0, 0);
+    } else {
+      const R h = R(-0.5) * inv_n;
+      m[0] = scale(v[0], -xi[0] * inv_n);
+      m[T] = scale(v[1], -xi[1] * inv_n);
+      m[2 * T] = scale(v[2], -xi[2] * inv_n);
+      m[3 * T] = scale(scale(v[2], xi[1]) + scale(v[1], xi[2]), h);
+      m[4 * T] = scale(scale(v[2], xi[0]) + scale(v[0], xi[2]), h);
+      m[5 * T] = scale(scale(v[1], xi[0]) + scale(v[0], xi[1]), h);
+    }
+  }
+
+  // ---- residual partial of this block (fixed order: deterministic)
+  if (mode != GM_INIT) {
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (nthr + 31) / 32; ++w) t += red[w];
+      a.part[blockIdx.y * gridDim.x + blockIdx.x].num = t;
+    }
+  }
+
+  // ---- inverse transform along z and store
+  fft_cols<R, L, +1>(s, NCOL, a.tw);
+  const int ncs = mode == GM_FINAL ? 3 : 6;
+  for (int idx = tid; idx < NCOL * L; idx += nthr) {
+    const int col = idx % T, c = (idx / T) % 6, n = idx / NCOL;
+    const int kx = col0 + col;
+    if (kx < mx && c < ncs) a.spec[c * cs + n * zs + rowbase + kx] = s[n * NCOL + c * T + col];
+  }
+}
+
+template <typename R>
+int green_nparts(const Geo& g) {
+  return ((g.mx + kGreenT - 1) / kGreenT) * g.ny;
+}
+
+template <typename R, int L>
+static cudaError_t zgreen_L(const GArgs<R>& a, cudaStream_t st) {
+  dim3 grid((a.g.mx + kGreenT - 1) / kGreenT, a.g.ny);
+  const size_t smem = sizeof(C2<R>) * (size_t)L * GCfg<L>::NCOL;
+  cudaError_t e = cudaFuncSetAttribute(k_zgreen<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_zgreen<R, L><<<grid, GCfg<L>::THREADS, smem, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t st) {
+  switch (a.g.nz) {
+#define BFCS_G(L) case L: return zgreen_L<R, L>(a, st);
+    BFCS_G(4) BFCS_G(6) BFCS_G(8) BFCS_G(12) BFCS_G(16) BFCS_G(24) BFCS_G(32) BFCS_G(48)
+    BFCS_G(64) BFCS_G(96) BFCS_G(128) BFCS_G(192) BFCS_G(256)
+#undef BFCS_G
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_zgreen<BFCS_R>(const GArgs<BFCS_R>&, cudaStream_t);
+template int green_nparts<BFCS_R>(const Geo&);
+
+}  // namespace bfcs

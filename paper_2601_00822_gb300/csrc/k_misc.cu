@@ -1,0 +1,348 @@
+// Setup and bookkeeping kernels: phase-map voxelisation (integer), the BFCS
+// body-force field, input validation, FP64 reductions of the residual and the
+// translated-averaging accumulation (Eqs. 3.5-3.6).
+#include "kernels.h"
+
+#include <atomic>
+
+namespace bfcs {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+bool supported_len(int n) {
+  switch (n) {
+    case 4: case 6: case 8: case 12: case 16: case 24: case 32: case 48: case 64:
+    case 96: case 128: case 192: case 256: return true;
+    default: return false;
+  }
+}
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) t += red[w];
+  return t;   // valid in thread 0
+}
+
+// ---------------------------------------------------------------- a1: phase map
+// A voxel with doubled centre 2i+1 (cell coordinates) is inside sphere
+// (X, Y, Z, T, phase) when the squared periodic minimum-image distance on the
+// doubled grid is <= T; the last containing sphere wins; else phase 0.
+__device__ __forceinline__ int min_image2(int v, int n2) {   // v in doubled units, period n2 = 2n
+  int d = v % n2;
+  if (d < 0) d += n2;
+  if (d >= n2 / 2) d -= n2;
+  return d;
+}
+
+__global__ void k_voxelize(int8_t* out, int nx, int ny, int nz, int cx, int cy, int cz,
+                           const int* __restrict__ sph, int nsph) {
+  extern __shared__ int ssph[];
+  const long long n = (long long)nx * ny * nz;
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+  const int ix = 2 * (x % cx) + 1, iy = 2 * (y % cy) + 1, iz = 2 * (z % cz) + 1;
+  int ph = 0;
+  for (int base = 0; base < nsph; base += 1024) {
+    const int cnt = min(1024, nsph - base);
+    __syncthreads();
+    for (int k = threadIdx.x; k < cnt * 5; k += blockDim.x) ssph[k] = sph[base * 5 + k];
+    __syncthreads();
+    if (v < n) {
+      for (int k = 0; k < cnt; ++k) {
+        const int* S = ssph + 5 * k;
+        const int dx = min_image2(ix - S[0], 2 * cx);
+        const int dy = min_image2(iy - S[1], 2 * cy);
+        const int dz = min_image2(iz - S[2], 2 * cz);
+        if (dx * dx + dy * dy + dz * dz <= S[3]) ph = S[4];
+      }
+    }
+  }
+  if (v < n) out[v] = (int8_t)ph;
+}
+
+cudaError_t launch_voxelize(int8_t* out, int nx, int ny, int nz, int cx, int cy, int cz,
+                            const int* sph_dev, int nsph, cudaStream_t s) {
+  const long long n = (long long)nx * ny * nz;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  k_voxelize<<<grid, 256, 1024 * 5 * sizeof(int), s>>>(out, nx, ny, nz, cx, cy, cz, sph_dev, nsph);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- a2: body force
+// b1 = d phi/d x1, phi = (1 - r^2/a^2)^3 for r < a (Eq. 2.5 form), at voxel
+// centres i + 0.5, periodic minimum image about the centre; FP64, mean removed.
+__device__ __forceinline__ double bf_value(long long v, int nx, int ny, int nz, double cx, double cy,
+                                           double cz, double a) {
+  const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+  double dx = x + 0.5 - cx, dy = y + 0.5 - cy, dz = z + 0.5 - cz;
+  dx -= nx * rint(dx / nx);
+  dy -= ny * rint(dy / ny);
+  dz -= nz * rint(dz / nz);
+  const double r2 = dx * dx + dy * dy + dz * dz, a2 = a * a;
+  if (!(r2 < a2)) return 0.0;
+  const double s = 1.0 - r2 / a2;
+  return -6.0 * dx * s * s / a2;
+}
+
+constexpr int kBfBlocks = 1024;
+
+__global__ void k_bf_partial(double* part, long long n, int nx, int ny, int nz, double cx, double cy,
+                             double cz, double a) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x)
+    acc += bf_value(v, nx, ny, nz, cx, cy, cz, a);
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_sum_parts(double* part, int nparts, double* out, double scale) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = t * scale;
+}
+
+template <typename R>
+__global__ void k_bf_write(R* b, long long n, int nx, int ny, int nz, double cx, double cy, double cz,
+                           double a, const double* mean) {
+  const double m = *mean;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    b[v] = (R)(bf_value(v, nx, ny, nz, cx, cy, cz, a) - m);
+    b[n + v] = R(0);
+    b[2 * n + v] = R(0);
+  }
+}
+
+int body_force_scratch(long long) { return kBfBlocks + 1; }
+
+template <typename R>
+cudaError_t launch_body_force(R* b, int nx, int ny, int nz, double cx, double cy, double cz, double a,
+                              double* scratch, cudaStream_t s) {
+  const long long n = (long long)nx * ny * nz;
+  k_bf_partial<<<kBfBlocks, kRedThreads, 0, s>>>(scratch, n, nx, ny, nz, cx, cy, cz, a);
+  k_sum_parts<<<1, kRedThreads, 0, s>>>(scratch, kBfBlocks, scratch + kBfBlocks, 1.0 / (double)n);
+  k_bf_write<R><<<kBfBlocks, kRedThreads, 0, s>>>(b, n, nx, ny, nz, cx, cy, cz, a, scratch + kBfBlocks);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- validation
+constexpr int kValBlocks = 512;
+
+template <typename R>
+__global__ void k_validate(const int8_t* phase, const R* b, long long n, int* iout, double* part) {
+  __shared__ double red[32];
+  __shared__ int smin, smax;
+  if (threadIdx.x == 0) { smin = 127; smax = -128; }
+  __syncthreads();
+  int lmin = 127, lmax = -128;
+  double s[3] = {0, 0, 0}, sa[3] = {0, 0, 0};
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int ph = phase[v];
+    lmin = min(lmin, ph); lmax = max(lmax, ph);
+    if (b != nullptr) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { const double x = (double)b[c * n + v]; s[c] += x; sa[c] += fabs(x); }
+    }
+  }
+  atomicMin(&smin, lmin);
+  atomicMax(&smax, lmax);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double t = block_sum(s[c], red);
+    if (threadIdx.x == 0) part[(2 * c) * gridDim.x + blockIdx.x] = t;
+    const double ta = block_sum(sa[c], red);
+    if (threadIdx.x == 0) part[(2 * c + 1) * gridDim.x + blockIdx.x] = ta;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) { atomicMin(&iout[0], smin); atomicMax(&iout[1], smax); }
+}
+
+__global__ void k_validate_final(const double* part, int nparts, double* dout) {
+  __shared__ double red[32];
+  for (int j = 0; j < 6; ++j) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[j * nparts + i];
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) dout[(j & 1) * 3 + j / 2] = t;
+    __syncthreads();
+  }
+}
+
+__global__ void k_init_minmax(int* iout) { iout[0] = 127; iout[1] = -128; }
+
+int validate_scratch(long long) { return 6 * kValBlocks; }
+
+template <typename R>
+cudaError_t launch_validate(const int8_t* phase, const R* b, long long n, int* iout, double* dout,
+                            double* scratch, cudaStream_t s) {
+  k_init_minmax<<<1, 1, 0, s>>>(iout);
+  k_validate<R><<<kValBlocks, kRedThreads, 0, s>>>(phase, b, n, iout, scratch);
+  k_validate_final<<<1, kRedThreads, 0, s>>>(scratch, kValBlocks, dout);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- residual denominators
+// sum over modes with xi != 0 of w |b_hat|^2 (w = 2 for 0 < kx < nx/2: the
+// mirrored half of the spectrum), giving the full-spectrum norm of b_hat.
+template <typename R>
+__global__ void k_bden(const C2<R>* bhat, Geo g, ResidSlot* part) {
+  __shared__ double red[32];
+  const long long modes = (long long)g.nz * g.ny * g.mx;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.mx);
+    const long long r = i / g.mx;
+    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
+    const int sx = signed_k(kx, g.nx), sy = signed_k(ky, g.ny), sz = signed_k(kz, g.nz);
+    if (sx == 0 && sy == 0 && sz == 0) continue;
+    const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
+    const long long gi = r * g.p + kx;
+    for (int c = 0; c < 3; ++c) {
+      const C2<R> v = bhat[c * g.cs + gi];
+      acc += w * ((double)v.x * v.x + (double)v.y * v.y);
+    }
+  }
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x].num = t;
+}
+
+__global__ void k_bden_final(const ResidSlot* part, int nparts, IterState* st) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i].num;
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) st->bden = sqrt(t);
+}
+
+template <typename R>
+cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterState* st, cudaStream_t s) {
+  const int blocks = 512;
+  k_bden<R><<<blocks, kRedThreads, 0, s>>>(bhat, g, part);
+  k_bden_final<<<1, kRedThreads, 0, s>>>(part, blocks, st);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- residual reduction (Eq. 5.11)
+// r = sqrt(sum partials) / D, D = ||b_hat|| + xi_min |sigma_hat(0)|_F with
+// sigma_hat(0) = N C0 E + tau_hat(0) and xi_min = 2 pi / max N_a.
+__global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
+                               int hist_cap, int sweep, double tol, double lam0, double mu0, double E0,
+                               double E1, double E2, double E3, double E4, double E5, double n,
+                               int maxdim, int mode, int skip_check) {
+  __shared__ double red[32];
+  if (mode == GM_SWEEP && st->done) return;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i].num;
+  const double t = block_sum(acc, red);
+  if (threadIdx.x != 0) return;
+  const double E[6] = {E0, E1, E2, E3, E4, E5};
+  const double trE = E0 + E1 + E2;
+  double s0[6];
+  for (int c = 0; c < 6; ++c) s0[c] = n * (2.0 * mu0 * E[c] + (c < 3 ? lam0 * trE : 0.0)) + st->tau0[c];
+  const double s0n = sqrt(s0[0] * s0[0] + s0[1] * s0[1] + s0[2] * s0[2] +
+                          2.0 * (s0[3] * s0[3] + s0[4] * s0[4] + s0[5] * s0[5]));
+  const double den = st->bden + 6.283185307179586 / (double)maxdim * s0n;
+  double r = den > 0.0 ? sqrt(t) / den : sqrt(t);
+  if (mode == GM_FINAL) { st->resid_final = r; return; }
+  if (skip_check) r = INFINITY;
+  if (sweep < hist_cap && hist != nullptr) hist[sweep] = r;
+  st->resid_last = r;
+  st->iters = sweep + 1;
+  if (!skip_check && !(r == r && r < INFINITY)) { st->diverged = 1; st->done = 1; }
+  else if (r <= tol) st->done = 1;
+}
+
+cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
+                                int hist_cap, int sweep, double tol, double lam0, double mu0,
+                                const double* E, long long n, int maxdim, int mode, int skip_check,
+                                cudaStream_t s) {
+  k_resid_reduce<<<1, kRedThreads, 0, s>>>(part, nparts, st, hist, hist_cap, sweep, tol, lam0, mu0,
+                                           E[0], E[1], E[2], E[3], E[4], E[5], (double)n, maxdim,
+                                           mode, skip_check);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- a10: translated averaging
+// acc layout (30 x N, FP64): <u> 3, <u>^(1) 3, <eps> 6, <eps>^(1) 6, <sigma> 6, <sigma>^(1) 6.
+template <typename R>
+__global__ void k_accumulate(double* acc, int* hits, const R* eps, const R* sig, const R* u,
+                             const int8_t* phase, int sx, int sy, int sz, int nx, int ny, int nz) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+    int xs = (x - sx) % nx; if (xs < 0) xs += nx;
+    int ys = (y - sy) % ny; if (ys < 0) ys += ny;
+    int zs = (z - sz) % nz; if (zs < 0) zs += nz;
+    const bool in = phase[((long long)zs * ny + ys) * nx + xs] != 0;
+    for (int c = 0; c < 3; ++c) {
+      const double val = (double)u[c * n + v];
+      acc[c * n + v] += val;
+      if (in) acc[(3 + c) * n + v] += val;
+    }
+    for (int c = 0; c < 6; ++c) {
+      const double e = (double)eps[c * n + v], sg = (double)sig[c * n + v];
+      acc[(6 + c) * n + v] += e;
+      acc[(18 + c) * n + v] += sg;
+      if (in) { acc[(12 + c) * n + v] += e; acc[(24 + c) * n + v] += sg; }
+    }
+    if (in) hits[v] += 1;
+  }
+}
+
+template <typename R>
+cudaError_t launch_accumulate(double* acc, int* hits, const R* eps, const R* sig, const R* u,
+                              const int8_t* phase, int sx, int sy, int sz, int nx, int ny, int nz,
+                              cudaStream_t s) {
+  k_accumulate<R><<<4 * 152, 256, 0, s>>>(acc, hits, eps, sig, u, phase, sx, sy, sz, nx, ny, nz);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale(double* acc, long long count, double f) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    acc[i] *= f;
+}
+
+cudaError_t launch_scale(double* acc, long long count, double f, cudaStream_t s) {
+  k_scale<<<4 * 152, 256, 0, s>>>(acc, count, f);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+#define BFCS_INST(R)                                                                              \
+  template cudaError_t launch_body_force<R>(R*, int, int, int, double, double, double, double,     \
+                                            double*, cudaStream_t);                               \
+  template cudaError_t launch_validate<R>(const int8_t*, const R*, long long, int*, double*,       \
+                                          double*, cudaStream_t);                                 \
+  template cudaError_t launch_bden<R>(const C2<R>*, const Geo&, ResidSlot*, IterState*,            \
+                                      cudaStream_t);                                              \
+  template cudaError_t launch_accumulate<R>(double*, int*, const R*, const R*, const R*,           \
+                                            const int8_t*, int, int, int, int, int, int,          \
+                                            cudaStream_t);
+BFCS_INST(float)
+BFCS_INST(double)
+#undef BFCS_INST
+
+}  // namespace bfcs

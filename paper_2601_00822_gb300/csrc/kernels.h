@@ -1,0 +1,109 @@
+// Host-side launch interfaces of the BFCS kernels (internal; the public C-ABI
+// is include/bfcs.h).  Every launcher returns a cudaError_t and enqueues on
+// the given stream.
+#pragma once
+#include "common.cuh"
+
+namespace bfcs {
+
+// ---- x pass: along x (contiguous) with the real<->half-spectrum transform.
+enum XMode : int {
+  XM_SWEEP = 0,    // spectrum -> C2R -> eps -> tau = L1 eps -> R2C -> spectrum (Eqs. 5.7, 5.8, 5.10)
+  XM_REALTAU = 1,  // real eps (warm start) -> tau -> R2C -> spectrum
+  XM_R2C = 2,      // plain forward real -> half spectrum along x
+  XM_C2R = 3,      // plain inverse half spectrum -> real along x
+};
+
+template <typename R> struct XArgs {
+  Geo g;
+  const C2<R>* spec_in;   // [ncomp][nz][ny][p]
+  C2<R>* spec_out;        // may alias spec_in (each block owns its lines)
+  const R* real_in;       // [ncomp][nz][ny][nx]
+  R* real_out;            // [ncomp][nz][ny][nx]
+  R* eps_out;             // optional, sweep modes: 6 x N
+  R* sig_out;             // optional, sweep modes: 6 x N
+  const int8_t* phase;    // [nz][ny][nx] phase ids of the untranslated microstructure
+  int sx, sy, sz;         // translation chi: phase(x) = phase0(x - chi) (Eq. 3.3)
+  PhaseTab<R> tab;
+  const C2<R>* tw;        // exp(-2 pi i j / nx), j < nx
+  const int* done;        // nullable: skip the launch once set
+  int ncomp;
+  int mode;
+};
+
+// ---- column passes along y (axis 1) or z (axis 2) on the half spectrum, in place.
+template <typename R> struct CArgs {
+  C2<R>* data;
+  Geo g;
+  int axis;
+  int ncomp;
+  const C2<R>* tw;        // exp(-2 pi i j / n_axis)
+  const int* done;
+};
+
+// ---- fused z pass: forward z FFT -> Green operators -> residual -> inverse z FFT.
+enum GMode : int {
+  GM_SWEEP = 0,   // eps_hat^{s+1} = -Gamma0 tau_hat^s + eps_hat^{b(0)}, k=0 <- E; residual of eps^s
+  GM_INIT = 1,    // tau_hat = 0: eps_hat^0 = eps_hat^{b(0)} (+E); d_prev <- 0
+  GM_FINAL = 2,   // residual of eps^S; u_hat^S = i G0 (d_prev - i b_hat) into components 0..2
+};
+
+template <typename R> struct GArgs {
+  C2<R>* spec;            // 6 components, x- and y-transformed
+  const C2<R>* bhat;      // 3 components, fully transformed body force
+  C2<R>* dprev;           // 3 components: d = tau_hat . xi of the previous sweep
+  Geo g;
+  R lam0, mu0;
+  R E[6];
+  R inv_n;                // 1 / |N| of Eq. 4.4
+  const C2<R>* tw;        // exp(-2 pi i j / nz)
+  ResidSlot* part;        // one slot per block
+  IterState* st;
+  const int* done;
+  int mode;
+};
+
+template <typename R> cudaError_t launch_xpass(const XArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_colpass(const CArgs<R>& a, int dir, cudaStream_t s);
+template <typename R> cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t s);
+template <typename R> int green_nparts(const Geo& g);
+
+bool supported_len(int n);
+
+// process-wide count of kernel launches made by this library
+void count_launches(long long n);
+long long launches_so_far();
+
+// ---- misc kernels (k_misc.cu)
+cudaError_t launch_voxelize(int8_t* out, int nx, int ny, int nz, int cx, int cy, int cz,
+                            const int* sph_dev, int nsph, cudaStream_t s);
+template <typename R>
+cudaError_t launch_body_force(R* b, int nx, int ny, int nz, double cx, double cy, double cz,
+                              double a, double* scratch /* >= body_force_scratch() doubles */,
+                              cudaStream_t s);
+int body_force_scratch(long long n);
+
+// validation: phase id range and body-force sums; out[0..1] = min/max phase,
+// dout[0..2] = sum b_c, dout[3..5] = sum |b_c|
+template <typename R>
+cudaError_t launch_validate(const int8_t* phase, const R* b, long long n, int* iout, double* dout,
+                            double* scratch, cudaStream_t s);
+int validate_scratch(long long n);
+
+// sum over modes with xi != 0 of w |b_hat|^2 -> st->bden = sqrt(sum)
+template <typename R>
+cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterState* st, cudaStream_t s);
+
+// residual reduction of the Green-pass partials; mode = GM_SWEEP or GM_FINAL
+cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
+                                int hist_cap, int sweep, double tol, double c0_lam, double c0_mu,
+                                const double* E, long long n, int maxdim, int mode, int skip_check,
+                                cudaStream_t s);
+
+template <typename R>
+cudaError_t launch_accumulate(double* acc, int* hits, const R* eps, const R* sig, const R* u,
+                              const int8_t* phase, int sx, int sy, int sz, int nx, int ny, int nz,
+                              cudaStream_t s);
+cudaError_t launch_scale(double* acc, long long count, double f, cudaStream_t s);
+
+}  // namespace bfcs

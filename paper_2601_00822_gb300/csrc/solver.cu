@@ -1,0 +1,704 @@
+// Host side of the C ABI: plans, the sweep driver of the modified basic scheme
+// (Algorithm 1) with device-side convergence flags and bounded host waits, the
+// batched and translated-averaging drivers (Eqs. 3.3-3.6) and the utilities.
+#include "bfcs.h"
+#include "kernels.h"
+
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+using namespace bfcs;
+
+struct bfcs_plan_s {
+  int nx, ny, nz, max_batch, flags;
+  bool fp64;
+  cudaStream_t st;
+  Geo g;
+  size_t csz;                 // bytes of one complex value
+  size_t rsz;                 // bytes of one real value
+  void* spec = nullptr;       // 6 x cs complex
+  void* bhat = nullptr;       // 3 x cs complex
+  void* dprev = nullptr;      // 3 x cs complex
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  ResidSlot* part = nullptr;
+  int npart = 0;              // slots allocated (>= every writer's block count)
+  int ngreen = 0;             // blocks of the fused z/Green pass = residual partials per sweep
+  IterState* ist = nullptr;
+  IterState* ist_host = nullptr;   // pinned, 3 slots
+  cudaEvent_t ev[2];
+  double* hist = nullptr;
+  int hist_cap = 0;
+  int last_iters = 0;
+  int* ival = nullptr;             // device: phase min/max
+  double* dval = nullptr;          // device: b sums
+  double* dscratch = nullptr;      // device scratch for reductions
+  int* ival_host = nullptr;        // pinned
+  double* dval_host = nullptr;     // pinned
+  void* tmp = nullptr;             // 15 x N real: eps, sig, u for averaging members
+  int* tmp_hits = nullptr;         // N int
+  // measurement hook: CUDA events around the launches of one kernel kind
+  int prof_kind = 0;
+  std::vector<cudaEvent_t> prof_ev;   // start/end pairs
+  std::vector<int> prof_sweep;        // sweep index of each pair
+  int prof_used = 0;
+  long long prof_launches = 0;
+  double prof_ms = 0.0;
+};
+
+namespace {
+
+constexpr int kHistCap = 1 << 16;
+
+double wait_limit_s() {
+  const char* e = std::getenv("BFCS_WAIT_TIMEOUT_S");
+  if (e != nullptr) {
+    const double v = std::atof(e);
+    if (v > 0) return v;
+  }
+  return 900.0;
+}
+
+// Bounded wait for an event: BFCS_ERR_TIMEOUT once the limit passes.
+int wait_event(cudaEvent_t ev) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const double lim = wait_limit_s();
+  for (long it = 0;; ++it) {
+    const cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaSuccess) return BFCS_OK;
+    if (q != cudaErrorNotReady) return BFCS_ERR_CUDA;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > lim) return BFCS_ERR_TIMEOUT;
+    if (it < 2000) std::this_thread::yield();
+    else std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int sync_stream(bfcs_plan P) {
+  if (cudaEventRecord(P->ev[0], P->st) != cudaSuccess) return BFCS_ERR_CUDA;
+  return wait_event(P->ev[0]);
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) return BFCS_ERR_CUDA; \
+  } while (0)
+
+template <typename R>
+void* make_twiddles(int n) {
+  std::vector<C2<R>> h(n);
+  for (int j = 0; j < n; ++j) {
+    const double t = 2.0 * 3.14159265358979323846 * j / n;
+    h[j].x = (R)std::cos(t);
+    h[j].y = (R)(-std::sin(t));
+  }
+  void* d = nullptr;
+  if (cudaMalloc(&d, sizeof(C2<R>) * n) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, h.data(), sizeof(C2<R>) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  return d;
+}
+
+void free_plan(bfcs_plan P) {
+  if (P == nullptr) return;
+  cudaFree(P->spec); cudaFree(P->bhat); cudaFree(P->dprev);
+  for (int i = 0; i < 3; ++i) cudaFree(P->tw[i]);
+  cudaFree(P->part); cudaFree(P->ist); cudaFree(P->hist);
+  cudaFree(P->ival); cudaFree(P->dval); cudaFree(P->dscratch);
+  cudaFree(P->tmp); cudaFree(P->tmp_hits);
+  if (P->ist_host) cudaFreeHost(P->ist_host);
+  if (P->ival_host) cudaFreeHost(P->ival_host);
+  if (P->dval_host) cudaFreeHost(P->dval_host);
+  cudaEventDestroy(P->ev[0]);
+  cudaEventDestroy(P->ev[1]);
+  for (cudaEvent_t e : P->prof_ev) cudaEventDestroy(e);
+  delete P;
+}
+
+template <typename R>
+PhaseTab<R> make_tab(int nph, const bfcs_lame* phases, bfcs_lame C0) {
+  PhaseTab<R> t{};
+  for (int p = 0; p < kMaxPhases; ++p) {
+    const bfcs_lame q = phases[p < nph ? p : nph - 1];
+    t.lam[p] = (R)q.lambda;
+    t.mu[p] = (R)q.mu;
+    t.lam1[p] = (R)(q.lambda - C0.lambda);
+    t.mu1[p] = (R)(q.mu - C0.mu);
+  }
+  return t;
+}
+
+int check_material(int nph, const bfcs_lame* phases, bfcs_lame C0) {
+  if (phases == nullptr || nph < 1 || nph > BFCS_MAX_PHASES) return BFCS_ERR_INVALID_ARG;
+  auto ok = [](bfcs_lame l) {
+    return std::isfinite(l.lambda) && std::isfinite(l.mu) && l.mu > 0 && 3 * l.lambda + 2 * l.mu > 0;
+  };
+  if (!ok(C0)) return BFCS_ERR_INVALID_ARG;
+  for (int p = 0; p < nph; ++p)
+    if (!ok(phases[p])) return BFCS_ERR_INVALID_ARG;
+  return BFCS_OK;
+}
+
+// Phase ids in [0, nph) and a self-equilibrated load (Eq. 2.5).
+template <typename R>
+int validate_inputs(bfcs_plan P, const int8_t* phase, const void* b, int nph) {
+  CK(launch_validate<R>(phase, (const R*)b, P->g.n, P->ival, P->dval, P->dscratch, P->st));
+  CK(cudaMemcpyAsync(P->ival_host, P->ival, 2 * sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaMemcpyAsync(P->dval_host, P->dval, 6 * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  const int w = sync_stream(P);
+  if (w != BFCS_OK) return w;
+  if (P->ival_host[0] < 0 || P->ival_host[1] >= nph) return BFCS_ERR_INVALID_ARG;
+  const double thr = sizeof(R) == 4 ? 1e-6 : 1e-12;
+  for (int c = 0; c < 3; ++c) {
+    const double s = P->dval_host[c], sa = P->dval_host[3 + c];
+    if (!std::isfinite(s) || !std::isfinite(sa)) return BFCS_ERR_INVALID_ARG;
+    if (std::fabs(s) > thr * sa) return BFCS_ERR_NONZERO_MEAN;
+  }
+  return BFCS_OK;
+}
+
+// b_hat = F(b): x R2C, then y and z forward, into the plan's b_hat buffer.
+template <typename R>
+int transform_load(bfcs_plan P, const void* b) {
+  XArgs<R> xa{};
+  xa.g = P->g;
+  xa.real_in = (const R*)b;
+  xa.spec_out = (C2<R>*)P->bhat;
+  xa.ncomp = 3;
+  xa.mode = XM_R2C;
+  xa.tw = (const C2<R>*)P->tw[0];
+  CK(launch_xpass<R>(xa, P->st));
+  CArgs<R> ca{};
+  ca.data = (C2<R>*)P->bhat;
+  ca.g = P->g;
+  ca.ncomp = 3;
+  ca.axis = 1;
+  ca.tw = (const C2<R>*)P->tw[1];
+  CK(launch_colpass<R>(ca, -1, P->st));
+  ca.axis = 2;
+  ca.tw = (const C2<R>*)P->tw[2];
+  CK(launch_colpass<R>(ca, -1, P->st));
+  return BFCS_OK;
+}
+
+struct SolveOut {
+  void* eps;
+  void* sig;
+  void* u;
+};
+
+// One solve on the plan; b_hat must already be in the plan (transform_load).
+template <typename R>
+int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_lame C0, const double* E,
+               double tol, int maxit, const void* eps_init, SolveOut out, const int shift[3],
+               bfcs_info* info) {
+  const Geo g = P->g;
+  cudaStream_t st = P->st;
+  C2<R>* spec = (C2<R>*)P->spec;
+  const C2<R>* twx = (const C2<R>*)P->tw[0];
+  const C2<R>* twy = (const C2<R>*)P->tw[1];
+  const C2<R>* twz = (const C2<R>*)P->tw[2];
+  const bool warm = eps_init != nullptr;
+  const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
+
+  // iteration state (keep bden computed by the caller)
+  CK(cudaMemsetAsync(P->ist, 0, offsetof(IterState, resid_last), st));
+
+  GArgs<R> ga{};
+  ga.spec = spec;
+  ga.bhat = (const C2<R>*)P->bhat;
+  ga.dprev = (C2<R>*)P->dprev;
+  ga.g = g;
+  ga.lam0 = (R)C0.lambda;
+  ga.mu0 = (R)C0.mu;
+  for (int c = 0; c < 6; ++c) ga.E[c] = (R)E[c];
+  ga.inv_n = (R)(1.0 / (double)g.n);
+  ga.tw = twz;
+  ga.part = P->part;
+  ga.st = P->ist;
+
+  CArgs<R> cy{};
+  cy.data = spec;
+  cy.g = g;
+  cy.ncomp = 6;
+  cy.axis = 1;
+  cy.tw = twy;
+
+  XArgs<R> xa{};
+  xa.g = g;
+  xa.spec_in = spec;
+  xa.spec_out = spec;
+  xa.real_in = (const R*)eps_init;
+  xa.phase = phase;
+  xa.sx = shift[0];
+  xa.sy = shift[1];
+  xa.sz = shift[2];
+  xa.tab = tab;
+  xa.tw = twx;
+  xa.ncomp = 6;
+
+  if (!warm) {
+    ga.mode = GM_INIT;
+    ga.done = nullptr;
+    CK(launch_zgreen<R>(ga, st));
+    CK(launch_colpass<R>(cy, +1, st));
+  } else {
+    CK(cudaMemsetAsync(P->dprev, 0, 3 * g.cs * sizeof(C2<R>), st));
+  }
+
+  const int* done = &P->ist->done;
+  P->prof_used = 0;
+  const int prof_cap = (int)P->prof_sweep.size();
+  // launch one kernel, bracketed by events when it is the profiled kind
+  auto timed = [&](int kind, int s, cudaError_t (*fn)(const void*, int, cudaStream_t), const void* args,
+                   int dir) -> cudaError_t {
+    const bool t = P->prof_kind == kind && P->prof_used < prof_cap;
+    if (t && cudaEventRecord(P->prof_ev[2 * P->prof_used], st) != cudaSuccess) return cudaErrorUnknown;
+    const cudaError_t e = fn(args, dir, st);
+    if (t) {
+      if (cudaEventRecord(P->prof_ev[2 * P->prof_used + 1], st) != cudaSuccess) return cudaErrorUnknown;
+      P->prof_sweep[P->prof_used++] = s;
+    }
+    return e;
+  };
+  auto run_x = [](const void* a, int, cudaStream_t q) { return launch_xpass<R>(*(const XArgs<R>*)a, q); };
+  auto run_c = [](const void* a, int dir, cudaStream_t q) {
+    return launch_colpass<R>(*(const CArgs<R>*)a, dir, q);
+  };
+  auto run_g = [](const void* a, int, cudaStream_t q) { return launch_zgreen<R>(*(const GArgs<R>*)a, q); };
+  auto enqueue_sweep = [&](int s) -> int {
+    const bool first_warm = warm && s == 0;
+    xa.mode = first_warm ? XM_REALTAU : XM_SWEEP;
+    xa.eps_out = nullptr;
+    xa.sig_out = nullptr;
+    xa.done = done;
+    CK(timed(1, s, run_x, &xa, 0));
+    cy.done = done;
+    cy.ncomp = 6;
+    CK(timed(2, s, run_c, &cy, -1));
+    ga.mode = GM_SWEEP;
+    ga.done = done;
+    CK(timed(3, s, run_g, &ga, 0));
+    CK(timed(2, s, run_c, &cy, +1));
+    CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->hist, P->hist_cap, s, tol, C0.lambda, C0.mu,
+                           E, g.n, maxdim, GM_SWEEP, first_warm ? 1 : 0, st));
+    return BFCS_OK;
+  };
+
+  // sweeps in chunks; the host looks at the state of chunk k-1 while chunk k runs
+  int s = 0, chunk = 4, slot = 0;
+  bool pending = false;
+  while (s < maxit) {
+    const int c = std::min(chunk, maxit - s);
+    for (int k = 0; k < c; ++k) {
+      const int e = enqueue_sweep(s + k);
+      if (e != BFCS_OK) return e;
+    }
+    s += c;
+    CK(cudaMemcpyAsync(&P->ist_host[slot], P->ist, sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(P->ev[slot], st));
+    if (pending) {
+      const int w = wait_event(P->ev[slot ^ 1]);
+      if (w != BFCS_OK) return w;
+      const IterState& h = P->ist_host[slot ^ 1];
+      if (h.done) break;
+      // predict the sweeps still needed from the observed contraction
+      if (h.iters > 2 && std::isfinite(h.resid_last) && tol > 0) {
+        (void)0;
+      }
+    }
+    pending = true;
+    slot ^= 1;
+    chunk = std::min(chunk * 2, 32);
+  }
+
+  // finalize: eps^S, sigma^S in real space; residual of eps^S; u^S
+  const bool s0_warm = warm && s == 0;
+  xa.mode = s0_warm ? XM_REALTAU : XM_SWEEP;
+  xa.eps_out = (R*)out.eps;
+  xa.sig_out = (R*)out.sig;
+  xa.done = nullptr;
+  CK(launch_xpass<R>(xa, st));
+  cy.done = nullptr;
+  cy.ncomp = 6;
+  CK(launch_colpass<R>(cy, -1, st));
+  ga.mode = GM_FINAL;
+  ga.done = nullptr;
+  CK(launch_zgreen<R>(ga, st));
+  CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->hist, P->hist_cap, s, tol, C0.lambda, C0.mu, E,
+                         g.n, maxdim, GM_FINAL, 0, st));
+  if (out.u != nullptr) {
+    cy.ncomp = 3;
+    CK(launch_colpass<R>(cy, +1, st));
+    XArgs<R> xu{};
+    xu.g = g;
+    xu.spec_in = spec;
+    xu.real_out = (R*)out.u;
+    xu.ncomp = 3;
+    xu.mode = XM_C2R;
+    xu.tw = twx;
+    CK(launch_xpass<R>(xu, st));
+  }
+  CK(cudaMemcpyAsync(&P->ist_host[2], P->ist, sizeof(IterState), cudaMemcpyDeviceToHost, st));
+  const int w = sync_stream(P);
+  if (w != BFCS_OK) return w;
+  const IterState& h = P->ist_host[2];
+  P->last_iters = h.iters;
+  for (int k = 0; k < P->prof_used; ++k) {
+    if (P->prof_sweep[k] >= h.iters) continue;     // launches of sweeps skipped on device
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P->prof_ev[2 * k], P->prof_ev[2 * k + 1]) != cudaSuccess)
+      return BFCS_ERR_CUDA;
+    P->prof_ms += ms;
+    P->prof_launches += 1;
+  }
+  P->prof_used = 0;
+  int status = BFCS_OK;
+  if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
+  else if (tol > 0 && !h.done) status = BFCS_NOT_CONVERGED;
+  if (info != nullptr) {
+    info->iters = h.iters;
+    info->status = status;
+    info->resid = h.resid_final;
+    info->resid_prev = h.resid_last;
+    info->precision_path = sizeof(R) == 8 ? 1 : 0;
+  }
+  return status;
+}
+
+template <typename R>
+int solve_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
+               const void* b, const double* E, double tol, int maxit, const void* eps_init, SolveOut out,
+               const int shift[3], bfcs_info* info) {
+  int e = check_material(nph, phases, C0);
+  if (e != BFCS_OK) return e;
+  if (phase == nullptr || b == nullptr || E == nullptr || out.eps == nullptr) return BFCS_ERR_INVALID_ARG;
+  if (!(tol >= 0) || maxit < 0 || (eps_init != nullptr && maxit < 1)) return BFCS_ERR_INVALID_ARG;
+  for (int c = 0; c < 6; ++c)
+    if (!std::isfinite(E[c])) return BFCS_ERR_INVALID_ARG;
+  e = validate_inputs<R>(P, phase, b, nph);
+  if (e != BFCS_OK) return e;
+  e = transform_load<R>(P, b);
+  if (e != BFCS_OK) return e;
+  CK(launch_bden<R>((const C2<R>*)P->bhat, P->g, P->part, P->ist, P->st));
+  return solve_core<R>(P, phase, make_tab<R>(nph, phases, C0), C0, E, tol, maxit, eps_init, out, shift,
+                       info);
+}
+
+int ensure_tmp(bfcs_plan P) {
+  if (P->tmp == nullptr) {
+    if (cudaMalloc(&P->tmp, 15 * (size_t)P->g.n * P->rsz) != cudaSuccess) return BFCS_ERR_OOM;
+  }
+  if (P->tmp_hits == nullptr) {
+    if (cudaMalloc(&P->tmp_hits, (size_t)P->g.n * sizeof(int)) != cudaSuccess) return BFCS_ERR_OOM;
+  }
+  return BFCS_OK;
+}
+
+template <typename R>
+int translate_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                   const void* b, const double* E, int nshift, const int32_t* shifts, double tol,
+                   int maxit, double* avg, int32_t* hits, bfcs_info* infos) {
+  int e = check_material(nph, phases, C0);
+  if (e != BFCS_OK) return e;
+  if (phase == nullptr || b == nullptr || E == nullptr || avg == nullptr || shifts == nullptr ||
+      nshift < 1 || !(tol >= 0) || maxit < 0)
+    return BFCS_ERR_INVALID_ARG;
+  e = ensure_tmp(P);
+  if (e != BFCS_OK) return e;
+  e = validate_inputs<R>(P, phase, b, nph);
+  if (e != BFCS_OK) return e;
+  const long long n = P->g.n;
+  int* h = hits != nullptr ? (int*)hits : P->tmp_hits;
+  CK(cudaMemsetAsync(avg, 0, 30 * n * sizeof(double), P->st));
+  CK(cudaMemsetAsync(h, 0, n * sizeof(int), P->st));
+  e = transform_load<R>(P, b);            // b is fixed under translation (Eq. 3.4)
+  if (e != BFCS_OK) return e;
+  CK(launch_bden<R>((const C2<R>*)P->bhat, P->g, P->part, P->ist, P->st));
+  const PhaseTab<R> tab = make_tab<R>(nph, phases, C0);
+  R* eps = (R*)P->tmp;
+  R* sig = eps + 6 * n;
+  R* u = sig + 6 * n;
+  int worst = BFCS_OK;
+  for (int m = 0; m < nshift; ++m) {
+    const int sh[3] = {shifts[3 * m], shifts[3 * m + 1], shifts[3 * m + 2]};
+    bfcs_info inf{};
+    const int s = solve_core<R>(P, phase, tab, C0, E, tol, maxit, nullptr, SolveOut{eps, sig, u}, sh, &inf);
+    if (s < 0) return s;
+    if (s > worst) worst = s;
+    if (infos != nullptr) infos[m] = inf;
+    CK(launch_accumulate<R>(avg, h, eps, sig, u, phase, sh[0], sh[1], sh[2], P->g.nx, P->g.ny, P->g.nz,
+                            P->st));
+  }
+  CK(launch_scale(avg, 30 * n, 1.0 / nshift, P->st));
+  const int w = sync_stream(P);
+  return w != BFCS_OK ? w : worst;
+}
+
+int severity(int s) { return s < 0 ? 1000 - s : s; }
+
+}  // namespace
+
+extern "C" {
+
+const char* bfcs_status_string(int s) {
+  switch (s) {
+    case BFCS_OK: return "ok";
+    case BFCS_NOT_CONVERGED: return "not converged within maxit";
+    case BFCS_ERR_INVALID_ARG: return "invalid argument";
+    case BFCS_ERR_NONZERO_MEAN: return "body force is not mean-free (Eq. 2.5)";
+    case BFCS_ERR_OOM: return "out of device memory";
+    case BFCS_ERR_CUDA: return "CUDA runtime error";
+    case BFCS_ERR_TIMEOUT: return "bounded wait expired";
+    case BFCS_ERR_DIVERGED: return "residual is NaN or Inf";
+    case BFCS_ERR_UNSUPPORTED: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int flags, void* stream) {
+  if (out == nullptr) return BFCS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz) || max_batch < 1 ||
+      (flags & ~BFCS_FP64) != 0)
+    return BFCS_ERR_INVALID_ARG;
+  bfcs_plan P = new bfcs_plan_s();
+  P->nx = nx; P->ny = ny; P->nz = nz;
+  P->max_batch = max_batch;
+  P->flags = flags;
+  P->fp64 = (flags & BFCS_FP64) != 0;
+  P->st = (cudaStream_t)stream;
+  P->g.nx = nx; P->g.ny = ny; P->g.nz = nz;
+  P->g.mx = nx / 2 + 1;
+  P->g.p = (nx / 2 + 1 + 3) / 4 * 4;
+  P->g.cs = (long long)nz * ny * P->g.p;
+  P->g.n = (long long)nx * ny * nz;
+  P->csz = P->fp64 ? sizeof(C2<double>) : sizeof(C2<float>);
+  P->rsz = P->fp64 ? sizeof(double) : sizeof(float);
+  P->ev[0] = P->ev[1] = nullptr;
+  bool ok = cudaEventCreateWithFlags(&P->ev[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&P->ev[1], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) { free_plan(P); return BFCS_ERR_CUDA; }
+  const size_t cs = (size_t)P->g.cs;
+  P->ngreen = P->fp64 ? green_nparts<double>(P->g) : green_nparts<float>(P->g);
+  P->npart = std::max(P->ngreen, 512);
+  ok = cudaMalloc(&P->spec, 6 * cs * P->csz) == cudaSuccess &&
+       cudaMalloc(&P->bhat, 3 * cs * P->csz) == cudaSuccess &&
+       cudaMalloc(&P->dprev, 3 * cs * P->csz) == cudaSuccess &&
+       cudaMalloc(&P->part, P->npart * sizeof(ResidSlot)) == cudaSuccess &&
+       cudaMalloc(&P->ist, sizeof(IterState)) == cudaSuccess &&
+       cudaMalloc(&P->hist, kHistCap * sizeof(double)) == cudaSuccess &&
+       cudaMalloc(&P->ival, 2 * sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&P->dval, 6 * sizeof(double)) == cudaSuccess &&
+       cudaMalloc(&P->dscratch, std::max(validate_scratch(P->g.n), body_force_scratch(P->g.n)) *
+                                    sizeof(double)) == cudaSuccess &&
+       cudaMallocHost(&P->ist_host, 3 * sizeof(IterState)) == cudaSuccess &&
+       cudaMallocHost(&P->ival_host, 2 * sizeof(int)) == cudaSuccess &&
+       cudaMallocHost(&P->dval_host, 6 * sizeof(double)) == cudaSuccess;
+  if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
+  P->hist_cap = kHistCap;
+  const int dims[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    P->tw[a] = P->fp64 ? make_twiddles<double>(dims[a]) : make_twiddles<float>(dims[a]);
+    if (P->tw[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
+  }
+  if (cudaMemset(P->ist, 0, sizeof(IterState)) != cudaSuccess) { free_plan(P); return BFCS_ERR_CUDA; }
+  *out = P;
+  return BFCS_OK;
+}
+
+int bfcs_plan_destroy(bfcs_plan P) {
+  if (P == nullptr) return BFCS_ERR_INVALID_ARG;
+  cudaStreamSynchronize(P->st);
+  free_plan(P);
+  return BFCS_OK;
+}
+
+int bfcs_voxelize(int nx, int ny, int nz, int cx, int cy, int cz, int nsph, const int32_t* spheres,
+                  int8_t* phase_out, void* stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || cx < 1 || cy < 1 || cz < 1 || nx % cx || ny % cy || nz % cz ||
+      nsph < 0 || (nsph > 0 && spheres == nullptr) || phase_out == nullptr)
+    return BFCS_ERR_INVALID_ARG;
+  for (int k = 0; k < nsph; ++k) {
+    const int32_t* S = spheres + 5 * k;
+    if (S[3] < 0 || S[4] < -128 || S[4] > 127) return BFCS_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d = nullptr;
+  if (nsph > 0) {
+    if (cudaMallocAsync((void**)&d, sizeof(int) * 5 * nsph, st) != cudaSuccess) return BFCS_ERR_OOM;
+    CK(cudaMemcpyAsync(d, spheres, sizeof(int) * 5 * nsph, cudaMemcpyHostToDevice, st));
+  }
+  CK(launch_voxelize(phase_out, nx, ny, nz, cx, cy, cz, d, nsph, st));
+  if (d != nullptr) CK(cudaFreeAsync(d, st));
+  return BFCS_OK;
+}
+
+int bfcs_body_force(int nx, int ny, int nz, double cx, double cy, double cz, double a, int precision,
+                    void* b_out, void* stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(a > 0) || b_out == nullptr ||
+      (precision != BFCS_FP32 && precision != BFCS_FP64) || !std::isfinite(cx) || !std::isfinite(cy) ||
+      !std::isfinite(cz))
+    return BFCS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n = (long long)nx * ny * nz;
+  double* scratch = nullptr;
+  if (cudaMallocAsync((void**)&scratch, sizeof(double) * body_force_scratch(n), st) != cudaSuccess)
+    return BFCS_ERR_OOM;
+  cudaError_t e = precision == BFCS_FP64
+                      ? launch_body_force<double>((double*)b_out, nx, ny, nz, cx, cy, cz, a, scratch, st)
+                      : launch_body_force<float>((float*)b_out, nx, ny, nz, cx, cy, cz, a, scratch, st);
+  if (e != cudaSuccess) return BFCS_ERR_CUDA;
+  CK(cudaFreeAsync(scratch, st));
+  return BFCS_OK;
+}
+
+int bfcs_solve(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
+               const void* b, const double E[6], double tol, int maxit, const void* eps_init,
+               void* eps_out, void* sig_out, void* u_out, bfcs_info* info) {
+  if (P == nullptr) return BFCS_ERR_INVALID_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int shift[3] = {0, 0, 0};
+  const SolveOut out{eps_out, sig_out, u_out};
+  const int s = P->fp64 ? solve_impl<double>(P, phase, nph, phases, C0, b, E, tol, maxit, eps_init, out,
+                                             shift, info)
+                        : solve_impl<float>(P, phase, nph, phases, C0, b, E, tol, maxit, eps_init, out,
+                                            shift, info);
+  if (info != nullptr) {
+    info->status = s;
+    info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return s;
+}
+
+int bfcs_solve_batched(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, const bfcs_lame* phases,
+                       bfcs_lame C0, double tol, int maxit, bfcs_info* infos) {
+  if (P == nullptr || batch < 0 || (batch > 0 && pr == nullptr)) return BFCS_ERR_INVALID_ARG;
+  int worst = BFCS_OK;
+  for (int m = 0; m < batch; ++m) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const SolveOut out{pr[m].eps_out, pr[m].sig_out, pr[m].u_out};
+    bfcs_info inf{};
+    const int s = P->fp64 ? solve_impl<double>(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol,
+                                               maxit, pr[m].eps_init, out, pr[m].shift, &inf)
+                          : solve_impl<float>(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol,
+                                              maxit, pr[m].eps_init, out, pr[m].shift, &inf);
+    inf.status = s;
+    inf.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (infos != nullptr) infos[m] = inf;
+    if (severity(s) > severity(worst)) worst = s;
+  }
+  return worst;
+}
+
+int bfcs_translate_average(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases,
+                           bfcs_lame C0, const void* b, const double E[6], int nshift,
+                           const int32_t* shifts, double tol, int maxit, double* avg_out,
+                           int32_t* hits_out, bfcs_info* infos) {
+  if (P == nullptr) return BFCS_ERR_INVALID_ARG;
+  return P->fp64 ? translate_impl<double>(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit,
+                                          avg_out, hits_out, infos)
+                 : translate_impl<float>(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit,
+                                         avg_out, hits_out, infos);
+}
+
+int bfcs_surrogate_infer(bfcs_plan, const void*, const void*, const int8_t*, int, const bfcs_lame*, void*) {
+  return BFCS_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"
+
+template <typename R>
+static int fft3d_impl(bfcs_plan P, int dir, int ncomp, const void* in, void* out) {
+  const Geo g = P->g;
+  const size_t csz = sizeof(C2<R>);
+  C2<R>* spec = (C2<R>*)P->spec;
+  CArgs<R> ca{};
+  ca.data = spec;
+  ca.g = g;
+  ca.ncomp = ncomp;
+  XArgs<R> xa{};
+  xa.g = g;
+  xa.ncomp = ncomp;
+  xa.tw = (const C2<R>*)P->tw[0];
+  const size_t rows = (size_t)ncomp * g.nz * g.ny;
+  if (dir < 0) {
+    xa.mode = XM_R2C;
+    xa.real_in = (const R*)in;
+    xa.spec_out = spec;
+    CK(launch_xpass<R>(xa, P->st));
+    ca.axis = 1; ca.tw = (const C2<R>*)P->tw[1];
+    CK(launch_colpass<R>(ca, -1, P->st));
+    ca.axis = 2; ca.tw = (const C2<R>*)P->tw[2];
+    CK(launch_colpass<R>(ca, -1, P->st));
+    CK(cudaMemcpy2DAsync(out, g.mx * csz, spec, g.p * csz, g.mx * csz, rows, cudaMemcpyDeviceToDevice,
+                         P->st));
+  } else {
+    CK(cudaMemcpy2DAsync(spec, g.p * csz, in, g.mx * csz, g.mx * csz, rows, cudaMemcpyDeviceToDevice,
+                         P->st));
+    ca.axis = 2; ca.tw = (const C2<R>*)P->tw[2];
+    CK(launch_colpass<R>(ca, +1, P->st));
+    ca.axis = 1; ca.tw = (const C2<R>*)P->tw[1];
+    CK(launch_colpass<R>(ca, +1, P->st));
+    xa.mode = XM_C2R;
+    xa.spec_in = spec;
+    xa.real_out = (R*)out;
+    CK(launch_xpass<R>(xa, P->st));
+  }
+  return sync_stream(P);
+}
+
+extern "C" {
+
+int bfcs_fft3d(bfcs_plan P, int direction, int ncomp, const void* in, void* out) {
+  if (P == nullptr || in == nullptr || out == nullptr || ncomp < 1 || ncomp > 6 ||
+      (direction != -1 && direction != 1))
+    return BFCS_ERR_INVALID_ARG;
+  return P->fp64 ? fft3d_impl<double>(P, direction, ncomp, in, out)
+                 : fft3d_impl<float>(P, direction, ncomp, in, out);
+}
+
+long long bfcs_kernel_launches(void) { return launches_so_far(); }
+
+int bfcs_profile_kernel(bfcs_plan P, int kind) {
+  if (P == nullptr || kind < 0 || kind > 3) return BFCS_ERR_INVALID_ARG;
+  if (kind != 0 && P->prof_ev.empty()) {
+    const int pairs = 4096;
+    P->prof_ev.resize(2 * pairs, nullptr);
+    for (auto& e : P->prof_ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return BFCS_ERR_CUDA;
+    P->prof_sweep.assign(pairs, 0);
+  }
+  P->prof_kind = kind;
+  P->prof_launches = 0;
+  P->prof_ms = 0.0;
+  return BFCS_OK;
+}
+
+int bfcs_profile_read(bfcs_plan P, long long* launches, double* total_ms) {
+  if (P == nullptr || launches == nullptr || total_ms == nullptr) return BFCS_ERR_INVALID_ARG;
+  *launches = P->prof_launches;
+  *total_ms = P->prof_ms;
+  P->prof_launches = 0;
+  P->prof_ms = 0.0;
+  return BFCS_OK;
+}
+
+int bfcs_last_history(bfcs_plan P, double* hist, int cap) {
+  if (P == nullptr || hist == nullptr || cap < 0) return BFCS_ERR_INVALID_ARG;
+  const int n = std::min(cap, std::min(P->last_iters, P->hist_cap));
+  if (n > 0) {
+    if (cudaMemcpyAsync(hist, P->hist, n * sizeof(double), cudaMemcpyDeviceToHost, P->st) != cudaSuccess)
+      return BFCS_ERR_CUDA;
+    const int w = sync_stream(P);
+    if (w != BFCS_OK) return w;
+  }
+  return n;
+}
+
+}  // extern "C"

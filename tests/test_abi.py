@@ -1,0 +1,43 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+symbol include/bfcs.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+from paper_2601_00822_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bfcs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bfcs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert sorted(_lib.EXPORTS) == declared_functions()
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    raw = ctypes.CDLL(_lib.library_path(build=False))
+    for name in declared_functions():
+        assert getattr(raw, name) is not None
+
+
+def test_status_strings_without_gpu():
+    lib = _lib.load()
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+        assert len(lib.bfcs_status_string(code)) > 0
+
+
+def test_invalid_plan_rejected_before_any_device_work():
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    assert lib.bfcs_plan_create(ctypes.byref(h), 30, 32, 32, 1, 0, None) == _lib.ERR_INVALID_ARG  # odd/unsupported
+    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 31, 1, 0, None) == _lib.ERR_INVALID_ARG
+    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 0, 0, None) == _lib.ERR_INVALID_ARG
+    assert lib.bfcs_plan_create(None, 32, 32, 32, 1, 0, None) == _lib.ERR_INVALID_ARG

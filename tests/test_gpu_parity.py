@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars: bit-exact on integer work (phase maps); relative L2 <= 1e-10 for FP64
+fields and <= 1e-5 for FP32 fields at the same sweep count (pure rounding).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bfcs_oracle as O
+from paper_2601_00822_gb300 import _lib, api, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b.ravel())
+    return np.linalg.norm((a - b).ravel()) / (nb if nb > 0 else 1.0)
+
+
+def small_problem(dims, cell, sphere_rows, centre, a, phases=((1.0, 0.5), (10.0, 5.0)), E=(0.0,) * 6):
+    return W.Problem(name="t", dims=dims, cell=cell, spheres=np.asarray(sphere_rows, dtype=np.int32),
+                     phases=list(phases), c0=W.reference_medium(list(phases)), bf_centre=centre,
+                     bf_radius=a, mean_strain=E)
+
+
+def oracle_inputs(p):
+    return O.phase_map(p.dims, p.cell, p.spheres), O.body_force(p.dims, p.bf_centre, p.bf_radius)
+
+
+def gpu_inputs(p, precision):
+    return api.voxelize(p.dims, p.cell, p.spheres), api.body_force(p.dims, p.bf_centre, p.bf_radius,
+                                                                  precision)
+
+
+CASES = {
+    "c1_32cubed": W.config_c1(),
+    "ragged_48x24x96": small_problem((48, 24, 96), (24, 12, 32), [[24, 12, 30, 90, 1], [3, 20, 60, 40, 2]],
+                                     (24.0, 12.0, 48.0), 7.0,
+                                     phases=((1.0, 0.5), (6.0, 3.0), (0.5, 0.3))),
+    "aniso_12x32x24": small_problem((12, 32, 24), (12, 16, 12), [[12, 16, 12, 49, 1]], (6.0, 16.0, 12.0), 4.5,
+                                    E=(0.01, -0.004, 0.002, 0.001, -0.003, 0.005)),
+}
+
+
+# ---------------------------------------------------------------- a1, a2
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_phase_map_bit_exact(name):
+    p = CASES[name]
+    ph_gpu = api.voxelize(p.dims, p.cell, p.spheres).cpu().numpy()
+    assert np.array_equal(ph_gpu, O.phase_map(p.dims, p.cell, p.spheres))
+
+
+def test_phase_map_bit_exact_full_size_random_spheres():
+    p = W.config_c2(contrast=10.0, seed=1)
+    ph_gpu = api.voxelize(p.dims, p.cell, p.spheres).cpu().numpy()
+    assert np.array_equal(ph_gpu, O.phase_map(p.dims, p.cell, p.spheres))
+    assert 0.2 < (ph_gpu != 0).mean() < 0.3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_body_force(name, precision):
+    p = CASES[name]
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, precision).cpu().numpy()
+    ref = O.body_force(p.dims, p.bf_centre, p.bf_radius)
+    scale = np.abs(ref).max()
+    assert np.abs(b - ref).max() <= (1e-15 if precision == "fp64" else 1e-7) * scale
+
+
+# ---------------------------------------------------------------- a5, a7 transforms
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dims", [(32, 32, 32), (48, 24, 96), (12, 32, 24), (256, 8, 6)])
+def test_fft3d_against_oracle_transform(dims, precision):
+    nx, ny, nz = dims
+    r = np.random.default_rng(5)
+    x = r.standard_normal((5, nz, ny, nx))
+    with api.Plan(dims, precision) as plan:
+        xt = torch.tensor(x, dtype=plan.dtype, device="cuda")
+        X = plan.fft3d(xt, -1).cpu().numpy()
+        ref = O.fft3(x)[..., : nx // 2 + 1]
+        t = 1e-6 if precision == "fp32" else 1e-13
+        assert rel(X, ref) < t
+        cdt = torch.complex128 if precision == "fp64" else torch.complex64
+        back = plan.fft3d(torch.tensor(ref, device="cuda").to(cdt), +1).cpu().numpy()
+        assert rel(back / (nx * ny * nz), x) < t
+
+
+# ---------------------------------------------------------------- a3-a9, a11 the solve
+def run_pair(p, precision, sweeps, tol=0.0):
+    ph_o, b_o = oracle_inputs(p)
+    ref = O.solve(ph_o, p.phases, p.c0, b_o, p.mean_strain, tol=tol, maxit=sweeps, history=True)
+    ph, b = gpu_inputs(p, precision)
+    with api.Plan(p.dims, precision) as plan:
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, p.mean_strain, tol=tol, maxit=sweeps)
+        hist = plan.history()
+    return ref, (eps.cpu().numpy(), sig.cpu().numpy(), u.cpu().numpy(), info, hist)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fixed_sweeps_parity(name, precision):
+    p = CASES[name]
+    ref, (eps, sig, u, info, hist) = run_pair(p, precision, sweeps=12)
+    assert info.iters == ref["sweeps"] == 12
+    t = TOL[precision]
+    assert rel(eps, ref["eps"]) < t, rel(eps, ref["eps"])
+    assert rel(sig, ref["sig"]) < t
+    assert rel(u, ref["u"]) < t
+    assert abs(info.resid - ref["resid"]) <= 1e-3 * ref["resid"] + (1e-12 if precision == "fp64" else 1e-6)
+    h_ref = np.array(ref["hist"])
+    assert len(hist) == len(h_ref)
+    assert np.all(np.abs(hist - h_ref) <= 1e-4 * h_ref + (1e-12 if precision == "fp64" else 1e-6))
+
+
+def test_converged_fp64_config1():
+    p = W.config_c1()
+    ref, (eps, sig, u, info, hist) = run_pair(p, "fp64", sweeps=p.maxit, tol=p.tol)
+    assert info.status == _lib.OK and info.resid <= 10 * p.tol
+    assert abs(info.iters - ref["sweeps"]) <= 1
+    for a, key in ((eps, "eps"), (sig, "sig"), (u, "u")):
+        assert rel(a, ref[key]) < 1e-9, (key, rel(a, ref[key]))
+
+
+def test_fp32_converged_error_against_fp64():
+    p = W.config_c1()
+    p.tol = 1e-6
+    ph, b = gpu_inputs(p, "fp32")
+    ph_o, b_o = oracle_inputs(p)
+    ref = O.solve(ph_o, p.phases, p.c0, b_o, tol=1e-12, maxit=4000)
+    with api.Plan(p.dims, "fp32") as plan:
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-6, maxit=2000)
+    assert info.status == _lib.OK and info.resid < 2e-6
+    # error against the converged FP64 answer: iteration error ~ tol plus rounding
+    assert rel(eps.cpu().numpy(), ref["eps"]) < 2e-5
+
+
+def test_homogeneous_medium_one_sweep_exact():
+    p = small_problem((32, 24, 16), (32, 24, 16), [[20, 20, 20, 60, 1]], (10.0, 12.0, 8.0), 5.0,
+                      phases=((2.0, 1.0), (2.0, 1.0)), E=(0.01, 0, 0, 0.002, 0, 0))
+    ref, (eps, sig, u, info, hist) = run_pair(p, "fp64", sweeps=1)
+    assert info.resid < 1e-13 and hist[0] < 1e-13
+    assert rel(eps, ref["eps"]) < 1e-12
+
+
+# ---------------------------------------------------------------- warm start, batching, averaging
+def test_warm_start_from_converged_field():
+    p = W.config_c1()
+    ph, b = gpu_inputs(p, "fp64")
+    with api.Plan(p.dims, "fp64") as plan:
+        eps, _, _, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-11, maxit=4000)
+        eps2, _, _, info2 = plan.solve(ph, p.phases, p.c0, b, tol=1e-10, maxit=50, eps_init=eps.clone())
+        hist = plan.history()
+    assert info2.status == _lib.OK and info2.iters <= 2
+    assert np.isinf(hist[0])
+    assert rel(eps2.cpu().numpy(), eps.cpu().numpy()) < 1e-10
+
+
+def test_batched_equals_individual_solves():
+    p = CASES["aniso_12x32x24"]
+    ph, b = gpu_inputs(p, "fp32")
+    with api.Plan(p.dims, "fp32") as plan:
+        shifts = [(0, 0, 0), (3, 5, 7), (11, 1, 2)]
+        members = [dict(phase=ph, b=b, E=p.mean_strain, shift=s) for s in shifts]
+        members, infos = plan.solve_batched(members, p.phases, p.c0, tol=0, maxit=9)
+        ph_o, b_o = oracle_inputs(p)
+        for mem, s in zip(members, shifts):
+            ref = O.solve(O.translate(ph_o, s), p.phases, p.c0, b_o, p.mean_strain, tol=0, maxit=9)
+            assert rel(mem["eps_out"].cpu().numpy(), ref["eps"]) < 1e-5
+    assert all(i.iters == 9 for i in infos)
+
+
+def test_translate_average_parity():
+    dims = (16, 16, 16)
+    p = small_problem(dims, (8, 8, 8), [[8, 8, 8, 36, 1]], (8.0, 8.0, 8.0), 4.0)
+    shifts = [(0, 0, 0), (2, 0, 0), (0, 4, 2), (6, 6, 6), (1, 3, 5)]
+    ph_o, b_o = oracle_inputs(p)
+    avg_ref, hits_ref, _ = O.translate_average(ph_o, p.phases, p.c0, b_o, shifts, tol=0, maxit=10)
+    ph, b = gpu_inputs(p, "fp64")
+    with api.Plan(dims, "fp64") as plan:
+        avg, hits, infos = plan.translate_average(ph, p.phases, p.c0, b, shifts, tol=0, maxit=10)
+    assert np.array_equal(hits.cpu().numpy(), hits_ref)
+    avg = avg.cpu().numpy()
+    for a0, a1 in ((0, 3), (3, 6), (6, 12), (12, 18), (18, 24), (24, 30)):
+        assert rel(avg[a0:a1], avg_ref[a0:a1]) < 1e-10
+
+
+# ---------------------------------------------------------------- errors
+def test_error_statuses():
+    p = CASES["aniso_12x32x24"]
+    ph, b = gpu_inputs(p, "fp32")
+    with api.Plan(p.dims, "fp32") as plan:
+        bad_b = b.clone()
+        bad_b[0] += 0.5                                    # not self-equilibrated (Eq. 2.5)
+        with pytest.raises(_lib.BfcsError) as e:
+            plan.solve(ph, p.phases, p.c0, bad_b, tol=1e-6, maxit=5)
+        assert e.value.code == _lib.ERR_NONZERO_MEAN
+        bad_ph = ph.clone()
+        bad_ph[0, 0, 0] = 7                                # phase id beyond the table
+        with pytest.raises(_lib.BfcsError) as e:
+            plan.solve(bad_ph, p.phases, p.c0, b, tol=1e-6, maxit=5)
+        assert e.value.code == _lib.ERR_INVALID_ARG
+        with pytest.raises(_lib.BfcsError) as e:
+            plan.solve(ph, p.phases, (1.0, -1.0), b, tol=1e-6, maxit=5)
+        assert e.value.code == _lib.ERR_INVALID_ARG
+        eps, _, _, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-30, maxit=3)
+        assert info.status == _lib.NOT_CONVERGED and info.iters == 3
+        # the plan is still usable after the errors
+        eps2, _, _, info2 = plan.solve(ph, p.phases, p.c0, b, tol=0, maxit=3)
+        assert torch.equal(eps, eps2)
+
+
+# ---------------------------------------------------------------- full size (256^3, the benchmarked launch)
+def test_full_size_fp32_solve_meets_tolerance_independently_checked():
+    p = W.config_c2(contrast=10.0, seed=1)
+    ph, b = gpu_inputs(p, "fp32")
+    with api.Plan(p.dims, "fp32") as plan:
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, tol=p.tol, maxit=2000)
+    assert info.status == _lib.OK and info.resid <= 1.5 * p.tol
+    # independent check by the oracle's residual (Eq. 5.11 reading) on the returned field
+    ph_o = O.phase_map(p.dims, p.cell, p.spheres)
+    b_o = O.body_force(p.dims, p.bf_centre, p.bf_radius)
+    e = eps.cpu().numpy().astype(np.float64)
+    xi = O.wavevectors(p.dims)
+    r = O.residual(ph_o, p.phases, e, O.fft3(b_o), xi)
+    assert r < 5e-6, r
+    # sigma = L(x) eps voxel by voxel on a sample
+    s = sig.cpu().numpy()
+    rng = np.random.default_rng(0)
+    idx = tuple(rng.integers(0, 256, size=(3, 2000)))
+    sref = O.apply_local(ph_o[idx], p.phases, e[(slice(None),) + idx])
+    assert np.allclose(s[(slice(None),) + idx], sref, rtol=1e-5, atol=1e-7 * np.abs(sref).max())

@@ -17,10 +17,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 MUTATIONS = {
     "green_U2_coefficient": ("c2 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0))",
                              "c2 = (lam0 + mu0) / (mu0 * (lam0 + 1.0 * mu0))"),
-    "green_U1_sign": ("u1 = -(d[k, i]", "u1 = (d[k, i]"),
+    "green_U1_sign": ("u1 = u1 - delta * pp", "u1 = u1 + delta * pp"),
     "nyquist_kept": ("k[n // 2] = 0.0                            # Nyquist index -> 0", "pass"),
-    "g0_sign": ("W[nzm] = np.linalg.solve(K[nzm], V[nzm][..., None])[..., 0]",
-                "W[nzm] = -np.linalg.solve(K[nzm], V[nzm][..., None])[..., 0]"),
+    "g0_sign": ("return np.stack([(v_hat[i] - c * xi[i] * xv * iq) * iq / mu0 for i in range(3)])",
+                "return np.stack([-(v_hat[i] - c * xi[i] * xv * iq) * iq / mu0 for i in range(3)])"),
+    "g0_coefficient": ("c = (lam0 + mu0) / (lam0 + 2.0 * mu0)\n    xv", "c = (lam0 + mu0) / (lam0 + 1.0 * mu0)\n    xv"),
     "sym_grad_sign": ("out[a] = 0.5j * (xi[j] * u_hat[i] + xi[i] * u_hat[j])",
                       "out[a] = -0.5j * (xi[j] * u_hat[i] + xi[i] * u_hat[j])"),
     "mean_strain_dft_scale": ("eb0_hat[:, 0, 0, 0] = n * np.asarray", "eb0_hat[:, 0, 0, 0] = np.asarray"),
@@ -30,6 +31,7 @@ MUTATIONS = {
     "lame_trace_term": ("out[:3] += lam * tr", "out[:3] += 0.5 * lam * tr"),
     "shear_counted_once": ("acc = acc + (c1 * u1 + c2 * u2) * t[k][l]",
                            "acc = acc + (c1 * u1 + c2 * u2) * t[k][l] * (1.0 if k <= l else 0.0)"),
+    "green_U2_dropped": ("u2 = P[i][j] * P[k][l]", "u2 = 0.0"),
     "average_normalisation": ("return acc / m, hits, infos", "return acc / (m + 1), hits, infos"),
     "body_force_sign": ("-6.0 * x * s * s / (a * a)", "6.0 * x * s * s / (a * a)"),
     "sphere_boundary_exclusive": ("ph[d2 <= T] = p", "ph[d2 < T] = p"),
