@@ -67,7 +67,7 @@ typedef struct {
   double resid;         /* residual (Eq. 5.11 reading below) of the returned strain, FP64 */
   double resid_prev;    /* residual of the iterate that triggered the stop */
   int precision_path;   /* 0 = FP32 sweeps, 1 = FP64 sweeps */
-  int pad;
+  int stalled;          /* 1 if the residual did not drop by 10% over 100 sweeps (stops the solve) */
   double ms;            /* host wall time of the call, milliseconds */
 } bfcs_info;
 
@@ -136,7 +136,9 @@ int bfcs_body_force(int nx, int ny, int nz, double cx, double cy, double cz, dou
  *           eps^S - <eps^S> and zero mean (Eqs. 2.9-2.10).
  *  info:    host, filled on return (may be NULL).
  * Sweep s forms tau^s = (L - L0) eps^s, its transform, the residual r(eps^s)
- * and eps^{s+1}; the call stops after the first sweep with r(eps^s) <= tol.
+ * and eps^{s+1}; the call stops after the first sweep with r(eps^s) <= tol,
+ * or when the residual has not dropped by 10% over 100 sweeps (a stalled
+ * fixed point, e.g. the FP32 rounding floor; status NOT_CONVERGED, info.stalled = 1).
  * Residual (reading of Eq. 5.11): r = ||i xi.sigma_hat + b_hat|| / D over modes
  * with xi != 0, D = ||b_hat|| + (2 pi / max N_a) |sigma_hat(0)|.  With a warm
  * start r(eps^0) is not evaluated (reported as +inf).

@@ -39,7 +39,7 @@ class Lame(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("resid", C.c_double),
-                ("resid_prev", C.c_double), ("precision_path", C.c_int), ("pad", C.c_int),
+                ("resid_prev", C.c_double), ("precision_path", C.c_int), ("stalled", C.c_int),
                 ("ms", C.c_double)]
 
 

@@ -48,11 +48,12 @@ class SolveInfo:
     resid_prev: float
     precision_path: int
     ms: float
+    stalled: int = 0
 
     @staticmethod
     def of(info: _lib.Info) -> "SolveInfo":
         return SolveInfo(info.iters, info.status, info.resid, info.resid_prev, info.precision_path,
-                         info.ms)
+                         info.ms, info.stalled)
 
 
 def kernel_launches() -> int:

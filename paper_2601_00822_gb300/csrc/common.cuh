@@ -211,12 +211,16 @@ __device__ __forceinline__ int signed_k(int k, int n) {
 // Residual bookkeeping written by the Green pass, reduced in FP64.
 struct ResidSlot { double num; double pad; };
 
-// Device-side iteration state of one solve.
+// Device-side iteration state of one solve.  Everything before resid_last is
+// zeroed at the start of a solve.
 struct IterState {
-  int done;          // 1 once r <= tol (further sweeps become no-ops)
+  int done;          // 1 once r <= tol, the iteration stalled or diverged (later sweeps are no-ops)
   int iters;         // sweeps executed
   int diverged;      // NaN/Inf seen
+  int stalled;       // no 10% drop of the residual over the stall window
+  int stall_at;      // sweep of the last stall checkpoint
   int pad;
+  double stall_ref;  // residual at that checkpoint (0 = none yet)
   double resid_last;
   double bden;       // sqrt(sum |b_hat|^2) over modes with xi != 0
   double resid_final;

@@ -247,7 +247,7 @@ cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterSt
 __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
                                int hist_cap, int sweep, double tol, double lam0, double mu0, double E0,
                                double E1, double E2, double E3, double E4, double E5, double n,
-                               int maxdim, int mode, int skip_check) {
+                               int maxdim, int mode, int skip_check, int stall_window) {
   __shared__ double red[32];
   if (mode == GM_SWEEP && st->done) return;
   double acc = 0.0;
@@ -267,17 +267,26 @@ __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* st,
   if (sweep < hist_cap && hist != nullptr) hist[sweep] = r;
   st->resid_last = r;
   st->iters = sweep + 1;
-  if (!skip_check && !(r == r && r < INFINITY)) { st->diverged = 1; st->done = 1; }
-  else if (r <= tol) st->done = 1;
+  if (skip_check) return;
+  if (!(r == r && r < INFINITY)) { st->diverged = 1; st->done = 1; return; }
+  if (r <= tol) { st->done = 1; return; }
+  // stall: the residual did not drop by 10% over stall_window sweeps
+  if (stall_window > 0) {
+    if (st->stall_ref == 0.0) { st->stall_ref = r; st->stall_at = sweep; }
+    else if (sweep - st->stall_at >= stall_window) {
+      if (r > 0.9 * st->stall_ref) { st->stalled = 1; st->done = 1; }
+      else { st->stall_ref = r; st->stall_at = sweep; }
+    }
+  }
 }
 
 cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
                                 int hist_cap, int sweep, double tol, double lam0, double mu0,
                                 const double* E, long long n, int maxdim, int mode, int skip_check,
-                                cudaStream_t s) {
+                                int stall_window, cudaStream_t s) {
   k_resid_reduce<<<1, kRedThreads, 0, s>>>(part, nparts, st, hist, hist_cap, sweep, tol, lam0, mu0,
                                            E[0], E[1], E[2], E[3], E[4], E[5], (double)n, maxdim,
-                                           mode, skip_check);
+                                           mode, skip_check, stall_window);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -98,7 +98,7 @@ cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterSt
 cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
                                 int hist_cap, int sweep, double tol, double c0_lam, double c0_mu,
                                 const double* E, long long n, int maxdim, int mode, int skip_check,
-                                cudaStream_t s);
+                                int stall_window, cudaStream_t s);
 
 template <typename R>
 cudaError_t launch_accumulate(double* acc, int* hits, const R* eps, const R* sig, const R* u,

@@ -27,6 +27,7 @@ struct bfcs_plan_s {
   ResidSlot* part = nullptr;
   int npart = 0;              // slots allocated (>= every writer's block count)
   int ngreen = 0;             // blocks of the fused z/Green pass = residual partials per sweep
+  int stall_window = 100;     // sweeps without a 10% residual drop that end a solve
   IterState* ist = nullptr;
   IterState* ist_host = nullptr;   // pinned, 3 slots
   cudaEvent_t ev[2];
@@ -286,7 +287,7 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
     CK(timed(3, s, run_g, &ga, 0));
     CK(timed(2, s, run_c, &cy, +1));
     CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->hist, P->hist_cap, s, tol, C0.lambda, C0.mu,
-                           E, g.n, maxdim, GM_SWEEP, first_warm ? 1 : 0, st));
+                           E, g.n, maxdim, GM_SWEEP, first_warm ? 1 : 0, P->stall_window, st));
     return BFCS_OK;
   };
 
@@ -331,7 +332,7 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
   ga.done = nullptr;
   CK(launch_zgreen<R>(ga, st));
   CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->hist, P->hist_cap, s, tol, C0.lambda, C0.mu, E,
-                         g.n, maxdim, GM_FINAL, 0, st));
+                         g.n, maxdim, GM_FINAL, 0, 0, st));
   if (out.u != nullptr) {
     cy.ncomp = 3;
     CK(launch_colpass<R>(cy, +1, st));
@@ -360,13 +361,14 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
   P->prof_used = 0;
   int status = BFCS_OK;
   if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
-  else if (tol > 0 && !h.done) status = BFCS_NOT_CONVERGED;
+  else if (tol > 0 && (!h.done || h.stalled)) status = BFCS_NOT_CONVERGED;
   if (info != nullptr) {
     info->iters = h.iters;
     info->status = status;
     info->resid = h.resid_final;
     info->resid_prev = h.resid_last;
     info->precision_path = sizeof(R) == 8 ? 1 : 0;
+    info->stalled = h.stalled;
   }
   return status;
 }
