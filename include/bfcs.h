@@ -120,6 +120,31 @@ int bfcs_body_force(int nx, int ny, int nz, double cx, double cy, double cz, dou
                     void* b_out, void* stream);
 
 /*
+ * bfcs_body_force_noalloc - the same field as bfcs_body_force, for callers that
+ * must not allocate device memory during the call (their device memory is
+ * owned by their own pool or caching allocator, or an allocation could stall
+ * a time-critical loop).  It makes no cudaMalloc/cudaMallocAsync/cudaFree call
+ * and uses no allocating library routine.  The paper has no counterpart: this
+ * is an allocation-free way to produce the load of Eq. 2.5.
+ *  Scratch: a fixed 16 KiB FP64 array inside the library (2048 partial sums +
+ *           the mean), held on every GPU that loads the library until exit.
+ *  Limit:   nx*ny*nz <= 134217728 voxels (2048 blocks of 65536); larger grids
+ *           return BFCS_ERR_INVALID_ARG before any device work.
+ *  Set-up:  the first call on each device looks up the array's device address
+ *           (cudaGetSymbolAddress) with that device current; make that first
+ *           call before any stream capture on the device.
+ *  Sharing: every call uses the same array, which keeps the last call's
+ *           contents; each call writes every slot it reads before reading it,
+ *           so nothing needs clearing.  Calls whose work overlaps on the GPU
+ *           (different streams, no ordering) race on the array: order them on
+ *           one stream.  The mean is summed over a different number of blocks
+ *           than bfcs_body_force uses, so results may differ in the last bits.
+ * Arguments and layout as bfcs_body_force.
+ */
+int bfcs_body_force_noalloc(int nx, int ny, int nz, double cx, double cy, double cz, double a,
+                            int precision, void* b_out, void* stream);
+
+/*
  * bfcs_solve - modified basic scheme, Algorithm 1 (Eqs. 5.7-5.10).
  *  phase:   dev, N int8 phase ids in [0, nphases).
  *  phases:  host, nphases (1..16) isotropic phases, phase id = index.

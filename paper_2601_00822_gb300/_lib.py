@@ -29,7 +29,7 @@ EXPORTS = (
     "bfcs_plan_create", "bfcs_plan_destroy", "bfcs_voxelize", "bfcs_body_force", "bfcs_solve",
     "bfcs_solve_batched", "bfcs_translate_average", "bfcs_surrogate_infer", "bfcs_fft3d",
     "bfcs_last_history", "bfcs_status_string", "bfcs_kernel_launches", "bfcs_profile_kernel",
-    "bfcs_profile_read",
+    "bfcs_profile_read", "bfcs_body_force_noalloc",
 )
 
 
@@ -55,6 +55,7 @@ def _declare(lib):
     lib.bfcs_plan_destroy.argtypes = [vp]
     lib.bfcs_voxelize.argtypes = [i, i, i, i, i, i, i, vp, vp, vp]
     lib.bfcs_body_force.argtypes = [i, i, i, d, d, d, d, i, vp, vp]
+    lib.bfcs_body_force_noalloc.argtypes = [i, i, i, d, d, d, d, i, vp, vp]
     lib.bfcs_solve.argtypes = [vp, vp, i, C.POINTER(Lame), Lame, vp, C.POINTER(d), d, i, vp, vp, vp,
                                vp, C.POINTER(Info)]
     lib.bfcs_solve_batched.argtypes = [vp, i, C.POINTER(Problem), i, C.POINTER(Lame), Lame, d, i,

@@ -31,6 +31,7 @@ UNITS = [
     ("k_green.cu", ["-DBFCS_R=double"], "k_green_f64.o"),
     ("k_misc.cu", [], "k_misc.o"),
     ("solver.cu", [], "solver.o"),
+    ("noalloc.cu", [], "noalloc.o"),
 ]
 
 

@@ -140,6 +140,19 @@ cudaError_t launch_body_force(R* b, int nx, int ny, int nz, double cx, double cy
   return cudaGetLastError();
 }
 
+// Same three kernels with a caller-chosen block count; the scratch holds
+// `blocks` FP64 partial sums and the mean at scratch[blocks].
+template <typename R>
+cudaError_t launch_body_force_blocks(R* b, int nx, int ny, int nz, double cx, double cy, double cz,
+                                     double a, int blocks, double* scratch, cudaStream_t s) {
+  const long long n = (long long)nx * ny * nz;
+  k_bf_partial<<<blocks, kRedThreads, 0, s>>>(scratch, n, nx, ny, nz, cx, cy, cz, a);
+  k_sum_parts<<<1, kRedThreads, 0, s>>>(scratch, blocks, scratch + blocks, 1.0 / (double)n);
+  k_bf_write<R><<<blocks, kRedThreads, 0, s>>>(b, n, nx, ny, nz, cx, cy, cz, a, scratch + blocks);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- validation
 constexpr int kValBlocks = 512;
 
@@ -343,6 +356,8 @@ cudaError_t launch_scale(double* acc, long long count, double f, cudaStream_t s)
 #define BFCS_INST(R)                                                                              \
   template cudaError_t launch_body_force<R>(R*, int, int, int, double, double, double, double,     \
                                             double*, cudaStream_t);                               \
+  template cudaError_t launch_body_force_blocks<R>(R*, int, int, int, double, double, double,      \
+                                                   double, int, double*, cudaStream_t);           \
   template cudaError_t launch_validate<R>(const int8_t*, const R*, long long, int*, double*,       \
                                           double*, cudaStream_t);                                 \
   template cudaError_t launch_bden<R>(const C2<R>*, const Geo&, ResidSlot*, IterState*,            \

@@ -82,6 +82,10 @@ cudaError_t launch_body_force(R* b, int nx, int ny, int nz, double cx, double cy
                               double a, double* scratch /* >= body_force_scratch() doubles */,
                               cudaStream_t s);
 int body_force_scratch(long long n);
+template <typename R>
+cudaError_t launch_body_force_blocks(R* b, int nx, int ny, int nz, double cx, double cy, double cz,
+                                     double a, int blocks, double* scratch /* >= blocks + 1 doubles */,
+                                     cudaStream_t s);
 
 // validation: phase id range and body-force sums; out[0..1] = min/max phase,
 // dout[0..2] = sum b_c, dout[3..5] = sum |b_c|
