@@ -53,6 +53,7 @@ extern "C" {
 /* ---- plan flags */
 #define BFCS_FP32 0                   /* FP32 fields and FFTs, FP64 residual sums */
 #define BFCS_FP64 1                   /* FP64 throughout */
+#define BFCS_MIXED 2                  /* FP32 sweeps with FP64 defect correction; FP64 fields */
 
 #define BFCS_MAX_PHASES 16
 
@@ -89,7 +90,9 @@ typedef struct {
  *  nx,ny,nz:  grid (BFUC of Eq. 2.7 / Sec. 4 unit cell), even, supported sizes.
  *  max_batch: >= 1; members of bfcs_solve_batched are run in groups of at most
  *             this many.
- *  flags:     BFCS_FP32 or BFCS_FP64.
+ *  flags:     BFCS_FP32, BFCS_FP64 or BFCS_MIXED.  BFCS_MIXED runs the sweeps in
+ *             FP32 and corrects them in FP64 (below); its fields at the API
+ *             (b, eps, sigma, u, eps_init, fft3d data) are double.
  *  stream:    cudaStream_t to order work on (NULL = legacy default stream).
  * Allocates about (6 + 3 + 3) * nz*ny*(nx/2+4) complex values of workspace.
  * Errors: INVALID_ARG, OOM, CUDA.
@@ -167,6 +170,15 @@ int bfcs_body_force_noalloc(int nx, int ny, int nz, double cx, double cy, double
  * Residual (reading of Eq. 5.11): r = ||i xi.sigma_hat + b_hat|| / D over modes
  * with xi != 0, D = ||b_hat|| + (2 pi / max N_a) |sigma_hat(0)|.  With a warm
  * start r(eps^0) is not evaluated (reported as +inf).
+ * BFCS_MIXED plans (precision ladder): FP32 sweeps until r <= max(tol, 1e-4)
+ * or the FP32 stall, then rounds of defect correction: the residual of the
+ * FP64 strain is evaluated in FP64 (sigma = L eps, its transform, R_hat =
+ * i xi.sigma_hat + b_hat), and while it exceeds tol an FP32 solve with load R
+ * and E = 0 gives a correction added to the FP64 strain and displacement
+ * (at most 8 rounds; maxit bounds the FP32 sweeps of all rounds together).
+ * info.resid is then the FP64 residual of the returned FP64 strain, and an
+ * eps_init skips the first FP32 phase.  The FP32-only path cannot go below
+ * its rounding floor (~1e-7 times the load's length scale in voxels).
  * Returns OK, NOT_CONVERGED, INVALID_ARG, NONZERO_MEAN, CUDA, TIMEOUT, DIVERGED.
  */
 int bfcs_solve(bfcs_plan plan, const int8_t* phase, int nphases, const bfcs_lame* phases, bfcs_lame C0,

@@ -23,6 +23,7 @@ ERR_DIVERGED = -6
 ERR_UNSUPPORTED = -7
 FP32 = 0
 FP64 = 1
+MIXED = 2
 
 # every symbol declared in include/bfcs.h
 EXPORTS = (

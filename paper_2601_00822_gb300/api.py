@@ -3,7 +3,7 @@
 Only argument marshalling lives here: torch tensors supply device memory and
 the current CUDA stream; every step of the solver runs in libbfcs.so.
 Field tensors are contiguous, shaped (components, nz, ny, nx), float32 for
-'fp32' plans and float64 for 'fp64' plans.
+'fp32' plans and float64 for 'fp64' and 'mixed' plans.
 """
 from __future__ import annotations
 
@@ -77,9 +77,9 @@ def body_force(dims, centre, a, precision="fp32", device="cuda", stream=None) ->
     """bfcs_body_force: mean-free BFCS field (3, nz, ny, nx)."""
     lib = _lib.load()
     nx, ny, nz = dims
-    dt = torch.float64 if precision == "fp64" else torch.float32
+    dt = torch.float32 if precision == "fp32" else torch.float64
     out = torch.empty((3, nz, ny, nx), dtype=dt, device=device)
-    flag = _lib.FP64 if precision == "fp64" else _lib.FP32
+    flag = _lib.FP32 if precision == "fp32" else _lib.FP64
     _lib.check(lib.bfcs_body_force(nx, ny, nz, float(centre[0]), float(centre[1]), float(centre[2]),
                                    float(a), flag, _ptr(out), _stream_ptr(stream)), "bfcs_body_force")
     return out
@@ -92,10 +92,10 @@ class Plan:
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.precision = precision
-        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
-        flag = _lib.FP64 if precision == "fp64" else _lib.FP32
+        flag = {"fp32": _lib.FP32, "fp64": _lib.FP64, "mixed": _lib.MIXED}[precision]
         nx, ny, nz = self.dims
         _lib.check(self.lib.bfcs_plan_create(C.byref(h), nx, ny, nz, int(max_batch), flag,
                                              _stream_ptr(self.stream)), "bfcs_plan_create")

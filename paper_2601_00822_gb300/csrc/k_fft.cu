@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
   const int mode = a.mode;
 
   // ---- 1. stage the lines in shared memory, column f = i * npair + q
-  if (mode == XM_SWEEP || mode == XM_C2R) {
+  if (mode == XM_SWEEP || mode == XM_C2R || mode == XM_SWEEPSIG) {
     // Hermitian extension of the half spectrum into a full line for the pair
     // Z = A + i B; DC and Nyquist keep only their real parts (C2R rule).
     for (int idx = tid; idx < ncol * L; idx += nthr) {
@@ -90,8 +90,10 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
     return;
   }
 
-  // ---- 2. polarization tau = (L(x) - L0) eps, isotropic phases (Eq. 5.7)
-  if (mode == XM_SWEEP || mode == XM_REALTAU) {
+  // ---- 2. polarization tau = (L(x) - L0) eps, isotropic phases (Eq. 5.7);
+  //         in XM_REALSIG the full stress sigma = L(x) eps instead
+  if (mode == XM_SWEEP || mode == XM_REALTAU || mode == XM_REALSIG || mode == XM_SWEEPSIG) {
+    const bool full = mode == XM_REALSIG || mode == XM_SWEEPSIG;
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
     for (int idx = tid; idx < LPB * L; idx += nthr) {
       const int n = idx % L, i = idx / L;
@@ -119,7 +121,8 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
         o[0] = lt + m2 * e0; o[rn] = lt + m2 * e1; o[2 * rn] = lt + m2 * e2;
         o[3 * rn] = m2 * e3; o[4 * rn] = m2 * e4; o[5 * rn] = m2 * e5;
       }
-      const R lt = a.tab.lam1[ph] * tr, m2 = R(2) * a.tab.mu1[ph];
+      const R lt = (full ? a.tab.lam[ph] : a.tab.lam1[ph]) * tr;
+      const R m2 = R(2) * (full ? a.tab.mu[ph] : a.tab.mu1[ph]);
       c[0] = mk<R>(lt + m2 * e0, lt + m2 * e1);
       c[1] = mk<R>(lt + m2 * e2, m2 * e3);
       c[2] = mk<R>(m2 * e4, m2 * e5);

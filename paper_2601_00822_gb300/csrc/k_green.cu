@@ -174,6 +174,157 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS) k_zgreen(GArgs<R> a) {
   }
 }
 
+// Defect of an approximate strain (precision ladder): R_hat = i xi . sigma_hat +
+// b_hat on modes with xi != 0 (Eq. 2.1 in Fourier form with Eq. 4.8), the load
+// of the correction problem.  Grid-stride over the stored modes.
+template <typename R>
+__global__ void k_defect(DArgs<R> a) {
+  __shared__ double red[32];
+  const Geo g = a.g;
+  const long long modes = (long long)g.nz * g.ny * g.mx;
+  const R two_pi = R(6.283185307179586);
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.mx);
+    const long long r = i / g.mx;
+    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
+    const long long gi = r * g.p + kx;
+    const C2<R>* sp = a.spec + gi;
+    const R xi0 = two_pi / R(g.nx) * R(signed_k(kx, g.nx));
+    const R xi1 = two_pi / R(g.ny) * R(signed_k(ky, g.ny));
+    const R xi2 = two_pi / R(g.nz) * R(signed_k(kz, g.nz));
+    const C2<R> s0 = sp[0], s1 = sp[g.cs], s2 = sp[2 * g.cs], s3 = sp[3 * g.cs], s4 = sp[4 * g.cs],
+                s5 = sp[5 * g.cs];
+    if (kx == 0 && ky == 0 && kz == 0) {
+      a.st->tau0[0] = (double)s0.x; a.st->tau0[1] = (double)s1.x; a.st->tau0[2] = (double)s2.x;
+      a.st->tau0[3] = (double)s3.x; a.st->tau0[4] = (double)s4.x; a.st->tau0[5] = (double)s5.x;
+    }
+    C2<R> d[3];
+    if (xi0 == R(0) && xi1 == R(0) && xi2 == R(0)) {
+      d[0] = d[1] = d[2] = mk<R>(0, 0);
+    } else {
+      // sigma_hat . xi (xx yy zz yz xz xy), then i (.) + b_hat
+      const C2<R> v0 = scale(s0, xi0) + scale(s5, xi1) + scale(s4, xi2);
+      const C2<R> v1 = scale(s5, xi0) + scale(s1, xi1) + scale(s3, xi2);
+      const C2<R> v2 = scale(s4, xi0) + scale(s3, xi1) + scale(s2, xi2);
+      const C2<R> b0 = a.bhat[gi], b1 = a.bhat[g.cs + gi], b2 = a.bhat[2 * g.cs + gi];
+      d[0] = mk<R>(-v0.y + b0.x, v0.x + b0.y);
+      d[1] = mk<R>(-v1.y + b1.x, v1.x + b1.y);
+      d[2] = mk<R>(-v2.y + b2.x, v2.x + b2.y);
+      const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
+      double t = 0.0;
+      for (int c = 0; c < 3; ++c) t += (double)d[c].x * d[c].x + (double)d[c].y * d[c].y;
+      acc += w * t;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.out32[c * g.cs + gi] = mk<float>((float)d[c].x, (float)d[c].y);
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    a.part[blockIdx.x].num = t;
+  }
+}
+
+template <typename R>
+cudaError_t launch_defect(const DArgs<R>& a, int blocks, cudaStream_t st) {
+  k_defect<R><<<blocks, 256, 0, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_symgrad(C2<R>* spec, Geo g, R inv_n, R E0, R E1, R E2, R E3, R E4, R E5) {
+  const long long modes = (long long)g.nz * g.ny * g.mx;
+  const R two_pi = R(6.283185307179586);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.mx);
+    const long long r = i / g.mx;
+    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
+    C2<R>* sp = spec + r * g.p + kx;
+    const R x0 = two_pi / R(g.nx) * R(signed_k(kx, g.nx));
+    const R x1 = two_pi / R(g.ny) * R(signed_k(ky, g.ny));
+    const R x2 = two_pi / R(g.nz) * R(signed_k(kz, g.nz));
+    const C2<R> u0 = sp[0], u1 = sp[g.cs], u2 = sp[2 * g.cs];
+    C2<R> e[6];
+    if (x0 == R(0) && x1 == R(0) && x2 == R(0)) {
+      const bool k0 = kx == 0 && ky == 0 && kz == 0;
+      e[0] = mk<R>(k0 ? E0 : R(0), 0); e[1] = mk<R>(k0 ? E1 : R(0), 0); e[2] = mk<R>(k0 ? E2 : R(0), 0);
+      e[3] = mk<R>(k0 ? E3 : R(0), 0); e[4] = mk<R>(k0 ? E4 : R(0), 0); e[5] = mk<R>(k0 ? E5 : R(0), 0);
+    } else {
+      // eps_ij = (i/2)(xi_i u_j + xi_j u_i); i (a + ib) = (-b, a)
+      const R h = R(0.5) * inv_n;
+      auto ih = [&](C2<R> v, R f) { return mk<R>(-v.y * f, v.x * f); };
+      e[0] = ih(scale(u0, x0), inv_n);
+      e[1] = ih(scale(u1, x1), inv_n);
+      e[2] = ih(scale(u2, x2), inv_n);
+      e[3] = ih(scale(u2, x1) + scale(u1, x2), h);
+      e[4] = ih(scale(u2, x0) + scale(u0, x2), h);
+      e[5] = ih(scale(u1, x0) + scale(u0, x1), h);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sp[c * g.cs] = e[c];
+  }
+}
+
+template <typename R>
+cudaError_t launch_symgrad(C2<R>* spec, const Geo& g, const double* E, cudaStream_t st) {
+  k_symgrad<R><<<4 * 152, 256, 0, st>>>(spec, g, R(1.0 / (double)g.n), (R)E[0], (R)E[1], (R)E[2], (R)E[3],
+                                         (R)E[4], (R)E[5]);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_disp(C2<R>* spec, Geo g, R inv_n, R lam0, R mu0) {
+  const long long modes = (long long)g.nz * g.ny * g.mx;
+  const R two_pi = R(6.283185307179586);
+  const R c0 = (lam0 + mu0) / (lam0 + R(2) * mu0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.mx);
+    const long long r = i / g.mx;
+    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
+    C2<R>* sp = spec + r * g.p + kx;
+    R xi[3];
+    xi[0] = two_pi / R(g.nx) * R(signed_k(kx, g.nx));
+    xi[1] = two_pi / R(g.ny) * R(signed_k(ky, g.ny));
+    xi[2] = two_pi / R(g.nz) * R(signed_k(kz, g.nz));
+    const R q = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    C2<R> u[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+    if (q != R(0)) {
+      const C2<R> e0 = sp[0], e1 = sp[g.cs], e2 = sp[2 * g.cs], e3 = sp[3 * g.cs], e4 = sp[4 * g.cs],
+                  e5 = sp[5 * g.cs];
+      const C2<R> tr = scale(e0 + e1 + e2, lam0);
+      const R m2 = R(2) * mu0;
+      // w = (C0 eps_hat) xi
+      C2<R> w[3];
+      w[0] = scale(tr, xi[0]) + scale(scale(e0, xi[0]) + scale(e5, xi[1]) + scale(e4, xi[2]), m2);
+      w[1] = scale(tr, xi[1]) + scale(scale(e5, xi[0]) + scale(e1, xi[1]) + scale(e3, xi[2]), m2);
+      w[2] = scale(tr, xi[2]) + scale(scale(e4, xi[0]) + scale(e3, xi[1]) + scale(e2, xi[2]), m2);
+      C2<R> v[3];
+      g0_apply<R>(w, xi, q, mu0, c0, v);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u[k] = mk<R>(v[k].y * inv_n, -v[k].x * inv_n);   // -i v / N
+    }
+    sp[0] = u[0];
+    sp[g.cs] = u[1];
+    sp[2 * g.cs] = u[2];
+  }
+}
+
+template <typename R>
+cudaError_t launch_disp(C2<R>* spec, const Geo& g, double lam0, double mu0, cudaStream_t st) {
+  k_disp<R><<<4 * 152, 256, 0, st>>>(spec, g, R(1.0 / (double)g.n), (R)lam0, (R)mu0);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template <typename R>
 int green_nparts(const Geo& g) {
   return ((g.mx + kGreenT - 1) / kGreenT) * g.ny;
@@ -204,5 +355,8 @@ cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t st) {
 
 template cudaError_t launch_zgreen<BFCS_R>(const GArgs<BFCS_R>&, cudaStream_t);
 template int green_nparts<BFCS_R>(const Geo&);
+template cudaError_t launch_defect<BFCS_R>(const DArgs<BFCS_R>&, int, cudaStream_t);
+template cudaError_t launch_symgrad<BFCS_R>(C2<BFCS_R>*, const Geo&, const double*, cudaStream_t);
+template cudaError_t launch_disp<BFCS_R>(C2<BFCS_R>*, const Geo&, double, double, cudaStream_t);
 
 }  // namespace bfcs

@@ -270,12 +270,14 @@ __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* st,
   const double E[6] = {E0, E1, E2, E3, E4, E5};
   const double trE = E0 + E1 + E2;
   double s0[6];
-  for (int c = 0; c < 6; ++c) s0[c] = n * (2.0 * mu0 * E[c] + (c < 3 ? lam0 * trE : 0.0)) + st->tau0[c];
+  for (int c = 0; c < 6; ++c)
+    s0[c] = mode == kReduceDefect ? st->tau0[c]
+                                  : n * (2.0 * mu0 * E[c] + (c < 3 ? lam0 * trE : 0.0)) + st->tau0[c];
   const double s0n = sqrt(s0[0] * s0[0] + s0[1] * s0[1] + s0[2] * s0[2] +
                           2.0 * (s0[3] * s0[3] + s0[4] * s0[4] + s0[5] * s0[5]));
   const double den = st->bden + 6.283185307179586 / (double)maxdim * s0n;
   double r = den > 0.0 ? sqrt(t) / den : sqrt(t);
-  if (mode == GM_FINAL) { st->resid_final = r; return; }
+  if (mode == GM_FINAL || mode == kReduceDefect) { st->resid_final = r; return; }
   if (skip_check) r = INFINITY;
   if (sweep < hist_cap && hist != nullptr) hist[sweep] = r;
   st->resid_last = r;
@@ -349,6 +351,76 @@ __global__ void k_scale(double* acc, long long count, double f) {
 
 cudaError_t launch_scale(double* acc, long long count, double f, cudaStream_t s) {
   k_scale<<<4 * 152, 256, 0, s>>>(acc, count, f);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- precision-ladder helpers
+__global__ void k_cast_d2f(float* dst, const double* src, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+__global__ void k_cast_f2d(double* dst, const float* src, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+__global__ void k_add_f2d(double* dst, const float* src, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] += (double)src[i];
+}
+cudaError_t launch_cast_d2f(float* dst, const double* src, long long count, cudaStream_t s) {
+  k_cast_d2f<<<8 * 152, 256, 0, s>>>(dst, src, count);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_cast_f2d(double* dst, const float* src, long long count, cudaStream_t s) {
+  k_cast_f2d<<<8 * 152, 256, 0, s>>>(dst, src, count);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_f2d(double* dst, const float* src, long long count, cudaStream_t s) {
+  k_add_f2d<<<8 * 152, 256, 0, s>>>(dst, src, count);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_cast_spec(C2<float>* dst, const C2<double>* src, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const C2<double> v = src[i];
+    dst[i] = mk<float>((float)v.x, (float)v.y);
+  }
+}
+cudaError_t launch_cast_spec(C2<float>* dst, const C2<double>* src, const Geo& g, int ncomp, cudaStream_t s) {
+  k_cast_spec<<<8 * 152, 256, 0, s>>>(dst, src, (long long)ncomp * g.cs);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_stress(double* sig, const double* eps, const int8_t* phase, PhaseTab<double> tab, int sx,
+                         int sy, int sz, int nx, int ny, int nz) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+    int xs = (x - sx) % nx; if (xs < 0) xs += nx;
+    int ys = (y - sy) % ny; if (ys < 0) ys += ny;
+    int zs = (z - sz) % nz; if (zs < 0) zs += nz;
+    const int ph = phase[((long long)zs * ny + ys) * nx + xs];
+    const double e0 = eps[v], e1 = eps[n + v], e2 = eps[2 * n + v];
+    const double lt = tab.lam[ph] * (e0 + e1 + e2), m2 = 2.0 * tab.mu[ph];
+    sig[v] = lt + m2 * e0;
+    sig[n + v] = lt + m2 * e1;
+    sig[2 * n + v] = lt + m2 * e2;
+    for (int c = 3; c < 6; ++c) sig[c * n + v] = m2 * eps[c * n + v];
+  }
+}
+cudaError_t launch_stress(double* sig, const double* eps, const int8_t* phase, const PhaseTab<double>& tab,
+                          int sx, int sy, int sz, int nx, int ny, int nz, cudaStream_t s) {
+  k_stress<<<8 * 152, 256, 0, s>>>(sig, eps, phase, tab, sx, sy, sz, nx, ny, nz);
   count_launches(1);
   return cudaGetLastError();
 }

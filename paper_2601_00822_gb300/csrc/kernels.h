@@ -12,6 +12,8 @@ enum XMode : int {
   XM_REALTAU = 1,  // real eps (warm start) -> tau -> R2C -> spectrum
   XM_R2C = 2,      // plain forward real -> half spectrum along x
   XM_C2R = 3,      // plain inverse half spectrum -> real along x
+  XM_REALSIG = 4,  // real eps -> sigma = L eps -> R2C -> spectrum (defect evaluation)
+  XM_SWEEPSIG = 5, // spectrum -> C2R -> eps (written) -> sigma = L eps -> R2C -> spectrum
 };
 
 template <typename R> struct XArgs {
@@ -63,7 +65,30 @@ template <typename R> struct GArgs {
   int mode;
 };
 
+// ---- defect of an approximate strain on the fully transformed stress spectrum:
+// R_hat = i xi . sigma_hat + b_hat on modes with xi != 0 (0 elsewhere), written
+// as complex64 to out32; per-block partial sums of w |R_hat|^2; sigma_hat(0)
+// (6 values) into st->tau0.
+template <typename R> struct DArgs {
+  const C2<R>* spec;      // 6 components: sigma_hat
+  const C2<R>* bhat;      // 3 components
+  C2<float>* out32;       // 3 components: R_hat rounded to complex64 (the FP32 correction load)
+  Geo g;
+  ResidSlot* part;
+  IterState* st;
+};
+
+// eps_hat = sym(i xi (x) u_hat) / N on modes with xi != 0, E at k = 0, 0 on the
+// other xi = 0 modes: components 0..2 of `spec` (u_hat, fully transformed) in,
+// components 0..5 out, in place.
+template <typename R> cudaError_t launch_symgrad(C2<R>* spec, const Geo& g, const double* E, cudaStream_t s);
+// u_hat = -i G0(xi) (C0 eps_hat) xi / N on modes with xi != 0, else 0: the
+// displacement whose symmetric gradient is the compatible part of eps (in the
+// C0 energy norm); components 0..5 in, 0..2 out, in place.
+template <typename R> cudaError_t launch_disp(C2<R>* spec, const Geo& g, double lam0, double mu0, cudaStream_t s);
+
 template <typename R> cudaError_t launch_xpass(const XArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_defect(const DArgs<R>& a, int blocks, cudaStream_t s);
 template <typename R> cudaError_t launch_colpass(const CArgs<R>& a, int dir, cudaStream_t s);
 template <typename R> cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t s);
 template <typename R> int green_nparts(const Geo& g);
@@ -103,6 +128,18 @@ cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st
                                 int hist_cap, int sweep, double tol, double c0_lam, double c0_mu,
                                 const double* E, long long n, int maxdim, int mode, int skip_check,
                                 int stall_window, cudaStream_t s);
+// mode for launch_resid_reduce: tau0 already holds sigma_hat(0) (defect evaluation)
+constexpr int kReduceDefect = 7;
+
+// elementwise helpers (k_misc.cu)
+cudaError_t launch_cast_d2f(float* dst, const double* src, long long count, cudaStream_t s);
+cudaError_t launch_cast_f2d(double* dst, const float* src, long long count, cudaStream_t s);
+cudaError_t launch_add_f2d(double* dst, const float* src, long long count, cudaStream_t s);
+// complex128 -> complex64 copy of ncomp spectral components (same geometry)
+cudaError_t launch_cast_spec(C2<float>* dst, const C2<double>* src, const Geo& g, int ncomp, cudaStream_t s);
+// sigma = L(x) eps pointwise (FP64), phase translated by (sx, sy, sz)
+cudaError_t launch_stress(double* sig, const double* eps, const int8_t* phase, const PhaseTab<double>& tab,
+                          int sx, int sy, int sz, int nx, int ny, int nz, cudaStream_t s);
 
 template <typename R>
 cudaError_t launch_accumulate(double* acc, int* hits, const R* eps, const R* sig, const R* u,

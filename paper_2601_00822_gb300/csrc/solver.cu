@@ -15,7 +15,8 @@ using namespace bfcs;
 
 struct bfcs_plan_s {
   int nx, ny, nz, max_batch, flags;
-  bool fp64;
+  bool fp64;                  // sweeps in FP64 (BFCS_FP64)
+  bool mixed;                 // FP32 sweeps + FP64 defect correction (BFCS_MIXED)
   cudaStream_t st;
   Geo g;
   size_t csz;                 // bytes of one complex value
@@ -48,6 +49,15 @@ struct bfcs_plan_s {
   int prof_used = 0;
   long long prof_launches = 0;
   double prof_ms = 0.0;
+  // precision ladder (BFCS_MIXED): FP64 transform workspace and FP32 real scratch
+  void* spec64 = nullptr;          // 6 x cs complex128
+  void* bhat64 = nullptr;          // 3 x cs complex128
+  void* tw64[3] = {nullptr, nullptr, nullptr};
+  IterState* ist64 = nullptr;
+  float* r32 = nullptr;            // 12 x N floats: b32 (3) | eps32 (6) | u32 (3)
+  double* u64 = nullptr;           // 3 x N doubles: FP64 displacement when the caller passes none
+  int max_rounds = 8;              // defect-correction rounds
+  double switch_tol = 1e-4;        // FP32 phase stops here (or at the stall)
 };
 
 namespace {
@@ -112,6 +122,8 @@ void free_plan(bfcs_plan P) {
   cudaFree(P->part); cudaFree(P->ist); cudaFree(P->hist);
   cudaFree(P->ival); cudaFree(P->dval); cudaFree(P->dscratch);
   cudaFree(P->tmp); cudaFree(P->tmp_hits);
+  cudaFree(P->spec64); cudaFree(P->bhat64); cudaFree(P->ist64); cudaFree(P->r32); cudaFree(P->u64);
+  for (int i = 0; i < 3; ++i) cudaFree(P->tw64[i]);
   if (P->ist_host) cudaFreeHost(P->ist_host);
   if (P->ival_host) cudaFreeHost(P->ival_host);
   if (P->dval_host) cudaFreeHost(P->dval_host);
@@ -163,28 +175,33 @@ int validate_inputs(bfcs_plan P, const int8_t* phase, const void* b, int nph) {
   return BFCS_OK;
 }
 
-// b_hat = F(b): x R2C, then y and z forward, into the plan's b_hat buffer.
+// b_hat = F(b): x R2C, then y and z forward, into `dst` (3 components).
 template <typename R>
-int transform_load(bfcs_plan P, const void* b) {
+int transform_into(bfcs_plan P, const void* b, void* dst, void* const* tw) {
   XArgs<R> xa{};
   xa.g = P->g;
   xa.real_in = (const R*)b;
-  xa.spec_out = (C2<R>*)P->bhat;
+  xa.spec_out = (C2<R>*)dst;
   xa.ncomp = 3;
   xa.mode = XM_R2C;
-  xa.tw = (const C2<R>*)P->tw[0];
+  xa.tw = (const C2<R>*)tw[0];
   CK(launch_xpass<R>(xa, P->st));
   CArgs<R> ca{};
-  ca.data = (C2<R>*)P->bhat;
+  ca.data = (C2<R>*)dst;
   ca.g = P->g;
   ca.ncomp = 3;
   ca.axis = 1;
-  ca.tw = (const C2<R>*)P->tw[1];
+  ca.tw = (const C2<R>*)tw[1];
   CK(launch_colpass<R>(ca, -1, P->st));
   ca.axis = 2;
-  ca.tw = (const C2<R>*)P->tw[2];
+  ca.tw = (const C2<R>*)tw[2];
   CK(launch_colpass<R>(ca, -1, P->st));
   return BFCS_OK;
+}
+
+template <typename R>
+int transform_load(bfcs_plan P, const void* b) {
+  return transform_into<R>(P, b, P->bhat, P->tw);
 }
 
 struct SolveOut {
@@ -392,6 +409,178 @@ int solve_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phase
                        info);
 }
 
+// FP64 strain and defect from the FP64 displacement (precision ladder):
+// eps64 = E + sym grad u64 (spectral, exactly compatible), then sigma = L eps64,
+// its transform, R_hat = i xi . sigma_hat + b_hat, the FP64 residual r(eps64)
+// into ist64->resid_final, and R_hat rounded to complex64 into the plan's FP32
+// load spectrum (the load of the correction problem, already transformed).
+// eps64 is written to `eps_out`.  Needs b_hat64 and ist64->bden.
+int defect64(bfcs_plan P, const int8_t* phase, const PhaseTab<double>& tab, bfcs_lame C0, const double* E,
+             const double* u64, double* eps_out, const int shift[3]) {
+  const Geo g = P->g;
+  cudaStream_t st = P->st;
+  C2<double>* spec = (C2<double>*)P->spec64;
+  int e = transform_into<double>(P, u64, spec, P->tw64);            // u_hat (3 components)
+  if (e != BFCS_OK) return e;
+  CK(launch_symgrad<double>(spec, g, E, st));                        // eps_hat / N (6 components)
+  CArgs<double> ca{};
+  ca.data = spec;
+  ca.g = g;
+  ca.ncomp = 6;
+  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
+  CK(launch_colpass<double>(ca, +1, st));
+  ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
+  CK(launch_colpass<double>(ca, +1, st));
+  XArgs<double> xa{};                                                // eps out, sigma = L eps, R2C
+  xa.g = g;
+  xa.spec_in = spec;
+  xa.spec_out = spec;
+  xa.eps_out = eps_out;
+  xa.phase = phase;
+  xa.sx = shift[0]; xa.sy = shift[1]; xa.sz = shift[2];
+  xa.tab = tab;
+  xa.tw = (const C2<double>*)P->tw64[0];
+  xa.ncomp = 6;
+  xa.mode = XM_SWEEPSIG;
+  CK(launch_xpass<double>(xa, st));
+  CK(launch_colpass<double>(ca, -1, st));                            // y forward
+  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
+  CK(launch_colpass<double>(ca, -1, st));                            // z forward
+  DArgs<double> da{};
+  da.spec = spec;
+  da.bhat = (const C2<double>*)P->bhat64;
+  da.out32 = (C2<float>*)P->bhat;
+  da.g = g;
+  da.part = P->part;
+  da.st = P->ist64;
+  const int blocks = 512;
+  CK(launch_defect<double>(da, blocks, st));
+  const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
+  CK(launch_resid_reduce(P->part, blocks, P->ist64, nullptr, 0, 0, 0.0, C0.lambda, C0.mu, E, g.n, maxdim,
+                         kReduceDefect, 0, 0, st));
+  return BFCS_OK;
+}
+
+// FP32 sweeps with FP64 defect correction; every field at the API is FP64.
+// The FP64 state is the displacement u64, so the strain eps64 = E + sym grad
+// u64 stays exactly compatible.  Phase 1: FP32 solve to max(tol, switch_tol)
+// (or its stall), u64 = its displacement.  Then rounds: eps64 and its FP64
+// residual r64; stop when r64 <= tol; else solve the correction problem (load
+// = the FP64 defect rounded to FP32, E = 0) in FP32 to 0.5 tol / r64 and add
+// its displacement to u64.
+int solve_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                const void* b, const double* E, double tol, int maxit, const void* eps_init, SolveOut out,
+                const int shift[3], bfcs_info* info) {
+  int e = check_material(nph, phases, C0);
+  if (e != BFCS_OK) return e;
+  if (phase == nullptr || b == nullptr || E == nullptr || out.eps == nullptr) return BFCS_ERR_INVALID_ARG;
+  if (!(tol >= 0) || maxit < 0) return BFCS_ERR_INVALID_ARG;
+  for (int c = 0; c < 6; ++c)
+    if (!std::isfinite(E[c])) return BFCS_ERR_INVALID_ARG;
+  e = validate_inputs<double>(P, phase, b, nph);
+  if (e != BFCS_OK) return e;
+  const Geo g = P->g;
+  const long long n = g.n;
+  cudaStream_t st = P->st;
+  float* eps32 = P->r32 + 3 * n;
+  float* u32 = eps32 + 6 * n;
+  double* eps64 = (double*)out.eps;
+  double* u64 = out.u != nullptr ? (double*)out.u : P->u64;
+  const PhaseTab<float> tab32 = make_tab<float>(nph, phases, C0);
+  const PhaseTab<double> tab64 = make_tab<double>(nph, phases, C0);
+  const double zeroE[6] = {0, 0, 0, 0, 0, 0};
+
+  // FP64 load transform and its norm (residual denominator)
+  e = transform_into<double>(P, b, P->bhat64, P->tw64);
+  if (e != BFCS_OK) return e;
+  CK(cudaMemsetAsync(P->ist64, 0, sizeof(IterState), st));
+  CK(launch_bden<double>((const C2<double>*)P->bhat64, g, P->part, P->ist64, st));
+
+  int sweeps = 0, stalled = 0;
+  double r_last = INFINITY;
+  CK(launch_cast_spec((C2<float>*)P->bhat, (const C2<double>*)P->bhat64, g, 3, st));   // FP32 load spectrum
+  CK(launch_bden<float>((const C2<float>*)P->bhat, g, P->part, P->ist, st));
+  if (eps_init == nullptr) {
+    bfcs_info inf{};
+    const int s1 = solve_core<float>(P, phase, tab32, C0, E, std::max(tol, P->switch_tol), maxit, nullptr,
+                                     SolveOut{eps32, nullptr, u32}, shift, &inf);
+    if (s1 < 0) return s1;
+    sweeps += inf.iters;
+    r_last = inf.resid;
+    CK(launch_cast_f2d(u64, u32, 3 * n, st));
+  } else {
+    // warm start: u64 from the compatible part of eps_init, in FP64
+    C2<double>* spec = (C2<double>*)P->spec64;
+    XArgs<double> xa{};
+    xa.g = g;
+    xa.real_in = (const double*)eps_init;
+    xa.spec_out = spec;
+    xa.ncomp = 6;
+    xa.mode = XM_R2C;
+    xa.tw = (const C2<double>*)P->tw64[0];
+    CK(launch_xpass<double>(xa, st));
+    CArgs<double> ca{};
+    ca.data = spec;
+    ca.g = g;
+    ca.ncomp = 6;
+    ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
+    CK(launch_colpass<double>(ca, -1, st));
+    ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
+    CK(launch_colpass<double>(ca, -1, st));
+    CK(launch_disp<double>(spec, g, C0.lambda, C0.mu, st));
+    ca.ncomp = 3;
+    CK(launch_colpass<double>(ca, +1, st));
+    ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
+    CK(launch_colpass<double>(ca, +1, st));
+    XArgs<double> xc{};
+    xc.g = g;
+    xc.spec_in = spec;
+    xc.real_out = u64;
+    xc.ncomp = 3;
+    xc.mode = XM_C2R;
+    xc.tw = (const C2<double>*)P->tw64[0];
+    CK(launch_xpass<double>(xc, st));
+  }
+
+  double r64 = INFINITY;
+  for (int round = 0;; ++round) {
+    e = defect64(P, phase, tab64, C0, E, u64, eps64, shift);
+    if (e != BFCS_OK) return e;
+    CK(cudaMemcpyAsync(&P->ist_host[2], P->ist64, sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    const int w = sync_stream(P);
+    if (w != BFCS_OK) return w;
+    r64 = P->ist_host[2].resid_final;
+    if (!std::isfinite(r64)) return BFCS_ERR_DIVERGED;
+    if (r64 <= tol || round >= P->max_rounds || sweeps >= maxit) break;
+    // correction problem: load = the defect (its spectrum is already in place), E = 0, cold start
+    CK(launch_bden<float>((const C2<float>*)P->bhat, g, P->part, P->ist, st));
+    const double tol_c = std::min(0.5, std::max(0.5 * tol / r64, 1e-7));
+    bfcs_info inf{};
+    const int s2 = solve_core<float>(P, phase, tab32, C0, zeroE, tol_c, maxit - sweeps, nullptr,
+                                     SolveOut{eps32, nullptr, u32}, shift, &inf);
+    if (s2 < 0) return s2;
+    sweeps += inf.iters;
+    stalled = inf.stalled;
+    CK(launch_add_f2d(u64, u32, 3 * n, st));
+  }
+  if (out.sig != nullptr)
+    CK(launch_stress((double*)out.sig, eps64, phase, tab64, shift[0], shift[1], shift[2], g.nx, g.ny, g.nz,
+                     st));
+  const int w = sync_stream(P);
+  if (w != BFCS_OK) return w;
+  P->last_iters = 0;     // history of the FP32 phases is not kept across rounds
+  const int status = r64 <= tol ? BFCS_OK : BFCS_NOT_CONVERGED;
+  if (info != nullptr) {
+    info->iters = sweeps;
+    info->status = status;
+    info->resid = r64;
+    info->resid_prev = r_last;
+    info->precision_path = 2;
+    info->stalled = stalled;
+  }
+  return status;
+}
+
 int ensure_tmp(bfcs_plan P) {
   if (P->tmp == nullptr) {
     if (cudaMalloc(&P->tmp, 15 * (size_t)P->g.n * P->rsz) != cudaSuccess) return BFCS_ERR_OOM;
@@ -442,6 +631,36 @@ int translate_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* p
   return w != BFCS_OK ? w : worst;
 }
 
+int translate_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                    const void* b, const double* E, int nshift, const int32_t* shifts, double tol, int maxit,
+                    double* avg, int32_t* hits, bfcs_info* infos) {
+  if (avg == nullptr || shifts == nullptr || nshift < 1) return BFCS_ERR_INVALID_ARG;
+  int e = ensure_tmp(P);
+  if (e != BFCS_OK) return e;
+  const long long n = P->g.n;
+  int* h = hits != nullptr ? (int*)hits : P->tmp_hits;
+  CK(cudaMemsetAsync(avg, 0, 30 * n * sizeof(double), P->st));
+  CK(cudaMemsetAsync(h, 0, n * sizeof(int), P->st));
+  double* eps = (double*)P->tmp;
+  double* sig = eps + 6 * n;
+  double* u = sig + 6 * n;
+  int worst = BFCS_OK;
+  for (int m = 0; m < nshift; ++m) {
+    const int sh[3] = {shifts[3 * m], shifts[3 * m + 1], shifts[3 * m + 2]};
+    bfcs_info inf{};
+    const int s = solve_mixed(P, phase, nph, phases, C0, b, E, tol, maxit, nullptr, SolveOut{eps, sig, u}, sh,
+                              &inf);
+    if (s < 0) return s;
+    if (s > worst) worst = s;
+    if (infos != nullptr) infos[m] = inf;
+    CK(launch_accumulate<double>(avg, h, eps, sig, u, phase, sh[0], sh[1], sh[2], P->g.nx, P->g.ny,
+                                 P->g.nz, P->st));
+  }
+  CK(launch_scale(avg, 30 * n, 1.0 / nshift, P->st));
+  const int w = sync_stream(P);
+  return w != BFCS_OK ? w : worst;
+}
+
 int severity(int s) { return s < 0 ? 1000 - s : s; }
 
 }  // namespace
@@ -467,13 +686,14 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   if (out == nullptr) return BFCS_ERR_INVALID_ARG;
   *out = nullptr;
   if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz) || max_batch < 1 ||
-      (flags & ~BFCS_FP64) != 0)
+      (flags != BFCS_FP32 && flags != BFCS_FP64 && flags != BFCS_MIXED))
     return BFCS_ERR_INVALID_ARG;
   bfcs_plan P = new bfcs_plan_s();
   P->nx = nx; P->ny = ny; P->nz = nz;
   P->max_batch = max_batch;
   P->flags = flags;
-  P->fp64 = (flags & BFCS_FP64) != 0;
+  P->fp64 = flags == BFCS_FP64;
+  P->mixed = flags == BFCS_MIXED;
   P->st = (cudaStream_t)stream;
   P->g.nx = nx; P->g.ny = ny; P->g.nz = nz;
   P->g.mx = nx / 2 + 1;
@@ -481,7 +701,7 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   P->g.cs = (long long)nz * ny * P->g.p;
   P->g.n = (long long)nx * ny * nz;
   P->csz = P->fp64 ? sizeof(C2<double>) : sizeof(C2<float>);
-  P->rsz = P->fp64 ? sizeof(double) : sizeof(float);
+  P->rsz = (P->fp64 || P->mixed) ? sizeof(double) : sizeof(float);
   P->ev[0] = P->ev[1] = nullptr;
   bool ok = cudaEventCreateWithFlags(&P->ev[0], cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&P->ev[1], cudaEventDisableTiming) == cudaSuccess;
@@ -508,6 +728,18 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   for (int a = 0; a < 3; ++a) {
     P->tw[a] = P->fp64 ? make_twiddles<double>(dims[a]) : make_twiddles<float>(dims[a]);
     if (P->tw[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
+  }
+  if (P->mixed) {
+    ok = cudaMalloc(&P->spec64, 6 * cs * sizeof(C2<double>)) == cudaSuccess &&
+         cudaMalloc(&P->bhat64, 3 * cs * sizeof(C2<double>)) == cudaSuccess &&
+         cudaMalloc(&P->ist64, sizeof(IterState)) == cudaSuccess &&
+         cudaMalloc(&P->r32, 12 * (size_t)P->g.n * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&P->u64, 3 * (size_t)P->g.n * sizeof(double)) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
+    for (int a = 0; a < 3; ++a) {
+      P->tw64[a] = make_twiddles<double>(dims[a]);
+      if (P->tw64[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
+    }
   }
   if (cudaMemset(P->ist, 0, sizeof(IterState)) != cudaSuccess) { free_plan(P); return BFCS_ERR_CUDA; }
   *out = P;
@@ -567,10 +799,12 @@ int bfcs_solve(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phase
   const auto t0 = std::chrono::steady_clock::now();
   const int shift[3] = {0, 0, 0};
   const SolveOut out{eps_out, sig_out, u_out};
-  const int s = P->fp64 ? solve_impl<double>(P, phase, nph, phases, C0, b, E, tol, maxit, eps_init, out,
-                                             shift, info)
-                        : solve_impl<float>(P, phase, nph, phases, C0, b, E, tol, maxit, eps_init, out,
-                                            shift, info);
+  const int s = P->mixed ? solve_mixed(P, phase, nph, phases, C0, b, E, tol, maxit, eps_init, out, shift,
+                                       info)
+                : P->fp64 ? solve_impl<double>(P, phase, nph, phases, C0, b, E, tol, maxit, eps_init, out,
+                                               shift, info)
+                          : solve_impl<float>(P, phase, nph, phases, C0, b, E, tol, maxit, eps_init, out,
+                                              shift, info);
   if (info != nullptr) {
     info->status = s;
     info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -586,10 +820,12 @@ int bfcs_solve_batched(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, 
     const auto t0 = std::chrono::steady_clock::now();
     const SolveOut out{pr[m].eps_out, pr[m].sig_out, pr[m].u_out};
     bfcs_info inf{};
-    const int s = P->fp64 ? solve_impl<double>(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol,
-                                               maxit, pr[m].eps_init, out, pr[m].shift, &inf)
-                          : solve_impl<float>(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol,
-                                              maxit, pr[m].eps_init, out, pr[m].shift, &inf);
+    const int s = P->mixed  ? solve_mixed(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol, maxit,
+                                          pr[m].eps_init, out, pr[m].shift, &inf)
+                  : P->fp64 ? solve_impl<double>(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol,
+                                                 maxit, pr[m].eps_init, out, pr[m].shift, &inf)
+                            : solve_impl<float>(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol,
+                                                maxit, pr[m].eps_init, out, pr[m].shift, &inf);
     inf.status = s;
     inf.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (infos != nullptr) infos[m] = inf;
@@ -603,6 +839,9 @@ int bfcs_translate_average(bfcs_plan P, const int8_t* phase, int nph, const bfcs
                            const int32_t* shifts, double tol, int maxit, double* avg_out,
                            int32_t* hits_out, bfcs_info* infos) {
   if (P == nullptr) return BFCS_ERR_INVALID_ARG;
+  if (P->mixed)
+    return translate_mixed(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit, avg_out, hits_out,
+                           infos);
   return P->fp64 ? translate_impl<double>(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit,
                                           avg_out, hits_out, infos)
                  : translate_impl<float>(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit,
@@ -616,10 +855,11 @@ int bfcs_surrogate_infer(bfcs_plan, const void*, const void*, const int8_t*, int
 }  // extern "C"
 
 template <typename R>
-static int fft3d_impl(bfcs_plan P, int dir, int ncomp, const void* in, void* out) {
+static int fft3d_impl(bfcs_plan P, int dir, int ncomp, const void* in, void* out, void* specbuf,
+                      void* const* twb) {
   const Geo g = P->g;
   const size_t csz = sizeof(C2<R>);
-  C2<R>* spec = (C2<R>*)P->spec;
+  C2<R>* spec = (C2<R>*)specbuf;
   CArgs<R> ca{};
   ca.data = spec;
   ca.g = g;
@@ -627,25 +867,25 @@ static int fft3d_impl(bfcs_plan P, int dir, int ncomp, const void* in, void* out
   XArgs<R> xa{};
   xa.g = g;
   xa.ncomp = ncomp;
-  xa.tw = (const C2<R>*)P->tw[0];
+  xa.tw = (const C2<R>*)twb[0];
   const size_t rows = (size_t)ncomp * g.nz * g.ny;
   if (dir < 0) {
     xa.mode = XM_R2C;
     xa.real_in = (const R*)in;
     xa.spec_out = spec;
     CK(launch_xpass<R>(xa, P->st));
-    ca.axis = 1; ca.tw = (const C2<R>*)P->tw[1];
+    ca.axis = 1; ca.tw = (const C2<R>*)twb[1];
     CK(launch_colpass<R>(ca, -1, P->st));
-    ca.axis = 2; ca.tw = (const C2<R>*)P->tw[2];
+    ca.axis = 2; ca.tw = (const C2<R>*)twb[2];
     CK(launch_colpass<R>(ca, -1, P->st));
     CK(cudaMemcpy2DAsync(out, g.mx * csz, spec, g.p * csz, g.mx * csz, rows, cudaMemcpyDeviceToDevice,
                          P->st));
   } else {
     CK(cudaMemcpy2DAsync(spec, g.p * csz, in, g.mx * csz, g.mx * csz, rows, cudaMemcpyDeviceToDevice,
                          P->st));
-    ca.axis = 2; ca.tw = (const C2<R>*)P->tw[2];
+    ca.axis = 2; ca.tw = (const C2<R>*)twb[2];
     CK(launch_colpass<R>(ca, +1, P->st));
-    ca.axis = 1; ca.tw = (const C2<R>*)P->tw[1];
+    ca.axis = 1; ca.tw = (const C2<R>*)twb[1];
     CK(launch_colpass<R>(ca, +1, P->st));
     xa.mode = XM_C2R;
     xa.spec_in = spec;
@@ -661,8 +901,9 @@ int bfcs_fft3d(bfcs_plan P, int direction, int ncomp, const void* in, void* out)
   if (P == nullptr || in == nullptr || out == nullptr || ncomp < 1 || ncomp > 6 ||
       (direction != -1 && direction != 1))
     return BFCS_ERR_INVALID_ARG;
-  return P->fp64 ? fft3d_impl<double>(P, direction, ncomp, in, out)
-                 : fft3d_impl<float>(P, direction, ncomp, in, out);
+  if (P->mixed) return fft3d_impl<double>(P, direction, ncomp, in, out, P->spec64, P->tw64);
+  return P->fp64 ? fft3d_impl<double>(P, direction, ncomp, in, out, P->spec, P->tw)
+                 : fft3d_impl<float>(P, direction, ncomp, in, out, P->spec, P->tw);
 }
 
 long long bfcs_kernel_launches(void) { return launches_so_far(); }
