@@ -185,6 +185,36 @@ __device__ __forceinline__ void fft_cols(C2<R>* s, int ncol, const C2<R>* __rest
   __syncthreads();
 }
 
+// Register-staged pieces of the same four-step FFT.  A thread holding the R1
+// inputs x[R2 n1 + n2] (n1 = 0..R1-1) of one line runs stage1(); after the
+// exchange through shared memory a thread holding the R2 values Y[n2][k1]
+// (n2 = 0..R2-1) runs stage2() and owns the outputs X[k1 + R1 k2].
+template <typename R, int L, int DIR>
+__device__ __forceinline__ void stage1(C2<R>* x, int n2, const C2<R>* __restrict__ tw) {
+  constexpr int R1 = LineInfo<L>::R1;
+  Dft<R, R1, DIR>::run(x);
+#pragma unroll
+  for (int k1 = 1; k1 < R1; ++k1) {
+    C2<R> w = tw[(n2 * k1) % L];
+    if (DIR > 0) w.y = -w.y;
+    x[k1] = cmul(x[k1], w);
+  }
+}
+template <typename R, int L, int DIR>
+__device__ __forceinline__ void stage2(C2<R>* y) {
+  Dft<R, LineInfo<L>::R2, DIR>::run(y);
+}
+
+// ------------------------------------------------------------------ async copies
+// 16-byte global -> shared copy that does not pass through registers
+// (cp.async, completion tracked per thread with commit/wait groups).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------ problem descriptors
 constexpr int kMaxPhases = 16;
 

@@ -13,23 +13,33 @@
 
 namespace bfcs {
 
-// lines per block of the x pass: about 64 register-DFT tasks per pair column
+// x pass: LPB lines per block, each line as up to 3 complex pair-lines
+// (components 2q and 2q+1 as real and imaginary parts), one group of TPF
+// threads per pair-line.  Pair-line f keeps its L values in shared memory at
+// s[f * LP + pad(n)], pad(n) = n + n/16, which keeps every access below free
+// of bank conflicts.
 template <int L> struct XCfg {
   static constexpr int RMAX = LineInfo<L>::RMAX;
-  static constexpr int LPB = 64 / RMAX > 0 ? 64 / RMAX : 1;
-  static constexpr int NCOL = 3 * LPB;        // up to 3 complex pair-columns per line
-  static constexpr int THREADS = NCOL * RMAX;
+  static constexpr int TPF = RMAX <= 2 ? 2 : RMAX <= 4 ? 4 : RMAX <= 8 ? 8 : 16;   // threads per pair-line
+  static constexpr int LPB = 64 / TPF;
+  static constexpr int NCOL = 3 * LPB;
+  static constexpr int LP = L + L / 16 + 1;
+  static constexpr int THREADS = NCOL * TPF;
 };
+
+__device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
 
 template <typename R, int L>
 __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
   if (a.done != nullptr && *a.done) return;
-  constexpr int LPB = XCfg<L>::LPB;
+  using C = XCfg<L>;
+  constexpr int LPB = C::LPB, TPF = C::TPF, LP = C::LP;
+  constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
   constexpr int H = L / 2;
   extern __shared__ unsigned char smem_raw[];
   C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);
 
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const int ncomp = a.ncomp;
   const int npair = (ncomp + 1) >> 1;
   const int ncol = LPB * npair;
@@ -38,70 +48,88 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
   const long long cs = a.g.cs, rn = a.g.n;
   const int p = a.g.p;
   const int mode = a.mode;
+  // this thread's pair-line and lane within it
+  const int f = tid / TPF, t = tid % TPF;
+  const int li = f / npair, q = f - li * npair;
+  const long long line = line0 + li;
+  const bool fval = f < ncol && line < lines;
+  const bool has_b = 2 * q + 1 < ncomp;
+  C2<R>* sf = s + f * LP;
 
-  // ---- 1. stage the lines in shared memory, column f = i * npair + q
+  // ---- 1. inverse transform along x of the pair-line Z = A + i B (C2R), or load real data
   if (mode == XM_SWEEP || mode == XM_C2R || mode == XM_SWEEPSIG) {
-    // Hermitian extension of the half spectrum into a full line for the pair
-    // Z = A + i B; DC and Nyquist keep only their real parts (C2R rule).
-    for (int idx = tid; idx < ncol * L; idx += nthr) {
-      const int k = idx % L, f = idx / L;
-      const int i = f / npair, q = f - i * npair;
-      const long long line = line0 + i;
-      C2<R> z = mk<R>(0, 0);
-      if (line < lines) {
+    if (fval && t < R2) {
+      const C2<R>* rowA = a.spec_in + (2 * q) * cs + line * p;
+      const C2<R>* rowB = rowA + cs;
+      C2<R> x[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) {
+        const int k = R2 * n1 + t;
         const int kk = k <= H ? k : L - k;
-        const C2<R>* row = a.spec_in + line * p + kk;
-        C2<R> A = row[(2 * q) * cs];
-        C2<R> B = (2 * q + 1 < ncomp) ? row[(2 * q + 1) * cs] : mk<R>(0, 0);
-        if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }
-        if (k > H) { A.y = -A.y; B.y = -B.y; }
-        z = mk<R>(A.x - B.y, A.y + B.x);
+        C2<R> A = rowA[kk];
+        C2<R> B = has_b ? rowB[kk] : mk<R>(0, 0);
+        if (kk == 0 || kk == H) { A.y = 0; B.y = 0; }     // DC and Nyquist keep their real parts
+        if (k > H) { A.y = -A.y; B.y = -B.y; }            // Hermitian extension
+        x[n1] = mk<R>(A.x - B.y, A.y + B.x);
       }
-      s[k * ncol + f] = z;
-    }
-    fft_cols<R, L, +1>(s, ncol, a.tw);
-  } else {
-    for (int idx = tid; idx < ncol * L; idx += nthr) {
-      const int n = idx % L, f = idx / L;
-      const int i = f / npair, q = f - i * npair;
-      const long long line = line0 + i;
-      C2<R> z = mk<R>(0, 0);
-      if (line < lines) {
-        const R* row = a.real_in + line * L + n;
-        z.x = row[(2 * q) * rn];
-        z.y = (2 * q + 1 < ncomp) ? row[(2 * q + 1) * rn] : R(0);
-      }
-      s[n * ncol + f] = z;
+      stage1<R, L, +1>(x, t, a.tw);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) sf[xpad(t * R1 + k1)] = x[k1];
     }
     __syncthreads();
+    C2<R> y[R2];
+    if (fval && t < R1) {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) y[n2] = sf[xpad(n2 * R1 + t)];
+      stage2<R, L, +1>(y);
+    }
+    __syncthreads();
+    if (fval && t < R1) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) sf[xpad(t + R1 * k2)] = y[k2];
+    }
+  } else {
+    for (int idx = tid; idx < ncol * L; idx += blockDim.x) {
+      const int n = idx % L, ff = idx / L;
+      const int i = ff / npair, qq = ff - i * npair;
+      const long long ln = line0 + i;
+      C2<R> z = mk<R>(0, 0);
+      if (ln < lines) {
+        const R* row = a.real_in + ln * L + n;
+        z.x = row[(2 * qq) * rn];
+        z.y = (2 * qq + 1 < ncomp) ? row[(2 * qq + 1) * rn] : R(0);
+      }
+      s[ff * LP + xpad(n)] = z;
+    }
   }
+  __syncthreads();
 
   if (mode == XM_C2R) {
-    for (int idx = tid; idx < ncol * L; idx += nthr) {
-      const int n = idx % L, f = idx / L;
-      const int i = f / npair, q = f - i * npair;
-      const long long line = line0 + i;
-      if (line >= lines) continue;
-      const C2<R> z = s[n * ncol + f];
-      R* row = a.real_out + line * L + n;
-      row[(2 * q) * rn] = z.x;
-      if (2 * q + 1 < ncomp) row[(2 * q + 1) * rn] = z.y;
+    for (int idx = tid; idx < ncol * L; idx += blockDim.x) {
+      const int n = idx % L, ff = idx / L;
+      const int i = ff / npair, qq = ff - i * npair;
+      const long long ln = line0 + i;
+      if (ln >= lines) continue;
+      const C2<R> z = s[ff * LP + xpad(n)];
+      R* row = a.real_out + ln * L + n;
+      row[(2 * qq) * rn] = z.x;
+      if (2 * qq + 1 < ncomp) row[(2 * qq + 1) * rn] = z.y;
     }
     return;
   }
 
   // ---- 2. polarization tau = (L(x) - L0) eps, isotropic phases (Eq. 5.7);
-  //         in XM_REALSIG the full stress sigma = L(x) eps instead
+  //         sigma = L(x) eps instead in the stress modes
   if (mode == XM_SWEEP || mode == XM_REALTAU || mode == XM_REALSIG || mode == XM_SWEEPSIG) {
     const bool full = mode == XM_REALSIG || mode == XM_SWEEPSIG;
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    for (int idx = tid; idx < LPB * L; idx += nthr) {
+    for (int idx = tid; idx < LPB * L; idx += blockDim.x) {
       const int n = idx % L, i = idx / L;
-      const long long line = line0 + i;
-      if (line >= lines) continue;
-      const int y = (int)(line % ny), z = (int)(line / ny);
-      C2<R>* c = s + n * ncol + i * 3;
-      const C2<R> p0 = c[0], p1 = c[1], p2 = c[2];
+      const long long ln = line0 + i;
+      if (ln >= lines) continue;
+      const int y = (int)(ln % ny), z = (int)(ln / ny);
+      C2<R>* c0 = s + (i * 3) * LP + xpad(n);
+      const C2<R> p0 = c0[0], p1 = c0[LP], p2 = c0[2 * LP];
       // eps: xx yy zz yz xz xy
       const R e0 = p0.x, e1 = p0.y, e2 = p1.x, e3 = p1.y, e4 = p2.x, e5 = p2.y;
       int xs = n - a.sx, ys = y - a.sy, zs = z - a.sz;
@@ -110,7 +138,7 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
       zs %= nz; if (zs < 0) zs += nz;
       const int ph = a.phase[((long long)zs * ny + ys) * nx + xs];
       const R tr = e0 + e1 + e2;
-      const long long vox = line * L + n;
+      const long long vox = ln * L + n;
       if (a.eps_out != nullptr) {
         R* o = a.eps_out + vox;
         o[0] = e0; o[rn] = e1; o[2 * rn] = e2; o[3 * rn] = e3; o[4 * rn] = e4; o[5 * rn] = e5;
@@ -123,24 +151,52 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
       }
       const R lt = (full ? a.tab.lam[ph] : a.tab.lam1[ph]) * tr;
       const R m2 = R(2) * (full ? a.tab.mu[ph] : a.tab.mu1[ph]);
-      c[0] = mk<R>(lt + m2 * e0, lt + m2 * e1);
-      c[1] = mk<R>(lt + m2 * e2, m2 * e3);
-      c[2] = mk<R>(m2 * e4, m2 * e5);
+      c0[0] = mk<R>(lt + m2 * e0, lt + m2 * e1);
+      c0[LP] = mk<R>(lt + m2 * e2, m2 * e3);
+      c0[2 * LP] = mk<R>(m2 * e4, m2 * e5);
     }
+    __syncthreads();
   }
 
-  // ---- 3. forward transform of the pair lines and split into two half spectra
-  fft_cols<R, L, -1>(s, ncol, a.tw);
-  for (int idx = tid; idx < ncol * (H + 1); idx += nthr) {
-    const int k = idx % (H + 1), f = idx / (H + 1);
-    const int i = f / npair, q = f - i * npair;
-    const long long line = line0 + i;
-    if (line >= lines) continue;
-    const C2<R> Z = s[k * ncol + f];
-    const C2<R> Zm = s[((L - k) % L) * ncol + f];
-    C2<R>* row = a.spec_out + line * p + k;
-    row[(2 * q) * cs] = mk<R>(R(0.5) * (Z.x + Zm.x), R(0.5) * (Z.y - Zm.y));
-    if (2 * q + 1 < ncomp) row[(2 * q + 1) * cs] = mk<R>(R(0.5) * (Z.y + Zm.y), R(-0.5) * (Z.x - Zm.x));
+  // ---- 3. forward transform along x and split the pair-line into two half spectra
+  {
+    C2<R> x[R1];
+    if (fval && t < R2) {
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) x[n1] = sf[xpad(R2 * n1 + t)];
+      stage1<R, L, -1>(x, t, a.tw);
+    }
+    __syncthreads();
+    if (fval && t < R2) {
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) sf[xpad(t * R1 + k1)] = x[k1];
+    }
+  }
+  __syncthreads();
+  C2<R> y[R2];
+  if (fval && t < R1) {
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) y[n2] = sf[xpad(n2 * R1 + t)];
+    stage2<R, L, -1>(y);
+  }
+  // Thread k1 owns Z[k1 + R1 k2]; Z[L - k] sits in thread (R1 - k1) % R1 at
+  // k2' = R2 - 1 - k2 (k1 > 0) or (R2 - k2) % R2 (k1 = 0): one shuffle per k2.
+  const int lane = threadIdx.x & 31;
+  const int src = (lane & ~(TPF - 1)) | ((R1 - t) % R1);
+  C2<R>* rowA = a.spec_out + (2 * q) * cs + line * p;
+  C2<R>* rowB = rowA + cs;
+#pragma unroll
+  for (int k2 = 0; k2 < R2; ++k2) {
+    const C2<R> send = (t == 0) ? y[(R2 - k2) % R2] : y[(R2 - 1 - k2 + R2) % R2];
+    C2<R> zm;
+    zm.x = __shfl_sync(0xffffffffu, send.x, src);
+    zm.y = __shfl_sync(0xffffffffu, send.y, src);
+    const int k = t + R1 * k2;
+    if (fval && t < R1 && k <= H) {
+      const C2<R> Z = y[k2];
+      rowA[k] = mk<R>(R(0.5) * (Z.x + zm.x), R(0.5) * (Z.y - zm.y));
+      if (has_b) rowB[k] = mk<R>(R(0.5) * (Z.y + zm.y), R(-0.5) * (Z.x - zm.x));
+    }
   }
 }
 
@@ -153,27 +209,41 @@ template <int L> struct CCfg {
 };
 
 template <typename R, int L, int DIR>
-__global__ void __launch_bounds__(CCfg<L>::THREADS) k_colpass(CArgs<R> a) {
+__global__ void __launch_bounds__(CCfg<L>::THREADS, sizeof(R) == 4 ? 3 : 1) k_colpass(CArgs<R> a) {
   if (a.done != nullptr && *a.done) return;
+  constexpr int T = kColT, R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
   extern __shared__ unsigned char smem_raw[];
   C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const int mx = a.g.mx, p = a.g.p, ny = a.g.ny;
   const int other = a.axis == 1 ? a.g.nz : ny;
-  const int c = blockIdx.y / other, o = blockIdx.y - c * other;
+  const int comp = blockIdx.y / other, o = blockIdx.y - comp * other;
   const long long ls = a.axis == 1 ? (long long)p : (long long)ny * p;
-  C2<R>* base = a.data + c * a.g.cs + (a.axis == 1 ? (long long)o * ny * p : (long long)o * p);
-  const int col0 = blockIdx.x * kColT;
-  for (int idx = tid; idx < kColT * L; idx += nthr) {
-    const int col = idx % kColT, n = idx / kColT;
-    const int kx = col0 + col;
-    s[n * kColT + col] = kx < mx ? base[n * ls + kx] : mk<R>(0, 0);
+  C2<R>* base = a.data + comp * a.g.cs + (a.axis == 1 ? (long long)o * ny * p : (long long)o * p);
+  const int c = tid % T, j = tid / T;
+  const int kx = blockIdx.x * T + c;
+  const bool valid = kx < mx;
+  C2<R>* col = base + kx;
+  // stage 1 straight from global: thread (c, j) owns rows R2 n1 + j of column c
+  if (j < R2) {
+    C2<R> x[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) x[n1] = valid ? col[(R2 * n1 + j) * ls] : mk<R>(0, 0);
+    stage1<R, L, DIR>(x, j, a.tw);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * T + c] = x[k1];
   }
-  fft_cols<R, L, DIR>(s, kColT, a.tw);
-  for (int idx = tid; idx < kColT * L; idx += nthr) {
-    const int col = idx % kColT, n = idx / kColT;
-    const int kx = col0 + col;
-    if (kx < mx) base[n * ls + kx] = s[n * kColT + col];
+  __syncthreads();
+  // stage 2, outputs straight to global: thread (c, j) owns rows j + R1 k2
+  if (j < R1) {
+    C2<R> y[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * T + c];
+    stage2<R, L, DIR>(y);
+    if (valid) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) col[(j + R1 * k2) * ls] = y[k2];
+    }
   }
 }
 
@@ -183,7 +253,7 @@ static cudaError_t xpass_L(const XArgs<R>& a, cudaStream_t st) {
   using C = XCfg<L>;
   const long long lines = (long long)a.g.ny * a.g.nz;
   const unsigned grid = (unsigned)((lines + C::LPB - 1) / C::LPB);
-  const size_t smem = sizeof(C2<R>) * (size_t)L * C::NCOL;
+  const size_t smem = sizeof(C2<R>) * (size_t)C::LP * C::NCOL;
   cudaError_t e = cudaFuncSetAttribute(k_xpass<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

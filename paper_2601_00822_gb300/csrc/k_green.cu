@@ -40,12 +40,14 @@ __device__ __forceinline__ void g0_apply(const C2<R> g[3], const R xi[3], R q, R
 }
 
 template <typename R, int L>
-__global__ void __launch_bounds__(GCfg<L>::THREADS) k_zgreen(GArgs<R> a) {
+__global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zgreen(GArgs<R> a) {
   if (a.done != nullptr && *a.done) return;
   constexpr int T = kGreenT;
   constexpr int NCOL = GCfg<L>::NCOL;
+  constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
   extern __shared__ unsigned char smem_raw[];
-  C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);
+  C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);      // [n][c], c = component * T + column
+  C2<R>* pre = s + L * NCOL;                          // [6][n][col]: b_hat 0..2, d_prev 3..5
   __shared__ double red[32];
 
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -56,31 +58,69 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS) k_zgreen(GArgs<R> a) {
   const long long zs = (long long)ny * p;          // z stride
   const long long rowbase = (long long)ky * p;
   const int mode = a.mode;
+  // line-column owned by this thread in the FFT stages
+  const int c = tid % NCOL, j = tid / NCOL;
+  const int ccomp = c / T, ccol = c - ccomp * T;
+  const int ckx = col0 + ccol;
+  const bool cvalid = ckx < mx;
+  C2<R>* gcol = a.spec + ccomp * cs + rowbase + ckx;  // element z of this column at gcol[z * zs]
 
-  // ---- load the six component tiles and transform forward along z
-  if (mode != GM_INIT) {
-    for (int idx = tid; idx < NCOL * L; idx += nthr) {
-      const int col = idx % T, c = (idx / T) % 6, n = idx / NCOL;
-      const int kx = col0 + col;
-      s[n * NCOL + c * T + col] =
-          kx < mx ? a.spec[c * cs + n * zs + rowbase + kx] : mk<R>(0, 0);
+  // ---- start the copies of the b_hat and d_prev tiles; they land during the FFT
+  {
+    constexpr int PER = 16 / sizeof(C2<R>);          // complex values per 16-byte copy
+    constexpr int CPR = T / PER;                     // copies per row of the tile
+    const int narr = mode == GM_INIT ? 3 : 6;
+    for (int idx = tid; idx < narr * L * CPR; idx += nthr) {
+      const int part = idx % CPR, n = (idx / CPR) % L, arr = idx / (CPR * L);
+      const C2<R>* src = (arr < 3 ? a.bhat + arr * cs : a.dprev + (arr - 3) * cs) + n * zs + rowbase +
+                         col0 + part * PER;
+      cp_async16(pre + (arr * L + n) * T + part * PER, src);
     }
-    fft_cols<R, L, -1>(s, NCOL, a.tw);
+    cp_async_commit();
   }
+
+  // ---- forward transform along z: stage 1 straight from global
+  if (mode != GM_INIT) {
+    if (j < R2) {
+      C2<R> x[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) x[n1] = cvalid ? gcol[(R2 * n1 + j) * zs] : mk<R>(0, 0);
+      stage1<R, L, -1>(x, j, a.tw);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + c] = x[k1];
+    }
+    __syncthreads();
+    C2<R> y[R2];
+    if (j < R1) {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + c];
+      stage2<R, L, -1>(y);
+    }
+    __syncthreads();
+    if (j < R1) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) s[(j + R1 * k2) * NCOL + c] = y[k2];
+    }
+    __syncthreads();
+  }
+
+  cp_async_wait_all();
+  __syncthreads();
 
   // ---- Green operators per mode
   const R two_pi = R(6.283185307179586);
   const R fx = two_pi / R(nx), fy = two_pi / R(ny), fz = two_pi / R(L);
   const R mu0 = a.mu0, c0 = (a.lam0 + a.mu0) / (a.lam0 + R(2) * a.mu0);
   const R inv_n = a.inv_n;
-  double acc = 0.0;
+  R acc = R(0);
   for (int idx = tid; idx < T * L; idx += nthr) {
     const int col = idx % T, n = idx / T;
     const int kx = col0 + col;
-    C2<R>* m = s + n * NCOL + col;                  // component c at m[c * T]
+    C2<R>* m = s + n * NCOL + col;                  // component q at m[q * T]
+    const C2<R>* pm = pre + n * T + col;            // array r at pm[r * L * T]
     if (kx >= mx) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) m[c * T] = mk<R>(0, 0);
+      for (int q = 0; q < 6; ++q) m[q * T] = mk<R>(0, 0);
       continue;
     }
     const long long gi = n * zs + rowbase + kx;     // index in a 3-component spectrum
@@ -88,23 +128,26 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS) k_zgreen(GArgs<R> a) {
     xi[0] = fx * R(signed_k(kx, nx));
     xi[1] = fy * R(signed_k(ky, ny));
     xi[2] = fz * R(signed_k(n, L));
-    const R q = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    const R qq = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
     const R wgt = (kx == 0 || 2 * kx == nx) ? R(1) : R(2);
 
-    if (q == R(0)) {
+    if (qq == R(0)) {
       const bool k0 = (kx == 0 && ky == 0 && n == 0);
       if (k0 && mode != GM_INIT && a.st != nullptr) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) a.st->tau0[c] = (double)m[c * T].x;
+        for (int q = 0; q < 6; ++q) a.st->tau0[q] = (double)m[q * T].x;
       }
       if (mode == GM_SWEEP || mode == GM_INIT) {
         a.dprev[gi] = mk<R>(0, 0); a.dprev[cs + gi] = mk<R>(0, 0); a.dprev[2 * cs + gi] = mk<R>(0, 0);
       }
 #pragma unroll
-      for (int c = 0; c < 6; ++c)
-        m[c * T] = (mode != GM_FINAL && k0) ? mk<R>(a.E[c], R(0)) : mk<R>(0, 0);
+      for (int q = 0; q < 6; ++q)
+        m[q * T] = (mode != GM_FINAL && k0) ? mk<R>(a.E[q], R(0)) : mk<R>(0, 0);
       continue;
     }
+    const C2<R> bh0 = pm[0], bh1 = pm[L * T], bh2 = pm[2 * L * T];
+    C2<R> dp[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+    if (mode != GM_INIT) { dp[0] = pm[3 * L * T]; dp[1] = pm[4 * L * T]; dp[2] = pm[5 * L * T]; }
 
     C2<R> d[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
     if (mode != GM_INIT) {
@@ -113,14 +156,13 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS) k_zgreen(GArgs<R> a) {
       d[0] = scale(t0, xi[0]) + scale(t5, xi[1]) + scale(t4, xi[2]);
       d[1] = scale(t5, xi[0]) + scale(t1, xi[1]) + scale(t3, xi[2]);
       d[2] = scale(t4, xi[0]) + scale(t3, xi[1]) + scale(t2, xi[2]);
-      C2<R> dp[3] = {a.dprev[gi], a.dprev[cs + gi], a.dprev[2 * cs + gi]};
-      double r2 = 0.0;
+      R r2 = R(0);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const double ex = (double)d[i].x - (double)dp[i].x, ey = (double)d[i].y - (double)dp[i].y;
+        const R ex = d[i].x - dp[i].x, ey = d[i].y - dp[i].y;
         r2 += ex * ex + ey * ey;
       }
-      acc += (double)wgt * r2;
+      acc += wgt * r2;
       if (mode == GM_FINAL) { d[0] = dp[0]; d[1] = dp[1]; d[2] = dp[2]; }
     }
     if (mode == GM_SWEEP || mode == GM_INIT) {
@@ -128,19 +170,17 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS) k_zgreen(GArgs<R> a) {
     }
     // w = d - i b_hat
     C2<R> w[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const C2<R> bh = a.bhat[i * cs + gi];
-      w[i] = mk<R>(d[i].x + bh.y, d[i].y - bh.x);
-    }
+    w[0] = mk<R>(d[0].x + bh0.y, d[0].y - bh0.x);
+    w[1] = mk<R>(d[1].x + bh1.y, d[1].y - bh1.x);
+    w[2] = mk<R>(d[2].x + bh2.y, d[2].y - bh2.x);
     C2<R> v[3];
-    g0_apply<R>(w, xi, q, mu0, c0, v);
+    g0_apply<R>(w, xi, qq, mu0, c0, v);
     if (mode == GM_FINAL) {
       // u_hat = i v, scaled for the unnormalised inverse transforms
 #pragma unroll
       for (int i = 0; i < 3; ++i) m[i * T] = mk<R>(-v[i].y * inv_n, v[i].x * inv_n);
 #pragma unroll
-      for (int c = 3; c < 6; ++c) m[c * T] = mk<R>(0, 0);
+      for (int q = 3; q < 6; ++q) m[q * T] = mk<R>(0, 0);
     } else {
       const R h = R(-0.5) * inv_n;
       m[0] = scale(v[0], -xi[0] * inv_n);
@@ -152,25 +192,44 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS) k_zgreen(GArgs<R> a) {
     }
   }
 
-  // ---- residual partial of this block (fixed order: deterministic)
+  // ---- residual partial of this block in FP64 (fixed order: deterministic)
   if (mode != GM_INIT) {
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (nthr + 31) / 32; ++w) t += red[w];
-      a.part[blockIdx.y * gridDim.x + blockIdx.x].num = t;
-    }
+    double accd = (double)acc;
+    for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
+    if ((tid & 31) == 0) red[tid >> 5] = accd;
+  }
+  __syncthreads();
+  if (mode != GM_INIT && tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (nthr + 31) / 32; ++w) t += red[w];
+    a.part[blockIdx.y * gridDim.x + blockIdx.x].num = t;
   }
 
-  // ---- inverse transform along z and store
-  fft_cols<R, L, +1>(s, NCOL, a.tw);
-  const int ncs = mode == GM_FINAL ? 3 : 6;
-  for (int idx = tid; idx < NCOL * L; idx += nthr) {
-    const int col = idx % T, c = (idx / T) % 6, n = idx / NCOL;
-    const int kx = col0 + col;
-    if (kx < mx && c < ncs) a.spec[c * cs + n * zs + rowbase + kx] = s[n * NCOL + c * T + col];
+  // ---- inverse transform along z, stage 2 straight to global
+  const bool keep = mode != GM_FINAL || ccomp < 3;
+  {
+    C2<R> x[R1];
+    if (j < R2) {
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) x[n1] = s[((R2 * n1 + j) * NCOL) + c];
+      stage1<R, L, +1>(x, j, a.tw);
+    }
+    __syncthreads();
+    if (j < R2) {
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + c] = x[k1];
+    }
+  }
+  __syncthreads();
+  if (j < R1) {
+    C2<R> y[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + c];
+    stage2<R, L, +1>(y);
+    if (cvalid && keep) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) gcol[(j + R1 * k2) * zs] = y[k2];
+    }
   }
 }
 
@@ -333,7 +392,7 @@ int green_nparts(const Geo& g) {
 template <typename R, int L>
 static cudaError_t zgreen_L(const GArgs<R>& a, cudaStream_t st) {
   dim3 grid((a.g.mx + kGreenT - 1) / kGreenT, a.g.ny);
-  const size_t smem = sizeof(C2<R>) * (size_t)L * GCfg<L>::NCOL;
+  const size_t smem = sizeof(C2<R>) * (size_t)L * (GCfg<L>::NCOL + 6 * kGreenT);
   cudaError_t e = cudaFuncSetAttribute(k_zgreen<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
