@@ -45,18 +45,20 @@ __device__ __forceinline__ int min_image2(int v, int n2) {   // v in doubled uni
 
 __global__ void k_voxelize(int8_t* out, int nx, int ny, int nz, int cx, int cy, int cz,
                            const int* __restrict__ sph, int nsph) {
+  // one thread per voxel of the unit cell; its phase is written to every
+  // periodic replica of that voxel in the grid
   extern __shared__ int ssph[];
-  const long long n = (long long)nx * ny * nz;
+  const long long ncell = (long long)cx * cy * cz;
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-  const int ix = 2 * (x % cx) + 1, iy = 2 * (y % cy) + 1, iz = 2 * (z % cz) + 1;
+  const int x = (int)(v % cx), y = (int)((v / cx) % cy), z = (int)(v / ((long long)cx * cy));
+  const int ix = 2 * x + 1, iy = 2 * y + 1, iz = 2 * z + 1;
   int ph = 0;
   for (int base = 0; base < nsph; base += 1024) {
     const int cnt = min(1024, nsph - base);
     __syncthreads();
     for (int k = threadIdx.x; k < cnt * 5; k += blockDim.x) ssph[k] = sph[base * 5 + k];
     __syncthreads();
-    if (v < n) {
+    if (v < ncell) {
       for (int k = 0; k < cnt; ++k) {
         const int* S = ssph + 5 * k;
         const int dx = min_image2(ix - S[0], 2 * cx);
@@ -66,13 +68,18 @@ __global__ void k_voxelize(int8_t* out, int nx, int ny, int nz, int cx, int cy, 
       }
     }
   }
-  if (v < n) out[v] = (int8_t)ph;
+  if (v >= ncell) return;
+  const int rx = nx / cx, ry = ny / cy, rz = nz / cz;
+  for (int kz = 0; kz < rz; ++kz)
+    for (int ky = 0; ky < ry; ++ky)
+      for (int kx = 0; kx < rx; ++kx)
+        out[((long long)(kz * cz + z) * ny + (ky * cy + y)) * nx + (kx * cx + x)] = (int8_t)ph;
 }
 
 cudaError_t launch_voxelize(int8_t* out, int nx, int ny, int nz, int cx, int cy, int cz,
                             const int* sph_dev, int nsph, cudaStream_t s) {
-  const long long n = (long long)nx * ny * nz;
-  const unsigned grid = (unsigned)((n + 255) / 256);
+  const long long ncell = (long long)cx * cy * cz;
+  const unsigned grid = (unsigned)((ncell + 255) / 256);
   k_voxelize<<<grid, 256, 1024 * 5 * sizeof(int), s>>>(out, nx, ny, nz, cx, cy, cz, sph_dev, nsph);
   count_launches(1);
   return cudaGetLastError();
@@ -84,6 +91,15 @@ cudaError_t launch_voxelize(int8_t* out, int nx, int ny, int nz, int cx, int cy,
 __device__ __forceinline__ double bf_value(long long v, int nx, int ny, int nz, double cx, double cy,
                                            double cz, double a) {
   const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+  {
+    // cheap FP32 screen: voxels clearly outside the support (beyond a + 1 voxel) are 0
+    float fx = (float)x + 0.5f - (float)cx, fy = (float)y + 0.5f - (float)cy, fz = (float)z + 0.5f - (float)cz;
+    fx -= (float)nx * rintf(fx / (float)nx);
+    fy -= (float)ny * rintf(fy / (float)ny);
+    fz -= (float)nz * rintf(fz / (float)nz);
+    const float lim = (float)a + 1.0f;
+    if (fabsf(fx) > lim || fabsf(fy) > lim || fabsf(fz) > lim) return 0.0;
+  }
   double dx = x + 0.5 - cx, dy = y + 0.5 - cy, dz = z + 0.5 - cz;
   dx -= nx * rint(dx / nx);
   dy -= ny * rint(dy / ny);
@@ -299,7 +315,7 @@ cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st
                                 int hist_cap, int sweep, double tol, double lam0, double mu0,
                                 const double* E, long long n, int maxdim, int mode, int skip_check,
                                 int stall_window, cudaStream_t s) {
-  k_resid_reduce<<<1, kRedThreads, 0, s>>>(part, nparts, st, hist, hist_cap, sweep, tol, lam0, mu0,
+  k_resid_reduce<<<1, 1024, 0, s>>>(part, nparts, st, hist, hist_cap, sweep, tol, lam0, mu0,
                                            E[0], E[1], E[2], E[3], E[4], E[5], (double)n, maxdim,
                                            mode, skip_check, stall_window);
   count_launches(1);

@@ -308,9 +308,17 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
     return BFCS_OK;
   };
 
-  // sweeps in chunks; the host looks at the state of chunk k-1 while chunk k runs
+  // Sweeps in chunks; the host reads the device state of chunk k-1 while chunk
+  // k runs.  From two observed residuals the contraction rate gives the sweeps
+  // still needed, which sizes the next chunk; once the chunk in flight is
+  // expected to reach the tolerance, the host waits for it before sending more
+  // (sweeps enqueued past convergence are skipped on the device, but still
+  // cost their launches).
   int s = 0, chunk = 4, slot = 0;
   bool pending = false;
+  int last_c = 0;                 // size of the chunk in flight
+  int obs_it = -1;                // last observed (iters, residual)
+  double obs_r = 0.0;
   while (s < maxit) {
     const int c = std::min(chunk, maxit - s);
     for (int k = 0; k < c; ++k) {
@@ -320,19 +328,38 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
     s += c;
     CK(cudaMemcpyAsync(&P->ist_host[slot], P->ist, sizeof(IterState), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(P->ev[slot], st));
+    int next = std::min(chunk * 2, 64);
+    bool drain = false;           // wait for the chunk just sent before sending more
     if (pending) {
       const int w = wait_event(P->ev[slot ^ 1]);
       if (w != BFCS_OK) return w;
       const IterState& h = P->ist_host[slot ^ 1];
       if (h.done) break;
-      // predict the sweeps still needed from the observed contraction
-      if (h.iters > 2 && std::isfinite(h.resid_last) && tol > 0) {
-        (void)0;
+      if (tol > 0 && h.iters > 0 && std::isfinite(h.resid_last) && h.resid_last > 0) {
+        if (obs_it >= 0 && h.iters > obs_it && h.resid_last < obs_r) {
+          const double rate = std::pow(h.resid_last / obs_r, 1.0 / (h.iters - obs_it));
+          const double need = std::log(tol / h.resid_last) / std::log(rate);   // sweeps after h.iters
+          const double left = need - last_c;                                     // after the chunk in flight
+          if (left <= 0.5) drain = true;
+          else next = std::max(1, std::min(64, (int)std::ceil(left) + 1));
+        }
+        obs_it = h.iters;
+        obs_r = h.resid_last;
       }
     }
     pending = true;
     slot ^= 1;
-    chunk = std::min(chunk * 2, 32);
+    last_c = c;
+    chunk = next;
+    if (drain) {
+      const int w = wait_event(P->ev[slot ^ 1]);
+      if (w != BFCS_OK) return w;
+      const IterState& h = P->ist_host[slot ^ 1];
+      if (h.done) break;
+      pending = false;
+      chunk = 2;
+      if (std::isfinite(h.resid_last) && h.resid_last > 0) { obs_it = h.iters; obs_r = h.resid_last; }
+    }
   }
 
   // finalize: eps^S, sigma^S in real space; residual of eps^S; u^S
