@@ -241,6 +241,20 @@ __device__ __forceinline__ int signed_k(int k, int n) {
 // Residual bookkeeping written by the Green pass, reduced in FP64.
 struct ResidSlot { double num; double pad; };
 
+// Per-member descriptor of a batched solve (device memory, one per member).
+// Field arrays are of the plan's real type.
+struct Member {
+  const int8_t* phase;    // phase ids of the untranslated microstructure
+  int sx, sy, sz;         // translation chi: phase(x) = phase0(x - chi) (Eq. 3.3)
+  int warm;               // 1: sweep 0 reads eps_init (its residual is not evaluated)
+  double E[6];            // prescribed mean strain
+  const void* b;          // 3 x N body force
+  const void* eps_init;   // 6 x N or null
+  void* eps_out;          // 6 x N
+  void* sig_out;          // 6 x N or null
+  void* u_out;            // 3 x N or null
+};
+
 // Device-side iteration state of one solve.  Everything before resid_last is
 // zeroed at the start of a solve.
 struct IterState {

@@ -30,8 +30,9 @@ template <int L> struct XCfg {
 __device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
 
 template <typename R, int L>
-__global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
-  if (a.done != nullptr && *a.done) return;
+__global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xpass(XArgs<R> a) {
+  const int m = blockIdx.z;
+  if (a.st != nullptr && a.st[m].done) return;   // a member that has converged skips
   using C = XCfg<L>;
   constexpr int LPB = C::LPB, TPF = C::TPF, LP = C::LP;
   constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
@@ -47,6 +48,8 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
   const long long line0 = (long long)blockIdx.x * LPB;
   const long long cs = a.g.cs, rn = a.g.n;
   const int p = a.g.p;
+  // member-specific fields are read from the launch arguments (a.xm[m]) at
+  // their point of use, so none of them stays live in registers across the FFT
   const int mode = a.mode;
   // this thread's pair-line and lane within it
   const int f = tid / TPF, t = tid % TPF;
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
   // ---- 1. inverse transform along x of the pair-line Z = A + i B (C2R), or load real data
   if (mode == XM_SWEEP || mode == XM_C2R || mode == XM_SWEEPSIG) {
     if (fval && t < R2) {
-      const C2<R>* rowA = a.spec_in + (2 * q) * cs + line * p;
+      const C2<R>* rowA = a.spec_in + m * a.spec_ms + (2 * q) * cs + line * p;
       const C2<R>* rowB = rowA + cs;
       C2<R> x[R1];
 #pragma unroll
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
       const long long ln = line0 + i;
       C2<R> z = mk<R>(0, 0);
       if (ln < lines) {
-        const R* row = a.real_in + ln * L + n;
+        const R* row = (const R*)a.xm[m].real_in + ln * L + n;
         z.x = row[(2 * qq) * rn];
         z.y = (2 * qq + 1 < ncomp) ? row[(2 * qq + 1) * rn] : R(0);
       }
@@ -105,13 +108,14 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
   __syncthreads();
 
   if (mode == XM_C2R) {
+    if (a.xm[m].real_out == nullptr) return;     // a member without this output
     for (int idx = tid; idx < ncol * L; idx += blockDim.x) {
       const int n = idx % L, ff = idx / L;
       const int i = ff / npair, qq = ff - i * npair;
       const long long ln = line0 + i;
       if (ln >= lines) continue;
       const C2<R> z = s[ff * LP + xpad(n)];
-      R* row = a.real_out + ln * L + n;
+      R* row = (R*)a.xm[m].real_out + ln * L + n;
       row[(2 * qq) * rn] = z.x;
       if (2 * qq + 1 < ncomp) row[(2 * qq + 1) * rn] = z.y;
     }
@@ -132,20 +136,21 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
       const C2<R> p0 = c0[0], p1 = c0[LP], p2 = c0[2 * LP];
       // eps: xx yy zz yz xz xy
       const R e0 = p0.x, e1 = p0.y, e2 = p1.x, e3 = p1.y, e4 = p2.x, e5 = p2.y;
-      int xs = n - a.sx, ys = y - a.sy, zs = z - a.sz;
+      const XMember& M = a.xm[m];
+      int xs = n - M.sx, ys = y - M.sy, zs = z - M.sz;
       xs %= nx; if (xs < 0) xs += nx;
       ys %= ny; if (ys < 0) ys += ny;
       zs %= nz; if (zs < 0) zs += nz;
-      const int ph = a.phase[((long long)zs * ny + ys) * nx + xs];
+      const int ph = M.phase[((long long)zs * ny + ys) * nx + xs];
       const R tr = e0 + e1 + e2;
       const long long vox = ln * L + n;
-      if (a.eps_out != nullptr) {
-        R* o = a.eps_out + vox;
+      if (M.eps_out != nullptr) {
+        R* o = (R*)M.eps_out + vox;
         o[0] = e0; o[rn] = e1; o[2 * rn] = e2; o[3 * rn] = e3; o[4 * rn] = e4; o[5 * rn] = e5;
       }
-      if (a.sig_out != nullptr) {
+      if (M.sig_out != nullptr) {
         const R lt = a.tab.lam[ph] * tr, m2 = R(2) * a.tab.mu[ph];
-        R* o = a.sig_out + vox;
+        R* o = (R*)M.sig_out + vox;
         o[0] = lt + m2 * e0; o[rn] = lt + m2 * e1; o[2 * rn] = lt + m2 * e2;
         o[3 * rn] = m2 * e3; o[4 * rn] = m2 * e4; o[5 * rn] = m2 * e5;
       }
@@ -183,7 +188,8 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
   // k2' = R2 - 1 - k2 (k1 > 0) or (R2 - k2) % R2 (k1 = 0): one shuffle per k2.
   const int lane = threadIdx.x & 31;
   const int src = (lane & ~(TPF - 1)) | ((R1 - t) % R1);
-  C2<R>* rowA = a.spec_out + (2 * q) * cs + line * p;
+  const R half = R(0.5) * ((mode == XM_R2C && a.out_scale != R(0)) ? a.out_scale : R(1));
+  C2<R>* rowA = a.spec_out + m * a.spec_ms + (2 * q) * cs + line * p;
   C2<R>* rowB = rowA + cs;
 #pragma unroll
   for (int k2 = 0; k2 < R2; ++k2) {
@@ -194,8 +200,8 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS) k_xpass(XArgs<R> a) {
     const int k = t + R1 * k2;
     if (fval && t < R1 && k <= H) {
       const C2<R> Z = y[k2];
-      rowA[k] = mk<R>(R(0.5) * (Z.x + zm.x), R(0.5) * (Z.y - zm.y));
-      if (has_b) rowB[k] = mk<R>(R(0.5) * (Z.y + zm.y), R(-0.5) * (Z.x - zm.x));
+      rowA[k] = mk<R>(half * (Z.x + zm.x), half * (Z.y - zm.y));
+      if (has_b) rowB[k] = mk<R>(half * (Z.y + zm.y), -half * (Z.x - zm.x));
     }
   }
 }
@@ -209,8 +215,9 @@ template <int L> struct CCfg {
 };
 
 template <typename R, int L, int DIR>
-__global__ void __launch_bounds__(CCfg<L>::THREADS, sizeof(R) == 4 ? 3 : 1) k_colpass(CArgs<R> a) {
-  if (a.done != nullptr && *a.done) return;
+__global__ void __launch_bounds__(CCfg<L>::THREADS, sizeof(R) == 4 ? 3 : 2) k_colpass(CArgs<R> a) {
+  const int m = blockIdx.z;
+  if (a.st != nullptr && a.st[m].done) return;   // a member that has converged skips
   constexpr int T = kColT, R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
   extern __shared__ unsigned char smem_raw[];
   C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);
@@ -219,7 +226,7 @@ __global__ void __launch_bounds__(CCfg<L>::THREADS, sizeof(R) == 4 ? 3 : 1) k_co
   const int other = a.axis == 1 ? a.g.nz : ny;
   const int comp = blockIdx.y / other, o = blockIdx.y - comp * other;
   const long long ls = a.axis == 1 ? (long long)p : (long long)ny * p;
-  C2<R>* base = a.data + comp * a.g.cs + (a.axis == 1 ? (long long)o * ny * p : (long long)o * p);
+  C2<R>* base = a.data + m * a.ms + comp * a.g.cs + (a.axis == 1 ? (long long)o * ny * p : (long long)o * p);
   const int c = tid % T, j = tid / T;
   const int kx = blockIdx.x * T + c;
   const bool valid = kx < mx;
@@ -249,10 +256,10 @@ __global__ void __launch_bounds__(CCfg<L>::THREADS, sizeof(R) == 4 ? 3 : 1) k_co
 
 // ---------------------------------------------------------------- dispatch
 template <typename R, int L>
-static cudaError_t xpass_L(const XArgs<R>& a, cudaStream_t st) {
+static cudaError_t xpass_L(const XArgs<R>& a, int batch, cudaStream_t st) {
   using C = XCfg<L>;
   const long long lines = (long long)a.g.ny * a.g.nz;
-  const unsigned grid = (unsigned)((lines + C::LPB - 1) / C::LPB);
+  const dim3 grid((unsigned)((lines + C::LPB - 1) / C::LPB), 1, batch);
   const size_t smem = sizeof(C2<R>) * (size_t)C::LP * C::NCOL;
   cudaError_t e = cudaFuncSetAttribute(k_xpass<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -263,9 +270,25 @@ static cudaError_t xpass_L(const XArgs<R>& a, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_xpass(const XArgs<R>& a, cudaStream_t st) {
+cudaError_t launch_xpass_b(const XArgs<R>& a0, int batch, cudaStream_t st) {
+  const XArgs<R>* ap = &a0;
+  XArgs<R> one;
+  if (!a0.use_xm) {          // single launch: its scalar fields become member 0
+    one = a0;
+    XMember& x = one.xm[0];
+    x.phase = a0.phase;
+    x.sx = a0.sx; x.sy = a0.sy; x.sz = a0.sz;
+    x.warm = 0;
+    x.real_in = a0.real_in;
+    x.eps_out = a0.eps_out;
+    x.sig_out = a0.sig_out;
+    x.real_out = a0.real_out;
+    one.use_xm = 1;
+    ap = &one;
+  }
+  const XArgs<R>& a = *ap;
   switch (a.g.nx) {
-#define BFCS_X(L) case L: return xpass_L<R, L>(a, st);
+#define BFCS_X(L) case L: return xpass_L<R, L>(a, batch, st);
     BFCS_X(4) BFCS_X(6) BFCS_X(8) BFCS_X(12) BFCS_X(16) BFCS_X(24) BFCS_X(32) BFCS_X(48)
     BFCS_X(64) BFCS_X(96) BFCS_X(128) BFCS_X(192) BFCS_X(256)
 #undef BFCS_X
@@ -274,9 +297,9 @@ cudaError_t launch_xpass(const XArgs<R>& a, cudaStream_t st) {
 }
 
 template <typename R, int L, int DIR>
-static cudaError_t colpass_L(const CArgs<R>& a, cudaStream_t st) {
+static cudaError_t colpass_L(const CArgs<R>& a, int batch, cudaStream_t st) {
   const int other = a.axis == 1 ? a.g.nz : a.g.ny;
-  dim3 grid((a.g.mx + kColT - 1) / kColT, other * a.ncomp);
+  dim3 grid((a.g.mx + kColT - 1) / kColT, other * a.ncomp, batch);
   const size_t smem = sizeof(C2<R>) * (size_t)L * kColT;
   cudaError_t e = cudaFuncSetAttribute(k_colpass<R, L, DIR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -287,10 +310,10 @@ static cudaError_t colpass_L(const CArgs<R>& a, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_colpass(const CArgs<R>& a, int dir, cudaStream_t st) {
+cudaError_t launch_colpass_b(const CArgs<R>& a, int dir, int batch, cudaStream_t st) {
   const int n = a.axis == 1 ? a.g.ny : a.g.nz;
   switch (n) {
-#define BFCS_C(L) case L: return dir < 0 ? colpass_L<R, L, -1>(a, st) : colpass_L<R, L, +1>(a, st);
+#define BFCS_C(L) case L: return dir < 0 ? colpass_L<R, L, -1>(a, batch, st) : colpass_L<R, L, +1>(a, batch, st);
     BFCS_C(4) BFCS_C(6) BFCS_C(8) BFCS_C(12) BFCS_C(16) BFCS_C(24) BFCS_C(32) BFCS_C(48)
     BFCS_C(64) BFCS_C(96) BFCS_C(128) BFCS_C(192) BFCS_C(256)
 #undef BFCS_C
@@ -298,7 +321,14 @@ cudaError_t launch_colpass(const CArgs<R>& a, int dir, cudaStream_t st) {
   }
 }
 
+template <typename R>
+cudaError_t launch_xpass(const XArgs<R>& a, cudaStream_t st) { return launch_xpass_b<R>(a, 1, st); }
+template <typename R>
+cudaError_t launch_colpass(const CArgs<R>& a, int dir, cudaStream_t st) { return launch_colpass_b<R>(a, dir, 1, st); }
+
 template cudaError_t launch_xpass<BFCS_R>(const XArgs<BFCS_R>&, cudaStream_t);
 template cudaError_t launch_colpass<BFCS_R>(const CArgs<BFCS_R>&, int, cudaStream_t);
+template cudaError_t launch_xpass_b<BFCS_R>(const XArgs<BFCS_R>&, int, cudaStream_t);
+template cudaError_t launch_colpass_b<BFCS_R>(const CArgs<BFCS_R>&, int, int, cudaStream_t);
 
 }  // namespace bfcs

@@ -41,7 +41,15 @@ __device__ __forceinline__ void g0_apply(const C2<R> g[3], const R xi[3], R q, R
 
 template <typename R, int L>
 __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zgreen(GArgs<R> a) {
-  if (a.done != nullptr && *a.done) return;
+  const int mbr = blockIdx.z;
+  if (a.skip_done && a.st[mbr].done) return;     // a member that has converged skips
+  // this member's buffers and mean strain
+  C2<R>* const spec = a.spec + mbr * a.spec_ms;
+  const C2<R>* const bhat = a.bhat + mbr * a.b_ms;
+  C2<R>* const dprev = a.dprev + mbr * a.d_ms;
+  ResidSlot* const part = a.part + mbr * a.part_ms;
+  IterState* const stm = a.st + mbr;
+  const R* const Em = a.use_me ? a.mE[mbr] : a.E;
   constexpr int T = kGreenT;
   constexpr int NCOL = GCfg<L>::NCOL;
   constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
@@ -63,7 +71,7 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
   const int ccomp = c / T, ccol = c - ccomp * T;
   const int ckx = col0 + ccol;
   const bool cvalid = ckx < mx;
-  C2<R>* gcol = a.spec + ccomp * cs + rowbase + ckx;  // element z of this column at gcol[z * zs]
+  C2<R>* gcol = spec + ccomp * cs + rowbase + ckx;    // element z of this column at gcol[z * zs]
 
   // ---- start the copies of the b_hat and d_prev tiles; they land during the FFT
   {
@@ -72,7 +80,7 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
     const int narr = mode == GM_INIT ? 3 : 6;
     for (int idx = tid; idx < narr * L * CPR; idx += nthr) {
       const int part = idx % CPR, n = (idx / CPR) % L, arr = idx / (CPR * L);
-      const C2<R>* src = (arr < 3 ? a.bhat + arr * cs : a.dprev + (arr - 3) * cs) + n * zs + rowbase +
+      const C2<R>* src = (arr < 3 ? bhat + arr * cs : dprev + (arr - 3) * cs) + n * zs + rowbase +
                          col0 + part * PER;
       cp_async16(pre + (arr * L + n) * T + part * PER, src);
     }
@@ -133,16 +141,16 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
 
     if (qq == R(0)) {
       const bool k0 = (kx == 0 && ky == 0 && n == 0);
-      if (k0 && mode != GM_INIT && a.st != nullptr) {
+      if (k0 && mode != GM_INIT) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) a.st->tau0[q] = (double)m[q * T].x;
+        for (int q = 0; q < 6; ++q) stm->tau0[q] = (double)m[q * T].x;
       }
       if (mode == GM_SWEEP || mode == GM_INIT) {
-        a.dprev[gi] = mk<R>(0, 0); a.dprev[cs + gi] = mk<R>(0, 0); a.dprev[2 * cs + gi] = mk<R>(0, 0);
+        dprev[gi] = mk<R>(0, 0); dprev[cs + gi] = mk<R>(0, 0); dprev[2 * cs + gi] = mk<R>(0, 0);
       }
 #pragma unroll
       for (int q = 0; q < 6; ++q)
-        m[q * T] = (mode != GM_FINAL && k0) ? mk<R>(a.E[q], R(0)) : mk<R>(0, 0);
+        m[q * T] = (mode != GM_FINAL && k0) ? mk<R>(Em[q], R(0)) : mk<R>(0, 0);
       continue;
     }
     const C2<R> bh0 = pm[0], bh1 = pm[L * T], bh2 = pm[2 * L * T];
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
       if (mode == GM_FINAL) { d[0] = dp[0]; d[1] = dp[1]; d[2] = dp[2]; }
     }
     if (mode == GM_SWEEP || mode == GM_INIT) {
-      a.dprev[gi] = d[0]; a.dprev[cs + gi] = d[1]; a.dprev[2 * cs + gi] = d[2];
+      dprev[gi] = d[0]; dprev[cs + gi] = d[1]; dprev[2 * cs + gi] = d[2];
     }
     // w = d - i b_hat
     C2<R> w[3];
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
   if (mode != GM_INIT && tid == 0) {
     double t = 0.0;
     for (int w = 0; w < (nthr + 31) / 32; ++w) t += red[w];
-    a.part[blockIdx.y * gridDim.x + blockIdx.x].num = t;
+    part[blockIdx.y * gridDim.x + blockIdx.x].num = t;
   }
 
   // ---- inverse transform along z, stage 2 straight to global
@@ -390,8 +398,8 @@ int green_nparts(const Geo& g) {
 }
 
 template <typename R, int L>
-static cudaError_t zgreen_L(const GArgs<R>& a, cudaStream_t st) {
-  dim3 grid((a.g.mx + kGreenT - 1) / kGreenT, a.g.ny);
+static cudaError_t zgreen_L(const GArgs<R>& a, int batch, cudaStream_t st) {
+  dim3 grid((a.g.mx + kGreenT - 1) / kGreenT, a.g.ny, batch);
   const size_t smem = sizeof(C2<R>) * (size_t)L * (GCfg<L>::NCOL + 6 * kGreenT);
   cudaError_t e = cudaFuncSetAttribute(k_zgreen<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -402,9 +410,9 @@ static cudaError_t zgreen_L(const GArgs<R>& a, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t st) {
+cudaError_t launch_zgreen_b(const GArgs<R>& a, int batch, cudaStream_t st) {
   switch (a.g.nz) {
-#define BFCS_G(L) case L: return zgreen_L<R, L>(a, st);
+#define BFCS_G(L) case L: return zgreen_L<R, L>(a, batch, st);
     BFCS_G(4) BFCS_G(6) BFCS_G(8) BFCS_G(12) BFCS_G(16) BFCS_G(24) BFCS_G(32) BFCS_G(48)
     BFCS_G(64) BFCS_G(96) BFCS_G(128) BFCS_G(192) BFCS_G(256)
 #undef BFCS_G
@@ -412,7 +420,11 @@ cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t st) {
   }
 }
 
+template <typename R>
+cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t st) { return launch_zgreen_b<R>(a, 1, st); }
+
 template cudaError_t launch_zgreen<BFCS_R>(const GArgs<BFCS_R>&, cudaStream_t);
+template cudaError_t launch_zgreen_b<BFCS_R>(const GArgs<BFCS_R>&, int, cudaStream_t);
 template int green_nparts<BFCS_R>(const Geo&);
 template cudaError_t launch_defect<BFCS_R>(const DArgs<BFCS_R>&, int, cudaStream_t);
 template cudaError_t launch_symgrad<BFCS_R>(C2<BFCS_R>*, const Geo&, const double*, cudaStream_t);

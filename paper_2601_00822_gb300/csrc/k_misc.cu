@@ -231,8 +231,11 @@ cudaError_t launch_validate(const int8_t* phase, const R* b, long long n, int* i
 // sum over modes with xi != 0 of w |b_hat|^2 (w = 2 for 0 < kx < nx/2: the
 // mirrored half of the spectrum), giving the full-spectrum norm of b_hat.
 template <typename R>
-__global__ void k_bden(const C2<R>* bhat, Geo g, ResidSlot* part) {
+__global__ void k_bden(const C2<R>* bhat, Geo g, ResidSlot* part, long long b_ms) {
   __shared__ double red[32];
+  const int m = blockIdx.y;
+  bhat += m * b_ms;
+  part += m * gridDim.x;
   const long long modes = (long long)g.nz * g.ny * g.mx;
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
@@ -255,17 +258,20 @@ __global__ void k_bden(const C2<R>* bhat, Geo g, ResidSlot* part) {
 
 __global__ void k_bden_final(const ResidSlot* part, int nparts, IterState* st) {
   __shared__ double red[32];
+  const int m = blockIdx.x;
+  part += m * nparts;
   double acc = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i].num;
   const double t = block_sum(acc, red);
-  if (threadIdx.x == 0) st->bden = sqrt(t);
+  if (threadIdx.x == 0) st[m].bden = sqrt(t);
 }
 
 template <typename R>
-cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterState* st, cudaStream_t s) {
+cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterState* st, cudaStream_t s,
+                        int batch, long long b_ms) {
   const int blocks = 512;
-  k_bden<R><<<blocks, kRedThreads, 0, s>>>(bhat, g, part);
-  k_bden_final<<<1, kRedThreads, 0, s>>>(part, blocks, st);
+  k_bden<R><<<dim3(blocks, batch), kRedThreads, 0, s>>>(bhat, g, part, b_ms);
+  k_bden_final<<<batch, kRedThreads, 0, s>>>(part, blocks, st);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -273,18 +279,26 @@ cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterSt
 // ---------------------------------------------------------------- residual reduction (Eq. 5.11)
 // r = sqrt(sum partials) / D, D = ||b_hat|| + xi_min |sigma_hat(0)|_F with
 // sigma_hat(0) = N C0 E + tau_hat(0) and xi_min = 2 pi / max N_a.
-__global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
-                               int hist_cap, int sweep, double tol, double lam0, double mu0, double E0,
-                               double E1, double E2, double E3, double E4, double E5, double n,
-                               int maxdim, int mode, int skip_check, int stall_window) {
+__global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* sts, const Member* mem,
+                               double* hist, int hist_cap, double tol, double lam0, double mu0, double E0,
+                               double E1, double E2, double E3, double E4, double E5, double n, int maxdim,
+                               int mode, int warm_all, int stall_window) {
   __shared__ double red[32];
+  const int m = blockIdx.x;
+  IterState* st = sts + m;
   if (mode == GM_SWEEP && st->done) return;
+  part += m * nparts;
   double acc = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i].num;
   const double t = block_sum(acc, red);
   if (threadIdx.x != 0) return;
-  const double E[6] = {E0, E1, E2, E3, E4, E5};
-  const double trE = E0 + E1 + E2;
+  double E[6] = {E0, E1, E2, E3, E4, E5};
+  int warm = warm_all;
+  if (mem != nullptr) {
+    for (int c = 0; c < 6; ++c) E[c] = mem[m].E[c];
+    warm = mem[m].warm;
+  }
+  const double trE = E[0] + E[1] + E[2];
   double s0[6];
   for (int c = 0; c < 6; ++c)
     s0[c] = mode == kReduceDefect ? st->tau0[c]
@@ -294,8 +308,10 @@ __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* st,
   const double den = st->bden + 6.283185307179586 / (double)maxdim * s0n;
   double r = den > 0.0 ? sqrt(t) / den : sqrt(t);
   if (mode == GM_FINAL || mode == kReduceDefect) { st->resid_final = r; return; }
+  const int sweep = st->iters;
+  const bool skip_check = warm && sweep == 0;
   if (skip_check) r = INFINITY;
-  if (sweep < hist_cap && hist != nullptr) hist[sweep] = r;
+  if (sweep < hist_cap && hist != nullptr) hist[(long long)m * hist_cap + sweep] = r;
   st->resid_last = r;
   st->iters = sweep + 1;
   if (skip_check) return;
@@ -311,13 +327,13 @@ __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* st,
   }
 }
 
-cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
-                                int hist_cap, int sweep, double tol, double lam0, double mu0,
-                                const double* E, long long n, int maxdim, int mode, int skip_check,
-                                int stall_window, cudaStream_t s) {
-  k_resid_reduce<<<1, 1024, 0, s>>>(part, nparts, st, hist, hist_cap, sweep, tol, lam0, mu0,
-                                           E[0], E[1], E[2], E[3], E[4], E[5], (double)n, maxdim,
-                                           mode, skip_check, stall_window);
+cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, const Member* mem,
+                                double* hist, int hist_cap, double tol, double lam0, double mu0,
+                                const double* E, long long n, int maxdim, int mode, int warm_all,
+                                int stall_window, int batch, cudaStream_t s) {
+  k_resid_reduce<<<batch, 1024, 0, s>>>(part, nparts, st, mem, hist, hist_cap, tol, lam0, mu0, E[0], E[1],
+                                        E[2], E[3], E[4], E[5], (double)n, maxdim, mode, warm_all,
+                                        stall_window);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -449,7 +465,7 @@ cudaError_t launch_stress(double* sig, const double* eps, const int8_t* phase, c
   template cudaError_t launch_validate<R>(const int8_t*, const R*, long long, int*, double*,       \
                                           double*, cudaStream_t);                                 \
   template cudaError_t launch_bden<R>(const C2<R>*, const Geo&, ResidSlot*, IterState*,            \
-                                      cudaStream_t);                                              \
+                                      cudaStream_t, int, long long);                              \
   template cudaError_t launch_accumulate<R>(double*, int*, const R*, const R*, const R*,           \
                                             const int8_t*, int, int, int, int, int, int,          \
                                             cudaStream_t);

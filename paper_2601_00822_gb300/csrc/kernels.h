@@ -16,6 +16,26 @@ enum XMode : int {
   XM_SWEEPSIG = 5, // spectrum -> C2R -> eps (written) -> sigma = L eps -> R2C -> spectrum
 };
 
+// Which member fields a batched x pass reads and writes (host-side selection).
+enum XMemIO : int {
+  XIN_NONE = 0, XIN_EPS_INIT = 1, XIN_B = 2,
+  XOUT_EPS = 1, XOUT_SIG = 2, XOUT_U = 4,
+};
+
+// Members per batched launch (their x-pass fields travel in the launch arguments).
+constexpr int kMaxBatch = 64;
+
+// Per-member fields of the x pass, passed by value in the launch arguments so
+// that every block reads them from the constant bank.
+struct XMember {
+  const int8_t* phase;
+  const void* real_in;    // selected input (b or eps_init) or null
+  void* eps_out;
+  void* sig_out;
+  void* real_out;         // u output or null
+  int sx, sy, sz, warm;
+};
+
 template <typename R> struct XArgs {
   Geo g;
   const C2<R>* spec_in;   // [ncomp][nz][ny][p]
@@ -28,9 +48,13 @@ template <typename R> struct XArgs {
   int sx, sy, sz;         // translation chi: phase(x) = phase0(x - chi) (Eq. 3.3)
   PhaseTab<R> tab;
   const C2<R>* tw;        // exp(-2 pi i j / nx), j < nx
-  const int* done;        // nullable: skip the launch once set
+  const IterState* st;    // nullable: per-member state; a member with st[m].done skips
+  long long spec_ms;      // spectrum stride between members (complex elements)
+  int use_xm;             // 1: member m = blockIdx.z takes phase, shift, I/O from xm[m]
+  R out_scale;            // XM_R2C: factor applied to the stored half spectrum (0 means 1)
   int ncomp;
   int mode;
+  XMember xm[kMaxBatch];
 };
 
 // ---- column passes along y (axis 1) or z (axis 2) on the half spectrum, in place.
@@ -40,7 +64,8 @@ template <typename R> struct CArgs {
   int axis;
   int ncomp;
   const C2<R>* tw;        // exp(-2 pi i j / n_axis)
-  const int* done;
+  const IterState* st;    // nullable: member m = blockIdx.z skips once st[m].done
+  long long ms;           // data stride between members (complex elements)
 };
 
 // ---- fused z pass: forward z FFT -> Green operators -> residual -> inverse z FFT.
@@ -59,10 +84,14 @@ template <typename R> struct GArgs {
   R E[6];
   R inv_n;                // 1 / |N| of Eq. 4.4
   const C2<R>* tw;        // exp(-2 pi i j / nz)
-  ResidSlot* part;        // one slot per block
-  IterState* st;
-  const int* done;
+  ResidSlot* part;        // one slot per block (per member: part_ms slots)
+  IterState* st;          // per member
+  long long spec_ms, b_ms, d_ms;   // member strides (complex elements)
+  int part_ms;
+  int skip_done;          // 1: members with st[m].done skip the launch
+  int use_me;             // 1: member m takes its mean strain from mE[m]
   int mode;
+  R mE[kMaxBatch][6];
 };
 
 // ---- defect of an approximate strain on the fully transformed stress spectrum:
@@ -92,6 +121,9 @@ template <typename R> cudaError_t launch_defect(const DArgs<R>& a, int blocks, c
 template <typename R> cudaError_t launch_colpass(const CArgs<R>& a, int dir, cudaStream_t s);
 template <typename R> cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t s);
 template <typename R> int green_nparts(const Geo& g);
+template <typename R> cudaError_t launch_xpass_b(const XArgs<R>& a, int batch, cudaStream_t s);
+template <typename R> cudaError_t launch_colpass_b(const CArgs<R>& a, int dir, int batch, cudaStream_t s);
+template <typename R> cudaError_t launch_zgreen_b(const GArgs<R>& a, int batch, cudaStream_t s);
 
 bool supported_len(int n);
 
@@ -119,15 +151,21 @@ cudaError_t launch_validate(const int8_t* phase, const R* b, long long n, int* i
                             double* scratch, cudaStream_t s);
 int validate_scratch(long long n);
 
-// sum over modes with xi != 0 of w |b_hat|^2 -> st->bden = sqrt(sum)
+// sum over modes with xi != 0 of w |b_hat|^2 -> st->bden = sqrt(sum); batched:
+// member m uses bhat + m * b_ms, part + m * 512 and st + m
 template <typename R>
-cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterState* st, cudaStream_t s);
+cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterState* st, cudaStream_t s,
+                        int batch = 1, long long b_ms = 0);
 
-// residual reduction of the Green-pass partials; mode = GM_SWEEP or GM_FINAL
-cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, double* hist,
-                                int hist_cap, int sweep, double tol, double c0_lam, double c0_mu,
-                                const double* E, long long n, int maxdim, int mode, int skip_check,
-                                int stall_window, cudaStream_t s);
+// residual reduction of the Green-pass partials; mode = GM_SWEEP, GM_FINAL or
+// kReduceDefect.  One block per member: member m reduces part[m * nparts ...],
+// updates st[m] and writes hist[m * hist_cap + sweep]; its E and warm flag
+// come from mem[m] when mem is given, else from E / warm_all.  In GM_SWEEP the
+// sweep index is the device counter st[m].iters.
+cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, const Member* mem,
+                                double* hist, int hist_cap, double tol, double c0_lam, double c0_mu,
+                                const double* E, long long n, int maxdim, int mode, int warm_all,
+                                int stall_window, int batch, cudaStream_t s);
 // mode for launch_resid_reduce: tau0 already holds sigma_hat(0) (defect evaluation)
 constexpr int kReduceDefect = 7;
 

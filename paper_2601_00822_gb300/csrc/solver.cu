@@ -29,14 +29,20 @@ struct bfcs_plan_s {
   int npart = 0;              // slots allocated (>= every writer's block count)
   int ngreen = 0;             // blocks of the fused z/Green pass = residual partials per sweep
   int stall_window = 100;     // sweeps without a 10% residual drop that end a solve
-  IterState* ist = nullptr;
-  IterState* ist_host = nullptr;   // pinned, 3 slots
+  IterState* ist = nullptr;        // max_batch members
+  IterState* ist_host = nullptr;   // pinned, 3 slots x max_batch
+  Member* mem_dev = nullptr;       // max_batch member descriptors
+  Member* mem_host = nullptr;      // pinned staging of the descriptors
+  int graph_sweeps = 8;            // sweeps per captured graph (0: no graphs)
+  cudaStream_t loop_st = nullptr;  // private stream of the sweep loop (capturable), ordered with st
+  cudaEvent_t order_ev[2];
   cudaEvent_t ev[2];
   double* hist = nullptr;
   int hist_cap = 0;
   int last_iters = 0;
-  int* ival = nullptr;             // device: phase min/max
-  double* dval = nullptr;          // device: b sums
+  int last_batch = 0;
+  int* ival = nullptr;             // device: phase min/max, 2 per member
+  double* dval = nullptr;          // device: b sums, 6 per member
   double* dscratch = nullptr;      // device scratch for reductions
   int* ival_host = nullptr;        // pinned
   double* dval_host = nullptr;     // pinned
@@ -62,7 +68,9 @@ struct bfcs_plan_s {
 
 namespace {
 
-constexpr int kHistCap = 1 << 16;
+int severity(int s) { return s < 0 ? 1000 - s : s; }
+
+constexpr int kHistCap = 1 << 14;   // residual history entries kept per member
 
 double wait_limit_s() {
   const char* e = std::getenv("BFCS_WAIT_TIMEOUT_S");
@@ -119,7 +127,8 @@ void free_plan(bfcs_plan P) {
   if (P == nullptr) return;
   cudaFree(P->spec); cudaFree(P->bhat); cudaFree(P->dprev);
   for (int i = 0; i < 3; ++i) cudaFree(P->tw[i]);
-  cudaFree(P->part); cudaFree(P->ist); cudaFree(P->hist);
+  cudaFree(P->part); cudaFree(P->ist); cudaFree(P->hist); cudaFree(P->mem_dev);
+  if (P->mem_host) cudaFreeHost(P->mem_host);
   cudaFree(P->ival); cudaFree(P->dval); cudaFree(P->dscratch);
   cudaFree(P->tmp); cudaFree(P->tmp_hits);
   cudaFree(P->spec64); cudaFree(P->bhat64); cudaFree(P->ist64); cudaFree(P->r32); cudaFree(P->u64);
@@ -130,6 +139,9 @@ void free_plan(bfcs_plan P) {
   cudaEventDestroy(P->ev[0]);
   cudaEventDestroy(P->ev[1]);
   for (cudaEvent_t e : P->prof_ev) cudaEventDestroy(e);
+  if (P->loop_st) cudaStreamDestroy(P->loop_st);
+  if (P->order_ev[0]) cudaEventDestroy(P->order_ev[0]);
+  if (P->order_ev[1]) cudaEventDestroy(P->order_ev[1]);
   delete P;
 }
 
@@ -157,22 +169,32 @@ int check_material(int nph, const bfcs_lame* phases, bfcs_lame C0) {
   return BFCS_OK;
 }
 
-// Phase ids in [0, nph) and a self-equilibrated load (Eq. 2.5).
+// Phase ids in [0, nph) and a self-equilibrated load (Eq. 2.5), for members
+// whose phase maps and loads are given in the host arrays.
 template <typename R>
-int validate_inputs(bfcs_plan P, const int8_t* phase, const void* b, int nph) {
-  CK(launch_validate<R>(phase, (const R*)b, P->g.n, P->ival, P->dval, P->dscratch, P->st));
-  CK(cudaMemcpyAsync(P->ival_host, P->ival, 2 * sizeof(int), cudaMemcpyDeviceToHost, P->st));
-  CK(cudaMemcpyAsync(P->dval_host, P->dval, 6 * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+int validate_members(bfcs_plan P, int B, const int8_t* const* phase, const void* const* b, int nph) {
+  for (int m = 0; m < B; ++m)
+    CK(launch_validate<R>(phase[m], (const R*)b[m], P->g.n, P->ival + 2 * m, P->dval + 6 * m, P->dscratch,
+                          P->st));
+  CK(cudaMemcpyAsync(P->ival_host, P->ival, 2 * B * sizeof(int), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaMemcpyAsync(P->dval_host, P->dval, 6 * B * sizeof(double), cudaMemcpyDeviceToHost, P->st));
   const int w = sync_stream(P);
   if (w != BFCS_OK) return w;
-  if (P->ival_host[0] < 0 || P->ival_host[1] >= nph) return BFCS_ERR_INVALID_ARG;
   const double thr = sizeof(R) == 4 ? 1e-6 : 1e-12;
-  for (int c = 0; c < 3; ++c) {
-    const double s = P->dval_host[c], sa = P->dval_host[3 + c];
-    if (!std::isfinite(s) || !std::isfinite(sa)) return BFCS_ERR_INVALID_ARG;
-    if (std::fabs(s) > thr * sa) return BFCS_ERR_NONZERO_MEAN;
+  for (int m = 0; m < B; ++m) {
+    if (P->ival_host[2 * m] < 0 || P->ival_host[2 * m + 1] >= nph) return BFCS_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c) {
+      const double sm = P->dval_host[6 * m + c], sa = P->dval_host[6 * m + 3 + c];
+      if (!std::isfinite(sm) || !std::isfinite(sa)) return BFCS_ERR_INVALID_ARG;
+      if (std::fabs(sm) > thr * sa) return BFCS_ERR_NONZERO_MEAN;
+    }
   }
   return BFCS_OK;
+}
+
+template <typename R>
+int validate_inputs(bfcs_plan P, const int8_t* phase, const void* b, int nph) {
+  return validate_members<R>(P, 1, &phase, &b, nph);
 }
 
 // b_hat = F(b): x R2C, then y and z forward, into `dst` (3 components).
@@ -210,22 +232,75 @@ struct SolveOut {
   void* u;
 };
 
-// One solve on the plan; b_hat must already be in the plan (transform_load).
+// x-pass member fields (launch arguments) from the host-side descriptors.
 template <typename R>
-int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_lame C0, const double* E,
-               double tol, int maxit, const void* eps_init, SolveOut out, const int shift[3],
-               bfcs_info* info) {
+void fill_xm(XArgs<R>& xa, const Member* m, int B, int in_sel, int out_sel) {
+  xa.use_xm = 1;
+  for (int k = 0; k < B; ++k) {
+    XMember& x = xa.xm[k];
+    x.phase = m[k].phase;
+    x.sx = m[k].sx; x.sy = m[k].sy; x.sz = m[k].sz;
+    x.warm = m[k].warm;
+    x.real_in = in_sel == XIN_B ? m[k].b : (in_sel == XIN_EPS_INIT || m[k].warm) ? m[k].eps_init : nullptr;
+    x.eps_out = (out_sel & XOUT_EPS) ? m[k].eps_out : nullptr;
+    x.sig_out = (out_sel & XOUT_SIG) ? m[k].sig_out : nullptr;
+    x.real_out = (out_sel & XOUT_U) ? m[k].u_out : nullptr;
+  }
+}
+
+// Upload B member descriptors (host array) to the plan.
+int upload_members(bfcs_plan P, int B, const Member* m) {
+  std::memcpy(P->mem_host, m, B * sizeof(Member));
+  CK(cudaMemcpyAsync(P->mem_dev, P->mem_host, B * sizeof(Member), cudaMemcpyHostToDevice, P->st));
+  return BFCS_OK;
+}
+
+// b_hat of every member: x R2C of mem[m].b, then y and z forward; and its norm.
+template <typename R>
+int transform_members(bfcs_plan P, int B) {
+  XArgs<R> xa{};
+  xa.g = P->g;
+  xa.spec_out = (C2<R>*)P->bhat;
+  xa.spec_ms = 3 * P->g.cs;
+  fill_xm(xa, P->mem_host, B, XIN_B, 0);
+  xa.ncomp = 3;
+  xa.mode = XM_R2C;
+  xa.tw = (const C2<R>*)P->tw[0];
+  CK(launch_xpass_b<R>(xa, B, P->st));
+  CArgs<R> ca{};
+  ca.data = (C2<R>*)P->bhat;
+  ca.ms = 3 * P->g.cs;
+  ca.g = P->g;
+  ca.ncomp = 3;
+  ca.axis = 1;
+  ca.tw = (const C2<R>*)P->tw[1];
+  CK(launch_colpass_b<R>(ca, -1, B, P->st));
+  ca.axis = 2;
+  ca.tw = (const C2<R>*)P->tw[2];
+  CK(launch_colpass_b<R>(ca, -1, B, P->st));
+  CK(launch_bden<R>((const C2<R>*)P->bhat, P->g, P->part, P->ist, P->st, B, 3 * P->g.cs));
+  return BFCS_OK;
+}
+
+// Algorithm 1 for B members of one grid, advancing together: each sweep is
+// one launch per pass for all members; converged members skip on the device.
+// Needs the member descriptors, b_hat and bden in place.  Outputs through the
+// descriptors' eps_out / sig_out / u_out.
+template <typename R>
+int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const double* E0, double tol,
+              int maxit, bfcs_info* infos, bool any_warm) {
   const Geo g = P->g;
   cudaStream_t st = P->st;
   C2<R>* spec = (C2<R>*)P->spec;
   const C2<R>* twx = (const C2<R>*)P->tw[0];
   const C2<R>* twy = (const C2<R>*)P->tw[1];
   const C2<R>* twz = (const C2<R>*)P->tw[2];
-  const bool warm = eps_init != nullptr;
   const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
+  const long long sms = 6 * g.cs;
 
   // iteration state (keep bden computed by the caller)
-  CK(cudaMemsetAsync(P->ist, 0, offsetof(IterState, resid_last), st));
+  for (int m = 0; m < B; ++m)
+    CK(cudaMemsetAsync(P->ist + m, 0, offsetof(IterState, resid_last), st));
 
   GArgs<R> ga{};
   ga.spec = spec;
@@ -234,14 +309,22 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
   ga.g = g;
   ga.lam0 = (R)C0.lambda;
   ga.mu0 = (R)C0.mu;
-  for (int c = 0; c < 6; ++c) ga.E[c] = (R)E[c];
+  for (int c = 0; c < 6; ++c) ga.E[c] = (R)E0[c];
   ga.inv_n = (R)(1.0 / (double)g.n);
   ga.tw = twz;
   ga.part = P->part;
   ga.st = P->ist;
+  ga.use_me = 1;
+  for (int m = 0; m < B; ++m)
+    for (int c = 0; c < 6; ++c) ga.mE[m][c] = (R)P->mem_host[m].E[c];
+  ga.spec_ms = sms;
+  ga.b_ms = 3 * g.cs;
+  ga.d_ms = 3 * g.cs;
+  ga.part_ms = P->ngreen;
 
   CArgs<R> cy{};
   cy.data = spec;
+  cy.ms = sms;
   cy.g = g;
   cy.ncomp = 6;
   cy.axis = 1;
@@ -251,100 +334,165 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
   xa.g = g;
   xa.spec_in = spec;
   xa.spec_out = spec;
-  xa.real_in = (const R*)eps_init;
-  xa.phase = phase;
-  xa.sx = shift[0];
-  xa.sy = shift[1];
-  xa.sz = shift[2];
+  xa.spec_ms = sms;
   xa.tab = tab;
   xa.tw = twx;
   xa.ncomp = 6;
 
-  if (!warm) {
-    ga.mode = GM_INIT;
-    ga.done = nullptr;
-    CK(launch_zgreen<R>(ga, st));
-    CK(launch_colpass<R>(cy, +1, st));
-  } else {
-    CK(cudaMemsetAsync(P->dprev, 0, 3 * g.cs * sizeof(C2<R>), st));
+  // eps^0 = eps^{b(0)} + E for every member, d_prev = 0
+  ga.mode = GM_INIT;
+  ga.skip_done = 0;
+  CK(launch_zgreen_b<R>(ga, B, st));
+  cy.st = nullptr;
+  CK(launch_colpass_b<R>(cy, +1, B, st));
+  // A warm-started member instead starts from its eps_init: the state kept
+  // between sweeps is the x-transform of eps scaled by 1/nx (y, z in real space).
+  if (any_warm) {
+    for (int m = 0; m < B; ++m) {
+      if (!P->mem_host[m].warm) continue;
+      XArgs<R> xw{};
+      xw.g = g;
+      xw.real_in = (const R*)P->mem_host[m].eps_init;
+      xw.spec_out = spec + m * sms;
+      xw.out_scale = (R)(1.0 / g.nx);
+      xw.ncomp = 6;
+      xw.mode = XM_R2C;
+      xw.tw = twx;
+      CK(launch_xpass<R>(xw, st));
+    }
   }
 
-  const int* done = &P->ist->done;
   P->prof_used = 0;
   const int prof_cap = (int)P->prof_sweep.size();
-  // launch one kernel, bracketed by events when it is the profiled kind
-  auto timed = [&](int kind, int s, cudaError_t (*fn)(const void*, int, cudaStream_t), const void* args,
+  auto timed = [&](int kind, int sweep, cudaError_t (*fn)(const void*, int, int, cudaStream_t), const void* args,
                    int dir) -> cudaError_t {
-    const bool t = P->prof_kind == kind && P->prof_used < prof_cap;
+    const bool t = P->prof_kind == kind && P->prof_used < prof_cap && sweep >= 0;
     if (t && cudaEventRecord(P->prof_ev[2 * P->prof_used], st) != cudaSuccess) return cudaErrorUnknown;
-    const cudaError_t e = fn(args, dir, st);
+    const cudaError_t e = fn(args, dir, B, st);
     if (t) {
       if (cudaEventRecord(P->prof_ev[2 * P->prof_used + 1], st) != cudaSuccess) return cudaErrorUnknown;
-      P->prof_sweep[P->prof_used++] = s;
+      P->prof_sweep[P->prof_used++] = sweep;
     }
     return e;
   };
-  auto run_x = [](const void* a, int, cudaStream_t q) { return launch_xpass<R>(*(const XArgs<R>*)a, q); };
-  auto run_c = [](const void* a, int dir, cudaStream_t q) {
-    return launch_colpass<R>(*(const CArgs<R>*)a, dir, q);
+  auto run_x = [](const void* a, int, int b, cudaStream_t q) { return launch_xpass_b<R>(*(const XArgs<R>*)a, b, q); };
+  auto run_c = [](const void* a, int dir, int b, cudaStream_t q) {
+    return launch_colpass_b<R>(*(const CArgs<R>*)a, dir, b, q);
   };
-  auto run_g = [](const void* a, int, cudaStream_t q) { return launch_zgreen<R>(*(const GArgs<R>*)a, q); };
-  auto enqueue_sweep = [&](int s) -> int {
-    const bool first_warm = warm && s == 0;
-    xa.mode = first_warm ? XM_REALTAU : XM_SWEEP;
-    xa.eps_out = nullptr;
-    xa.sig_out = nullptr;
-    xa.done = done;
-    CK(timed(1, s, run_x, &xa, 0));
-    cy.done = done;
+  auto run_g = [](const void* a, int, int b, cudaStream_t q) { return launch_zgreen_b<R>(*(const GArgs<R>*)a, b, q); };
+  // one sweep for all members; identical launches every sweep (graph-capturable);
+  // `sweep` is only used to label profiled launches (-1 inside graphs)
+  fill_xm(xa, P->mem_host, B, XIN_NONE, 0);
+  auto enqueue_sweep = [&](int sweep) -> int {
+    xa.mode = XM_SWEEP;
+    xa.st = P->ist;
+    CK(timed(1, sweep, run_x, &xa, 0));
+    cy.st = P->ist;
     cy.ncomp = 6;
-    CK(timed(2, s, run_c, &cy, -1));
+    CK(timed(2, sweep, run_c, &cy, -1));
     ga.mode = GM_SWEEP;
-    ga.done = done;
-    CK(timed(3, s, run_g, &ga, 0));
-    CK(timed(2, s, run_c, &cy, +1));
-    CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->hist, P->hist_cap, s, tol, C0.lambda, C0.mu,
-                           E, g.n, maxdim, GM_SWEEP, first_warm ? 1 : 0, P->stall_window, st));
+    ga.skip_done = 1;
+    CK(timed(3, sweep, run_g, &ga, 0));
+    CK(timed(2, sweep, run_c, &cy, +1));
+    CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda,
+                           C0.mu, E0, g.n, maxdim, GM_SWEEP, 0, P->stall_window, B, st));
     return BFCS_OK;
   };
 
+  // The sweep loop runs on the plan's private stream (capturable even when the
+  // caller's stream is the legacy default stream), ordered after and before
+  // the caller's stream with events.
+  CK(cudaEventRecord(P->order_ev[0], st));
+  CK(cudaStreamWaitEvent(P->loop_st, P->order_ev[0], 0));
+  cudaStream_t const caller_st = st;
+  st = P->loop_st;
+
+  // CUDA graph of graph_sweeps sweeps (used when no launch is being profiled)
+  const int G = (P->prof_kind == 0) ? P->graph_sweeps : 0;
+  cudaGraphExec_t gexec = nullptr;
+  if (G > 0 && maxit >= G) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < G; ++k) {
+      const int e = enqueue_sweep(-1);
+      if (e != BFCS_OK) {
+        cudaStreamEndCapture(st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        return e;
+      }
+    }
+    CK(cudaStreamEndCapture(st, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return BFCS_ERR_CUDA;
+  }
+  struct GraphGuard {
+    cudaGraphExec_t g;
+    ~GraphGuard() { if (g) cudaGraphExecDestroy(g); }
+  } guard{gexec};
+
   // Sweeps in chunks; the host reads the device state of chunk k-1 while chunk
   // k runs.  From two observed residuals the contraction rate gives the sweeps
-  // still needed, which sizes the next chunk; once the chunk in flight is
-  // expected to reach the tolerance, the host waits for it before sending more
-  // (sweeps enqueued past convergence are skipped on the device, but still
-  // cost their launches).
+  // still needed (slowest member), which sizes the next chunk; once the chunk
+  // in flight is expected to finish every member, the host waits for it before
+  // sending more (sweeps enqueued past convergence are skipped on the device,
+  // but still cost their launches).
   int s = 0, chunk = 4, slot = 0;
   bool pending = false;
-  int last_c = 0;                 // size of the chunk in flight
-  int obs_it = -1;                // last observed (iters, residual)
-  double obs_r = 0.0;
+  int last_c = 0;
+  std::vector<int> obs_it(B, -1);
+  std::vector<double> obs_r(B, 0.0);
+  auto all_done = [&](const IterState* h) {
+    for (int m = 0; m < B; ++m)
+      if (!h[m].done) return false;
+    return true;
+  };
+  // sweeps still needed by the slowest member after the observed state (<0: unknown)
+  auto predict = [&](const IterState* h) {
+    double worst = 0.0;
+    bool known = true;
+    for (int m = 0; m < B; ++m) {
+      if (h[m].done) continue;
+      const double r = h[m].resid_last;
+      if (!(tol > 0) || !(h[m].iters > 0) || !std::isfinite(r) || !(r > 0) || obs_it[m] < 0 ||
+          !(h[m].iters > obs_it[m]) || !(r < obs_r[m])) {
+        known = false;
+      } else {
+        const double rate = std::pow(r / obs_r[m], 1.0 / (h[m].iters - obs_it[m]));
+        worst = std::max(worst, std::log(tol / r) / std::log(rate));
+      }
+      if (std::isfinite(r) && r > 0) { obs_it[m] = h[m].iters; obs_r[m] = r; }
+    }
+    return known ? worst : -1.0;
+  };
   while (s < maxit) {
-    const int c = std::min(chunk, maxit - s);
-    for (int k = 0; k < c; ++k) {
-      const int e = enqueue_sweep(s + k);
-      if (e != BFCS_OK) return e;
+    int c;
+    if (gexec != nullptr && maxit - s >= G) {
+      c = G * std::max(1, chunk / G);
+      for (int k = 0; k < c; k += G) CK(cudaGraphLaunch(gexec, st));
+    } else {
+      c = std::min(chunk, maxit - s);
+      for (int k = 0; k < c; ++k) {
+        const int e = enqueue_sweep(s + k);
+        if (e != BFCS_OK) return e;
+      }
     }
     s += c;
-    CK(cudaMemcpyAsync(&P->ist_host[slot], P->ist, sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    IterState* hs = P->ist_host + slot * P->max_batch;
+    CK(cudaMemcpyAsync(hs, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(P->ev[slot], st));
     int next = std::min(chunk * 2, 64);
-    bool drain = false;           // wait for the chunk just sent before sending more
+    bool drain = false;
     if (pending) {
       const int w = wait_event(P->ev[slot ^ 1]);
       if (w != BFCS_OK) return w;
-      const IterState& h = P->ist_host[slot ^ 1];
-      if (h.done) break;
-      if (tol > 0 && h.iters > 0 && std::isfinite(h.resid_last) && h.resid_last > 0) {
-        if (obs_it >= 0 && h.iters > obs_it && h.resid_last < obs_r) {
-          const double rate = std::pow(h.resid_last / obs_r, 1.0 / (h.iters - obs_it));
-          const double need = std::log(tol / h.resid_last) / std::log(rate);   // sweeps after h.iters
-          const double left = need - last_c;                                     // after the chunk in flight
-          if (left <= 0.5) drain = true;
-          else next = std::max(1, std::min(64, (int)std::ceil(left) + 1));
-        }
-        obs_it = h.iters;
-        obs_r = h.resid_last;
+      const IterState* h = P->ist_host + (slot ^ 1) * P->max_batch;
+      if (all_done(h)) break;
+      const double need = predict(h);
+      if (need >= 0) {
+        const double left = need - last_c;
+        if (left <= 0.5) drain = true;
+        else next = std::max(1, std::min(64, (int)std::ceil(left) + 1));
       }
     }
     pending = true;
@@ -354,48 +502,51 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
     if (drain) {
       const int w = wait_event(P->ev[slot ^ 1]);
       if (w != BFCS_OK) return w;
-      const IterState& h = P->ist_host[slot ^ 1];
-      if (h.done) break;
+      const IterState* h = P->ist_host + (slot ^ 1) * P->max_batch;
+      if (all_done(h)) break;
       pending = false;
       chunk = 2;
-      if (std::isfinite(h.resid_last) && h.resid_last > 0) { obs_it = h.iters; obs_r = h.resid_last; }
+      predict(h);
     }
   }
 
+  // back on the caller's stream
+  CK(cudaEventRecord(P->order_ev[1], st));
+  CK(cudaStreamWaitEvent(caller_st, P->order_ev[1], 0));
+  st = caller_st;
+
   // finalize: eps^S, sigma^S in real space; residual of eps^S; u^S
-  const bool s0_warm = warm && s == 0;
-  xa.mode = s0_warm ? XM_REALTAU : XM_SWEEP;
-  xa.eps_out = (R*)out.eps;
-  xa.sig_out = (R*)out.sig;
-  xa.done = nullptr;
-  CK(launch_xpass<R>(xa, st));
-  cy.done = nullptr;
+  xa.mode = XM_SWEEP;
+  fill_xm(xa, P->mem_host, B, XIN_NONE, XOUT_EPS | XOUT_SIG);
+  xa.st = nullptr;
+  CK(launch_xpass_b<R>(xa, B, st));
+  cy.st = nullptr;
   cy.ncomp = 6;
-  CK(launch_colpass<R>(cy, -1, st));
+  CK(launch_colpass_b<R>(cy, -1, B, st));
   ga.mode = GM_FINAL;
-  ga.done = nullptr;
-  CK(launch_zgreen<R>(ga, st));
-  CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->hist, P->hist_cap, s, tol, C0.lambda, C0.mu, E,
-                         g.n, maxdim, GM_FINAL, 0, 0, st));
-  if (out.u != nullptr) {
-    cy.ncomp = 3;
-    CK(launch_colpass<R>(cy, +1, st));
-    XArgs<R> xu{};
-    xu.g = g;
-    xu.spec_in = spec;
-    xu.real_out = (R*)out.u;
-    xu.ncomp = 3;
-    xu.mode = XM_C2R;
-    xu.tw = twx;
-    CK(launch_xpass<R>(xu, st));
-  }
-  CK(cudaMemcpyAsync(&P->ist_host[2], P->ist, sizeof(IterState), cudaMemcpyDeviceToHost, st));
+  ga.skip_done = 0;
+  CK(launch_zgreen_b<R>(ga, B, st));
+  CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda, C0.mu,
+                         E0, g.n, maxdim, GM_FINAL, 0, 0, B, st));
+  cy.ncomp = 3;
+  CK(launch_colpass_b<R>(cy, +1, B, st));
+  XArgs<R> xu{};
+  xu.g = g;
+  xu.spec_in = spec;
+  xu.spec_ms = sms;
+  fill_xm(xu, P->mem_host, B, XIN_NONE, XOUT_U);
+  xu.ncomp = 3;
+  xu.mode = XM_C2R;
+  xu.tw = twx;
+  CK(launch_xpass_b<R>(xu, B, st));   // members without u_out write nothing (null rows skipped below)
+  IterState* hf = P->ist_host + 2 * P->max_batch;
+  CK(cudaMemcpyAsync(hf, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
   const int w = sync_stream(P);
   if (w != BFCS_OK) return w;
-  const IterState& h = P->ist_host[2];
-  P->last_iters = h.iters;
+  P->last_iters = hf[0].iters;
+  P->last_batch = B;
   for (int k = 0; k < P->prof_used; ++k) {
-    if (P->prof_sweep[k] >= h.iters) continue;     // launches of sweeps skipped on device
+    if (P->prof_sweep[k] >= hf[0].iters) continue;     // launches of sweeps skipped on device
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, P->prof_ev[2 * k], P->prof_ev[2 * k + 1]) != cudaSuccess)
       return BFCS_ERR_CUDA;
@@ -403,18 +554,49 @@ int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_la
     P->prof_launches += 1;
   }
   P->prof_used = 0;
-  int status = BFCS_OK;
-  if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
-  else if (tol > 0 && (!h.done || h.stalled)) status = BFCS_NOT_CONVERGED;
-  if (info != nullptr) {
-    info->iters = h.iters;
-    info->status = status;
-    info->resid = h.resid_final;
-    info->resid_prev = h.resid_last;
-    info->precision_path = sizeof(R) == 8 ? 1 : 0;
-    info->stalled = h.stalled;
+  int worst = BFCS_OK;
+  for (int m = 0; m < B; ++m) {
+    const IterState& h = hf[m];
+    int status = BFCS_OK;
+    if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
+    else if (tol > 0 && (!h.done || h.stalled)) status = BFCS_NOT_CONVERGED;
+    if (infos != nullptr) {
+      infos[m].iters = h.iters;
+      infos[m].status = status;
+      infos[m].resid = h.resid_final;
+      infos[m].resid_prev = h.resid_last;
+      infos[m].precision_path = sizeof(R) == 8 ? 1 : 0;
+      infos[m].stalled = h.stalled;
+    }
+    if (severity(status) > severity(worst)) worst = status;
   }
-  return status;
+  return worst;
+}
+
+Member make_member(const int8_t* phase, const int shift[3], const double* E, const void* b,
+                   const void* eps_init, SolveOut out) {
+  Member m{};
+  m.phase = phase;
+  m.sx = shift[0]; m.sy = shift[1]; m.sz = shift[2];
+  m.warm = eps_init != nullptr ? 1 : 0;
+  for (int c = 0; c < 6; ++c) m.E[c] = E[c];
+  m.b = b;
+  m.eps_init = eps_init;
+  m.eps_out = out.eps;
+  m.sig_out = out.sig;
+  m.u_out = out.u;
+  return m;
+}
+
+// One solve whose b_hat and bden are already in the plan (member 0).
+template <typename R>
+int solve_core(bfcs_plan P, const int8_t* phase, const PhaseTab<R>& tab, bfcs_lame C0, const double* E,
+               double tol, int maxit, const void* eps_init, SolveOut out, const int shift[3],
+               bfcs_info* info) {
+  const Member m = make_member(phase, shift, E, nullptr, eps_init, out);
+  int e = upload_members(P, 1, &m);
+  if (e != BFCS_OK) return e;
+  return run_batch<R>(P, 1, tab, C0, E, tol, maxit, info, eps_init != nullptr);
 }
 
 template <typename R>
@@ -429,11 +611,56 @@ int solve_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phase
     if (!std::isfinite(E[c])) return BFCS_ERR_INVALID_ARG;
   e = validate_inputs<R>(P, phase, b, nph);
   if (e != BFCS_OK) return e;
-  e = transform_load<R>(P, b);
+  const Member m = make_member(phase, shift, E, b, eps_init, out);
+  e = upload_members(P, 1, &m);
   if (e != BFCS_OK) return e;
-  CK(launch_bden<R>((const C2<R>*)P->bhat, P->g, P->part, P->ist, P->st));
-  return solve_core<R>(P, phase, make_tab<R>(nph, phases, C0), C0, E, tol, maxit, eps_init, out, shift,
-                       info);
+  e = transform_members<R>(P, 1);
+  if (e != BFCS_OK) return e;
+  return run_batch<R>(P, 1, make_tab<R>(nph, phases, C0), C0, E, tol, maxit, info, eps_init != nullptr);
+}
+
+// bfcs_solve_batched on FP32/FP64 plans: groups of up to max_batch members
+// advance together (one launch per pass per sweep for the whole group).
+template <typename R>
+int solve_batch_impl(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, const bfcs_lame* phases,
+                     bfcs_lame C0, double tol, int maxit, bfcs_info* infos) {
+  int e = check_material(nph, phases, C0);
+  if (e != BFCS_OK) return e;
+  if (!(tol >= 0) || maxit < 0) return BFCS_ERR_INVALID_ARG;
+  for (int m = 0; m < batch; ++m) {
+    if (pr[m].phase == nullptr || pr[m].b == nullptr || pr[m].eps_out == nullptr) return BFCS_ERR_INVALID_ARG;
+    if (pr[m].eps_init != nullptr && maxit < 1) return BFCS_ERR_INVALID_ARG;
+    for (int c = 0; c < 6; ++c)
+      if (!std::isfinite(pr[m].E[c])) return BFCS_ERR_INVALID_ARG;
+  }
+  const PhaseTab<R> tab = make_tab<R>(nph, phases, C0);
+  int worst = BFCS_OK;
+  std::vector<Member> mem;
+  std::vector<const int8_t*> ph;
+  std::vector<const void*> bs;
+  for (int start = 0; start < batch; start += P->max_batch) {
+    const int B = std::min(P->max_batch, batch - start);
+    mem.clear(); ph.clear(); bs.clear();
+    bool warm = false;
+    for (int m = start; m < start + B; ++m) {
+      mem.push_back(make_member(pr[m].phase, pr[m].shift, pr[m].E, pr[m].b, pr[m].eps_init,
+                                SolveOut{pr[m].eps_out, pr[m].sig_out, pr[m].u_out}));
+      ph.push_back(pr[m].phase);
+      bs.push_back(pr[m].b);
+      warm = warm || pr[m].eps_init != nullptr;
+    }
+    e = validate_members<R>(P, B, ph.data(), bs.data(), nph);
+    if (e != BFCS_OK) return e;
+    e = upload_members(P, B, mem.data());
+    if (e != BFCS_OK) return e;
+    e = transform_members<R>(P, B);
+    if (e != BFCS_OK) return e;
+    const int s = run_batch<R>(P, B, tab, C0, pr[start].E, tol, maxit, infos != nullptr ? infos + start : nullptr,
+                               warm);
+    if (s < 0) return s;
+    if (severity(s) > severity(worst)) worst = s;
+  }
+  return worst;
 }
 
 // FP64 strain and defect from the FP64 displacement (precision ladder):
@@ -483,8 +710,8 @@ int defect64(bfcs_plan P, const int8_t* phase, const PhaseTab<double>& tab, bfcs
   const int blocks = 512;
   CK(launch_defect<double>(da, blocks, st));
   const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
-  CK(launch_resid_reduce(P->part, blocks, P->ist64, nullptr, 0, 0, 0.0, C0.lambda, C0.mu, E, g.n, maxdim,
-                         kReduceDefect, 0, 0, st));
+  CK(launch_resid_reduce(P->part, blocks, P->ist64, nullptr, nullptr, 0, 0.0, C0.lambda, C0.mu, E, g.n,
+                         maxdim, kReduceDefect, 0, 0, 1, st));
   return BFCS_OK;
 }
 
@@ -573,10 +800,11 @@ int solve_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phas
   for (int round = 0;; ++round) {
     e = defect64(P, phase, tab64, C0, E, u64, eps64, shift);
     if (e != BFCS_OK) return e;
-    CK(cudaMemcpyAsync(&P->ist_host[2], P->ist64, sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    IterState* h64 = P->ist_host + 2 * P->max_batch;
+    CK(cudaMemcpyAsync(h64, P->ist64, sizeof(IterState), cudaMemcpyDeviceToHost, st));
     const int w = sync_stream(P);
     if (w != BFCS_OK) return w;
-    r64 = P->ist_host[2].resid_final;
+    r64 = h64->resid_final;
     if (!std::isfinite(r64)) return BFCS_ERR_DIVERGED;
     if (r64 <= tol || round >= P->max_rounds || sweeps >= maxit) break;
     // correction problem: load = the defect (its spectrum is already in place), E = 0, cold start
@@ -610,7 +838,8 @@ int solve_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phas
 
 int ensure_tmp(bfcs_plan P) {
   if (P->tmp == nullptr) {
-    if (cudaMalloc(&P->tmp, 15 * (size_t)P->g.n * P->rsz) != cudaSuccess) return BFCS_ERR_OOM;
+    const size_t members = P->mixed ? 1 : (size_t)P->max_batch;
+    if (cudaMalloc(&P->tmp, members * 15 * (size_t)P->g.n * P->rsz) != cudaSuccess) return BFCS_ERR_OOM;
   }
   if (P->tmp_hits == nullptr) {
     if (cudaMalloc(&P->tmp_hits, (size_t)P->g.n * sizeof(int)) != cudaSuccess) return BFCS_ERR_OOM;
@@ -635,23 +864,30 @@ int translate_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* p
   int* h = hits != nullptr ? (int*)hits : P->tmp_hits;
   CK(cudaMemsetAsync(avg, 0, 30 * n * sizeof(double), P->st));
   CK(cudaMemsetAsync(h, 0, n * sizeof(int), P->st));
-  e = transform_load<R>(P, b);            // b is fixed under translation (Eq. 3.4)
-  if (e != BFCS_OK) return e;
-  CK(launch_bden<R>((const C2<R>*)P->bhat, P->g, P->part, P->ist, P->st));
   const PhaseTab<R> tab = make_tab<R>(nph, phases, C0);
-  R* eps = (R*)P->tmp;
-  R* sig = eps + 6 * n;
-  R* u = sig + 6 * n;
   int worst = BFCS_OK;
-  for (int m = 0; m < nshift; ++m) {
-    const int sh[3] = {shifts[3 * m], shifts[3 * m + 1], shifts[3 * m + 2]};
-    bfcs_info inf{};
-    const int s = solve_core<R>(P, phase, tab, C0, E, tol, maxit, nullptr, SolveOut{eps, sig, u}, sh, &inf);
+  std::vector<Member> mem;
+  for (int start = 0; start < nshift; start += P->max_batch) {
+    const int B = std::min(P->max_batch, nshift - start);
+    mem.clear();
+    for (int m = 0; m < B; ++m) {
+      R* eps = (R*)P->tmp + (size_t)m * 15 * n;
+      const int32_t* sh = shifts + 3 * (start + m);
+      const int shv[3] = {sh[0], sh[1], sh[2]};
+      mem.push_back(make_member(phase, shv, E, b, nullptr, SolveOut{eps, eps + 6 * n, eps + 12 * n}));
+    }
+    e = upload_members(P, B, mem.data());
+    if (e != BFCS_OK) return e;
+    e = transform_members<R>(P, B);            // b is fixed under translation (Eq. 3.4)
+    if (e != BFCS_OK) return e;
+    const int s = run_batch<R>(P, B, tab, C0, E, tol, maxit, infos != nullptr ? infos + start : nullptr, false);
     if (s < 0) return s;
-    if (s > worst) worst = s;
-    if (infos != nullptr) infos[m] = inf;
-    CK(launch_accumulate<R>(avg, h, eps, sig, u, phase, sh[0], sh[1], sh[2], P->g.nx, P->g.ny, P->g.nz,
-                            P->st));
+    if (severity(s) > severity(worst)) worst = s;
+    for (int m = 0; m < B; ++m) {
+      const R* eps = (const R*)P->tmp + (size_t)m * 15 * n;
+      CK(launch_accumulate<R>(avg, h, eps, eps + 6 * n, eps + 12 * n, phase, mem[m].sx, mem[m].sy, mem[m].sz,
+                              P->g.nx, P->g.ny, P->g.nz, P->st));
+    }
   }
   CK(launch_scale(avg, 30 * n, 1.0 / nshift, P->st));
   const int w = sync_stream(P);
@@ -688,8 +924,6 @@ int translate_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* 
   return w != BFCS_OK ? w : worst;
 }
 
-int severity(int s) { return s < 0 ? 1000 - s : s; }
-
 }  // namespace
 
 extern "C" {
@@ -712,7 +946,7 @@ const char* bfcs_status_string(int s) {
 int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int flags, void* stream) {
   if (out == nullptr) return BFCS_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz) || max_batch < 1 ||
+  if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz) || max_batch < 1 || max_batch > kMaxBatch ||
       (flags != BFCS_FP32 && flags != BFCS_FP64 && flags != BFCS_MIXED))
     return BFCS_ERR_INVALID_ARG;
   bfcs_plan P = new bfcs_plan_s();
@@ -730,25 +964,32 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   P->csz = P->fp64 ? sizeof(C2<double>) : sizeof(C2<float>);
   P->rsz = (P->fp64 || P->mixed) ? sizeof(double) : sizeof(float);
   P->ev[0] = P->ev[1] = nullptr;
+  P->order_ev[0] = P->order_ev[1] = nullptr;
   bool ok = cudaEventCreateWithFlags(&P->ev[0], cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&P->ev[1], cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&P->ev[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&P->order_ev[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&P->order_ev[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&P->loop_st, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) { free_plan(P); return BFCS_ERR_CUDA; }
   const size_t cs = (size_t)P->g.cs;
   P->ngreen = P->fp64 ? green_nparts<double>(P->g) : green_nparts<float>(P->g);
   P->npart = std::max(P->ngreen, 512);
-  ok = cudaMalloc(&P->spec, 6 * cs * P->csz) == cudaSuccess &&
-       cudaMalloc(&P->bhat, 3 * cs * P->csz) == cudaSuccess &&
-       cudaMalloc(&P->dprev, 3 * cs * P->csz) == cudaSuccess &&
-       cudaMalloc(&P->part, P->npart * sizeof(ResidSlot)) == cudaSuccess &&
-       cudaMalloc(&P->ist, sizeof(IterState)) == cudaSuccess &&
-       cudaMalloc(&P->hist, kHistCap * sizeof(double)) == cudaSuccess &&
-       cudaMalloc(&P->ival, 2 * sizeof(int)) == cudaSuccess &&
-       cudaMalloc(&P->dval, 6 * sizeof(double)) == cudaSuccess &&
+  const size_t MB = (size_t)max_batch;
+  ok = cudaMalloc(&P->spec, MB * 6 * cs * P->csz) == cudaSuccess &&
+       cudaMalloc(&P->bhat, MB * 3 * cs * P->csz) == cudaSuccess &&
+       cudaMalloc(&P->dprev, MB * 3 * cs * P->csz) == cudaSuccess &&
+       cudaMalloc(&P->part, MB * P->npart * sizeof(ResidSlot)) == cudaSuccess &&
+       cudaMalloc(&P->ist, MB * sizeof(IterState)) == cudaSuccess &&
+       cudaMalloc(&P->hist, MB * kHistCap * sizeof(double)) == cudaSuccess &&
+       cudaMalloc(&P->mem_dev, MB * sizeof(Member)) == cudaSuccess &&
+       cudaMallocHost(&P->mem_host, MB * sizeof(Member)) == cudaSuccess &&
+       cudaMalloc(&P->ival, MB * 2 * sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&P->dval, MB * 6 * sizeof(double)) == cudaSuccess &&
        cudaMalloc(&P->dscratch, std::max(validate_scratch(P->g.n), body_force_scratch(P->g.n)) *
                                     sizeof(double)) == cudaSuccess &&
-       cudaMallocHost(&P->ist_host, 3 * sizeof(IterState)) == cudaSuccess &&
-       cudaMallocHost(&P->ival_host, 2 * sizeof(int)) == cudaSuccess &&
-       cudaMallocHost(&P->dval_host, 6 * sizeof(double)) == cudaSuccess;
+       cudaMallocHost(&P->ist_host, 3 * MB * sizeof(IterState)) == cudaSuccess &&
+       cudaMallocHost(&P->ival_host, MB * 2 * sizeof(int)) == cudaSuccess &&
+       cudaMallocHost(&P->dval_host, MB * 6 * sizeof(double)) == cudaSuccess;
   if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
   P->hist_cap = kHistCap;
   const int dims[3] = {nx, ny, nz};
@@ -768,7 +1009,8 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
       if (P->tw64[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
     }
   }
-  if (cudaMemset(P->ist, 0, sizeof(IterState)) != cudaSuccess) { free_plan(P); return BFCS_ERR_CUDA; }
+  if (cudaMemset(P->ist, 0, MB * sizeof(IterState)) != cudaSuccess) { free_plan(P); return BFCS_ERR_CUDA; }
+  if (const char* gs = std::getenv("BFCS_GRAPH_SWEEPS")) P->graph_sweeps = std::max(0, std::atoi(gs));
   *out = P;
   return BFCS_OK;
 }
@@ -842,19 +1084,26 @@ int bfcs_solve(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phase
 int bfcs_solve_batched(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, const bfcs_lame* phases,
                        bfcs_lame C0, double tol, int maxit, bfcs_info* infos) {
   if (P == nullptr || batch < 0 || (batch > 0 && pr == nullptr)) return BFCS_ERR_INVALID_ARG;
+  if (batch == 0) return BFCS_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!P->mixed) {
+    const int s = P->fp64 ? solve_batch_impl<double>(P, batch, pr, nph, phases, C0, tol, maxit, infos)
+                          : solve_batch_impl<float>(P, batch, pr, nph, phases, C0, tol, maxit, infos);
+    if (infos != nullptr) {
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      for (int m = 0; m < batch; ++m) infos[m].ms = ms;
+    }
+    return s;
+  }
   int worst = BFCS_OK;
-  for (int m = 0; m < batch; ++m) {
-    const auto t0 = std::chrono::steady_clock::now();
+  for (int m = 0; m < batch; ++m) {     // the ladder runs member by member
+    const auto t1 = std::chrono::steady_clock::now();
     const SolveOut out{pr[m].eps_out, pr[m].sig_out, pr[m].u_out};
     bfcs_info inf{};
-    const int s = P->mixed  ? solve_mixed(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol, maxit,
-                                          pr[m].eps_init, out, pr[m].shift, &inf)
-                  : P->fp64 ? solve_impl<double>(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol,
-                                                 maxit, pr[m].eps_init, out, pr[m].shift, &inf)
-                            : solve_impl<float>(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol,
-                                                maxit, pr[m].eps_init, out, pr[m].shift, &inf);
+    const int s = solve_mixed(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol, maxit, pr[m].eps_init,
+                              out, pr[m].shift, &inf);
     inf.status = s;
-    inf.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    inf.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
     if (infos != nullptr) infos[m] = inf;
     if (severity(s) > severity(worst)) worst = s;
   }

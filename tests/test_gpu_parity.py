@@ -178,19 +178,56 @@ def test_batched_equals_individual_solves():
     assert all(i.iters == 9 for i in infos)
 
 
-def test_translate_average_parity():
+@pytest.mark.parametrize("max_batch", [1, 3])
+def test_translate_average_parity(max_batch):
     dims = (16, 16, 16)
     p = small_problem(dims, (8, 8, 8), [[8, 8, 8, 36, 1]], (8.0, 8.0, 8.0), 4.0)
     shifts = [(0, 0, 0), (2, 0, 0), (0, 4, 2), (6, 6, 6), (1, 3, 5)]
     ph_o, b_o = oracle_inputs(p)
     avg_ref, hits_ref, _ = O.translate_average(ph_o, p.phases, p.c0, b_o, shifts, tol=0, maxit=10)
     ph, b = gpu_inputs(p, "fp64")
-    with api.Plan(dims, "fp64") as plan:
+    with api.Plan(dims, "fp64", max_batch=max_batch) as plan:
         avg, hits, infos = plan.translate_average(ph, p.phases, p.c0, b, shifts, tol=0, maxit=10)
     assert np.array_equal(hits.cpu().numpy(), hits_ref)
     avg = avg.cpu().numpy()
     for a0, a1 in ((0, 3), (3, 6), (6, 12), (12, 18), (18, 24), (24, 30)):
         assert rel(avg[a0:a1], avg_ref[a0:a1]) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_members_advance_together(precision):
+    """Members with different shifts, mean strains and a warm start, in one batch."""
+    p = CASES["ragged_48x24x96"]
+    ph, b = gpu_inputs(p, precision)
+    ph_o, b_o = oracle_inputs(p)
+    sweeps = 9
+    init_ref = O.solve(ph_o, p.phases, p.c0, b_o, tol=0, maxit=3)["eps"]
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    init = torch.tensor(init_ref, dtype=dt, device="cuda")
+    specs = [((0, 0, 0), (0,) * 6, None), ((5, 3, 11), (0.01, 0, 0, 0, 0, 0.002), None),
+             ((47, 23, 95), (0,) * 6, init), ((24, 12, 48), (0, -0.003, 0, 0.001, 0, 0), None)]
+    with api.Plan(p.dims, precision, max_batch=4) as plan:
+        members = [dict(phase=ph, b=b, E=E, shift=sh, eps_init=ei) for sh, E, ei in specs]
+        members, infos = plan.solve_batched(members, p.phases, p.c0, tol=0, maxit=sweeps)
+    for mem, (sh, E, ei), info in zip(members, specs, infos):
+        ref = O.solve(O.translate(ph_o, sh), p.phases, p.c0, b_o, E, tol=0, maxit=sweeps,
+                      eps_init=init_ref if ei is not None else None)
+        assert info.iters == sweeps
+        for key, k2 in (("eps_out", "eps"), ("sig_out", "sig"), ("u_out", "u")):
+            assert rel(mem[key].cpu().numpy(), ref[k2]) < TOL[precision], (sh, key)
+
+
+def test_graph_and_stream_sweeps_identical(monkeypatch):
+    p = CASES["c1_32cubed"]
+    ph, b = gpu_inputs(p, "fp32")
+    out = []
+    for g in ("0", "4"):
+        monkeypatch.setenv("BFCS_GRAPH_SWEEPS", g)
+        with api.Plan(p.dims, "fp32") as plan:
+            eps, _, _, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-5, maxit=500)
+        out.append((eps.clone(), info.iters))
+    assert out[0][1] == out[1][1]
+    assert torch.equal(out[0][0], out[1][0])
 
 
 # ---------------------------------------------------------------- errors
