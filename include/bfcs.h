@@ -212,8 +212,80 @@ int bfcs_translate_average(bfcs_plan plan, const int8_t* phase, int nphases, con
                            int32_t* hits_out, bfcs_info* infos);
 
 /*
- * bfcs_surrogate_infer - learned warm start / surrogate (3D U-net, BF16).
- * Not available in this build: returns BFCS_ERR_UNSUPPORTED.
+ * Learned warm start / surrogate.  The paper proposes replacing the solver by
+ * a learned map of the averaged nonlocal response (Sec. 6, Eqs. 6.9-6.10,
+ * Fig. 5) without fixing a model; this library's model is a 4-level 3D U-net
+ * on periodic volumes (BFCS_NET_PARAMS = 523654 parameters):
+ *   input  4 channels: b / max|b| (3) and mu(x) / mu_max - 1/2;
+ *   output 6 channels: eps mu_max / max|b| (normalised strain);
+ *   widths 32, 32, 32, 48; two circular 3^3 convolutions per level with leaky
+ *   ReLU (slope 0.1); 2^3 average pooling; 2^3 stride-2 transposed
+ *   convolutions; skip concatenation [upsampled, skip]; 1^3 head.
+ * Parameters ("params"): dev, BFCS_NET_PARAMS float (FP32 master copy); per
+ * layer in the order e0a e0b e1a e1b e2a e2b e3a e3b u2 d2a d2b u1 d1a d1b u0
+ * d0a d0b head, the weight in PyTorch's shape (conv: cout, cin, k, k, k;
+ * transposed conv: cin, cout, 2, 2, 2) then the bias.  Every call rounds the
+ * weights to BF16 on the device; activations are BF16, accumulation FP32.
+ * Grids: nx, ny, nz multiples of 8 (three 2^3 poolings), any size otherwise.
+ * Network tensors (x, y, target) are FP32, sample-major then channel-major:
+ * element (sample s, channel c, voxel v) at [(s*C + c)*N + v].
+ */
+#define BFCS_NET_PARAMS 523654
+#define BFCS_NET_TRAIN 1              /* bfcs_net_create: keep what the backward pass needs */
+
+typedef struct bfcs_net_s* bfcs_net;
+
+/* Number of parameters (BFCS_NET_PARAMS). */
+long long bfcs_net_param_count(void);
+
+/* Create a network context for nx x ny x nz grids and up to max_batch (1..1024)
+ * samples per call; flags 0 (inference) or BFCS_NET_TRAIN.  The context owns
+ * its activations (about 370 bytes per voxel and sample with BFCS_NET_TRAIN,
+ * 180 without) and orders all work on stream.  Errors: INVALID_ARG, OOM. */
+int bfcs_net_create(bfcs_net* out, int nx, int ny, int nz, int max_batch, int flags, void* stream);
+int bfcs_net_destroy(bfcs_net net);
+
+/* Network input of one sample: x_out (dev, 4 x N float) from the body force b
+ * (dev, 3 x N, float for BFCS_FP32 or double for BFCS_FP64 = precision) and
+ * the phase map (dev, N int8; shear moduli from phases, host).  With eps (dev
+ * 6 x N, same type as b) also the training target (dev, 6 x N float)
+ * eps mu_max / max|b|; eps NULL: target_out unused. */
+int bfcs_net_prepare(bfcs_net net, int precision, const void* b, const int8_t* phase, int nphases,
+                     const bfcs_lame* phases, const void* eps, float* x_out, float* target_out);
+
+/* y (dev, batch x 6 x N float) = network(x) for x (dev, batch x 4 x N float). */
+int bfcs_net_forward(bfcs_net net, const float* params, int batch, const float* x, float* y);
+
+/* Loss L = mean over the batch of ||y - target||^2 / ||target||^2 and its
+ * gradient grad (dev, BFCS_NET_PARAMS float, overwritten) with respect to
+ * params; loss_dev (dev, 1 double) or NULL.  Needs BFCS_NET_TRAIN.  The
+ * result is deterministic (fixed-order reductions). */
+int bfcs_net_grad(bfcs_net net, const float* params, int batch, const float* x, const float* target,
+                  float* grad, double* loss_dev);
+
+/* One Adam step (Kingma and Ba 2014; beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * correction for step t >= 1) on params with moments m, v (dev, float,
+ * BFCS_NET_PARAMS each, zero before step 1). */
+int bfcs_net_adam(bfcs_net net, float* params, const float* grad, float* m, float* v, long long t, float lr);
+
+/* bfcs_net_grad followed by bfcs_net_adam (grad is the caller's scratch). */
+int bfcs_net_train_step(bfcs_net net, float* params, float* grad, float* m, float* v, long long t, float lr,
+                        int batch, const float* x, const float* target, double* loss_dev);
+
+/* Predicted strain for batch samples (host arrays of dev pointers): b[i]
+ * (3 x N), phase[i] (N int8), eps_out[i] (6 x N), element type float for
+ * precision BFCS_FP32 or double for BFCS_FP64; processed max_batch at a time.
+ * The result is a warm start for bfcs_solve / bfcs_problem.eps_init. */
+int bfcs_net_predict(bfcs_net net, const float* params, int precision, int batch, const void* const* b,
+                     const int8_t* const* phase, int nphases, const bfcs_lame* phases, void* const* eps_out);
+
+/*
+ * bfcs_surrogate_infer - the network's strain prediction on the plan's grid:
+ * eps_pred (dev, 6 x N, element type of the plan: float for BFCS_FP32, double
+ * otherwise) from b (dev, 3 x N, same type) and phase (dev, N int8).
+ * weights: dev, BFCS_NET_PARAMS float (layout above).  The plan keeps an
+ * inference context (created on the first call, ~180 bytes per voxel).
+ * Errors: INVALID_ARG (grid not a multiple of 8, bad pointers or phases), OOM.
  */
 int bfcs_surrogate_infer(bfcs_plan plan, const void* weights, const void* b, const int8_t* phase,
                          int nphases, const bfcs_lame* phases, void* eps_pred);

@@ -11,7 +11,7 @@ the project's): a 4-level 3D U-net on periodic volumes.
 
   inputs  (4 channels): b1, b2, b3 scaled by 1/max|b|, and the phase shear
           modulus mu(x) / mu_max - 1/2
-  outputs (6 channels): eps * mu_ref / max|b|, tensorial components
+  outputs (6 channels): eps * mu_max / max|b|, tensorial components
           (xx yy zz yz xz xy)
   level widths 32, 32, 32, 48; two 3^3 convolutions per level (circular
   padding: the fields are periodic), leaky ReLU (slope 0.1), 2^3 average
@@ -134,6 +134,13 @@ def features(b, phase, mus):
     mu = torch.as_tensor([m for m in mus], dtype=torch.float64)[torch.as_tensor(phase).long()]
     x = torch.cat([b / s, (mu / mu.max() - 0.5)[None]], dim=0)
     return x, s
+
+
+def targets(eps, b, mus):
+    """Training target of a strain field eps (6, ...): eps * mu_max / max|b|."""
+    eps = torch.as_tensor(eps, dtype=torch.float64)
+    s = float(torch.as_tensor(b, dtype=torch.float64).abs().max())
+    return eps * (max(float(m) for m in mus) / s)
 
 
 def adam_step(flat, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

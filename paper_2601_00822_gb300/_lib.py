@@ -30,8 +30,12 @@ EXPORTS = (
     "bfcs_plan_create", "bfcs_plan_destroy", "bfcs_voxelize", "bfcs_body_force", "bfcs_solve",
     "bfcs_solve_batched", "bfcs_translate_average", "bfcs_surrogate_infer", "bfcs_fft3d",
     "bfcs_last_history", "bfcs_status_string", "bfcs_kernel_launches", "bfcs_profile_kernel",
-    "bfcs_profile_read", "bfcs_body_force_noalloc",
+    "bfcs_profile_read", "bfcs_body_force_noalloc", "bfcs_net_param_count", "bfcs_net_create",
+    "bfcs_net_destroy", "bfcs_net_prepare", "bfcs_net_forward", "bfcs_net_grad", "bfcs_net_adam",
+    "bfcs_net_train_step", "bfcs_net_predict",
 )
+NET_PARAMS = 523654
+NET_TRAIN = 1
 
 
 class Lame(C.Structure):
@@ -69,12 +73,24 @@ def _declare(lib):
     lib.bfcs_kernel_launches.argtypes = []
     lib.bfcs_profile_kernel.argtypes = [vp, i]
     lib.bfcs_profile_read.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(d)]
+    ll, f = C.c_longlong, C.c_float
+    lib.bfcs_net_param_count.argtypes = []
+    lib.bfcs_net_create.argtypes = [C.POINTER(vp), i, i, i, i, i, vp]
+    lib.bfcs_net_destroy.argtypes = [vp]
+    lib.bfcs_net_prepare.argtypes = [vp, i, vp, vp, i, C.POINTER(Lame), vp, vp, vp]
+    lib.bfcs_net_forward.argtypes = [vp, vp, i, vp, vp]
+    lib.bfcs_net_grad.argtypes = [vp, vp, i, vp, vp, vp, vp]
+    lib.bfcs_net_adam.argtypes = [vp, vp, vp, vp, vp, ll, f]
+    lib.bfcs_net_train_step.argtypes = [vp, vp, vp, vp, vp, ll, f, i, vp, vp, vp]
+    lib.bfcs_net_predict.argtypes = [vp, vp, i, i, C.POINTER(vp), C.POINTER(vp), i, C.POINTER(Lame),
+                                     C.POINTER(vp)]
     lib.bfcs_status_string.argtypes = [i]
     lib.bfcs_status_string.restype = C.c_char_p
     for name in EXPORTS:
         if name != "bfcs_status_string":
             getattr(lib, name).restype = C.c_int
     lib.bfcs_kernel_launches.restype = C.c_longlong
+    lib.bfcs_net_param_count.restype = C.c_longlong
     return lib
 
 

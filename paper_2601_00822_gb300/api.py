@@ -224,3 +224,144 @@ class Plan:
         if n < 0:
             raise _lib.BfcsError(n, "bfcs_last_history")
         return np.array(buf[:n])
+
+    def surrogate_infer(self, weights, b, phase, phases, eps_out=None):
+        """bfcs_surrogate_infer: the network's strain prediction (6, nz, ny, nx) on this plan's grid."""
+        _check_tensor(weights, (_lib.NET_PARAMS,), torch.float32, "weights")
+        _check_tensor(b, self._shape(3), self.dtype, "b")
+        _check_tensor(phase, self._shape(1)[1:], torch.int8, "phase")
+        eps = eps_out if eps_out is not None else self._alloc(6)
+        _check_tensor(eps, self._shape(6), self.dtype, "eps_out")
+        arr = _lames(phases)
+        _lib.check(self.lib.bfcs_surrogate_infer(self.handle, _ptr(weights), _ptr(b), _ptr(phase), len(phases),
+                                                 arr, _ptr(eps)), "bfcs_surrogate_infer")
+        return eps
+
+
+def _ptr_array(ts):
+    arr = (C.c_void_p * len(ts))()
+    for k, t in enumerate(ts):
+        arr[k] = t.data_ptr()
+    return arr
+
+
+class Net:
+    """bfcs_net_create / bfcs_net_destroy with the network calls as methods.
+
+    params, grads and Adam moments are float32 CUDA tensors of NET_PARAMS
+    entries (layout of include/bfcs.h); x is (batch, 4, nz, ny, nx), targets
+    and outputs (batch, 6, nz, ny, nx), float32.
+    """
+
+    def __init__(self, dims, max_batch=1, train=False, stream=None):
+        self.lib = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.max_batch = int(max_batch)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        nx, ny, nz = self.dims
+        _lib.check(self.lib.bfcs_net_create(C.byref(h), nx, ny, nz, self.max_batch,
+                                            _lib.NET_TRAIN if train else 0, _stream_ptr(self.stream)),
+                   "bfcs_net_create")
+        self.handle = h
+
+    @staticmethod
+    def param_count() -> int:
+        return int(_lib.load().bfcs_net_param_count())
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.bfcs_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vol(self, batch, ch):
+        nx, ny, nz = self.dims
+        return (batch, ch, nz, ny, nx)
+
+    def prepare(self, b, phase, phases, eps=None, x_out=None, target_out=None):
+        """bfcs_net_prepare: network input (4, nz, ny, nx) [and target (6, ...)] of one sample."""
+        nx, ny, nz = self.dims
+        prec = _lib.FP64 if b.dtype == torch.float64 else _lib.FP32
+        _check_tensor(b, (3, nz, ny, nx), b.dtype, "b")
+        _check_tensor(phase, (nz, ny, nx), torch.int8, "phase")
+        _check_tensor(eps, (6, nz, ny, nx), b.dtype, "eps")
+        x = x_out if x_out is not None else torch.empty((4, nz, ny, nx), dtype=torch.float32, device="cuda")
+        t = None
+        if eps is not None:
+            t = target_out if target_out is not None else torch.empty((6, nz, ny, nx), dtype=torch.float32,
+                                                                      device="cuda")
+        _check_tensor(x, (4, nz, ny, nx), torch.float32, "x_out")
+        _check_tensor(t, (6, nz, ny, nx), torch.float32, "target_out")
+        arr = _lames(phases)
+        _lib.check(self.lib.bfcs_net_prepare(self.handle, prec, _ptr(b), _ptr(phase), len(phases), arr,
+                                             _ptr(eps), _ptr(x), _ptr(t)), "bfcs_net_prepare")
+        return x if eps is None else (x, t)
+
+    def forward(self, params, x, y=None):
+        """bfcs_net_forward."""
+        B = x.shape[0]
+        _check_tensor(params, (_lib.NET_PARAMS,), torch.float32, "params")
+        _check_tensor(x, self._vol(B, 4), torch.float32, "x")
+        y = y if y is not None else torch.empty(self._vol(B, 6), dtype=torch.float32, device="cuda")
+        _check_tensor(y, self._vol(B, 6), torch.float32, "y")
+        _lib.check(self.lib.bfcs_net_forward(self.handle, _ptr(params), B, _ptr(x), _ptr(y)), "bfcs_net_forward")
+        return y
+
+    def grad(self, params, x, target, grad=None, loss=None):
+        """bfcs_net_grad: (grad, loss) with loss a 1-element float64 CUDA tensor."""
+        B = x.shape[0]
+        _check_tensor(params, (_lib.NET_PARAMS,), torch.float32, "params")
+        _check_tensor(x, self._vol(B, 4), torch.float32, "x")
+        _check_tensor(target, self._vol(B, 6), torch.float32, "target")
+        grad = grad if grad is not None else torch.empty(_lib.NET_PARAMS, dtype=torch.float32, device="cuda")
+        loss = loss if loss is not None else torch.empty(1, dtype=torch.float64, device="cuda")
+        _check_tensor(grad, (_lib.NET_PARAMS,), torch.float32, "grad")
+        _lib.check(self.lib.bfcs_net_grad(self.handle, _ptr(params), B, _ptr(x), _ptr(target), _ptr(grad),
+                                          _ptr(loss)), "bfcs_net_grad")
+        return grad, loss
+
+    def adam(self, params, grad, m, v, t, lr):
+        """bfcs_net_adam: one Adam step in place on params, m, v."""
+        for name, ten in (("params", params), ("grad", grad), ("m", m), ("v", v)):
+            _check_tensor(ten, (_lib.NET_PARAMS,), torch.float32, name)
+        _lib.check(self.lib.bfcs_net_adam(self.handle, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(t),
+                                          float(lr)), "bfcs_net_adam")
+
+    def train_step(self, params, grad, m, v, t, lr, x, target, loss=None):
+        """bfcs_net_train_step: gradient then Adam; returns the loss tensor (device)."""
+        B = x.shape[0]
+        for name, ten in (("params", params), ("grad", grad), ("m", m), ("v", v)):
+            _check_tensor(ten, (_lib.NET_PARAMS,), torch.float32, name)
+        _check_tensor(x, self._vol(B, 4), torch.float32, "x")
+        _check_tensor(target, self._vol(B, 6), torch.float32, "target")
+        loss = loss if loss is not None else torch.empty(1, dtype=torch.float64, device="cuda")
+        _lib.check(self.lib.bfcs_net_train_step(self.handle, _ptr(params), _ptr(grad), _ptr(m), _ptr(v),
+                                                int(t), float(lr), B, _ptr(x), _ptr(target), _ptr(loss)),
+                   "bfcs_net_train_step")
+        return loss
+
+    def predict(self, params, bs, phases_maps, phases, eps_out=None):
+        """bfcs_net_predict: strain warm starts (6, nz, ny, nx) for lists of b and phase maps."""
+        nx, ny, nz = self.dims
+        B = len(bs)
+        dt = bs[0].dtype
+        prec = _lib.FP64 if dt == torch.float64 else _lib.FP32
+        for b in bs:
+            _check_tensor(b, (3, nz, ny, nx), dt, "b")
+        for ph in phases_maps:
+            _check_tensor(ph, (nz, ny, nx), torch.int8, "phase")
+        outs = eps_out if eps_out is not None else [
+            torch.empty((6, nz, ny, nx), dtype=dt, device="cuda") for _ in range(B)]
+        for e in outs:
+            _check_tensor(e, (6, nz, ny, nx), dt, "eps_out")
+        arr = _lames(phases)
+        _lib.check(self.lib.bfcs_net_predict(self.handle, _ptr(params), prec, B, _ptr_array(bs),
+                                             _ptr_array(phases_maps), len(phases), arr, _ptr_array(outs)),
+                   "bfcs_net_predict")
+        return outs

@@ -32,6 +32,7 @@ UNITS = [
     ("k_misc.cu", [], "k_misc.o"),
     ("solver.cu", [], "solver.o"),
     ("noalloc.cu", [], "noalloc.o"),
+    ("unet.cu", [], "unet.o"),
 ]
 
 

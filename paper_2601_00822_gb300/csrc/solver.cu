@@ -64,6 +64,7 @@ struct bfcs_plan_s {
   double* u64 = nullptr;           // 3 x N doubles: FP64 displacement when the caller passes none
   int max_rounds = 8;              // defect-correction rounds
   double switch_tol = 1e-4;        // FP32 phase stops here (or at the stall)
+  bfcs_net net = nullptr;          // inference context of bfcs_surrogate_infer (created on first use)
 };
 
 namespace {
@@ -142,6 +143,7 @@ void free_plan(bfcs_plan P) {
   if (P->loop_st) cudaStreamDestroy(P->loop_st);
   if (P->order_ev[0]) cudaEventDestroy(P->order_ev[0]);
   if (P->order_ev[1]) cudaEventDestroy(P->order_ev[1]);
+  if (P->net) bfcs_net_destroy(P->net);
   delete P;
 }
 
@@ -1124,8 +1126,19 @@ int bfcs_translate_average(bfcs_plan P, const int8_t* phase, int nph, const bfcs
                                          avg_out, hits_out, infos);
 }
 
-int bfcs_surrogate_infer(bfcs_plan, const void*, const void*, const int8_t*, int, const bfcs_lame*, void*) {
-  return BFCS_ERR_UNSUPPORTED;
+int bfcs_surrogate_infer(bfcs_plan P, const void* weights, const void* b, const int8_t* phase, int nph,
+                         const bfcs_lame* phases, void* eps_pred) {
+  if (P == nullptr || weights == nullptr || b == nullptr || phase == nullptr || eps_pred == nullptr)
+    return BFCS_ERR_INVALID_ARG;
+  if (P->net == nullptr) {
+    const int s = bfcs_net_create(&P->net, P->nx, P->ny, P->nz, 1, 0, P->st);
+    if (s != BFCS_OK) return s;
+  }
+  const void* bs[1] = {b};
+  const int8_t* ps[1] = {phase};
+  void* es[1] = {eps_pred};
+  const int prec = (P->fp64 || P->mixed) ? BFCS_FP64 : BFCS_FP32;
+  return bfcs_net_predict(P->net, (const float*)weights, prec, 1, bs, ps, nph, phases, es);
 }
 
 }  // extern "C"

@@ -41,3 +41,15 @@ def test_invalid_plan_rejected_before_any_device_work():
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 31, 1, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 0, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_plan_create(None, 32, 32, 32, 1, 0, None) == _lib.ERR_INVALID_ARG
+
+
+def test_network_parameter_count_and_invalid_contexts():
+    from oracle import unet_oracle as U
+    lib = _lib.load()
+    assert lib.bfcs_net_param_count() == U.param_count() == _lib.NET_PARAMS
+    h = ctypes.c_void_p()
+    assert lib.bfcs_net_create(ctypes.byref(h), 12, 16, 16, 1, 0, None) == _lib.ERR_INVALID_ARG  # not /8
+    assert lib.bfcs_net_create(ctypes.byref(h), 16, 16, 16, 0, 0, None) == _lib.ERR_INVALID_ARG
+    assert lib.bfcs_net_create(ctypes.byref(h), 16, 16, 16, 1, 4, None) == _lib.ERR_INVALID_ARG  # flags
+    assert lib.bfcs_net_create(None, 16, 16, 16, 1, 0, None) == _lib.ERR_INVALID_ARG
+    assert lib.bfcs_net_destroy(None) == _lib.ERR_INVALID_ARG
