@@ -253,6 +253,7 @@ struct Member {
   void* eps_out;          // 6 x N
   void* sig_out;          // 6 x N or null
   void* u_out;            // 3 x N or null
+  double tol;             // >= 0: this member's tolerance (overrides the launch's), < 0: the launch's
 };
 
 // Device-side iteration state of one solve.  Everything before resid_last is

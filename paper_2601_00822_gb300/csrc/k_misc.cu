@@ -297,6 +297,7 @@ __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* sts
   if (mem != nullptr) {
     for (int c = 0; c < 6; ++c) E[c] = mem[m].E[c];
     warm = mem[m].warm;
+    if (mem[m].tol >= 0.0) tol = mem[m].tol;
   }
   const double trE = E[0] + E[1] + E[2];
   double s0[6];

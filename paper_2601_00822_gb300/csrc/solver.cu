@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <array>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -57,11 +58,11 @@ struct bfcs_plan_s {
   double prof_ms = 0.0;
   // precision ladder (BFCS_MIXED): FP64 transform workspace and FP32 real scratch
   void* spec64 = nullptr;          // 6 x cs complex128
-  void* bhat64 = nullptr;          // 3 x cs complex128
+  void* bhat64 = nullptr;          // max_batch x 3 x cs complex128: FP64 load spectra
   void* tw64[3] = {nullptr, nullptr, nullptr};
-  IterState* ist64 = nullptr;
-  float* r32 = nullptr;            // 12 x N floats: b32 (3) | eps32 (6) | u32 (3)
-  double* u64 = nullptr;           // 3 x N doubles: FP64 displacement when the caller passes none
+  IterState* ist64 = nullptr;      // max_batch FP64 residual states
+  float* r32 = nullptr;            // max_batch x 12 x N floats: (unused 3) | eps32 (6) | u32 (3)
+  double* u64 = nullptr;           // max_batch x 3 x N doubles: FP64 displacements when the caller passes none
   int max_rounds = 8;              // defect-correction rounds
   double switch_tol = 1e-4;        // FP32 phase stops here (or at the stall)
   bfcs_net net = nullptr;          // inference context of bfcs_surrogate_infer (created on first use)
@@ -456,12 +457,13 @@ int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const do
     for (int m = 0; m < B; ++m) {
       if (h[m].done) continue;
       const double r = h[m].resid_last;
-      if (!(tol > 0) || !(h[m].iters > 0) || !std::isfinite(r) || !(r > 0) || obs_it[m] < 0 ||
+      const double tl = P->mem_host[m].tol >= 0 ? P->mem_host[m].tol : tol;
+      if (!(tl > 0) || !(h[m].iters > 0) || !std::isfinite(r) || !(r > 0) || obs_it[m] < 0 ||
           !(h[m].iters > obs_it[m]) || !(r < obs_r[m])) {
         known = false;
       } else {
         const double rate = std::pow(r / obs_r[m], 1.0 / (h[m].iters - obs_it[m]));
-        worst = std::max(worst, std::log(tol / r) / std::log(rate));
+        worst = std::max(worst, std::log(tl / r) / std::log(rate));
       }
       if (std::isfinite(r) && r > 0) { obs_it[m] = h[m].iters; obs_r[m] = r; }
     }
@@ -587,6 +589,7 @@ Member make_member(const int8_t* phase, const int shift[3], const double* E, con
   m.eps_out = out.eps;
   m.sig_out = out.sig;
   m.u_out = out.u;
+  m.tol = -1.0;
   return m;
 }
 
@@ -665,14 +668,15 @@ int solve_batch_impl(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, co
   return worst;
 }
 
-// FP64 strain and defect from the FP64 displacement (precision ladder):
-// eps64 = E + sym grad u64 (spectral, exactly compatible), then sigma = L eps64,
-// its transform, R_hat = i xi . sigma_hat + b_hat, the FP64 residual r(eps64)
-// into ist64->resid_final, and R_hat rounded to complex64 into the plan's FP32
-// load spectrum (the load of the correction problem, already transformed).
-// eps64 is written to `eps_out`.  Needs b_hat64 and ist64->bden.
-int defect64(bfcs_plan P, const int8_t* phase, const PhaseTab<double>& tab, bfcs_lame C0, const double* E,
-             const double* u64, double* eps_out, const int shift[3]) {
+// FP64 strain and defect from the FP64 displacement (precision ladder), member
+// slot m: eps64 = E + sym grad u64 (spectral, exactly compatible), then
+// sigma = L eps64, its transform, R_hat = i xi . sigma_hat + b_hat64[m], the
+// FP64 residual r(eps64) into ist64[m].resid_final, and R_hat rounded to
+// complex64 into `out32` (the load of the correction problem, already
+// transformed).  eps64 is written to `eps_out`.  Needs b_hat64[m] and
+// ist64[m].bden.
+int defect64(bfcs_plan P, int m, const int8_t* phase, const PhaseTab<double>& tab, bfcs_lame C0,
+             const double* E, const double* u64, double* eps_out, const int shift[3], C2<float>* out32) {
   const Geo g = P->g;
   cudaStream_t st = P->st;
   C2<double>* spec = (C2<double>*)P->spec64;
@@ -704,138 +708,231 @@ int defect64(bfcs_plan P, const int8_t* phase, const PhaseTab<double>& tab, bfcs
   CK(launch_colpass<double>(ca, -1, st));                            // z forward
   DArgs<double> da{};
   da.spec = spec;
-  da.bhat = (const C2<double>*)P->bhat64;
-  da.out32 = (C2<float>*)P->bhat;
+  da.bhat = (const C2<double>*)P->bhat64 + (size_t)m * 3 * g.cs;
+  da.out32 = out32;
   da.g = g;
   da.part = P->part;
-  da.st = P->ist64;
+  da.st = P->ist64 + m;
   const int blocks = 512;
   CK(launch_defect<double>(da, blocks, st));
   const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
-  CK(launch_resid_reduce(P->part, blocks, P->ist64, nullptr, nullptr, 0, 0.0, C0.lambda, C0.mu, E, g.n,
+  CK(launch_resid_reduce(P->part, blocks, P->ist64 + m, nullptr, nullptr, 0, 0.0, C0.lambda, C0.mu, E, g.n,
                          maxdim, kReduceDefect, 0, 0, 1, st));
   return BFCS_OK;
 }
 
-// FP32 sweeps with FP64 defect correction; every field at the API is FP64.
-// The FP64 state is the displacement u64, so the strain eps64 = E + sym grad
-// u64 stays exactly compatible.  Phase 1: FP32 solve to max(tol, switch_tol)
-// (or its stall), u64 = its displacement.  Then rounds: eps64 and its FP64
-// residual r64; stop when r64 <= tol; else solve the correction problem (load
-// = the FP64 defect rounded to FP32, E = 0) in FP32 to 0.5 tol / r64 and add
-// its displacement to u64.
-int solve_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
-                const void* b, const double* E, double tol, int maxit, const void* eps_init, SolveOut out,
-                const int shift[3], bfcs_info* info) {
+// Warm start of the ladder in FP64: u64 = the displacement of the compatible
+// part of eps_init, u_hat = -i G0(xi) (C0 eps_hat) xi (the strain's
+// incompatible part and its mean are dropped; E is imposed by the defect step).
+int warm_disp64(bfcs_plan P, const void* eps_init, double* u64, bfcs_lame C0) {
+  const Geo g = P->g;
+  cudaStream_t st = P->st;
+  C2<double>* spec = (C2<double>*)P->spec64;
+  XArgs<double> xa{};
+  xa.g = g;
+  xa.real_in = (const double*)eps_init;
+  xa.spec_out = spec;
+  xa.ncomp = 6;
+  xa.mode = XM_R2C;
+  xa.tw = (const C2<double>*)P->tw64[0];
+  CK(launch_xpass<double>(xa, st));
+  CArgs<double> ca{};
+  ca.data = spec;
+  ca.g = g;
+  ca.ncomp = 6;
+  ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
+  CK(launch_colpass<double>(ca, -1, st));
+  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
+  CK(launch_colpass<double>(ca, -1, st));
+  CK(launch_disp<double>(spec, g, C0.lambda, C0.mu, st));
+  ca.ncomp = 3;
+  CK(launch_colpass<double>(ca, +1, st));
+  ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
+  CK(launch_colpass<double>(ca, +1, st));
+  XArgs<double> xc{};
+  xc.g = g;
+  xc.spec_in = spec;
+  xc.real_out = u64;
+  xc.ncomp = 3;
+  xc.mode = XM_C2R;
+  xc.tw = (const C2<double>*)P->tw64[0];
+  CK(launch_xpass<double>(xc, st));
+  return BFCS_OK;
+}
+
+// FP32 sweeps with FP64 defect correction for B <= max_batch members of one
+// grid; every field at the API is FP64 (Member pointers).  The FP64 state of a
+// member is its displacement u64, so eps64 = E + sym grad u64 stays exactly
+// compatible.
+//  Phase 1: members without a warm start run one batched FP32 solve to
+//  max(tol, switch_tol) (or their stall); u64 = its displacement.  A warm
+//  member takes u64 from its eps_init (FP64 projection).
+//  Rounds: every unfinished member gets eps64 and its FP64 residual r64 (one
+//  member at a time, FP64 workspace); a member stops when r64 <= tol (or after
+//  max_rounds / maxit); the others solve their correction problems (load = the
+//  FP64 defect rounded to FP32, E = 0) together in one batched FP32 solve, each
+//  to its own relative tolerance 0.5 tol / r64 (at least switch_tol, so that no
+//  FP32 solve is asked to go near its rounding floor), and add the correction's
+//  displacement.
+int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                      double tol, int maxit, bfcs_info* infos) {
   int e = check_material(nph, phases, C0);
   if (e != BFCS_OK) return e;
-  if (phase == nullptr || b == nullptr || E == nullptr || out.eps == nullptr) return BFCS_ERR_INVALID_ARG;
-  if (!(tol >= 0) || maxit < 0) return BFCS_ERR_INVALID_ARG;
-  for (int c = 0; c < 6; ++c)
-    if (!std::isfinite(E[c])) return BFCS_ERR_INVALID_ARG;
-  e = validate_inputs<double>(P, phase, b, nph);
+  if (B < 1 || B > P->max_batch || !(tol >= 0) || maxit < 0) return BFCS_ERR_INVALID_ARG;
+  std::vector<const int8_t*> phs(B);
+  std::vector<const void*> bs(B);
+  for (int m = 0; m < B; ++m) {
+    if (in[m].phase == nullptr || in[m].b == nullptr || in[m].eps_out == nullptr) return BFCS_ERR_INVALID_ARG;
+    for (int c = 0; c < 6; ++c)
+      if (!std::isfinite(in[m].E[c])) return BFCS_ERR_INVALID_ARG;
+    phs[m] = in[m].phase;
+    bs[m] = in[m].b;
+  }
+  e = validate_members<double>(P, B, phs.data(), bs.data(), nph);
   if (e != BFCS_OK) return e;
   const Geo g = P->g;
   const long long n = g.n;
+  const size_t cs = (size_t)g.cs;
   cudaStream_t st = P->st;
-  float* eps32 = P->r32 + 3 * n;
-  float* u32 = eps32 + 6 * n;
-  double* eps64 = (double*)out.eps;
-  double* u64 = out.u != nullptr ? (double*)out.u : P->u64;
+  C2<float>* bhat32 = (C2<float>*)P->bhat;
+  C2<double>* bhat64 = (C2<double>*)P->bhat64;
+  auto eps32 = [&](int j) { return P->r32 + (size_t)j * 12 * n + 3 * n; };
+  auto u32 = [&](int j) { return P->r32 + (size_t)j * 12 * n + 9 * n; };
+  std::vector<double*> u64(B);
+  for (int m = 0; m < B; ++m)
+    u64[m] = in[m].u_out != nullptr ? (double*)in[m].u_out : P->u64 + (size_t)m * 3 * n;
   const PhaseTab<float> tab32 = make_tab<float>(nph, phases, C0);
   const PhaseTab<double> tab64 = make_tab<double>(nph, phases, C0);
   const double zeroE[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<int> sweeps(B, 0), stalled(B, 0), status(B, BFCS_OK);
+  std::vector<double> r_last(B, INFINITY), r64(B, INFINITY);
+  std::vector<char> fin(B, 0);
+  std::vector<Member> mem;
+  std::vector<bfcs_info> inf(P->max_batch);
+  auto shift_of = [&](int m) { return std::array<int, 3>{in[m].sx, in[m].sy, in[m].sz}; };
 
-  // FP64 load transform and its norm (residual denominator)
-  e = transform_into<double>(P, b, P->bhat64, P->tw64);
-  if (e != BFCS_OK) return e;
-  CK(cudaMemsetAsync(P->ist64, 0, sizeof(IterState), st));
-  CK(launch_bden<double>((const C2<double>*)P->bhat64, g, P->part, P->ist64, st));
-
-  int sweeps = 0, stalled = 0;
-  double r_last = INFINITY;
-  CK(launch_cast_spec((C2<float>*)P->bhat, (const C2<double>*)P->bhat64, g, 3, st));   // FP32 load spectrum
-  CK(launch_bden<float>((const C2<float>*)P->bhat, g, P->part, P->ist, st));
-  if (eps_init == nullptr) {
-    bfcs_info inf{};
-    const int s1 = solve_core<float>(P, phase, tab32, C0, E, std::max(tol, P->switch_tol), maxit, nullptr,
-                                     SolveOut{eps32, nullptr, u32}, shift, &inf);
-    if (s1 < 0) return s1;
-    sweeps += inf.iters;
-    r_last = inf.resid;
-    CK(launch_cast_f2d(u64, u32, 3 * n, st));
-  } else {
-    // warm start: u64 from the compatible part of eps_init, in FP64
-    C2<double>* spec = (C2<double>*)P->spec64;
-    XArgs<double> xa{};
-    xa.g = g;
-    xa.real_in = (const double*)eps_init;
-    xa.spec_out = spec;
-    xa.ncomp = 6;
-    xa.mode = XM_R2C;
-    xa.tw = (const C2<double>*)P->tw64[0];
-    CK(launch_xpass<double>(xa, st));
-    CArgs<double> ca{};
-    ca.data = spec;
-    ca.g = g;
-    ca.ncomp = 6;
-    ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
-    CK(launch_colpass<double>(ca, -1, st));
-    ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
-    CK(launch_colpass<double>(ca, -1, st));
-    CK(launch_disp<double>(spec, g, C0.lambda, C0.mu, st));
-    ca.ncomp = 3;
-    CK(launch_colpass<double>(ca, +1, st));
-    ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
-    CK(launch_colpass<double>(ca, +1, st));
-    XArgs<double> xc{};
-    xc.g = g;
-    xc.spec_in = spec;
-    xc.real_out = u64;
-    xc.ncomp = 3;
-    xc.mode = XM_C2R;
-    xc.tw = (const C2<double>*)P->tw64[0];
-    CK(launch_xpass<double>(xc, st));
+  // FP64 load spectra and their norms (residual denominators)
+  CK(cudaMemsetAsync(P->ist64, 0, B * sizeof(IterState), st));
+  for (int m = 0; m < B; ++m) {
+    e = transform_into<double>(P, in[m].b, bhat64 + (size_t)m * 3 * cs, P->tw64);
+    if (e != BFCS_OK) return e;
+    CK(launch_bden<double>(bhat64 + (size_t)m * 3 * cs, g, P->part, P->ist64 + m, st));
   }
 
-  double r64 = INFINITY;
-  for (int round = 0;; ++round) {
-    e = defect64(P, phase, tab64, C0, E, u64, eps64, shift);
+  // phase 1
+  std::vector<int> cold;
+  for (int m = 0; m < B; ++m) {
+    if (in[m].eps_init != nullptr) {
+      e = warm_disp64(P, in[m].eps_init, u64[m], C0);
+      if (e != BFCS_OK) return e;
+    } else {
+      cold.push_back(m);
+    }
+  }
+  if (!cold.empty()) {
+    const int k = (int)cold.size();
+    mem.clear();
+    for (int j = 0; j < k; ++j) {
+      const int m = cold[j];
+      CK(launch_cast_spec(bhat32 + (size_t)j * 3 * cs, bhat64 + (size_t)m * 3 * cs, g, 3, st));
+      const auto sh = shift_of(m);
+      mem.push_back(make_member(in[m].phase, sh.data(), in[m].E, nullptr, nullptr,
+                                SolveOut{eps32(j), nullptr, u32(j)}));
+    }
+    CK(launch_bden<float>(bhat32, g, P->part, P->ist, st, k, 3 * cs));
+    e = upload_members(P, k, mem.data());
     if (e != BFCS_OK) return e;
+    const int s1 = run_batch<float>(P, k, tab32, C0, in[cold[0]].E, std::max(tol, P->switch_tol), maxit,
+                                    inf.data(), false);
+    if (s1 < 0) return s1;
+    for (int j = 0; j < k; ++j) {
+      const int m = cold[j];
+      sweeps[m] += inf[j].iters;
+      r_last[m] = inf[j].resid;
+      CK(launch_cast_f2d(u64[m], u32(j), 3 * n, st));
+    }
+  }
+
+  for (int round = 0;; ++round) {
+    std::vector<int> act;
+    for (int m = 0; m < B; ++m)
+      if (!fin[m]) act.push_back(m);
+    if (act.empty()) break;
+    for (int m : act) {
+      const auto sh = shift_of(m);
+      e = defect64(P, m, in[m].phase, tab64, C0, in[m].E, u64[m], (double*)in[m].eps_out, sh.data(),
+                   bhat32 + (size_t)m * 3 * cs);
+      if (e != BFCS_OK) return e;
+    }
     IterState* h64 = P->ist_host + 2 * P->max_batch;
-    CK(cudaMemcpyAsync(h64, P->ist64, sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h64, P->ist64, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
     const int w = sync_stream(P);
     if (w != BFCS_OK) return w;
-    r64 = h64->resid_final;
-    if (!std::isfinite(r64)) return BFCS_ERR_DIVERGED;
-    if (r64 <= tol || round >= P->max_rounds || sweeps >= maxit) break;
-    // correction problem: load = the defect (its spectrum is already in place), E = 0, cold start
-    CK(launch_bden<float>((const C2<float>*)P->bhat, g, P->part, P->ist, st));
-    const double tol_c = std::min(0.5, std::max(0.5 * tol / r64, 1e-7));
-    bfcs_info inf{};
-    const int s2 = solve_core<float>(P, phase, tab32, C0, zeroE, tol_c, maxit - sweeps, nullptr,
-                                     SolveOut{eps32, nullptr, u32}, shift, &inf);
+    std::vector<int> next;
+    for (int m : act) {
+      r64[m] = h64[m].resid_final;
+      if (!std::isfinite(r64[m])) { status[m] = BFCS_ERR_DIVERGED; fin[m] = 1; continue; }
+      if (r64[m] <= tol || round >= P->max_rounds || sweeps[m] >= maxit) { fin[m] = 1; continue; }
+      next.push_back(m);
+    }
+    if (next.empty()) break;
+    // correction problems of the unfinished members, packed into slots 0..k-1
+    const int k = (int)next.size();
+    int left = maxit;
+    mem.clear();
+    for (int j = 0; j < k; ++j) {
+      const int m = next[j];
+      if (j != m)   // j < m: slot j's own spectrum is no longer needed
+        CK(cudaMemcpyAsync(bhat32 + (size_t)j * 3 * cs, bhat32 + (size_t)m * 3 * cs, 3 * cs * sizeof(C2<float>),
+                           cudaMemcpyDeviceToDevice, st));
+      const auto sh = shift_of(m);
+      Member c = make_member(in[m].phase, sh.data(), zeroE, nullptr, nullptr, SolveOut{eps32(j), nullptr, u32(j)});
+      c.tol = std::min(0.5, std::max(0.5 * tol / r64[m], P->switch_tol));   // well above the FP32 floor
+      mem.push_back(c);
+      left = std::min(left, maxit - sweeps[m]);
+    }
+    CK(launch_bden<float>(bhat32, g, P->part, P->ist, st, k, 3 * cs));
+    e = upload_members(P, k, mem.data());
+    if (e != BFCS_OK) return e;
+    const int s2 = run_batch<float>(P, k, tab32, C0, zeroE, 0.5, std::max(left, 1), inf.data(), false);
     if (s2 < 0) return s2;
-    sweeps += inf.iters;
-    stalled = inf.stalled;
-    CK(launch_add_f2d(u64, u32, 3 * n, st));
+    for (int j = 0; j < k; ++j) {
+      const int m = next[j];
+      sweeps[m] += inf[j].iters;
+      stalled[m] = inf[j].stalled;
+      CK(launch_add_f2d(u64[m], u32(j), 3 * n, st));
+    }
   }
-  if (out.sig != nullptr)
-    CK(launch_stress((double*)out.sig, eps64, phase, tab64, shift[0], shift[1], shift[2], g.nx, g.ny, g.nz,
-                     st));
+  for (int m = 0; m < B; ++m)
+    if (in[m].sig_out != nullptr)
+      CK(launch_stress((double*)in[m].sig_out, (const double*)in[m].eps_out, in[m].phase, tab64, in[m].sx,
+                       in[m].sy, in[m].sz, g.nx, g.ny, g.nz, st));
   const int w = sync_stream(P);
   if (w != BFCS_OK) return w;
   P->last_iters = 0;     // history of the FP32 phases is not kept across rounds
-  const int status = r64 <= tol ? BFCS_OK : BFCS_NOT_CONVERGED;
-  if (info != nullptr) {
-    info->iters = sweeps;
-    info->status = status;
-    info->resid = r64;
-    info->resid_prev = r_last;
-    info->precision_path = 2;
-    info->stalled = stalled;
+  int worst = BFCS_OK;
+  for (int m = 0; m < B; ++m) {
+    if (status[m] == BFCS_OK && !(r64[m] <= tol)) status[m] = BFCS_NOT_CONVERGED;
+    if (infos != nullptr) {
+      infos[m].iters = sweeps[m];
+      infos[m].status = status[m];
+      infos[m].resid = r64[m];
+      infos[m].resid_prev = r_last[m];
+      infos[m].precision_path = 2;
+      infos[m].stalled = stalled[m];
+    }
+    if (severity(status[m]) > severity(worst)) worst = status[m];
   }
-  return status;
+  return worst;
+}
+
+// One member through the batched ladder.
+int solve_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                const void* b, const double* E, double tol, int maxit, const void* eps_init, SolveOut out,
+                const int shift[3], bfcs_info* info) {
+  if (E == nullptr || out.eps == nullptr || phase == nullptr || b == nullptr) return BFCS_ERR_INVALID_ARG;
+  const Member m = make_member(phase, shift, E, b, eps_init, out);
+  return solve_mixed_batch(P, 1, &m, nph, phases, C0, tol, maxit, info);
 }
 
 int ensure_tmp(bfcs_plan P) {
@@ -1001,10 +1098,10 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   }
   if (P->mixed) {
     ok = cudaMalloc(&P->spec64, 6 * cs * sizeof(C2<double>)) == cudaSuccess &&
-         cudaMalloc(&P->bhat64, 3 * cs * sizeof(C2<double>)) == cudaSuccess &&
-         cudaMalloc(&P->ist64, sizeof(IterState)) == cudaSuccess &&
-         cudaMalloc(&P->r32, 12 * (size_t)P->g.n * sizeof(float)) == cudaSuccess &&
-         cudaMalloc(&P->u64, 3 * (size_t)P->g.n * sizeof(double)) == cudaSuccess;
+         cudaMalloc(&P->bhat64, MB * 3 * cs * sizeof(C2<double>)) == cudaSuccess &&
+         cudaMalloc(&P->ist64, MB * sizeof(IterState)) == cudaSuccess &&
+         cudaMalloc(&P->r32, MB * 12 * (size_t)P->g.n * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&P->u64, MB * 3 * (size_t)P->g.n * sizeof(double)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
     for (int a = 0; a < 3; ++a) {
       P->tw64[a] = make_twiddles<double>(dims[a]);
@@ -1098,16 +1195,21 @@ int bfcs_solve_batched(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, 
     return s;
   }
   int worst = BFCS_OK;
-  for (int m = 0; m < batch; ++m) {     // the ladder runs member by member
-    const auto t1 = std::chrono::steady_clock::now();
-    const SolveOut out{pr[m].eps_out, pr[m].sig_out, pr[m].u_out};
-    bfcs_info inf{};
-    const int s = solve_mixed(P, pr[m].phase, nph, phases, C0, pr[m].b, pr[m].E, tol, maxit, pr[m].eps_init,
-                              out, pr[m].shift, &inf);
-    inf.status = s;
-    inf.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
-    if (infos != nullptr) infos[m] = inf;
+  std::vector<Member> mem;
+  for (int start = 0; start < batch; start += P->max_batch) {   // the ladder, max_batch members at a time
+    const int B = std::min(P->max_batch, batch - start);
+    mem.clear();
+    for (int m = start; m < start + B; ++m)
+      mem.push_back(make_member(pr[m].phase, pr[m].shift, pr[m].E, pr[m].b, pr[m].eps_init,
+                                SolveOut{pr[m].eps_out, pr[m].sig_out, pr[m].u_out}));
+    const int s = solve_mixed_batch(P, B, mem.data(), nph, phases, C0, tol, maxit,
+                                    infos != nullptr ? infos + start : nullptr);
+    if (s < 0) return s;
     if (severity(s) > severity(worst)) worst = s;
+  }
+  if (infos != nullptr) {
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int m = 0; m < batch; ++m) infos[m].ms = ms;
   }
   return worst;
 }

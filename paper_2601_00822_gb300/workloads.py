@@ -169,13 +169,15 @@ def config_c4(seed: int = 1, n: int = 256) -> Problem:
 
 
 def config_c5_sample(seed: int, n: int = 64) -> Problem:
-    """One training sample: one 16^3-cell RSA microstructure of vf ~U[0.1, 0.3],
-    contrast 10, BFCS radius a ~ U[4, 12] at a uniform random voxel corner."""
+    """One training sample: one 16^3-cell RSA microstructure of vf ~U[0.1, 0.3]
+    (addition stops at vf or after 4000 tries: the one-voxel gap jams the
+    packing near vf 0.25), contrast 10, BFCS radius a ~ U[4, 12] at a uniform
+    random voxel corner."""
     rng = SplitMix64(0xC5C5 ^ (seed * 0x9E3779B1))
     vf = 0.1 + 0.2 * rng.uniform()
     a = 4.0 + 8.0 * rng.uniform()
     centre = tuple(float(int(rng.uniform() * n)) for _ in range(3))
-    spheres = rsa_spheres((16, 16, 16), vf, 2.0, 4.0, seed ^ 0x5EED)
+    spheres = rsa_spheres((16, 16, 16), vf, 2.0, 4.0, seed ^ 0x5EED, max_tries=4000)
     phases = [lame_from_young(1.0, 0.3), lame_from_young(10.0, 0.2)]
     return Problem(
         name=f"c5_{n}cubed_seed{seed}", dims=(n, n, n), cell=(16, 16, 16),

@@ -278,6 +278,34 @@ def test_mixed_ladder_goes_below_the_fp32_floor():
         assert rel(u2.cpu().numpy(), u.cpu().numpy()) < 1e-8
 
 
+def test_mixed_batched_equals_individual_and_meets_tolerance():
+    """The batched ladder (FP32 sweeps of all members in one launch per pass,
+    FP64 defects per member) gives each member exactly the individual result;
+    every returned field meets the tolerance by the oracle's own residual."""
+    p = W.config_c1()
+    ph_o, b_o = oracle_inputs(p)
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    init = torch.tensor(O.solve(ph_o, p.phases, p.c0, b_o, tol=0, maxit=5)["eps"], device="cuda")
+    specs = [((0, 0, 0), (0,) * 6, None), ((5, 3, 11), (0.01, 0, 0, 0, 0, 0.002), None),
+             ((0, 0, 0), (0,) * 6, init), ((31, 16, 2), (0, -0.003, 0, 0.001, 0, 0), None),
+             ((7, 7, 7), (0,) * 6, init)]
+    tol = 1e-9
+    with api.Plan(p.dims, "mixed", max_batch=3) as plan, api.Plan(p.dims, "mixed") as single:
+        members = [dict(phase=ph, b=b, E=E, shift=sh, eps_init=ei) for sh, E, ei in specs]
+        members, infos = plan.solve_batched(members, p.phases, p.c0, tol=tol, maxit=4000)
+        for mem, (sh, E, ei), info in zip(members, specs, infos):
+            assert info.status == _lib.OK and info.resid <= tol and info.precision_path == 2
+            (one_m,), (one,) = single.solve_batched([dict(phase=ph, b=b, E=E, shift=sh, eps_init=ei)],
+                                                    p.phases, p.c0, tol=tol, maxit=4000)
+            assert one.iters == info.iters and one.resid == info.resid
+            for key in ("eps_out", "sig_out", "u_out"):
+                assert torch.equal(one_m[key], mem[key]), (sh, key)
+            r = O.residual(O.translate(ph_o, sh), p.phases, mem["eps_out"].cpu().numpy(), O.fft3(b_o),
+                           O.wavevectors(p.dims))
+            assert r <= 2 * tol, (sh, r)
+
+
 def test_mixed_translate_average_against_oracle():
     dims = (16, 16, 16)
     p = small_problem(dims, (8, 8, 8), [[8, 8, 8, 36, 1]], (8.0, 8.0, 8.0), 4.0)
