@@ -189,6 +189,130 @@ __global__ void __launch_bounds__(kConvWarps * 32) k_conv(ConvArgs a) {
   }
 }
 
+// Tiled 3^3 convolution (IN_CONV, OUT_BF16): a block computes a 16 x 8 x 2
+// voxel tile for 32 output columns.  The tile's circular halo (18 x 10 x 4
+// voxels, all cin channels) is staged once in shared memory with cp.async;
+// A fragments come from it by ldmatrix (rows = 16 consecutive x voxels, one
+// 16-byte chunk of 8 channels per row).  Chunk c of halo voxel v sits at
+// chunk c ^ ((v >> sh) & (chunks - 1)): 8 consecutive voxels then hit 8
+// distinct 16-byte bank groups (conflict-free ldmatrix) for cin = 16, 32, 64.
+// B fragments (weights, at most 110 KB per layer) are read from L1/L2.
+// Needs nx % 16 == 0, ny % 8 == 0, nz % 2 == 0, cin in {16, 32, 64}, ldi and
+// offi multiples of 8.
+constexpr int kTX = 16, kTY = 8, kTZ = 2;
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2, kHalo = kHX * kHY * kHZ;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
+}
+__device__ __forceinline__ void ldsm_x4(unsigned* r, unsigned saddr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(saddr));
+}
+
+size_t conv3t_smem(int cin) { return (size_t)kHalo * cin * sizeof(bf16); }
+
+__global__ void __launch_bounds__(128) k_conv3t(ConvArgs a) {
+  extern __shared__ __align__(128) unsigned char smh[];
+  const int chunks = a.cin >> 3;
+  const int sh = chunks == 8 ? 0 : chunks == 4 ? 1 : 2;
+  const int rowb = a.cin * 2;
+  const int ntx = a.v.nx / kTX, nty = a.v.ny / kTY;
+  int tb = blockIdx.x;
+  const int x0 = (tb % ntx) * kTX;
+  tb /= ntx;
+  const int y0 = (tb % nty) * kTY, z0 = (tb / nty) * kTZ;
+  const int b = blockIdx.z;
+  const long long nvox = (long long)a.v.nx * a.v.ny * a.v.nz;
+  const bf16* inb = a.in + (long long)b * nvox * a.ldi + a.offi;
+  for (int i = threadIdx.x; i < kHalo * chunks; i += blockDim.x) {
+    const int v = i / chunks, c = i - v * chunks;
+    const int hx = v % kHX, hy = (v / kHX) % kHY, hz = v / (kHX * kHY);
+    const int gx = wrap(x0 + hx - 1, a.v.nx), gy = wrap(y0 + hy - 1, a.v.ny), gz = wrap(z0 + hz - 1, a.v.nz);
+    const bf16* src = inb + (((long long)gz * a.v.ny + gy) * a.v.nx + gx) * a.ldi + c * 8;
+    cp_async16(smh + v * rowb + 16 * (c ^ ((v >> sh) & (chunks - 1))), src);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int col0 = blockIdx.y * 32;
+  const int ntiles = min(4, (a.cout_p - col0) / 8);
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  int rowv[4];   // halo index of x = 0 of this warp's tile rows, plus the ldmatrix row of this lane
+  const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lk = lane >> 4;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = warp * 4 + q;
+    rowv[q] = ((r / kTY + 1) * kHY + (r % kTY + 1)) * kHX + 1 + lrow;
+  }
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(smh);
+  for (int tap = 0; tap < 27; ++tap) {
+    const int doff = ((tap / 9 - 1) * kHY + ((tap / 3) % 3 - 1)) * kHX + (tap % 3 - 1);
+    const bf16* wt = a.w + (long long)tap * a.cout_p * a.cin + (long long)(col0 + g) * a.cin + 2 * t;
+    for (int kc = 0; kc < a.cin; kc += 16) {
+      const int c = (kc >> 3) + lk;
+      unsigned af[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int v = rowv[q] + doff;
+        ldsm_x4(af[q], sbase + v * rowb + 16 * (c ^ ((v >> sh) & (chunks - 1))));
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j < ntiles) {
+          const bf16* wr = wt + (long long)j * 8 * a.cin + kc;
+          const unsigned bfr[2] = {ld32(wr), ld32(wr + 8)};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) mma16816(acc[q][j], af[q], bfr);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = warp * 4 + q;
+    const int y = y0 + r % kTY, z = z0 + r / kTY;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long vox = ((long long)z * a.v.ny + y) * a.v.nx + x0 + g + 8 * h;
+      bf16* orow = (bf16*)a.out + ((long long)b * nvox + vox) * a.ldo + a.offo;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j >= ntiles) continue;
+        const int col = col0 + j * 8 + 2 * t;
+        float v0 = acc[q][j][2 * h], v1 = acc[q][j][2 * h + 1];
+        if (a.bias != nullptr) {
+          v0 += a.bias[col % a.bias_mod];
+          v1 += a.bias[(col + 1) % a.bias_mod];
+        }
+        if (a.act) {
+          v0 = v0 > 0.f ? v0 : kSlope * v0;
+          v1 = v1 > 0.f ? v1 : kSlope * v1;
+        }
+        *reinterpret_cast<__nv_bfloat162*>(orow + col) = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+  }
+}
+
+bool conv3t_ok(const ConvArgs& a) {
+  return a.ksize == 3 && a.in_mode == IN_CONV && a.out_mode == OUT_BF16 && a.v.nx % kTX == 0 &&
+         a.v.ny % kTY == 0 && a.v.nz % kTZ == 0 && (a.cin == 16 || a.cin == 32 || a.cin == 64) &&
+         a.ldi % 8 == 0 && a.offi % 8 == 0 && a.cout_p % 8 == 0;
+}
+
 // ------------------------------------------------------------------ weight gradient
 // dW[tap][co][ci] = sum over (b, v) of dY[b][v][co] X[b][v + d_tap][ci]; for an
 // up-convolution (up_c > 0) dW[o up_c + co][ci] = sum over (b, u) of
@@ -312,6 +436,126 @@ __global__ void __launch_bounds__(128) k_wgrad(WgArgs a) {
       }
     }
   }
+}
+
+// Tiled weight gradient of a 3^3 convolution with 32 output channels:
+// block (i, s) walks voxel tiles i, i + gridDim.x, ... (16 x 8 x 2 voxels of
+// one sample); per tile it stages dY (256 x 32, row pitch 40 elements:
+// conflict-free ldmatrix.trans) and the circular halo of X for the input
+// channels [32 s, 32 s + 32) (swizzled as in k_conv3t), then warp w
+// accumulates the taps 3w .. 3w + 2 in registers: dW[tap] += dY^T X_shifted,
+// K = the 16 voxels of one tile row per step.  partial[i][tap][co][ci] FP32.
+// Needs cout_p == 32, the tiled grid, cin in {16, 32, 64}.
+constexpr int kWgtWarps = 9, kWgtDP = 40;
+
+size_t wgrad3t_smem(int cin) {
+  return (size_t)kTX * kTY * kTZ * kWgtDP * sizeof(bf16) + (size_t)kHalo * (cin < 32 ? cin : 32) * sizeof(bf16);
+}
+
+__global__ void __launch_bounds__(kWgtWarps * 32) k_wgrad3t(WgArgs a) {
+  extern __shared__ __align__(128) unsigned char smw[];
+  const int cs = min(a.cin, 32);
+  const int c0 = blockIdx.y * cs;
+  const int chunks = cs >> 3;
+  const int sh = chunks == 4 ? 1 : 2;
+  const int rowb = cs * 2;
+  bf16* sD = reinterpret_cast<bf16*>(smw);
+  unsigned char* sX = smw + kTX * kTY * kTZ * kWgtDP * sizeof(bf16);
+  const unsigned sXb = (unsigned)__cvta_generic_to_shared(sX);
+  const int ntx = a.v.nx / kTX, nty = a.v.ny / kTY, ntz = a.v.nz / kTZ;
+  const int per_sample = ntx * nty * ntz;
+  const long long nvox = (long long)a.v.nx * a.v.ny * a.v.nz;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mi = lane >> 3, rr = lane & 7;
+  const int tap0 = warp * 3;
+  const int np = cs / 16;     // n16 pairs
+  float acc[3][2][4][4];
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[u][i][j][q] = 0.f;
+  for (int tile = blockIdx.x; tile < per_sample * a.batch; tile += gridDim.x) {
+    const int b = tile / per_sample;
+    int tb = tile - b * per_sample;
+    const int x0 = (tb % ntx) * kTX;
+    tb /= ntx;
+    const int y0 = (tb % nty) * kTY, z0 = (tb / nty) * kTZ;
+    __syncthreads();   // the previous tile's shared-memory reads are done
+    for (int i = threadIdx.x; i < kTX * kTY * kTZ * 4; i += blockDim.x) {
+      const int v = i >> 2, c = i & 3;
+      const long long vox = ((long long)(z0 + v / (kTX * kTY)) * a.v.ny + y0 + (v / kTX) % kTY) * a.v.nx + x0 + v % kTX;
+      cp_async16(sD + v * kWgtDP + c * 8, a.dy + ((long long)b * nvox + vox) * a.ldd + a.offd + c * 8);
+    }
+    for (int i = threadIdx.x; i < kHalo * chunks; i += blockDim.x) {
+      const int v = i / chunks, c = i - v * chunks;
+      const int hx = v % kHX, hy = (v / kHX) % kHY, hz = v / (kHX * kHY);
+      const int gx = wrap(x0 + hx - 1, a.v.nx), gy = wrap(y0 + hy - 1, a.v.ny), gz = wrap(z0 + hz - 1, a.v.nz);
+      const bf16* src = a.x + ((long long)b * nvox + ((long long)gz * a.v.ny + gy) * a.v.nx + gx) * a.ldx + a.offx +
+                        c0 + c * 8;
+      cp_async16(sX + v * rowb + 16 * (c ^ ((v >> sh) & (chunks - 1))), src);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (tap0 >= 27) continue;
+    for (int r = 0; r < kTY * kTZ; ++r) {
+      const int yy = r % kTY, zz = r / kTY;
+      unsigned af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+        ldsm_x4_trans(af[i], sD + (r * kTX + (mi >> 1) * 8 + rr) * kWgtDP + i * 16 + (mi & 1) * 8);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int tap = tap0 + u;
+        const int hv0 = ((zz + 1 + tap / 9 - 1) * kHY + (yy + 1 + (tap / 3) % 3 - 1)) * kHX + 1 + (tap % 3 - 1) +
+                        (mi & 1) * 8 + rr;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          if (p < np) {
+            const int ch = 2 * p + (mi >> 1);
+            unsigned bq[4];
+            const unsigned addr = sXb + hv0 * rowb + 16 * (ch ^ ((hv0 >> sh) & (chunks - 1)));
+            asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                         : "=r"(bq[0]), "=r"(bq[1]), "=r"(bq[2]), "=r"(bq[3])
+                         : "r"(addr));
+            const unsigned b0[2] = {bq[0], bq[1]};
+            const unsigned b1[2] = {bq[2], bq[3]};
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              mma16816(acc[u][i][2 * p], af[i], b0);
+              mma16816(acc[u][i][2 * p + 1], af[i], b1);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (tap0 >= 27) return;
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    float* out = a.part + ((long long)blockIdx.x * 27 + tap0 + u) * 32 * a.cin + c0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j >= 2 * np) continue;
+        const int co = i * 16 + g, ci = j * 8 + 2 * t;
+        out[(long long)co * a.cin + ci] = acc[u][i][j][0];
+        out[(long long)co * a.cin + ci + 1] = acc[u][i][j][1];
+        out[(long long)(co + 8) * a.cin + ci] = acc[u][i][j][2];
+        out[(long long)(co + 8) * a.cin + ci + 1] = acc[u][i][j][3];
+      }
+  }
+}
+
+bool wgrad3t_ok(const WgArgs& a) {
+  return a.ksize == 3 && a.up_c == 0 && a.cout_p == 32 && a.v.nx % kTX == 0 && a.v.ny % kTY == 0 &&
+         a.v.nz % kTZ == 0 && (a.cin == 16 || a.cin == 32 || a.cin == 64) && a.ldd % 8 == 0 && a.offd % 8 == 0 &&
+         a.ldx % 8 == 0 && a.offx % 8 == 0;
 }
 
 // out[i] = sum over c (in order) of part[c * per + i]
@@ -667,6 +911,18 @@ cudaError_t pack_all(bfcs_net_s* N, const float* params) {
 }
 
 // forward GEMM of layer l: in -> out on the grid of level lv (coarse level for an up layer)
+cudaError_t launch_conv(const ConvArgs& a, long long nvox, cudaStream_t st) {
+  if (conv3t_ok(a)) {
+    const int tiles = (a.v.nx / kTX) * (a.v.ny / kTY) * (a.v.nz / kTZ);
+    k_conv3t<<<dim3(tiles, ceil_div(a.cout_p, 32), a.batch), 128, conv3t_smem(a.cin), st>>>(a);
+  } else {
+    k_conv<<<dim3(ceil_div(nvox, kConvWarps * 32), ceil_div(a.cout_p, kConvNT * 8), a.batch), kConvWarps * 32, 0,
+             st>>>(a);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t conv_fwd(bfcs_net_s* N, int l, const float* params, int B, View in, int lv, int out_mode, void* out,
                      int ldo, int offo) {
   const LayerDef& L = N->def[l];
@@ -686,10 +942,7 @@ cudaError_t conv_fwd(bfcs_net_s* N, int l, const float* params, int B, View in, 
   a.out_mode = out_mode;
   a.out = out; a.ldo = ldo; a.offo = offo;
   a.up_c = L.cout;
-  dim3 grid(ceil_div(N->n[lv], kConvWarps * 32), ceil_div(a.cout_p, kConvNT * 8), B);
-  k_conv<<<grid, kConvWarps * 32, 0, N->st>>>(a);
-  count_launches(1);
-  return cudaGetLastError();
+  return launch_conv(a, N->n[lv], N->st);
 }
 
 cudaError_t pool(bfcs_net_s* N, View in, View out, int C, int coarse_lv, int B) {
@@ -764,9 +1017,16 @@ cudaError_t layer_bwd(bfcs_net_s* N, int l, int B, View dout, View out, View in,
   const int nblk = std::max(1, std::min(1024, ceil_div(orows, 512)));
   if ((long long)nchunks * per + (long long)nblk * bc > N->part_cap) return cudaErrorInvalidValue;
   w.part = N->part;
-  const int mcols = std::min(64, w.cout_p);
-  const size_t smem = (size_t)kWgRows * (mcols + 8 + w.cin + 8) * sizeof(bf16);
-  k_wgrad<<<dim3(nchunks, taps * mchunks), 128, smem, N->st>>>(w);
+  if (wgrad3t_ok(w)) {
+    const long long tiles = (long long)(w.v.nx / kTX) * (w.v.ny / kTY) * (w.v.nz / kTZ) * B;
+    nchunks = (int)std::min<long long>(tiles, 152);
+    if ((long long)nchunks * per + (long long)nblk * bc > N->part_cap) return cudaErrorInvalidValue;
+    k_wgrad3t<<<dim3(nchunks, w.cin > 32 ? w.cin / 32 : 1), kWgtWarps * 32, wgrad3t_smem(w.cin), N->st>>>(w);
+  } else {
+    const int mcols = std::min(64, w.cout_p);
+    const size_t smem = (size_t)kWgRows * (mcols + 8 + w.cin + 8) * sizeof(bf16);
+    k_wgrad<<<dim3(nchunks, taps * mchunks), 128, smem, N->st>>>(w);
+  }
   k_sum_chunks<<<grid_for(per), 256, 0, N->st>>>(N->part, nchunks, per, N->gw[l]);
   // bias gradient (over the rows of the output gradient)
   const long long bper = (orows + nblk - 1) / nblk;
@@ -790,9 +1050,8 @@ cudaError_t layer_bwd(bfcs_net_s* N, int l, int B, View dout, View out, View in,
     a.out_mode = OUT_BF16;
     a.out = din.p; a.ldo = din.ld; a.offo = din.off;
     a.up_c = L.cout;
-    dim3 grid(ceil_div(N->n[lv], kConvWarps * 32), ceil_div(a.cout_p, kConvNT * 8), B);
-    k_conv<<<grid, kConvWarps * 32, 0, N->st>>>(a);
-    count_launches(1);
+    const cudaError_t e = launch_conv(a, N->n[lv], N->st);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -949,7 +1208,7 @@ int bfcs_net_create(bfcs_net* out, int nx, int ny, int nz, int max_batch, int fl
       const long long per = taps * (L.kind == 2 ? 8 * L.cout : L.cout_p) * L.cin_p;
       const long long mch = L.kind == 2 ? 8 * L.cout / 64 : 1;
       const long long nch = std::max<long long>(1, ceil_div(152 * 8, taps * mch));
-      N->part_cap = std::max(N->part_cap, nch * per + 1024LL * 64);
+      N->part_cap = std::max(N->part_cap, std::max(nch, 152LL) * per + 1024LL * 64);
     }
     add(&N->part, (size_t)N->part_cap * sizeof(float));
   }
@@ -964,6 +1223,14 @@ int bfcs_net_create(bfcs_net* out, int nx, int ny, int nz, int max_batch, int fl
   for (auto& r : req) {
     *r.first = N->base + pos;
     pos += (r.second + 255) / 256 * 256;
+  }
+  if (cudaFuncSetAttribute(k_conv3t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv3t_smem(64)) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_wgrad3t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad3t_smem(64)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    free_net(N);
+    return BFCS_ERR_CUDA;
   }
   // zero everything once: padded input channels stay zero
   if (cudaMemsetAsync(N->base, 0, total, N->st) != cudaSuccess) { free_net(N); return BFCS_ERR_CUDA; }

@@ -42,7 +42,7 @@ def sample_inputs(seed, n, precision="fp64"):
     return ph, b
 
 
-def generate(seeds, n, solve_batch=64, tol=1e-5, maxit=5000, log=print):
+def generate(seeds, n, solve_batch=64, tol=1e-4, maxit=5000, log=print):
     """Solver-generated training pairs: X (S, 4, n, n, n) and T (S, 6, n, n, n),
     float32 on the device (FP32 batched solves to tol)."""
     phases, c0 = material()
@@ -92,9 +92,9 @@ LAYERS = (("conv3", 4, 32), ("conv3", 32, 32), ("conv3", 32, 32), ("conv3", 32, 
           ("conv3", 64, 32), ("conv3", 32, 32), ("conv1", 32, 6))
 
 
-def train(X, T, steps, batch=8, lr=2e-3, seed=0, params=None, log=print, log_every=200):
-    """Adam with a cosine learning-rate decay over contiguous minibatches of a
-    shuffled-once sample order; returns (params, losses)."""
+def train(X, T, steps, batch=8, lr=1e-3, seed=0, params=None, log=print, log_every=200, warmup=300):
+    """Adam with a linear warm-up and a cosine learning-rate decay over
+    contiguous minibatches of a shuffled-once sample order; returns (params, losses)."""
     S = X.shape[0]
     dims = tuple(X.shape[2:][::-1])
     net = api.Net(dims, max_batch=batch, train=True)
@@ -108,7 +108,7 @@ def train(X, T, steps, batch=8, lr=2e-3, seed=0, params=None, log=print, log_eve
     t0 = time.time()
     for t in range(1, steps + 1):
         i = ((t - 1) % nb) * batch
-        lr_t = lr * 0.5 * (1 + math.cos(math.pi * (t - 1) / steps))
+        lr_t = lr * min(1.0, t / max(warmup, 1)) * 0.5 * (1 + math.cos(math.pi * (t - 1) / steps))
         net.train_step(params, grad, m, v, t, lr_t, X[i:i + batch], T[i:i + batch], loss=loss)
         if t % log_every == 0 or t == steps:
             losses.append((t, float(loss.item())))
@@ -212,7 +212,7 @@ def main(argv=None):
     t.add_argument("--grid", type=int, default=64)
     t.add_argument("--steps", type=int, default=6000)
     t.add_argument("--batch", type=int, default=8)
-    t.add_argument("--lr", type=float, default=2e-3)
+    t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--out", default=DEFAULT_WEIGHTS)
     t.add_argument("--log", default=None)
     b = sub.add_parser("bench")
