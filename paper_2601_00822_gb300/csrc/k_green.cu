@@ -248,6 +248,14 @@ template <typename R>
 __global__ void k_defect(DArgs<R> a) {
   __shared__ double red[32];
   const Geo g = a.g;
+  {
+    const int j = blockIdx.y, m = a.idx[j];
+    a.spec += j * a.spec_ms;
+    a.part += j * gridDim.x;
+    a.bhat += m * a.b_ms;
+    a.out32 += m * a.o_ms;
+    a.st += m;
+  }
   const long long modes = (long long)g.nz * g.ny * g.mx;
   const R two_pi = R(6.283185307179586);
   double acc = 0.0;
@@ -298,14 +306,17 @@ __global__ void k_defect(DArgs<R> a) {
 }
 
 template <typename R>
-cudaError_t launch_defect(const DArgs<R>& a, int blocks, cudaStream_t st) {
-  k_defect<R><<<blocks, 256, 0, st>>>(a);
+cudaError_t launch_defect(const DArgs<R>& a, int blocks, int batch, cudaStream_t st) {
+  k_defect<R><<<dim3(blocks, batch), 256, 0, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename R>
-__global__ void k_symgrad(C2<R>* spec, Geo g, R inv_n, R E0, R E1, R E2, R E3, R E4, R E5) {
+__global__ void k_symgrad(C2<R>* spec, long long ms, Geo g, R inv_n, const Member* mem) {
+  spec += blockIdx.y * ms;
+  const double* E = mem[blockIdx.y].E;
+  const R E0 = (R)E[0], E1 = (R)E[1], E2 = (R)E[2], E3 = (R)E[3], E4 = (R)E[4], E5 = (R)E[5];
   const long long modes = (long long)g.nz * g.ny * g.mx;
   const R two_pi = R(6.283185307179586);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
@@ -340,57 +351,12 @@ __global__ void k_symgrad(C2<R>* spec, Geo g, R inv_n, R E0, R E1, R E2, R E3, R
 }
 
 template <typename R>
-cudaError_t launch_symgrad(C2<R>* spec, const Geo& g, const double* E, cudaStream_t st) {
-  k_symgrad<R><<<4 * 152, 256, 0, st>>>(spec, g, R(1.0 / (double)g.n), (R)E[0], (R)E[1], (R)E[2], (R)E[3],
-                                         (R)E[4], (R)E[5]);
+cudaError_t launch_symgrad(C2<R>* spec, long long ms, const Geo& g, const Member* mem, int batch, cudaStream_t st) {
+  k_symgrad<R><<<dim3(4 * 152, batch), 256, 0, st>>>(spec, ms, g, R(1.0 / (double)g.n), mem);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template <typename R>
-__global__ void k_disp(C2<R>* spec, Geo g, R inv_n, R lam0, R mu0) {
-  const long long modes = (long long)g.nz * g.ny * g.mx;
-  const R two_pi = R(6.283185307179586);
-  const R c0 = (lam0 + mu0) / (lam0 + R(2) * mu0);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % g.mx);
-    const long long r = i / g.mx;
-    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
-    C2<R>* sp = spec + r * g.p + kx;
-    R xi[3];
-    xi[0] = two_pi / R(g.nx) * R(signed_k(kx, g.nx));
-    xi[1] = two_pi / R(g.ny) * R(signed_k(ky, g.ny));
-    xi[2] = two_pi / R(g.nz) * R(signed_k(kz, g.nz));
-    const R q = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
-    C2<R> u[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
-    if (q != R(0)) {
-      const C2<R> e0 = sp[0], e1 = sp[g.cs], e2 = sp[2 * g.cs], e3 = sp[3 * g.cs], e4 = sp[4 * g.cs],
-                  e5 = sp[5 * g.cs];
-      const C2<R> tr = scale(e0 + e1 + e2, lam0);
-      const R m2 = R(2) * mu0;
-      // w = (C0 eps_hat) xi
-      C2<R> w[3];
-      w[0] = scale(tr, xi[0]) + scale(scale(e0, xi[0]) + scale(e5, xi[1]) + scale(e4, xi[2]), m2);
-      w[1] = scale(tr, xi[1]) + scale(scale(e5, xi[0]) + scale(e1, xi[1]) + scale(e3, xi[2]), m2);
-      w[2] = scale(tr, xi[2]) + scale(scale(e4, xi[0]) + scale(e3, xi[1]) + scale(e2, xi[2]), m2);
-      C2<R> v[3];
-      g0_apply<R>(w, xi, q, mu0, c0, v);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) u[k] = mk<R>(v[k].y * inv_n, -v[k].x * inv_n);   // -i v / N
-    }
-    sp[0] = u[0];
-    sp[g.cs] = u[1];
-    sp[2 * g.cs] = u[2];
-  }
-}
-
-template <typename R>
-cudaError_t launch_disp(C2<R>* spec, const Geo& g, double lam0, double mu0, cudaStream_t st) {
-  k_disp<R><<<4 * 152, 256, 0, st>>>(spec, g, R(1.0 / (double)g.n), (R)lam0, (R)mu0);
-  count_launches(1);
-  return cudaGetLastError();
-}
 
 template <typename R>
 int green_nparts(const Geo& g) {
@@ -426,8 +392,7 @@ cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t st) { return launch_zg
 template cudaError_t launch_zgreen<BFCS_R>(const GArgs<BFCS_R>&, cudaStream_t);
 template cudaError_t launch_zgreen_b<BFCS_R>(const GArgs<BFCS_R>&, int, cudaStream_t);
 template int green_nparts<BFCS_R>(const Geo&);
-template cudaError_t launch_defect<BFCS_R>(const DArgs<BFCS_R>&, int, cudaStream_t);
-template cudaError_t launch_symgrad<BFCS_R>(C2<BFCS_R>*, const Geo&, const double*, cudaStream_t);
-template cudaError_t launch_disp<BFCS_R>(C2<BFCS_R>*, const Geo&, double, double, cudaStream_t);
+template cudaError_t launch_defect<BFCS_R>(const DArgs<BFCS_R>&, int, int, cudaStream_t);
+template cudaError_t launch_symgrad<BFCS_R>(C2<BFCS_R>*, long long, const Geo&, const Member*, int, cudaStream_t);
 
 }  // namespace bfcs

@@ -339,6 +339,33 @@ cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st
   return cudaGetLastError();
 }
 
+struct SlotIdx { int idx[kMaxBatch]; };
+
+__global__ void k_defect_final(const ResidSlot* part, int nparts, IterState* sts, SlotIdx si, int maxdim) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  part += j * nparts;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i].num;
+  const double t = block_sum(acc, red);
+  if (threadIdx.x != 0) return;
+  IterState* st = sts + si.idx[j];
+  const double* s0 = st->tau0;
+  const double s0n = sqrt(s0[0] * s0[0] + s0[1] * s0[1] + s0[2] * s0[2] +
+                          2.0 * (s0[3] * s0[3] + s0[4] * s0[4] + s0[5] * s0[5]));
+  const double den = st->bden + 6.283185307179586 / (double)maxdim * s0n;
+  st->resid_final = den > 0.0 ? sqrt(t) / den : sqrt(t);
+}
+
+cudaError_t launch_defect_final(const ResidSlot* part, int nparts, IterState* st, const int* idx_host, int batch,
+                                int maxdim, cudaStream_t s) {
+  SlotIdx si{};
+  for (int j = 0; j < batch; ++j) si.idx[j] = idx_host[j];
+  k_defect_final<<<batch, kRedThreads, 0, s>>>(part, nparts, st, si, maxdim);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- a10: translated averaging
 // acc layout (30 x N, FP64): <u> 3, <u>^(1) 3, <eps> 6, <eps>^(1) 6, <sigma> 6, <sigma>^(1) 6.
 template <typename R>

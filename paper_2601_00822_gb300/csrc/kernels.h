@@ -98,6 +98,8 @@ template <typename R> struct GArgs {
 // R_hat = i xi . sigma_hat + b_hat on modes with xi != 0 (0 elsewhere), written
 // as complex64 to out32; per-block partial sums of w |R_hat|^2; sigma_hat(0)
 // (6 values) into st->tau0.
+// Batched over slots (blockIdx.y): slot j works on member idx[j]; spec and part
+// are slot-major, bhat, out32 and st member-major.
 template <typename R> struct DArgs {
   const C2<R>* spec;      // 6 components: sigma_hat
   const C2<R>* bhat;      // 3 components
@@ -105,19 +107,22 @@ template <typename R> struct DArgs {
   Geo g;
   ResidSlot* part;
   IterState* st;
+  long long spec_ms, b_ms, o_ms;   // member strides (elements)
+  int idx[kMaxBatch];
 };
 
 // eps_hat = sym(i xi (x) u_hat) / N on modes with xi != 0, E at k = 0, 0 on the
 // other xi = 0 modes: components 0..2 of `spec` (u_hat, fully transformed) in,
 // components 0..5 out, in place.
-template <typename R> cudaError_t launch_symgrad(C2<R>* spec, const Geo& g, const double* E, cudaStream_t s);
-// u_hat = -i G0(xi) (C0 eps_hat) xi / N on modes with xi != 0, else 0: the
-// displacement whose symmetric gradient is the compatible part of eps (in the
-// C0 energy norm); components 0..5 in, 0..2 out, in place.
-template <typename R> cudaError_t launch_disp(C2<R>* spec, const Geo& g, double lam0, double mu0, cudaStream_t s);
+template <typename R> cudaError_t launch_symgrad(C2<R>* spec, long long ms, const Geo& g, const Member* mem, int batch,
+                                                 cudaStream_t s);
 
 template <typename R> cudaError_t launch_xpass(const XArgs<R>& a, cudaStream_t s);
-template <typename R> cudaError_t launch_defect(const DArgs<R>& a, int blocks, cudaStream_t s);
+template <typename R> cudaError_t launch_defect(const DArgs<R>& a, int blocks, int batch, cudaStream_t s);
+// r(eps64) of slot j's member idx[j] from its defect partials (Eq. 5.11 reading):
+// st[idx[j]].resid_final = sqrt(sum part) / (bden + 2 pi / maxdim |sigma_hat(0)|_F).
+cudaError_t launch_defect_final(const ResidSlot* part, int nparts, IterState* st, const int* idx_host, int batch,
+                                int maxdim, cudaStream_t s);
 template <typename R> cudaError_t launch_colpass(const CArgs<R>& a, int dir, cudaStream_t s);
 template <typename R> cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t s);
 template <typename R> int green_nparts(const Geo& g);

@@ -57,7 +57,7 @@ struct bfcs_plan_s {
   long long prof_launches = 0;
   double prof_ms = 0.0;
   // precision ladder (BFCS_MIXED): FP64 transform workspace and FP32 real scratch
-  void* spec64 = nullptr;          // 6 x cs complex128
+  void* spec64 = nullptr;          // max_batch x 6 x cs complex128
   void* bhat64 = nullptr;          // max_batch x 3 x cs complex128: FP64 load spectra
   void* tw64[3] = {nullptr, nullptr, nullptr};
   IterState* ist64 = nullptr;      // max_batch FP64 residual states
@@ -668,95 +668,74 @@ int solve_batch_impl(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, co
   return worst;
 }
 
-// FP64 strain and defect from the FP64 displacement (precision ladder), member
-// slot m: eps64 = E + sym grad u64 (spectral, exactly compatible), then
-// sigma = L eps64, its transform, R_hat = i xi . sigma_hat + b_hat64[m], the
-// FP64 residual r(eps64) into ist64[m].resid_final, and R_hat rounded to
-// complex64 into `out32` (the load of the correction problem, already
-// transformed).  eps64 is written to `eps_out`.  Needs b_hat64[m] and
-// ist64[m].bden.
-int defect64(bfcs_plan P, int m, const int8_t* phase, const PhaseTab<double>& tab, bfcs_lame C0,
-             const double* E, const double* u64, double* eps_out, const int shift[3], C2<float>* out32) {
+// FP64 strain and defect from the FP64 displacements (precision ladder) of k
+// members in one launch per pass.  Slot j holds member idx[j]; dm[j] (host)
+// carries its phase, shift, E, the displacement u64 (as `b`, the real input
+// of the x transform) and eps_out.  eps64 = E + sym grad u64 (spectral,
+// exactly compatible), sigma = L eps64, its transform, R_hat = i xi .
+// sigma_hat + b_hat64[m], the FP64 residual r(eps64) into
+// ist64[m].resid_final, and R_hat rounded to complex64 into the member's FP32
+// load spectrum (slot m of the plan's b_hat: the load of its correction
+// problem, already transformed).  eps64 goes to eps_out.
+int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTab<double>& tab) {
   const Geo g = P->g;
   cudaStream_t st = P->st;
+  const long long sms = 6 * g.cs;
   C2<double>* spec = (C2<double>*)P->spec64;
-  int e = transform_into<double>(P, u64, spec, P->tw64);            // u_hat (3 components)
+  int e = upload_members(P, k, dm);
   if (e != BFCS_OK) return e;
-  CK(launch_symgrad<double>(spec, g, E, st));                        // eps_hat / N (6 components)
-  CArgs<double> ca{};
-  ca.data = spec;
-  ca.g = g;
-  ca.ncomp = 6;
-  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
-  CK(launch_colpass<double>(ca, +1, st));
-  ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
-  CK(launch_colpass<double>(ca, +1, st));
-  XArgs<double> xa{};                                                // eps out, sigma = L eps, R2C
+  XArgs<double> xa{};                                                // u_hat, x direction
   xa.g = g;
-  xa.spec_in = spec;
   xa.spec_out = spec;
-  xa.eps_out = eps_out;
-  xa.phase = phase;
-  xa.sx = shift[0]; xa.sy = shift[1]; xa.sz = shift[2];
-  xa.tab = tab;
-  xa.tw = (const C2<double>*)P->tw64[0];
-  xa.ncomp = 6;
-  xa.mode = XM_SWEEPSIG;
-  CK(launch_xpass<double>(xa, st));
-  CK(launch_colpass<double>(ca, -1, st));                            // y forward
-  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
-  CK(launch_colpass<double>(ca, -1, st));                            // z forward
-  DArgs<double> da{};
-  da.spec = spec;
-  da.bhat = (const C2<double>*)P->bhat64 + (size_t)m * 3 * g.cs;
-  da.out32 = out32;
-  da.g = g;
-  da.part = P->part;
-  da.st = P->ist64 + m;
-  const int blocks = 512;
-  CK(launch_defect<double>(da, blocks, st));
-  const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
-  CK(launch_resid_reduce(P->part, blocks, P->ist64 + m, nullptr, nullptr, 0, 0.0, C0.lambda, C0.mu, E, g.n,
-                         maxdim, kReduceDefect, 0, 0, 1, st));
-  return BFCS_OK;
-}
-
-// Warm start of the ladder in FP64: u64 = the displacement of the compatible
-// part of eps_init, u_hat = -i G0(xi) (C0 eps_hat) xi (the strain's
-// incompatible part and its mean are dropped; E is imposed by the defect step).
-int warm_disp64(bfcs_plan P, const void* eps_init, double* u64, bfcs_lame C0) {
-  const Geo g = P->g;
-  cudaStream_t st = P->st;
-  C2<double>* spec = (C2<double>*)P->spec64;
-  XArgs<double> xa{};
-  xa.g = g;
-  xa.real_in = (const double*)eps_init;
-  xa.spec_out = spec;
-  xa.ncomp = 6;
+  xa.spec_ms = sms;
+  fill_xm(xa, dm, k, XIN_B, 0);
+  xa.ncomp = 3;
   xa.mode = XM_R2C;
   xa.tw = (const C2<double>*)P->tw64[0];
-  CK(launch_xpass<double>(xa, st));
+  CK(launch_xpass_b<double>(xa, k, st));
   CArgs<double> ca{};
   ca.data = spec;
+  ca.ms = sms;
   ca.g = g;
-  ca.ncomp = 6;
-  ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
-  CK(launch_colpass<double>(ca, -1, st));
-  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
-  CK(launch_colpass<double>(ca, -1, st));
-  CK(launch_disp<double>(spec, g, C0.lambda, C0.mu, st));
   ca.ncomp = 3;
-  CK(launch_colpass<double>(ca, +1, st));
   ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
-  CK(launch_colpass<double>(ca, +1, st));
-  XArgs<double> xc{};
-  xc.g = g;
-  xc.spec_in = spec;
-  xc.real_out = u64;
-  xc.ncomp = 3;
-  xc.mode = XM_C2R;
-  xc.tw = (const C2<double>*)P->tw64[0];
-  CK(launch_xpass<double>(xc, st));
+  CK(launch_colpass_b<double>(ca, -1, k, st));
+  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
+  CK(launch_colpass_b<double>(ca, -1, k, st));
+  CK(launch_symgrad<double>(spec, sms, g, P->mem_dev, k, st));     // eps_hat / N (6 components)
+  ca.ncomp = 6;
+  CK(launch_colpass_b<double>(ca, +1, k, st));                      // z inverse
+  ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
+  CK(launch_colpass_b<double>(ca, +1, k, st));                      // y inverse
+  XArgs<double> xs{};                                                // eps out, sigma = L eps, R2C
+  xs.g = g;
+  xs.spec_in = spec;
+  xs.spec_out = spec;
+  xs.spec_ms = sms;
+  fill_xm(xs, dm, k, XIN_NONE, XOUT_EPS);
+  xs.tab = tab;
+  xs.tw = (const C2<double>*)P->tw64[0];
+  xs.ncomp = 6;
+  xs.mode = XM_SWEEPSIG;
+  CK(launch_xpass_b<double>(xs, k, st));
+  CK(launch_colpass_b<double>(ca, -1, k, st));                      // y forward
+  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
+  CK(launch_colpass_b<double>(ca, -1, k, st));                      // z forward
+  DArgs<double> da{};
+  da.spec = spec;
+  da.spec_ms = sms;
+  da.bhat = (const C2<double>*)P->bhat64;
+  da.b_ms = 3 * g.cs;
+  da.out32 = (C2<float>*)P->bhat;
+  da.o_ms = 3 * g.cs;
+  da.g = g;
+  da.part = P->part;
+  da.st = P->ist64;
+  for (int j = 0; j < k; ++j) da.idx[j] = idx[j];
+  const int blocks = 512;
+  CK(launch_defect<double>(da, blocks, k, st));
+  const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
+  CK(launch_defect_final(P->part, blocks, P->ist64, idx, k, maxdim, st));
   return BFCS_OK;
 }
 
@@ -764,11 +743,11 @@ int warm_disp64(bfcs_plan P, const void* eps_init, double* u64, bfcs_lame C0) {
 // grid; every field at the API is FP64 (Member pointers).  The FP64 state of a
 // member is its displacement u64, so eps64 = E + sym grad u64 stays exactly
 // compatible.
-//  Phase 1: members without a warm start run one batched FP32 solve to
-//  max(tol, switch_tol) (or their stall); u64 = its displacement.  A warm
-//  member takes u64 from its eps_init (FP64 projection).
+//  Phase 1: one batched FP32 solve of all members to max(tol, switch_tol) (or
+//  their stall), cold members from eps^{b(0)} + E, warm members from their
+//  eps_init rounded to FP32; u64 = its displacement.
 //  Rounds: every unfinished member gets eps64 and its FP64 residual r64 (one
-//  member at a time, FP64 workspace); a member stops when r64 <= tol (or after
+//  batched set of FP64 passes); a member stops when r64 <= tol (or after
 //  max_rounds / maxit); the others solve their correction problems (load = the
 //  FP64 defect rounded to FP32, E = 0) together in one batched FP32 solve, each
 //  to its own relative tolerance 0.5 tol / r64 (at least switch_tol, so that no
@@ -811,46 +790,54 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
   std::vector<bfcs_info> inf(P->max_batch);
   auto shift_of = [&](int m) { return std::array<int, 3>{in[m].sx, in[m].sy, in[m].sz}; };
 
-  // FP64 load spectra and their norms (residual denominators)
+  // FP64 load spectra of all members (slot = member) and their norms
   CK(cudaMemsetAsync(P->ist64, 0, B * sizeof(IterState), st));
-  for (int m = 0; m < B; ++m) {
-    e = transform_into<double>(P, in[m].b, bhat64 + (size_t)m * 3 * cs, P->tw64);
-    if (e != BFCS_OK) return e;
-    CK(launch_bden<double>(bhat64 + (size_t)m * 3 * cs, g, P->part, P->ist64 + m, st));
+  {
+    XArgs<double> xa{};
+    xa.g = g;
+    xa.spec_out = bhat64;
+    xa.spec_ms = 3 * cs;
+    fill_xm(xa, in, B, XIN_B, 0);
+    xa.ncomp = 3;
+    xa.mode = XM_R2C;
+    xa.tw = (const C2<double>*)P->tw64[0];
+    CK(launch_xpass_b<double>(xa, B, st));
+    CArgs<double> ca{};
+    ca.data = bhat64;
+    ca.ms = 3 * cs;
+    ca.g = g;
+    ca.ncomp = 3;
+    ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
+    CK(launch_colpass_b<double>(ca, -1, B, st));
+    ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
+    CK(launch_colpass_b<double>(ca, -1, B, st));
+    CK(launch_bden<double>(bhat64, g, P->part, P->ist64, st, B, 3 * cs));
   }
 
-  // phase 1
-  std::vector<int> cold;
+  // phase 1: all members, FP32
+  bool any_warm = false;
+  mem.clear();
   for (int m = 0; m < B; ++m) {
+    CK(launch_cast_spec(bhat32 + (size_t)m * 3 * cs, bhat64 + (size_t)m * 3 * cs, g, 3, st));
+    const void* init = nullptr;
     if (in[m].eps_init != nullptr) {
-      e = warm_disp64(P, in[m].eps_init, u64[m], C0);
-      if (e != BFCS_OK) return e;
-    } else {
-      cold.push_back(m);
+      CK(launch_cast_d2f(eps32(m), (const double*)in[m].eps_init, 6 * n, st));
+      init = eps32(m);
+      any_warm = true;
     }
+    const auto sh = shift_of(m);
+    mem.push_back(make_member(in[m].phase, sh.data(), in[m].E, nullptr, init, SolveOut{eps32(m), nullptr, u32(m)}));
   }
-  if (!cold.empty()) {
-    const int k = (int)cold.size();
-    mem.clear();
-    for (int j = 0; j < k; ++j) {
-      const int m = cold[j];
-      CK(launch_cast_spec(bhat32 + (size_t)j * 3 * cs, bhat64 + (size_t)m * 3 * cs, g, 3, st));
-      const auto sh = shift_of(m);
-      mem.push_back(make_member(in[m].phase, sh.data(), in[m].E, nullptr, nullptr,
-                                SolveOut{eps32(j), nullptr, u32(j)}));
-    }
-    CK(launch_bden<float>(bhat32, g, P->part, P->ist, st, k, 3 * cs));
-    e = upload_members(P, k, mem.data());
-    if (e != BFCS_OK) return e;
-    const int s1 = run_batch<float>(P, k, tab32, C0, in[cold[0]].E, std::max(tol, P->switch_tol), maxit,
-                                    inf.data(), false);
-    if (s1 < 0) return s1;
-    for (int j = 0; j < k; ++j) {
-      const int m = cold[j];
-      sweeps[m] += inf[j].iters;
-      r_last[m] = inf[j].resid;
-      CK(launch_cast_f2d(u64[m], u32(j), 3 * n, st));
-    }
+  CK(launch_bden<float>(bhat32, g, P->part, P->ist, st, B, 3 * cs));
+  e = upload_members(P, B, mem.data());
+  if (e != BFCS_OK) return e;
+  const int s1 = run_batch<float>(P, B, tab32, C0, in[0].E, std::max(tol, P->switch_tol), maxit, inf.data(),
+                                  any_warm);
+  if (s1 < 0) return s1;
+  for (int m = 0; m < B; ++m) {
+    sweeps[m] += inf[m].iters;
+    r_last[m] = inf[m].resid;
+    CK(launch_cast_f2d(u64[m], u32(m), 3 * n, st));
   }
 
   for (int round = 0;; ++round) {
@@ -858,12 +845,14 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
     for (int m = 0; m < B; ++m)
       if (!fin[m]) act.push_back(m);
     if (act.empty()) break;
-    for (int m : act) {
+    mem.clear();
+    for (int m : act) {      // defect inputs: u64 as the real input, eps64 out
       const auto sh = shift_of(m);
-      e = defect64(P, m, in[m].phase, tab64, C0, in[m].E, u64[m], (double*)in[m].eps_out, sh.data(),
-                   bhat32 + (size_t)m * 3 * cs);
-      if (e != BFCS_OK) return e;
+      mem.push_back(make_member(in[m].phase, sh.data(), in[m].E, u64[m], nullptr,
+                                SolveOut{in[m].eps_out, nullptr, nullptr}));
     }
+    e = defect64(P, (int)act.size(), mem.data(), act.data(), tab64);
+    if (e != BFCS_OK) return e;
     IterState* h64 = P->ist_host + 2 * P->max_batch;
     CK(cudaMemcpyAsync(h64, P->ist64, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
     const int w = sync_stream(P);
@@ -937,7 +926,7 @@ int solve_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phas
 
 int ensure_tmp(bfcs_plan P) {
   if (P->tmp == nullptr) {
-    const size_t members = P->mixed ? 1 : (size_t)P->max_batch;
+    const size_t members = (size_t)P->max_batch;
     if (cudaMalloc(&P->tmp, members * 15 * (size_t)P->g.n * P->rsz) != cudaSuccess) return BFCS_ERR_OOM;
   }
   if (P->tmp_hits == nullptr) {
@@ -996,27 +985,34 @@ int translate_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* p
 int translate_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
                     const void* b, const double* E, int nshift, const int32_t* shifts, double tol, int maxit,
                     double* avg, int32_t* hits, bfcs_info* infos) {
-  if (avg == nullptr || shifts == nullptr || nshift < 1) return BFCS_ERR_INVALID_ARG;
+  if (avg == nullptr || shifts == nullptr || nshift < 1 || E == nullptr || phase == nullptr || b == nullptr)
+    return BFCS_ERR_INVALID_ARG;
   int e = ensure_tmp(P);
   if (e != BFCS_OK) return e;
   const long long n = P->g.n;
   int* h = hits != nullptr ? (int*)hits : P->tmp_hits;
   CK(cudaMemsetAsync(avg, 0, 30 * n * sizeof(double), P->st));
   CK(cudaMemsetAsync(h, 0, n * sizeof(int), P->st));
-  double* eps = (double*)P->tmp;
-  double* sig = eps + 6 * n;
-  double* u = sig + 6 * n;
   int worst = BFCS_OK;
-  for (int m = 0; m < nshift; ++m) {
-    const int sh[3] = {shifts[3 * m], shifts[3 * m + 1], shifts[3 * m + 2]};
-    bfcs_info inf{};
-    const int s = solve_mixed(P, phase, nph, phases, C0, b, E, tol, maxit, nullptr, SolveOut{eps, sig, u}, sh,
-                              &inf);
+  std::vector<Member> mem;
+  for (int start = 0; start < nshift; start += P->max_batch) {   // the batched ladder, max_batch shifts at a time
+    const int B = std::min(P->max_batch, nshift - start);
+    mem.clear();
+    for (int m = 0; m < B; ++m) {
+      double* eps = (double*)P->tmp + (size_t)m * 15 * n;
+      const int32_t* sh = shifts + 3 * (start + m);
+      const int shv[3] = {sh[0], sh[1], sh[2]};
+      mem.push_back(make_member(phase, shv, E, b, nullptr, SolveOut{eps, eps + 6 * n, eps + 12 * n}));
+    }
+    const int s = solve_mixed_batch(P, B, mem.data(), nph, phases, C0, tol, maxit,
+                                    infos != nullptr ? infos + start : nullptr);
     if (s < 0) return s;
-    if (s > worst) worst = s;
-    if (infos != nullptr) infos[m] = inf;
-    CK(launch_accumulate<double>(avg, h, eps, sig, u, phase, sh[0], sh[1], sh[2], P->g.nx, P->g.ny,
-                                 P->g.nz, P->st));
+    if (severity(s) > severity(worst)) worst = s;
+    for (int m = 0; m < B; ++m) {
+      const double* eps = (const double*)mem[m].eps_out;
+      CK(launch_accumulate<double>(avg, h, eps, eps + 6 * n, eps + 12 * n, phase, mem[m].sx, mem[m].sy, mem[m].sz,
+                                   P->g.nx, P->g.ny, P->g.nz, P->st));
+    }
   }
   CK(launch_scale(avg, 30 * n, 1.0 / nshift, P->st));
   const int w = sync_stream(P);
@@ -1097,7 +1093,7 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
     if (P->tw[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
   }
   if (P->mixed) {
-    ok = cudaMalloc(&P->spec64, 6 * cs * sizeof(C2<double>)) == cudaSuccess &&
+    ok = cudaMalloc(&P->spec64, MB * 6 * cs * sizeof(C2<double>)) == cudaSuccess &&
          cudaMalloc(&P->bhat64, MB * 3 * cs * sizeof(C2<double>)) == cudaSuccess &&
          cudaMalloc(&P->ist64, MB * sizeof(IterState)) == cudaSuccess &&
          cudaMalloc(&P->r32, MB * 12 * (size_t)P->g.n * sizeof(float)) == cudaSuccess &&

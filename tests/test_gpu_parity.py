@@ -270,10 +270,12 @@ def test_mixed_ladder_goes_below_the_fp32_floor():
         # the returned FP64 field's residual, evaluated by the oracle
         r = O.residual(ph_o, p.phases, eps.cpu().numpy(), O.fft3(b_o), O.wavevectors(p.dims))
         assert r <= 2e-9
-        # a warm start from the converged field needs no FP32 sweep
-        eps2, _, u2, info2 = plan.solve(ph, p.phases, p.c0, b, tol=1e-9, maxit=50, eps_init=eps.clone())
-        assert info2.iters == 0 and info2.resid <= 1e-9
-        assert rel(eps2.cpu().numpy(), eps.cpu().numpy()) < 1e-12
+        # a warm start from the converged field enters the FP32 phase already
+        # converged there; one correction below the FP32 floor remains
+        eps2, _, u2, info2 = plan.solve(ph, p.phases, p.c0, b, tol=1e-9, maxit=4000, eps_init=eps.clone())
+        assert info2.status == _lib.OK and info2.resid <= 1e-9
+        assert info2.iters < 0.5 * info.iters, (info2.iters, info.iters)
+        assert rel(eps2.cpu().numpy(), eps.cpu().numpy()) < 1e-8
         # the displacement agrees up to its rounding-level mean (gauge) component
         assert rel(u2.cpu().numpy(), u.cpu().numpy()) < 1e-8
 
