@@ -32,7 +32,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "voxel-iter/s"
+METRIC = "voxel-iter/s & %HBM peak; solves/s to resid 1e-6, batched+NN warm vs plain"
 UNIT = "voxel-iter/s"
 
 
@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--contrast", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the solves/s comparison (64 solves at 64^3: plain, batched, batched + network)")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling aid: run one FP32 solve of exactly this many sweeps and exit")
     return ap.parse_args()
@@ -353,11 +355,18 @@ def run_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"one Algorithm-1 sweep of the same {args.n}^3 problem (oracle setup untimed), "
                          f"{tcpu:.1f} s, FP64 numpy/scipy single thread"}
+    warm = None
+    if not args.no_warm_start:
+        from paper_2601_00822_gb300 import surrogate as S
+        warm = S.warm_start_benchmark(S.load(S.DEFAULT_WEIGHTS), list(range(64)), 64, tol=1e-6, batch=64)
+        warm["workload"] = ("64 held-out config_c5 samples at 64^3 (RSA spheres vf 0.1-0.3 in 16^3 cells, "
+                            "contrast 10, BFCS a in [4, 12]), mixed ladder to resid 1e-6; network inference "
+                            "inside the warm timing")
     fin = infos[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": config_dict(p, args, world),
         "solves_per_s": solves / secs,
         "sweeps_per_solve": sweeps / args.steps,
@@ -379,6 +388,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
+        "warm_start": warm,
     }
     print(json.dumps(line))
     if world > 1:

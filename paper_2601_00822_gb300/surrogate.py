@@ -220,7 +220,33 @@ def main(argv=None):
     b.add_argument("--grid", type=int, default=64)
     b.add_argument("--batch", type=int, default=64)
     b.add_argument("--tol", type=float, default=1e-6)
+    st = sub.add_parser("step", help="time training steps and a forward pass on random data (profiling aid)")
+    st.add_argument("--grid", type=int, default=64)
+    st.add_argument("--batch", type=int, default=8)
+    st.add_argument("--steps", type=int, default=4)
     a = ap.parse_args(argv)
+    if a.cmd == "step":
+        n, B = a.grid, a.batch
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        X = torch.randn((B, 4, n, n, n), device="cuda", generator=gen)
+        T = torch.randn((B, 6, n, n, n), device="cuda", generator=gen)
+        net = api.Net((n, n, n), max_batch=B, train=True)
+        params = init_params(0)
+        grad, m, v = torch.zeros_like(params), torch.zeros_like(params), torch.zeros_like(params)
+        for t in range(1, 4):
+            net.train_step(params, grad, m, v, t, 1e-4, X, T)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        for t in range(4, 4 + a.steps):
+            net.train_step(params, grad, m, v, t, 1e-4, X, T)
+        ev[1].record()
+        net.forward(params, X)
+        ev[2].record()
+        torch.cuda.synchronize()
+        print(json.dumps({"grid": n, "batch": B, "train_step_ms": ev[0].elapsed_time(ev[1]) / a.steps,
+                          "forward_ms": ev[1].elapsed_time(ev[2])}))
+        return
     if a.cmd == "train":
         logf = open(a.log, "w") if a.log else None
 
