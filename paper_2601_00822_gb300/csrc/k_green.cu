@@ -28,6 +28,15 @@ template <int L> struct GCfg {
   static constexpr int THREADS = NCOL * LineInfo<L>::RMAX;
 };
 
+// Shared-memory slot of line-column c in tile row `row`: rows with bit 1 set
+// swap neighbouring components (c ^ 4 with T = 4 columns per component).  Each
+// row keeps the same set of slots for every aligned group of 8 columns, so the
+// FFT exchanges (32 consecutive columns over one or two rows) stay
+// conflict-free, and the Green phase (8 rows x 4 columns of one component per
+// warp) covers all 16 eight-byte bank pairs twice instead of 8 of them 4 times.
+static_assert(kGreenT == 4 && (6 * kGreenT) % 8 == 0, "the swizzle flips one component bit");
+__device__ __forceinline__ int gslot(int row, int c) { return c ^ (((row >> 1) & 1) << 2); }
+
 template <typename R>
 __device__ __forceinline__ void g0_apply(const C2<R> g[3], const R xi[3], R q, R mu0, R c,
                                          C2<R> v[3]) {
@@ -95,19 +104,19 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
       for (int n1 = 0; n1 < R1; ++n1) x[n1] = cvalid ? gcol[(R2 * n1 + j) * zs] : mk<R>(0, 0);
       stage1<R, L, -1>(x, j, a.tw);
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + c] = x[k1];
+      for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + gslot(j * R1 + k1, c)] = x[k1];
     }
     __syncthreads();
     C2<R> y[R2];
     if (j < R1) {
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + c];
+      for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + gslot(n2 * R1 + j, c)];
       stage2<R, L, -1>(y);
     }
     __syncthreads();
     if (j < R1) {
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) s[(j + R1 * k2) * NCOL + c] = y[k2];
+      for (int k2 = 0; k2 < R2; ++k2) s[(j + R1 * k2) * NCOL + gslot(j + R1 * k2, c)] = y[k2];
     }
     __syncthreads();
   }
@@ -124,11 +133,13 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
   for (int idx = tid; idx < T * L; idx += nthr) {
     const int col = idx % T, n = idx / T;
     const int kx = col0 + col;
-    C2<R>* m = s + n * NCOL + col;                  // component q at m[q * T]
+    C2<R>* const m = s + n * NCOL + col;
+    const int qs = (n >> 1) & 1;                    // component q sits at m[(q ^ qs) * T] (gslot)
+    auto M = [&](int q) -> C2<R>& { return m[(q ^ qs) * T]; };
     const C2<R>* pm = pre + n * T + col;            // array r at pm[r * L * T]
     if (kx >= mx) {
 #pragma unroll
-      for (int q = 0; q < 6; ++q) m[q * T] = mk<R>(0, 0);
+      for (int q = 0; q < 6; ++q) M(q) = mk<R>(0, 0);
       continue;
     }
     const long long gi = n * zs + rowbase + kx;     // index in a 3-component spectrum
@@ -143,14 +154,14 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
       const bool k0 = (kx == 0 && ky == 0 && n == 0);
       if (k0 && mode != GM_INIT) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) stm->tau0[q] = (double)m[q * T].x;
+        for (int q = 0; q < 6; ++q) stm->tau0[q] = (double)M(q).x;
       }
       if (mode == GM_SWEEP || mode == GM_INIT) {
         dprev[gi] = mk<R>(0, 0); dprev[cs + gi] = mk<R>(0, 0); dprev[2 * cs + gi] = mk<R>(0, 0);
       }
 #pragma unroll
       for (int q = 0; q < 6; ++q)
-        m[q * T] = (mode != GM_FINAL && k0) ? mk<R>(Em[q], R(0)) : mk<R>(0, 0);
+        M(q) = (mode != GM_FINAL && k0) ? mk<R>(Em[q], R(0)) : mk<R>(0, 0);
       continue;
     }
     const C2<R> bh0 = pm[0], bh1 = pm[L * T], bh2 = pm[2 * L * T];
@@ -160,7 +171,7 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
     C2<R> d[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
     if (mode != GM_INIT) {
       // d_i = tau_hat_ij xi_j (xx yy zz yz xz xy)
-      const C2<R> t0 = m[0], t1 = m[T], t2 = m[2 * T], t3 = m[3 * T], t4 = m[4 * T], t5 = m[5 * T];
+      const C2<R> t0 = M(0), t1 = M(1), t2 = M(2), t3 = M(3), t4 = M(4), t5 = M(5);
       d[0] = scale(t0, xi[0]) + scale(t5, xi[1]) + scale(t4, xi[2]);
       d[1] = scale(t5, xi[0]) + scale(t1, xi[1]) + scale(t3, xi[2]);
       d[2] = scale(t4, xi[0]) + scale(t3, xi[1]) + scale(t2, xi[2]);
@@ -186,17 +197,17 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
     if (mode == GM_FINAL) {
       // u_hat = i v, scaled for the unnormalised inverse transforms
 #pragma unroll
-      for (int i = 0; i < 3; ++i) m[i * T] = mk<R>(-v[i].y * inv_n, v[i].x * inv_n);
+      for (int i = 0; i < 3; ++i) M(i) = mk<R>(-v[i].y * inv_n, v[i].x * inv_n);
 #pragma unroll
-      for (int q = 3; q < 6; ++q) m[q * T] = mk<R>(0, 0);
+      for (int q = 3; q < 6; ++q) M(q) = mk<R>(0, 0);
     } else {
       const R h = R(-0.5) * inv_n;
-      m[0] = scale(v[0], -xi[0] * inv_n);
-      m[T] = scale(v[1], -xi[1] * inv_n);
-      m[2 * T] = scale(v[2], -xi[2] * inv_n);
-      m[3 * T] = scale(scale(v[2], xi[1]) + scale(v[1], xi[2]), h);
-      m[4 * T] = scale(scale(v[2], xi[0]) + scale(v[0], xi[2]), h);
-      m[5 * T] = scale(scale(v[1], xi[0]) + scale(v[0], xi[1]), h);
+      M(0) = scale(v[0], -xi[0] * inv_n);
+      M(1) = scale(v[1], -xi[1] * inv_n);
+      M(2) = scale(v[2], -xi[2] * inv_n);
+      M(3) = scale(scale(v[2], xi[1]) + scale(v[1], xi[2]), h);
+      M(4) = scale(scale(v[2], xi[0]) + scale(v[0], xi[2]), h);
+      M(5) = scale(scale(v[1], xi[0]) + scale(v[0], xi[1]), h);
     }
   }
 
@@ -219,20 +230,20 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
     C2<R> x[R1];
     if (j < R2) {
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) x[n1] = s[((R2 * n1 + j) * NCOL) + c];
+      for (int n1 = 0; n1 < R1; ++n1) x[n1] = s[(R2 * n1 + j) * NCOL + gslot(R2 * n1 + j, c)];
       stage1<R, L, +1>(x, j, a.tw);
     }
     __syncthreads();
     if (j < R2) {
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + c] = x[k1];
+      for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + gslot(j * R1 + k1, c)] = x[k1];
     }
   }
   __syncthreads();
   if (j < R1) {
     C2<R> y[R2];
 #pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + c];
+    for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + gslot(n2 * R1 + j, c)];
     stage2<R, L, +1>(y);
     if (cvalid && keep) {
 #pragma unroll
