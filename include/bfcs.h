@@ -54,6 +54,7 @@ extern "C" {
 #define BFCS_FP32 0                   /* FP32 fields and FFTs, FP64 residual sums */
 #define BFCS_FP64 1                   /* FP64 throughout */
 #define BFCS_MIXED 2                  /* FP32 sweeps with FP64 defect correction; FP64 fields */
+#define BFCS_AUTOTUNE 4               /* OR-ed with FP32 or MIXED: time the y-pass variants at plan creation */
 
 #define BFCS_MAX_PHASES 16
 
@@ -90,9 +91,11 @@ typedef struct {
  *  nx,ny,nz:  grid (BFUC of Eq. 2.7 / Sec. 4 unit cell), even, supported sizes.
  *  max_batch: >= 1; members of bfcs_solve_batched are run in groups of at most
  *             this many.
- *  flags:     BFCS_FP32, BFCS_FP64 or BFCS_MIXED.  BFCS_MIXED runs the sweeps in
- *             FP32 and corrects them in FP64 (below); its fields at the API
- *             (b, eps, sigma, u, eps_init, fft3d data) are double.
+ *  flags:     BFCS_FP32, BFCS_FP64 or BFCS_MIXED, optionally OR BFCS_AUTOTUNE
+ *             (FP32 / MIXED: pick the y-pass variant by timing, see
+ *             bfcs_plan_tuning).  BFCS_MIXED runs the sweeps in FP32 and
+ *             corrects them in FP64 (below); its fields at the API (b, eps,
+ *             sigma, u, eps_init, fft3d data) are double.
  *  stream:    cudaStream_t to order work on (NULL = legacy default stream).
  * Allocates about (6 + 3 + 3) * nz*ny*(nx/2+4) complex values of workspace.
  * Errors: INVALID_ARG, OOM, CUDA.
@@ -194,6 +197,30 @@ int bfcs_solve(bfcs_plan plan, const int8_t* phase, int nphases, const bfcs_lame
  */
 int bfcs_solve_batched(bfcs_plan plan, int batch, const bfcs_problem* problems, int nphases,
                        const bfcs_lame* phases, bfcs_lame C0, double tol, int maxit, bfcs_info* infos);
+
+/*
+ * bfcs_solve_group - batches on different grids in one loop (project feature:
+ * the paper solves one problem at a time).  Item i runs items[i].batch
+ * members (1..max_batch of its plan; bfcs_problem as for bfcs_solve_batched)
+ * on items[i].plan, whose grid may differ from the other items'.  All plans
+ * are FP32 or all FP64 (BFCS_MIXED: BFCS_ERR_UNSUPPORTED) and distinct; phases
+ * and C0 are shared.  The sweeps of all items run together: one CUDA graph
+ * launch per chunk of sweeps advances every item (the items' launches are
+ * parallel branches of the graph, one stream per plan), and the loop ends when
+ * every member of every item is done.  Each plan's stream waits for the loop
+ * and finalises its own members; the call returns when all are written.
+ * infos (per item, host, batch entries) may be NULL.  Returns the most severe
+ * member status.  nitems in 1..BFCS_MAX_GROUP.
+ */
+#define BFCS_MAX_GROUP 8
+typedef struct {
+  bfcs_plan plan;
+  int batch;
+  const bfcs_problem* problems;
+  bfcs_info* infos;
+} bfcs_group_item;
+int bfcs_solve_group(int nitems, const bfcs_group_item* items, int nphases, const bfcs_lame* phases,
+                     bfcs_lame C0, double tol, int maxit);
 
 /*
  * bfcs_translate_average - translated averaging (Eqs. 3.3-3.6) and the
@@ -310,6 +337,15 @@ int bfcs_fft3d(bfcs_plan plan, int direction, int ncomp, const void* in, void* o
 long long bfcs_kernel_launches(void);
 int bfcs_profile_kernel(bfcs_plan plan, int kind);
 int bfcs_profile_read(bfcs_plan plan, long long* launches, double* total_ms);
+
+/* bfcs_plan_tuning - the plan's choice for the y passes of its FP32 sweeps
+ * (project feature, not in the paper): variant 0..5 = column tile of 16, 8 or
+ * 32 kx columns per block, then the same three with the two radices of the
+ * line length ny = R1 R2 in the other order.  With BFCS_AUTOTUNE the plan
+ * timed every variant valid for ny on its own buffers and kept the fastest
+ * (variant_ms: 6 doubles, ms per y forward + inverse pair, 0 = not timed);
+ * without it the variant is 0.  Any output pointer may be NULL. */
+int bfcs_plan_tuning(bfcs_plan plan, int* col_variant, int* col_tile, int* col_swap, double* variant_ms);
 
 /* Residual history of the last solve on the plan: copies min(cap, iters)
  * values r(eps^s) into hist (host); returns the count or a negative status. */

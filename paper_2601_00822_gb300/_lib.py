@@ -24,6 +24,7 @@ ERR_UNSUPPORTED = -7
 FP32 = 0
 FP64 = 1
 MIXED = 2
+AUTOTUNE = 4
 
 # every symbol declared in include/bfcs.h
 EXPORTS = (
@@ -32,7 +33,7 @@ EXPORTS = (
     "bfcs_last_history", "bfcs_status_string", "bfcs_kernel_launches", "bfcs_profile_kernel",
     "bfcs_profile_read", "bfcs_body_force_noalloc", "bfcs_net_param_count", "bfcs_net_create",
     "bfcs_net_destroy", "bfcs_net_prepare", "bfcs_net_forward", "bfcs_net_grad", "bfcs_net_adam",
-    "bfcs_net_train_step", "bfcs_net_predict",
+    "bfcs_net_train_step", "bfcs_net_predict", "bfcs_plan_tuning", "bfcs_solve_group",
 )
 NET_PARAMS = 523654
 NET_TRAIN = 1
@@ -52,6 +53,11 @@ class Problem(C.Structure):
     _fields_ = [("phase", C.c_void_p), ("b", C.c_void_p), ("E", C.c_double * 6),
                 ("shift", C.c_int * 3), ("eps_init", C.c_void_p), ("eps_out", C.c_void_p),
                 ("sig_out", C.c_void_p), ("u_out", C.c_void_p)]
+
+
+class GroupItem(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("batch", C.c_int), ("problems", C.POINTER(Problem)),
+                ("infos", C.POINTER(Info))]
 
 
 def _declare(lib):
@@ -84,6 +90,8 @@ def _declare(lib):
     lib.bfcs_net_train_step.argtypes = [vp, vp, vp, vp, vp, ll, f, i, vp, vp, vp]
     lib.bfcs_net_predict.argtypes = [vp, vp, i, i, C.POINTER(vp), C.POINTER(vp), i, C.POINTER(Lame),
                                      C.POINTER(vp)]
+    lib.bfcs_solve_group.argtypes = [i, C.POINTER(GroupItem), i, C.POINTER(Lame), Lame, d, i]
+    lib.bfcs_plan_tuning.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(d)]
     lib.bfcs_status_string.argtypes = [i]
     lib.bfcs_status_string.restype = C.c_char_p
     for name in EXPORTS:

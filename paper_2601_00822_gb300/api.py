@@ -88,7 +88,7 @@ def body_force(dims, centre, a, precision="fp32", device="cuda", stream=None) ->
 class Plan:
     """bfcs_plan_create / bfcs_plan_destroy with the solver calls as methods."""
 
-    def __init__(self, dims, precision="fp32", max_batch=1, stream=None):
+    def __init__(self, dims, precision="fp32", max_batch=1, stream=None, autotune=False):
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.precision = precision
@@ -96,6 +96,8 @@ class Plan:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         flag = {"fp32": _lib.FP32, "fp64": _lib.FP64, "mixed": _lib.MIXED}[precision]
+        if autotune:
+            flag |= _lib.AUTOTUNE
         nx, ny, nz = self.dims
         _lib.check(self.lib.bfcs_plan_create(C.byref(h), nx, ny, nz, int(max_batch), flag,
                                              _stream_ptr(self.stream)), "bfcs_plan_create")
@@ -174,6 +176,24 @@ class Plan:
         _lib.check(code, "bfcs_solve_batched", allow)
         return members, [SolveInfo.of(infos[m]) for m in range(n)]
 
+    def _problems(self, members):
+        n = len(members)
+        arr = (_lib.Problem * n)()
+        for m, mem in enumerate(members):
+            mem.setdefault("eps_out", self._alloc(6))
+            for key, comp in (("sig_out", 6), ("u_out", 3)):
+                if key not in mem:
+                    mem[key] = self._alloc(comp)
+            arr[m].phase = mem["phase"].data_ptr()
+            arr[m].b = mem["b"].data_ptr()
+            arr[m].E = (C.c_double * 6)(*[float(v) for v in mem.get("E", (0.0,) * 6)])
+            arr[m].shift = (C.c_int * 3)(*[int(v) for v in mem.get("shift", (0, 0, 0))])
+            arr[m].eps_init = mem["eps_init"].data_ptr() if mem.get("eps_init") is not None else None
+            arr[m].eps_out = mem["eps_out"].data_ptr()
+            arr[m].sig_out = mem["sig_out"].data_ptr() if mem["sig_out"] is not None else None
+            arr[m].u_out = mem["u_out"].data_ptr() if mem["u_out"] is not None else None
+        return arr
+
     def translate_average(self, phase, phases, c0, b, shifts, E=(0.0,) * 6, tol=1e-6, maxit=10000,
                           allow=(_lib.OK, _lib.NOT_CONVERGED)):
         """bfcs_translate_average; returns (avg (30, nz, ny, nx) float64, hits int32, infos)."""
@@ -224,6 +244,14 @@ class Plan:
         if n < 0:
             raise _lib.BfcsError(n, "bfcs_last_history")
         return np.array(buf[:n])
+
+    def tuning(self):
+        """bfcs_plan_tuning: dict(variant, tile, swap, variant_ms)."""
+        v, t, sw = C.c_int(), C.c_int(), C.c_int()
+        ms = (C.c_double * 6)()
+        _lib.check(self.lib.bfcs_plan_tuning(self.handle, C.byref(v), C.byref(t), C.byref(sw), ms),
+                   "bfcs_plan_tuning")
+        return {"variant": v.value, "tile": t.value, "swap": bool(sw.value), "variant_ms": list(ms)}
 
     def surrogate_infer(self, weights, b, phase, phases, eps_out=None):
         """bfcs_surrogate_infer: the network's strain prediction (6, nz, ny, nx) on this plan's grid."""
@@ -365,3 +393,24 @@ class Net:
                                              _ptr_array(phases_maps), len(phases), arr, _ptr_array(outs)),
                    "bfcs_net_predict")
         return outs
+
+
+def solve_group(groups, phases, c0, tol=1e-6, maxit=10000, allow=(_lib.OK, _lib.NOT_CONVERGED)):
+    """bfcs_solve_group: groups = [(plan, members), ...] with plans of different grids (all
+    'fp32' or all 'fp64'); members as for Plan.solve_batched.  Returns [(members, infos), ...]."""
+    lib = _lib.load()
+    n = len(groups)
+    items = (_lib.GroupItem * n)()
+    keep = []
+    for i, (plan, members) in enumerate(groups):
+        arr = plan._problems(members)
+        infos = (_lib.Info * len(members))()
+        keep.append((arr, infos))
+        items[i].plan = plan.handle.value
+        items[i].batch = len(members)
+        items[i].problems = C.cast(arr, C.POINTER(_lib.Problem))
+        items[i].infos = C.cast(infos, C.POINTER(_lib.Info))
+    code = lib.bfcs_solve_group(n, items, len(phases), _lames(phases), _lib.Lame(*c0), float(tol), int(maxit))
+    _lib.check(code, "bfcs_solve_group", allow)
+    return [(members, [SolveInfo.of(infos[m]) for m in range(len(members))])
+            for (plan, members), (_, infos) in zip(groups, keep)]

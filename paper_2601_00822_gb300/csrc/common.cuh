@@ -189,9 +189,10 @@ __device__ __forceinline__ void fft_cols(C2<R>* s, int ncol, const C2<R>* __rest
 // inputs x[R2 n1 + n2] (n1 = 0..R1-1) of one line runs stage1(); after the
 // exchange through shared memory a thread holding the R2 values Y[n2][k1]
 // (n2 = 0..R2-1) runs stage2() and owns the outputs X[k1 + R1 k2].
-template <typename R, int L, int DIR>
-__device__ __forceinline__ void stage1(C2<R>* x, int n2, const C2<R>* __restrict__ tw) {
-  constexpr int R1 = LineInfo<L>::R1;
+// stage1f / stage2f take the factor R1 explicitly (L = R1 * (L / R1), either
+// order of the two radices); stage1 / stage2 use the default order of Fac<L>.
+template <typename R, int L, int R1, int DIR>
+__device__ __forceinline__ void stage1f(C2<R>* x, int n2, const C2<R>* __restrict__ tw) {
   Dft<R, R1, DIR>::run(x);
 #pragma unroll
   for (int k1 = 1; k1 < R1; ++k1) {
@@ -200,9 +201,17 @@ __device__ __forceinline__ void stage1(C2<R>* x, int n2, const C2<R>* __restrict
     x[k1] = cmul(x[k1], w);
   }
 }
+template <typename R, int R2, int DIR>
+__device__ __forceinline__ void stage2f(C2<R>* y) {
+  Dft<R, R2, DIR>::run(y);
+}
+template <typename R, int L, int DIR>
+__device__ __forceinline__ void stage1(C2<R>* x, int n2, const C2<R>* __restrict__ tw) {
+  stage1f<R, L, LineInfo<L>::R1, DIR>(x, n2, tw);
+}
 template <typename R, int L, int DIR>
 __device__ __forceinline__ void stage2(C2<R>* y) {
-  Dft<R, LineInfo<L>::R2, DIR>::run(y);
+  stage2f<R, LineInfo<L>::R2, DIR>(y);
 }
 
 // ------------------------------------------------------------------ async copies

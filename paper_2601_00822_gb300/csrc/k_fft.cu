@@ -208,17 +208,25 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
 
 // Column FFT along y or z: each block owns T consecutive kx columns of one
 // (other-axis, component) slab; loads are T-wide contiguous row segments.
+// L = F1 * F2 in the order given by SW (the default order of Fac<L>, or
+// swapped); T and SW are the autotuned choices of an FP32 plan.
 constexpr int kColT = 16;
 
-template <int L> struct CCfg {
-  static constexpr int THREADS = kColT * LineInfo<L>::RMAX;
+template <int L, int T, bool SW> struct CCfg {
+  static constexpr int F1 = SW ? Fac<L>::R2 : Fac<L>::R1;
+  static constexpr int F2 = SW ? Fac<L>::R1 : Fac<L>::R2;
+  static constexpr int RMAX = F1 > F2 ? F1 : F2;
+  static constexpr int THREADS = T * RMAX;
 };
+template <typename R, int T> constexpr int col_min_blocks() {
+  return sizeof(R) == 4 ? (T == 8 ? 6 : T == 16 ? 3 : 1) : 2;
+}
 
-template <typename R, int L, int DIR>
-__global__ void __launch_bounds__(CCfg<L>::THREADS, sizeof(R) == 4 ? 3 : 2) k_colpass(CArgs<R> a) {
+template <typename R, int L, int DIR, int T, bool SW>
+__global__ void __launch_bounds__(CCfg<L, T, SW>::THREADS, col_min_blocks<R, T>()) k_colpass(CArgs<R> a) {
   const int m = blockIdx.z;
   if (a.st != nullptr && a.st[m].done) return;   // a member that has converged skips
-  constexpr int T = kColT, R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
+  constexpr int R1 = CCfg<L, T, SW>::F1, R2 = CCfg<L, T, SW>::F2;
   extern __shared__ unsigned char smem_raw[];
   C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -236,7 +244,7 @@ __global__ void __launch_bounds__(CCfg<L>::THREADS, sizeof(R) == 4 ? 3 : 2) k_co
     C2<R> x[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) x[n1] = valid ? col[(R2 * n1 + j) * ls] : mk<R>(0, 0);
-    stage1<R, L, DIR>(x, j, a.tw);
+    stage1f<R, L, R1, DIR>(x, j, a.tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * T + c] = x[k1];
   }
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(CCfg<L>::THREADS, sizeof(R) == 4 ? 3 : 2) k_co
     C2<R> y[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * T + c];
-    stage2<R, L, DIR>(y);
+    stage2f<R, R2, DIR>(y);
     if (valid) {
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) col[(j + R1 * k2) * ls] = y[k2];
@@ -296,17 +304,38 @@ cudaError_t launch_xpass_b(const XArgs<R>& a0, int batch, cudaStream_t st) {
   }
 }
 
-template <typename R, int L, int DIR>
-static cudaError_t colpass_L(const CArgs<R>& a, int batch, cudaStream_t st) {
+template <typename R, int L, int DIR, int T, bool SW>
+static cudaError_t colpass_LT(const CArgs<R>& a, int batch, cudaStream_t st) {
   const int other = a.axis == 1 ? a.g.nz : a.g.ny;
-  dim3 grid((a.g.mx + kColT - 1) / kColT, other * a.ncomp, batch);
-  const size_t smem = sizeof(C2<R>) * (size_t)L * kColT;
-  cudaError_t e = cudaFuncSetAttribute(k_colpass<R, L, DIR>,
+  dim3 grid((a.g.mx + T - 1) / T, other * a.ncomp, batch);
+  const size_t smem = sizeof(C2<R>) * (size_t)L * T;
+  cudaError_t e = cudaFuncSetAttribute(k_colpass<R, L, DIR, T, SW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_colpass<R, L, DIR><<<grid, CCfg<L>::THREADS, smem, st>>>(a);
+  k_colpass<R, L, DIR, T, SW><<<grid, CCfg<L, T, SW>::THREADS, smem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
+}
+
+template <typename R, int L, int DIR>
+static cudaError_t colpass_L(const CArgs<R>& a, int batch, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4 && L >= 32 && Fac<L>::R1 != Fac<L>::R2) {
+    switch (a.variant) {
+      case 1: return colpass_LT<R, L, DIR, 8, false>(a, batch, st);
+      case 2: return colpass_LT<R, L, DIR, 32, false>(a, batch, st);
+      case 3: return colpass_LT<R, L, DIR, 16, true>(a, batch, st);
+      case 4: return colpass_LT<R, L, DIR, 8, true>(a, batch, st);
+      case 5: return colpass_LT<R, L, DIR, 32, true>(a, batch, st);
+      default: break;
+    }
+  } else if constexpr (sizeof(R) == 4 && L >= 32) {
+    switch (a.variant) {
+      case 1: return colpass_LT<R, L, DIR, 8, false>(a, batch, st);
+      case 2: return colpass_LT<R, L, DIR, 32, false>(a, batch, st);
+      default: break;
+    }
+  }
+  return colpass_LT<R, L, DIR, kColT, false>(a, batch, st);
 }
 
 template <typename R>

@@ -366,6 +366,13 @@ cudaError_t launch_defect_final(const ResidSlot* part, int nparts, IterState* st
   return cudaGetLastError();
 }
 
+bool col_variant_valid(int v, int n) {
+  if (v == 0) return true;
+  if (v < 0 || v >= kColVariants || n < 32 || !supported_len(n)) return false;
+  if (!col_variant_swap(v)) return true;
+  return n != 64 && n != 256;   // 64 = 8 x 8 and 256 = 16 x 16 have one order only
+}
+
 // ---------------------------------------------------------------- a10: translated averaging
 // acc layout (30 x N, FP64): <u> 3, <u>^(1) 3, <eps> 6, <eps>^(1) 6, <sigma> 6, <sigma>^(1) 6.
 template <typename R>

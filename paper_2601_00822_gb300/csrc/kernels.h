@@ -66,7 +66,17 @@ template <typename R> struct CArgs {
   const C2<R>* tw;        // exp(-2 pi i j / n_axis)
   const IterState* st;    // nullable: member m = blockIdx.z skips once st[m].done
   long long ms;           // data stride between members (complex elements)
+  int variant;            // FP32 only: column tile and factor order (kColVariants; 0 = default)
 };
+
+// Column-pass variants an autotuner can pick from (FP32): tile width in kx
+// columns and the order of the two radices of the line length.
+constexpr int kColVariants = 6;
+constexpr int col_variant_tile(int v) { return v % 3 == 0 ? 16 : v % 3 == 1 ? 8 : 32; }
+constexpr bool col_variant_swap(int v) { return v >= 3; }
+// whether variant v exists for line length n (only lengths with two different
+// radices have a swapped order; the tunable lengths are 32..256)
+bool col_variant_valid(int v, int n);
 
 // ---- fused z pass: forward z FFT -> Green operators -> residual -> inverse z FFT.
 enum GMode : int {

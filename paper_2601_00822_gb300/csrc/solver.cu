@@ -66,6 +66,8 @@ struct bfcs_plan_s {
   int max_rounds = 8;              // defect-correction rounds
   double switch_tol = 1e-4;        // FP32 phase stops here (or at the stall)
   bfcs_net net = nullptr;          // inference context of bfcs_surrogate_infer (created on first use)
+  int col_variant = 0;             // y-pass tile / factor order of the FP32 sweeps (autotuned or default)
+  double col_variant_ms[kColVariants] = {0, 0, 0, 0, 0, 0};   // tuning times (ms per y forward+inverse pair)
 };
 
 namespace {
@@ -146,6 +148,52 @@ void free_plan(bfcs_plan P) {
   if (P->order_ev[1]) cudaEventDestroy(P->order_ev[1]);
   if (P->net) bfcs_net_destroy(P->net);
   delete P;
+}
+
+// Autotuner of the FP32 sweep's y passes: every valid column-pass variant
+// (tile width, factor order) runs a y forward + inverse pair over the plan's
+// own spectrum buffer (max_batch members, zeroed), CUDA events on the plan's
+// stream, 2 untimed + 5 timed pairs; the fastest is kept.  All variants
+// compute the same transform (the factor order changes the rounding only).
+int autotune(bfcs_plan P) {
+  cudaStream_t st = P->st;
+  const size_t bytes = (size_t)P->max_batch * 6 * P->g.cs * sizeof(C2<float>);
+  if (cudaMemsetAsync(P->spec, 0, bytes, st) != cudaSuccess) return BFCS_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return BFCS_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return BFCS_ERR_CUDA; }
+  CArgs<float> ca{};
+  ca.data = (C2<float>*)P->spec;
+  ca.g = P->g;
+  ca.axis = 1;
+  ca.ncomp = 6;
+  ca.tw = (const C2<float>*)P->tw[1];
+  ca.ms = 6 * P->g.cs;
+  double best = INFINITY;
+  int bestv = 0, status = BFCS_OK;
+  for (int v = 0; v < kColVariants && status == BFCS_OK; ++v) {
+    P->col_variant_ms[v] = 0.0;
+    if (!col_variant_valid(v, P->g.ny)) continue;
+    ca.variant = v;
+    bool ok = true;
+    for (int k = 0; k < 7 && ok; ++k) {
+      if (k == 2) ok = cudaEventRecord(e0, st) == cudaSuccess;
+      ok = ok && launch_colpass_b<float>(ca, -1, P->max_batch, st) == cudaSuccess &&
+           launch_colpass_b<float>(ca, +1, P->max_batch, st) == cudaSuccess;
+    }
+    ok = ok && cudaEventRecord(e1, st) == cudaSuccess;
+    if (!ok) { status = BFCS_ERR_CUDA; break; }
+    const int w = wait_event(e1);
+    if (w != BFCS_OK) { status = w; break; }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { status = BFCS_ERR_CUDA; break; }
+    P->col_variant_ms[v] = ms / 5.0;
+    if (ms / 5.0 < best) { best = ms / 5.0; bestv = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->col_variant = bestv;
+  return status;
 }
 
 template <typename R>
@@ -285,146 +333,260 @@ int transform_members(bfcs_plan P, int B) {
   return BFCS_OK;
 }
 
-// Algorithm 1 for B members of one grid, advancing together: each sweep is
-// one launch per pass for all members; converged members skip on the device.
-// Needs the member descriptors, b_hat and bden in place.  Outputs through the
-// descriptors' eps_out / sig_out / u_out.
+// One plan's batch of B members advancing together (Algorithm 1): the kernel
+// arguments of one sweep, the INIT step, the sweep enqueue and the
+// finalisation.  Needs the member descriptors, b_hat and bden in place;
+// outputs go through the descriptors' eps_out / sig_out / u_out.
 template <typename R>
-int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const double* E0, double tol,
-              int maxit, bfcs_info* infos, bool any_warm) {
-  const Geo g = P->g;
-  cudaStream_t st = P->st;
-  C2<R>* spec = (C2<R>*)P->spec;
-  const C2<R>* twx = (const C2<R>*)P->tw[0];
-  const C2<R>* twy = (const C2<R>*)P->tw[1];
-  const C2<R>* twz = (const C2<R>*)P->tw[2];
-  const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
-  const long long sms = 6 * g.cs;
-
-  // iteration state (keep bden computed by the caller)
-  for (int m = 0; m < B; ++m)
-    CK(cudaMemsetAsync(P->ist + m, 0, offsetof(IterState, resid_last), st));
-
+struct SweepSet {
+  bfcs_plan P = nullptr;
+  int B = 0;
+  double tol = 0.0;
+  bfcs_lame C0{};
+  const double* E0 = nullptr;
+  int maxdim = 0;
   GArgs<R> ga{};
-  ga.spec = spec;
-  ga.bhat = (const C2<R>*)P->bhat;
-  ga.dprev = (C2<R>*)P->dprev;
-  ga.g = g;
-  ga.lam0 = (R)C0.lambda;
-  ga.mu0 = (R)C0.mu;
-  for (int c = 0; c < 6; ++c) ga.E[c] = (R)E0[c];
-  ga.inv_n = (R)(1.0 / (double)g.n);
-  ga.tw = twz;
-  ga.part = P->part;
-  ga.st = P->ist;
-  ga.use_me = 1;
-  for (int m = 0; m < B; ++m)
-    for (int c = 0; c < 6; ++c) ga.mE[m][c] = (R)P->mem_host[m].E[c];
-  ga.spec_ms = sms;
-  ga.b_ms = 3 * g.cs;
-  ga.d_ms = 3 * g.cs;
-  ga.part_ms = P->ngreen;
-
   CArgs<R> cy{};
-  cy.data = spec;
-  cy.ms = sms;
-  cy.g = g;
-  cy.ncomp = 6;
-  cy.axis = 1;
-  cy.tw = twy;
-
   XArgs<R> xa{};
-  xa.g = g;
-  xa.spec_in = spec;
-  xa.spec_out = spec;
-  xa.spec_ms = sms;
-  xa.tab = tab;
-  xa.tw = twx;
-  xa.ncomp = 6;
 
-  // eps^0 = eps^{b(0)} + E for every member, d_prev = 0
-  ga.mode = GM_INIT;
-  ga.skip_done = 0;
-  CK(launch_zgreen_b<R>(ga, B, st));
-  cy.st = nullptr;
-  CK(launch_colpass_b<R>(cy, +1, B, st));
-  // A warm-started member instead starts from its eps_init: the state kept
-  // between sweeps is the x-transform of eps scaled by 1/nx (y, z in real space).
-  if (any_warm) {
-    for (int m = 0; m < B; ++m) {
-      if (!P->mem_host[m].warm) continue;
-      XArgs<R> xw{};
-      xw.g = g;
-      xw.real_in = (const R*)P->mem_host[m].eps_init;
-      xw.spec_out = spec + m * sms;
-      xw.out_scale = (R)(1.0 / g.nx);
-      xw.ncomp = 6;
-      xw.mode = XM_R2C;
-      xw.tw = twx;
-      CK(launch_xpass<R>(xw, st));
-    }
+  void prepare(bfcs_plan plan, int batch, const PhaseTab<R>& tab, bfcs_lame c0, const double* e0, double t) {
+    P = plan; B = batch; tol = t; C0 = c0; E0 = e0;
+    const Geo g = P->g;
+    maxdim = std::max(g.nx, std::max(g.ny, g.nz));
+    const long long sms = 6 * g.cs;
+    ga.spec = (C2<R>*)P->spec;
+    ga.bhat = (const C2<R>*)P->bhat;
+    ga.dprev = (C2<R>*)P->dprev;
+    ga.g = g;
+    ga.lam0 = (R)C0.lambda;
+    ga.mu0 = (R)C0.mu;
+    for (int c = 0; c < 6; ++c) ga.E[c] = (R)E0[c];
+    ga.inv_n = (R)(1.0 / (double)g.n);
+    ga.tw = (const C2<R>*)P->tw[2];
+    ga.part = P->part;
+    ga.st = P->ist;
+    ga.use_me = 1;
+    for (int m = 0; m < B; ++m)
+      for (int c = 0; c < 6; ++c) ga.mE[m][c] = (R)P->mem_host[m].E[c];
+    ga.spec_ms = sms;
+    ga.b_ms = 3 * g.cs;
+    ga.d_ms = 3 * g.cs;
+    ga.part_ms = P->ngreen;
+    cy.data = (C2<R>*)P->spec;
+    cy.ms = sms;
+    cy.g = g;
+    cy.ncomp = 6;
+    cy.axis = 1;
+    cy.tw = (const C2<R>*)P->tw[1];
+    cy.variant = P->col_variant;
+    xa.g = g;
+    xa.spec_in = (C2<R>*)P->spec;
+    xa.spec_out = (C2<R>*)P->spec;
+    xa.spec_ms = sms;
+    xa.tab = tab;
+    xa.tw = (const C2<R>*)P->tw[0];
+    xa.ncomp = 6;
+    fill_xm(xa, P->mem_host, B, XIN_NONE, 0);
   }
 
-  P->prof_used = 0;
-  const int prof_cap = (int)P->prof_sweep.size();
-  auto timed = [&](int kind, int sweep, cudaError_t (*fn)(const void*, int, int, cudaStream_t), const void* args,
-                   int dir) -> cudaError_t {
-    const bool t = P->prof_kind == kind && P->prof_used < prof_cap && sweep >= 0;
-    if (t && cudaEventRecord(P->prof_ev[2 * P->prof_used], st) != cudaSuccess) return cudaErrorUnknown;
-    const cudaError_t e = fn(args, dir, B, st);
-    if (t) {
-      if (cudaEventRecord(P->prof_ev[2 * P->prof_used + 1], st) != cudaSuccess) return cudaErrorUnknown;
-      P->prof_sweep[P->prof_used++] = sweep;
+  // eps^0 = eps^{b(0)} + E for every member, d_prev = 0; a warm-started member
+  // instead starts from its eps_init: the state kept between sweeps is the
+  // x-transform of eps scaled by 1/nx (y, z in real space).  On the plan's stream.
+  int init(bool any_warm) {
+    cudaStream_t st = P->st;
+    for (int m = 0; m < B; ++m)
+      CK(cudaMemsetAsync(P->ist + m, 0, offsetof(IterState, resid_last), st));
+    ga.mode = GM_INIT;
+    ga.skip_done = 0;
+    CK(launch_zgreen_b<R>(ga, B, st));
+    cy.st = nullptr;
+    cy.ncomp = 6;
+    CK(launch_colpass_b<R>(cy, +1, B, st));
+    if (any_warm) {
+      for (int m = 0; m < B; ++m) {
+        if (!P->mem_host[m].warm) continue;
+        XArgs<R> xw{};
+        xw.g = P->g;
+        xw.real_in = (const R*)P->mem_host[m].eps_init;
+        xw.spec_out = (C2<R>*)P->spec + m * 6 * P->g.cs;
+        xw.out_scale = (R)(1.0 / P->g.nx);
+        xw.ncomp = 6;
+        xw.mode = XM_R2C;
+        xw.tw = (const C2<R>*)P->tw[0];
+        CK(launch_xpass<R>(xw, st));
+      }
     }
-    return e;
-  };
-  auto run_x = [](const void* a, int, int b, cudaStream_t q) { return launch_xpass_b<R>(*(const XArgs<R>*)a, b, q); };
-  auto run_c = [](const void* a, int dir, int b, cudaStream_t q) {
-    return launch_colpass_b<R>(*(const CArgs<R>*)a, dir, b, q);
-  };
-  auto run_g = [](const void* a, int, int b, cudaStream_t q) { return launch_zgreen_b<R>(*(const GArgs<R>*)a, b, q); };
-  // one sweep for all members; identical launches every sweep (graph-capturable);
-  // `sweep` is only used to label profiled launches (-1 inside graphs)
-  fill_xm(xa, P->mem_host, B, XIN_NONE, 0);
-  auto enqueue_sweep = [&](int sweep) -> int {
+    P->prof_used = 0;
+    return BFCS_OK;
+  }
+
+  // one sweep for all members on stream q; identical launches every sweep
+  // (graph-capturable); `sweep` labels profiled launches (-1: not profiled)
+  int enqueue(cudaStream_t q, int sweep) {
+    const int prof_cap = (int)P->prof_sweep.size();
+    auto timed = [&](int kind, auto&& fn) -> cudaError_t {
+      const bool t = P->prof_kind == kind && P->prof_used < prof_cap && sweep >= 0;
+      if (t && cudaEventRecord(P->prof_ev[2 * P->prof_used], q) != cudaSuccess) return cudaErrorUnknown;
+      const cudaError_t e = fn();
+      if (t) {
+        if (cudaEventRecord(P->prof_ev[2 * P->prof_used + 1], q) != cudaSuccess) return cudaErrorUnknown;
+        P->prof_sweep[P->prof_used++] = sweep;
+      }
+      return e;
+    };
     xa.mode = XM_SWEEP;
     xa.st = P->ist;
-    CK(timed(1, sweep, run_x, &xa, 0));
+    CK(timed(1, [&] { return launch_xpass_b<R>(xa, B, q); }));
     cy.st = P->ist;
     cy.ncomp = 6;
-    CK(timed(2, sweep, run_c, &cy, -1));
+    CK(timed(2, [&] { return launch_colpass_b<R>(cy, -1, B, q); }));
     ga.mode = GM_SWEEP;
     ga.skip_done = 1;
-    CK(timed(3, sweep, run_g, &ga, 0));
-    CK(timed(2, sweep, run_c, &cy, +1));
-    CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda,
-                           C0.mu, E0, g.n, maxdim, GM_SWEEP, 0, P->stall_window, B, st));
+    CK(timed(3, [&] { return launch_zgreen_b<R>(ga, B, q); }));
+    CK(timed(2, [&] { return launch_colpass_b<R>(cy, +1, B, q); }));
+    CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda, C0.mu,
+                           E0, P->g.n, maxdim, GM_SWEEP, 0, P->stall_window, B, q));
+    return BFCS_OK;
+  }
+
+  // eps^S, sigma^S in real space; residual of eps^S; u^S; per-member infos.
+  // On the plan's stream; ends with a bounded wait.
+  int finalize(bfcs_info* infos) {
+    cudaStream_t st = P->st;
+    const long long sms = 6 * P->g.cs;
+    xa.mode = XM_SWEEP;
+    fill_xm(xa, P->mem_host, B, XIN_NONE, XOUT_EPS | XOUT_SIG);
+    xa.st = nullptr;
+    CK(launch_xpass_b<R>(xa, B, st));
+    cy.st = nullptr;
+    cy.ncomp = 6;
+    CK(launch_colpass_b<R>(cy, -1, B, st));
+    ga.mode = GM_FINAL;
+    ga.skip_done = 0;
+    CK(launch_zgreen_b<R>(ga, B, st));
+    CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda, C0.mu,
+                           E0, P->g.n, maxdim, GM_FINAL, 0, 0, B, st));
+    cy.ncomp = 3;
+    CK(launch_colpass_b<R>(cy, +1, B, st));
+    XArgs<R> xu{};
+    xu.g = P->g;
+    xu.spec_in = (C2<R>*)P->spec;
+    xu.spec_ms = sms;
+    fill_xm(xu, P->mem_host, B, XIN_NONE, XOUT_U);
+    xu.ncomp = 3;
+    xu.mode = XM_C2R;
+    xu.tw = (const C2<R>*)P->tw[0];
+    CK(launch_xpass_b<R>(xu, B, st));   // members without u_out write nothing
+    IterState* hf = P->ist_host + 2 * P->max_batch;
+    CK(cudaMemcpyAsync(hf, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    const int w = sync_stream(P);
+    if (w != BFCS_OK) return w;
+    P->last_iters = hf[0].iters;
+    P->last_batch = B;
+    for (int k = 0; k < P->prof_used; ++k) {
+      if (P->prof_sweep[k] >= hf[0].iters) continue;     // launches of sweeps skipped on device
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, P->prof_ev[2 * k], P->prof_ev[2 * k + 1]) != cudaSuccess)
+        return BFCS_ERR_CUDA;
+      P->prof_ms += ms;
+      P->prof_launches += 1;
+    }
+    P->prof_used = 0;
+    int worst = BFCS_OK;
+    for (int m = 0; m < B; ++m) {
+      const IterState& h = hf[m];
+      int status = BFCS_OK;
+      if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
+      else if (tol > 0 && (!h.done || h.stalled)) status = BFCS_NOT_CONVERGED;
+      if (infos != nullptr) {
+        infos[m].iters = h.iters;
+        infos[m].status = status;
+        infos[m].resid = h.resid_final;
+        infos[m].resid_prev = h.resid_last;
+        infos[m].precision_path = sizeof(R) == 8 ? 1 : 0;
+        infos[m].stalled = h.stalled;
+      }
+      if (severity(status) > severity(worst)) worst = status;
+    }
+    return worst;
+  }
+};
+
+// The sweep loop of one or more sweep sets (plans of possibly different grid
+// sizes), after their init().  It runs on the first plan's private stream
+// (capturable even when a caller's stream is the legacy default stream); every
+// other plan's private stream forks from it and joins it again, so one CUDA
+// graph launch advances every set by graph_sweeps sweeps, the sets running
+// side by side on the GPU.  The host reads the device states of chunk k-1
+// while chunk k runs; the contraction rate of two observed residuals gives the
+// sweeps still needed by the slowest member of any set, which sizes the next
+// chunk; once the chunk in flight is expected to finish every member, the host
+// waits for it before sending more (sweeps enqueued past convergence are
+// skipped on the device, but still cost their launches).  Each set's own
+// stream waits for the loop before its finalize().
+template <typename R>
+int run_sets(std::vector<SweepSet<R>*>& sets, int maxit) {
+  const int S = (int)sets.size();
+  bfcs_plan P0 = sets[0]->P;
+  cudaStream_t const main = P0->loop_st;
+  std::vector<cudaEvent_t> evs;                      // fork/join events of this call
+  struct EvGuard {
+    std::vector<cudaEvent_t>& v;
+    ~EvGuard() { for (cudaEvent_t e : v) cudaEventDestroy(e); }
+  } evguard{evs};
+  auto new_event = [&](cudaEvent_t* e) -> bool {
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return false;
+    evs.push_back(*e);
+    return true;
+  };
+  // the loop stream starts after every set's stream (their INIT work)
+  for (auto* ss : sets) {
+    cudaEvent_t e;
+    if (!new_event(&e)) return BFCS_ERR_CUDA;
+    CK(cudaEventRecord(e, ss->P->st));
+    CK(cudaStreamWaitEvent(main, e, 0));
+  }
+  // enqueue k sweeps of every set: set 0 on the main stream, the others forked
+  auto enqueue_all = [&](int k, int label0) -> int {
+    cudaEvent_t fork;
+    if (S > 1) {
+      if (!new_event(&fork)) return BFCS_ERR_CUDA;
+      CK(cudaEventRecord(fork, main));
+    }
+    for (int i = 1; i < S; ++i) {
+      cudaStream_t q = sets[i]->P->loop_st;
+      CK(cudaStreamWaitEvent(q, fork, 0));
+      for (int j = 0; j < k; ++j) {
+        const int e = sets[i]->enqueue(q, label0 < 0 ? -1 : label0 + j);
+        if (e != BFCS_OK) return e;
+      }
+    }
+    for (int j = 0; j < k; ++j) {
+      const int e = sets[0]->enqueue(main, label0 < 0 ? -1 : label0 + j);
+      if (e != BFCS_OK) return e;
+    }
+    for (int i = 1; i < S; ++i) {
+      cudaEvent_t join;
+      if (!new_event(&join)) return BFCS_ERR_CUDA;
+      CK(cudaEventRecord(join, sets[i]->P->loop_st));
+      CK(cudaStreamWaitEvent(main, join, 0));
+    }
     return BFCS_OK;
   };
 
-  // The sweep loop runs on the plan's private stream (capturable even when the
-  // caller's stream is the legacy default stream), ordered after and before
-  // the caller's stream with events.
-  CK(cudaEventRecord(P->order_ev[0], st));
-  CK(cudaStreamWaitEvent(P->loop_st, P->order_ev[0], 0));
-  cudaStream_t const caller_st = st;
-  st = P->loop_st;
-
-  // CUDA graph of graph_sweeps sweeps (used when no launch is being profiled)
-  const int G = (P->prof_kind == 0) ? P->graph_sweeps : 0;
+  bool profiling = false;
+  for (auto* ss : sets) profiling = profiling || ss->P->prof_kind != 0;
+  const int G = profiling ? 0 : P0->graph_sweeps;
   cudaGraphExec_t gexec = nullptr;
   if (G > 0 && maxit >= G) {
     cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < G; ++k) {
-      const int e = enqueue_sweep(-1);
-      if (e != BFCS_OK) {
-        cudaStreamEndCapture(st, &graph);
-        if (graph) cudaGraphDestroy(graph);
-        return e;
-      }
+    CK(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+    const int e = enqueue_all(G, -1);
+    const cudaError_t ce = cudaStreamEndCapture(main, &graph);
+    if (e != BFCS_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return e != BFCS_OK ? e : BFCS_ERR_CUDA;
     }
-    CK(cudaStreamEndCapture(st, &graph));
     const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return BFCS_ERR_CUDA;
@@ -434,65 +596,76 @@ int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const do
     ~GraphGuard() { if (g) cudaGraphExecDestroy(g); }
   } guard{gexec};
 
-  // Sweeps in chunks; the host reads the device state of chunk k-1 while chunk
-  // k runs.  From two observed residuals the contraction rate gives the sweeps
-  // still needed (slowest member), which sizes the next chunk; once the chunk
-  // in flight is expected to finish every member, the host waits for it before
-  // sending more (sweeps enqueued past convergence are skipped on the device,
-  // but still cost their launches).
-  int s = 0, chunk = 4, slot = 0;
-  bool pending = false;
-  int last_c = 0;
-  std::vector<int> obs_it(B, -1);
-  std::vector<double> obs_r(B, 0.0);
-  auto all_done = [&](const IterState* h) {
-    for (int m = 0; m < B; ++m)
-      if (!h[m].done) return false;
+  // all members of all sets, in order
+  int total = 0;
+  for (auto* ss : sets) total += ss->B;
+  std::vector<int> obs_it(total, -1);
+  std::vector<double> obs_r(total, 0.0);
+  cudaEvent_t ev[2];
+  if (!new_event(&ev[0]) || !new_event(&ev[1])) return BFCS_ERR_CUDA;
+  auto host_state = [&](int slot, int i) { return sets[i]->P->ist_host + slot * sets[i]->P->max_batch; };
+  auto all_done = [&](int slot) {
+    for (int i = 0; i < S; ++i) {
+      const IterState* h = host_state(slot, i);
+      for (int m = 0; m < sets[i]->B; ++m)
+        if (!h[m].done) return false;
+    }
     return true;
   };
   // sweeps still needed by the slowest member after the observed state (<0: unknown)
-  auto predict = [&](const IterState* h) {
+  auto predict = [&](int slot) {
     double worst = 0.0;
     bool known = true;
-    for (int m = 0; m < B; ++m) {
-      if (h[m].done) continue;
-      const double r = h[m].resid_last;
-      const double tl = P->mem_host[m].tol >= 0 ? P->mem_host[m].tol : tol;
-      if (!(tl > 0) || !(h[m].iters > 0) || !std::isfinite(r) || !(r > 0) || obs_it[m] < 0 ||
-          !(h[m].iters > obs_it[m]) || !(r < obs_r[m])) {
-        known = false;
-      } else {
-        const double rate = std::pow(r / obs_r[m], 1.0 / (h[m].iters - obs_it[m]));
-        worst = std::max(worst, std::log(tl / r) / std::log(rate));
+    int gm = 0;
+    for (int i = 0; i < S; ++i) {
+      const IterState* h = host_state(slot, i);
+      const SweepSet<R>& ss = *sets[i];
+      for (int m = 0; m < ss.B; ++m, ++gm) {
+        if (h[m].done) continue;
+        const double r = h[m].resid_last;
+        const double tl = ss.P->mem_host[m].tol >= 0 ? ss.P->mem_host[m].tol : ss.tol;
+        if (!(tl > 0) || !(h[m].iters > 0) || !std::isfinite(r) || !(r > 0) || obs_it[gm] < 0 ||
+            !(h[m].iters > obs_it[gm]) || !(r < obs_r[gm])) {
+          known = false;
+        } else {
+          const double rate = std::pow(r / obs_r[gm], 1.0 / (h[m].iters - obs_it[gm]));
+          worst = std::max(worst, std::log(tl / r) / std::log(rate));
+        }
+        if (std::isfinite(r) && r > 0) { obs_it[gm] = h[m].iters; obs_r[gm] = r; }
       }
-      if (std::isfinite(r) && r > 0) { obs_it[m] = h[m].iters; obs_r[m] = r; }
     }
     return known ? worst : -1.0;
   };
+  auto read_states = [&](int slot) -> int {
+    for (int i = 0; i < S; ++i)
+      CK(cudaMemcpyAsync(host_state(slot, i), sets[i]->P->ist, sets[i]->B * sizeof(IterState),
+                         cudaMemcpyDeviceToHost, main));
+    CK(cudaEventRecord(ev[slot], main));
+    return BFCS_OK;
+  };
+  int s = 0, chunk = 4, slot = 0;
+  bool pending = false;
+  int last_c = 0;
   while (s < maxit) {
     int c;
     if (gexec != nullptr && maxit - s >= G) {
       c = G * std::max(1, chunk / G);
-      for (int k = 0; k < c; k += G) CK(cudaGraphLaunch(gexec, st));
+      for (int k = 0; k < c; k += G) CK(cudaGraphLaunch(gexec, main));
     } else {
       c = std::min(chunk, maxit - s);
-      for (int k = 0; k < c; ++k) {
-        const int e = enqueue_sweep(s + k);
-        if (e != BFCS_OK) return e;
-      }
+      const int e = enqueue_all(c, s);
+      if (e != BFCS_OK) return e;
     }
     s += c;
-    IterState* hs = P->ist_host + slot * P->max_batch;
-    CK(cudaMemcpyAsync(hs, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
-    CK(cudaEventRecord(P->ev[slot], st));
+    int e = read_states(slot);
+    if (e != BFCS_OK) return e;
     int next = std::min(chunk * 2, 64);
     bool drain = false;
     if (pending) {
-      const int w = wait_event(P->ev[slot ^ 1]);
+      const int w = wait_event(ev[slot ^ 1]);
       if (w != BFCS_OK) return w;
-      const IterState* h = P->ist_host + (slot ^ 1) * P->max_batch;
-      if (all_done(h)) break;
-      const double need = predict(h);
+      if (all_done(slot ^ 1)) break;
+      const double need = predict(slot ^ 1);
       if (need >= 0) {
         const double left = need - last_c;
         if (left <= 0.5) drain = true;
@@ -504,77 +677,35 @@ int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const do
     last_c = c;
     chunk = next;
     if (drain) {
-      const int w = wait_event(P->ev[slot ^ 1]);
+      const int w = wait_event(ev[slot ^ 1]);
       if (w != BFCS_OK) return w;
-      const IterState* h = P->ist_host + (slot ^ 1) * P->max_batch;
-      if (all_done(h)) break;
+      if (all_done(slot ^ 1)) break;
       pending = false;
       chunk = 2;
-      predict(h);
+      predict(slot ^ 1);
     }
   }
+  // back on every set's own stream
+  cudaEvent_t done;
+  if (!new_event(&done)) return BFCS_ERR_CUDA;
+  CK(cudaEventRecord(done, main));
+  for (auto* ss : sets) CK(cudaStreamWaitEvent(ss->P->st, done, 0));
+  return BFCS_OK;
+}
 
-  // back on the caller's stream
-  CK(cudaEventRecord(P->order_ev[1], st));
-  CK(cudaStreamWaitEvent(caller_st, P->order_ev[1], 0));
-  st = caller_st;
-
-  // finalize: eps^S, sigma^S in real space; residual of eps^S; u^S
-  xa.mode = XM_SWEEP;
-  fill_xm(xa, P->mem_host, B, XIN_NONE, XOUT_EPS | XOUT_SIG);
-  xa.st = nullptr;
-  CK(launch_xpass_b<R>(xa, B, st));
-  cy.st = nullptr;
-  cy.ncomp = 6;
-  CK(launch_colpass_b<R>(cy, -1, B, st));
-  ga.mode = GM_FINAL;
-  ga.skip_done = 0;
-  CK(launch_zgreen_b<R>(ga, B, st));
-  CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda, C0.mu,
-                         E0, g.n, maxdim, GM_FINAL, 0, 0, B, st));
-  cy.ncomp = 3;
-  CK(launch_colpass_b<R>(cy, +1, B, st));
-  XArgs<R> xu{};
-  xu.g = g;
-  xu.spec_in = spec;
-  xu.spec_ms = sms;
-  fill_xm(xu, P->mem_host, B, XIN_NONE, XOUT_U);
-  xu.ncomp = 3;
-  xu.mode = XM_C2R;
-  xu.tw = twx;
-  CK(launch_xpass_b<R>(xu, B, st));   // members without u_out write nothing (null rows skipped below)
-  IterState* hf = P->ist_host + 2 * P->max_batch;
-  CK(cudaMemcpyAsync(hf, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
-  const int w = sync_stream(P);
-  if (w != BFCS_OK) return w;
-  P->last_iters = hf[0].iters;
-  P->last_batch = B;
-  for (int k = 0; k < P->prof_used; ++k) {
-    if (P->prof_sweep[k] >= hf[0].iters) continue;     // launches of sweeps skipped on device
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, P->prof_ev[2 * k], P->prof_ev[2 * k + 1]) != cudaSuccess)
-      return BFCS_ERR_CUDA;
-    P->prof_ms += ms;
-    P->prof_launches += 1;
-  }
-  P->prof_used = 0;
-  int worst = BFCS_OK;
-  for (int m = 0; m < B; ++m) {
-    const IterState& h = hf[m];
-    int status = BFCS_OK;
-    if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
-    else if (tol > 0 && (!h.done || h.stalled)) status = BFCS_NOT_CONVERGED;
-    if (infos != nullptr) {
-      infos[m].iters = h.iters;
-      infos[m].status = status;
-      infos[m].resid = h.resid_final;
-      infos[m].resid_prev = h.resid_last;
-      infos[m].precision_path = sizeof(R) == 8 ? 1 : 0;
-      infos[m].stalled = h.stalled;
-    }
-    if (severity(status) > severity(worst)) worst = status;
-  }
-  return worst;
+// Algorithm 1 for B members of one grid, advancing together: each sweep is
+// one launch per pass for all members; converged members skip on the device.
+template <typename R>
+int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const double* E0, double tol,
+              int maxit, bfcs_info* infos, bool any_warm) {
+  SweepSet<R> ss;
+  ss.prepare(P, B, tab, C0, E0, tol);
+  int e = ss.init(any_warm);
+  if (e != BFCS_OK) return e;
+  std::vector<SweepSet<R>*> sets{&ss};
+  e = run_sets<R>(sets, maxit);
+  if (e != BFCS_OK) return e;
+  return ss.finalize(infos);
 }
 
 Member make_member(const int8_t* phase, const int shift[3], const double* E, const void* b,
@@ -662,6 +793,58 @@ int solve_batch_impl(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, co
     if (e != BFCS_OK) return e;
     const int s = run_batch<R>(P, B, tab, C0, pr[start].E, tol, maxit, infos != nullptr ? infos + start : nullptr,
                                warm);
+    if (s < 0) return s;
+    if (severity(s) > severity(worst)) worst = s;
+  }
+  return worst;
+}
+
+// bfcs_solve_group: batches of different grids (one plan each) advancing
+// together; one graph launch per chunk runs every plan's sweeps side by side.
+template <typename R>
+int solve_group_impl(int n, const bfcs_group_item* items, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                     double tol, int maxit) {
+  int e = check_material(nph, phases, C0);
+  if (e != BFCS_OK) return e;
+  if (!(tol >= 0) || maxit < 0) return BFCS_ERR_INVALID_ARG;
+  const PhaseTab<R> tab = make_tab<R>(nph, phases, C0);
+  std::vector<SweepSet<R>> sets(n);
+  std::vector<SweepSet<R>*> ptrs;
+  for (int i = 0; i < n; ++i) {
+    bfcs_plan P = items[i].plan;
+    const bfcs_problem* pr = items[i].problems;
+    const int B = items[i].batch;
+    std::vector<Member> mem;
+    std::vector<const int8_t*> ph;
+    std::vector<const void*> bs;
+    bool warm = false;
+    for (int m = 0; m < B; ++m) {
+      if (pr[m].phase == nullptr || pr[m].b == nullptr || pr[m].eps_out == nullptr) return BFCS_ERR_INVALID_ARG;
+      if (pr[m].eps_init != nullptr && maxit < 1) return BFCS_ERR_INVALID_ARG;
+      for (int c = 0; c < 6; ++c)
+        if (!std::isfinite(pr[m].E[c])) return BFCS_ERR_INVALID_ARG;
+      mem.push_back(make_member(pr[m].phase, pr[m].shift, pr[m].E, pr[m].b, pr[m].eps_init,
+                                SolveOut{pr[m].eps_out, pr[m].sig_out, pr[m].u_out}));
+      ph.push_back(pr[m].phase);
+      bs.push_back(pr[m].b);
+      warm = warm || pr[m].eps_init != nullptr;
+    }
+    e = validate_members<R>(P, B, ph.data(), bs.data(), nph);
+    if (e != BFCS_OK) return e;
+    e = upload_members(P, B, mem.data());
+    if (e != BFCS_OK) return e;
+    e = transform_members<R>(P, B);
+    if (e != BFCS_OK) return e;
+    sets[i].prepare(P, B, tab, C0, pr[0].E, tol);
+    e = sets[i].init(warm);
+    if (e != BFCS_OK) return e;
+    ptrs.push_back(&sets[i]);
+  }
+  e = run_sets<R>(ptrs, maxit);
+  if (e != BFCS_OK) return e;
+  int worst = BFCS_OK;
+  for (int i = 0; i < n; ++i) {
+    const int s = sets[i].finalize(items[i].infos);
     if (s < 0) return s;
     if (severity(s) > severity(worst)) worst = s;
   }
@@ -1041,15 +1224,16 @@ const char* bfcs_status_string(int s) {
 int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int flags, void* stream) {
   if (out == nullptr) return BFCS_ERR_INVALID_ARG;
   *out = nullptr;
+  const int prec = flags & 3;
   if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz) || max_batch < 1 || max_batch > kMaxBatch ||
-      (flags != BFCS_FP32 && flags != BFCS_FP64 && flags != BFCS_MIXED))
+      (prec != BFCS_FP32 && prec != BFCS_FP64 && prec != BFCS_MIXED) || (flags & ~(3 | BFCS_AUTOTUNE)) != 0)
     return BFCS_ERR_INVALID_ARG;
   bfcs_plan P = new bfcs_plan_s();
   P->nx = nx; P->ny = ny; P->nz = nz;
   P->max_batch = max_batch;
   P->flags = flags;
-  P->fp64 = flags == BFCS_FP64;
-  P->mixed = flags == BFCS_MIXED;
+  P->fp64 = prec == BFCS_FP64;
+  P->mixed = prec == BFCS_MIXED;
   P->st = (cudaStream_t)stream;
   P->g.nx = nx; P->g.ny = ny; P->g.nz = nz;
   P->g.mx = nx / 2 + 1;
@@ -1106,6 +1290,16 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   }
   if (cudaMemset(P->ist, 0, MB * sizeof(IterState)) != cudaSuccess) { free_plan(P); return BFCS_ERR_CUDA; }
   if (const char* gs = std::getenv("BFCS_GRAPH_SWEEPS")) P->graph_sweeps = std::max(0, std::atoi(gs));
+  if (!P->fp64) {
+    const char* cv = std::getenv("BFCS_COL_VARIANT");
+    if (cv != nullptr) {
+      const int v = std::atoi(cv);
+      P->col_variant = col_variant_valid(v, ny) ? v : 0;
+    } else if (flags & BFCS_AUTOTUNE) {
+      const int e = autotune(P);
+      if (e != BFCS_OK) { free_plan(P); return e; }
+    }
+  }
   *out = P;
   return BFCS_OK;
 }
@@ -1210,6 +1404,28 @@ int bfcs_solve_batched(bfcs_plan P, int batch, const bfcs_problem* pr, int nph, 
   return worst;
 }
 
+int bfcs_solve_group(int nitems, const bfcs_group_item* items, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                     double tol, int maxit) {
+  if (nitems < 1 || nitems > BFCS_MAX_GROUP || items == nullptr) return BFCS_ERR_INVALID_ARG;
+  for (int i = 0; i < nitems; ++i) {
+    const bfcs_plan P = items[i].plan;
+    if (P == nullptr || items[i].batch < 1 || items[i].batch > P->max_batch || items[i].problems == nullptr)
+      return BFCS_ERR_INVALID_ARG;
+    if (P->mixed) return BFCS_ERR_UNSUPPORTED;
+    if (P->fp64 != items[0].plan->fp64) return BFCS_ERR_INVALID_ARG;
+    for (int k = 0; k < i; ++k)
+      if (items[k].plan == P) return BFCS_ERR_INVALID_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  const int s = items[0].plan->fp64 ? solve_group_impl<double>(nitems, items, nph, phases, C0, tol, maxit)
+                                    : solve_group_impl<float>(nitems, items, nph, phases, C0, tol, maxit);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < nitems; ++i)
+    if (items[i].infos != nullptr)
+      for (int m = 0; m < items[i].batch; ++m) items[i].infos[m].ms = ms;
+  return s;
+}
+
 int bfcs_translate_average(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases,
                            bfcs_lame C0, const void* b, const double E[6], int nshift,
                            const int32_t* shifts, double tol, int maxit, double* avg_out,
@@ -1222,6 +1438,16 @@ int bfcs_translate_average(bfcs_plan P, const int8_t* phase, int nph, const bfcs
                                           avg_out, hits_out, infos)
                  : translate_impl<float>(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit,
                                          avg_out, hits_out, infos);
+}
+
+int bfcs_plan_tuning(bfcs_plan P, int* col_variant, int* col_tile, int* col_swap, double* variant_ms) {
+  if (P == nullptr) return BFCS_ERR_INVALID_ARG;
+  if (col_variant) *col_variant = P->col_variant;
+  if (col_tile) *col_tile = col_variant_tile(P->col_variant);
+  if (col_swap) *col_swap = col_variant_swap(P->col_variant) ? 1 : 0;
+  if (variant_ms)
+    for (int v = 0; v < kColVariants; ++v) variant_ms[v] = P->col_variant_ms[v];
+  return BFCS_OK;
 }
 
 int bfcs_surrogate_infer(bfcs_plan P, const void* weights, const void* b, const int8_t* phase, int nph,

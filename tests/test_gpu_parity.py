@@ -230,6 +230,90 @@ def test_graph_and_stream_sweeps_identical(monkeypatch):
     assert torch.equal(out[0][0], out[1][0])
 
 
+# ---------------------------------------------------------------- a13 autotuned y-pass variants
+TUNE_CASES = {
+    "c1_32cubed": W.config_c1(),                                   # ny = 32 = 8 x 4
+    "tall_16x96x12": small_problem((16, 96, 12), (16, 48, 12), [[16, 48, 12, 64, 1]], (8.0, 48.0, 6.0), 5.0),
+}
+
+
+@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("name", sorted(TUNE_CASES))
+def test_every_y_pass_variant_matches_oracle(name, variant, monkeypatch):
+    """Each column tile / factor order computes the same sweeps (FP32 rounding only)."""
+    p = TUNE_CASES[name]
+    monkeypatch.setenv("BFCS_COL_VARIANT", str(variant))
+    ph, b = gpu_inputs(p, "fp32")
+    ph_o, b_o = oracle_inputs(p)
+    sweeps = 10
+    with api.Plan(p.dims, "fp32") as plan:
+        t = plan.tuning()
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, tol=0, maxit=sweeps)
+    ref = O.solve(ph_o, p.phases, p.c0, b_o, tol=0, maxit=sweeps)
+    ny = p.dims[1]
+    valid = variant == 0 or (ny >= 32 and (variant < 3 or ny not in (64, 256)))
+    assert t["variant"] == (variant if valid else 0)
+    for a, key in ((eps, "eps"), (sig, "sig"), (u, "u")):
+        assert rel(a.cpu().numpy(), ref[key]) < TOL["fp32"], (variant, key)
+
+
+def test_autotuned_plan_reports_and_uses_its_choice(monkeypatch):
+    p = W.config_c2(n=128, cell=32, bf_radius=12.0)
+    ph, b = gpu_inputs(p, "fp32")
+    monkeypatch.delenv("BFCS_COL_VARIANT", raising=False)
+    with api.Plan(p.dims, "fp32", max_batch=2, autotune=True) as plan:
+        t = plan.tuning()
+        eps, _, _, info = plan.solve(ph, p.phases, p.c0, b, tol=0, maxit=6)
+    assert 0 <= t["variant"] < 6 and t["variant_ms"][t["variant"]] > 0
+    assert t["variant_ms"][t["variant"]] == min(v for v in t["variant_ms"] if v > 0)
+    assert t["tile"] in (8, 16, 32)
+    monkeypatch.setenv("BFCS_COL_VARIANT", str(t["variant"]))
+    with api.Plan(p.dims, "fp32") as plan:
+        eps2, _, _, _ = plan.solve(ph, p.phases, p.c0, b, tol=0, maxit=6)
+    assert torch.equal(eps, eps2)
+
+
+# ---------------------------------------------------------------- a13 mixed grid sizes in one loop
+GROUP = [("c1_32cubed", [((0, 0, 0), (0,) * 6), ((5, 3, 11), (0.01, 0, 0, 0, 0, 0.002))]),
+         ("aniso_12x32x24", [((0, 0, 0), (0,) * 6), ((11, 31, 23), (0, -0.003, 0, 0.001, 0, 0))]),
+         ("tall_16x96x12", [((3, 7, 1), (0,) * 6)])]     # all three share the phases and C0 of C1
+
+
+def _group_case(name):
+    return CASES[name] if name in CASES else TUNE_CASES[name]
+
+
+@pytest.mark.parametrize("precision,tol,maxit", [("fp32", 0.0, 9), ("fp32", 1e-4, 400), ("fp64", 0.0, 7)])
+def test_group_of_grids_equals_separate_batches(precision, tol, maxit):
+    """Three grids advancing in one graph-launched loop give every member exactly
+    what its own batched solve gives (same sweeps), and match the oracle."""
+    cases = [(name, _group_case(name), specs) for name, specs in GROUP]
+    p0 = cases[0][1]
+    plans = [api.Plan(p.dims, precision, max_batch=len(specs)) for _, p, specs in cases]
+    try:
+        groups, inputs = [], []
+        for plan, (name, p, specs) in zip(plans, cases):
+            ph, b = gpu_inputs(p, precision)
+            inputs.append((ph, b))
+            groups.append((plan, [dict(phase=ph, b=b, E=E, shift=sh) for sh, E in specs]))
+        out = api.solve_group(groups, p0.phases, p0.c0, tol=tol, maxit=maxit)
+        for plan, (name, p, specs), (ph, b), (members, infos) in zip(plans, cases, inputs, out):
+            ref_m, ref_i = plan.solve_batched([dict(phase=ph, b=b, E=E, shift=sh) for sh, E in specs],
+                                              p0.phases, p0.c0, tol=tol, maxit=maxit)
+            for mem, rm, inf, ri in zip(members, ref_m, infos, ref_i):
+                assert inf.iters == ri.iters and inf.status == ri.status, name
+                for key in ("eps_out", "sig_out", "u_out"):
+                    assert torch.equal(mem[key], rm[key]), (name, key)
+            if tol == 0.0:
+                sh, E = specs[-1]
+                ph_o, b_o = oracle_inputs(p)
+                ref = O.solve(O.translate(ph_o, sh), p0.phases, p0.c0, b_o, E, tol=0, maxit=maxit)
+                assert rel(members[-1]["eps_out"].cpu().numpy(), ref["eps"]) < TOL[precision], name
+    finally:
+        for plan in plans:
+            plan.close()
+
+
 # ---------------------------------------------------------------- errors
 def test_error_statuses():
     p = CASES["aniso_12x32x24"]
