@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--contrast", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the translated-averaging and mixed-grid group measurements")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the solves/s comparison (64 solves at 64^3: plain, batched, batched + network)")
     ap.add_argument("--sweeps-only", type=int, default=0,
@@ -245,7 +247,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    plan = api.Plan(p.dims, "mixed")          # FP32 sweeps + FP64 defect correction
+    plan = api.Plan(p.dims, "mixed", autotune=True)   # FP32 sweeps + FP64 defect correction
     stream = plan.stream
     eps = torch.empty((6, nz, ny, nx), dtype=torch.float64, device=dev)
     sig = torch.empty_like(eps)
@@ -355,6 +357,7 @@ def run_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"one Algorithm-1 sweep of the same {args.n}^3 problem (oracle setup untimed), "
                          f"{tcpu:.1f} s, FP64 numpy/scipy single thread"}
+    extras = None if args.no_extras else measure_extras(api, torch)
     warm = None
     if not args.no_warm_start:
         from paper_2601_00822_gb300 import surrogate as S
@@ -389,10 +392,71 @@ def run_ours(args):
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "warm_start": warm,
+        "tuning": plan.tuning(),
+        "extras": extras,
     }
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_extras(api, torch):
+    """Two secondary measurements (rank 0): (1) translated averaging of config C3
+    (128^3, 8^3 cells of 16^3 with one R = 5.8 sphere, contrast 10, a = 6, 4^3 = 64
+    shifts of stride 4) to residual 1e-6 with the batched mixed ladder; (2) one
+    bfcs_solve_group of 16 members on each of 64^3, 96^3 and 128^3 (config C2
+    microstructure at each size, FP32, residual 1e-4) against the same three
+    batches solved one grid after the other."""
+    from paper_2601_00822_gb300 import workloads as W
+    out = {}
+    p = W.config_c3()
+    shifts = W.c3_shifts()
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    with api.Plan(p.dims, "mixed", max_batch=16, autotune=True) as plan:
+        plan.translate_average(ph, p.phases, p.c0, b, shifts[:16], tol=p.tol, maxit=p.maxit)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, infos = plan.translate_average(ph, p.phases, p.c0, b, shifts, tol=p.tol, maxit=p.maxit)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    nvox = p.dims[0] * p.dims[1] * p.dims[2]
+    sw = sum(i.iters for i in infos)
+    out["translated_averaging"] = {
+        "workload": "C3: 128^3, 64 shifts, contrast 10, residual 1e-6, mixed ladder, max_batch 16",
+        "seconds": t, "shifts_per_s": len(shifts) / t, "voxel_iter_per_s": nvox * sw / t,
+        "mean_sweeps": sw / len(shifts), "max_resid": max(i.resid for i in infos)}
+    groups = []
+    for n in (64, 96, 128):
+        q = W.config_c2(n=n, cell=32 if n % 32 == 0 else 16, bf_radius=24.0 * n / 256.0)
+        phq = api.voxelize(q.dims, q.cell, q.spheres)
+        bq = api.body_force(q.dims, q.bf_centre, q.bf_radius, "fp32")
+        plan = api.Plan(q.dims, "fp32", max_batch=16, autotune=True)
+        members = [dict(phase=phq, b=bq, shift=(3 * k % n, 5 * k % n, 7 * k % n), sig_out=None, u_out=None)
+                   for k in range(16)]
+        groups.append((plan, members, q))
+    ph0 = groups[0][2]
+    api.solve_group([(pl, m) for pl, m, _ in groups], ph0.phases, ph0.c0, tol=1e-4, maxit=5000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = api.solve_group([(pl, m) for pl, m, _ in groups], ph0.phases, ph0.c0, tol=1e-4, maxit=5000)
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for pl, m, _ in groups:
+        pl.solve_batched(m, ph0.phases, ph0.c0, tol=1e-4, maxit=5000)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    vox = sum(q.dims[0] * q.dims[1] * q.dims[2] * sum(i.iters for i in infos)
+              for (_, _, q), (_, infos) in zip(groups, res))
+    out["group_solve"] = {
+        "workload": "16 members each on 64^3, 96^3, 128^3 (C2 microstructure, contrast 10), FP32, residual 1e-4",
+        "grouped_solves_per_s": 48 / tg, "separate_solves_per_s": 48 / ts,
+        "grouped_voxel_iter_per_s": vox / tg,
+        "tuning": [pl.tuning()["variant"] for pl, _, _ in groups]}
+    for pl, _, _ in groups:
+        pl.close()
+    return out
 
 
 def run_sweeps_only(args):
