@@ -50,6 +50,9 @@ def parse():
                     help="skip the translated-averaging and mixed-grid group measurements")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the solves/s comparison (64 solves at 64^3: plain, batched, batched + network)")
+    ap.add_argument("--precision-study", type=int, default=0, metavar="N",
+                    help="config C4 (contrast 1000, vf 0.3) on an N^3 grid: mixed ladder vs all-FP64 GPU "
+                         "solve, errors and sweep counts; prints one JSON line and exits")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling aid: run one FP32 solve of exactly this many sweeps and exit")
     return ap.parse_args()
@@ -459,6 +462,44 @@ def measure_extras(api, torch):
     return out
 
 
+def run_precision_study(args):
+    """C4 precision study: the same contrast-1000 problem solved (1) by the mixed
+    ladder (FP32 sweeps, FP64 correction) to 1e-6, (2) all-FP64 on the GPU to 1e-6
+    and (3) all-FP64 to 1e-9 as the reference; relative L2 errors of eps, sigma and
+    of the translated averages over 4 shifts, sweep counts and times."""
+    import torch
+    from paper_2601_00822_gb300 import api, workloads as W
+    n = args.precision_study
+    p = W.config_c2(contrast=1000.0, seed=1, n=n, cell=32, vf=0.3, bf_radius=24.0 * n / 256.0)
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    shifts = [(0, 0, 0), (8, 0, 0), (0, 8, 8), (16, 16, 16)]
+    out = {"workload": f"C4 at {n}^3: RSA vf 0.3 in 32^3 cells, Young contrast 1000, a = {p.bf_radius:g}",
+           "runs": {}}
+    fields = {}
+    for name, prec, tol in (("reference_fp64_1e-9", "fp64", 1e-9), ("fp64_1e-6", "fp64", 1e-6),
+                            ("mixed_1e-6", "mixed", 1e-6)):
+        with api.Plan(p.dims, prec) as plan:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            eps, sig, _, info = plan.solve(ph, p.phases, p.c0, b, tol=tol, maxit=500000)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            avg, _, infos = plan.translate_average(ph, p.phases, p.c0, b, shifts, tol=tol, maxit=500000)
+        fields[name] = (eps, sig, avg)
+        out["runs"][name] = {"sweeps": info.iters, "resid": info.resid, "status": info.status, "seconds": t,
+                             "avg_sweeps": [i.iters for i in infos]}
+    ref = fields["reference_fp64_1e-9"]
+
+    def relerr(a, r):
+        return float(torch.linalg.vector_norm(a - r) / torch.linalg.vector_norm(r))
+    for name in ("fp64_1e-6", "mixed_1e-6"):
+        e, s_, a = fields[name]
+        out["runs"][name].update({"eps_rel_l2": relerr(e, ref[0]), "sig_rel_l2": relerr(s_, ref[1]),
+                                  "avg_rel_l2": relerr(a, ref[2])})
+    print(json.dumps(out))
+
+
 def run_sweeps_only(args):
     """One FP32 solve with a fixed number of sweeps (tol = 0) on the bench workload;
     used as the command under ncu (no clocks, no oracle, no end-to-end pass)."""
@@ -477,6 +518,9 @@ def main():
     args = parse()
     if args.sweeps_only > 0:
         run_sweeps_only(args)
+        return
+    if args.precision_study > 0:
+        run_precision_study(args)
         return
     if args.impl == "reference":
         run_reference(args)

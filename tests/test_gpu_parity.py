@@ -409,6 +409,33 @@ def test_mixed_translate_average_against_oracle():
         assert rel(avg[a0:a1], avg_ref[a0:a1]) < 1e-8
 
 
+# ---------------------------------------------------------------- C4: stiff inclusions, contrast 1000
+def test_precision_study_contrast_1000():
+    """C4's microstructure (RSA vf 0.3, Young contrast 1000) at 32^3: FP32 and FP64
+    sweeps match the oracle at a fixed sweep count, and the converged mixed ladder
+    agrees with an all-FP64 GPU solve to within what the tolerances allow."""
+    p = W.config_c2(contrast=1000.0, seed=1, n=32, cell=32, vf=0.3, bf_radius=6.0)
+    ph_o, b_o = oracle_inputs(p)
+    ref = O.solve(ph_o, p.phases, p.c0, b_o, tol=0, maxit=15)
+    for precision in ("fp32", "fp64"):
+        ph, b = gpu_inputs(p, precision)
+        with api.Plan(p.dims, precision) as plan:
+            eps, sig, _, _ = plan.solve(ph, p.phases, p.c0, b, tol=0, maxit=15)
+        assert rel(eps.cpu().numpy(), ref["eps"]) < TOL[precision], precision
+        assert rel(sig.cpu().numpy(), ref["sig"]) < TOL[precision], precision
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    with api.Plan(p.dims, "fp64") as plan:
+        e64, s64, _, i64 = plan.solve(ph, p.phases, p.c0, b, tol=1e-9, maxit=200000)
+    with api.Plan(p.dims, "mixed") as plan:
+        em, sm, _, im = plan.solve(ph, p.phases, p.c0, b, tol=1e-7, maxit=200000)
+    assert i64.status == _lib.OK and im.status == _lib.OK and im.resid <= 1e-7
+    assert i64.iters > 1000            # the slow fixed point of a stiff, high-contrast composite
+    err_e = rel(em.cpu().numpy(), e64.cpu().numpy())
+    err_s = rel(sm.cpu().numpy(), s64.cpu().numpy())
+    assert err_e < 1e-4 and err_s < 1e-4, (err_e, err_s, im.iters, i64.iters)
+
+
 # ---------------------------------------------------------------- full size (256^3, the benchmarked launch)
 def test_full_size_solve_meets_tolerance_independently_checked():
     p = W.config_c2(contrast=10.0, seed=1)
