@@ -136,6 +136,9 @@ cudaError_t launch_defect_final(const ResidSlot* part, int nparts, IterState* st
 template <typename R> cudaError_t launch_colpass(const CArgs<R>& a, int dir, cudaStream_t s);
 template <typename R> cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t s);
 template <typename R> int green_nparts(const Geo& g);
+// residual partial slots per member written by a GM_SWEEP launch of the z pass
+// (fewer than green_nparts when the persistent form runs)
+template <typename R> int green_sweep_parts(const Geo& g);
 template <typename R> cudaError_t launch_xpass_b(const XArgs<R>& a, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_colpass_b(const CArgs<R>& a, int dir, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_zgreen_b(const GArgs<R>& a, int batch, cudaStream_t s);

@@ -444,8 +444,8 @@ struct SweepSet {
     ga.skip_done = 1;
     CK(timed(3, [&] { return launch_zgreen_b<R>(ga, B, q); }));
     CK(timed(2, [&] { return launch_colpass_b<R>(cy, +1, B, q); }));
-    CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda, C0.mu,
-                           E0, P->g.n, maxdim, GM_SWEEP, 0, P->stall_window, B, q));
+    CK(launch_resid_reduce(P->part, green_sweep_parts<R>(P->g), P->ist, P->mem_dev, P->hist, P->hist_cap, tol,
+                           C0.lambda, C0.mu, E0, P->g.n, maxdim, GM_SWEEP, 0, P->stall_window, B, q));
     return BFCS_OK;
   }
 

@@ -314,6 +314,31 @@ def test_group_of_grids_equals_separate_batches(precision, tol, maxit):
             plan.close()
 
 
+@pytest.mark.parametrize("dims", [(64, 64, 64), (96, 128, 48)])
+def test_persistent_z_pass_equals_one_tile_per_block(dims, monkeypatch):
+    """The persistent, double-buffered z/Green pass computes every mode exactly as
+    the one-tile-per-block form (bit-identical fields after fixed sweeps, batched
+    members with one converging early); only the grouping of the residual
+    partial sums differs."""
+    nx, ny, nz = dims
+    p = small_problem(dims, (nx // 2, ny // 2, nz // 2), [[nx // 2, ny // 2, nz // 2, 100, 1]],
+                      (nx / 2, ny / 2, nz / 2), 6.0)
+    ph, b = gpu_inputs(p, "fp32")
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("BFCS_ZGREEN_PERSISTENT", flag)
+        with api.Plan(dims, "fp32", max_batch=3) as plan:
+            members = [dict(phase=ph, b=b, shift=(k, 2 * k, 3 * k)) for k in range(3)]
+            members, infos = plan.solve_batched(members, p.phases, p.c0, tol=0, maxit=12)
+            hist = plan.history()
+            eps, _, _, one = plan.solve(ph, p.phases, p.c0, b, tol=3e-3, maxit=500)
+        out[flag] = ([m["eps_out"].clone() for m in members], hist, eps.clone(), one.iters)
+    for a, b2 in zip(out["0"][0], out["1"][0]):
+        assert torch.equal(a, b2)
+    assert np.allclose(out["0"][1], out["1"][1], rtol=1e-9, atol=0)
+    assert out["0"][3] == out["1"][3] and torch.equal(out["0"][2], out["1"][2])
+
+
 # ---------------------------------------------------------------- errors
 def test_error_statuses():
     p = CASES["aniso_12x32x24"]
