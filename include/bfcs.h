@@ -272,6 +272,10 @@ long long bfcs_net_param_count(void);
 int bfcs_net_create(bfcs_net* out, int nx, int ny, int nz, int max_batch, int flags, void* stream);
 int bfcs_net_destroy(bfcs_net net);
 
+/* Waits for the context's stream and reports whether any network kernel gave
+ * up a bounded wait (BFCS_ERR_TIMEOUT; its outputs are then unspecified). */
+int bfcs_net_status(bfcs_net net);
+
 /* Network input of one sample: x_out (dev, 4 x N float) from the body force b
  * (dev, 3 x N, float for BFCS_FP32 or double for BFCS_FP64 = precision) and
  * the phase map (dev, N int8; shear moduli from phases, host).  With eps (dev

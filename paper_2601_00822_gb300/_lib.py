@@ -33,7 +33,7 @@ EXPORTS = (
     "bfcs_last_history", "bfcs_status_string", "bfcs_kernel_launches", "bfcs_profile_kernel",
     "bfcs_profile_read", "bfcs_body_force_noalloc", "bfcs_net_param_count", "bfcs_net_create",
     "bfcs_net_destroy", "bfcs_net_prepare", "bfcs_net_forward", "bfcs_net_grad", "bfcs_net_adam",
-    "bfcs_net_train_step", "bfcs_net_predict", "bfcs_plan_tuning", "bfcs_solve_group",
+    "bfcs_net_train_step", "bfcs_net_predict", "bfcs_plan_tuning", "bfcs_solve_group", "bfcs_net_status",
 )
 NET_PARAMS = 523654
 NET_TRAIN = 1
@@ -83,6 +83,7 @@ def _declare(lib):
     lib.bfcs_net_param_count.argtypes = []
     lib.bfcs_net_create.argtypes = [C.POINTER(vp), i, i, i, i, i, vp]
     lib.bfcs_net_destroy.argtypes = [vp]
+    lib.bfcs_net_status.argtypes = [vp]
     lib.bfcs_net_prepare.argtypes = [vp, i, vp, vp, i, C.POINTER(Lame), vp, vp, vp]
     lib.bfcs_net_forward.argtypes = [vp, vp, i, vp, vp]
     lib.bfcs_net_grad.argtypes = [vp, vp, i, vp, vp, vp, vp]

@@ -308,6 +308,10 @@ class Net:
         except Exception:
             pass
 
+    def status(self):
+        """bfcs_net_status: raises if a network kernel gave up a bounded wait."""
+        _lib.check(self.lib.bfcs_net_status(self.handle), "bfcs_net_status")
+
     def _vol(self, batch, ch):
         nx, ny, nz = self.dims
         return (batch, ch, nz, ny, nx)

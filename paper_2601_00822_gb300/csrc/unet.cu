@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -311,6 +312,194 @@ bool conv3t_ok(const ConvArgs& a) {
   return a.ksize == 3 && a.in_mode == IN_CONV && a.out_mode == OUT_BF16 && a.v.nx % kTX == 0 &&
          a.v.ny % kTY == 0 && a.v.nz % kTZ == 0 && (a.cin == 16 || a.cin == 32 || a.cin == 64) &&
          a.ldi % 8 == 0 && a.offi % 8 == 0 && a.cout_p % 8 == 0;
+}
+
+// ------------------------------------------------------------------ tcgen05 convolution
+// 3^3 circular convolution on the 5th-generation tensor cores (tcgen05.mma,
+// kind::f16, BF16 operands, FP32 accumulator in tensor memory).  A persistent
+// block of 4 warps keeps the layer's weights in shared memory and walks
+// 128-voxel tiles (8 x-voxels x 16 y-rows x 1 z-slab).  Per tile the circular
+// halo (10 x 18 x 3 voxels, all cin channels) is staged with cp.async in the
+// canonical K-major no-swizzle layout: 8-channel chunk c of halo voxel v at
+// byte (c * NV + v) * 16.  Eight consecutive x-voxels then form one 8 x 16 B
+// core matrix, the next tile row (y + 1) sits HX voxels further (the stride
+// between 8-row groups, SBO) and the next channel chunk NV voxels further
+// (the stride along K, LBO) - so the A operand of every tap is the same
+// descriptor at a different start address.  Weights: chunk c of output
+// channel n of tap t at ((t * KC + c) * N + n) * 16 (SBO = 128 B, LBO = N * 16).
+// One thread issues 27 * cin / 16 MMAs of 128 x N x 16 into the accumulator,
+// tcgen05.commit arrives on an mbarrier, and the four warps read their 32
+// TMEM lanes (= tile voxels) back for bias, activation and the BF16 store.
+// Needs nx % 8 == 0, ny % 16 == 0, cin in {16, 32, 64}, cout_p in {32, 64},
+// IN_CONV / OUT_BF16, ldi, offi, ldo, offo multiples of 8.
+constexpr int kTcX = 8, kTcY = 16;
+constexpr int kTcHX = kTcX + 2, kTcHY = kTcY + 2, kTcHZ = 3, kTcNV = kTcHX * kTcHY * kTcHZ;
+constexpr unsigned kTcSpinLimit = 1u << 26;    // bounded wait on the MMA completion barrier
+
+// halo (rounded to 1 KB) + weights; two to four blocks share an SM for cin <= 32
+size_t conv3tc_smem(int cin, int n) {
+  return ((size_t)kTcNV * (cin / 8) * 16 + 1023) / 1024 * 1024 + (size_t)27 * (cin / 8) * n * 16;
+}
+
+__device__ __forceinline__ uint64_t umma_sdesc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  // start address, leading (K) and stride (M/N) byte offsets in 16-byte units,
+  // descriptor version 1 (bit 46), no swizzle, base offset 0
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ unsigned umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(128, 2) k_conv3_tc(ConvArgs a, int* err) {
+  extern __shared__ __align__(1024) unsigned char smt[];
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ unsigned tmem_base_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int KC = a.cin >> 3, N = a.cout_p;
+  // halo first, weights after it
+  const unsigned h_bytes = (unsigned)kTcNV * KC * 16u;
+  unsigned char* sh = smt;
+  unsigned char* sw = smt + ((h_bytes + 1023u) & ~1023u);
+  const unsigned sw_a = (unsigned)__cvta_generic_to_shared(sw);
+  const unsigned sh_a = (unsigned)__cvta_generic_to_shared(sh);
+  const unsigned mbar_a = (unsigned)__cvta_generic_to_shared(&mbar);
+  const long long nvox = (long long)a.v.nx * a.v.ny * a.v.nz;
+  const int ntx = a.v.nx / kTcX, nty = a.v.ny / kTcY;
+  const int tiles_ps = ntx * nty * a.v.nz;
+  const int total = tiles_ps * a.batch;
+
+  // tensor memory: N columns (32 or 64) x 128 lanes of FP32
+  if (warp == 0) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(&tmem_base_s);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  // weights -> shared memory (core-matrix layout)
+  for (int i = tid; i < 27 * N * KC; i += blockDim.x) {
+    const int c = i % KC, n = (i / KC) % N, tap = i / (KC * N);
+    cp_async16(sw + ((tap * KC + c) * N + n) * 16, a.w + ((long long)tap * N + n) * a.cin + c * 8);
+  }
+  cp_async_wait_all();
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const unsigned tmem = tmem_base_s;
+  const unsigned idesc = umma_idesc_bf16(128, N);
+  unsigned phase = 0;
+  bool ok = true;
+
+  for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+    const int b = tile / tiles_ps;
+    int tt = tile - b * tiles_ps;
+    const int x0 = (tt % ntx) * kTcX;
+    tt /= ntx;
+    const int y0 = (tt % nty) * kTcY, z0 = tt / nty;
+    const bf16* inb = a.in + (long long)b * nvox * a.ldi + a.offi;
+    for (int i = tid; i < kTcNV * KC; i += blockDim.x) {
+      const int v = i / KC, c = i - v * KC;
+      const int hx = v % kTcHX, hy = (v / kTcHX) % kTcHY, hz = v / (kTcHX * kTcHY);
+      const int gx = wrap(x0 + hx - 1, a.v.nx), gy = wrap(y0 + hy - 1, a.v.ny), gz = wrap(z0 + hz - 1, a.v.nz);
+      cp_async16(sh + (c * kTcNV + v) * 16, inb + (((long long)gz * a.v.ny + gy) * a.v.nx + gx) * a.ldi + c * 8);
+    }
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      int first = 1;
+      for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;      // halo offsets of the tap (0..2)
+        const unsigned a0 = sh_a + (unsigned)(((dz * kTcHY + dy) * kTcHX + dx) * 16);
+        for (int kk = 0; kk < KC; kk += 2) {
+          const uint64_t ad = umma_sdesc(a0 + (unsigned)(kk * kTcNV * 16), kTcNV * 16, kTcHX * 16);
+          const uint64_t bd = umma_sdesc(sw_a + (unsigned)((tap * KC + kk) * N * 16), N * 16, 128);
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.eq.u32 p, %4, 0;\n"            // p: accumulate into D (not the first MMA)
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(first));
+          first = 0;
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_a)
+                   : "memory");
+    }
+    // bounded wait for the MMAs of this tile
+    {
+      unsigned done = 0, spins = 0;
+      while (!done) {
+        asm volatile(
+            "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(done)
+            : "r"(mbar_a), "r"(phase)
+            : "memory");
+        if (!done && ++spins > kTcSpinLimit) break;
+      }
+      if (__syncthreads_or(!done)) {     // one decision for the whole block
+        if (tid == 0) atomicExch(err, 1);
+        ok = false;
+      }
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+      // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile voxels (x = r % 8, y = r / 8)
+      const int r = warp * 32 + lane;
+      const long long vox = ((long long)z0 * a.v.ny + y0 + r / kTcX) * a.v.nx + x0 + r % kTcX;
+      bf16* orow = (bf16*)a.out + ((long long)b * nvox + vox) * a.ldo + a.offo;
+      for (int c0 = 0; c0 < N; c0 += 32) {
+        unsigned v[32];
+        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) {
+          __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int col = c0 + q + 2 * u;
+            float f0 = __uint_as_float(v[q + 2 * u]), f1 = __uint_as_float(v[q + 2 * u + 1]);
+            if (a.bias != nullptr) {
+              f0 += a.bias[col % a.bias_mod];
+              f1 += a.bias[(col + 1) % a.bias_mod];
+            }
+            if (a.act) {
+              f0 = f0 > 0.f ? f0 : kSlope * f0;
+              f1 = f1 > 0.f ? f1 : kSlope * f1;
+            }
+            o[u] = __floats2bfloat162_rn(f0, f1);
+          }
+          *reinterpret_cast<uint4*>(orow + c0 + q) = *reinterpret_cast<const uint4*>(o);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();   // TMEM and the halo buffer are free for the next tile
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(N));
+}
+
+bool conv3tc_ok(const ConvArgs& a) {
+  return a.ksize == 3 && a.in_mode == IN_CONV && a.out_mode == OUT_BF16 && a.v.nx % kTcX == 0 &&
+         a.v.ny % kTcY == 0 && (a.cin == 16 || a.cin == 32 || a.cin == 64) && (a.cout_p == 32 || a.cout_p == 64) &&
+         a.ldi % 8 == 0 && a.offi % 8 == 0 && a.ldo % 8 == 0 && a.offo % 8 == 0 &&
+         conv3tc_smem(a.cin, a.cout_p) <= 225 * 1024;
 }
 
 // ------------------------------------------------------------------ weight gradient
@@ -896,6 +1085,7 @@ struct bfcs_net_s {
   double* lden;
   double* den_b;
   unsigned* sbits;           // per-sample max |b|
+  int* err;                  // set by a kernel whose bounded wait expired
 };
 
 namespace {
@@ -911,8 +1101,31 @@ cudaError_t pack_all(bfcs_net_s* N, const float* params) {
 }
 
 // forward GEMM of layer l: in -> out on the grid of level lv (coarse level for an up layer)
-cudaError_t launch_conv(const ConvArgs& a, long long nvox, cudaStream_t st) {
-  if (conv3t_ok(a)) {
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || n < 1)
+      n = 1;
+  }
+  return n;
+}
+
+// BFCS_NET_TCGEN05=0 keeps the convolutions on the mma.sync kernels
+bool tcgen05_enabled() {
+  const char* e = std::getenv("BFCS_NET_TCGEN05");
+  return !(e != nullptr && std::atoi(e) == 0);
+}
+
+cudaError_t launch_conv(const ConvArgs& a, long long nvox, int* err, cudaStream_t st) {
+  if (tcgen05_enabled() && conv3tc_ok(a)) {
+    const long long tiles = (long long)(a.v.nx / kTcX) * (a.v.ny / kTcY) * a.v.nz * a.batch;
+    const size_t smem = conv3tc_smem(a.cin, a.cout_p);
+    const int per_sm = std::max(1, std::min(4, (int)((227 * 1024) / (smem + 2048))));
+    const int blocks = (int)std::min<long long>(tiles, (long long)sm_count() * per_sm);
+    k_conv3_tc<<<blocks, 128, smem, st>>>(a, err);
+  } else if (conv3t_ok(a)) {
     const int tiles = (a.v.nx / kTX) * (a.v.ny / kTY) * (a.v.nz / kTZ);
     k_conv3t<<<dim3(tiles, ceil_div(a.cout_p, 32), a.batch), 128, conv3t_smem(a.cin), st>>>(a);
   } else {
@@ -942,7 +1155,7 @@ cudaError_t conv_fwd(bfcs_net_s* N, int l, const float* params, int B, View in, 
   a.out_mode = out_mode;
   a.out = out; a.ldo = ldo; a.offo = offo;
   a.up_c = L.cout;
-  return launch_conv(a, N->n[lv], N->st);
+  return launch_conv(a, N->n[lv], N->err, N->st);
 }
 
 cudaError_t pool(bfcs_net_s* N, View in, View out, int C, int coarse_lv, int B) {
@@ -1050,7 +1263,7 @@ cudaError_t layer_bwd(bfcs_net_s* N, int l, int B, View dout, View out, View in,
     a.out_mode = OUT_BF16;
     a.out = din.p; a.ldo = din.ld; a.offo = din.off;
     a.up_c = L.cout;
-    const cudaError_t e = launch_conv(a, N->n[lv], N->st);
+    const cudaError_t e = launch_conv(a, N->n[lv], N->err, N->st);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
@@ -1195,6 +1408,7 @@ int bfcs_net_create(bfcs_net* out, int nx, int ny, int nz, int max_batch, int fl
   add(&N->lden, (size_t)kLossBlocks * B * sizeof(double));
   add(&N->den_b, (size_t)B * sizeof(double));
   add(&N->sbits, (size_t)B * sizeof(unsigned));
+  add(&N->err, sizeof(int));
   if (train) {
     act(&N->dOUT, 0, 16); act(&N->dA0, 0, 32); act(&N->dC0, 0, 64); act(&N->dD0a, 0, 32); act(&N->dD0b, 0, 32);
     act(&N->dP0, 1, 32); act(&N->dA1, 1, 32); act(&N->dC1, 1, 64); act(&N->dD1a, 1, 32); act(&N->dD1b, 1, 32);
@@ -1226,6 +1440,7 @@ int bfcs_net_create(bfcs_net* out, int nx, int ny, int nz, int max_batch, int fl
   }
   if (cudaFuncSetAttribute(k_conv3t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv3t_smem(64)) !=
           cudaSuccess ||
+      cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024) != cudaSuccess ||
       cudaFuncSetAttribute(k_wgrad3t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad3t_smem(64)) !=
           cudaSuccess) {
     cudaGetLastError();
@@ -1236,6 +1451,15 @@ int bfcs_net_create(bfcs_net* out, int nx, int ny, int nz, int max_batch, int fl
   if (cudaMemsetAsync(N->base, 0, total, N->st) != cudaSuccess) { free_net(N); return BFCS_ERR_CUDA; }
   *out = N;
   return BFCS_OK;
+}
+
+int bfcs_net_status(bfcs_net N) {
+  if (N == nullptr) return BFCS_ERR_INVALID_ARG;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, N->err, sizeof(int), cudaMemcpyDeviceToHost, N->st) != cudaSuccess ||
+      cudaStreamSynchronize(N->st) != cudaSuccess)
+    return BFCS_ERR_CUDA;
+  return h ? BFCS_ERR_TIMEOUT : BFCS_OK;
 }
 
 int bfcs_net_destroy(bfcs_net N) {

@@ -61,6 +61,7 @@ def test_forward_matches_oracle(dims):
     x = inputs(5, 2, dims)
     net = api.Net(dims, max_batch=2)
     y = net.forward(flat.float().cuda(), x.float().cuda()).double().cpu()
+    net.status()
     ref = U.forward(bf16(flat), bf16(x))
     for s in range(2):
         assert rel(y[s], ref[s]) <= 2e-2, (s, rel(y[s], ref[s]))
@@ -72,6 +73,7 @@ def test_forward_full_training_size_matches_oracle():
     x = inputs(6, 1, dims)
     net = api.Net(dims, max_batch=1)
     y = net.forward(flat.float().cuda(), x.float().cuda()).double().cpu()
+    net.status()
     assert rel(y, U.forward(bf16(flat), bf16(x))) <= 2e-2
 
 
