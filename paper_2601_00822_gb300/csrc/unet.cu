@@ -336,10 +336,13 @@ constexpr int kTcX = 8, kTcY = 16;
 constexpr int kTcHX = kTcX + 2, kTcHY = kTcY + 2, kTcHZ = 3, kTcNV = kTcHX * kTcHY * kTcHZ;
 constexpr unsigned kTcSpinLimit = 1u << 26;    // bounded wait on the MMA completion barrier
 
-// halo (rounded to 1 KB) + weights; two to four blocks share an SM for cin <= 32
-size_t conv3tc_smem(int cin, int n) {
-  return ((size_t)kTcNV * (cin / 8) * 16 + 1023) / 1024 * 1024 + (size_t)27 * (cin / 8) * n * 16;
+// nbuf halo buffers (each rounded to 1 KB) + weights
+size_t conv3tc_smem(int cin, int n, int nbuf) {
+  return nbuf * (((size_t)kTcNV * (cin / 8) * 16 + 1023) / 1024 * 1024) + (size_t)27 * (cin / 8) * n * 16;
 }
+// two halo buffers only where two blocks still fit on an SM (measured: two
+// co-resident blocks beat one double-buffered block for the 32-channel layers)
+int conv3tc_nbuf(int cin, int n) { return conv3tc_smem(cin, n, 2) <= 111 * 1024 ? 2 : 1; }
 
 __device__ __forceinline__ uint64_t umma_sdesc(unsigned saddr, unsigned lbo, unsigned sbo) {
   // start address, leading (K) and stride (M/N) byte offsets in 16-byte units,
@@ -353,153 +356,188 @@ __device__ __forceinline__ unsigned umma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
 }
 
-__global__ void __launch_bounds__(128, 2) k_conv3_tc(ConvArgs a, int* err) {
+// Pipelined: with two halo buffers (nbuf = 2) the halo of tile k+1 streams in
+// and the epilogue of tile k-1 runs while the tensor cores work on tile k (two
+// TMEM accumulators of N columns); with one buffer the next halo waits for
+// the current tile's MMAs.
+constexpr int kTcThreads = 256;   // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31
+
+__global__ void __launch_bounds__(kTcThreads, 2) k_conv3_tc(ConvArgs a, int* err, int nbuf) {
   extern __shared__ __align__(1024) unsigned char smt[];
-  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ __align__(8) unsigned long long mbar[2];
   __shared__ unsigned tmem_base_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int KC = a.cin >> 3, N = a.cout_p;
-  // halo first, weights after it
-  const unsigned h_bytes = (unsigned)kTcNV * KC * 16u;
-  unsigned char* sh = smt;
-  unsigned char* sw = smt + ((h_bytes + 1023u) & ~1023u);
+  const unsigned h_stride = ((unsigned)kTcNV * KC * 16u + 1023u) & ~1023u;   // one halo buffer
+  unsigned char* sw = smt + nbuf * h_stride;                                 // weights after the halos
+  const unsigned sh_a = (unsigned)__cvta_generic_to_shared(smt);
   const unsigned sw_a = (unsigned)__cvta_generic_to_shared(sw);
-  const unsigned sh_a = (unsigned)__cvta_generic_to_shared(sh);
-  const unsigned mbar_a = (unsigned)__cvta_generic_to_shared(&mbar);
+  const unsigned mbar_a0 = (unsigned)__cvta_generic_to_shared(&mbar[0]);
   const long long nvox = (long long)a.v.nx * a.v.ny * a.v.nz;
   const int ntx = a.v.nx / kTcX, nty = a.v.ny / kTcY;
   const int tiles_ps = ntx * nty * a.v.nz;
   const int total = tiles_ps * a.batch;
+  const int G = gridDim.x;
 
-  // tensor memory: N columns (32 or 64) x 128 lanes of FP32
-  if (warp == 0) {
+  if (warp == 0) {   // tensor memory: 2 accumulators of N FP32 columns x 128 lanes
     const unsigned dst = (unsigned)__cvta_generic_to_shared(&tmem_base_s);
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(N));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst), "r"(2 * N));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a0 + 8));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
-  // weights -> shared memory (core-matrix layout)
-  for (int i = tid; i < 27 * N * KC; i += blockDim.x) {
+  for (int i = tid; i < 27 * N * KC; i += blockDim.x) {   // weights (core-matrix layout)
     const int c = i % KC, n = (i / KC) % N, tap = i / (KC * N);
     cp_async16(sw + ((tap * KC + c) * N + n) * 16, a.w + ((long long)tap * N + n) * a.cin + c * 8);
   }
-  cp_async_wait_all();
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  const unsigned tmem = tmem_base_s;
-  const unsigned idesc = umma_idesc_bf16(128, N);
-  unsigned phase = 0;
-  bool ok = true;
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
 
-  for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-    const int b = tile / tiles_ps;
-    int tt = tile - b * tiles_ps;
-    const int x0 = (tt % ntx) * kTcX;
+  struct TileXY { int b, x0, y0, z0; };
+  auto tile_of = [&](int t) {
+    TileXY r;
+    r.b = t / tiles_ps;
+    int tt = t - r.b * tiles_ps;
+    r.x0 = (tt % ntx) * kTcX;
     tt /= ntx;
-    const int y0 = (tt % nty) * kTcY, z0 = tt / nty;
-    const bf16* inb = a.in + (long long)b * nvox * a.ldi + a.offi;
+    r.y0 = (tt % nty) * kTcY;
+    r.z0 = tt / nty;
+    return r;
+  };
+  auto issue_halo = [&](int t, int buf) {
+    const TileXY q = tile_of(t);
+    unsigned char* sh = smt + buf * h_stride;
+    const bf16* inb = a.in + (long long)q.b * nvox * a.ldi + a.offi;
     for (int i = tid; i < kTcNV * KC; i += blockDim.x) {
       const int v = i / KC, c = i - v * KC;
       const int hx = v % kTcHX, hy = (v / kTcHX) % kTcHY, hz = v / (kTcHX * kTcHY);
-      const int gx = wrap(x0 + hx - 1, a.v.nx), gy = wrap(y0 + hy - 1, a.v.ny), gz = wrap(z0 + hz - 1, a.v.nz);
+      const int gx = wrap(q.x0 + hx - 1, a.v.nx), gy = wrap(q.y0 + hy - 1, a.v.ny),
+                gz = wrap(q.z0 + hz - 1, a.v.nz);
       cp_async16(sh + (c * kTcNV + v) * 16, inb + (((long long)gz * a.v.ny + gy) * a.v.nx + gx) * a.ldi + c * 8);
     }
-    cp_async_wait_all();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  bool ok = true;
+  // bounded wait for the k-th commit on barrier k % 2 (its (k / 2)-th phase); one decision per block
+  auto wait_mma = [&](int k) {
+    const unsigned bar = mbar_a0 + 8u * (unsigned)(k & 1), parity = (unsigned)((k >> 1) & 1);
+    unsigned done = 0, spins = 0;
+    while (!done) {
+      asm volatile(
+          "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+          : "=r"(done)
+          : "r"(bar), "r"(parity)
+          : "memory");
+      if (!done && ++spins > kTcSpinLimit) break;
+    }
+    if (__syncthreads_or(!done)) {
+      if (tid == 0) atomicExch(err, 1);
+      ok = false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  };
+  auto epilogue = [&](const TileXY& q, int slot) {
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;   // TMEM lane = tile voxel (x = r % 8, y = r / 8)
+    const long long vox = ((long long)q.z0 * a.v.ny + q.y0 + r / kTcX) * a.v.nx + q.x0 + r % kTcX;
+    bf16* orow = (bf16*)a.out + ((long long)q.b * nvox + vox) * a.ldo + a.offo;
+    for (int c0 = half * 16; c0 < N; c0 += 32) {   // this warp's 16-column slices
+      unsigned v[16];
+      const unsigned taddr = tmem_base_s + ((unsigned)(quarter * 32) << 16) + (unsigned)(slot * N + c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+      for (int q8 = 0; q8 < 16; q8 += 8) {
+        __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int col = c0 + q8 + 2 * u;
+          float f0 = __uint_as_float(v[q8 + 2 * u]), f1 = __uint_as_float(v[q8 + 2 * u + 1]);
+          if (a.bias != nullptr) {
+            f0 += a.bias[col % a.bias_mod];
+            f1 += a.bias[(col + 1) % a.bias_mod];
+          }
+          if (a.act) {
+            f0 = f0 > 0.f ? f0 : kSlope * f0;
+            f1 = f1 > 0.f ? f1 : kSlope * f1;
+          }
+          o[u] = __floats2bfloat162_rn(f0, f1);
+        }
+        *reinterpret_cast<uint4*>(orow + c0 + q8) = *reinterpret_cast<const uint4*>(o);
+      }
+    }
+  };
+
+  const unsigned idesc = umma_idesc_bf16(128, N);
+  int t = blockIdx.x, k = 0;
+  TileXY prev{};
+  if (t < total) issue_halo(t, 0);
+  for (; t < total && ok; t += G, ++k) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // weights and halo of tile k
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const unsigned d_tmem = tmem_base_s + (unsigned)((k & 1) * N);
+      // descriptors of tap 0, chunk 0; later MMAs only move the start address
+      // (16-byte units in the low bits, which never carry past bit 13 here)
+      const uint64_t ad0 = umma_sdesc(sh_a + (unsigned)(k % nbuf) * h_stride, kTcNV * 16, kTcHX * 16);
+      const uint64_t bd0 = umma_sdesc(sw_a, N * 16, 128);
       int first = 1;
+#pragma unroll 1
       for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;      // halo offsets of the tap (0..2)
-        const unsigned a0 = sh_a + (unsigned)(((dz * kTcHY + dy) * kTcHX + dx) * 16);
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        const unsigned aoff = (unsigned)((dz * kTcHY + dy) * kTcHX + dx);        // 16-byte units
+#pragma unroll 4
         for (int kk = 0; kk < KC; kk += 2) {
-          const uint64_t ad = umma_sdesc(a0 + (unsigned)(kk * kTcNV * 16), kTcNV * 16, kTcHX * 16);
-          const uint64_t bd = umma_sdesc(sw_a + (unsigned)((tap * KC + kk) * N * 16), N * 16, 128);
+          const uint64_t ad = ad0 + aoff + (unsigned)(kk * kTcNV);
+          const uint64_t bd = bd0 + (unsigned)((tap * KC + kk) * N);
           asm volatile(
               "{\n.reg .pred p;\nsetp.eq.u32 p, %4, 0;\n"            // p: accumulate into D (not the first MMA)
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
               "l"(ad), "l"(bd), "r"(idesc), "r"(first));
           first = 0;
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_a)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       mbar_a0 + 8u * (unsigned)(k & 1))
                    : "memory");
     }
-    // bounded wait for the MMAs of this tile
-    {
-      unsigned done = 0, spins = 0;
-      while (!done) {
-        asm volatile(
-            "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
-            : "=r"(done)
-            : "r"(mbar_a), "r"(phase)
-            : "memory");
-        if (!done && ++spins > kTcSpinLimit) break;
-      }
-      if (__syncthreads_or(!done)) {     // one decision for the whole block
-        if (tid == 0) atomicExch(err, 1);
-        ok = false;
-      }
+    const TileXY cur = tile_of(t);
+    if (k >= 1) {   // tile k-1: its MMAs are done, its accumulator is read while tile k's MMAs run
+      wait_mma(k - 1);
+      if (ok) epilogue(prev, (k - 1) & 1);
     }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (ok) {
-      // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile voxels (x = r % 8, y = r / 8)
-      const int r = warp * 32 + lane;
-      const long long vox = ((long long)z0 * a.v.ny + y0 + r / kTcX) * a.v.nx + x0 + r % kTcX;
-      bf16* orow = (bf16*)a.out + ((long long)b * nvox + vox) * a.ldo + a.offo;
-      for (int c0 = 0; c0 < N; c0 += 32) {
-        unsigned v[32];
-        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-        for (int q = 0; q < 32; q += 8) {
-          __align__(16) __nv_bfloat162 o[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int col = c0 + q + 2 * u;
-            float f0 = __uint_as_float(v[q + 2 * u]), f1 = __uint_as_float(v[q + 2 * u + 1]);
-            if (a.bias != nullptr) {
-              f0 += a.bias[col % a.bias_mod];
-              f1 += a.bias[(col + 1) % a.bias_mod];
-            }
-            if (a.act) {
-              f0 = f0 > 0.f ? f0 : kSlope * f0;
-              f1 = f1 > 0.f ? f1 : kSlope * f1;
-            }
-            o[u] = __floats2bfloat162_rn(f0, f1);
-          }
-          *reinterpret_cast<uint4*>(orow + c0 + q) = *reinterpret_cast<const uint4*>(o);
-        }
-      }
+    if (ok && t + G < total) {
+      if (nbuf == 1) wait_mma(k);   // the only halo buffer is still being read by tile k's MMAs
+      if (ok) issue_halo(t + G, (k + 1) % nbuf);
     }
+    prev = cur;
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();   // TMEM and the halo buffer are free for the next tile
+    __syncthreads();
   }
+  if (ok && k >= 1) {
+    wait_mma(k - 1);
+    if (ok) epilogue(prev, (k - 1) & 1);
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(N));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem_base_s), "r"(2 * N));
 }
 
 bool conv3tc_ok(const ConvArgs& a) {
   return a.ksize == 3 && a.in_mode == IN_CONV && a.out_mode == OUT_BF16 && a.v.nx % kTcX == 0 &&
          a.v.ny % kTcY == 0 && (a.cin == 16 || a.cin == 32 || a.cin == 64) && (a.cout_p == 32 || a.cout_p == 64) &&
          a.ldi % 8 == 0 && a.offi % 8 == 0 && a.ldo % 8 == 0 && a.offo % 8 == 0 &&
-         conv3tc_smem(a.cin, a.cout_p) <= 225 * 1024;
+         conv3tc_smem(a.cin, a.cout_p, 1) <= 225 * 1024;
 }
 
 // ------------------------------------------------------------------ weight gradient
@@ -816,15 +854,23 @@ __global__ void k_unpool_add(const bf16* dco, int ldc, int offc, bf16* dfine, in
     *d = __float2bfloat16(__bfloat162float(*d) + 0.125f * __bfloat162float(dco[r * ldc + offc + c]));
   }
 }
-// dY *= act'(pre) in place; the sign of the saved post-activation output equals the sign of the pre-activation
+// dY *= act'(pre) in place; the sign of the saved post-activation output
+// equals the sign of the pre-activation.  8 channels (16 bytes) per thread.
 __global__ void k_act_bwd(bf16* dy, int ldd, int offd, const bf16* y, int ldy, int offy, int C, long long rows) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < rows * C;
+  const int cv = C / 8;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < rows * cv;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / C;
-    const int c = (int)(i - r * C);
-    const float yv = __bfloat162float(y[r * ldy + offy + c]);
-    bf16* d = dy + r * ldd + offd + c;
-    if (!(yv > 0.f)) *d = __float2bfloat16(__bfloat162float(*d) * kSlope);
+    const long long r = i / cv;
+    const int c = (int)(i - r * cv) * 8;
+    uint4* dp = reinterpret_cast<uint4*>(dy + r * ldd + offd + c);
+    uint4 dv = *dp;
+    const uint4 yv = *reinterpret_cast<const uint4*>(y + r * ldy + offy + c);
+    bf16* d8 = reinterpret_cast<bf16*>(&dv);
+    const bf16* y8 = reinterpret_cast<const bf16*>(&yv);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (!(__bfloat162float(y8[k]) > 0.f)) d8[k] = __float2bfloat16(__bfloat162float(d8[k]) * kSlope);
+    *dp = dv;
   }
 }
 // bias gradient partials: part[block][c] = sum over this block's rows of dY[r][c]
@@ -846,20 +892,22 @@ __global__ void __launch_bounds__(kBiasThreads) k_bias_grad(const bf16* dy, int 
     part[(long long)blockIdx.x * C + threadIdx.x] = t;
   }
 }
-// relative squared L2 loss: per (block, sample) sums of (p - t)^2 and t^2 in FP64
+// relative squared L2 loss: per (block, sample) sums of (p - t)^2 and t^2 in
+// FP64; one voxel per thread (6 contiguous predictions, 6 coalesced targets)
 constexpr int kLossBlocks = 64;
 __global__ void k_loss(const float* pred, const float* target, long long n, double* num, double* den) {
   __shared__ double rn[32], rd[32];
   const int b = blockIdx.y;
   double sn = 0.0, sd = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n * 6;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long v = i / 6;
-    const int c = (int)(i - v * 6);
-    const double p = pred[((long long)b * n + v) * 6 + c];
-    const double t = target[((long long)b * 6 + c) * n + v];
-    sn += (p - t) * (p - t);
-    sd += t * t;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const float* pr = pred + ((long long)b * n + v) * 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const double p = pr[c];
+      const double t = target[((long long)b * 6 + c) * n + v];
+      sn += (p - t) * (p - t);
+      sd += t * t;
+    }
   }
   for (int off = 16; off > 0; off >>= 1) {
     sn += __shfl_down_sync(0xffffffffu, sn, off);
@@ -886,20 +934,22 @@ __global__ void k_loss_final(const double* num, const double* den, int nblk, int
   }
   if (loss != nullptr) *loss = l / batch;
 }
-// dL/dpred = 2 (p - t) / (den_b B), written as the head's output gradient [B][N][16] BF16
+// dL/dpred = 2 (p - t) / (den_b B), written as the head's output gradient
+// [B][N][16] BF16 (channels 6..15 zero); one voxel per thread
 __global__ void k_loss_grad(const float* pred, const float* target, const double* den_b, long long n, int batch,
                             bf16* dy) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n * batch * 16;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % 16);
-    const long long r = i / 16;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n * batch;
+       r += (long long)gridDim.x * blockDim.x) {
     const long long b = r / n, v = r - b * n;
-    float gr = 0.f;
-    if (c < 6) {
-      const double p = pred[r * 6 + c], t = target[(b * 6 + c) * n + v];
-      gr = (float)(2.0 * (p - t) / (den_b[b] * batch));
-    }
-    dy[r * 16 + c] = __float2bfloat16(gr);
+    const double f = 2.0 / (den_b[b] * batch);
+    __align__(16) bf16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      o[c] = __float2bfloat16((float)(((double)pred[r * 6 + c] - (double)target[(b * 6 + c) * n + v]) * f));
+    reinterpret_cast<uint4*>(dy + r * 16)[0] = reinterpret_cast<const uint4*>(o)[0];
+    reinterpret_cast<uint4*>(dy + r * 16)[1] = reinterpret_cast<const uint4*>(o)[1];
   }
 }
 // Adam (Kingma and Ba 2014), bias-corrected, FP32 state
@@ -1121,10 +1171,11 @@ bool tcgen05_enabled() {
 cudaError_t launch_conv(const ConvArgs& a, long long nvox, int* err, cudaStream_t st) {
   if (tcgen05_enabled() && conv3tc_ok(a)) {
     const long long tiles = (long long)(a.v.nx / kTcX) * (a.v.ny / kTcY) * a.v.nz * a.batch;
-    const size_t smem = conv3tc_smem(a.cin, a.cout_p);
-    const int per_sm = std::max(1, std::min(4, (int)((227 * 1024) / (smem + 2048))));
+    const int nbuf = conv3tc_nbuf(a.cin, a.cout_p);
+    const size_t smem = conv3tc_smem(a.cin, a.cout_p, nbuf);
+    const int per_sm = std::max(1, std::min(2, (int)((227 * 1024) / (smem + 2048))));
     const int blocks = (int)std::min<long long>(tiles, (long long)sm_count() * per_sm);
-    k_conv3_tc<<<blocks, 128, smem, st>>>(a, err);
+    k_conv3_tc<<<blocks, kTcThreads, smem, st>>>(a, err, nbuf);
   } else if (conv3t_ok(a)) {
     const int tiles = (a.v.nx / kTX) * (a.v.ny / kTY) * (a.v.nz / kTZ);
     k_conv3t<<<dim3(tiles, ceil_div(a.cout_p, 32), a.batch), 128, conv3t_smem(a.cin), st>>>(a);
@@ -1207,7 +1258,8 @@ cudaError_t layer_bwd(bfcs_net_s* N, int l, int B, View dout, View out, View in,
   const long long orows = up ? rows * 8 : rows;         // rows of the output gradient
   const int dch = up ? L.cout : L.cout_p;               // channels of the output gradient view
   if (L.kind == 0) {
-    k_act_bwd<<<grid_for(orows * dch), 256, 0, N->st>>>(dout.p, dout.ld, dout.off, out.p, out.ld, out.off, dch, orows);
+    k_act_bwd<<<grid_for(orows * dch / 8), 256, 0, N->st>>>(dout.p, dout.ld, dout.off, out.p, out.ld, out.off, dch,
+                                                            orows);
     count_launches(1);
   }
   // weight gradient
@@ -1307,7 +1359,7 @@ cudaError_t backward(bfcs_net_s* N, int B) {
 cudaError_t loss_and_grad(bfcs_net_s* N, int B, const float* target, double* loss_dev) {
   k_loss<<<dim3(kLossBlocks, B), 256, 0, N->st>>>(N->OUT, target, N->n[0], N->lnum, N->lden);
   k_loss_final<<<1, 32, 0, N->st>>>(N->lnum, N->lden, kLossBlocks, B, N->den_b, loss_dev);
-  k_loss_grad<<<grid_for(N->n[0] * B * 16), 256, 0, N->st>>>(N->OUT, target, N->den_b, N->n[0], B, N->dOUT);
+  k_loss_grad<<<grid_for(N->n[0] * B), 256, 0, N->st>>>(N->OUT, target, N->den_b, N->n[0], B, N->dOUT);
   count_launches(3);
   return cudaGetLastError();
 }
