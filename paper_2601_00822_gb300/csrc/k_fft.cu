@@ -39,6 +39,8 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
   constexpr int H = L / 2;
   extern __shared__ unsigned char smem_raw[];
   C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);
+  __shared__ int prow_s[LPB];     // phase-map row of each line of the block, translated by chi
+  __shared__ int sx_s;            // x translation in [0, nx)
 
   const int tid = threadIdx.x;
   const int ncomp = a.ncomp;
@@ -58,6 +60,21 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
   const bool fval = f < ncol && line < lines;
   const bool has_b = 2 * q + 1 < ncomp;
   C2<R>* sf = s + f * LP;
+
+  // per-line translation bookkeeping of the polarization (made visible by the
+  // barriers of step 1): the phase of voxel (n, y, z) is phase0(n - sx, y - sy, z - sz)
+  if (tid < LPB && (mode == XM_SWEEP || mode == XM_REALTAU || mode == XM_REALSIG || mode == XM_SWEEPSIG)) {
+    const XMember& M = a.xm[m];
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const long long ln = line0 + tid;
+    if (ln < lines) {
+      int y = (int)(ln % ny) - ((M.sy % ny) + ny) % ny, z = (int)(ln / ny) - ((M.sz % nz) + nz) % nz;
+      if (y < 0) y += ny;
+      if (z < 0) z += nz;
+      prow_s[tid] = (z * ny + y) * nx;
+    }
+    if (tid == 0) sx_s = ((M.sx % nx) + nx) % nx;
+  }
 
   // ---- 1. inverse transform along x of the pair-line Z = A + i B (C2R), or load real data
   if (mode == XM_SWEEP || mode == XM_C2R || mode == XM_SWEEPSIG) {
@@ -126,22 +143,20 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
   //         sigma = L(x) eps instead in the stress modes
   if (mode == XM_SWEEP || mode == XM_REALTAU || mode == XM_REALSIG || mode == XM_SWEEPSIG) {
     const bool full = mode == XM_REALSIG || mode == XM_SWEEPSIG;
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int nx = a.g.nx;
+    const int sx = sx_s;
     for (int idx = tid; idx < LPB * L; idx += blockDim.x) {
       const int n = idx % L, i = idx / L;
       const long long ln = line0 + i;
       if (ln >= lines) continue;
-      const int y = (int)(ln % ny), z = (int)(ln / ny);
       C2<R>* c0 = s + (i * 3) * LP + xpad(n);
       const C2<R> p0 = c0[0], p1 = c0[LP], p2 = c0[2 * LP];
       // eps: xx yy zz yz xz xy
       const R e0 = p0.x, e1 = p0.y, e2 = p1.x, e3 = p1.y, e4 = p2.x, e5 = p2.y;
       const XMember& M = a.xm[m];
-      int xs = n - M.sx, ys = y - M.sy, zs = z - M.sz;
-      xs %= nx; if (xs < 0) xs += nx;
-      ys %= ny; if (ys < 0) ys += ny;
-      zs %= nz; if (zs < 0) zs += nz;
-      const int ph = M.phase[((long long)zs * ny + ys) * nx + xs];
+      int xs = n - sx;
+      if (xs < 0) xs += nx;
+      const int ph = M.phase[prow_s[i] + xs];
       const R tr = e0 + e1 + e2;
       const long long vox = ln * L + n;
       if (M.eps_out != nullptr) {
