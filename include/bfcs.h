@@ -55,6 +55,7 @@ extern "C" {
 #define BFCS_FP64 1                   /* FP64 throughout */
 #define BFCS_MIXED 2                  /* FP32 sweeps with FP64 defect correction; FP64 fields */
 #define BFCS_AUTOTUNE 4               /* OR-ed with FP32 or MIXED: time the y-pass variants at plan creation */
+#define BFCS_CG 8                     /* OR-ed with any precision: conjugate gradients (Algorithm 2) */
 
 #define BFCS_MAX_PHASES 16
 
@@ -93,7 +94,12 @@ typedef struct {
  *             this many.
  *  flags:     BFCS_FP32, BFCS_FP64 or BFCS_MIXED, optionally OR BFCS_AUTOTUNE
  *             (FP32 / MIXED: pick the y-pass variant by timing, see
- *             bfcs_plan_tuning).  BFCS_MIXED runs the sweeps in FP32 and
+ *             bfcs_plan_tuning) and BFCS_CG (the sweeps are driven by
+ *             conjugate gradients on the operator of Eq. 5.13, Algorithm 2:
+ *             rounds of CG to 0.1 tol, 0.01 tol, ... relative to their start
+ *             in the C0-weighted norm, each verified by two sweeps of the
+ *             residual of Eq. 5.11; info.iters counts operator applications;
+ *             allocates four more strain spectra per member).  BFCS_MIXED runs the sweeps in FP32 and
  *             corrects them in FP64 (below); its fields at the API (b, eps,
  *             sigma, u, eps_init, fft3d data) are double.
  *  stream:    cudaStream_t to order work on (NULL = legacy default stream).

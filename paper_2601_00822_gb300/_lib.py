@@ -25,6 +25,7 @@ FP32 = 0
 FP64 = 1
 MIXED = 2
 AUTOTUNE = 4
+CG = 8
 
 # every symbol declared in include/bfcs.h
 EXPORTS = (

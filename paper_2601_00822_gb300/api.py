@@ -88,7 +88,7 @@ def body_force(dims, centre, a, precision="fp32", device="cuda", stream=None) ->
 class Plan:
     """bfcs_plan_create / bfcs_plan_destroy with the solver calls as methods."""
 
-    def __init__(self, dims, precision="fp32", max_batch=1, stream=None, autotune=False):
+    def __init__(self, dims, precision="fp32", max_batch=1, stream=None, autotune=False, cg=False):
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.precision = precision
@@ -98,6 +98,8 @@ class Plan:
         flag = {"fp32": _lib.FP32, "fp64": _lib.FP64, "mixed": _lib.MIXED}[precision]
         if autotune:
             flag |= _lib.AUTOTUNE
+        if cg:
+            flag |= _lib.CG
         nx, ny, nz = self.dims
         _lib.check(self.lib.bfcs_plan_create(C.byref(h), nx, ny, nz, int(max_batch), flag,
                                              _stream_ptr(self.stream)), "bfcs_plan_create")

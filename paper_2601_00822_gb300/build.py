@@ -29,6 +29,8 @@ UNITS = [
     ("k_fft.cu", ["-DBFCS_R=double"], "k_fft_f64.o"),
     ("k_green.cu", ["-DBFCS_R=float"], "k_green_f32.o"),
     ("k_green.cu", ["-DBFCS_R=double"], "k_green_f64.o"),
+    ("k_cg.cu", ["-DBFCS_R=float"], "k_cg_f32.o"),
+    ("k_cg.cu", ["-DBFCS_R=double"], "k_cg_f64.o"),
     ("k_misc.cu", [], "k_misc.o"),
     ("solver.cu", [], "solver.o"),
     ("noalloc.cu", [], "noalloc.o"),

@@ -93,7 +93,7 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
 
     if (qq == R(0)) {
       const bool k0 = (kx == 0 && ky == 0 && n == 0);
-      if (k0 && mode != GM_INIT) {
+      if (k0 && mode != GM_INIT && mode != GM_APPLY) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) stm->tau0[q] = (double)M(q).x;
       }
@@ -102,12 +102,14 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
       }
 #pragma unroll
       for (int q = 0; q < 6; ++q)
-        M(q) = (mode != GM_FINAL && k0) ? mk<R>(Em[q], R(0)) : mk<R>(0, 0);
+        M(q) = (mode != GM_FINAL && mode != GM_APPLY && k0) ? mk<R>(Em[q], R(0)) : mk<R>(0, 0);
       continue;
     }
-    const C2<R> bh0 = pm[0], bh1 = pm[L * T], bh2 = pm[2 * L * T];
+    const bool load = mode != GM_APPLY;
+    const C2<R> bh0 = load ? pm[0] : mk<R>(0, 0), bh1 = load ? pm[L * T] : mk<R>(0, 0),
+                bh2 = load ? pm[2 * L * T] : mk<R>(0, 0);
     C2<R> dp[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
-    if (mode != GM_INIT) { dp[0] = pm[3 * L * T]; dp[1] = pm[4 * L * T]; dp[2] = pm[5 * L * T]; }
+    if (mode == GM_SWEEP || mode == GM_FINAL) { dp[0] = pm[3 * L * T]; dp[1] = pm[4 * L * T]; dp[2] = pm[5 * L * T]; }
 
     C2<R> d[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
     if (mode != GM_INIT) {
@@ -122,7 +124,7 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
         const R ex = d[i].x - dp[i].x, ey = d[i].y - dp[i].y;
         r2 += ex * ex + ey * ey;
       }
-      acc += wgt * r2;
+      if (mode != GM_APPLY) acc += wgt * r2;
       if (mode == GM_FINAL) { d[0] = dp[0]; d[1] = dp[1]; d[2] = dp[2]; }
     }
     if (mode == GM_SWEEP || mode == GM_INIT) {
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
   {
     constexpr int PER = 16 / sizeof(C2<R>);          // complex values per 16-byte copy
     constexpr int CPR = T / PER;                     // copies per row of the tile
-    const int narr = mode == GM_INIT ? 3 : 6;
+    const int narr = mode == GM_INIT ? 3 : mode == GM_APPLY ? 0 : 6;
     for (int idx = tid; idx < narr * L * CPR; idx += nthr) {
       const int part = idx % CPR, n = (idx / CPR) % L, arr = idx / (CPR * L);
       const C2<R>* src = (arr < 3 ? bhat + arr * cs : dprev + (arr - 3) * cs) + n * zs + rowbase +
@@ -235,13 +237,14 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
   R acc = green_tile<R, L>(a, s, pre, col0, ky, mode, dprev, stm, Em);
 
   // ---- residual partial of this block in FP64 (fixed order: deterministic)
-  if (mode != GM_INIT) {
+  const bool resid = mode == GM_SWEEP || mode == GM_FINAL;
+  if (resid) {
     double accd = (double)acc;
     for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
     if ((tid & 31) == 0) red[tid >> 5] = accd;
   }
   __syncthreads();
-  if (mode != GM_INIT && tid == 0) {
+  if (resid && tid == 0) {
     double t = 0.0;
     for (int w = 0; w < (nthr + 31) / 32; ++w) t += red[w];
     part[blockIdx.y * gridDim.x + blockIdx.x].num = t;

@@ -78,11 +78,40 @@ constexpr bool col_variant_swap(int v) { return v >= 3; }
 // radices have a swapped order; the tunable lengths are 32..256)
 bool col_variant_valid(int v, int n);
 
+// ---- conjugate gradients on the operator of Eq. 5.13 (k_cg.cu)
+struct CgState {
+  double rr, rr0;        // <r, r>_C0 now and at the start
+  double alpha, beta;
+  double tol2;           // stop once <r, r> <= tol2 * rr0
+  double best;           // smallest <r, r> so far
+  int done, iters, maxit;
+  int best_it;           // iteration of `best`; no new best for kCgStagnation iterations ends the member
+};
+constexpr int kCgStagnation = 50;
+constexpr int kCgParts = 512;       // partial sums per member
+template <typename R> struct CgArgs {
+  C2<R>* c;              // iterate (state layout, members at ms)
+  C2<R>* r;              // residual
+  C2<R>* p;              // search direction
+  C2<R>* q;              // A p (holds U0 * L1 p on entry of the PQ step)
+  const C2<R>* s;        // INIT: one sweep applied to c
+  long long ms;
+  Geo g;
+  double lam0, mu0;
+  double* part;          // kCgParts doubles per member
+  CgState* cg;
+  IterState* skip;       // done flags read by the FFT passes of A p
+};
+// mode 0 INIT (r = s - c, p = r), 1 PQ (q = p - q, alpha), 2 UPDATE (c, r, beta,
+// convergence), 3 DIR (p = r + beta p); the scalar step follows modes 0-2.
+template <typename R> cudaError_t launch_cg_vec(const CgArgs<R>& a, int mode, int batch, cudaStream_t st);
+
 // ---- fused z pass: forward z FFT -> Green operators -> residual -> inverse z FFT.
 enum GMode : int {
   GM_SWEEP = 0,   // eps_hat^{s+1} = -Gamma0 tau_hat^s + eps_hat^{b(0)}, k=0 <- E; residual of eps^s
   GM_INIT = 1,    // tau_hat = 0: eps_hat^0 = eps_hat^{b(0)} (+E); d_prev <- 0
   GM_FINAL = 2,   // residual of eps^S; u_hat^S = i G0 (d_prev - i b_hat) into components 0..2
+  GM_APPLY = 3,   // the operator alone (Eq. 5.13): eps_hat = U0 tau_hat, no load, k=0 <- 0, no d, no residual
 };
 
 template <typename R> struct GArgs {

@@ -66,6 +66,12 @@ struct bfcs_plan_s {
   int max_rounds = 8;              // defect-correction rounds
   double switch_tol = 1e-4;        // FP32 phase stops here (or at the stall)
   bfcs_net net = nullptr;          // inference context of bfcs_surrogate_infer (created on first use)
+  bool use_cg = false;             // BFCS_CG: conjugate gradients (Algorithm 2) drive the sweeps
+  void* cg_vec = nullptr;          // c, r, p, q: 4 x max_batch x 6 x cs complex (sweep precision)
+  double* cg_part = nullptr;       // kCgParts per member
+  CgState* cg_state = nullptr;     // max_batch
+  IterState* cg_skip = nullptr;    // max_batch done flags for the FFT passes of A p
+  CgState* cg_host = nullptr;      // pinned copy
   int col_variant = 0;             // y-pass tile / factor order of the FP32 sweeps (autotuned or default)
   double col_variant_ms[kColVariants] = {0, 0, 0, 0, 0, 0};   // tuning times (ms per y forward+inverse pair)
 };
@@ -147,6 +153,8 @@ void free_plan(bfcs_plan P) {
   if (P->order_ev[0]) cudaEventDestroy(P->order_ev[0]);
   if (P->order_ev[1]) cudaEventDestroy(P->order_ev[1]);
   if (P->net) bfcs_net_destroy(P->net);
+  cudaFree(P->cg_vec); cudaFree(P->cg_part); cudaFree(P->cg_state); cudaFree(P->cg_skip);
+  if (P->cg_host) cudaFreeHost(P->cg_host);
   delete P;
 }
 
@@ -693,8 +701,103 @@ int run_sets(std::vector<SweepSet<R>*>& sets, int maxit) {
   return BFCS_OK;
 }
 
+// Conjugate gradients (Algorithm 2, operator of Eq. 5.13) from the current
+// state of every member of the set: c = the state, one standard sweep gives
+// s, r = p = s - c (the fixed-point residual is the CG residual), then
+// iterations of A p = p - F^-1 U0 F L1 p (the sweep's passes with the load
+// switched off) until <r, r>_C0 <= (scale tol_m)^2 <r0, r0>_C0 (tol_m: the
+// member's own tolerance) or `maxit` iterations; the state becomes c.  Adds the
+// operator applications to `applied`.
+template <typename R>
+int run_cg(SweepSet<R>& ss, double scale, int maxit, std::vector<int>& applied) {
+  bfcs_plan P = ss.P;
+  const int B = ss.B;
+  cudaStream_t st = P->st;
+  const Geo g = P->g;
+  const long long sms = 6 * g.cs;
+  const size_t vbytes = (size_t)B * sms * sizeof(C2<R>);
+  C2<R>* base = (C2<R>*)P->cg_vec;
+  const long long vstride = (long long)P->max_batch * sms;
+  CgArgs<R> ca{};
+  ca.c = base;
+  ca.r = base + vstride;
+  ca.p = base + 2 * vstride;
+  ca.q = base + 3 * vstride;
+  ca.ms = sms;
+  ca.g = g;
+  ca.lam0 = ss.C0.lambda;
+  ca.mu0 = ss.C0.mu;
+  ca.part = P->cg_part;
+  ca.cg = P->cg_state;
+  ca.skip = P->cg_skip;
+  // c = state; s = one sweep of it (the standard pass, load included)
+  CK(cudaMemcpyAsync(ca.c, P->spec, vbytes, cudaMemcpyDeviceToDevice, st));
+  int e = ss.enqueue(st, -1);
+  if (e != BFCS_OK) return e;
+  for (int m = 0; m < B; ++m) {
+    CgState& h = P->cg_host[m];
+    h = CgState{};
+    const double tl = P->mem_host[m].tol >= 0 ? P->mem_host[m].tol : ss.tol;
+    h.tol2 = (scale * tl) * (scale * tl);
+    h.maxit = std::max(1, maxit);
+  }
+  CK(cudaMemcpyAsync(P->cg_state, P->cg_host, B * sizeof(CgState), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(P->cg_skip, 0, B * sizeof(IterState), st));
+  ca.s = (const C2<R>*)P->spec;
+  CK(launch_cg_vec<R>(ca, 0, B, st));
+  ca.s = nullptr;
+  // A p through the sweep's passes: x (tau = L1 p, forward x) -> y -> z/Green (operator only) -> y
+  XArgs<R> xa = ss.xa;
+  xa.mode = XM_SWEEP;
+  xa.spec_in = ca.p;
+  xa.spec_out = ca.q;
+  xa.st = P->cg_skip;
+  CArgs<R> cy = ss.cy;
+  cy.data = ca.q;
+  cy.st = P->cg_skip;
+  cy.ncomp = 6;
+  GArgs<R> ga = ss.ga;
+  ga.spec = ca.q;
+  ga.st = P->cg_skip;
+  ga.mode = GM_APPLY;
+  ga.skip_done = 1;
+  auto iteration = [&]() -> int {
+    CK(launch_xpass_b<R>(xa, B, st));
+    CK(launch_colpass_b<R>(cy, -1, B, st));
+    CK(launch_zgreen_b<R>(ga, B, st));
+    CK(launch_colpass_b<R>(cy, +1, B, st));
+    CK(launch_cg_vec<R>(ca, 1, B, st));
+    CK(launch_cg_vec<R>(ca, 2, B, st));
+    CK(launch_cg_vec<R>(ca, 3, B, st));
+    return BFCS_OK;
+  };
+  int done_all = 0, it = 0, chunk = 8;
+  while (!done_all && it < maxit) {
+    const int c = std::min(chunk, maxit - it);
+    for (int k = 0; k < c; ++k) {
+      e = iteration();
+      if (e != BFCS_OK) return e;
+    }
+    it += c;
+    chunk = std::min(chunk * 2, 64);
+    CK(cudaMemcpyAsync(P->cg_host, P->cg_state, B * sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    const int w = sync_stream(P);
+    if (w != BFCS_OK) return w;
+    done_all = 1;
+    for (int m = 0; m < B; ++m) done_all = done_all && P->cg_host[m].done;
+  }
+  for (int m = 0; m < B; ++m) applied[m] += 1 + P->cg_host[m].iters;
+  CK(cudaMemcpyAsync(P->spec, ca.c, vbytes, cudaMemcpyDeviceToDevice, st));
+  return BFCS_OK;
+}
+
 // Algorithm 1 for B members of one grid, advancing together: each sweep is
 // one launch per pass for all members; converged members skip on the device.
+// With BFCS_CG the sweeps are driven by conjugate gradients (Algorithm 2):
+// rounds of CG followed by two verifying sweeps (the first one as a warm
+// start, whose residual is not evaluated); a round whose members do not all
+// meet their tolerance is followed by one with a ten times tighter CG
+// tolerance; after four rounds plain sweeps finish the job.
 template <typename R>
 int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const double* E0, double tol,
               int maxit, bfcs_info* infos, bool any_warm) {
@@ -703,6 +806,50 @@ int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const do
   int e = ss.init(any_warm);
   if (e != BFCS_OK) return e;
   std::vector<SweepSet<R>*> sets{&ss};
+  if (P->use_cg && tol > 0 && maxit > 2) {
+    std::vector<int> applied(B, 0), verify(B, 0);
+    int left = maxit;
+    if (any_warm) {               // a warm start need not be compatible: one plain sweep makes it so
+      e = ss.enqueue(P->st, -1);
+      if (e != BFCS_OK) return e;
+      for (int m = 0; m < B; ++m) applied[m] += 1;
+      left -= 1;
+    }
+    bool all = false;
+    double scale = 0.1;
+    for (int round = 0; round < 4 && !all && left > 2; ++round, scale *= 0.1) {
+      e = run_cg<R>(ss, scale, left - 2, applied);
+      if (e != BFCS_OK) return e;
+      // verify: the CG iterate is the warm start of two sweeps
+      for (int m = 0; m < B; ++m) P->mem_host[m].warm = 1;
+      e = upload_members(P, B, P->mem_host);
+      if (e != BFCS_OK) return e;
+      for (int m = 0; m < B; ++m)
+        CK(cudaMemsetAsync(P->ist + m, 0, offsetof(IterState, resid_last), P->st));
+      e = run_sets<R>(sets, 2);
+      if (e != BFCS_OK) return e;
+      CK(cudaMemcpyAsync(P->ist_host, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, P->st));
+      const int w = sync_stream(P);
+      if (w != BFCS_OK) return w;
+      all = true;
+      int most = 0;
+      for (int m = 0; m < B; ++m) {
+        verify[m] = P->ist_host[m].iters;
+        applied[m] += verify[m];
+        most = std::max(most, applied[m]);
+        all = all && P->ist_host[m].done;
+      }
+      left = maxit - most;
+    }
+    if (!all && left > 0) {        // plain sweeps from the last state (same iteration state)
+      e = run_sets<R>(sets, left);
+      if (e != BFCS_OK) return e;
+    }
+    e = ss.finalize(infos);       // infos[m].iters = sweeps since the last verification started
+    if (infos != nullptr)
+      for (int m = 0; m < B; ++m) infos[m].iters += applied[m] - verify[m];
+    return e;
+  }
   e = run_sets<R>(sets, maxit);
   if (e != BFCS_OK) return e;
   return ss.finalize(infos);
@@ -1226,7 +1373,8 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   *out = nullptr;
   const int prec = flags & 3;
   if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz) || max_batch < 1 || max_batch > kMaxBatch ||
-      (prec != BFCS_FP32 && prec != BFCS_FP64 && prec != BFCS_MIXED) || (flags & ~(3 | BFCS_AUTOTUNE)) != 0)
+      (prec != BFCS_FP32 && prec != BFCS_FP64 && prec != BFCS_MIXED) ||
+      (flags & ~(3 | BFCS_AUTOTUNE | BFCS_CG)) != 0)
     return BFCS_ERR_INVALID_ARG;
   bfcs_plan P = new bfcs_plan_s();
   P->nx = nx; P->ny = ny; P->nz = nz;
@@ -1287,6 +1435,15 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
       P->tw64[a] = make_twiddles<double>(dims[a]);
       if (P->tw64[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
     }
+  }
+  if (flags & BFCS_CG) {
+    P->use_cg = true;
+    ok = cudaMalloc(&P->cg_vec, 4 * MB * 6 * cs * P->csz) == cudaSuccess &&
+         cudaMalloc(&P->cg_part, MB * kCgParts * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&P->cg_state, MB * sizeof(CgState)) == cudaSuccess &&
+         cudaMalloc(&P->cg_skip, MB * sizeof(IterState)) == cudaSuccess &&
+         cudaMallocHost(&P->cg_host, MB * sizeof(CgState)) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
   }
   if (cudaMemset(P->ist, 0, MB * sizeof(IterState)) != cudaSuccess) { free_plan(P); return BFCS_ERR_CUDA; }
   if (const char* gs = std::getenv("BFCS_GRAPH_SWEEPS")) P->graph_sweeps = std::max(0, std::atoi(gs));

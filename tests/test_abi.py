@@ -41,7 +41,7 @@ def test_invalid_plan_rejected_before_any_device_work():
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 31, 1, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 0, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_plan_create(None, 32, 32, 32, 1, 0, None) == _lib.ERR_INVALID_ARG
-    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 8, None) == _lib.ERR_INVALID_ARG  # unknown flag
+    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 16, None) == _lib.ERR_INVALID_ARG  # unknown flag
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 3, None) == _lib.ERR_INVALID_ARG  # no precision 3
     assert lib.bfcs_plan_tuning(None, None, None, None, None) == _lib.ERR_INVALID_ARG
 

@@ -461,6 +461,58 @@ def test_precision_study_contrast_1000():
     assert err_e < 1e-4 and err_s < 1e-4, (err_e, err_s, im.iters, i64.iters)
 
 
+# ---------------------------------------------------------------- conjugate gradients (Algorithm 2)
+def test_cg_converges_to_the_oracle_fixed_point_in_fewer_applications():
+    p = W.config_c1()
+    ph_o, b_o = oracle_inputs(p)
+    ref = O.solve(ph_o, p.phases, p.c0, b_o, tol=1e-12, maxit=4000)
+    ph, b = gpu_inputs(p, "fp64")
+    with api.Plan(p.dims, "fp64", cg=True) as plan:
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-10, maxit=4000)
+    with api.Plan(p.dims, "fp64") as plan:
+        _, _, _, basic = plan.solve(ph, p.phases, p.c0, b, tol=1e-10, maxit=4000)
+    assert info.status == _lib.OK and info.resid <= 1e-10
+    for a, key in ((eps, "eps"), (sig, "sig"), (u, "u")):
+        assert rel(a.cpu().numpy(), ref[key]) < 1e-8, key
+    r = O.residual(ph_o, p.phases, eps.cpu().numpy(), O.fft3(b_o), O.wavevectors(p.dims))
+    assert r <= 2e-10
+    assert info.iters < basic.iters, (info.iters, basic.iters)
+
+
+def test_cg_at_contrast_1000_against_plain_sweeps():
+    """Stiff inclusions (C4's microstructure at 32^3): CG reaches the same field
+    as the plain scheme with a small fraction of its operator applications."""
+    p = W.config_c2(contrast=1000.0, seed=1, n=32, cell=32, vf=0.3, bf_radius=6.0)
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    with api.Plan(p.dims, "fp64") as plan:
+        e0, s0, _, i0 = plan.solve(ph, p.phases, p.c0, b, tol=1e-9, maxit=200000)
+    with api.Plan(p.dims, "fp64", cg=True) as plan:
+        e1, s1, _, i1 = plan.solve(ph, p.phases, p.c0, b, tol=1e-9, maxit=200000)
+    assert i0.status == _lib.OK and i1.status == _lib.OK and i1.resid <= 1e-9
+    assert rel(e1.cpu().numpy(), e0.cpu().numpy()) < 1e-6
+    assert i1.iters * 5 < i0.iters, (i1.iters, i0.iters)
+
+
+def test_cg_inside_the_mixed_ladder_and_batched_equals_individual():
+    p = W.config_c1()
+    ph_o, b_o = oracle_inputs(p)
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    specs = [((0, 0, 0), (0,) * 6), ((5, 3, 11), (0.01, 0, 0, 0, 0, 0.002)), ((31, 16, 2), (0,) * 6)]
+    with api.Plan(p.dims, "mixed", max_batch=3, cg=True) as plan, api.Plan(p.dims, "mixed", cg=True) as one:
+        members, infos = plan.solve_batched([dict(phase=ph, b=b, E=E, shift=sh) for sh, E in specs],
+                                            p.phases, p.c0, tol=1e-9, maxit=4000)
+        for mem, (sh, E), info in zip(members, specs, infos):
+            assert info.status == _lib.OK and info.resid <= 1e-9
+            (m1,), (i1,) = one.solve_batched([dict(phase=ph, b=b, E=E, shift=sh)], p.phases, p.c0, tol=1e-9,
+                                             maxit=4000)
+            assert i1.iters == info.iters and torch.equal(m1["eps_out"], mem["eps_out"])
+            r = O.residual(O.translate(ph_o, sh), p.phases, mem["eps_out"].cpu().numpy(), O.fft3(b_o),
+                           O.wavevectors(p.dims))
+            assert r <= 2e-9, (sh, r)
+
+
 # ---------------------------------------------------------------- full size (256^3, the benchmarked launch)
 def test_full_size_solve_meets_tolerance_independently_checked():
     p = W.config_c2(contrast=10.0, seed=1)
