@@ -429,6 +429,20 @@ def measure_extras(api, torch):
         "workload": "C3: 128^3, 64 shifts, contrast 10, residual 1e-6, mixed ladder, max_batch 16",
         "seconds": t, "shifts_per_s": len(shifts) / t, "voxel_iter_per_s": nvox * sw / t,
         "mean_sweeps": sw / len(shifts), "max_resid": max(i.resid for i in infos)}
+    q = W.config_c2(contrast=100.0, seed=1)
+    phq = api.voxelize(q.dims, q.cell, q.spheres)
+    bq = api.body_force(q.dims, q.bf_centre, q.bf_radius, "fp64")
+    c100 = {"workload": "C2 at contrast 100: 256^3, RSA vf 0.25 r 4-6, a = 24, mixed ladder to residual 1e-6"}
+    for label, cg in (("plain", False), ("cg", True)):
+        with api.Plan(q.dims, "mixed", autotune=True, cg=cg) as plan:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, _, info = plan.solve(phq, q.phases, q.c0, bq, tol=q.tol, maxit=q.maxit, want_sig=False,
+                                       want_u=False)
+            torch.cuda.synchronize()
+            c100[label] = {"seconds": time.perf_counter() - t0, "operator_applications": info.iters,
+                           "resid": info.resid, "status": info.status}
+    out["contrast_100"] = c100
     groups = []
     for n in (64, 96, 128):
         q = W.config_c2(n=n, cell=32 if n % 32 == 0 else 16, bf_radius=24.0 * n / 256.0)
@@ -463,10 +477,11 @@ def measure_extras(api, torch):
 
 
 def run_precision_study(args):
-    """C4 precision study: the same contrast-1000 problem solved (1) by the mixed
-    ladder (FP32 sweeps, FP64 correction) to 1e-6, (2) all-FP64 on the GPU to 1e-6
-    and (3) all-FP64 to 1e-9 as the reference; relative L2 errors of eps, sigma and
-    of the translated averages over 4 shifts, sweep counts and times."""
+    """C4 precision study: the same contrast-1000 problem solved by the mixed
+    ladder (FP32 sweeps, FP64 correction) and all-FP64 on the GPU, each with plain
+    sweeps (Algorithm 1) and with conjugate gradients (Algorithm 2), to 1e-6, and
+    all-FP64 to 1e-9 as the reference; relative L2 errors of eps, sigma and of the
+    translated averages over 4 shifts, operator applications and times."""
     import torch
     from paper_2601_00822_gb300 import api, workloads as W
     n = args.precision_study
@@ -477,9 +492,10 @@ def run_precision_study(args):
     out = {"workload": f"C4 at {n}^3: RSA vf 0.3 in 32^3 cells, Young contrast 1000, a = {p.bf_radius:g}",
            "runs": {}}
     fields = {}
-    for name, prec, tol in (("reference_fp64_1e-9", "fp64", 1e-9), ("fp64_1e-6", "fp64", 1e-6),
-                            ("mixed_1e-6", "mixed", 1e-6)):
-        with api.Plan(p.dims, prec) as plan:
+    for name, prec, tol, cg in (("reference_fp64_1e-9", "fp64", 1e-9, False), ("fp64_1e-6", "fp64", 1e-6, False),
+                                ("mixed_1e-6", "mixed", 1e-6, False), ("fp64_cg_1e-6", "fp64", 1e-6, True),
+                                ("mixed_cg_1e-6", "mixed", 1e-6, True)):
+        with api.Plan(p.dims, prec, cg=cg) as plan:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             eps, sig, _, info = plan.solve(ph, p.phases, p.c0, b, tol=tol, maxit=500000)
@@ -493,7 +509,7 @@ def run_precision_study(args):
 
     def relerr(a, r):
         return float(torch.linalg.vector_norm(a - r) / torch.linalg.vector_norm(r))
-    for name in ("fp64_1e-6", "mixed_1e-6"):
+    for name in ("fp64_1e-6", "mixed_1e-6", "fp64_cg_1e-6", "mixed_cg_1e-6"):
         e, s_, a = fields[name]
         out["runs"][name].update({"eps_rel_l2": relerr(e, ref[0]), "sig_rel_l2": relerr(s_, ref[1]),
                                   "avg_rel_l2": relerr(a, ref[2])})

@@ -705,11 +705,15 @@ int run_sets(std::vector<SweepSet<R>*>& sets, int maxit) {
 // state of every member of the set: c = the state, one standard sweep gives
 // s, r = p = s - c (the fixed-point residual is the CG residual), then
 // iterations of A p = p - F^-1 U0 F L1 p (the sweep's passes with the load
-// switched off) until <r, r>_C0 <= (scale tol_m)^2 <r0, r0>_C0 (tol_m: the
-// member's own tolerance) or `maxit` iterations; the state becomes c.  Adds the
+// switched off) until <r, r>_C0 <= rel_m^2 <r0, r0>_C0 or `maxit` iterations
+// (or stagnation); the state becomes c.  rel_m = 0.5 tol_m / req_m, clamped to
+// [floor, 0.5] (floor: 1e-6 in FP32, 1e-13 in FP64), with req_m the member's
+// last measured residual of Eq. 5.11 (req_m <= 0: unknown; then the first
+// sweep's residual is used for a cold start, else rel_m = 0.1).  Adds the
 // operator applications to `applied`.
 template <typename R>
-int run_cg(SweepSet<R>& ss, double scale, int maxit, std::vector<int>& applied) {
+int run_cg(SweepSet<R>& ss, std::vector<double>& req, int maxit, std::vector<int>& applied,
+           const std::vector<char>& finished) {
   bfcs_plan P = ss.P;
   const int B = ss.B;
   cudaStream_t st = P->st;
@@ -734,11 +738,23 @@ int run_cg(SweepSet<R>& ss, double scale, int maxit, std::vector<int>& applied) 
   CK(cudaMemcpyAsync(ca.c, P->spec, vbytes, cudaMemcpyDeviceToDevice, st));
   int e = ss.enqueue(st, -1);
   if (e != BFCS_OK) return e;
+  bool unknown = false;
+  for (int m = 0; m < B; ++m) unknown = unknown || (!(req[m] > 0) && !P->mem_host[m].warm);
+  if (unknown) {   // cold start: the sweep just run evaluated r(eps^0)
+    CK(cudaMemcpyAsync(P->ist_host, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    const int w = sync_stream(P);
+    if (w != BFCS_OK) return w;
+    for (int m = 0; m < B; ++m)
+      if (!(req[m] > 0) && !P->mem_host[m].warm && std::isfinite(P->ist_host[m].resid_last))
+        req[m] = P->ist_host[m].resid_last;
+  }
+  const double floor = sizeof(R) == 4 ? 1e-6 : 1e-13;
   for (int m = 0; m < B; ++m) {
     CgState& h = P->cg_host[m];
     h = CgState{};
     const double tl = P->mem_host[m].tol >= 0 ? P->mem_host[m].tol : ss.tol;
-    h.tol2 = (scale * tl) * (scale * tl);
+    const double rel = req[m] > 0 ? std::min(0.5, std::max(floor, 0.5 * tl / req[m])) : 0.1;
+    h.tol2 = rel * rel;
     h.maxit = std::max(1, maxit);
   }
   CK(cudaMemcpyAsync(P->cg_state, P->cg_host, B * sizeof(CgState), cudaMemcpyHostToDevice, st));
@@ -786,7 +802,8 @@ int run_cg(SweepSet<R>& ss, double scale, int maxit, std::vector<int>& applied) 
     done_all = 1;
     for (int m = 0; m < B; ++m) done_all = done_all && P->cg_host[m].done;
   }
-  for (int m = 0; m < B; ++m) applied[m] += 1 + P->cg_host[m].iters;
+  for (int m = 0; m < B; ++m)
+    if (!finished[m]) applied[m] += 1 + P->cg_host[m].iters;   // finished members skipped both
   CK(cudaMemcpyAsync(P->spec, ca.c, vbytes, cudaMemcpyDeviceToDevice, st));
   return BFCS_OK;
 }
@@ -794,10 +811,10 @@ int run_cg(SweepSet<R>& ss, double scale, int maxit, std::vector<int>& applied) 
 // Algorithm 1 for B members of one grid, advancing together: each sweep is
 // one launch per pass for all members; converged members skip on the device.
 // With BFCS_CG the sweeps are driven by conjugate gradients (Algorithm 2):
-// rounds of CG followed by two verifying sweeps (the first one as a warm
-// start, whose residual is not evaluated); a round whose members do not all
-// meet their tolerance is followed by one with a ten times tighter CG
-// tolerance; after four rounds plain sweeps finish the job.
+// rounds of CG, each aimed at 0.5 tol relative to the last measured residual
+// of Eq. 5.11 and followed by two verifying sweeps (the first one as a warm
+// start, whose residual is not evaluated); rounds repeat while they at least
+// halve the residual, then plain sweeps finish the job.
 template <typename R>
 int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const double* E0, double tol,
               int maxit, bfcs_info* infos, bool any_warm) {
@@ -808,6 +825,7 @@ int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const do
   std::vector<SweepSet<R>*> sets{&ss};
   if (P->use_cg && tol > 0 && maxit > 2) {
     std::vector<int> applied(B, 0), verify(B, 0);
+    std::vector<double> req(B, -1.0);
     int left = maxit;
     if (any_warm) {               // a warm start need not be compatible: one plain sweep makes it so
       e = ss.enqueue(P->st, -1);
@@ -816,30 +834,44 @@ int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const do
       left -= 1;
     }
     bool all = false;
-    double scale = 0.1;
-    for (int round = 0; round < 4 && !all && left > 2; ++round, scale *= 0.1) {
-      e = run_cg<R>(ss, scale, left - 2, applied);
+    std::vector<char> finished(B, 0);      // met the tolerance in a verification: left alone afterwards
+    for (int round = 0; round < 30 && !all && left > 2; ++round) {
+      const std::vector<double> before = req;
+      e = run_cg<R>(ss, req, left - 2, applied, finished);   // finished members skip (iteration state done)
       if (e != BFCS_OK) return e;
       // verify: the CG iterate is the warm start of two sweeps
       for (int m = 0; m < B; ++m) P->mem_host[m].warm = 1;
       e = upload_members(P, B, P->mem_host);
       if (e != BFCS_OK) return e;
       for (int m = 0; m < B; ++m)
-        CK(cudaMemsetAsync(P->ist + m, 0, offsetof(IterState, resid_last), P->st));
+        if (!finished[m]) CK(cudaMemsetAsync(P->ist + m, 0, offsetof(IterState, resid_last), P->st));
       e = run_sets<R>(sets, 2);
       if (e != BFCS_OK) return e;
       CK(cudaMemcpyAsync(P->ist_host, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, P->st));
       const int w = sync_stream(P);
       if (w != BFCS_OK) return w;
       all = true;
+      bool progress = false;
       int most = 0;
       for (int m = 0; m < B; ++m) {
-        verify[m] = P->ist_host[m].iters;
-        applied[m] += verify[m];
+        const IterState& h = P->ist_host[m];
+        if (!finished[m]) {
+          verify[m] = h.iters;
+          applied[m] += verify[m];
+          if (h.done) {
+            finished[m] = 1;
+          } else {
+            all = false;
+            if (std::isfinite(h.resid_last) && h.resid_last > 0) {
+              progress = progress || !(before[m] > 0) || h.resid_last < 0.5 * before[m];
+              req[m] = h.resid_last;
+            }
+          }
+        }
         most = std::max(most, applied[m]);
-        all = all && P->ist_host[m].done;
       }
       left = maxit - most;
+      if (!all && !progress) break;          // CG no longer helps (e.g. the FP32 floor): plain sweeps finish
     }
     if (!all && left > 0) {        // plain sweeps from the last state (same iteration state)
       e = run_sets<R>(sets, left);
