@@ -338,3 +338,33 @@ def translate_average(phase0, table, c0, b, shifts, mean_strain=(0.0,) * 6,
         infos.append((res["sweeps"], res["resid"]))
     m = max(len(infos), 1)
     return acc / m, hits, infos
+
+
+# ---------------------------------------------------------------- effective moduli and concentration
+def unit_strain(J):
+    """Unit mean strain of tensorial component J (xx yy zz yz xz xy): for a shear
+    J both symmetric entries are 1."""
+    E = [0.0] * 6
+    E[J] = 1.0
+    return tuple(E)
+
+
+def effective_moduli(phase, table, c0, tol=1e-12, maxit=4000):
+    """Effective stiffness L* of Eq. 6.3 (<sigma> = L* <eps>, averages of Eqs.
+    6.1-6.2 over the unit cell) and strain concentration A* of Eq. 3.2 (<eps>_i =
+    A* <eps>, <.>_i the average over the inclusion voxels, phase != 0): six
+    solves with b = 0 and the unit mean strains of unit_strain(J) (the classical
+    problem, Eq. 2.24).  Column J of each 6 x 6 matrix is the response to
+    unit_strain(J) in tensorial components.  A* is NaN when there is no
+    inclusion voxel."""
+    nz, ny, nx = phase.shape
+    b = np.zeros((3, nz, ny, nx))
+    incl = phase != 0
+    Ls = np.zeros((6, 6))
+    As = np.full((6, 6), np.nan)
+    for J in range(6):
+        res = solve(phase, table, c0, b, unit_strain(J), tol=tol, maxit=maxit)
+        Ls[:, J] = res["sig"].reshape(6, -1).mean(axis=1)
+        if incl.any():
+            As[:, J] = res["eps"][:, incl].mean(axis=1)
+    return Ls, As

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import bfcs_oracle as O
+from paper_2601_00822_gb300 import workloads as W
 
 RNG = np.random.default_rng(20260103)
 WEIGHT = np.array([1, 1, 1, 2, 2, 2], dtype=float)   # shear components count twice
@@ -488,3 +489,70 @@ def test_translation_direction_by_index():
         for y in range(6):
             for x in range(7):
                 assert g[z, y, x] == f[(z - chi[2]) % 5, (y - chi[1]) % 6, (x - chi[0]) % 7]
+
+
+# ------------------------------------------------------------ effective moduli (Eqs. 6.1-6.3, 3.2)
+def _stiffness_matrix(lam, mu):
+    """Response <sigma>_I to unit tensorial E_J of a homogeneous isotropic medium."""
+    M = np.zeros((6, 6))
+    M[:3, :3] = lam
+    for i in range(3):
+        M[i, i] = lam + 2 * mu
+    for i in range(3, 6):
+        M[i, i] = 2 * mu
+    return M
+
+
+def _laminate_uniaxial(comp, target):
+    """1D laminate along x under reading R1: the stress sigma = c0 + c1 (-1)^x is
+    in equilibrium, the strain comp * sigma must have mean `target` and no
+    Nyquist component.  Returns the stress."""
+    n = comp.size
+    alt = (-1.0) ** np.arange(n)
+    A = np.array([[comp.sum(), (alt * comp).sum()], [(alt * comp).sum(), (alt * alt * comp).sum()]])
+    c0, c1 = np.linalg.solve(A, np.array([n * target, 0.0]))
+    return c0 + c1 * alt
+
+
+def test_effective_moduli_homogeneous_and_identical_phases():
+    phase = np.zeros((4, 4, 6), dtype=np.int8)
+    phase[1:3, 1:3, 2:4] = 1
+    table = [(2.0, 1.5), (2.0, 1.5)]
+    Ls, As = O.effective_moduli(phase, table, (1.0, 1.0), tol=1e-13)
+    assert np.allclose(Ls, _stiffness_matrix(2.0, 1.5), atol=1e-11)
+    assert np.allclose(As, np.eye(6), atol=1e-11)
+
+
+def test_effective_moduli_laminate_closed_forms():
+    nx, ny, nz = 12, 2, 2
+    layers = np.array([0, 1, 1, 0, 0, 0, 1, 0, 1, 1, 1, 0], dtype=np.int8)
+    lam_ph, mu_ph = np.array([1.0, 8.0]), np.array([0.6, 4.0])
+    phase = np.broadcast_to(layers[None, None, :], (nz, ny, nx)).copy()
+    table = list(zip(lam_ph, mu_ph))
+    Ls, As = O.effective_moduli(phase, table, (4.5, 2.3), tol=1e-13, maxit=8000)
+    lam, mu = lam_ph[layers], mu_ph[layers]
+    incl = layers != 0
+    # E = e_xx: sigma_xx uniform up to the Nyquist mode, eps_xx = sigma_xx / (lam + 2 mu)
+    s_xx = _laminate_uniaxial(1.0 / (lam + 2 * mu), 1.0)
+    e_xx = s_xx / (lam + 2 * mu)
+    assert abs(Ls[0, 0] - s_xx.mean()) < 1e-10
+    assert abs(Ls[1, 0] - (lam * e_xx).mean()) < 1e-10 and abs(Ls[2, 0] - Ls[1, 0]) < 1e-10
+    assert abs(As[0, 0] - e_xx[incl].mean()) < 1e-10
+    # E = e_yz (in-plane shear): strain uniform, <sigma_yz> = 2 <mu>
+    assert abs(Ls[3, 3] - 2 * mu.mean()) < 1e-10 and abs(As[3, 3] - 1.0) < 1e-10
+    # E = e_xy (shear across the layers): sigma_xy as in the uniaxial case with compliance 1 / (2 mu)
+    s_xy = _laminate_uniaxial(1.0 / (2 * mu), 1.0)
+    assert abs(Ls[5, 5] - s_xy.mean()) < 1e-10
+    assert abs(As[5, 5] - (s_xy / (2 * mu))[incl].mean()) < 1e-10
+
+
+def test_effective_stiffness_is_symmetric_positive_definite():
+    p = W.config_c1()
+    phase = O.phase_map((8, 8, 8), (8, 8, 8), np.asarray([W.sphere_row(4, 4, 4, 2.6)], dtype=np.int32))
+    Ls, As = O.effective_moduli(phase, p.phases, p.c0, tol=1e-12)
+    S = Ls @ np.diag([1, 1, 1, 0.5, 0.5, 0.5])     # Voigt-symmetric form of the tensorial response
+    assert np.allclose(S, S.T, atol=1e-9 * abs(S).max())
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > 0
+    # between the phases' stiffnesses (Voigt / Reuss-type ordering of the bulk response)
+    k = S[:3, :3].sum() / 9
+    assert p.phases[0][0] + 2 / 3 * p.phases[0][1] < k < p.phases[1][0] + 2 / 3 * p.phases[1][1]
