@@ -245,6 +245,28 @@ int bfcs_translate_average(bfcs_plan plan, const int8_t* phase, int nphases, con
                            int32_t* hits_out, bfcs_info* infos);
 
 /*
+ * bfcs_effective_stiffness - effective stiffness L* and inclusion strain
+ * concentration A* of the periodic microstructure (Eqs. 6.1-6.3 and Eq. 3.2):
+ * the classical problem (b = 0, Eq. 2.24) is solved under the six unit mean
+ * strains E_J (J = xx yy zz yz xz xy, tensorial: a unit shear sets both
+ * symmetric entries to 1), min(max_batch, 6) members at a time through
+ * bfcs_solve_batched, and the fields are averaged in FP64 on the device.
+ *  phase:  dev, N int8 phase ids; phases, C0, tol, maxit as for bfcs_solve.
+ *  Lstar:  host, 36 doubles, row-major: Lstar[6 I + J] = <sigma_I> (cell
+ *          average) for E = E_J, i.e. <sigma> = Lstar <eps> in tensorial
+ *          components.
+ *  Astar:  host, 36 doubles or NULL: Astar[6 I + J] = average of eps_I over
+ *          the inclusion voxels (phase != 0) for E = E_J; NaN when there is
+ *          no inclusion voxel.
+ *  infos:  host, 6 entries (one per E_J) or NULL.
+ * Uses the plan's translated-averaging scratch (allocated on first use).
+ * Returns the most severe member status (as bfcs_solve_batched).
+ */
+int bfcs_effective_stiffness(bfcs_plan plan, const int8_t* phase, int nphases, const bfcs_lame* phases,
+                             bfcs_lame C0, double tol, int maxit, double* Lstar, double* Astar,
+                             bfcs_info* infos);
+
+/*
  * Learned warm start / surrogate.  The paper proposes replacing the solver by
  * a learned map of the averaged nonlocal response (Sec. 6, Eqs. 6.9-6.10,
  * Fig. 5) without fixing a model; this library's model is a 4-level 3D U-net

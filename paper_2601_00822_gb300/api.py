@@ -212,6 +212,21 @@ class Plan:
         _lib.check(code, "bfcs_translate_average", allow)
         return avg, hits, [SolveInfo.of(infos[m]) for m in range(sh.shape[0])]
 
+    def effective_stiffness(self, phase, phases, c0, tol=1e-6, maxit=10000,
+                            allow=(_lib.OK, _lib.NOT_CONVERGED)):
+        """bfcs_effective_stiffness: (L* (6, 6), A* (6, 6), infos) with column J the
+        response to the unit tensorial mean strain J (Eqs. 6.1-6.3, 3.2)."""
+        _check_tensor(phase, (self.dims[2], self.dims[1], self.dims[0]), torch.int8, "phase")
+        ls = np.zeros(36)
+        as_ = np.zeros(36)
+        infos = (_lib.Info * 6)()
+        code = self.lib.bfcs_effective_stiffness(self.handle, _ptr(phase), len(phases), _lames(phases),
+                                                 _lib.Lame(*c0), float(tol), int(maxit),
+                                                 ls.ctypes.data_as(C.c_void_p),
+                                                 as_.ctypes.data_as(C.c_void_p), infos)
+        _lib.check(code, "bfcs_effective_stiffness", allow)
+        return ls.reshape(6, 6), as_.reshape(6, 6), [SolveInfo.of(infos[m]) for m in range(6)]
+
     def fft3d(self, x, direction=-1):
         """bfcs_fft3d: forward real (c, nz, ny, nx) -> complex (c, nz, ny, nx/2+1) or back
         (inverse without the 1/N factor)."""

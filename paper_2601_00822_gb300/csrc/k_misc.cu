@@ -422,6 +422,62 @@ cudaError_t launch_scale(double* acc, long long count, double f, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- effective moduli (Eqs. 6.1-6.3, 3.2)
+// Per member m (blockIdx.y): the 13 FP64 sums  sum sigma_c (6), sum over the
+// inclusion voxels (phase != 0) of eps_c (6) and their count, as one partial per
+// block in part[(m * gridDim.x + block) * 13 + j]; k_moduli_final adds them in
+// block order, so the result does not depend on the launch.
+template <typename R>
+__global__ void __launch_bounds__(256) k_moduli_partial(ModArgs<R> a, double* part) {
+  const int m = blockIdx.y;
+  const R* eps = a.eps[m];
+  const R* sig = a.sig[m];
+  const long long n = a.n;
+  double acc[kModSums];
+#pragma unroll
+  for (int j = 0; j < kModSums; ++j) acc[j] = 0.0;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    const bool in = a.phase[v] != 0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      acc[c] += (double)sig[c * n + v];
+      if (in) acc[6 + c] += (double)eps[c * n + v];
+    }
+    if (in) acc[12] += 1.0;
+  }
+  __shared__ double red[kModSums][8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kModSums; ++j) {
+    double t = acc[j];
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if (lane == 0) red[j][w] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < kModSums) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x / 32; ++k) t += red[threadIdx.x][k];
+    part[((long long)m * gridDim.x + blockIdx.x) * kModSums + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_moduli_final(const double* part, int nparts, double* out) {
+  const int m = blockIdx.x, j = threadIdx.x;
+  if (j >= kModSums) return;
+  double t = 0.0;
+  for (int k = 0; k < nparts; ++k) t += part[((long long)m * nparts + k) * kModSums + j];
+  out[m * kModSums + j] = t;
+}
+
+template <typename R>
+cudaError_t launch_moduli(const ModArgs<R>& a, int batch, double* part, double* out, cudaStream_t s) {
+  k_moduli_partial<R><<<dim3(kModParts, batch), 256, 0, s>>>(a, part);
+  k_moduli_final<<<batch, 32, 0, s>>>(part, kModParts, out);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- precision-ladder helpers
 __global__ void k_cast_d2f(float* dst, const double* src, long long count) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -503,7 +559,8 @@ cudaError_t launch_stress(double* sig, const double* eps, const int8_t* phase, c
                                       cudaStream_t, int, long long);                              \
   template cudaError_t launch_accumulate<R>(double*, int*, const R*, const R*, const R*,           \
                                             const int8_t*, int, int, int, int, int, int,          \
-                                            cudaStream_t);
+                                            cudaStream_t);                                        \
+  template cudaError_t launch_moduli<R>(const ModArgs<R>&, int, double*, double*, cudaStream_t);
 BFCS_INST(float)
 BFCS_INST(double)
 #undef BFCS_INST

@@ -232,4 +232,20 @@ cudaError_t launch_accumulate(double* acc, int* hits, const R* eps, const R* sig
                               cudaStream_t s);
 cudaError_t launch_scale(double* acc, long long count, double f, cudaStream_t s);
 
+// Effective moduli (Eqs. 6.1-6.3, 3.2): for each of up to kModMembers members the
+// FP64 sums of sigma over the cell, of eps over the inclusion voxels and their
+// count (kModSums values per member, written to out[m * kModSums + j]).
+constexpr int kModMembers = 6;
+constexpr int kModSums = 13;
+constexpr int kModParts = 2 * 152;
+template <typename R>
+struct ModArgs {
+  const R* eps[kModMembers];
+  const R* sig[kModMembers];
+  const int8_t* phase;
+  long long n;
+};
+template <typename R>
+cudaError_t launch_moduli(const ModArgs<R>& a, int batch, double* part, double* out, cudaStream_t s);
+
 }  // namespace bfcs

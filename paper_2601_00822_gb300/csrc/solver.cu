@@ -49,6 +49,7 @@ struct bfcs_plan_s {
   double* dval_host = nullptr;     // pinned
   void* tmp = nullptr;             // 15 x N real: eps, sig, u for averaging members
   int* tmp_hits = nullptr;         // N int
+  double* mod_buf = nullptr;       // effective-moduli partial sums and totals
   // measurement hook: CUDA events around the launches of one kernel kind
   int prof_kind = 0;
   std::vector<cudaEvent_t> prof_ev;   // start/end pairs
@@ -140,7 +141,7 @@ void free_plan(bfcs_plan P) {
   cudaFree(P->part); cudaFree(P->ist); cudaFree(P->hist); cudaFree(P->mem_dev);
   if (P->mem_host) cudaFreeHost(P->mem_host);
   cudaFree(P->ival); cudaFree(P->dval); cudaFree(P->dscratch);
-  cudaFree(P->tmp); cudaFree(P->tmp_hits);
+  cudaFree(P->tmp); cudaFree(P->tmp_hits); cudaFree(P->mod_buf);
   cudaFree(P->spec64); cudaFree(P->bhat64); cudaFree(P->ist64); cudaFree(P->r32); cudaFree(P->u64);
   for (int i = 0; i < 3; ++i) cudaFree(P->tw64[i]);
   if (P->ist_host) cudaFreeHost(P->ist_host);
@@ -1381,6 +1382,65 @@ int translate_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* 
   return w != BFCS_OK ? w : worst;
 }
 
+// Effective stiffness L* (<sigma> = L* <eps>, Eqs. 6.1-6.3) and inclusion strain
+// concentration A* (<eps>_i = A* <eps>, Eq. 3.2): the classical problem (b = 0)
+// under the six unit mean strains, min(max_batch, 6) members at a time; column
+// J of both matrices is the response to unit tensorial strain J.  The members'
+// fields sit in the plan's scratch: eps, sigma, and in the displacement slot
+// the zero load (no displacement is formed).
+template <typename R>
+int moduli_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0, double tol,
+                int maxit, double* Lstar, double* Astar, bfcs_info* infos) {
+  if (phase == nullptr || Lstar == nullptr) return BFCS_ERR_INVALID_ARG;
+  int e = ensure_tmp(P);
+  if (e != BFCS_OK) return e;
+  if (P->mod_buf == nullptr &&
+      cudaMalloc(&P->mod_buf, (size_t)kModMembers * (kModParts + 1) * kModSums * sizeof(double)) != cudaSuccess)
+    return BFCS_ERR_OOM;
+  const long long n = P->g.n;
+  double* part = P->mod_buf;
+  double* sums = P->mod_buf + (size_t)kModMembers * kModParts * kModSums;
+  const int chunk = std::min(P->max_batch, kModMembers);
+  int worst = BFCS_OK;
+  for (int start = 0; start < kModMembers; start += chunk) {
+    const int B = std::min(chunk, kModMembers - start);
+    bfcs_problem pr[kModMembers];
+    ModArgs<R> ma{};
+    for (int m = 0; m < B; ++m) {
+      R* eps = (R*)P->tmp + (size_t)m * 15 * n;
+      R* b = eps + 12 * n;
+      CK(cudaMemsetAsync(b, 0, 3 * n * sizeof(R), P->st));
+      bfcs_problem& q = pr[m];
+      std::memset(&q, 0, sizeof(q));
+      q.phase = phase;
+      q.b = b;
+      q.E[start + m] = 1.0;
+      q.eps_out = eps;
+      q.sig_out = eps + 6 * n;
+      ma.eps[m] = eps;
+      ma.sig[m] = eps + 6 * n;
+    }
+    ma.phase = phase;
+    ma.n = n;
+    const int s = bfcs_solve_batched(P, B, pr, nph, phases, C0, tol, maxit, infos != nullptr ? infos + start : nullptr);
+    if (s < 0) return s;
+    if (severity(s) > severity(worst)) worst = s;
+    CK(launch_moduli<R>(ma, B, part, sums + (size_t)start * kModSums, P->st));
+  }
+  double host[kModMembers * kModSums];
+  CK(cudaMemcpyAsync(host, sums, sizeof(host), cudaMemcpyDeviceToHost, P->st));
+  const int w = sync_stream(P);
+  if (w != BFCS_OK) return w;
+  for (int J = 0; J < 6; ++J) {
+    const double* h = host + J * kModSums;
+    for (int I = 0; I < 6; ++I) {
+      Lstar[I * 6 + J] = h[I] / (double)n;
+      if (Astar != nullptr) Astar[I * 6 + J] = h[12] > 0.0 ? h[6 + I] / h[12] : std::nan("");
+    }
+  }
+  return worst;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1627,6 +1687,13 @@ int bfcs_translate_average(bfcs_plan P, const int8_t* phase, int nph, const bfcs
                                           avg_out, hits_out, infos)
                  : translate_impl<float>(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit,
                                          avg_out, hits_out, infos);
+}
+
+int bfcs_effective_stiffness(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                             double tol, int maxit, double* Lstar, double* Astar, bfcs_info* infos) {
+  if (P == nullptr) return BFCS_ERR_INVALID_ARG;
+  return P->fp64 || P->mixed ? moduli_impl<double>(P, phase, nph, phases, C0, tol, maxit, Lstar, Astar, infos)
+                             : moduli_impl<float>(P, phase, nph, phases, C0, tol, maxit, Lstar, Astar, infos);
 }
 
 int bfcs_plan_tuning(bfcs_plan P, int* col_variant, int* col_tile, int* col_swap, double* variant_ms) {

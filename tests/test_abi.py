@@ -28,6 +28,20 @@ def test_library_exports_every_declared_symbol():
         assert getattr(raw, name) is not None
 
 
+def test_every_export_has_a_ctypes_signature():
+    lib = _lib.load()
+    for name in _lib.EXPORTS:
+        assert getattr(lib, name).argtypes is not None, name
+
+
+def test_effective_stiffness_rejects_null_arguments():
+    lib = _lib.load()
+    out = (ctypes.c_double * 36)()
+    lame = (_lib.Lame * 1)(_lib.Lame(1.0, 0.5))
+    assert lib.bfcs_effective_stiffness(None, None, 1, lame, _lib.Lame(1.0, 0.5), 1e-6, 10, out, None,
+                                        None) == _lib.ERR_INVALID_ARG
+
+
 def test_status_strings_without_gpu():
     lib = _lib.load()
     for code in (0, 1, -1, -2, -3, -4, -5, -6, -7):

@@ -556,3 +556,7 @@ def test_effective_stiffness_is_symmetric_positive_definite():
     # between the phases' stiffnesses (Voigt / Reuss-type ordering of the bulk response)
     k = S[:3, :3].sum() / 9
     assert p.phases[0][0] + 2 / 3 * p.phases[0][1] < k < p.phases[1][0] + 2 / 3 * p.phases[1][1]
+    # sigma = L(x) eps voxel by voxel, so for two phases <sigma> = L_m E + f (L_i - L_m) <eps>_i
+    f = (phase != 0).mean()
+    L0, L1 = _stiffness_matrix(*p.phases[0]), _stiffness_matrix(*p.phases[1])
+    assert np.allclose(Ls, L0 + f * (L1 - L0) @ As, atol=1e-12 * abs(Ls).max())
