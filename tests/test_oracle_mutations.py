@@ -36,7 +36,30 @@ MUTATIONS = {
     "body_force_sign": ("-6.0 * x * s * s / (a * a)", "6.0 * x * s * s / (a * a)"),
     "sphere_boundary_exclusive": ("ph[d2 <= T] = p", "ph[d2 < T] = p"),
     "residual_misses_load": ("div = div_hat(sig_hat, xi) + b_hat", "div = div_hat(sig_hat, xi)"),
+    "moduli_engineering_shear": ("    E[J] = 1.0\n", "    E[J] = 1.0 if J < 3 else 0.5\n"),
+    "concentration_over_all_voxels": ('As[:, J] = res["eps"][:, incl].mean(axis=1)',
+                                      'As[:, J] = res["eps"].reshape(6, -1).mean(axis=1)'),
+    "stiffness_over_inclusions": ('Ls[:, J] = res["sig"].reshape(6, -1).mean(axis=1)',
+                                  'Ls[:, J] = res["sig"][:, incl].mean(axis=1)'),
 }
+
+
+def run_pins(tmp_path, src):
+    (tmp_path / "oracle").mkdir()
+    (tmp_path / "oracle" / "__init__.py").write_text("")
+    (tmp_path / "oracle" / "bfcs_oracle.py").write_text(src)
+    (tmp_path / "tests").mkdir()
+    shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "tests")
+    env = dict(os.environ, PYTHONPATH=str(tmp_path))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           "tests/test_oracle_pins.py"], cwd=tmp_path, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_unmutated_copy_passes(tmp_path):
+    """Control: the copied pin suite runs and passes on the real oracle alone."""
+    r = run_pins(tmp_path, open(os.path.join(ROOT, "oracle", "bfcs_oracle.py")).read())
+    assert r.returncode == 0, r.stdout[-2000:]
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
@@ -44,13 +67,7 @@ def test_planted_mistake_is_caught(name, tmp_path):
     before, after = MUTATIONS[name]
     src = open(os.path.join(ROOT, "oracle", "bfcs_oracle.py")).read()
     assert src.count(before) == 1, "mutation anchor drifted"
-    (tmp_path / "oracle").mkdir()
-    (tmp_path / "oracle" / "__init__.py").write_text("")
-    (tmp_path / "oracle" / "bfcs_oracle.py").write_text(src.replace(before, after))
-    (tmp_path / "tests").mkdir()
-    shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "tests")
-    env = dict(os.environ, PYTHONPATH=str(tmp_path))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py"], cwd=tmp_path, env=env,
-                       capture_output=True, text=True, timeout=600)
+    r = run_pins(tmp_path, src.replace(before, after))
     assert r.returncode != 0, f"planted mistake {name!r} passed every pin:\n{r.stdout[-2000:]}"
+    # caught by a failing pin, not by an import or collection error
+    assert r.returncode == 1 and " failed" in r.stdout and " error" not in r.stdout, r.stdout[-2000:]
