@@ -340,6 +340,35 @@ def translate_average(phase0, table, c0, b, shifts, mean_strain=(0.0,) * 6,
     return acc / m, hits, infos
 
 
+# ---------------------------------------------------------------- ensemble dataset D^d
+def ensemble_average(configs, table, c0, b, mean_strain=(0.0,) * 6, tol=1e-10, maxit=1000):
+    """Ensemble dataset of Eq. 3.8: the same load b is applied to each of the
+    deterministic configurations X^j (phase maps, none derived from another),
+    each is solved, and the fields are averaged over the configurations in the
+    way Eq. 3.7 averages over translations: u, V u, eps, V eps, sigma, V sigma
+    (V the inclusion indicator of the configuration, phase != 0) summed and
+    divided by the number of configurations.  Returns (avg (30, nz, ny, nx) in
+    the order of translate_average, hits (number of configurations with
+    V = 1), infos)."""
+    configs = list(configs)
+    nz, ny, nx = configs[0].shape
+    acc = np.zeros((30, nz, ny, nx))
+    hits = np.zeros((nz, ny, nx), dtype=np.int64)
+    infos = []
+    for ph in configs:
+        res = solve(ph, table, c0, b, mean_strain, tol, maxit)
+        v = (ph != 0).astype(float)
+        acc[0:3] += res["u"]
+        acc[3:6] += v * res["u"]
+        acc[6:12] += res["eps"]
+        acc[12:18] += v * res["eps"]
+        acc[18:24] += res["sig"]
+        acc[24:30] += v * res["sig"]
+        hits += (ph != 0)
+        infos.append((res["sweeps"], res["resid"]))
+    return acc / len(configs), hits, infos
+
+
 # ---------------------------------------------------------------- effective moduli and concentration
 def unit_strain(J):
     """Unit mean strain of tensorial component J (xx yy zz yz xz xy): for a shear

@@ -39,6 +39,8 @@ MUTATIONS = {
     "moduli_engineering_shear": ("    E[J] = 1.0\n", "    E[J] = 1.0 if J < 3 else 0.5\n"),
     "concentration_over_all_voxels": ('As[:, J] = res["eps"][:, incl].mean(axis=1)',
                                       'As[:, J] = res["eps"].reshape(6, -1).mean(axis=1)'),
+    "ensemble_indicator_of_first_configuration": ("        v = (ph != 0).astype(float)\n        acc[0:3] += res[\"u\"]\n        acc[3:6] += v * res[\"u\"]\n        acc[6:12] += res[\"eps\"]\n        acc[12:18] += v * res[\"eps\"]\n        acc[18:24] += res[\"sig\"]\n        acc[24:30] += v * res[\"sig\"]\n        hits += (ph != 0)\n        infos.append((res[\"sweeps\"], res[\"resid\"]))\n    return acc / len(configs)",
+                                                  "        v = (configs[0] != 0).astype(float)\n        acc[0:3] += res[\"u\"]\n        acc[3:6] += v * res[\"u\"]\n        acc[6:12] += res[\"eps\"]\n        acc[12:18] += v * res[\"eps\"]\n        acc[18:24] += res[\"sig\"]\n        acc[24:30] += v * res[\"sig\"]\n        hits += (ph != 0)\n        infos.append((res[\"sweeps\"], res[\"resid\"]))\n    return acc / len(configs)"),
     "stiffness_over_inclusions": ('Ls[:, J] = res["sig"].reshape(6, -1).mean(axis=1)',
                                   'Ls[:, J] = res["sig"][:, incl].mean(axis=1)'),
 }

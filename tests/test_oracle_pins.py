@@ -559,3 +559,55 @@ def test_effective_stiffness_is_symmetric_positive_definite():
     f = (phase != 0).mean()
     L0, L1 = _stiffness_matrix(*phases[0]), _stiffness_matrix(*phases[1])
     assert np.allclose(Ls, L0 + f * (L1 - L0) @ As, atol=1e-12 * abs(Ls).max())
+
+
+# ------------------------------------------------------------ ensemble dataset D^d (Eq. 3.8)
+def _ensemble_case():
+    nx, ny, nz = 8, 6, 4
+    ph = (RNG.random((nz, ny, nx)) < 0.3).astype(np.int8)
+    ph[RNG.random((nz, ny, nx)) < 0.15] = 2
+    table = [(1.0, 0.5), (6.0, 3.0), (0.4, 0.2)]
+    b = O.body_force((nx, ny, nz), (4.0, 3.0, 2.0), 2.5)
+    return ph, table, (3.2, 1.6), b
+
+
+def test_ensemble_of_one_configuration_is_its_solution():
+    ph, table, c0, b = _ensemble_case()
+    avg, hits, _ = O.ensemble_average([ph, ph, ph], table, c0, b, tol=1e-12)
+    res = O.solve(ph, table, c0, b, tol=1e-12)
+    v = (ph != 0)
+    assert np.allclose(avg[0:3], res["u"], atol=1e-13) and np.allclose(avg[3:6], v * res["u"], atol=1e-13)
+    assert np.allclose(avg[6:12], res["eps"], atol=1e-13) and np.allclose(avg[24:30], v * res["sig"], atol=1e-13)
+    assert np.array_equal(hits, 3 * v)
+
+
+def test_ensemble_of_mirror_pair_is_mirror_symmetric():
+    """X and its reflection x -> 2c - x about the load centre plane c = 4: b_x is
+    odd, so the averaged fields of the pair are symmetric under the reflection
+    (vectors: x component odd; symmetric tensors: xz, xy odd), the inclusion
+    weighted ones included."""
+    ph, table, c0, b = _ensemble_case()
+    refl = ph[:, :, ::-1].copy()                 # voxel i -> 2c - 1 - i = 7 - i for c = 4
+    assert np.allclose(b[0][:, :, ::-1], -b[0], atol=1e-15)
+    avg, hits, _ = O.ensemble_average([ph, refl], table, c0, b, tol=1e-13, maxit=4000)
+    vec_sign = np.array([-1, 1, 1])[:, None, None, None]
+    ten_sign = np.array([1, 1, 1, 1, -1, -1])[:, None, None, None]
+    for lo, sign in ((0, vec_sign), (3, vec_sign), (6, ten_sign), (12, ten_sign), (18, ten_sign), (24, ten_sign)):
+        f = avg[lo:lo + sign.shape[0]]
+        assert np.abs(f[..., ::-1] - sign * f).max() <= 1e-11 * np.abs(f).max(), lo
+    assert np.array_equal(hits, hits[:, :, ::-1])
+    # a single configuration is not symmetric, so the pair's symmetry is not trivial
+    one, _, _ = O.ensemble_average([ph], table, c0, b, tol=1e-13, maxit=4000)
+    assert np.abs(one[12:18][..., ::-1] - ten_sign * one[12:18]).max() > 1e-3 * np.abs(one[12:18]).max()
+
+
+def test_ensemble_of_all_translations_is_the_translated_average():
+    """Eq. 3.8 is the dataset of Eq. 3.7 with configurations in place of
+    translations: the ensemble of the translated copies of one cell gives the
+    translated average."""
+    ph, table, c0, b = _ensemble_case()
+    shifts = [(0, 0, 0), (3, 1, 0), (5, 4, 2), (1, 5, 3)]
+    configs = [O.translate(ph, np.asarray(s)) for s in shifts]
+    avg_e, hits_e, _ = O.ensemble_average(configs, table, c0, b, tol=1e-12)
+    avg_t, hits_t, _ = O.translate_average(ph, table, c0, b, shifts, tol=1e-12)
+    assert np.allclose(avg_e, avg_t, atol=1e-14) and np.array_equal(hits_e, hits_t)
