@@ -245,6 +245,23 @@ int bfcs_translate_average(bfcs_plan plan, const int8_t* phase, int nphases, con
                            int32_t* hits_out, bfcs_info* infos);
 
 /*
+ * bfcs_ensemble_average - the ensemble dataset of Eq. 3.8: the fixed load b is
+ * applied to each of nconf deterministic configurations X^j (phase maps with
+ * no relation to one another, e.g. different samples), each is solved, and
+ * the fields are averaged over the configurations as bfcs_translate_average
+ * averages over translations (same 30 FP64 output fields; ^(1) weighted by
+ * each configuration's own inclusion indicator, still divided by nconf).
+ *  configs: host array of nconf device pointers, each N int8 phase ids.
+ *  hits_out: dev, N int32 or NULL: number of configurations with phase != 0.
+ *  infos:   host, nconf entries or NULL.
+ * Other arguments and the batching (max_batch configurations per batched
+ * solve) as bfcs_translate_average.
+ */
+int bfcs_ensemble_average(bfcs_plan plan, int nconf, const int8_t* const* configs, int nphases,
+                          const bfcs_lame* phases, bfcs_lame C0, const void* b, const double E[6], double tol,
+                          int maxit, double* avg_out, int32_t* hits_out, bfcs_info* infos);
+
+/*
  * bfcs_effective_stiffness - effective stiffness L* and inclusion strain
  * concentration A* of the periodic microstructure (Eqs. 6.1-6.3 and Eq. 3.2):
  * the classical problem (b = 0, Eq. 2.24) is solved under the six unit mean

@@ -35,7 +35,7 @@ EXPORTS = (
     "bfcs_profile_read", "bfcs_body_force_noalloc", "bfcs_net_param_count", "bfcs_net_create",
     "bfcs_net_destroy", "bfcs_net_prepare", "bfcs_net_forward", "bfcs_net_grad", "bfcs_net_adam",
     "bfcs_net_train_step", "bfcs_net_predict", "bfcs_plan_tuning", "bfcs_solve_group", "bfcs_net_status",
-    "bfcs_effective_stiffness",
+    "bfcs_effective_stiffness", "bfcs_ensemble_average",
 )
 NET_PARAMS = 523654
 NET_TRAIN = 1
@@ -95,6 +95,8 @@ def _declare(lib):
                                      C.POINTER(vp)]
     lib.bfcs_solve_group.argtypes = [i, C.POINTER(GroupItem), i, C.POINTER(Lame), Lame, d, i]
     lib.bfcs_plan_tuning.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(d)]
+    lib.bfcs_ensemble_average.argtypes = [vp, i, C.POINTER(vp), i, C.POINTER(Lame), Lame, vp, C.POINTER(d), d, i,
+                                         vp, vp, C.POINTER(Info)]
     lib.bfcs_effective_stiffness.argtypes = [vp, vp, i, C.POINTER(Lame), Lame, d, i, vp, vp, C.POINTER(Info)]
     lib.bfcs_status_string.argtypes = [i]
     lib.bfcs_status_string.restype = C.c_char_p

@@ -212,6 +212,23 @@ class Plan:
         _lib.check(code, "bfcs_translate_average", allow)
         return avg, hits, [SolveInfo.of(infos[m]) for m in range(sh.shape[0])]
 
+    def ensemble_average(self, configs, phases, c0, b, E=(0.0,) * 6, tol=1e-6, maxit=10000,
+                         allow=(_lib.OK, _lib.NOT_CONVERGED)):
+        """bfcs_ensemble_average (Eq. 3.8); returns (avg (30, nz, ny, nx) float64, hits int32, infos)."""
+        nx, ny, nz = self.dims
+        for ph in configs:
+            _check_tensor(ph, (nz, ny, nx), torch.int8, "configs[j]")
+        ptrs = (C.c_void_p * len(configs))(*[_ptr(ph) for ph in configs])
+        avg = torch.empty((30, nz, ny, nx), dtype=torch.float64, device="cuda")
+        hits = torch.empty((nz, ny, nx), dtype=torch.int32, device="cuda")
+        infos = (_lib.Info * len(configs))()
+        e = (C.c_double * 6)(*[float(v) for v in E])
+        code = self.lib.bfcs_ensemble_average(self.handle, len(configs), ptrs, len(phases), _lames(phases),
+                                              _lib.Lame(*c0), _ptr(b), e, float(tol), int(maxit), _ptr(avg),
+                                              _ptr(hits), infos)
+        _lib.check(code, "bfcs_ensemble_average", allow)
+        return avg, hits, [SolveInfo.of(infos[m]) for m in range(len(configs))]
+
     def effective_stiffness(self, phase, phases, c0, tol=1e-6, maxit=10000,
                             allow=(_lib.OK, _lib.NOT_CONVERGED)):
         """bfcs_effective_stiffness: (L* (6, 6), A* (6, 6), infos) with column J the

@@ -1298,19 +1298,37 @@ int ensure_tmp(bfcs_plan P) {
   return BFCS_OK;
 }
 
+// Member m of an averaging run: its phase map (the shared one translated by
+// shift m, Eqs. 3.3-3.6, or configuration m of an ensemble, Eq. 3.8).
+struct AvgMembers {
+  const int8_t* phase;                // shared phase map (translations) or nullptr
+  const int8_t* const* configs;       // host array of configuration phase maps or nullptr
+  const int32_t* shifts;              // host, 3 per member, or nullptr (no translation)
+  const int8_t* phase_of(int m) const { return configs != nullptr ? configs[m] : phase; }
+  void shift_of(int m, int out[3]) const {
+    for (int a = 0; a < 3; ++a) out[a] = shifts != nullptr ? shifts[3 * m + a] : 0;
+  }
+};
+
+// Averages over `count` members with the load b fixed: u, V u, eps, V eps,
+// sigma, V sigma summed in FP64 and divided by count (V = phase != 0 of the
+// member's own phase map), max_batch members per batched solve.
 template <typename R>
-int translate_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
-                   const void* b, const double* E, int nshift, const int32_t* shifts, double tol,
-                   int maxit, double* avg, int32_t* hits, bfcs_info* infos) {
+int average_impl(bfcs_plan P, int count, const AvgMembers& am, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                 const void* b, const double* E, double tol, int maxit, double* avg, int32_t* hits,
+                 bfcs_info* infos) {
   int e = check_material(nph, phases, C0);
   if (e != BFCS_OK) return e;
-  if (phase == nullptr || b == nullptr || E == nullptr || avg == nullptr || shifts == nullptr ||
-      nshift < 1 || !(tol >= 0) || maxit < 0)
+  if (b == nullptr || E == nullptr || avg == nullptr || count < 1 || !(tol >= 0) || maxit < 0)
     return BFCS_ERR_INVALID_ARG;
+  for (int m = 0; m < count; ++m)
+    if (am.phase_of(m) == nullptr) return BFCS_ERR_INVALID_ARG;
   e = ensure_tmp(P);
   if (e != BFCS_OK) return e;
-  e = validate_inputs<R>(P, phase, b, nph);
-  if (e != BFCS_OK) return e;
+  if (am.configs == nullptr) {
+    e = validate_inputs<R>(P, am.phase, b, nph);
+    if (e != BFCS_OK) return e;
+  }
   const long long n = P->g.n;
   int* h = hits != nullptr ? (int*)hits : P->tmp_hits;
   CK(cudaMemsetAsync(avg, 0, 30 * n * sizeof(double), P->st));
@@ -1318,38 +1336,46 @@ int translate_impl(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* p
   const PhaseTab<R> tab = make_tab<R>(nph, phases, C0);
   int worst = BFCS_OK;
   std::vector<Member> mem;
-  for (int start = 0; start < nshift; start += P->max_batch) {
-    const int B = std::min(P->max_batch, nshift - start);
+  for (int start = 0; start < count; start += P->max_batch) {
+    const int B = std::min(P->max_batch, count - start);
+    if (am.configs != nullptr) {
+      const std::vector<const void*> bs(B, b);
+      e = validate_members<R>(P, B, am.configs + start, bs.data(), nph);
+      if (e != BFCS_OK) return e;
+    }
     mem.clear();
     for (int m = 0; m < B; ++m) {
       R* eps = (R*)P->tmp + (size_t)m * 15 * n;
-      const int32_t* sh = shifts + 3 * (start + m);
-      const int shv[3] = {sh[0], sh[1], sh[2]};
-      mem.push_back(make_member(phase, shv, E, b, nullptr, SolveOut{eps, eps + 6 * n, eps + 12 * n}));
+      int shv[3];
+      am.shift_of(start + m, shv);
+      mem.push_back(make_member(am.phase_of(start + m), shv, E, b, nullptr,
+                                SolveOut{eps, eps + 6 * n, eps + 12 * n}));
     }
     e = upload_members(P, B, mem.data());
     if (e != BFCS_OK) return e;
-    e = transform_members<R>(P, B);            // b is fixed under translation (Eq. 3.4)
+    e = transform_members<R>(P, B);            // b is fixed (Eq. 3.4)
     if (e != BFCS_OK) return e;
     const int s = run_batch<R>(P, B, tab, C0, E, tol, maxit, infos != nullptr ? infos + start : nullptr, false);
     if (s < 0) return s;
     if (severity(s) > severity(worst)) worst = s;
     for (int m = 0; m < B; ++m) {
       const R* eps = (const R*)P->tmp + (size_t)m * 15 * n;
-      CK(launch_accumulate<R>(avg, h, eps, eps + 6 * n, eps + 12 * n, phase, mem[m].sx, mem[m].sy, mem[m].sz,
-                              P->g.nx, P->g.ny, P->g.nz, P->st));
+      CK(launch_accumulate<R>(avg, h, eps, eps + 6 * n, eps + 12 * n, mem[m].phase, mem[m].sx, mem[m].sy,
+                              mem[m].sz, P->g.nx, P->g.ny, P->g.nz, P->st));
     }
   }
-  CK(launch_scale(avg, 30 * n, 1.0 / nshift, P->st));
+  CK(launch_scale(avg, 30 * n, 1.0 / count, P->st));
   const int w = sync_stream(P);
   return w != BFCS_OK ? w : worst;
 }
 
-int translate_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
-                    const void* b, const double* E, int nshift, const int32_t* shifts, double tol, int maxit,
-                    double* avg, int32_t* hits, bfcs_info* infos) {
-  if (avg == nullptr || shifts == nullptr || nshift < 1 || E == nullptr || phase == nullptr || b == nullptr)
-    return BFCS_ERR_INVALID_ARG;
+// The same through the batched precision ladder (fields in FP64).
+int average_mixed(bfcs_plan P, int count, const AvgMembers& am, int nph, const bfcs_lame* phases,
+                  bfcs_lame C0, const void* b, const double* E, double tol, int maxit, double* avg,
+                  int32_t* hits, bfcs_info* infos) {
+  if (avg == nullptr || count < 1 || E == nullptr || b == nullptr) return BFCS_ERR_INVALID_ARG;
+  for (int m = 0; m < count; ++m)
+    if (am.phase_of(m) == nullptr) return BFCS_ERR_INVALID_ARG;
   int e = ensure_tmp(P);
   if (e != BFCS_OK) return e;
   const long long n = P->g.n;
@@ -1358,14 +1384,15 @@ int translate_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* 
   CK(cudaMemsetAsync(h, 0, n * sizeof(int), P->st));
   int worst = BFCS_OK;
   std::vector<Member> mem;
-  for (int start = 0; start < nshift; start += P->max_batch) {   // the batched ladder, max_batch shifts at a time
-    const int B = std::min(P->max_batch, nshift - start);
+  for (int start = 0; start < count; start += P->max_batch) {   // the batched ladder, max_batch members at a time
+    const int B = std::min(P->max_batch, count - start);
     mem.clear();
     for (int m = 0; m < B; ++m) {
       double* eps = (double*)P->tmp + (size_t)m * 15 * n;
-      const int32_t* sh = shifts + 3 * (start + m);
-      const int shv[3] = {sh[0], sh[1], sh[2]};
-      mem.push_back(make_member(phase, shv, E, b, nullptr, SolveOut{eps, eps + 6 * n, eps + 12 * n}));
+      int shv[3];
+      am.shift_of(start + m, shv);
+      mem.push_back(make_member(am.phase_of(start + m), shv, E, b, nullptr,
+                                SolveOut{eps, eps + 6 * n, eps + 12 * n}));
     }
     const int s = solve_mixed_batch(P, B, mem.data(), nph, phases, C0, tol, maxit,
                                     infos != nullptr ? infos + start : nullptr);
@@ -1373,13 +1400,22 @@ int translate_mixed(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* 
     if (severity(s) > severity(worst)) worst = s;
     for (int m = 0; m < B; ++m) {
       const double* eps = (const double*)mem[m].eps_out;
-      CK(launch_accumulate<double>(avg, h, eps, eps + 6 * n, eps + 12 * n, phase, mem[m].sx, mem[m].sy, mem[m].sz,
-                                   P->g.nx, P->g.ny, P->g.nz, P->st));
+      CK(launch_accumulate<double>(avg, h, eps, eps + 6 * n, eps + 12 * n, mem[m].phase, mem[m].sx, mem[m].sy,
+                                   mem[m].sz, P->g.nx, P->g.ny, P->g.nz, P->st));
     }
   }
-  CK(launch_scale(avg, 30 * n, 1.0 / nshift, P->st));
+  CK(launch_scale(avg, 30 * n, 1.0 / count, P->st));
   const int w = sync_stream(P);
   return w != BFCS_OK ? w : worst;
+}
+
+int average_dispatch(bfcs_plan P, int count, const AvgMembers& am, int nph, const bfcs_lame* phases,
+                     bfcs_lame C0, const void* b, const double* E, double tol, int maxit, double* avg,
+                     int32_t* hits, bfcs_info* infos) {
+  if (P == nullptr) return BFCS_ERR_INVALID_ARG;
+  if (P->mixed) return average_mixed(P, count, am, nph, phases, C0, b, E, tol, maxit, avg, hits, infos);
+  return P->fp64 ? average_impl<double>(P, count, am, nph, phases, C0, b, E, tol, maxit, avg, hits, infos)
+                 : average_impl<float>(P, count, am, nph, phases, C0, b, E, tol, maxit, avg, hits, infos);
 }
 
 // Effective stiffness L* (<sigma> = L* <eps>, Eqs. 6.1-6.3) and inclusion strain
@@ -1679,14 +1715,17 @@ int bfcs_translate_average(bfcs_plan P, const int8_t* phase, int nph, const bfcs
                            bfcs_lame C0, const void* b, const double E[6], int nshift,
                            const int32_t* shifts, double tol, int maxit, double* avg_out,
                            int32_t* hits_out, bfcs_info* infos) {
-  if (P == nullptr) return BFCS_ERR_INVALID_ARG;
-  if (P->mixed)
-    return translate_mixed(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit, avg_out, hits_out,
-                           infos);
-  return P->fp64 ? translate_impl<double>(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit,
-                                          avg_out, hits_out, infos)
-                 : translate_impl<float>(P, phase, nph, phases, C0, b, E, nshift, shifts, tol, maxit,
-                                         avg_out, hits_out, infos);
+  if (phase == nullptr || shifts == nullptr) return BFCS_ERR_INVALID_ARG;
+  const AvgMembers am{phase, nullptr, shifts};
+  return average_dispatch(P, nshift, am, nph, phases, C0, b, E, tol, maxit, avg_out, hits_out, infos);
+}
+
+int bfcs_ensemble_average(bfcs_plan P, int nconf, const int8_t* const* configs, int nph, const bfcs_lame* phases,
+                          bfcs_lame C0, const void* b, const double E[6], double tol, int maxit, double* avg_out,
+                          int32_t* hits_out, bfcs_info* infos) {
+  if (configs == nullptr) return BFCS_ERR_INVALID_ARG;
+  const AvgMembers am{nullptr, configs, nullptr};
+  return average_dispatch(P, nconf, am, nph, phases, C0, b, E, tol, maxit, avg_out, hits_out, infos);
 }
 
 int bfcs_effective_stiffness(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
