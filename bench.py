@@ -68,12 +68,13 @@ def workload(args, rank):
 
 def config_dict(p, args, world):
     return {
-        "workload": f"plain FP32 single solve {args.n}^3 = {(args.n // p.cell[0])}^3 cells of {p.cell[0]}^3, "
+        "workload": f"single solve {args.n}^3 = {(args.n // p.cell[0])}^3 cells of {p.cell[0]}^3, "
                     f"RSA spheres vf 0.25 r 4-6, Young contrast {int(args.contrast)}, BFCS a="
                     f"{p.bf_radius:g}, residual {p.tol:g}",
         "grid": list(p.dims), "contrast": args.contrast, "tol": p.tol, "seed": p.extra["seed"],
-        "precision": "fp32 sweeps, fp64 residual sums, fp64 defect correction and fp64 fields "
-                     "(the FP32-only fixed point stalls near 1.1e-5 at this size)",
+        "precision": "fp32 sweeps with fp64 residual sums, then defect correction: defect passes in "
+                     "float-float arithmetic (~48 bits) on fp64 fields, fp64 results (the FP32-only fixed "
+                     "point stalls near 1.1e-5 at this size)",
         "l2": "inputs larger than L2 (the 6-component spectrum is 0.43 GB at 256^3; no flush needed)",
         "parallelism": f"replicas x{world} (independent seeded problems per GPU)",
     }

@@ -53,7 +53,7 @@ extern "C" {
 /* ---- plan flags */
 #define BFCS_FP32 0                   /* FP32 fields and FFTs, FP64 residual sums */
 #define BFCS_FP64 1                   /* FP64 throughout */
-#define BFCS_MIXED 2                  /* FP32 sweeps with FP64 defect correction; FP64 fields */
+#define BFCS_MIXED 2                  /* FP32 sweeps with float-float defect correction; FP64 fields */
 #define BFCS_AUTOTUNE 4               /* OR-ed with FP32 or MIXED: time the y-pass variants at plan creation */
 #define BFCS_CG 8                     /* OR-ed with any precision: conjugate gradients (Algorithm 2) */
 
@@ -100,7 +100,8 @@ typedef struct {
  *             in the C0-weighted norm, each verified by two sweeps of the
  *             residual of Eq. 5.11; info.iters counts operator applications;
  *             allocates four more strain spectra per member).  BFCS_MIXED runs the sweeps in FP32 and
- *             corrects them in FP64 (below); its fields at the API (b, eps,
+ *             corrects them with defects evaluated in float-float
+ *             arithmetic (below); its fields at the API (b, eps,
  *             sigma, u, eps_init, fft3d data) are double.
  *  stream:    cudaStream_t to order work on (NULL = legacy default stream).
  * Allocates about (6 + 3 + 3) * nz*ny*(nx/2+4) complex values of workspace.
@@ -181,11 +182,13 @@ int bfcs_body_force_noalloc(int nx, int ny, int nz, double cx, double cy, double
  * start r(eps^0) is not evaluated (reported as +inf).
  * BFCS_MIXED plans (precision ladder): FP32 sweeps until r <= max(tol, 1e-4)
  * or the FP32 stall, then rounds of defect correction: the residual of the
- * FP64 strain is evaluated in FP64 (sigma = L eps, its transform, R_hat =
- * i xi.sigma_hat + b_hat), and while it exceeds tol an FP32 solve with load R
+ * FP64 strain is evaluated in float-float arithmetic (two floats, about
+ * 48 significant bits, on the FP32 pipes; GB300's FP64 rate is a small
+ * fraction of its FP32 rate) from the FP64 fields (sigma = L eps, its
+ * transform, R_hat = i xi.sigma_hat + b_hat), and while it exceeds tol an FP32 solve with load R
  * and E = 0 gives a correction added to the FP64 strain and displacement
  * (at most 8 rounds; maxit bounds the FP32 sweeps of all rounds together).
- * info.resid is then the FP64 residual of the returned FP64 strain, and an
+ * info.resid is then that residual of the returned FP64 strain, and an
  * eps_init skips the first FP32 phase.  The FP32-only path cannot go below
  * its rounding floor (~1e-7 times the load's length scale in voxels).
  * Returns OK, NOT_CONVERGED, INVALID_ARG, NONZERO_MEAN, CUDA, TIMEOUT, DIVERGED.

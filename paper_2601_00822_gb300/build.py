@@ -1,7 +1,8 @@
 """Builds libbfcs.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
 Each translation unit is compiled in parallel; the per-precision kernel files
-are compiled twice (BFCS_R = float / double).  No cmake, no torch headers.
+are compiled per arithmetic type (BFCS_R = float / double, and ff = float-float
+for the FFT and defect kernels of the precision ladder).  No cmake, no torch headers.
 """
 from __future__ import annotations
 
@@ -29,6 +30,8 @@ UNITS = [
     ("k_fft.cu", ["-DBFCS_R=double"], "k_fft_f64.o"),
     ("k_green.cu", ["-DBFCS_R=float"], "k_green_f32.o"),
     ("k_green.cu", ["-DBFCS_R=double"], "k_green_f64.o"),
+    ("k_fft.cu", ["-DBFCS_R=ff"], "k_fft_ff.o"),
+    ("k_green.cu", ["-DBFCS_R=ff", "-DBFCS_FF"], "k_green_ff.o"),
     ("k_cg.cu", ["-DBFCS_R=float"], "k_cg_f32.o"),
     ("k_cg.cu", ["-DBFCS_R=double"], "k_cg_f64.o"),
     ("k_misc.cu", [], "k_misc.o"),

@@ -12,6 +12,71 @@
 namespace bfcs {
 
 template <typename R> struct alignas(2 * sizeof(R)) C2 { R x, y; };
+// ------------------------------------------------------------------ float-float arithmetic
+// A real number held as the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2: about 48 significant bits.  GB300 executes FP64
+// arithmetic at a small fraction of its FP32 rate, so the FFT passes of the
+// precision ladder's defect evaluation compute in this form on the FP32 pipes
+// while their fields stay FP64 in memory.  Sums use the error-free TwoSum of
+// Knuth (TAOCP vol. 2, 4.2.2, Theorem B) followed by Dekker's FastTwoSum
+// renormalisation (Dekker 1971, "A floating-point technique for extending the
+// available precision"); products take the rounding error of hi * hi from one
+// fused multiply-add.  The _rn intrinsics keep the compiler from contracting
+// the error terms into fused operations.
+struct ff {
+  float hi, lo;
+  ff() = default;
+  __host__ __device__ constexpr ff(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ constexpr ff(float f) : hi(f), lo(0.0f) {}
+  __host__ __device__ constexpr ff(int i) : hi((float)i), lo(0.0f) {}   // exact for |i| < 2^24
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+__host__ __device__ __forceinline__ ff ff_pair(float h, float l) { ff r; r.hi = h; r.lo = l; return r; }
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {   // requires |a| >= |b| (or a = 0)
+  const float s = __fadd_rn(a, b);
+  return ff_pair(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));   // TwoSum error of hi + hi
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return ff_fast_two_sum(s, e);
+}
+__device__ __forceinline__ ff operator-(ff a) { return ff_pair(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);               // exact rounding error of hi * hi
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff operator/(ff a, ff b) {    // two correction steps of the float quotient
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const ff r = a - b * ff(q1);
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  return ff_fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ bool operator==(ff a, ff b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(ff a, ff b) { return !(a == b); }
+
+// Storage type of a real (non-spectral) field for arithmetic type R: the
+// float-float passes read and write their real fields as FP64.
+template <typename R> struct RealOf { using T = R; };
+template <> struct RealOf<ff> { using T = double; };
+template <typename R> __device__ __forceinline__ R ld_real(typename RealOf<R>::T v) { return R(v); }
+template <typename R> __device__ __forceinline__ typename RealOf<R>::T st_real(R v) {
+  return (typename RealOf<R>::T)v;
+}
+// warp shuffle of one real
+template <typename R> __device__ __forceinline__ R shfl_real(R v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <> __device__ __forceinline__ ff shfl_real<ff>(ff v, int src) {
+  return ff_pair(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+
 
 template <typename R> __host__ __device__ __forceinline__ C2<R> mk(R a, R b) { C2<R> c; c.x = a; c.y = b; return c; }
 template <typename R> __device__ __forceinline__ C2<R> operator+(C2<R> a, C2<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
@@ -24,6 +89,15 @@ template <typename R> __device__ __forceinline__ C2<R> scale(C2<R> a, R s) { ret
 // multiply by dir * i, dir = +-1
 template <typename R, int DIR> __device__ __forceinline__ C2<R> mul_di(C2<R> a) {
   return DIR > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x);
+}
+
+// |z|^2 accumulated in FP64 (float-float: from the leading parts, which carry
+// the 24 bits a norm needs)
+template <typename R> __device__ __forceinline__ double norm2(C2<R> z) {
+  return (double)z.x * (double)z.x + (double)z.y * (double)z.y;
+}
+template <> __device__ __forceinline__ double norm2<ff>(C2<ff> z) {
+  return (double)__fmaf_rn(z.x.hi, z.x.hi, __fmul_rn(z.y.hi, z.y.hi));
 }
 
 // cos(2 pi j / 48), exact quarter-wave table extended by symmetry; every radix

@@ -4,7 +4,8 @@
 //    (Eq. 5.8) run back to back on lines held in shared memory, so the
 //    real-space strain never goes to HBM between sweeps;
 //  * the column passes along y and z on the half spectrum.
-// Compiled once per precision with BFCS_R = float or double.
+// Compiled once per arithmetic type with BFCS_R = float, double or ff
+// (float-float arithmetic on FP64 fields, for the precision ladder).
 #include "kernels.h"
 
 #ifndef BFCS_R
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
   const int m = blockIdx.z;
   if (a.st != nullptr && a.st[m].done) return;   // a member that has converged skips
   using C = XCfg<L>;
+  using RT = typename RealOf<R>::T;   // storage type of the real fields
   constexpr int LPB = C::LPB, TPF = C::TPF, LP = C::LP;
   constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
   constexpr int H = L / 2;
@@ -115,9 +117,9 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
       const long long ln = line0 + i;
       C2<R> z = mk<R>(0, 0);
       if (ln < lines) {
-        const R* row = (const R*)a.xm[m].real_in + ln * L + n;
-        z.x = row[(2 * qq) * rn];
-        z.y = (2 * qq + 1 < ncomp) ? row[(2 * qq + 1) * rn] : R(0);
+        const RT* row = (const RT*)a.xm[m].real_in + ln * L + n;
+        z.x = ld_real<R>(row[(2 * qq) * rn]);
+        z.y = (2 * qq + 1 < ncomp) ? ld_real<R>(row[(2 * qq + 1) * rn]) : R(0);
       }
       s[ff * LP + xpad(n)] = z;
     }
@@ -132,9 +134,9 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
       const long long ln = line0 + i;
       if (ln >= lines) continue;
       const C2<R> z = s[ff * LP + xpad(n)];
-      R* row = (R*)a.xm[m].real_out + ln * L + n;
-      row[(2 * qq) * rn] = z.x;
-      if (2 * qq + 1 < ncomp) row[(2 * qq + 1) * rn] = z.y;
+      RT* row = (RT*)a.xm[m].real_out + ln * L + n;
+      row[(2 * qq) * rn] = st_real<R>(z.x);
+      if (2 * qq + 1 < ncomp) row[(2 * qq + 1) * rn] = st_real<R>(z.y);
     }
     return;
   }
@@ -160,14 +162,15 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
       const R tr = e0 + e1 + e2;
       const long long vox = ln * L + n;
       if (M.eps_out != nullptr) {
-        R* o = (R*)M.eps_out + vox;
-        o[0] = e0; o[rn] = e1; o[2 * rn] = e2; o[3 * rn] = e3; o[4 * rn] = e4; o[5 * rn] = e5;
+        RT* o = (RT*)M.eps_out + vox;
+        o[0] = st_real<R>(e0); o[rn] = st_real<R>(e1); o[2 * rn] = st_real<R>(e2);
+        o[3 * rn] = st_real<R>(e3); o[4 * rn] = st_real<R>(e4); o[5 * rn] = st_real<R>(e5);
       }
       if (M.sig_out != nullptr) {
         const R lt = a.tab.lam[ph] * tr, m2 = R(2) * a.tab.mu[ph];
-        R* o = (R*)M.sig_out + vox;
-        o[0] = lt + m2 * e0; o[rn] = lt + m2 * e1; o[2 * rn] = lt + m2 * e2;
-        o[3 * rn] = m2 * e3; o[4 * rn] = m2 * e4; o[5 * rn] = m2 * e5;
+        RT* o = (RT*)M.sig_out + vox;
+        o[0] = st_real<R>(lt + m2 * e0); o[rn] = st_real<R>(lt + m2 * e1); o[2 * rn] = st_real<R>(lt + m2 * e2);
+        o[3 * rn] = st_real<R>(m2 * e3); o[4 * rn] = st_real<R>(m2 * e4); o[5 * rn] = st_real<R>(m2 * e5);
       }
       const R lt = (full ? a.tab.lam[ph] : a.tab.lam1[ph]) * tr;
       const R m2 = R(2) * (full ? a.tab.mu[ph] : a.tab.mu1[ph]);
@@ -210,8 +213,8 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
   for (int k2 = 0; k2 < R2; ++k2) {
     const C2<R> send = (t == 0) ? y[(R2 - k2) % R2] : y[(R2 - 1 - k2 + R2) % R2];
     C2<R> zm;
-    zm.x = __shfl_sync(0xffffffffu, send.x, src);
-    zm.y = __shfl_sync(0xffffffffu, send.y, src);
+    zm.x = shfl_real<R>(send.x, src);
+    zm.y = shfl_real<R>(send.y, src);
     const int k = t + R1 * k2;
     if (fval && t < R1 && k <= H) {
       const C2<R> Z = y[k2];

@@ -489,6 +489,7 @@ __global__ void k_defect(DArgs<R> a) {
   }
   const long long modes = (long long)g.nz * g.ny * g.mx;
   const R two_pi = R(6.283185307179586);
+  const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(g.nz);
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
        i += (long long)gridDim.x * blockDim.x) {
@@ -497,9 +498,9 @@ __global__ void k_defect(DArgs<R> a) {
     const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
     const long long gi = r * g.p + kx;
     const C2<R>* sp = a.spec + gi;
-    const R xi0 = two_pi / R(g.nx) * R(signed_k(kx, g.nx));
-    const R xi1 = two_pi / R(g.ny) * R(signed_k(ky, g.ny));
-    const R xi2 = two_pi / R(g.nz) * R(signed_k(kz, g.nz));
+    const R xi0 = dk0 * R(signed_k(kx, g.nx));
+    const R xi1 = dk1 * R(signed_k(ky, g.ny));
+    const R xi2 = dk2 * R(signed_k(kz, g.nz));
     const C2<R> s0 = sp[0], s1 = sp[g.cs], s2 = sp[2 * g.cs], s3 = sp[3 * g.cs], s4 = sp[4 * g.cs],
                 s5 = sp[5 * g.cs];
     if (kx == 0 && ky == 0 && kz == 0) {
@@ -520,7 +521,7 @@ __global__ void k_defect(DArgs<R> a) {
       d[2] = mk<R>(-v2.y + b2.x, v2.x + b2.y);
       const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
       double t = 0.0;
-      for (int c = 0; c < 3; ++c) t += (double)d[c].x * d[c].x + (double)d[c].y * d[c].y;
+      for (int c = 0; c < 3; ++c) t += norm2<R>(d[c]);
       acc += w * t;
     }
 #pragma unroll
@@ -550,15 +551,16 @@ __global__ void k_symgrad(C2<R>* spec, long long ms, Geo g, R inv_n, const Membe
   const R E0 = (R)E[0], E1 = (R)E[1], E2 = (R)E[2], E3 = (R)E[3], E4 = (R)E[4], E5 = (R)E[5];
   const long long modes = (long long)g.nz * g.ny * g.mx;
   const R two_pi = R(6.283185307179586);
+  const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(g.nz);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
        i += (long long)gridDim.x * blockDim.x) {
     const int kx = (int)(i % g.mx);
     const long long r = i / g.mx;
     const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
     C2<R>* sp = spec + r * g.p + kx;
-    const R x0 = two_pi / R(g.nx) * R(signed_k(kx, g.nx));
-    const R x1 = two_pi / R(g.ny) * R(signed_k(ky, g.ny));
-    const R x2 = two_pi / R(g.nz) * R(signed_k(kz, g.nz));
+    const R x0 = dk0 * R(signed_k(kx, g.nx));
+    const R x1 = dk1 * R(signed_k(ky, g.ny));
+    const R x2 = dk2 * R(signed_k(kz, g.nz));
     const C2<R> u0 = sp[0], u1 = sp[g.cs], u2 = sp[2 * g.cs];
     C2<R> e[6];
     if (x0 == R(0) && x1 == R(0) && x2 == R(0)) {
@@ -649,10 +651,12 @@ cudaError_t launch_zgreen_b(const GArgs<R>& a, int batch, cudaStream_t st) {
 template <typename R>
 cudaError_t launch_zgreen(const GArgs<R>& a, cudaStream_t st) { return launch_zgreen_b<R>(a, 1, st); }
 
+#ifndef BFCS_FF   // the float-float build carries only the ladder's defect kernels
 template cudaError_t launch_zgreen<BFCS_R>(const GArgs<BFCS_R>&, cudaStream_t);
 template cudaError_t launch_zgreen_b<BFCS_R>(const GArgs<BFCS_R>&, int, cudaStream_t);
 template int green_nparts<BFCS_R>(const Geo&);
 template int green_sweep_parts<BFCS_R>(const Geo&);
+#endif
 template cudaError_t launch_defect<BFCS_R>(const DArgs<BFCS_R>&, int, int, cudaStream_t);
 template cudaError_t launch_symgrad<BFCS_R>(C2<BFCS_R>*, long long, const Geo&, const Member*, int, cudaStream_t);
 

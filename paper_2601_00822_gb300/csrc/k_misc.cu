@@ -523,6 +523,20 @@ cudaError_t launch_cast_spec(C2<float>* dst, const C2<double>* src, const Geo& g
   return cudaGetLastError();
 }
 
+// float-float spectrum -> complex64 (the FP32 phases' copy of the load)
+__global__ void k_cast_spec_ff(C2<float>* dst, const C2<ff>* src, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const C2<ff> v = src[i];
+    dst[i] = mk<float>((float)v.x, (float)v.y);
+  }
+}
+cudaError_t launch_cast_spec_ff(C2<float>* dst, const C2<ff>* src, const Geo& g, int ncomp, cudaStream_t s) {
+  k_cast_spec_ff<<<8 * 152, 256, 0, s>>>(dst, src, (long long)ncomp * g.cs);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 __global__ void k_stress(double* sig, const double* eps, const int8_t* phase, PhaseTab<double> tab, int sx,
                          int sy, int sz, int nx, int ny, int nz) {
   const long long n = (long long)nx * ny * nz;

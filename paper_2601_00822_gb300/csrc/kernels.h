@@ -222,6 +222,7 @@ cudaError_t launch_cast_f2d(double* dst, const float* src, long long count, cuda
 cudaError_t launch_add_f2d(double* dst, const float* src, long long count, cudaStream_t s);
 // complex128 -> complex64 copy of ncomp spectral components (same geometry)
 cudaError_t launch_cast_spec(C2<float>* dst, const C2<double>* src, const Geo& g, int ncomp, cudaStream_t s);
+cudaError_t launch_cast_spec_ff(C2<float>* dst, const C2<ff>* src, const Geo& g, int ncomp, cudaStream_t s);
 // sigma = L(x) eps pointwise (FP64), phase translated by (sx, sy, sz)
 cudaError_t launch_stress(double* sig, const double* eps, const int8_t* phase, const PhaseTab<double>& tab,
                           int sx, int sy, int sz, int nx, int ny, int nz, cudaStream_t s);

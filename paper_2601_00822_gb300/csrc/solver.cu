@@ -58,9 +58,10 @@ struct bfcs_plan_s {
   long long prof_launches = 0;
   double prof_ms = 0.0;
   // precision ladder (BFCS_MIXED): FP64 transform workspace and FP32 real scratch
-  void* spec64 = nullptr;          // max_batch x 6 x cs complex128
-  void* bhat64 = nullptr;          // max_batch x 3 x cs complex128: FP64 load spectra
+  void* spec64 = nullptr;          // max_batch x 6 x cs: complex128 (bfcs_fft3d) or float-float (ladder)
+  void* bhat64 = nullptr;          // max_batch x 3 x cs float-float complex: the ladder's load spectra
   void* tw64[3] = {nullptr, nullptr, nullptr};
+  void* twff[3] = {nullptr, nullptr, nullptr};   // float-float twiddles of the ladder's passes
   IterState* ist64 = nullptr;      // max_batch FP64 residual states
   float* r32 = nullptr;            // max_batch x 12 x N floats: (unused 3) | eps32 (6) | u32 (3)
   double* u64 = nullptr;           // max_batch x 3 x N doubles: FP64 displacements when the caller passes none
@@ -143,7 +144,7 @@ void free_plan(bfcs_plan P) {
   cudaFree(P->ival); cudaFree(P->dval); cudaFree(P->dscratch);
   cudaFree(P->tmp); cudaFree(P->tmp_hits); cudaFree(P->mod_buf);
   cudaFree(P->spec64); cudaFree(P->bhat64); cudaFree(P->ist64); cudaFree(P->r32); cudaFree(P->u64);
-  for (int i = 0; i < 3; ++i) cudaFree(P->tw64[i]);
+  for (int i = 0; i < 3; ++i) { cudaFree(P->tw64[i]); cudaFree(P->twff[i]); }
   if (P->ist_host) cudaFreeHost(P->ist_host);
   if (P->ival_host) cudaFreeHost(P->ival_host);
   if (P->dval_host) cudaFreeHost(P->dval_host);
@@ -1032,7 +1033,9 @@ int solve_group_impl(int n, const bfcs_group_item* items, int nph, const bfcs_la
 }
 
 // FP64 strain and defect from the FP64 displacements (precision ladder) of k
-// members in one launch per pass.  Slot j holds member idx[j]; dm[j] (host)
+// members in one launch per pass.  The passes compute in float-float (about
+// 48 bits, on the FP32 pipes) with float-float spectra; the real fields (u64
+// in, eps64 out) are FP64.  Slot j holds member idx[j]; dm[j] (host)
 // carries its phase, shift, E, the displacement u64 (as `b`, the real input
 // of the x transform) and eps_out.  eps64 = E + sym grad u64 (spectral,
 // exactly compatible), sigma = L eps64, its transform, R_hat = i xi .
@@ -1040,54 +1043,54 @@ int solve_group_impl(int n, const bfcs_group_item* items, int nph, const bfcs_la
 // ist64[m].resid_final, and R_hat rounded to complex64 into the member's FP32
 // load spectrum (slot m of the plan's b_hat: the load of its correction
 // problem, already transformed).  eps64 goes to eps_out.
-int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTab<double>& tab) {
+int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTab<ff>& tab) {
   const Geo g = P->g;
   cudaStream_t st = P->st;
   const long long sms = 6 * g.cs;
-  C2<double>* spec = (C2<double>*)P->spec64;
+  C2<ff>* spec = (C2<ff>*)P->spec64;
   int e = upload_members(P, k, dm);
   if (e != BFCS_OK) return e;
-  XArgs<double> xa{};                                                // u_hat, x direction
+  XArgs<ff> xa{};                                                // u_hat, x direction
   xa.g = g;
   xa.spec_out = spec;
   xa.spec_ms = sms;
   fill_xm(xa, dm, k, XIN_B, 0);
   xa.ncomp = 3;
   xa.mode = XM_R2C;
-  xa.tw = (const C2<double>*)P->tw64[0];
-  CK(launch_xpass_b<double>(xa, k, st));
-  CArgs<double> ca{};
+  xa.tw = (const C2<ff>*)P->twff[0];
+  CK(launch_xpass_b<ff>(xa, k, st));
+  CArgs<ff> ca{};
   ca.data = spec;
   ca.ms = sms;
   ca.g = g;
   ca.ncomp = 3;
-  ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
-  CK(launch_colpass_b<double>(ca, -1, k, st));
-  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
-  CK(launch_colpass_b<double>(ca, -1, k, st));
-  CK(launch_symgrad<double>(spec, sms, g, P->mem_dev, k, st));     // eps_hat / N (6 components)
+  ca.axis = 1; ca.tw = (const C2<ff>*)P->twff[1];
+  CK(launch_colpass_b<ff>(ca, -1, k, st));
+  ca.axis = 2; ca.tw = (const C2<ff>*)P->twff[2];
+  CK(launch_colpass_b<ff>(ca, -1, k, st));
+  CK(launch_symgrad<ff>(spec, sms, g, P->mem_dev, k, st));     // eps_hat / N (6 components)
   ca.ncomp = 6;
-  CK(launch_colpass_b<double>(ca, +1, k, st));                      // z inverse
-  ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
-  CK(launch_colpass_b<double>(ca, +1, k, st));                      // y inverse
-  XArgs<double> xs{};                                                // eps out, sigma = L eps, R2C
+  CK(launch_colpass_b<ff>(ca, +1, k, st));                      // z inverse
+  ca.axis = 1; ca.tw = (const C2<ff>*)P->twff[1];
+  CK(launch_colpass_b<ff>(ca, +1, k, st));                      // y inverse
+  XArgs<ff> xs{};                                                // eps out, sigma = L eps, R2C
   xs.g = g;
   xs.spec_in = spec;
   xs.spec_out = spec;
   xs.spec_ms = sms;
   fill_xm(xs, dm, k, XIN_NONE, XOUT_EPS);
   xs.tab = tab;
-  xs.tw = (const C2<double>*)P->tw64[0];
+  xs.tw = (const C2<ff>*)P->twff[0];
   xs.ncomp = 6;
   xs.mode = XM_SWEEPSIG;
-  CK(launch_xpass_b<double>(xs, k, st));
-  CK(launch_colpass_b<double>(ca, -1, k, st));                      // y forward
-  ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
-  CK(launch_colpass_b<double>(ca, -1, k, st));                      // z forward
-  DArgs<double> da{};
+  CK(launch_xpass_b<ff>(xs, k, st));
+  CK(launch_colpass_b<ff>(ca, -1, k, st));                      // y forward
+  ca.axis = 2; ca.tw = (const C2<ff>*)P->twff[2];
+  CK(launch_colpass_b<ff>(ca, -1, k, st));                      // z forward
+  DArgs<ff> da{};
   da.spec = spec;
   da.spec_ms = sms;
-  da.bhat = (const C2<double>*)P->bhat64;
+  da.bhat = (const C2<ff>*)P->bhat64;
   da.b_ms = 3 * g.cs;
   da.out32 = (C2<float>*)P->bhat;
   da.o_ms = 3 * g.cs;
@@ -1096,7 +1099,7 @@ int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTa
   da.st = P->ist64;
   for (int j = 0; j < k; ++j) da.idx[j] = idx[j];
   const int blocks = 512;
-  CK(launch_defect<double>(da, blocks, k, st));
+  CK(launch_defect<ff>(da, blocks, k, st));
   const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
   CK(launch_defect_final(P->part, blocks, P->ist64, idx, k, maxdim, st));
   return BFCS_OK;
@@ -1137,7 +1140,7 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
   const size_t cs = (size_t)g.cs;
   cudaStream_t st = P->st;
   C2<float>* bhat32 = (C2<float>*)P->bhat;
-  C2<double>* bhat64 = (C2<double>*)P->bhat64;
+  C2<ff>* bhat64 = (C2<ff>*)P->bhat64;
   auto eps32 = [&](int j) { return P->r32 + (size_t)j * 12 * n + 3 * n; };
   auto u32 = [&](int j) { return P->r32 + (size_t)j * 12 * n + 9 * n; };
   std::vector<double*> u64(B);
@@ -1145,6 +1148,7 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
     u64[m] = in[m].u_out != nullptr ? (double*)in[m].u_out : P->u64 + (size_t)m * 3 * n;
   const PhaseTab<float> tab32 = make_tab<float>(nph, phases, C0);
   const PhaseTab<double> tab64 = make_tab<double>(nph, phases, C0);
+  const PhaseTab<ff> tabff = make_tab<ff>(nph, phases, C0);
   const double zeroE[6] = {0, 0, 0, 0, 0, 0};
   std::vector<int> sweeps(B, 0), stalled(B, 0), status(B, BFCS_OK);
   std::vector<double> r_last(B, INFINITY), r64(B, INFINITY);
@@ -1153,35 +1157,37 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
   std::vector<bfcs_info> inf(P->max_batch);
   auto shift_of = [&](int m) { return std::array<int, 3>{in[m].sx, in[m].sy, in[m].sz}; };
 
-  // FP64 load spectra of all members (slot = member) and their norms
+  // float-float load spectra of all members (slot = member), their complex64
+  // copies for the FP32 phases, and their norms (the norm is a normaliser:
+  // the complex64 copy carries all the digits it needs)
   CK(cudaMemsetAsync(P->ist64, 0, B * sizeof(IterState), st));
   {
-    XArgs<double> xa{};
+    XArgs<ff> xa{};
     xa.g = g;
     xa.spec_out = bhat64;
     xa.spec_ms = 3 * cs;
     fill_xm(xa, in, B, XIN_B, 0);
     xa.ncomp = 3;
     xa.mode = XM_R2C;
-    xa.tw = (const C2<double>*)P->tw64[0];
-    CK(launch_xpass_b<double>(xa, B, st));
-    CArgs<double> ca{};
+    xa.tw = (const C2<ff>*)P->twff[0];
+    CK(launch_xpass_b<ff>(xa, B, st));
+    CArgs<ff> ca{};
     ca.data = bhat64;
     ca.ms = 3 * cs;
     ca.g = g;
     ca.ncomp = 3;
-    ca.axis = 1; ca.tw = (const C2<double>*)P->tw64[1];
-    CK(launch_colpass_b<double>(ca, -1, B, st));
-    ca.axis = 2; ca.tw = (const C2<double>*)P->tw64[2];
-    CK(launch_colpass_b<double>(ca, -1, B, st));
-    CK(launch_bden<double>(bhat64, g, P->part, P->ist64, st, B, 3 * cs));
+    ca.axis = 1; ca.tw = (const C2<ff>*)P->twff[1];
+    CK(launch_colpass_b<ff>(ca, -1, B, st));
+    ca.axis = 2; ca.tw = (const C2<ff>*)P->twff[2];
+    CK(launch_colpass_b<ff>(ca, -1, B, st));
+    CK(launch_cast_spec_ff(bhat32, bhat64, g, 3 * B, st));
+    CK(launch_bden<float>(bhat32, g, P->part, P->ist64, st, B, 3 * cs));
   }
 
   // phase 1: all members, FP32
   bool any_warm = false;
   mem.clear();
   for (int m = 0; m < B; ++m) {
-    CK(launch_cast_spec(bhat32 + (size_t)m * 3 * cs, bhat64 + (size_t)m * 3 * cs, g, 3, st));
     const void* init = nullptr;
     if (in[m].eps_init != nullptr) {
       CK(launch_cast_d2f(eps32(m), (const double*)in[m].eps_init, 6 * n, st));
@@ -1214,7 +1220,7 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
       mem.push_back(make_member(in[m].phase, sh.data(), in[m].E, u64[m], nullptr,
                                 SolveOut{in[m].eps_out, nullptr, nullptr}));
     }
-    e = defect64(P, (int)act.size(), mem.data(), act.data(), tab64);
+    e = defect64(P, (int)act.size(), mem.data(), act.data(), tabff);
     if (e != BFCS_OK) return e;
     IterState* h64 = P->ist_host + 2 * P->max_batch;
     CK(cudaMemcpyAsync(h64, P->ist64, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
@@ -1561,7 +1567,8 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
     if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
     for (int a = 0; a < 3; ++a) {
       P->tw64[a] = make_twiddles<double>(dims[a]);
-      if (P->tw64[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
+      P->twff[a] = make_twiddles<ff>(dims[a]);
+      if (P->tw64[a] == nullptr || P->twff[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
     }
   }
   if (flags & BFCS_CG) {

@@ -389,6 +389,20 @@ def test_mixed_ladder_goes_below_the_fp32_floor():
         assert rel(u2.cpu().numpy(), u.cpu().numpy()) < 1e-8
 
 
+def test_mixed_ladder_defect_reaches_1e_12():
+    """The defect passes compute in float-float (~48 bits): tight enough for a
+    residual of 1e-12, confirmed by the oracle's FP64 residual of the field."""
+    p = W.config_c1()
+    ph_o, b_o = oracle_inputs(p)
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    with api.Plan(p.dims, "mixed") as plan:
+        eps, _, _, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-12, maxit=6000, want_sig=False, want_u=False)
+    assert info.status == _lib.OK and info.resid <= 1e-12
+    r = O.residual(ph_o, p.phases, eps.cpu().numpy(), O.fft3(b_o), O.wavevectors(p.dims))
+    assert r <= 2e-12, r
+
+
 def test_mixed_batched_equals_individual_and_meets_tolerance():
     """The batched ladder (FP32 sweeps of all members in one launch per pass,
     FP64 defects per member) gives each member exactly the individual result;
