@@ -63,6 +63,42 @@ __device__ __forceinline__ ff operator/(ff a, ff b) {    // two correction steps
 __device__ __forceinline__ bool operator==(ff a, ff b) { return a.hi == b.hi && a.lo == b.lo; }
 __device__ __forceinline__ bool operator!=(ff a, ff b) { return !(a == b); }
 
+// FP64 <-> float-float conversions with integer bit operations (the FP64
+// conversion instructions share GB300's slow FP64 pipe).  Both cover the
+// normal-float range: magnitudes below 2^-126 become zero, above 2^128 infinite.
+// float -> the equal double, exactly (binary32 fields widened into binary64)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu, sgn = u & 0x80000000u;
+  if (e == 0) return __hiloint2double((int)sgn, 0);
+  const unsigned eh = e == 0xFFu ? 0x7FFu : e + (1023u - 127u);
+  return __hiloint2double((int)(sgn | (eh << 20) | ((u & 0x7FFFFFu) >> 3)), (int)((u & 0x7u) << 29));
+}
+// double -> hi + lo: hi keeps the leading 24 significant bits (truncated), lo
+// the next 24 of the remaining 29 (truncated): relative error below 2^-47
+__device__ __forceinline__ ff d2ff_bits(double d) {
+  const unsigned h32 = (unsigned)__double2hiint(d), l32 = (unsigned)__double2loint(d);
+  const unsigned sgn = h32 & 0x80000000u;
+  const int e = (int)((h32 >> 20) & 0x7FFu) - 1023;
+  if (e < -126) return ff_pair(__uint_as_float(sgn), 0.0f);
+  if (e > 127) {
+    const bool nan = e == 1024 && (((h32 & 0xFFFFFu) | l32) != 0u);
+    return ff_pair(__uint_as_float(nan ? 0x7FC00000u : (sgn | 0x7F800000u)), 0.0f);
+  }
+  const float h = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+  const unsigned r = l32 & 0x1FFFFFFFu;               // weight of bit 0: 2^(e - 52)
+  float l = 0.0f;
+  if (r != 0u) {
+    const int top = 31 - __clz((int)r);               // position of the leading one of r
+    const int el = e - 52 + top;                      // exponent of lo
+    if (el >= -126) {
+      const unsigned mant = top >= 23 ? (r >> (top - 23)) : (r << (23 - top));
+      l = __uint_as_float(sgn | ((unsigned)(el + 127) << 23) | (mant & 0x7FFFFFu));
+    }
+  }
+  return ff_pair(h, l);
+}
+
 // Storage type of a real (non-spectral) field for arithmetic type R: the
 // float-float passes read and write their real fields as FP64.
 template <typename R> struct RealOf { using T = R; };
@@ -71,6 +107,8 @@ template <typename R> __device__ __forceinline__ R ld_real(typename RealOf<R>::T
 template <typename R> __device__ __forceinline__ typename RealOf<R>::T st_real(R v) {
   return (typename RealOf<R>::T)v;
 }
+template <> __device__ __forceinline__ ff ld_real<ff>(double v) { return d2ff_bits(v); }
+template <> __device__ __forceinline__ double st_real<ff>(ff v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
 // warp shuffle of one real
 template <typename R> __device__ __forceinline__ R shfl_real(R v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 template <> __device__ __forceinline__ ff shfl_real<ff>(ff v, int src) {

@@ -65,10 +65,10 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_vec(CgArgs<R> a, int mode) {
   const R alpha = (R)a.cg[m].alpha, beta = (R)a.cg[m].beta;
   const long long modes = (long long)g.nz * g.ny * g.mx;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % g.mx);
-    const long long gi = (i / g.mx) * g.p + kx;
+  // 32-bit index arithmetic: a member's spectrum has at most 256 * 256 * 129 modes
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)modes; i += gridDim.x * blockDim.x) {
+    const int kx = i % g.mx;
+    const long long gi = (long long)(i / g.mx) * g.p + kx;
     const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
     C2<R> u[6], v[6];
     if (mode == CgMode::INIT) {

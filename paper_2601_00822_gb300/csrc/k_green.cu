@@ -491,12 +491,12 @@ __global__ void k_defect(DArgs<R> a) {
   const R two_pi = R(6.283185307179586);
   const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(g.nz);
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % g.mx);
-    const long long r = i / g.mx;
-    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
-    const long long gi = r * g.p + kx;
+  // 32-bit index arithmetic: a member's spectrum has at most 256 * 256 * 129 modes
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)modes; i += gridDim.x * blockDim.x) {
+    const int kx = i % g.mx;
+    const int r = i / g.mx;
+    const int ky = r % g.ny, kz = r / g.ny;
+    const long long gi = (long long)r * g.p + kx;
     const C2<R>* sp = a.spec + gi;
     const R xi0 = dk0 * R(signed_k(kx, g.nx));
     const R xi1 = dk1 * R(signed_k(ky, g.ny));
@@ -552,12 +552,12 @@ __global__ void k_symgrad(C2<R>* spec, long long ms, Geo g, R inv_n, const Membe
   const long long modes = (long long)g.nz * g.ny * g.mx;
   const R two_pi = R(6.283185307179586);
   const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(g.nz);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % g.mx);
-    const long long r = i / g.mx;
-    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
-    C2<R>* sp = spec + r * g.p + kx;
+  // 32-bit index arithmetic: a member's spectrum has at most 256 * 256 * 129 modes
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)modes; i += gridDim.x * blockDim.x) {
+    const int kx = i % g.mx;
+    const int r = i / g.mx;
+    const int ky = r % g.ny, kz = r / g.ny;
+    C2<R>* sp = spec + (long long)r * g.p + kx;
     const R x0 = dk0 * R(signed_k(kx, g.nx));
     const R x1 = dk1 * R(signed_k(ky, g.ny));
     const R x2 = dk2 * R(signed_k(kz, g.nz));

@@ -238,15 +238,15 @@ __global__ void k_bden(const C2<R>* bhat, Geo g, ResidSlot* part, long long b_ms
   part += m * gridDim.x;
   const long long modes = (long long)g.nz * g.ny * g.mx;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % g.mx);
-    const long long r = i / g.mx;
-    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
+  // 32-bit index arithmetic: a member's spectrum has at most 256 * 256 * 129 modes
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)modes; i += gridDim.x * blockDim.x) {
+    const int kx = i % g.mx;
+    const int r = i / g.mx;
+    const int ky = r % g.ny, kz = r / g.ny;
     const int sx = signed_k(kx, g.nx), sy = signed_k(ky, g.ny), sz = signed_k(kz, g.nz);
     if (sx == 0 && sy == 0 && sz == 0) continue;
     const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
-    const long long gi = r * g.p + kx;
+    const long long gi = (long long)r * g.p + kx;
     for (int c = 0; c < 3; ++c) {
       const C2<R> v = bhat[c * g.cs + gi];
       acc += w * ((double)v.x * v.x + (double)v.y * v.y);
