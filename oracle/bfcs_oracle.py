@@ -369,6 +369,83 @@ def ensemble_average(configs, table, c0, b, mean_strain=(0.0,) * 6, tol=1e-10, m
     return acc / len(configs), hits, infos
 
 
+# ---------------------------------------------------------------- RVE size (Def. 2.2)
+def radial_profile(field, centre, nbins):
+    """Largest pointwise norm of `field` in each spherical shell about `centre`:
+    prof[k] = max |f(x)| over voxels x whose periodic minimum-image distance d
+    from the centre satisfies k <= d < k + 1 (voxel centres at i + 0.5; the
+    centre on the half-voxel lattice, so that every d^2 is a quarter integer
+    and the shell of a voxel is decided exactly).  |f| is the Euclidean norm
+    of a vector (3 components) or sqrt(f : f) of a symmetric tensor (6
+    components, shears counted twice).  Empty shells give 0.  Returns (prof,
+    counts)."""
+    f = np.asarray(field, dtype=np.float64)
+    ncomp, nz, ny, nx = f.shape
+    w = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0] if ncomp == 6 else [1.0] * ncomp)
+    norm = np.sqrt(np.tensordot(w, f * f, axes=(0, 0)))
+    c2 = [int(round(2 * c)) for c in centre]
+    if any(abs(2 * c - k) > 1e-12 for c, k in zip(centre, c2)):
+        raise ValueError("the centre must lie on the half-voxel lattice")
+
+    def dd(n, c):
+        d = (2 * np.arange(n, dtype=np.int64) + 1 - c) % (2 * n)
+        return np.where(d > n, d - 2 * n, d)
+
+    dx, dy, dz = dd(nx, c2[0]), dd(ny, c2[1]), dd(nz, c2[2])
+    D2 = dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2   # (2 d)^2
+    shell = np.floor(np.sqrt(D2.astype(np.float64)) / 2.0).astype(np.int64)        # exact: see pins
+    prof = np.zeros(nbins)
+    counts = np.zeros(nbins, dtype=np.int64)
+    inside = shell < nbins
+    np.maximum.at(prof, shell[inside], norm[inside])
+    np.add.at(counts, shell[inside], 1)
+    return prof, counts
+
+
+def rve_radius(profiles, tol_f, rmax):
+    """RVE radius of Def. 2.2 from shell profiles: the smallest r such that in
+    every shell k with r <= k < rmax each profile is at most tol_f times its
+    largest value (fields vanish outside the RVE, relative to their maximum).
+    None when even the outermost shell rmax - 1 exceeds that."""
+    r = 0
+    for prof in profiles:
+        lim = tol_f * prof[:rmax].max()
+        above = np.nonzero(prof[:rmax] > lim)[0]
+        rp = 0 if above.size == 0 else int(above[-1]) + 1
+        if rp >= rmax:
+            return None
+        r = max(r, rp)
+    return r
+
+
+def rve_size(cell, spheres, table, c0, a, sizes, tol=1e-8, tol_f=1e-3, maxit=4000):
+    """RVE-size loop (Def. 2.2; Sec. 5: enlarge the body-force unit cell until
+    the RVE lies inside it): for each cubic grid n in `sizes` (multiples of the
+    microstructure cell), the BFCS problem of radius a centred at the cell
+    corner nearest the grid centre is solved, the RVE radius is taken from the
+    shell profiles of eps and sigma up to rmax = n / 2, and the grid is accepted
+    when the RVE and an annulus of half the support radius fit inside it,
+    r + a / 2 <= n / 2.  Stops at the first accepted grid.  Returns one record
+    per grid solved."""
+    out = []
+    for n in sizes:
+        dims = (n, n, n)
+        ph = phase_map(dims, cell, spheres)
+        centre = tuple(float(k * int(np.floor(n / (2.0 * k) + 0.5))) for k in cell)
+        b = body_force(dims, centre, a)
+        res = solve(ph, table, c0, b, tol=tol, maxit=maxit)
+        rmax = n // 2
+        pe, _ = radial_profile(res["eps"], centre, rmax)
+        ps, _ = radial_profile(res["sig"], centre, rmax)
+        r = rve_radius([pe, ps], tol_f, rmax)
+        ok = r is not None and r + a / 2.0 <= n / 2.0
+        out.append(dict(n=n, centre=centre, r_rve=r, contained=ok, sweeps=res["sweeps"], resid=res["resid"],
+                        prof_eps=pe, prof_sig=ps))
+        if ok:
+            break
+    return out
+
+
 # ---------------------------------------------------------------- effective moduli and concentration
 def unit_strain(J):
     """Unit mean strain of tensorial component J (xx yy zz yz xz xy): for a shear

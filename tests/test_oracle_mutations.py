@@ -41,6 +41,14 @@ MUTATIONS = {
                                       'As[:, J] = res["eps"].reshape(6, -1).mean(axis=1)'),
     "ensemble_indicator_of_first_configuration": ("        v = (ph != 0).astype(float)\n        acc[0:3] += res[\"u\"]\n        acc[3:6] += v * res[\"u\"]\n        acc[6:12] += res[\"eps\"]\n        acc[12:18] += v * res[\"eps\"]\n        acc[18:24] += res[\"sig\"]\n        acc[24:30] += v * res[\"sig\"]\n        hits += (ph != 0)\n        infos.append((res[\"sweeps\"], res[\"resid\"]))\n    return acc / len(configs)",
                                                   "        v = (configs[0] != 0).astype(float)\n        acc[0:3] += res[\"u\"]\n        acc[3:6] += v * res[\"u\"]\n        acc[6:12] += res[\"eps\"]\n        acc[12:18] += v * res[\"eps\"]\n        acc[18:24] += res[\"sig\"]\n        acc[24:30] += v * res[\"sig\"]\n        hits += (ph != 0)\n        infos.append((res[\"sweeps\"], res[\"resid\"]))\n    return acc / len(configs)"),
+    "radial_shell_rounded_up": ("shell = np.floor(np.sqrt(D2.astype(np.float64)) / 2.0)",
+                                "shell = np.ceil(np.sqrt(D2.astype(np.float64)) / 2.0)"),
+    "radial_shear_counted_once": ("w = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0] if ncomp == 6",
+                                  "w = np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0] if ncomp == 6"),
+    "rve_radius_off_by_one": ("rp = 0 if above.size == 0 else int(above[-1]) + 1",
+                              "rp = 0 if above.size == 0 else int(above[-1])"),
+    "rve_containment_without_annulus": ("ok = r is not None and r + a / 2.0 <= n / 2.0",
+                                        "ok = r is not None and r <= n / 2.0"),
     "stiffness_over_inclusions": ('Ls[:, J] = res["sig"].reshape(6, -1).mean(axis=1)',
                                   'Ls[:, J] = res["sig"][:, incl].mean(axis=1)'),
 }

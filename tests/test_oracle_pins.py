@@ -611,3 +611,92 @@ def test_ensemble_of_all_translations_is_the_translated_average():
     avg_e, hits_e, _ = O.ensemble_average(configs, table, c0, b, tol=1e-12)
     avg_t, hits_t, _ = O.translate_average(ph, table, c0, b, shifts, tol=1e-12)
     assert np.allclose(avg_e, avg_t, atol=1e-14) and np.array_equal(hits_e, hits_t)
+
+
+# ------------------------------------------------------------ RVE size (Def. 2.2, Sec. 5)
+def test_radial_profile_against_brute_force_loops():
+    nx, ny, nz = 6, 4, 5
+    centre = (3.0, 2.0, 2.5)
+    f6 = RNG.standard_normal((6, nz, ny, nx))
+    f3 = RNG.standard_normal((3, nz, ny, nx))
+    for f, w in ((f6, (1, 1, 1, 2, 2, 2)), (f3, (1, 1, 1))):
+        prof, counts = O.radial_profile(f, centre, 5)
+        ref = np.zeros(5)
+        cnt = np.zeros(5, dtype=int)
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    d2 = 0.0
+                    for pos, c, n in ((x, centre[0], nx), (y, centre[1], ny), (z, centre[2], nz)):
+                        d = pos + 0.5 - c
+                        d = min(abs(d - n * k) for k in (-1, 0, 1))
+                        d2 += d * d
+                    k = int(math.floor(math.sqrt(d2)))
+                    if k < 5:
+                        v = math.sqrt(sum(wc * f[c, z, y, x] ** 2 for c, wc in enumerate(w)))
+                        ref[k] = max(ref[k], v)
+                        cnt[k] += 1
+        assert np.array_equal(counts, cnt)
+        assert np.allclose(prof, ref, rtol=1e-15, atol=0)
+
+
+def test_radial_profile_of_the_distance_itself():
+    """A field equal to the distance from the centre: shell k holds values in [k, k + 1);
+    about a voxel corner the innermost shell is the 8 voxels at sqrt(3) / 2."""
+    n = 8
+    c = (4.0, 4.0, 4.0)
+    g = np.arange(n) + 0.5 - 4.0
+    d = np.sqrt(g[None, None, :] ** 2 + g[None, :, None] ** 2 + g[:, None, None] ** 2)
+    f = np.stack([d, np.zeros_like(d), np.zeros_like(d)])
+    prof, counts = O.radial_profile(f, c, 4)
+    assert counts[0] == 8 and abs(prof[0] - math.sqrt(3) / 2) < 1e-15
+    for k in range(4):
+        assert counts[k] > 0 and k <= prof[k] < k + 1
+
+
+def test_rve_radius_rule():
+    p1 = np.array([1.0, 0.5, 0.1, 1e-4, 1e-5, 0.0])
+    p2 = np.array([2.0, 1.0, 0.05, 0.01, 1e-6, 0.0])
+    assert O.rve_radius([p1], 1e-3, 6) == 3
+    assert O.rve_radius([p2], 1e-3, 6) == 4
+    assert O.rve_radius([p1, p2], 1e-3, 6) == 4
+    assert O.rve_radius([p1], 1e-3, 3) is None          # the outermost shell considered is still above
+    assert O.rve_radius([np.array([1.0, 0.0, 0.0])], 1e-3, 3) == 1
+
+
+def test_rve_size_loop_accepts_the_first_cell_holding_the_rve_and_fields_stabilise():
+    """Cell 8^3 with one sphere, support radius a = 3, field tolerance 5%: the
+    16^3 cell holds no RVE, 24^3 does (r + a/2 <= 12) and ends the loop; the
+    strain inside that RVE then changes by less than the tolerance when the
+    cell is enlarged to 40^3 (Sec. 5: further enlargement leaves it unaffected)."""
+    cell = (8, 8, 8)
+    sph = np.asarray([[8, 8, 8, 25, 1]], np.int32)
+    table, c0, a, tol_f = [(1.0, 0.5), (6.0, 3.0)], (3.5, 1.75), 3.0, 0.05
+    recs = O.rve_size(cell, sph, table, c0, a, sizes=(16, 24, 32), tol=1e-11, tol_f=tol_f)
+    assert [r["n"] for r in recs] == [16, 24]
+    assert recs[0]["r_rve"] is None and not recs[0]["contained"]
+    r = recs[1]["r_rve"]
+    assert recs[1]["contained"] and r + a / 2 <= 12
+    pe = recs[1]["prof_eps"]
+    assert pe[r - 1] > tol_f * pe.max() and np.all(pe[r:12] <= tol_f * pe.max())
+
+    def solve(n):
+        ph = O.phase_map((n,) * 3, cell, sph)
+        cen = tuple(float(k * int(np.floor(n / (2.0 * k) + 0.5))) for k in cell)
+        return O.solve(ph, table, c0, O.body_force((n,) * 3, cen, a), tol=1e-11, maxit=4000)["eps"], int(cen[0])
+
+    (ea, ca), (eb, cb) = solve(24), solve(40)
+    g = np.arange(-r, r)
+    ball = (g[:, None, None] + 0.5) ** 2 + (g[None, :, None] + 0.5) ** 2 + (g[None, None, :] + 0.5) ** 2 < r * r
+    wa = ea[:, (ca + g)[:, None, None] % 24, (ca + g)[None, :, None] % 24, (ca + g)[None, None, :] % 24]
+    wb = eb[:, (cb + g)[:, None, None] % 40, (cb + g)[None, :, None] % 40, (cb + g)[None, None, :] % 40]
+    assert np.abs(wa - wb)[:, ball].max() <= tol_f * np.abs(ea).max()
+
+
+def test_rve_size_loop_needs_the_annulus_inside_the_cell():
+    """a = 4, field tolerance 4.8%: at 24^3 the fields fall below the tolerance
+    from r = 11 on, but r + a/2 = 13 > 12 leaves no room for the annulus of
+    half the support radius, so the loop goes on to 32^3 (r = 10 fits)."""
+    recs = O.rve_size((8, 8, 8), np.asarray([[8, 8, 8, 25, 1]], np.int32), [(1.0, 0.5), (6.0, 3.0)], (3.5, 1.75),
+                      4.0, sizes=(24, 32), tol=1e-11, tol_f=0.048)
+    assert [(r["n"], r["r_rve"], r["contained"]) for r in recs] == [(24, 11, False), (32, 10, True)]
