@@ -265,6 +265,62 @@ int bfcs_ensemble_average(bfcs_plan plan, int nconf, const int8_t* const* config
                           int maxit, double* avg_out, int32_t* hits_out, bfcs_info* infos);
 
 /*
+ * bfcs_radial_profile - the RVE diagnostic of Def. 2.2: for shells k = 0 ..
+ * nbins-1 about `centre`, prof_out[k] = the largest pointwise norm of `field`
+ * over the voxels whose periodic minimum-image distance d from the centre
+ * satisfies k <= d < k + 1 (voxel centres at i + 0.5).
+ *  field:   dev, ncomp x N in the plan's real type (float for BFCS_FP32,
+ *           double for BFCS_FP64 and BFCS_MIXED), component-major.
+ *  ncomp:   3 (vector: Euclidean norm) or 6 (symmetric tensor: sqrt(f : f),
+ *           shears counted twice).
+ *  centre:  host, 3 doubles in voxel units on the half-voxel lattice (2 c
+ *           integral), so that every shell is decided in integer arithmetic.
+ *  nbins:   1 .. 2048.
+ *  prof_out: host, nbins doubles (0 for empty shells); counts_out: host, nbins
+ *           voxel counts, or NULL.
+ * Uses a plan-owned scratch (allocated on first use).  Errors: INVALID_ARG,
+ * OOM, CUDA, TIMEOUT.
+ */
+int bfcs_radial_profile(bfcs_plan plan, const void* field, int ncomp, const double centre[3], int nbins,
+                        double* prof_out, int64_t* counts_out);
+
+/*
+ * bfcs_rve_size - the RVE-size loop (Def. 2.2; Sec. 5: a body-force unit cell
+ * that does not hold the RVE is enlarged and the problem solved again).  For
+ * each cubic grid n = sizes[i] (ascending, multiples of the microstructure
+ * cell cx x cy x cz; spheres as for bfcs_voxelize, tiled over the grid) the
+ * BFCS problem (bfcs_body_force of support radius a, centred at the cell
+ * corner nearest the grid centre, E = 0) is solved on a fresh plan with
+ * `flags`, tol and maxit; bfcs_radial_profile of eps and sigma about the
+ * centre over shells k < n/2 gives the RVE radius r: the smallest r such that
+ * both profiles stay at most tol_f times their largest value in every shell
+ * r <= k < n/2 (the fields vanish outside the RVE, relative to their maximum);
+ * the grid holds the RVE when r + a/2 <= n/2 (room for an annulus of half the
+ * support radius), and the loop stops there.
+ *  records:  host, nsizes entries, filled for the grids solved.
+ *  profiles: host, nsizes x 2 x (max sizes / 2) doubles (eps then sigma
+ *            profile per grid, zero beyond n/2), or NULL.
+ *  accepted: host, the index of the grid that holds the RVE, -1 if none.
+ *  stream:   cudaStream_t of the plans and helper calls (NULL = default).
+ * Allocates a plan and the grid's fields per step and frees them.
+ * Returns the most severe solve status, or an error.
+ */
+typedef struct {
+  int n;              /* cubic grid n^3 of this step */
+  int r_rve;          /* RVE radius in voxels; -1: the fields do not fall below tol_f inside the grid */
+  int contained;      /* 1: r_rve + a/2 <= n/2 (the loop stops at this grid) */
+  int iters;          /* sweeps of the solve */
+  int status;         /* status of the solve */
+  double centre[3];   /* load centre (voxel units) */
+  double resid;       /* residual of the returned strain */
+  double eps_max;     /* largest shell maximum of |eps| */
+  double sig_max;     /* largest shell maximum of |sigma| */
+} bfcs_rve_record;
+int bfcs_rve_size(int cx, int cy, int cz, int nsph, const int32_t* spheres, int nphases, const bfcs_lame* phases,
+                  bfcs_lame C0, double a, int nsizes, const int* sizes, int flags, double tol, int maxit,
+                  double tol_f, bfcs_rve_record* records, double* profiles, int* accepted, void* stream);
+
+/*
  * bfcs_effective_stiffness - effective stiffness L* and inclusion strain
  * concentration A* of the periodic microstructure (Eqs. 6.1-6.3 and Eq. 3.2):
  * the classical problem (b = 0, Eq. 2.24) is solved under the six unit mean

@@ -35,7 +35,7 @@ EXPORTS = (
     "bfcs_profile_read", "bfcs_body_force_noalloc", "bfcs_net_param_count", "bfcs_net_create",
     "bfcs_net_destroy", "bfcs_net_prepare", "bfcs_net_forward", "bfcs_net_grad", "bfcs_net_adam",
     "bfcs_net_train_step", "bfcs_net_predict", "bfcs_plan_tuning", "bfcs_solve_group", "bfcs_net_status",
-    "bfcs_effective_stiffness", "bfcs_ensemble_average",
+    "bfcs_effective_stiffness", "bfcs_ensemble_average", "bfcs_radial_profile", "bfcs_rve_size",
 )
 NET_PARAMS = 523654
 NET_TRAIN = 1
@@ -55,6 +55,12 @@ class Problem(C.Structure):
     _fields_ = [("phase", C.c_void_p), ("b", C.c_void_p), ("E", C.c_double * 6),
                 ("shift", C.c_int * 3), ("eps_init", C.c_void_p), ("eps_out", C.c_void_p),
                 ("sig_out", C.c_void_p), ("u_out", C.c_void_p)]
+
+
+class RveRecord(C.Structure):
+    _fields_ = [("n", C.c_int), ("r_rve", C.c_int), ("contained", C.c_int), ("iters", C.c_int),
+                ("status", C.c_int), ("centre", C.c_double * 3), ("resid", C.c_double), ("eps_max", C.c_double),
+                ("sig_max", C.c_double)]
 
 
 class GroupItem(C.Structure):
@@ -97,6 +103,9 @@ def _declare(lib):
     lib.bfcs_plan_tuning.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(d)]
     lib.bfcs_ensemble_average.argtypes = [vp, i, C.POINTER(vp), i, C.POINTER(Lame), Lame, vp, C.POINTER(d), d, i,
                                          vp, vp, C.POINTER(Info)]
+    lib.bfcs_radial_profile.argtypes = [vp, vp, i, C.POINTER(d), i, vp, vp]
+    lib.bfcs_rve_size.argtypes = [i, i, i, i, vp, i, C.POINTER(Lame), Lame, d, i, vp, i, d, i, d,
+                                  C.POINTER(RveRecord), vp, C.POINTER(i), vp]
     lib.bfcs_effective_stiffness.argtypes = [vp, vp, i, C.POINTER(Lame), Lame, d, i, vp, vp, C.POINTER(Info)]
     lib.bfcs_status_string.argtypes = [i]
     lib.bfcs_status_string.restype = C.c_char_p

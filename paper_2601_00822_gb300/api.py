@@ -229,6 +229,20 @@ class Plan:
         _lib.check(code, "bfcs_ensemble_average", allow)
         return avg, hits, [SolveInfo.of(infos[m]) for m in range(len(configs))]
 
+    def radial_profile(self, field, centre, nbins):
+        """bfcs_radial_profile: (shell maxima of the pointwise norm (nbins,), voxel counts (nbins,))."""
+        nx, ny, nz = self.dims
+        if field.shape[0] not in (3, 6):
+            raise ValueError("field: 3 (vector) or 6 (symmetric tensor) components")
+        _check_tensor(field, (field.shape[0], nz, ny, nx), self.dtype, "field")
+        prof = np.zeros(int(nbins))
+        counts = np.zeros(int(nbins), dtype=np.int64)
+        c = (C.c_double * 3)(*[float(v) for v in centre])
+        _lib.check(self.lib.bfcs_radial_profile(self.handle, _ptr(field), int(field.shape[0]), c, int(nbins),
+                                                prof.ctypes.data_as(C.c_void_p), counts.ctypes.data_as(C.c_void_p)),
+                   "bfcs_radial_profile")
+        return prof, counts
+
     def effective_stiffness(self, phase, phases, c0, tol=1e-6, maxit=10000,
                             allow=(_lib.OK, _lib.NOT_CONVERGED)):
         """bfcs_effective_stiffness: (L* (6, 6), A* (6, 6), infos) with column J the
@@ -298,6 +312,31 @@ class Plan:
         _lib.check(self.lib.bfcs_surrogate_infer(self.handle, _ptr(weights), _ptr(b), _ptr(phase), len(phases),
                                                  arr, _ptr(eps)), "bfcs_surrogate_infer")
         return eps
+
+
+def rve_size(cell, spheres, phases, c0, a, sizes, precision="mixed", tol=1e-6, maxit=20000, tol_f=1e-3,
+             stream=None, allow=(_lib.OK, _lib.NOT_CONVERGED)):
+    """bfcs_rve_size (Def. 2.2, Sec. 5): returns (records as dicts, profiles (nsizes, 2, max n/2), accepted index)."""
+    lib = _lib.load()
+    sph = np.ascontiguousarray(np.asarray(spheres, dtype=np.int32).reshape(-1, 5))
+    sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32).reshape(-1))
+    flag = {"fp32": _lib.FP32, "fp64": _lib.FP64, "mixed": _lib.MIXED}[precision]
+    recs = (_lib.RveRecord * sz.size)()
+    prof = np.zeros((sz.size, 2, int(sz.max()) // 2))
+    acc = C.c_int(-1)
+    code = lib.bfcs_rve_size(int(cell[0]), int(cell[1]), int(cell[2]), sph.shape[0], sph.ctypes.data_as(C.c_void_p),
+                             len(phases), _lames(phases), _lib.Lame(*c0), float(a), int(sz.size),
+                             sz.ctypes.data_as(C.c_void_p), int(flag), float(tol), int(maxit), float(tol_f), recs,
+                             prof.ctypes.data_as(C.c_void_p), C.byref(acc), _stream_ptr(stream))
+    _lib.check(code, "bfcs_rve_size", allow)
+    out = []
+    for r in recs:
+        if r.n == 0:
+            break
+        out.append(dict(n=r.n, r_rve=(None if r.r_rve < 0 else r.r_rve), contained=bool(r.contained),
+                        iters=r.iters, status=r.status, centre=tuple(r.centre), resid=r.resid,
+                        eps_max=r.eps_max, sig_max=r.sig_max))
+    return out, prof, acc.value
 
 
 def _ptr_array(ts):

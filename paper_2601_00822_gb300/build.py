@@ -35,6 +35,7 @@ UNITS = [
     ("k_cg.cu", ["-DBFCS_R=float"], "k_cg_f32.o"),
     ("k_cg.cu", ["-DBFCS_R=double"], "k_cg_f64.o"),
     ("k_misc.cu", [], "k_misc.o"),
+    ("rve.cu", [], "rve.o"),
     ("solver.cu", [], "solver.o"),
     ("noalloc.cu", [], "noalloc.o"),
     ("unet.cu", [], "unet.o"),

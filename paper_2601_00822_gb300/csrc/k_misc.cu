@@ -422,6 +422,61 @@ cudaError_t launch_scale(double* acc, long long count, double f, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- RVE diagnostic (Def. 2.2)
+// Shell maxima of the pointwise norm about a centre on the half-voxel lattice
+// (doubled coordinates c2): voxel v lies in shell k = floor(d) where (2d)^2 =
+// D2 is an integer, so the shell is decided exactly (k = isqrt(D2) >> 1).  Per
+// block the maxima are kept in shared memory as the bit patterns of
+// non-negative doubles (their unsigned order is the numeric order), then merged
+// into bits[] with one atomicMax per shell: the result does not depend on order.
+template <typename R>
+__global__ void __launch_bounds__(256) k_radial_max(const R* f, int ncomp, int nx, int ny, int nz, int c2x, int c2y,
+                                                  int c2z, int nbins, unsigned long long* bits,
+                                                  unsigned long long* counts) {
+  extern __shared__ unsigned long long rsh[];      // [nbins] maxima, [nbins] counts
+  for (int i = threadIdx.x; i < 2 * nbins; i += blockDim.x) rsh[i] = 0ull;
+  __syncthreads();
+  const int n = nx * ny * nz;                      // at most 256^3
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+    int dx = (2 * x + 1 - c2x) % (2 * nx), dy = (2 * y + 1 - c2y) % (2 * ny), dz = (2 * z + 1 - c2z) % (2 * nz);
+    if (dx < 0) dx += 2 * nx;
+    if (dy < 0) dy += 2 * ny;
+    if (dz < 0) dz += 2 * nz;
+    if (dx > nx) dx -= 2 * nx;
+    if (dy > ny) dy -= 2 * ny;
+    if (dz > nz) dz -= 2 * nz;
+    const int D2 = dx * dx + dy * dy + dz * dz;
+    int r = (int)sqrtf((float)D2);
+    while (r * r > D2) --r;
+    while ((r + 1) * (r + 1) <= D2) ++r;
+    const int k = r >> 1;
+    if (k >= nbins) continue;
+    double q = 0.0;
+    for (int c = 0; c < ncomp; ++c) {
+      const double fc = (double)f[(long long)c * n + v];
+      q += (c < 3 ? 1.0 : 2.0) * fc * fc;
+    }
+    atomicMax(&rsh[k], (unsigned long long)__double_as_longlong(sqrt(q)));
+    atomicAdd(&rsh[nbins + k], 1ull);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x)
+    if (rsh[nbins + i] != 0ull) {
+      atomicMax(&bits[i], rsh[i]);
+      atomicAdd(&counts[i], rsh[nbins + i]);
+    }
+}
+
+template <typename R>
+cudaError_t launch_radial_max(const R* f, int ncomp, int nx, int ny, int nz, const int c2[3], int nbins,
+                              unsigned long long* bits, unsigned long long* counts, cudaStream_t s) {
+  k_radial_max<R><<<2 * 152, 256, 2 * (size_t)nbins * sizeof(unsigned long long), s>>>(
+      f, ncomp, nx, ny, nz, c2[0], c2[1], c2[2], nbins, bits, counts);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- effective moduli (Eqs. 6.1-6.3, 3.2)
 // Per member m (blockIdx.y): the 13 FP64 sums  sum sigma_c (6), sum over the
 // inclusion voxels (phase != 0) of eps_c (6) and their count, as one partial per
@@ -574,7 +629,9 @@ cudaError_t launch_stress(double* sig, const double* eps, const int8_t* phase, c
   template cudaError_t launch_accumulate<R>(double*, int*, const R*, const R*, const R*,           \
                                             const int8_t*, int, int, int, int, int, int,          \
                                             cudaStream_t);                                        \
-  template cudaError_t launch_moduli<R>(const ModArgs<R>&, int, double*, double*, cudaStream_t);
+  template cudaError_t launch_moduli<R>(const ModArgs<R>&, int, double*, double*, cudaStream_t);   \
+  template cudaError_t launch_radial_max<R>(const R*, int, int, int, int, const int*, int,           \
+                                            unsigned long long*, unsigned long long*, cudaStream_t);
 BFCS_INST(float)
 BFCS_INST(double)
 #undef BFCS_INST

@@ -249,4 +249,13 @@ struct ModArgs {
 template <typename R>
 cudaError_t launch_moduli(const ModArgs<R>& a, int batch, double* part, double* out, cudaStream_t s);
 
+// RVE diagnostic (Def. 2.2): per shell k of the doubled-coordinate distance
+// about c2 (2 x centre), the largest pointwise norm (merged into bits[k] as the
+// bit pattern of a non-negative double) and the voxel count; ncomp 3 (vector)
+// or 6 (symmetric tensor, shears counted twice); nbins <= kMaxShells.
+constexpr int kMaxShells = 2048;
+template <typename R>
+cudaError_t launch_radial_max(const R* f, int ncomp, int nx, int ny, int nz, const int c2[3], int nbins,
+                              unsigned long long* bits, unsigned long long* counts, cudaStream_t s);
+
 }  // namespace bfcs

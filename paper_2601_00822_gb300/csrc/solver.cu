@@ -50,6 +50,7 @@ struct bfcs_plan_s {
   void* tmp = nullptr;             // 15 x N real: eps, sig, u for averaging members
   int* tmp_hits = nullptr;         // N int
   double* mod_buf = nullptr;       // effective-moduli partial sums and totals
+  unsigned long long* prof_buf = nullptr;   // shell maxima and counts of bfcs_radial_profile
   // measurement hook: CUDA events around the launches of one kernel kind
   int prof_kind = 0;
   std::vector<cudaEvent_t> prof_ev;   // start/end pairs
@@ -142,7 +143,7 @@ void free_plan(bfcs_plan P) {
   cudaFree(P->part); cudaFree(P->ist); cudaFree(P->hist); cudaFree(P->mem_dev);
   if (P->mem_host) cudaFreeHost(P->mem_host);
   cudaFree(P->ival); cudaFree(P->dval); cudaFree(P->dscratch);
-  cudaFree(P->tmp); cudaFree(P->tmp_hits); cudaFree(P->mod_buf);
+  cudaFree(P->tmp); cudaFree(P->tmp_hits); cudaFree(P->mod_buf); cudaFree(P->prof_buf);
   cudaFree(P->spec64); cudaFree(P->bhat64); cudaFree(P->ist64); cudaFree(P->r32); cudaFree(P->u64);
   for (int i = 0; i < 3; ++i) { cudaFree(P->tw64[i]); cudaFree(P->twff[i]); }
   if (P->ist_host) cudaFreeHost(P->ist_host);
@@ -1740,6 +1741,42 @@ int bfcs_effective_stiffness(bfcs_plan P, const int8_t* phase, int nph, const bf
   if (P == nullptr) return BFCS_ERR_INVALID_ARG;
   return P->fp64 || P->mixed ? moduli_impl<double>(P, phase, nph, phases, C0, tol, maxit, Lstar, Astar, infos)
                              : moduli_impl<float>(P, phase, nph, phases, C0, tol, maxit, Lstar, Astar, infos);
+}
+
+int bfcs_radial_profile(bfcs_plan P, const void* field, int ncomp, const double centre[3], int nbins,
+                        double* prof_out, int64_t* counts_out) {
+  if (P == nullptr || field == nullptr || centre == nullptr || prof_out == nullptr || (ncomp != 3 && ncomp != 6) ||
+      nbins < 1 || nbins > kMaxShells)
+    return BFCS_ERR_INVALID_ARG;
+  const int dims[3] = {P->g.nx, P->g.ny, P->g.nz};
+  int c2[3];
+  for (int a = 0; a < 3; ++a) {
+    const double t = 2.0 * centre[a];
+    if (!std::isfinite(t) || std::fabs(t - std::nearbyint(t)) > 1e-9 || std::fabs(t) > 1e9) return BFCS_ERR_INVALID_ARG;
+    const long long m = 2LL * dims[a];
+    c2[a] = (int)((((long long)std::nearbyint(t)) % m + m) % m);
+  }
+  if (P->prof_buf == nullptr &&
+      cudaMalloc(&P->prof_buf, 2 * (size_t)kMaxShells * sizeof(unsigned long long)) != cudaSuccess)
+    return BFCS_ERR_OOM;
+  CK(cudaMemsetAsync(P->prof_buf, 0, 2 * (size_t)nbins * sizeof(unsigned long long), P->st));
+  if (P->fp64 || P->mixed)
+    CK(launch_radial_max<double>((const double*)field, ncomp, dims[0], dims[1], dims[2], c2, nbins, P->prof_buf,
+                                 P->prof_buf + nbins, P->st));
+  else
+    CK(launch_radial_max<float>((const float*)field, ncomp, dims[0], dims[1], dims[2], c2, nbins, P->prof_buf,
+                                P->prof_buf + nbins, P->st));
+  std::vector<unsigned long long> h(2 * (size_t)nbins);
+  CK(cudaMemcpyAsync(h.data(), P->prof_buf, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, P->st));
+  const int w = sync_stream(P);
+  if (w != BFCS_OK) return w;
+  for (int k = 0; k < nbins; ++k) {
+    double v;
+    std::memcpy(&v, &h[k], sizeof(v));
+    prof_out[k] = v;
+    if (counts_out != nullptr) counts_out[k] = (int64_t)h[nbins + k];
+  }
+  return BFCS_OK;
 }
 
 int bfcs_plan_tuning(bfcs_plan P, int* col_variant, int* col_tile, int* col_swap, double* variant_ms) {
