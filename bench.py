@@ -463,6 +463,15 @@ def measure_extras(api, torch):
         "max_resid": max(i.resid for i in infos),
         "bulk_modulus": float(S[:3, :3].sum() / 9), "shear_modulus": float(np.mean(np.diag(Ls)[3:]) / 2),
         "inclusion_strain_concentration_xx": float(As[0, 0])}
+    t0 = time.perf_counter()
+    recs, _, acc = api.rve_size(q.cell, q.spheres, q.phases, q.c0, 8.0, (64, 128, 256), precision="mixed",
+                                tol=1e-6, tol_f=0.05)
+    out["rve_size"] = {
+        "workload": "C2 microstructure (32^3 cells, RSA vf 0.25, contrast 10), support radius a = 8, field "
+                    "tolerance 5%, grids 64/128/256, mixed ladder to residual 1e-6",
+        "seconds": time.perf_counter() - t0, "accepted_grid": recs[acc]["n"] if acc >= 0 else None,
+        "steps": [{"n": r["n"], "r_rve": r["r_rve"], "contained": r["contained"], "sweeps": r["iters"]}
+                  for r in recs]}
     groups = []
     for n in (64, 96, 128):
         q = W.config_c2(n=n, cell=32 if n % 32 == 0 else 16, bf_radius=24.0 * n / 256.0)
