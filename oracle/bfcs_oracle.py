@@ -52,6 +52,8 @@ translation equivariance, averaging invariants).
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 import scipy.fft as sfft
 
@@ -444,6 +446,73 @@ def rve_size(cell, spheres, table, c0, a, sizes, tol=1e-8, tol_f=1e-3, maxit=400
         if ok:
             break
     return out
+
+
+# ---------------------------------------------------------------- nonlocal kernel regression (Eqs. 6.5-6.6)
+def bernstein(M, t):
+    """Bernstein basis of degree M on [0, 1]: B_m(t) = C(M, m) t^m (1 - t)^(M - m), m = 0..M."""
+    t = np.asarray(t, dtype=np.float64)
+    return np.stack([math.comb(M, m) * t ** m * (1.0 - t) ** (M - m) for m in range(M + 1)])
+
+
+def horizon_offsets(delta):
+    """Integer voxel offsets xi with 0 < |xi| < delta (h = 1)."""
+    r = int(math.ceil(delta))
+    g = np.arange(-r, r + 1)
+    off = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    d = np.sqrt((off.astype(np.float64) ** 2).sum(axis=1))
+    keep = (d > 0) & (d < delta)
+    return off[keep], d[keep]
+
+
+def kernel_operator(u, coef, delta):
+    """The nonlocal operator of Eq. 6.5 on the periodic voxel grid for the
+    radial kernel K(r) = sum_m coef_m B_m(r / delta) (r < delta, 0 beyond):
+    L[u](x) = sum over offsets 0 < |xi| < delta of K(|xi|) (u(x + xi) - u(x)),
+    a direct sum (voxel volume 1).  u: (3, nz, ny, nx)."""
+    coef = np.asarray(coef, dtype=np.float64)
+    off, d = horizon_offsets(delta)
+    K = coef @ bernstein(coef.size - 1, d / delta)
+    out = np.zeros_like(u, dtype=np.float64)
+    for (ox, oy, oz), k in zip(off, K):
+        out += k * (np.roll(u, (-oz, -oy, -ox), axis=(-3, -2, -1)) - u)
+    return out
+
+
+def kernel_fit(us, gammas, delta, M, lam, iters=2000, lr=0.05, betas=(0.9, 0.999), eps=1e-8):
+    """Kernel regression of Eq. 6.6 for gamma = b (Gamma_k = -b_k, u_k the
+    averaged displacement of load k): minimise
+      J(c) = sum_k sum_x |L_c[u_k](x) - Gamma_k(x)|^2 + lam |c|^2
+    (Tikhonov regularisation) over the Bernstein coefficients c of K.  J is
+    quadratic: with A_m = L_{e_m}, G_mn = sum_k <A_m u_k, A_n u_k>, g_m =
+    sum_k <A_m u_k, Gamma_k> and s = sum_k |Gamma_k|^2, J = c.G.c - 2 g.c + s +
+    lam |c|^2.  Returns the Adam iterate from c = 0 after `iters` steps (Adam,
+    Kingma and Ba 2015: first/second moment averages with bias correction) with
+    its J, the exact minimiser (G + lam I)^-1 g, G, g and s."""
+    n = M + 1
+    G = np.zeros((n, n))
+    g = np.zeros(n)
+    s = 0.0
+    for u, gam in zip(us, gammas):
+        A = [kernel_operator(u, np.eye(n)[m], delta) for m in range(n)]
+        for a in range(n):
+            g[a] += float((A[a] * gam).sum())
+            for b in range(n):
+                G[a, b] += float((A[a] * A[b]).sum())
+        s += float((gam * gam).sum())
+    exact = np.linalg.solve(G + lam * np.eye(n), g)
+    c = np.zeros(n)
+    m1 = np.zeros(n)
+    v = np.zeros(n)
+    for t in range(1, iters + 1):
+        grad = 2.0 * (G @ c - g + lam * c)
+        m1 = betas[0] * m1 + (1 - betas[0]) * grad
+        v = betas[1] * v + (1 - betas[1]) * grad * grad
+        mh = m1 / (1 - betas[0] ** t)
+        vh = v / (1 - betas[1] ** t)
+        c = c - lr * mh / (np.sqrt(vh) + eps)
+    J = float(c @ G @ c - 2 * g @ c + s + lam * c @ c)
+    return dict(coef=c, loss=J, exact=exact, G=G, g=g, s=s)
 
 
 # ---------------------------------------------------------------- effective moduli and concentration

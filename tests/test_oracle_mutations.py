@@ -49,6 +49,11 @@ MUTATIONS = {
                               "rp = 0 if above.size == 0 else int(above[-1])"),
     "rve_containment_without_annulus": ("ok = r is not None and r + a / 2.0 <= n / 2.0",
                                         "ok = r is not None and r <= n / 2.0"),
+    "kernel_operator_sign": ("out += k * (np.roll(u, (-oz, -oy, -ox), axis=(-3, -2, -1)) - u)",
+                             "out += k * (u - np.roll(u, (-oz, -oy, -ox), axis=(-3, -2, -1)))"),
+    "horizon_inclusive": ("keep = (d > 0) & (d < delta)", "keep = (d > 0) & (d <= delta)"),
+    "adam_without_bias_correction": ("mh = m1 / (1 - betas[0] ** t)", "mh = m1"),
+    "tikhonov_dropped": ("exact = np.linalg.solve(G + lam * np.eye(n), g)", "exact = np.linalg.solve(G, g)"),
     "stiffness_over_inclusions": ('Ls[:, J] = res["sig"].reshape(6, -1).mean(axis=1)',
                                   'Ls[:, J] = res["sig"][:, incl].mean(axis=1)'),
 }

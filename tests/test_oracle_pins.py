@@ -700,3 +700,79 @@ def test_rve_size_loop_needs_the_annulus_inside_the_cell():
     recs = O.rve_size((8, 8, 8), np.asarray([[8, 8, 8, 25, 1]], np.int32), [(1.0, 0.5), (6.0, 3.0)], (3.5, 1.75),
                       4.0, sizes=(24, 32), tol=1e-11, tol_f=0.048)
     assert [(r["n"], r["r_rve"], r["contained"]) for r in recs] == [(24, 11, False), (32, 10, True)]
+
+
+# ------------------------------------------------------------ nonlocal kernel regression (Eqs. 6.5-6.6)
+def test_bernstein_basis_partition_of_unity_and_endpoints():
+    t = np.linspace(0, 1, 11)
+    for M in (0, 1, 3, 6):
+        B = O.bernstein(M, t)
+        assert np.allclose(B.sum(axis=0), 1.0, atol=1e-14)        # binomial theorem
+        assert B[0, 0] == 1.0 and B[M, -1] == 1.0 and np.all(B >= 0)
+
+
+@pytest.mark.parametrize("delta", [2.5, 2.0])     # 2.0: lattice points on the horizon are outside (r < delta)
+def test_kernel_operator_on_plane_waves(delta):
+    """cos(q . x) is an eigenfunction: L[u] = (sum_xi K(|xi|) (cos(q . xi) - 1)) u."""
+    nx, ny, nz = 8, 6, 10
+    coef = np.array([0.3, -1.2, 0.7, 2.0])
+    x = np.arange(nx)[None, None, :]
+    y = np.arange(ny)[None, :, None]
+    z = np.arange(nz)[:, None, None]
+    q = (2 * math.pi * 1 / nx, 2 * math.pi * 2 / ny, 2 * math.pi * 3 / nz)
+    wave = np.cos(q[0] * x + q[1] * y + q[2] * z) * np.ones((nz, ny, nx))
+    u = np.stack([wave, 2 * wave, -wave])
+    mult = 0.0
+    r = 2
+    for ox in range(-r, r + 1):
+        for oy in range(-r, r + 1):
+            for oz in range(-r, r + 1):
+                d = math.sqrt(ox * ox + oy * oy + oz * oz)
+                if 0 < d < delta:
+                    t = d / delta
+                    K = sum(c * math.comb(3, m) * t ** m * (1 - t) ** (3 - m) for m, c in enumerate(coef))
+                    mult += K * (math.cos(q[0] * ox + q[1] * oy + q[2] * oz) - 1)
+    assert np.allclose(O.kernel_operator(u, coef, delta), mult * u, atol=1e-12)
+    assert np.allclose(O.kernel_operator(np.ones((3, nz, ny, nx)), coef, delta), 0.0, atol=1e-13)
+
+
+def test_kernel_operator_with_unit_kernel_against_loops():
+    """All Bernstein coefficients 1 give K = 1 inside the horizon (partition of unity)."""
+    nx, ny, nz = 5, 4, 6
+    u = RNG.standard_normal((3, nz, ny, nx))
+    delta = 1.8
+    out = O.kernel_operator(u, np.ones(4), delta)
+    ref = np.zeros_like(u)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                for ox in (-1, 0, 1):
+                    for oy in (-1, 0, 1):
+                        for oz in (-1, 0, 1):
+                            d = math.sqrt(ox * ox + oy * oy + oz * oz)
+                            if 0 < d < delta:
+                                ref[:, z, y, x] += u[:, (z + oz) % nz, (y + oy) % ny, (x + ox) % nx] - u[:, z, y, x]
+    assert np.allclose(out, ref, atol=1e-12)
+
+
+def test_kernel_fit_recovers_a_planted_kernel_and_shrinks_with_tikhonov():
+    nx, ny, nz = 8, 8, 8
+    delta, M = 3.0, 4
+    c_true = np.array([1.5, -0.5, 0.8, 0.2, -1.0])
+    us = [RNG.standard_normal((3, nz, ny, nx)) for _ in range(2)]
+    gammas = [O.kernel_operator(u, c_true, delta) for u in us]
+    fit = O.kernel_fit(us, gammas, delta, M, lam=0.0, iters=3000, lr=0.02)
+    assert np.allclose(fit["exact"], c_true, rtol=1e-8, atol=1e-10)
+    assert fit["loss"] < 1e-3 * fit["s"]      # Adam from c = 0 (J = s there) gets close; G is ill-conditioned
+    norms = [np.linalg.norm(O.kernel_fit(us, gammas, delta, M, lam=lam, iters=1)["exact"])
+             for lam in (0.0, 1e2, 1e4, 1e6)]
+    assert all(a > b for a, b in zip(norms, norms[1:]))           # Tikhonov shrinks the coefficients
+
+
+def test_kernel_fit_first_adam_step_is_minus_lr_sign_gradient():
+    nx, ny, nz = 6, 6, 6
+    u = RNG.standard_normal((3, nz, ny, nx))
+    gam = RNG.standard_normal((3, nz, ny, nx))
+    fit = O.kernel_fit([u], [gam], 2.0, 2, lam=0.5, iters=1, lr=0.1)
+    grad0 = -2.0 * fit["g"]                                       # gradient at c = 0
+    assert np.allclose(fit["coef"], -0.1 * np.sign(grad0), atol=1e-6)
