@@ -321,6 +321,39 @@ int bfcs_rve_size(int cx, int cy, int cz, int nsph, const int32_t* spheres, int 
                   double tol_f, bfcs_rve_record* records, double* profiles, int* accepted, void* stream);
 
 /*
+ * bfcs_kernel_fit - the paper's nonlocal surrogate (Eqs. 6.5-6.6) for the
+ * displacement operator (gamma = b): a radial kernel K(r) = sum_m c_m
+ * B_m(r / delta), B_m the Bernstein basis of degree `degree` (0..7), zero for
+ * r >= delta, defines L[u](x) = sum over voxel offsets 0 < |xi| < delta of
+ * K(|xi|) (u(x + xi) - u(x)) on the periodic grid (voxel volume 1), and
+ *   J(c) = sum_k sum_x |L[u_k](x) - Gamma_k(x)|^2 + lam |c|^2
+ * (Tikhonov regularisation) is minimised by Adam (Kingma and Ba; betas 0.9,
+ * 0.999, eps 1e-8, step lr, `iters` steps from c = 0); the exact minimiser
+ * (G + lam I)^-1 g of the same quadratic is returned beside it.  Typically u_k
+ * is the averaged displacement <u> of translated averaging or of an ensemble
+ * (Eqs. 3.7-3.8) and Gamma_k = -b_k.  The sums over x are evaluated in Fourier
+ * space (Parseval; K is even, so its transform is real).
+ *  plan:    BFCS_FP64 or BFCS_MIXED plan of the grid (FP64 transforms; else
+ *           BFCS_ERR_UNSUPPORTED); 2 delta < min(nx, ny, nz).
+ *  u, gamma: host arrays of nload device pointers, each 3 x N double.
+ *  coef_out: host, degree+1 (the Adam iterate); exact_out: host, degree+1 or
+ *           NULL; loss_out: host, 2 (J of the Adam iterate, J of the exact
+ *           minimiser) or NULL; gram_out: host (degree+1)^2 (G) or NULL;
+ *           rhs_out: host degree+1 (g) or NULL.
+ * Allocates its working arrays per call.
+ */
+int bfcs_kernel_fit(bfcs_plan plan, int nload, const void* const* u, const void* const* gamma, double delta,
+                    int degree, double lam, int iters, double lr, double* coef_out, double* exact_out,
+                    double* loss_out, double* gram_out, double* rhs_out);
+
+/*
+ * bfcs_kernel_apply - evaluates the nonlocal operator L[u] of bfcs_kernel_fit
+ * for the kernel with Bernstein coefficients coef (host, degree+1) and
+ * horizon delta: u, out dev 3 x N double (same plan requirements).
+ */
+int bfcs_kernel_apply(bfcs_plan plan, int degree, const double* coef, double delta, const void* u, void* out);
+
+/*
  * bfcs_effective_stiffness - effective stiffness L* and inclusion strain
  * concentration A* of the periodic microstructure (Eqs. 6.1-6.3 and Eq. 3.2):
  * the classical problem (b = 0, Eq. 2.24) is solved under the six unit mean

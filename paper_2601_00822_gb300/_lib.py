@@ -36,6 +36,7 @@ EXPORTS = (
     "bfcs_net_destroy", "bfcs_net_prepare", "bfcs_net_forward", "bfcs_net_grad", "bfcs_net_adam",
     "bfcs_net_train_step", "bfcs_net_predict", "bfcs_plan_tuning", "bfcs_solve_group", "bfcs_net_status",
     "bfcs_effective_stiffness", "bfcs_ensemble_average", "bfcs_radial_profile", "bfcs_rve_size",
+    "bfcs_kernel_fit", "bfcs_kernel_apply",
 )
 NET_PARAMS = 523654
 NET_TRAIN = 1
@@ -106,6 +107,8 @@ def _declare(lib):
     lib.bfcs_radial_profile.argtypes = [vp, vp, i, C.POINTER(d), i, vp, vp]
     lib.bfcs_rve_size.argtypes = [i, i, i, i, vp, i, C.POINTER(Lame), Lame, d, i, vp, i, d, i, d,
                                   C.POINTER(RveRecord), vp, C.POINTER(i), vp]
+    lib.bfcs_kernel_fit.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), d, i, d, i, d, vp, vp, vp, vp, vp]
+    lib.bfcs_kernel_apply.argtypes = [vp, i, C.POINTER(d), d, vp, vp]
     lib.bfcs_effective_stiffness.argtypes = [vp, vp, i, C.POINTER(Lame), Lame, d, i, vp, vp, C.POINTER(Info)]
     lib.bfcs_status_string.argtypes = [i]
     lib.bfcs_status_string.restype = C.c_char_p

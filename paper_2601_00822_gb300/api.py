@@ -243,6 +243,35 @@ class Plan:
                    "bfcs_radial_profile")
         return prof, counts
 
+    def kernel_fit(self, us, gammas, delta, degree, lam=0.0, iters=2000, lr=0.05):
+        """bfcs_kernel_fit (Eqs. 6.5-6.6): dict(coef (Adam), exact, loss, exact_loss, G, g)."""
+        nx, ny, nz = self.dims
+        for t in list(us) + list(gammas):
+            _check_tensor(t, (3, nz, ny, nx), torch.float64, "u / gamma")
+        if len(us) != len(gammas) or not us:
+            raise ValueError("one gamma per u")
+        nb = int(degree) + 1
+        pu = (C.c_void_p * len(us))(*[_ptr(t) for t in us])
+        pg = (C.c_void_p * len(gammas))(*[_ptr(t) for t in gammas])
+        coef, exact, loss = np.zeros(nb), np.zeros(nb), np.zeros(2)
+        G, g = np.zeros((nb, nb)), np.zeros(nb)
+        _lib.check(self.lib.bfcs_kernel_fit(self.handle, len(us), pu, pg, float(delta), int(degree), float(lam),
+                                            int(iters), float(lr), coef.ctypes.data_as(C.c_void_p),
+                                            exact.ctypes.data_as(C.c_void_p), loss.ctypes.data_as(C.c_void_p),
+                                            G.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p)),
+                   "bfcs_kernel_fit")
+        return dict(coef=coef, exact=exact, loss=loss[0], exact_loss=loss[1], G=G, g=g)
+
+    def kernel_apply(self, coef, delta, u):
+        """bfcs_kernel_apply: L[u] (3, nz, ny, nx) float64 for Bernstein coefficients coef."""
+        nx, ny, nz = self.dims
+        _check_tensor(u, (3, nz, ny, nx), torch.float64, "u")
+        c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64))
+        out = torch.empty_like(u)
+        _lib.check(self.lib.bfcs_kernel_apply(self.handle, c.size - 1, c.ctypes.data_as(C.POINTER(C.c_double)),
+                                              float(delta), _ptr(u), _ptr(out)), "bfcs_kernel_apply")
+        return out
+
     def effective_stiffness(self, phase, phases, c0, tol=1e-6, maxit=10000,
                             allow=(_lib.OK, _lib.NOT_CONVERGED)):
         """bfcs_effective_stiffness: (L* (6, 6), A* (6, 6), infos) with column J the

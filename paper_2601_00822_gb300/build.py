@@ -36,6 +36,7 @@ UNITS = [
     ("k_cg.cu", ["-DBFCS_R=double"], "k_cg_f64.o"),
     ("k_misc.cu", [], "k_misc.o"),
     ("rve.cu", [], "rve.o"),
+    ("k_nonlocal.cu", [], "k_nonlocal.o"),
     ("solver.cu", [], "solver.o"),
     ("noalloc.cu", [], "noalloc.o"),
     ("unet.cu", [], "unet.o"),

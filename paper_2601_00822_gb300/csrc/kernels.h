@@ -172,6 +172,25 @@ template <typename R> cudaError_t launch_xpass_b(const XArgs<R>& a, int batch, c
 template <typename R> cudaError_t launch_colpass_b(const CArgs<R>& a, int dir, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_zgreen_b(const GArgs<R>& a, int batch, cudaStream_t s);
 
+// ---- nonlocal kernel regression (k_nonlocal.cu, FP64)
+constexpr int kNlMaxBasis = 8;      // Bernstein degree <= 7
+constexpr int kNlParts = 2 * 152;   // partial sums of the Gram reduction
+struct NlCoef { int use; double c[kNlMaxBasis]; };
+// nb basis fields B_{m0..m0+nb-1}(|xi| / delta) (or, coef.use, one field sum_m c_m B_m) at minimum-image offsets
+cudaError_t launch_basis_fields(double* w, int nb, int M, int m0, const NlCoef& coef, double delta, const Geo& g,
+                                cudaStream_t s);
+// W[(m0 + c) * modes + i] = Re of spectral component c at compact mode i
+cudaError_t launch_extract_real(const C2<double>* spec, int ncomp, const Geo& g, double* W, int m0, cudaStream_t s);
+// acc += (packed upper G, g, s) / N of one load: spec components 0..2 u_hat, 3..5 Gamma_hat
+cudaError_t launch_kernel_gram(int nb, const double* W, const C2<double>* spec, const Geo& g, double* part,
+                               double* acc, cudaStream_t s);
+// Adam (iters steps from 0) and the exact minimiser; out: coef, exact, J(coef), J(exact), G, g
+cudaError_t launch_kernel_adam(const double* acc, int nb, double lam, int iters, double lr, double* out,
+                               cudaStream_t s);
+// spec_c *= (K_hat - K_hat(0)) * scale, c < ncomp
+cudaError_t launch_kernel_mult(C2<double>* spec, int ncomp, const Geo& g, const double* Kr, double scale,
+                               cudaStream_t s);
+
 bool supported_len(int n);
 
 // process-wide count of kernel launches made by this library

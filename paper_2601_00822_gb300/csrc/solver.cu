@@ -1847,7 +1847,153 @@ static int fft3d_impl(bfcs_plan P, int dir, int ncomp, const void* in, void* out
   return sync_stream(P);
 }
 
+// FP64 forward transform of ncomp (<= 6) real fields into spec ([c][z][y][p]),
+// or the inverse of spec into real fields (unnormalised), with the given twiddles
+static int fp64_forward(bfcs_plan P, const double* in, int ncomp, C2<double>* spec, void* const* tw) {
+  XArgs<double> xa{};
+  xa.g = P->g;
+  xa.ncomp = ncomp;
+  xa.tw = (const C2<double>*)tw[0];
+  xa.mode = XM_R2C;
+  xa.real_in = in;
+  xa.spec_out = spec;
+  CK(launch_xpass<double>(xa, P->st));
+  CArgs<double> ca{};
+  ca.data = spec;
+  ca.g = P->g;
+  ca.ncomp = ncomp;
+  ca.axis = 1; ca.tw = (const C2<double>*)tw[1];
+  CK(launch_colpass<double>(ca, -1, P->st));
+  ca.axis = 2; ca.tw = (const C2<double>*)tw[2];
+  CK(launch_colpass<double>(ca, -1, P->st));
+  return BFCS_OK;
+}
+static int fp64_inverse(bfcs_plan P, C2<double>* spec, int ncomp, double* out, void* const* tw) {
+  CArgs<double> ca{};
+  ca.data = spec;
+  ca.g = P->g;
+  ca.ncomp = ncomp;
+  ca.axis = 2; ca.tw = (const C2<double>*)tw[2];
+  CK(launch_colpass<double>(ca, +1, P->st));
+  ca.axis = 1; ca.tw = (const C2<double>*)tw[1];
+  CK(launch_colpass<double>(ca, +1, P->st));
+  XArgs<double> xa{};
+  xa.g = P->g;
+  xa.ncomp = ncomp;
+  xa.tw = (const C2<double>*)tw[0];
+  xa.mode = XM_C2R;
+  xa.spec_in = spec;
+  xa.real_out = out;
+  CK(launch_xpass<double>(xa, P->st));
+  return BFCS_OK;
+}
+
+// device buffers of one nonlocal-kernel call, freed on exit
+struct NlBufs {
+  void* p[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  ~NlBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+  bool alloc(int i, size_t bytes) { return cudaMalloc(&p[i], bytes) == cudaSuccess; }
+};
+
+static int nl_check(bfcs_plan P, int degree, double delta) {
+  if (P == nullptr || degree < 0 || degree >= kNlMaxBasis || !(delta > 0) || !std::isfinite(delta))
+    return BFCS_ERR_INVALID_ARG;
+  if (!P->fp64 && !P->mixed) return BFCS_ERR_UNSUPPORTED;
+  if (2.0 * delta >= (double)std::min(P->g.nx, std::min(P->g.ny, P->g.nz))) return BFCS_ERR_INVALID_ARG;
+  return BFCS_OK;
+}
+
 extern "C" {
+
+int bfcs_kernel_fit(bfcs_plan P, int nload, const void* const* u, const void* const* gamma, double delta,
+                    int degree, double lam, int iters, double lr, double* coef_out, double* exact_out,
+                    double* loss_out, double* gram_out, double* rhs_out) {
+  int e = nl_check(P, degree, delta);
+  if (e != BFCS_OK) return e;
+  if (nload < 1 || u == nullptr || gamma == nullptr || coef_out == nullptr || !(lam >= 0) || !std::isfinite(lam) ||
+      iters < 0 || !(lr > 0) || !std::isfinite(lr))
+    return BFCS_ERR_INVALID_ARG;
+  for (int k = 0; k < nload; ++k)
+    if (u[k] == nullptr || gamma[k] == nullptr) return BFCS_ERR_INVALID_ARG;
+  const Geo g = P->g;
+  const int nb = degree + 1;
+  const int nacc = nb * (nb + 1) / 2 + nb + 1;
+  const int nout = 2 * nb + 2 + nb * nb + nb;
+  const size_t modes = (size_t)g.nz * g.ny * g.mx;
+  C2<double>* spec = (C2<double>*)(P->mixed ? P->spec64 : P->spec);
+  void* const* tw = P->mixed ? P->tw64 : P->tw;
+  NlBufs B;
+  if (!B.alloc(0, nb * modes * sizeof(double)) || !B.alloc(1, std::min(nb, 6) * (size_t)g.n * sizeof(double)) ||
+      !B.alloc(2, (size_t)kNlParts * nacc * sizeof(double)) || !B.alloc(3, nacc * sizeof(double)) ||
+      !B.alloc(4, nout * sizeof(double))) {
+    cudaGetLastError();
+    return BFCS_ERR_OOM;
+  }
+  double* W = (double*)B.p[0];
+  double* wf = (double*)B.p[1];
+  CK(cudaMemsetAsync(B.p[3], 0, nacc * sizeof(double), P->st));
+  const NlCoef none{};
+  for (int m0 = 0; m0 < nb; m0 += 6) {            // spectra of the basis kernels, six at a time
+    const int k = std::min(6, nb - m0);
+    CK(launch_basis_fields(wf, k, degree, m0, none, delta, g, P->st));
+    e = fp64_forward(P, wf, k, spec, tw);
+    if (e != BFCS_OK) return e;
+    CK(launch_extract_real(spec, k, g, W, m0, P->st));
+  }
+  for (int k = 0; k < nload; ++k) {                // Gram matrix, right-hand side and |Gamma|^2 of every load
+    e = fp64_forward(P, (const double*)u[k], 3, spec, tw);
+    if (e == BFCS_OK) e = fp64_forward(P, (const double*)gamma[k], 3, spec + 3 * g.cs, tw);
+    if (e != BFCS_OK) return e;
+    CK(launch_kernel_gram(nb, W, spec, g, (double*)B.p[2], (double*)B.p[3], P->st));
+  }
+  CK(launch_kernel_adam((const double*)B.p[3], nb, lam, iters, lr, (double*)B.p[4], P->st));
+  std::vector<double> h(nout);
+  CK(cudaMemcpyAsync(h.data(), B.p[4], nout * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  const int w = sync_stream(P);
+  if (w != BFCS_OK) return w;
+  for (int a = 0; a < nb; ++a) {
+    coef_out[a] = h[a];
+    if (exact_out != nullptr) exact_out[a] = h[nb + a];
+    if (rhs_out != nullptr) rhs_out[a] = h[2 * nb + 2 + nb * nb + a];
+  }
+  if (loss_out != nullptr) { loss_out[0] = h[2 * nb]; loss_out[1] = h[2 * nb + 1]; }
+  if (gram_out != nullptr)
+    for (int a = 0; a < nb * nb; ++a) gram_out[a] = h[2 * nb + 2 + a];
+  return BFCS_OK;
+}
+
+int bfcs_kernel_apply(bfcs_plan P, int degree, const double* coef, double delta, const void* u, void* out) {
+  int e = nl_check(P, degree, delta);
+  if (e != BFCS_OK) return e;
+  if (coef == nullptr || u == nullptr || out == nullptr) return BFCS_ERR_INVALID_ARG;
+  const Geo g = P->g;
+  NlCoef kc{};
+  kc.use = 1;
+  for (int m = 0; m <= degree; ++m) {
+    if (!std::isfinite(coef[m])) return BFCS_ERR_INVALID_ARG;
+    kc.c[m] = coef[m];
+  }
+  C2<double>* spec = (C2<double>*)(P->mixed ? P->spec64 : P->spec);
+  void* const* tw = P->mixed ? P->tw64 : P->tw;
+  NlBufs B;
+  if (!B.alloc(0, (size_t)g.n * sizeof(double)) ||
+      !B.alloc(1, (size_t)g.nz * g.ny * g.mx * sizeof(double))) {
+    cudaGetLastError();
+    return BFCS_ERR_OOM;
+  }
+  CK(launch_basis_fields((double*)B.p[0], 1, degree, 0, kc, delta, g, P->st));    // K on the grid
+  e = fp64_forward(P, (const double*)B.p[0], 1, spec, tw);
+  if (e != BFCS_OK) return e;
+  CK(launch_extract_real(spec, 1, g, (double*)B.p[1], 0, P->st));                 // K_hat (real)
+  e = fp64_forward(P, (const double*)u, 3, spec, tw);
+  if (e != BFCS_OK) return e;
+  CK(launch_kernel_mult(spec, 3, g, (const double*)B.p[1], 1.0 / (double)g.n, P->st));
+  e = fp64_inverse(P, spec, 3, (double*)out, tw);
+  if (e != BFCS_OK) return e;
+  return sync_stream(P);
+}
 
 int bfcs_fft3d(bfcs_plan P, int direction, int ncomp, const void* in, void* out) {
   if (P == nullptr || in == nullptr || out == nullptr || ncomp < 1 || ncomp > 6 ||
