@@ -138,6 +138,11 @@ template <> __device__ __forceinline__ double norm2<ff>(C2<ff> z) {
   return (double)__fmaf_rn(z.x.hi, z.x.hi, __fmul_rn(z.y.hi, z.y.hi));
 }
 
+// 1 / q rounded to nearest (FP32: the reciprocal intrinsic, without the
+// general division's special-case path)
+template <typename R> __device__ __forceinline__ R recip(R q) { return R(1) / q; }
+template <> __device__ __forceinline__ float recip<float>(float q) { return __frcp_rn(q); }
+
 // cos(2 pi j / 48), exact quarter-wave table extended by symmetry; every radix
 // used below divides 48, so these are all the constants the register DFTs need.
 __host__ __device__ constexpr double q48(int j) {

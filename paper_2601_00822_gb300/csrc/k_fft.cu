@@ -99,14 +99,12 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
       for (int k1 = 0; k1 < R1; ++k1) sf[xpad(t * R1 + k1)] = x[k1];
     }
     __syncthreads();
-    C2<R> y[R2];
+    // stage 2 reads and writes the same slots of its pair-line (t + R1 m, m < R2)
     if (fval && t < R1) {
+      C2<R> y[R2];
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) y[n2] = sf[xpad(n2 * R1 + t)];
       stage2<R, L, +1>(y);
-    }
-    __syncthreads();
-    if (fval && t < R1) {
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) sf[xpad(t + R1 * k2)] = y[k2];
     }

@@ -41,11 +41,11 @@ static_assert(kGreenT == 4 && (6 * kGreenT) % 8 == 0, "the swizzle flips one com
 __device__ __forceinline__ int gslot(int row, int c) { return c ^ (((row >> 1) & 1) << 2); }
 
 template <typename R>
-__device__ __forceinline__ void g0_apply(const C2<R> g[3], const R xi[3], R q, R mu0, R c,
+__device__ __forceinline__ void g0_apply(const C2<R> g[3], const R xi[3], R q, R inv_mu0, R c,
                                          C2<R> v[3]) {
   const C2<R> xg = scale(g[0], xi[0]) + scale(g[1], xi[1]) + scale(g[2], xi[2]);
-  const R iq = R(1) / q;
-  const R a = iq / mu0;
+  const R iq = recip(q);
+  const R a = iq * inv_mu0;
   const R b = c * iq;
 #pragma unroll
   for (int i = 0; i < 3; ++i) v[i] = scale(g[i] - scale(xg, b * xi[i]), a);
@@ -136,7 +136,7 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
     w[1] = mk<R>(d[1].x + bh1.y, d[1].y - bh1.x);
     w[2] = mk<R>(d[2].x + bh2.y, d[2].y - bh2.x);
     C2<R> v[3];
-    g0_apply<R>(w, xi, qq, mu0, c0, v);
+    g0_apply<R>(w, xi, qq, recip(mu0), c0, v);
     if (mode == GM_FINAL) {
       // u_hat = i v, scaled for the unnormalised inverse transforms
 #pragma unroll
@@ -216,14 +216,13 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
       for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + gslot(j * R1 + k1, c)] = x[k1];
     }
     __syncthreads();
-    C2<R> y[R2];
+    // stage 2 reads and writes the same slots (rows j + R1 m, m < R2, of column c):
+    // no other thread touches them, so no barrier separates the read and the write
     if (j < R1) {
+      C2<R> y[R2];
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + gslot(n2 * R1 + j, c)];
       stage2<R, L, -1>(y);
-    }
-    __syncthreads();
-    if (j < R1) {
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) s[(j + R1 * k2) * NCOL + gslot(j + R1 * k2, c)] = y[k2];
     }
