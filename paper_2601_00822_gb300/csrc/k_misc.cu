@@ -247,9 +247,20 @@ __global__ void k_bden(const C2<R>* bhat, Geo g, ResidSlot* part, long long b_ms
     if (sx == 0 && sy == 0 && sz == 0) continue;
     const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
     const long long gi = (long long)r * g.p + kx;
-    for (int c = 0; c < 3; ++c) {
-      const C2<R> v = bhat[c * g.cs + gi];
-      acc += w * ((double)v.x * v.x + (double)v.y * v.y);
+    if constexpr (sizeof(R) == 4) {
+      // |b_hat|^2 of the mode in FP32 (relative 1e-7 is ample for a normaliser), summed in
+      // FP64: one FP64 operation per mode instead of twelve on GB300's slow FP64 pipe
+      float t = 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        const C2<R> v = bhat[c * g.cs + gi];
+        t += v.x * v.x + v.y * v.y;
+      }
+      acc += w * (double)t;
+    } else {
+      for (int c = 0; c < 3; ++c) {
+        const C2<R> v = bhat[c * g.cs + gi];
+        acc += w * ((double)v.x * v.x + (double)v.y * v.y);
+      }
     }
   }
   const double t = block_sum(acc, red);
@@ -418,6 +429,20 @@ __global__ void k_scale(double* acc, long long count, double f) {
 
 cudaError_t launch_scale(double* acc, long long count, double f, cudaStream_t s) {
   k_scale<<<4 * 152, 256, 0, s>>>(acc, count, f);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- small device -> pinned-host reads
+// A kernel writes the words straight into the pinned host buffer (its address is
+// valid on the device under unified addressing): the read takes no copy engine, so
+// it never waits behind large transfers that other streams keep on the engines.
+__global__ void k_copy_words(unsigned* dst, const unsigned* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  __threadfence_system();
+}
+cudaError_t launch_copy_words(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  k_copy_words<<<1, 256, 0, s>>>((unsigned*)dst, (const unsigned*)src, (int)(bytes / sizeof(unsigned)));
   count_launches(1);
   return cudaGetLastError();
 }

@@ -191,6 +191,9 @@ cudaError_t launch_kernel_adam(const double* acc, int nb, double lam, int iters,
 cudaError_t launch_kernel_mult(C2<double>* spec, int ncomp, const Geo& g, const double* Kr, double scale,
                                cudaStream_t s);
 
+// copy `bytes` (a multiple of 4) from device memory into pinned host memory with a kernel
+cudaError_t launch_copy_words(void* dst, const void* src, size_t bytes, cudaStream_t s);
+
 bool supported_len(int n);
 
 // process-wide count of kernel launches made by this library

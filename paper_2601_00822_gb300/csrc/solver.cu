@@ -119,6 +119,24 @@ int sync_stream(bfcs_plan P) {
     if ((x) != cudaSuccess) return BFCS_ERR_CUDA; \
   } while (0)
 
+// Small reads of a solve's state into the plan's pinned host buffers.  With
+// unified addressing a kernel writes them directly (no copy engine: a user's
+// large host<->device copies on other streams do not hold the solve up); else an
+// ordinary asynchronous copy.
+bool host_writable_from_device() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0, ua = 0;
+    v = (cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&ua, cudaDevAttrUnifiedAddressing, dev) == cudaSuccess && ua == 1) ? 1 : 0;
+  }
+  return v == 1;
+}
+cudaError_t read_small(void* host, const void* dev, size_t bytes, cudaStream_t st) {
+  if (bytes % sizeof(unsigned) == 0 && host_writable_from_device()) return launch_copy_words(host, dev, bytes, st);
+  return cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st);
+}
+
 template <typename R>
 void* make_twiddles(int n) {
   std::vector<C2<R>> h(n);
@@ -238,8 +256,8 @@ int validate_members(bfcs_plan P, int B, const int8_t* const* phase, const void*
   for (int m = 0; m < B; ++m)
     CK(launch_validate<R>(phase[m], (const R*)b[m], P->g.n, P->ival + 2 * m, P->dval + 6 * m, P->dscratch,
                           P->st));
-  CK(cudaMemcpyAsync(P->ival_host, P->ival, 2 * B * sizeof(int), cudaMemcpyDeviceToHost, P->st));
-  CK(cudaMemcpyAsync(P->dval_host, P->dval, 6 * B * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+  CK(read_small(P->ival_host, P->ival, 2 * B * sizeof(int), P->st));
+  CK(read_small(P->dval_host, P->dval, 6 * B * sizeof(double), P->st));
   const int w = sync_stream(P);
   if (w != BFCS_OK) return w;
   const double thr = sizeof(R) == 4 ? 1e-6 : 1e-12;
@@ -489,7 +507,7 @@ struct SweepSet {
     xu.tw = (const C2<R>*)P->tw[0];
     CK(launch_xpass_b<R>(xu, B, st));   // members without u_out write nothing
     IterState* hf = P->ist_host + 2 * P->max_batch;
-    CK(cudaMemcpyAsync(hf, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    CK(read_small(hf, P->ist, B * sizeof(IterState), st));
     const int w = sync_stream(P);
     if (w != BFCS_OK) return w;
     P->last_iters = hf[0].iters;
@@ -649,8 +667,7 @@ int run_sets(std::vector<SweepSet<R>*>& sets, int maxit) {
   };
   auto read_states = [&](int slot) -> int {
     for (int i = 0; i < S; ++i)
-      CK(cudaMemcpyAsync(host_state(slot, i), sets[i]->P->ist, sets[i]->B * sizeof(IterState),
-                         cudaMemcpyDeviceToHost, main));
+      CK(read_small(host_state(slot, i), sets[i]->P->ist, sets[i]->B * sizeof(IterState), main));
     CK(cudaEventRecord(ev[slot], main));
     return BFCS_OK;
   };
@@ -744,7 +761,7 @@ int run_cg(SweepSet<R>& ss, std::vector<double>& req, int maxit, std::vector<int
   bool unknown = false;
   for (int m = 0; m < B; ++m) unknown = unknown || (!(req[m] > 0) && !P->mem_host[m].warm);
   if (unknown) {   // cold start: the sweep just run evaluated r(eps^0)
-    CK(cudaMemcpyAsync(P->ist_host, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    CK(read_small(P->ist_host, P->ist, B * sizeof(IterState), st));
     const int w = sync_stream(P);
     if (w != BFCS_OK) return w;
     for (int m = 0; m < B; ++m)
@@ -799,7 +816,7 @@ int run_cg(SweepSet<R>& ss, std::vector<double>& req, int maxit, std::vector<int
     }
     it += c;
     chunk = std::min(chunk * 2, 64);
-    CK(cudaMemcpyAsync(P->cg_host, P->cg_state, B * sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    CK(read_small(P->cg_host, P->cg_state, B * sizeof(CgState), st));
     const int w = sync_stream(P);
     if (w != BFCS_OK) return w;
     done_all = 1;
@@ -850,7 +867,7 @@ int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const do
         if (!finished[m]) CK(cudaMemsetAsync(P->ist + m, 0, offsetof(IterState, resid_last), P->st));
       e = run_sets<R>(sets, 2);
       if (e != BFCS_OK) return e;
-      CK(cudaMemcpyAsync(P->ist_host, P->ist, B * sizeof(IterState), cudaMemcpyDeviceToHost, P->st));
+      CK(read_small(P->ist_host, P->ist, B * sizeof(IterState), P->st));
       const int w = sync_stream(P);
       if (w != BFCS_OK) return w;
       all = true;
@@ -1224,7 +1241,7 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
     e = defect64(P, (int)act.size(), mem.data(), act.data(), tabff);
     if (e != BFCS_OK) return e;
     IterState* h64 = P->ist_host + 2 * P->max_batch;
-    CK(cudaMemcpyAsync(h64, P->ist64, B * sizeof(IterState), cudaMemcpyDeviceToHost, st));
+    CK(read_small(h64, P->ist64, B * sizeof(IterState), st));
     const int w = sync_stream(P);
     if (w != BFCS_OK) return w;
     std::vector<int> next;
