@@ -20,18 +20,20 @@ namespace bfcs {
 
 constexpr int kCgThreads = 256;
 
-// Re(a : C0 : conj b) for the 6 tensorial components (xx yy zz yz xz xy)
+// Re(a : C0 : conj b) for the 6 tensorial components (xx yy zz yz xz xy), in the
+// vectors' precision (FP32 vectors: FP32 per mode, the caller sums modes in FP64;
+// GB300's FP64 pipe would otherwise bound the vector kernels)
 template <typename R>
 __device__ __forceinline__ double c0dot(const C2<R> (&a)[6], const C2<R> (&b)[6], double lam0, double mu0) {
-  double ta_r = (double)a[0].x + a[1].x + a[2].x, ta_i = (double)a[0].y + a[1].y + a[2].y;
-  double tb_r = (double)b[0].x + b[1].x + b[2].x, tb_i = (double)b[0].y + b[1].y + b[2].y;
-  double s = 0.0;
+  const R ta_r = a[0].x + a[1].x + a[2].x, ta_i = a[0].y + a[1].y + a[2].y;
+  const R tb_r = b[0].x + b[1].x + b[2].x, tb_i = b[0].y + b[1].y + b[2].y;
+  R s = R(0);
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    const double w = c < 3 ? 1.0 : 2.0;
-    s += w * ((double)a[c].x * b[c].x + (double)a[c].y * b[c].y);
+    const R w = c < 3 ? R(1) : R(2);
+    s += w * (a[c].x * b[c].x + a[c].y * b[c].y);
   }
-  return lam0 * (ta_r * tb_r + ta_i * tb_i) + 2.0 * mu0 * s;
+  return (double)((R)lam0 * (ta_r * tb_r + ta_i * tb_i) + R(2) * (R)mu0 * s);
 }
 
 __device__ __forceinline__ double block_reduce(double v, double* red) {
