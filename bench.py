@@ -309,8 +309,9 @@ def run_ours(args):
 
     # end to end through host buffers: every step copies its phase map and b from pinned
     # memory to the device, solves through the public API and reads its strain back to
-    # pinned memory.  The copies run on a copy stream, pipelined with the solves (inputs
-    # and outputs double-buffered): step k+1's H2D and step k's D2H overlap solve k+1.
+    # pinned memory.  The copies run on two copy streams (one per direction, so both copy
+    # engines work), pipelined with the solves (inputs and outputs double-buffered): step
+    # k+1's H2D overlaps solve k and step k's D2H overlaps solve k+1.
     e2e = None
     if not args.no_e2e:
         ph_d = api.voxelize(p.dims, p.cell, p.spheres, device=dev)
@@ -321,7 +322,8 @@ def run_ours(args):
         ph_in = [torch.empty_like(ph_d) for _ in range(2)]
         b_in = [torch.empty_like(b_d) for _ in range(2)]
         eps_out = [eps, torch.empty_like(eps)]
-        cstream = torch.cuda.Stream(device=dev)
+        cstream = torch.cuda.Stream(device=dev)        # host -> device
+        dstream = torch.cuda.Stream(device=dev)        # device -> host
         ev_in = [torch.cuda.Event() for _ in range(2)]
         ev_done = [torch.cuda.Event() for _ in range(2)]
 
@@ -344,10 +346,11 @@ def run_ours(args):
                                            eps_out=eps_out[slot], sig_out=sig, u_out=u)
                 sweeps += info.iters
                 ev_done[slot].record(stream)
-                cstream.wait_event(ev_done[slot])
-                with torch.cuda.stream(cstream):
+                dstream.wait_event(ev_done[slot])
+                with torch.cuda.stream(dstream):
                     eps_h.copy_(eps_out[slot], non_blocking=True)
-            stream.wait_stream(cstream)                 # the last read-back is inside the timed region
+                ev_done[slot].record(dstream)           # the slot is free once its strain is read back
+            stream.wait_stream(dstream)                 # the last read-back is inside the timed region
             return sweeps
 
         e2e_run(1)
