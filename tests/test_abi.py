@@ -70,3 +70,28 @@ def test_network_parameter_count_and_invalid_contexts():
     assert lib.bfcs_net_create(ctypes.byref(h), 16, 16, 16, 1, 4, None) == _lib.ERR_INVALID_ARG  # flags
     assert lib.bfcs_net_create(None, 16, 16, 16, 1, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_net_destroy(None) == _lib.ERR_INVALID_ARG
+
+
+def test_new_entry_points_reject_bad_arguments_before_device_work():
+    lib = _lib.load()
+    lame = (_lib.Lame * 2)(_lib.Lame(1.0, 0.5), _lib.Lame(6.0, 3.0))
+    c0 = _lib.Lame(3.5, 1.75)
+    out = (ctypes.c_double * 64)()
+    centre = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    cfg = (ctypes.c_void_p * 1)(None)
+    assert lib.bfcs_radial_profile(None, None, 6, centre, 4, out, None) == _lib.ERR_INVALID_ARG
+    assert lib.bfcs_ensemble_average(None, 1, cfg, 2, lame, c0, None, out, 1e-6, 10, None, None, None) == \
+        _lib.ERR_INVALID_ARG
+    assert lib.bfcs_kernel_fit(None, 1, cfg, cfg, 2.0, 3, 0.0, 10, 0.01, out, None, None, None, None) == \
+        _lib.ERR_INVALID_ARG
+    assert lib.bfcs_kernel_apply(None, 3, out, 2.0, None, None) == _lib.ERR_INVALID_ARG
+    rec = (_lib.RveRecord * 2)()
+    acc = ctypes.c_int(7)
+    sph = (ctypes.c_int32 * 5)(8, 8, 8, 25, 1)
+    sizes = (ctypes.c_int * 2)(16, 20)                     # 20 is not a whole number of 8^3 cells
+    assert lib.bfcs_rve_size(8, 8, 8, 1, sph, 2, lame, c0, 3.0, 2, sizes, 0, 1e-6, 100, 0.05, rec, None,
+                             ctypes.byref(acc), None) == _lib.ERR_INVALID_ARG
+    sizes_ok = (ctypes.c_int * 2)(16, 24)
+    for a, tol_f in ((0.0, 0.05), (3.0, 0.0), (-1.0, 0.05)):  # support radius and field tolerance must be positive
+        assert lib.bfcs_rve_size(8, 8, 8, 1, sph, 2, lame, c0, a, 2, sizes_ok, 0, 1e-6, 100, tol_f, rec, None,
+                                 ctypes.byref(acc), None) == _lib.ERR_INVALID_ARG

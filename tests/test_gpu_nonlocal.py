@@ -91,3 +91,17 @@ def test_full_size_planted_kernel_and_loss():
         # the Parseval loss of the Adam iterate against a direct evaluation through the operator
         direct = sum(float(((plan.kernel_apply(fit["coef"], 3.0, u) - g) ** 2).sum()) for u, g in zip(us, gs))
         assert abs(direct - fit["loss"]) <= 1e-8 * sum(float((g * g).sum()) for g in gs)
+
+
+def test_kernel_fit_argument_errors():
+    u = torch.zeros((3, 16, 16, 16), dtype=torch.float64, device="cuda")
+    with api.Plan((16, 16, 16), "fp32") as plan:                # FP32 plans have no FP64 transforms
+        with pytest.raises(RuntimeError):
+            plan.kernel_apply([1.0, 1.0], 2.0, u)
+    with api.Plan((16, 16, 16), "fp64") as plan:
+        with pytest.raises(RuntimeError):
+            plan.kernel_apply([1.0, 1.0], 8.0, u)                # 2 delta must stay below the grid
+        with pytest.raises(RuntimeError):
+            plan.kernel_fit([u], [u], 2.0, 8)                    # degree above 7
+        out = plan.kernel_apply([1.0, -2.0, 0.5], 2.5, u)        # zero field -> zero operator
+        assert float(out.abs().max()) == 0.0

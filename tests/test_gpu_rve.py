@@ -91,3 +91,16 @@ def test_full_size_loop_decisions_and_stabilisation():
 
     diff = (window(ea, ca, n) - window(eb, cb, 256)).abs()[:, ball].max().item()
     assert diff <= tol_f * ea.abs().max().item(), diff
+
+
+def test_radial_profile_argument_errors():
+    with api.Plan((16, 16, 16), "fp64") as plan:
+        f = torch.zeros((6, 16, 16, 16), dtype=torch.float64, device="cuda")
+        with pytest.raises(RuntimeError):
+            plan.radial_profile(f, (8.25, 8.0, 8.0), 8)        # not on the half-voxel lattice
+        with pytest.raises(RuntimeError):
+            plan.radial_profile(f, (8.0, 8.0, 8.0), 0)         # no shells
+        with pytest.raises(RuntimeError):
+            plan.radial_profile(f, (8.0, 8.0, 8.0), 4096)      # more shells than the kernel keeps
+        prof, counts = plan.radial_profile(f, (-8.0, 24.0, 8.5), 8)   # centres wrap periodically
+        assert np.all(prof == 0) and counts.sum() > 0
