@@ -7,6 +7,7 @@
 // here is unnormalised.  `dir` is -1 for forward, +1 for inverse.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace bfcs {
@@ -311,11 +312,30 @@ __device__ __forceinline__ void fft_cols(C2<R>* s, int ncol, const C2<R>* __rest
 template <typename R, int L, int R1, int DIR>
 __device__ __forceinline__ void stage1f(C2<R>* x, int n2, const C2<R>* __restrict__ tw) {
   Dft<R, R1, DIR>::run(x);
+  if constexpr (R1 % 4 == 0 && R1 >= 8 && sizeof(R) <= 8 && !std::is_same<R, ff>::value) {
+    // W^(n2 k1) with k1 = 4 a + b as W^(4 n2 a) W^(n2 b): R1/4 - 1 + 3 table loads
+    // and (R1/4 - 1) * 3 products instead of R1 - 1 loads (each product adds about
+    // one rounding; float-float keeps the table, where a product costs more than a load)
+    constexpr int A = R1 / 4;
+    C2<R> wb[4], wa[A];
 #pragma unroll
-  for (int k1 = 1; k1 < R1; ++k1) {
-    C2<R> w = tw[(n2 * k1) % L];
-    if (DIR > 0) w.y = -w.y;
-    x[k1] = cmul(x[k1], w);
+    for (int b = 1; b < 4; ++b) wb[b] = tw[(n2 * b) % L];
+#pragma unroll
+    for (int a = 1; a < A; ++a) wa[a] = tw[(n2 * 4 * a) % L];
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      const int a = k1 / 4, b = k1 % 4;
+      C2<R> w = a == 0 ? wb[b] : b == 0 ? wa[a] : cmul(wa[a], wb[b]);
+      if (DIR > 0) w.y = -w.y;
+      x[k1] = cmul(x[k1], w);
+    }
+  } else {
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      C2<R> w = tw[(n2 * k1) % L];
+      if (DIR > 0) w.y = -w.y;
+      x[k1] = cmul(x[k1], w);
+    }
   }
 }
 template <typename R, int R2, int DIR>
