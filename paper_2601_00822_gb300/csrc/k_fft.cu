@@ -77,6 +77,28 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
     }
     if (tid == 0) sx_s = ((M.sx % nx) + nx) % nx;
   }
+  // the block's phase-map rows (untranslated in x) stream into shared memory during
+  // the inverse transform, so the polarization does not wait on one load per voxel
+  constexpr bool kPhaseStaged = L % 16 == 0;
+  __shared__ __align__(16) int8_t ph_s[kPhaseStaged ? LPB : 1][kPhaseStaged ? L : 16];
+  const bool polar = mode == XM_SWEEP || mode == XM_REALTAU || mode == XM_REALSIG || mode == XM_SWEEPSIG;
+  // 16-byte copies need a 16-byte aligned map (a caller may pass an offset view: then direct loads)
+  const bool staged = kPhaseStaged && polar && ((reinterpret_cast<uintptr_t>(a.xm[m].phase) & 15u) == 0);
+  if (staged) {
+    const XMember& M = a.xm[m];
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    constexpr int CH = L / 16;                     // 16-byte pieces per row
+    for (int q = tid; q < LPB * CH; q += blockDim.x) {
+      const int i = q / CH, ch = q - i * CH;
+      const long long ln = line0 + i;
+      if (ln >= lines) continue;
+      int y = (int)(ln % ny) - ((M.sy % ny) + ny) % ny, z = (int)(ln / ny) - ((M.sz % nz) + nz) % nz;
+      if (y < 0) y += ny;
+      if (z < 0) z += nz;
+      cp_async16(&ph_s[i][ch * 16], M.phase + (long long)(z * ny + y) * nx + ch * 16);
+    }
+    cp_async_commit();
+  }
 
   // ---- 1. inverse transform along x of the pair-line Z = A + i B (C2R), or load real data
   if (mode == XM_SWEEP || mode == XM_C2R || mode == XM_SWEEPSIG) {
@@ -122,6 +144,7 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
       s[ff * LP + xpad(n)] = z;
     }
   }
+  if (staged) cp_async_wait_all();
   __syncthreads();
 
   if (mode == XM_C2R) {
@@ -156,7 +179,7 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xp
       const XMember& M = a.xm[m];
       int xs = n - sx;
       if (xs < 0) xs += nx;
-      const int ph = M.phase[prow_s[i] + xs];
+      const int ph = staged ? (int)ph_s[kPhaseStaged ? i : 0][kPhaseStaged ? xs : 0] : (int)M.phase[prow_s[i] + xs];
       const R tr = e0 + e1 + e2;
       const long long vox = ln * L + n;
       if (M.eps_out != nullptr) {

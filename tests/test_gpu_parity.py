@@ -554,3 +554,23 @@ def test_full_size_solve_meets_tolerance_independently_checked():
     with api.Plan(p.dims, "fp32") as plan:
         _, _, _, info32 = plan.solve(ph, p.phases, p.c0, b32, tol=p.tol, maxit=4000)
     assert info32.status == _lib.NOT_CONVERGED and info32.stalled == 1 and info32.resid < 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_phase_map_at_an_unaligned_address(precision):
+    """A phase map passed as a view one byte into a larger buffer (the x pass then
+    reads it directly instead of staging 16-byte pieces) gives the same fields as
+    the same map at an aligned address; both match the oracle at a fixed sweep count."""
+    p = CASES["c1_32cubed"]
+    ph, b = gpu_inputs(p, precision)
+    big = torch.zeros(ph.numel() + 1, dtype=torch.int8, device="cuda")
+    big[1:].copy_(ph.view(-1))
+    ph_off = big[1:].view(ph.shape)
+    assert ph_off.data_ptr() % 16 == 1
+    with api.Plan(p.dims, precision) as plan:
+        e0, s0, u0, _ = plan.solve(ph, p.phases, p.c0, b, tol=0, maxit=6)
+        e1, s1, u1, _ = plan.solve(ph_off, p.phases, p.c0, b, tol=0, maxit=6)
+    assert torch.equal(e0, e1) and torch.equal(s0, s1) and torch.equal(u0, u1)
+    ph_o, b_o = oracle_inputs(p)
+    ref = O.solve(ph_o, p.phases, p.c0, b_o, tol=0, maxit=6)
+    assert rel(e1.cpu().numpy(), ref["eps"]) < TOL[precision] * 10
