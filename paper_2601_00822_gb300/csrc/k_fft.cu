@@ -31,7 +31,7 @@ template <int L> struct XCfg {
 __device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
 
 template <typename R, int L>
-__global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : 0) k_xpass(XArgs<R> a) {
+__global__ void __launch_bounds__(XCfg<L>::THREADS, sizeof(R) == 4 ? 5 : std::is_same<R, ff>::value ? 3 : 0) k_xpass(XArgs<R> a) {
   const int m = blockIdx.z;
   if (a.st != nullptr && a.st[m].done) return;   // a member that has converged skips
   using C = XCfg<L>;
