@@ -398,7 +398,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f32x2", "data": "synthetic",
         "config": config_dict(p, args, world),
         "solves_per_s": solves / secs,
         "sweeps_per_solve": sweeps / args.steps,
