@@ -338,6 +338,38 @@ __device__ __forceinline__ void stage1f(C2<R>* x, int n2, const C2<R>* __restric
     }
   }
 }
+// Twiddle, then DFT: x[k1] *= W_L^(DIR-conjugated n2 k1), then DFT_R1 over k1.  The
+// second step of an inverse (or forward) transform taken in the other order of the
+// four-step rule: with k = k1 + R1 k2 and n = R2 n1 + n2, a first in-place step
+// Y[k1][n2] = DFT_R2 over k2 of X[k1 + R1 k2] (rows k1 + R1 m read and written),
+// then for each n2 this step on Y[k1][n2] (k1 = 0..R1-1) gives x[R2 n1 + n2].
+template <typename R, int L, int R1, int DIR>
+__device__ __forceinline__ void twiddle_then_dft(C2<R>* x, int n2, const C2<R>* __restrict__ tw) {
+  if constexpr (R1 % 4 == 0 && R1 >= 8 && sizeof(R) <= 8 && !std::is_same<R, ff>::value) {
+    constexpr int A = R1 / 4;
+    C2<R> wb[4], wa[A];
+#pragma unroll
+    for (int b = 1; b < 4; ++b) wb[b] = tw[(n2 * b) % L];
+#pragma unroll
+    for (int a = 1; a < A; ++a) wa[a] = tw[(n2 * 4 * a) % L];
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      const int a = k1 / 4, b = k1 % 4;
+      C2<R> w = a == 0 ? wb[b] : b == 0 ? wa[a] : cmul(wa[a], wb[b]);
+      if (DIR > 0) w.y = -w.y;
+      x[k1] = cmul(x[k1], w);
+    }
+  } else {
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      C2<R> w = tw[(n2 * k1) % L];
+      if (DIR > 0) w.y = -w.y;
+      x[k1] = cmul(x[k1], w);
+    }
+  }
+  Dft<R, R1, DIR>::run(x);
+}
+
 template <typename R, int R2, int DIR>
 __device__ __forceinline__ void stage2f(C2<R>* y) {
   Dft<R, R2, DIR>::run(y);

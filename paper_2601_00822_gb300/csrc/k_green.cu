@@ -249,30 +249,28 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
     part[blockIdx.y * gridDim.x + blockIdx.x].num = t;
   }
 
-  // ---- inverse transform along z, stage 2 straight to global
+  // ---- inverse transform along z in the other order of the four-step rule
+  // (k = k1 + R1 k2, z = R2 n1 + n2): an R2-point step over the rows k1 + R1 m of
+  // each column, written back to the same rows (no other thread touches them), then
+  // the twiddled R1-point step over the rows n2 R1 + k1, straight to global memory
   const bool keep = mode != GM_FINAL || ccomp < 3;
-  {
-    C2<R> x[R1];
-    if (j < R2) {
-#pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) x[n1] = s[(R2 * n1 + j) * NCOL + gslot(R2 * n1 + j, c)];
-      stage1<R, L, +1>(x, j, a.tw);
-    }
-    __syncthreads();
-    if (j < R2) {
-#pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + gslot(j * R1 + k1, c)] = x[k1];
-    }
-  }
-  __syncthreads();
   if (j < R1) {
     C2<R> y[R2];
 #pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + gslot(n2 * R1 + j, c)];
-    stage2<R, L, +1>(y);
+    for (int k2 = 0; k2 < R2; ++k2) y[k2] = s[(j + R1 * k2) * NCOL + gslot(j + R1 * k2, c)];
+    Dft<R, R2, +1>::run(y);
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) s[(j + R1 * n2) * NCOL + gslot(j + R1 * n2, c)] = y[n2];
+  }
+  __syncthreads();
+  if (j < R2) {
+    C2<R> x[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) x[k1] = s[(j * R1 + k1) * NCOL + gslot(j * R1 + k1, c)];
+    twiddle_then_dft<R, L, R1, +1>(x, j, a.tw);
     if (cvalid && keep) {
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) gcol[(j + R1 * k2) * zs] = y[k2];
+      for (int n1 = 0; n1 < R1; ++n1) gcol[(R2 * n1 + j) * zs] = x[n1];
     }
   }
 }
@@ -406,31 +404,28 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, 1)
     __syncthreads();
     acc += (double)green_tile<R, L>(a, s, pre, col0, ky, GM_SWEEP, dprev, stm, Em);
     __syncthreads();
-    // inverse z transform; stage 2 stores straight to global
-    {
-      C2<R> x[R1];
-      if (j < R2) {
-#pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) x[n1] = s[(R2 * n1 + j) * NCOL + gslot(R2 * n1 + j, c)];
-        stage1<R, L, +1>(x, j, a.tw);
-      }
-      __syncthreads();
-      if (j < R2) {
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * NCOL + gslot(j * R1 + k1, c)] = x[k1];
-      }
-    }
-    __syncthreads();
+    // inverse z transform in the order of the one-tile-per-block form (the same
+    // arithmetic, so the two forms give identical fields): in-place R2-point step,
+    // then the twiddled R1-point step straight to global memory
     if (j < R1) {
       C2<R> y[R2];
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + gslot(n2 * R1 + j, c)];
-      stage2<R, L, +1>(y);
+      for (int k2 = 0; k2 < R2; ++k2) y[k2] = s[(j + R1 * k2) * NCOL + gslot(j + R1 * k2, c)];
+      Dft<R, R2, +1>::run(y);
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) s[(j + R1 * n2) * NCOL + gslot(j + R1 * n2, c)] = y[n2];
+    }
+    __syncthreads();
+    if (j < R2) {
+      C2<R> x[R1];
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) x[k1] = s[(j * R1 + k1) * NCOL + gslot(j * R1 + k1, c)];
+      twiddle_then_dft<R, L, R1, +1>(x, j, a.tw);
       const int kx = col0 + ccol;
       if (kx < a.g.mx) {
         C2<R>* gcol = a.spec + m * a.spec_ms + ccomp * cs + (long long)ky * p + kx;
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) gcol[(j + R1 * k2) * zs] = y[k2];
+        for (int n1 = 0; n1 < R1; ++n1) gcol[(R2 * n1 + j) * zs] = x[n1];
       }
     }
     __syncthreads();   // buffer `cur` is free for the prefetch after next
