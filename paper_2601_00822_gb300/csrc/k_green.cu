@@ -29,6 +29,9 @@ constexpr int kGreenT = 4;   // kx columns per block; 6 components -> 24 line co
 template <int L> struct GCfg {
   static constexpr int NCOL = 6 * kGreenT;
   static constexpr int THREADS = NCOL * LineInfo<L>::RMAX;
+  // block size of the z pass: whole warps (the full-mask shuffles of the residual
+  // reduction need them); threads past THREADS take no FFT task
+  static constexpr int BLOCK = (THREADS + 31) / 32 * 32;
 };
 
 // Shared-memory slot of line-column c in tile row `row`: rows with bit 1 set
@@ -106,9 +109,9 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
       continue;
     }
     const bool load = mode != GM_APPLY;
-    const C2<R> bh0 = load ? pm[0] : mk<R>(0, 0), bh1 = load ? pm[L * T] : mk<R>(0, 0),
-                bh2 = load ? pm[2 * L * T] : mk<R>(0, 0);
+    C2<R> bh0 = mk<R>(0, 0), bh1 = mk<R>(0, 0), bh2 = mk<R>(0, 0);
     C2<R> dp[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+    if (load) { bh0 = pm[0]; bh1 = pm[L * T]; bh2 = pm[2 * L * T]; }
     if (mode == GM_SWEEP || mode == GM_FINAL) { dp[0] = pm[3 * L * T]; dp[1] = pm[4 * L * T]; dp[2] = pm[5 * L * T]; }
 
     C2<R> d[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
@@ -157,8 +160,11 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
   return acc;
 }
 
+// Each FFT stage is a loop over its (line column c, row group j) tasks; with the
+// block of GCfg<L>::BLOCK threads every thread takes at most one.  The b_hat and
+// d_prev tiles are staged in shared memory while the forward transform runs.
 template <typename R, int L>
-__global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zgreen(GArgs<R> a) {
+__global__ void __launch_bounds__(GCfg<L>::BLOCK, sizeof(R) == 4 ? 2 : 1) k_zgreen(GArgs<R> a) {
   const int mbr = blockIdx.z;
   if (a.skip_done && a.st[mbr].done) return;     // a member that has converged skips
   // this member's buffers and mean strain
@@ -171,25 +177,22 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
   constexpr int T = kGreenT;
   constexpr int NCOL = GCfg<L>::NCOL;
   constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
+  constexpr int TASKS = NCOL * LineInfo<L>::RMAX;   // (column, row group) tasks of a stage
   extern __shared__ unsigned char smem_raw[];
   C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);      // [n][c], c = component * T + column
   C2<R>* pre = s + L * NCOL;                          // [6][n][col]: b_hat 0..2, d_prev 3..5
   __shared__ double red[32];
 
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int nx = a.g.nx, ny = a.g.ny, mx = a.g.mx, p = a.g.p;
+  const int ny = a.g.ny, mx = a.g.mx, p = a.g.p;
   const long long cs = a.g.cs;
   const int ky = blockIdx.y;
   const int col0 = blockIdx.x * T;
   const long long zs = (long long)ny * p;          // z stride
   const long long rowbase = (long long)ky * p;
   const int mode = a.mode;
-  // line-column owned by this thread in the FFT stages
-  const int c = tid % NCOL, j = tid / NCOL;
-  const int ccomp = c / T, ccol = c - ccomp * T;
-  const int ckx = col0 + ccol;
-  const bool cvalid = ckx < mx;
-  C2<R>* gcol = spec + ccomp * cs + rowbase + ckx;    // element z of this column at gcol[z * zs]
+  // element z of line column c at column(c)[z * zs]
+  auto column = [&](int c) { const int q = c / T; return spec + q * cs + rowbase + col0 + (c - q * T); };
 
   // ---- start the copies of the b_hat and d_prev tiles; they land during the FFT
   {
@@ -207,7 +210,11 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
 
   // ---- forward transform along z: stage 1 straight from global
   if (mode != GM_INIT) {
-    if (j < R2) {
+    for (int task = tid; task < TASKS; task += nthr) {
+      const int c = task % NCOL, j = task / NCOL;
+      if (j >= R2) continue;
+      const bool cvalid = col0 + (c % T) < mx;
+      const C2<R>* gcol = column(c);
       C2<R> x[R1];
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) x[n1] = cvalid ? gcol[(R2 * n1 + j) * zs] : mk<R>(0, 0);
@@ -217,8 +224,10 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
     }
     __syncthreads();
     // stage 2 reads and writes the same slots (rows j + R1 m, m < R2, of column c):
-    // no other thread touches them, so no barrier separates the read and the write
-    if (j < R1) {
+    // no other task touches them, so no barrier separates the read and the write
+    for (int task = tid; task < TASKS; task += nthr) {
+      const int c = task % NCOL, j = task / NCOL;
+      if (j >= R1) continue;
       C2<R> y[R2];
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * NCOL + gslot(n2 * R1 + j, c)];
@@ -251,10 +260,11 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
 
   // ---- inverse transform along z in the other order of the four-step rule
   // (k = k1 + R1 k2, z = R2 n1 + n2): an R2-point step over the rows k1 + R1 m of
-  // each column, written back to the same rows (no other thread touches them), then
+  // each column, written back to the same rows (no other task touches them), then
   // the twiddled R1-point step over the rows n2 R1 + k1, straight to global memory
-  const bool keep = mode != GM_FINAL || ccomp < 3;
-  if (j < R1) {
+  for (int task = tid; task < TASKS; task += nthr) {
+    const int c = task % NCOL, j = task / NCOL;
+    if (j >= R1) continue;
     C2<R> y[R2];
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) y[k2] = s[(j + R1 * k2) * NCOL + gslot(j + R1 * k2, c)];
@@ -263,12 +273,16 @@ __global__ void __launch_bounds__(GCfg<L>::THREADS, sizeof(R) == 4 ? 2 : 1) k_zg
     for (int n2 = 0; n2 < R2; ++n2) s[(j + R1 * n2) * NCOL + gslot(j + R1 * n2, c)] = y[n2];
   }
   __syncthreads();
-  if (j < R2) {
+  for (int task = tid; task < TASKS; task += nthr) {
+    const int c = task % NCOL, j = task / NCOL;
+    if (j >= R2) continue;
+    const bool keep = (mode != GM_FINAL || c / T < 3) && col0 + (c % T) < mx;
     C2<R> x[R1];
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) x[k1] = s[(j * R1 + k1) * NCOL + gslot(j * R1 + k1, c)];
     twiddle_then_dft<R, L, R1, +1>(x, j, a.tw);
-    if (cvalid && keep) {
+    if (keep) {
+      C2<R>* gcol = column(c);
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) gcol[(R2 * n1 + j) * zs] = x[n1];
     }
@@ -597,7 +611,7 @@ static cudaError_t zgreen_L(const GArgs<R>& a, int batch, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_zgreen<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_zgreen<R, L><<<grid, GCfg<L>::THREADS, smem, st>>>(a);
+  k_zgreen<R, L><<<grid, GCfg<L>::BLOCK, smem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
