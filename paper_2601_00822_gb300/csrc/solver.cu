@@ -1213,7 +1213,8 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
       any_warm = true;
     }
     const auto sh = shift_of(m);
-    mem.push_back(make_member(in[m].phase, sh.data(), in[m].E, nullptr, init, SolveOut{eps32(m), nullptr, u32(m)}));
+    // the ladder carries the FP32 phases' displacement only: their strain is not written
+    mem.push_back(make_member(in[m].phase, sh.data(), in[m].E, nullptr, init, SolveOut{nullptr, nullptr, u32(m)}));
   }
   CK(launch_bden<float>(bhat32, g, P->part, P->ist, st, B, 3 * cs));
   e = upload_members(P, B, mem.data());
@@ -1262,7 +1263,7 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
         CK(cudaMemcpyAsync(bhat32 + (size_t)j * 3 * cs, bhat32 + (size_t)m * 3 * cs, 3 * cs * sizeof(C2<float>),
                            cudaMemcpyDeviceToDevice, st));
       const auto sh = shift_of(m);
-      Member c = make_member(in[m].phase, sh.data(), zeroE, nullptr, nullptr, SolveOut{eps32(j), nullptr, u32(j)});
+      Member c = make_member(in[m].phase, sh.data(), zeroE, nullptr, nullptr, SolveOut{nullptr, nullptr, u32(j)});
       c.tol = std::min(0.5, std::max(0.5 * tol / r64[m], P->switch_tol));   // well above the FP32 floor
       mem.push_back(c);
       left = std::min(left, maxit - sweeps[m]);
