@@ -212,6 +212,14 @@ template <typename R, int RADIX, int DIR> struct Dft {
       for (int k1 = 1; k1 < A; ++k1) {
         if (n2 * k1 == 0) continue;
         constexpr int S = 48 / RADIX;
+        const int j = (S * n2 * k1) % 48;
+        if (j % 12 == 0) {
+          // exp(DIR i pi j / 24) is DIR i, -1 or -DIR i: an exact rotation (a
+          // product by the constants 0 and 1 is not folded without fast math)
+          const C2<R> v = u[n2][k1];
+          u[n2][k1] = j == 12 ? mul_di<R, DIR>(v) : j == 24 ? mk<R>(-v.x, -v.y) : mul_di<R, -DIR>(v);
+          continue;
+        }
         const C2<R> w = mk<R>(R(cos48(S * n2 * k1)), R(DIR * sin48(S * n2 * k1)));
         u[n2][k1] = cmul(u[n2][k1], w);
       }

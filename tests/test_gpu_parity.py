@@ -46,6 +46,11 @@ CASES = {
                                      phases=((1.0, 0.5), (6.0, 3.0), (0.5, 0.3))),
     "aniso_12x32x24": small_problem((12, 32, 24), (12, 16, 12), [[12, 16, 12, 49, 1]], (6.0, 16.0, 12.0), 4.5,
                                     E=(0.01, -0.004, 0.002, 0.001, -0.003, 0.005)),
+    # nz = 6 and 4: the z pass's 24 RMAX threads (72, 48) are rounded up to whole
+    # warps, which its residual reduction needs; the history checks the residuals
+    "thin_16x12x6": small_problem((16, 12, 6), (8, 12, 6), [[8, 12, 6, 16, 1]], (8.0, 6.0, 3.0), 2.5,
+                                  E=(0.002, 0.0, -0.001, 0.0, 0.0, 0.003)),
+    "thin_8x8x4": small_problem((8, 8, 4), (8, 8, 4), [[8, 8, 4, 12, 1]], (4.0, 4.0, 2.0), 1.8),
 }
 
 
