@@ -1,8 +1,9 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case plants one mistake (a dropped factor, a flipped sign, a wrong index
-or convention) into a temporary copy of the oracle and runs the pin suite
-against that copy in a subprocess; at least one pin must fail.  The real
+or convention) into a temporary copy of the oracle and runs the pin suite and
+the hand-derived golden values against that copy in a subprocess; at least one
+of them must fail.  The real
 oracle is never modified.
 """
 import os
@@ -65,9 +66,12 @@ def run_pins(tmp_path, src):
     (tmp_path / "oracle" / "bfcs_oracle.py").write_text(src)
     (tmp_path / "tests").mkdir()
     shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "tests")
+    shutil.copy(os.path.join(ROOT, "tests", "test_golden.py"), tmp_path / "tests")
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "tests" / "golden")
     env = dict(os.environ, PYTHONPATH=str(tmp_path))
-    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                           "tests/test_oracle_pins.py"], cwd=tmp_path, env=env,
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                           "-W", "ignore::pytest.PytestUnknownMarkWarning",
+                           "tests/test_oracle_pins.py", "tests/test_golden.py"], cwd=tmp_path, env=env,
                           capture_output=True, text=True, timeout=600)
 
 
