@@ -677,7 +677,8 @@ int run_sets(std::vector<SweepSet<R>*>& sets, int maxit) {
   while (s < maxit) {
     int c;
     if (gexec != nullptr && maxit - s >= G) {
-      c = G * std::max(1, chunk / G);
+      // whole graphs, never past maxit (the remainder runs as single sweeps)
+      c = G * std::max(1, std::min(chunk, maxit - s) / G);
       for (int k = 0; k < c; k += G) CK(cudaGraphLaunch(gexec, main));
     } else {
       c = std::min(chunk, maxit - s);

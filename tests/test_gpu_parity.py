@@ -124,6 +124,19 @@ def test_fixed_sweeps_parity(name, precision):
     assert np.all(np.abs(hist - h_ref) <= 1e-4 * h_ref + (1e-12 if precision == "fp64" else 1e-6))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("sweeps", [30, 45])
+def test_sweep_count_stops_at_maxit_with_sweep_graphs(precision, sweeps):
+    """A solve that ends at maxit runs exactly maxit sweeps when the sweeps are
+    launched as 8-sweep CUDA graphs and maxit is not a multiple of 8 (the growing
+    chunks of graph launches are cut at maxit), and matches the oracle there."""
+    p = CASES["c1_32cubed"]
+    ref, (eps, sig, u, info, hist) = run_pair(p, precision, sweeps=sweeps)
+    assert info.iters == ref["sweeps"] == sweeps and len(hist) == sweeps
+    t = TOL[precision]
+    assert rel(eps, ref["eps"]) < t and rel(sig, ref["sig"]) < t and rel(u, ref["u"]) < t
+
+
 def test_converged_fp64_config1():
     p = W.config_c1()
     ref, (eps, sig, u, info, hist) = run_pair(p, "fp64", sweeps=p.maxit, tol=p.tol)
