@@ -144,7 +144,7 @@ def warm_start_benchmark(params, seeds, n, tol=1e-6, maxit=20000, batch=64, plai
     """Solves/s to residual tol of the same problems (mixed-precision ladder):
     plain (one cold solve at a time), batched cold, batched with the network's
     warm start (inference included in the timing).  The warm results are
-    judged against the cold solver's: relative L2 of eps."""
+    compared with the cold solver's: relative L2 of eps."""
     phases, c0 = material()
     dims = (n, n, n)
     inputs = [sample_inputs(s, n, "fp64") for s in seeds]

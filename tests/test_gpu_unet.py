@@ -162,7 +162,7 @@ def test_trained_warm_start_reduces_sweeps_and_matches_cold_solver():
     training seeds start at 1000000): its prediction is within 35% relative L2 of
     the solution, the warm-started batched ladder needs fewer FP32 sweeps than
     the cold one, and both land within the tolerance of each other (the cold
-    solver is the judge)."""
+    solver is the reference)."""
     from paper_2601_00822_gb300 import surrogate as S
     params = S.load(S.DEFAULT_WEIGHTS)
     res = S.warm_start_benchmark(params, list(range(8)), 64, tol=1e-6, batch=8, plain=False)
