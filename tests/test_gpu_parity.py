@@ -51,6 +51,9 @@ CASES = {
     "thin_16x12x6": small_problem((16, 12, 6), (8, 12, 6), [[8, 12, 6, 16, 1]], (8.0, 6.0, 3.0), 2.5,
                                   E=(0.002, 0.0, -0.001, 0.0, 0.0, 0.003)),
     "thin_8x8x4": small_problem((8, 8, 4), (8, 8, 4), [[8, 8, 4, 12, 1]], (4.0, 4.0, 2.0), 1.8),
+    # line lengths 128 (x), 6 (y) and 192 (z) in one solve
+    "long_128x6x192": small_problem((128, 6, 192), (64, 6, 96), [[64, 6, 96, 36, 1], [10, 2, 40, 16, 1]],
+                                    (64.0, 3.0, 96.0), 2.8, E=(0.0, 0.001, 0.0, 0.0, 0.002, 0.0)),
 }
 
 
@@ -81,7 +84,8 @@ def test_body_force(name, precision):
 
 # ---------------------------------------------------------------- a5, a7 transforms
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("dims", [(32, 32, 32), (48, 24, 96), (12, 32, 24), (256, 8, 6)])
+@pytest.mark.parametrize("dims", [(32, 32, 32), (48, 24, 96), (12, 32, 24), (256, 8, 6),
+                                  (192, 6, 128), (6, 128, 192), (128, 192, 6)])
 def test_fft3d_against_oracle_transform(dims, precision):
     nx, ny, nz = dims
     r = np.random.default_rng(5)
