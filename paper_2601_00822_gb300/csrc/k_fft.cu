@@ -239,8 +239,10 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, xpass_min_blocks<R>()) k_xpa
   const R half = R(0.5) * ((mode == XM_R2C && a.out_scale != R(0)) ? a.out_scale : R(1));
   C2<R>* rowA = a.spec_out + m * a.spec_ms + (2 * q) * cs + line * p;
   C2<R>* rowB = rowA + cs;
+  // only the outputs k <= H are stored: k = t + R1 k2 with t < R1 needs k2 <= H / R1
+  constexpr int K2MAX = H / R1 + 1 < R2 ? H / R1 + 1 : R2;
 #pragma unroll
-  for (int k2 = 0; k2 < R2; ++k2) {
+  for (int k2 = 0; k2 < K2MAX; ++k2) {
     const C2<R> send = (t == 0) ? y[(R2 - k2) % R2] : y[(R2 - 1 - k2 + R2) % R2];
     C2<R> zm;
     zm.x = shfl_real<R>(send.x, src);
