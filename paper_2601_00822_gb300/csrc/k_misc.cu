@@ -85,18 +85,35 @@ cudaError_t launch_voxelize(int8_t* out, int nx, int ny, int nz, int cx, int cy,
   return cudaGetLastError();
 }
 
+// voxel (x, y, z) of linear index v = x + nx (y + ny z): 32-bit unsigned
+// arithmetic when the grid has fewer than 2^32 voxels (`small`), else 64-bit
+__device__ __forceinline__ void lin_xyz(long long v, int nx, int ny, bool small, int& x, int& y, int& z) {
+  if (small) {
+    const unsigned u = (unsigned)v, t = u / (unsigned)nx;
+    x = (int)(u - t * (unsigned)nx);
+    y = (int)(t % (unsigned)ny);
+    z = (int)(t / (unsigned)ny);
+  } else {
+    x = (int)(v % nx);
+    y = (int)((v / nx) % ny);
+    z = (int)(v / ((long long)nx * ny));
+  }
+}
+
 // ---------------------------------------------------------------- a2: body force
 // b1 = d phi/d x1, phi = (1 - r^2/a^2)^3 for r < a (Eq. 2.5 form), at voxel
 // centres i + 0.5, periodic minimum image about the centre; FP64, mean removed.
-__device__ __forceinline__ double bf_value(long long v, int nx, int ny, int nz, double cx, double cy,
-                                           double cz, double a) {
-  const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+// rn = (1/nx, 1/ny, 1/nz) in FP32 for the screen: a product and a quotient can
+// round differently only at offsets of exactly half a period, where both images
+// are equally far, so the screen's decision is the same.
+__device__ __forceinline__ double bf_value(int x, int y, int z, int nx, int ny, int nz, float3 rn, double cx,
+                                           double cy, double cz, double a) {
   {
     // cheap FP32 screen: voxels clearly outside the support (beyond a + 1 voxel) are 0
     float fx = (float)x + 0.5f - (float)cx, fy = (float)y + 0.5f - (float)cy, fz = (float)z + 0.5f - (float)cz;
-    fx -= (float)nx * rintf(fx / (float)nx);
-    fy -= (float)ny * rintf(fy / (float)ny);
-    fz -= (float)nz * rintf(fz / (float)nz);
+    fx -= (float)nx * rintf(fx * rn.x);
+    fy -= (float)ny * rintf(fy * rn.y);
+    fz -= (float)nz * rintf(fz * rn.z);
     const float lim = (float)a + 1.0f;
     if (fabsf(fx) > lim || fabsf(fy) > lim || fabsf(fz) > lim) return 0.0;
   }
@@ -116,9 +133,14 @@ __global__ void k_bf_partial(double* part, long long n, int nx, int ny, int nz, 
                              double cz, double a) {
   __shared__ double red[32];
   double acc = 0.0;
+  const bool small = n <= 0xFFFFFFFFLL;
+  const float3 rn = make_float3(1.0f / (float)nx, 1.0f / (float)ny, 1.0f / (float)nz);
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (long long)gridDim.x * blockDim.x)
-    acc += bf_value(v, nx, ny, nz, cx, cy, cz, a);
+       v += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    lin_xyz(v, nx, ny, small, x, y, z);
+    acc += bf_value(x, y, z, nx, ny, nz, rn, cx, cy, cz, a);
+  }
   const double t = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
@@ -135,9 +157,13 @@ template <typename R>
 __global__ void k_bf_write(R* b, long long n, int nx, int ny, int nz, double cx, double cy, double cz,
                            double a, const double* mean) {
   const double m = *mean;
+  const bool small = n <= 0xFFFFFFFFLL;
+  const float3 rn = make_float3(1.0f / (float)nx, 1.0f / (float)ny, 1.0f / (float)nz);
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
-    b[v] = (R)(bf_value(v, nx, ny, nz, cx, cy, cz, a) - m);
+    int x, y, z;
+    lin_xyz(v, nx, ny, small, x, y, z);
+    b[v] = (R)(bf_value(x, y, z, nx, ny, nz, rn, cx, cy, cz, a) - m);
     b[n + v] = R(0);
     b[2 * n + v] = R(0);
   }
@@ -390,12 +416,16 @@ template <typename R>
 __global__ void k_accumulate(double* acc, int* hits, const R* eps, const R* sig, const R* u,
                              const int8_t* phase, int sx, int sy, int sz, int nx, int ny, int nz) {
   const long long n = (long long)nx * ny * nz;
+  const bool small = n <= 0xFFFFFFFFLL;
+  // shifts reduced to [0, n) once: the per-voxel translation is then one compare
+  const int sxr = ((sx % nx) + nx) % nx, syr = ((sy % ny) + ny) % ny, szr = ((sz % nz) + nz) % nz;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-    int xs = (x - sx) % nx; if (xs < 0) xs += nx;
-    int ys = (y - sy) % ny; if (ys < 0) ys += ny;
-    int zs = (z - sz) % nz; if (zs < 0) zs += nz;
+    int x, y, z;
+    lin_xyz(v, nx, ny, small, x, y, z);
+    int xs = x - sxr; if (xs < 0) xs += nx;
+    int ys = y - syr; if (ys < 0) ys += ny;
+    int zs = z - szr; if (zs < 0) zs += nz;
     const bool in = phase[((long long)zs * ny + ys) * nx + xs] != 0;
     for (int c = 0; c < 3; ++c) {
       const double val = (double)u[c * n + v];
@@ -620,12 +650,16 @@ cudaError_t launch_cast_spec_ff(C2<float>* dst, const C2<ff>* src, const Geo& g,
 __global__ void k_stress(double* sig, const double* eps, const int8_t* phase, PhaseTab<double> tab, int sx,
                          int sy, int sz, int nx, int ny, int nz) {
   const long long n = (long long)nx * ny * nz;
+  const bool small = n <= 0xFFFFFFFFLL;
+  // shifts reduced to [0, n) once: the per-voxel translation is then one compare
+  const int sxr = ((sx % nx) + nx) % nx, syr = ((sy % ny) + ny) % ny, szr = ((sz % nz) + nz) % nz;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
-    int xs = (x - sx) % nx; if (xs < 0) xs += nx;
-    int ys = (y - sy) % ny; if (ys < 0) ys += ny;
-    int zs = (z - sz) % nz; if (zs < 0) zs += nz;
+    int x, y, z;
+    lin_xyz(v, nx, ny, small, x, y, z);
+    int xs = x - sxr; if (xs < 0) xs += nx;
+    int ys = y - syr; if (ys < 0) ys += ny;
+    int zs = z - szr; if (zs < 0) zs += nz;
     const int ph = phase[((long long)zs * ny + ys) * nx + xs];
     const double e0 = eps[v], e1 = eps[n + v], e2 = eps[2 * n + v];
     const double lt = tab.lam[ph] * (e0 + e1 + e2), m2 = 2.0 * tab.mu[ph];
