@@ -22,7 +22,9 @@
  *    the plan precision: float for BFCS_FP32, double for BFCS_FP64.
  *  - Streams: all device work of a plan is ordered on the plan's stream.  The
  *    solve calls return when their results are written (they wait on the stream
- *    with a bounded host-side wait; an expired wait returns BFCS_ERR_TIMEOUT).
+ *    with a bounded host-side wait; an expired wait returns BFCS_ERR_TIMEOUT.
+ *    The bound is 900 s, or the number of seconds in the environment variable
+ *    BFCS_WAIT_TIMEOUT_S).
  *  - Status: 0 = OK, > 0 = completed with a warning, < 0 = error (see below).
  *    On error the output buffers are unspecified.
  *  - Wavevector (where the paper writes F(grad f) = i k f_hat, Eq. 4.8):
