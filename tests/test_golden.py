@@ -67,6 +67,14 @@ def test_oracle_bfcs_field_is_the_hand_evaluation_of_eq_2_5():
     assert np.array_equal(b, golden_field())
 
 
+def test_oracle_bfcs_field_wraps_periodically():
+    """The same load centred at the grid corner: every offset beyond half a
+    period wraps to its minimum image, so the field is the fixture rolled by two
+    voxels along each axis (voxel i sits where voxel (i + 2) mod 4 sat)."""
+    b = O.body_force((4, 4, 4), (0.0, 0.0, 0.0), 2.0)
+    assert np.array_equal(b, np.roll(golden_field(), 2, axis=(1, 2, 3)))
+
+
 def test_oracle_u0_is_the_hand_evaluation_of_eqs_2_16_2_18():
     for r in rows("green_u0_isotropic.txt"):
         lam0, mu0 = num(r[0]), num(r[1])
@@ -99,6 +107,9 @@ def test_gpu_bfcs_field_is_the_hand_evaluation_of_eq_2_5(precision):
         assert np.array_equal(b, want)
     else:       # k/1024 with |k| < 2^10 is exact in binary32 too
         assert np.array_equal(b.astype(np.float64), want)
+    # centred at the grid corner: the minimum images wrap around the period
+    bc = api.body_force((4, 4, 4), (0.0, 0.0, 0.0), 2.0, precision).cpu().numpy().astype(np.float64)
+    assert np.array_equal(bc, np.roll(want, 2, axis=(1, 2, 3)))
 
 
 @pytest.mark.gpu

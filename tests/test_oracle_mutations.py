@@ -35,6 +35,9 @@ MUTATIONS = {
     "green_U2_dropped": ("u2 = P[i][j] * P[k][l]", "u2 = 0.0"),
     "average_normalisation": ("return acc / m, hits, infos", "return acc / (m + 1), hits, infos"),
     "body_force_sign": ("-6.0 * x * s * s / (a * a)", "6.0 * x * s * s / (a * a)"),
+    "body_force_power": ("-6.0 * x * s * s / (a * a)", "-6.0 * x * s / (a * a)"),
+    "body_force_without_minimum_image": ("        return d - n * np.round(d / n)", "        return d"),
+    "green_U1_coefficient": ("c1 = 1.0 / (4.0 * mu0)", "c1 = 1.0 / (2.0 * mu0)"),
     "sphere_boundary_exclusive": ("ph[d2 <= T] = p", "ph[d2 < T] = p"),
     "residual_misses_load": ("div = div_hat(sig_hat, xi) + b_hat", "div = div_hat(sig_hat, xi)"),
     "moduli_engineering_shear": ("    E[J] = 1.0\n", "    E[J] = 1.0 if J < 3 else 0.5\n"),
