@@ -38,6 +38,11 @@ MUTATIONS = {
     "body_force_power": ("-6.0 * x * s * s / (a * a)", "-6.0 * x * s / (a * a)"),
     "body_force_without_minimum_image": ("        return d - n * np.round(d / n)", "        return d"),
     "green_U1_coefficient": ("c1 = 1.0 / (4.0 * mu0)", "c1 = 1.0 / (2.0 * mu0)"),
+    "residual_normaliser_shear_once": ("2.0 * np.sum(np.abs(s0[3:]) ** 2)", "np.sum(np.abs(s0[3:]) ** 2)"),
+    "residual_xi_min_of_shortest_edge": ("2.0 * np.pi / max(dims) * s0n", "2.0 * np.pi / min(dims) * s0n"),
+    "wavevector_of_the_x_edge": ("        out.append(2.0 * np.pi * k / n)", "        out.append(2.0 * np.pi * k / dims[0])"),
+    "phase_map_without_minimum_image": ("        return np.where(d >= n, d - 2 * n, d)", "        return d"),
+    "initial_strain_zero": ('        eps = _real(eb0_hat, "eps0")', '        eps = np.zeros_like(_real(eb0_hat, "eps0"))'),
     "sphere_boundary_exclusive": ("ph[d2 <= T] = p", "ph[d2 < T] = p"),
     "residual_misses_load": ("div = div_hat(sig_hat, xi) + b_hat", "div = div_hat(sig_hat, xi)"),
     "moduli_engineering_shear": ("    E[J] = 1.0\n", "    E[J] = 1.0 if J < 3 else 0.5\n"),

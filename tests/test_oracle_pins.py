@@ -461,6 +461,26 @@ def test_translate_average_invariants():
     assert np.allclose(avg2[18:24], one["sig"], atol=1e-14)
 
 
+def test_residual_normaliser_closed_form():
+    """Reading R4 of Eq. 5.11 on a field whose residual is known by hand: a
+    homogeneous medium (mu = 1/2) under the uniform pure shear eps_xy = 0.05, so
+    sigma_xy = 0.05 everywhere and its divergence vanishes, with the load
+    b_x = cos(2 pi x / nx).  On the 8 x 4 x 2 grid (N = 64) the numerator is
+    |b_hat| = N / sqrt(2) (two modes of modulus N / 2); the normaliser adds
+    xi_min |sigma_hat(0)|_F with xi_min = 2 pi / 8 (the largest edge) and
+    |sigma_hat(0)|_F = N 0.05 sqrt(2) (the shear counted in both off-diagonal
+    entries).  Hence r = 1 / (1 + pi / 40)."""
+    dims = (8, 4, 2)
+    nx, ny, nz = dims
+    phase = np.zeros((nz, ny, nx), dtype=np.int8)
+    eps = np.zeros((6, nz, ny, nx))
+    eps[5] = 0.05
+    b = np.zeros((3, nz, ny, nx))
+    b[0] = np.cos(2 * np.pi * np.arange(nx) / nx)[None, None, :]
+    r = O.residual(phase, [(1.0, 0.5)], eps, O.fft3(b), O.wavevectors(dims))
+    assert r == pytest.approx(1.0 / (1.0 + math.pi / 40.0), rel=1e-14)
+
+
 def test_residual_decreases_and_parseval():
     dims, phase, table, c0 = _c1_small()
     b = O.body_force(dims, (8.0, 8.0, 8.0), 5.0)
