@@ -43,6 +43,13 @@ MUTATIONS = {
     "wavevector_of_the_x_edge": ("        out.append(2.0 * np.pi * k / n)", "        out.append(2.0 * np.pi * k / dims[0])"),
     "phase_map_without_minimum_image": ("        return np.where(d >= n, d - 2 * n, d)", "        return d"),
     "initial_strain_zero": ('        eps = _real(eb0_hat, "eps0")', '        eps = np.zeros_like(_real(eb0_hat, "eps0"))'),
+    "kernel_gradient_without_tikhonov": ("grad = 2.0 * (G @ c - g + lam * c)", "grad = 2.0 * (G @ c - g)"),
+    "kernel_loss_without_constant": ("J = float(c @ G @ c - 2 * g @ c + s + lam * c @ c)",
+                                     "J = float(c @ G @ c - 2 * g @ c + lam * c @ c)"),
+    "kernel_radius_unscaled": ("K = coef @ bernstein(coef.size - 1, d / delta)", "K = coef @ bernstein(coef.size - 1, d)"),
+    "concentration_over_matrix": ('As[:, J] = res["eps"][:, incl].mean(axis=1)',
+                                  'As[:, J] = res["eps"][:, ~incl].mean(axis=1)'),
+    "adam_second_moment_without_bias_correction": ("vh = v / (1 - betas[1] ** t)", "vh = v"),
     "sphere_boundary_exclusive": ("ph[d2 <= T] = p", "ph[d2 < T] = p"),
     "residual_misses_load": ("div = div_hat(sig_hat, xi) + b_hat", "div = div_hat(sig_hat, xi)"),
     "moduli_engineering_shear": ("    E[J] = 1.0\n", "    E[J] = 1.0 if J < 3 else 0.5\n"),

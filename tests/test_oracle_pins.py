@@ -789,6 +789,25 @@ def test_kernel_fit_recovers_a_planted_kernel_and_shrinks_with_tikhonov():
     assert all(a > b for a, b in zip(norms, norms[1:]))           # Tikhonov shrinks the coefficients
 
 
+def test_kernel_fit_loss_is_the_direct_sum_and_adam_reaches_the_tikhonov_minimiser():
+    """Eq. 6.6 with Tikhonov weight lam > 0: the reported J equals the sum
+    |L_c[u] - Gamma|^2 + lam |c|^2 evaluated directly with the operator (not
+    through G, g and s), and Adam ends at the minimiser (G + lam I)^-1 g of that
+    regularised J (lam = the mean eigenvalue of G keeps the problem well
+    conditioned)."""
+    nx, ny, nz = 6, 6, 6
+    delta, M = 2.5, 2
+    u = RNG.standard_normal((3, nz, ny, nx))
+    gam = RNG.standard_normal((3, nz, ny, nx))
+    G = O.kernel_fit([u], [gam], delta, M, lam=0.0, iters=1)["G"]
+    lam = float(np.trace(G)) / G.shape[0]
+    fit = O.kernel_fit([u], [gam], delta, M, lam=lam, iters=2000, lr=0.05)
+    c = fit["coef"]
+    direct = float(((O.kernel_operator(u, c, delta) - gam) ** 2).sum()) + lam * float(c @ c)
+    assert fit["loss"] == pytest.approx(direct, rel=1e-12)
+    assert np.allclose(c, fit["exact"], rtol=1e-8, atol=0)
+
+
 def test_kernel_fit_first_adam_step_is_minus_lr_sign_gradient():
     nx, ny, nz = 6, 6, 6
     u = RNG.standard_normal((3, nz, ny, nx))
