@@ -6,6 +6,7 @@ the hand-derived golden values against that copy in a subprocess; at least one
 of them must fail.  The real
 oracle is never modified.
 """
+import concurrent.futures as cf
 import os
 import shutil
 import subprocess
@@ -83,11 +84,29 @@ def run_pins(tmp_path, src):
     shutil.copy(os.path.join(ROOT, "tests", "test_oracle_pins.py"), tmp_path / "tests")
     shutil.copy(os.path.join(ROOT, "tests", "test_golden.py"), tmp_path / "tests")
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "tests" / "golden")
-    env = dict(os.environ, PYTHONPATH=str(tmp_path))
+    # one thread per child: the children run side by side
+    env = dict(os.environ, PYTHONPATH=str(tmp_path), OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1")
     return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
                            "-W", "ignore::pytest.PytestUnknownMarkWarning",
                            "tests/test_oracle_pins.py", "tests/test_golden.py"], cwd=tmp_path, env=env,
-                          capture_output=True, text=True, timeout=600)
+                          capture_output=True, text=True, timeout=900)
+
+
+@pytest.fixture(scope="module")
+def mutated_runs(tmp_path_factory):
+    """Every planted mistake run once, the children concurrently (one per core);
+    the parametrised tests below read their outcomes."""
+    src = open(os.path.join(ROOT, "oracle", "bfcs_oracle.py")).read()
+
+    def one(name):
+        before, after = MUTATIONS[name]
+        if src.count(before) != 1:
+            return name, None
+        return name, run_pins(tmp_path_factory.mktemp(name), src.replace(before, after))
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(ex.map(one, sorted(MUTATIONS)))
 
 
 def test_unmutated_copy_passes(tmp_path):
@@ -97,11 +116,9 @@ def test_unmutated_copy_passes(tmp_path):
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_planted_mistake_is_caught(name, tmp_path):
-    before, after = MUTATIONS[name]
-    src = open(os.path.join(ROOT, "oracle", "bfcs_oracle.py")).read()
-    assert src.count(before) == 1, "mutation anchor drifted"
-    r = run_pins(tmp_path, src.replace(before, after))
+def test_planted_mistake_is_caught(name, mutated_runs):
+    r = mutated_runs[name]
+    assert r is not None, "mutation anchor drifted"
     assert r.returncode != 0, f"planted mistake {name!r} passed every pin:\n{r.stdout[-2000:]}"
     # caught by a failing pin, not by an import or collection error
     assert r.returncode == 1 and " failed" in r.stdout and " error" not in r.stdout, r.stdout[-2000:]
