@@ -51,6 +51,17 @@ MUTATIONS = {
     "concentration_over_matrix": ('As[:, J] = res["eps"][:, incl].mean(axis=1)',
                                   'As[:, J] = res["eps"][:, ~incl].mean(axis=1)'),
     "adam_second_moment_without_bias_correction": ("vh = v / (1 - betas[1] ** t)", "vh = v"),
+    "displacement_without_lame_term": ("lam_tr = lam0 * (eps[0] + eps[1] + eps[2])",
+                                       "lam_tr = 0.0 * (eps[0] + eps[1] + eps[2])"),
+    "g0_projection_sign": ("(v_hat[i] - c * xi[i] * xv * iq) * iq / mu0", "(v_hat[i] + c * xi[i] * xv * iq) * iq / mu0"),
+    "reference_strain_sign": ("return sym_grad_hat(g0_apply(b_hat, xi, lam0, mu0), xi)",
+                              "return -sym_grad_hat(g0_apply(b_hat, xi, lam0, mu0), xi)"),
+    "translation_axes_swapped": ("np.roll(field, (sz, sy, sx), axis=(-3, -2, -1))",
+                                 "np.roll(field, (sx, sy, sz), axis=(-3, -2, -1))"),
+    "residual_over_all_modes": ("act = np.broadcast_to(q > 0, sig_hat.shape[1:])",
+                                "act = np.broadcast_to(q >= 0, sig_hat.shape[1:])"),
+    "stress_of_the_reference_medium": ("    sig = apply_local(phase, table, eps)\n    u = displacement",
+                                       "    sig = apply_local(phase, [c0] * len(table), eps)\n    u = displacement"),
     "sphere_boundary_exclusive": ("ph[d2 <= T] = p", "ph[d2 < T] = p"),
     "residual_misses_load": ("div = div_hat(sig_hat, xi) + b_hat", "div = div_hat(sig_hat, xi)"),
     "moduli_engineering_shear": ("    E[J] = 1.0\n", "    E[J] = 1.0 if J < 3 else 0.5\n"),
