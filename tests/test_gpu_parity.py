@@ -142,12 +142,20 @@ def test_sweep_count_stops_at_maxit_with_sweep_graphs(precision, sweeps):
 
 
 def test_converged_fp64_config1():
+    """Converged C1 in FP64 at the FP64 bar: the GPU solve stops at the tolerance
+    after S sweeps; the oracle run for exactly S sweeps gives the same fields to
+    1e-10 (pure rounding), and the oracle's own stopping rule ends within one
+    sweep of S (the two residuals differ by rounding only near the threshold)."""
     p = W.config_c1()
     ref, (eps, sig, u, info, hist) = run_pair(p, "fp64", sweeps=p.maxit, tol=p.tol)
     assert info.status == _lib.OK and info.resid <= 10 * p.tol
     assert abs(info.iters - ref["sweeps"]) <= 1
+    same = ref
+    if ref["sweeps"] != info.iters:
+        ph_o, b_o = oracle_inputs(p)
+        same = O.solve(ph_o, p.phases, p.c0, b_o, tol=0.0, maxit=info.iters)
     for a, key in ((eps, "eps"), (sig, "sig"), (u, "u")):
-        assert rel(a, ref[key]) < 1e-9, (key, rel(a, ref[key]))
+        assert rel(a, same[key]) < TOL["fp64"], (key, rel(a, same[key]))
 
 
 def test_fp32_converged_error_against_fp64():
