@@ -1634,13 +1634,15 @@ int bfcs_voxelize(int nx, int ny, int nz, int cx, int cy, int cz, int nsph, cons
   }
   cudaStream_t st = (cudaStream_t)stream;
   int* d = nullptr;
+  cudaError_t e = cudaSuccess;
   if (nsph > 0) {
     if (cudaMallocAsync((void**)&d, sizeof(int) * 5 * nsph, st) != cudaSuccess) return BFCS_ERR_OOM;
-    CK(cudaMemcpyAsync(d, spheres, sizeof(int) * 5 * nsph, cudaMemcpyHostToDevice, st));
+    e = cudaMemcpyAsync(d, spheres, sizeof(int) * 5 * nsph, cudaMemcpyHostToDevice, st);
   }
-  CK(launch_voxelize(phase_out, nx, ny, nz, cx, cy, cz, d, nsph, st));
-  if (d != nullptr) CK(cudaFreeAsync(d, st));
-  return BFCS_OK;
+  if (e == cudaSuccess) e = launch_voxelize(phase_out, nx, ny, nz, cx, cy, cz, d, nsph, st);
+  // the sphere table is released on every path, failed launches included
+  if (d != nullptr && cudaFreeAsync(d, st) != cudaSuccess) return BFCS_ERR_CUDA;
+  return e == cudaSuccess ? BFCS_OK : BFCS_ERR_CUDA;
 }
 
 int bfcs_body_force(int nx, int ny, int nz, double cx, double cy, double cz, double a, int precision,
@@ -1657,9 +1659,9 @@ int bfcs_body_force(int nx, int ny, int nz, double cx, double cy, double cz, dou
   cudaError_t e = precision == BFCS_FP64
                       ? launch_body_force<double>((double*)b_out, nx, ny, nz, cx, cy, cz, a, scratch, st)
                       : launch_body_force<float>((float*)b_out, nx, ny, nz, cx, cy, cz, a, scratch, st);
-  if (e != cudaSuccess) return BFCS_ERR_CUDA;
-  CK(cudaFreeAsync(scratch, st));
-  return BFCS_OK;
+  // the scratch is released on every path, a failed launch included
+  if (cudaFreeAsync(scratch, st) != cudaSuccess) return BFCS_ERR_CUDA;
+  return e == cudaSuccess ? BFCS_OK : BFCS_ERR_CUDA;
 }
 
 int bfcs_solve(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
