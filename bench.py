@@ -147,23 +147,25 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def green_algorithmic_bytes(dims, elem=8):
+def green_algorithmic_bytes(dims, elem=8, d_reads=1.0, d_writes=1.0):
     """Compulsory bytes of one fused z/Green launch: read the 6-component x,y-transformed
-    spectrum, write it back, read b_hat (3) and d_prev (3), write d (3) - over the
-    nz*ny*(nx/2+1) stored modes, complex64 each."""
+    spectrum, write it back, read b_hat (3), and on the launches that evaluate the
+    residual read d_prev (3) and on those before an evaluation write d (3) - over the
+    nz*ny*(nx/2+1) stored modes, complex64 each.  d_reads, d_writes: the fractions of
+    launches that do (1 and 1 when every sweep evaluates the residual)."""
     nx, ny, nz = dims
     modes = nz * ny * (nx // 2 + 1)
-    return (6 + 6 + 3 + 3 + 3) * elem * modes
+    return (6 + 6 + 3 + 3 * d_reads + 3 * d_writes) * elem * modes
 
 
-def sweep_hbm(dims, kern, peak):
+def sweep_hbm(dims, kern, peak, green_bytes):
     """%HBM peak of a whole sweep and of each pass: compulsory bytes (complex64 half
     spectra; the x pass also reads the phase map) over the live per-launch times."""
     nx, ny, nz = dims
     modes = nz * ny * (nx // 2 + 1)
     passes = {"x_pass_polarization": (12 * 8 * modes + nx * ny * nz, kern["x_pass_polarization"]["avg_ms"], 1),
               "y_passes": (12 * 8 * modes, kern["y_passes"]["avg_ms"], 2),
-              "z_green_pass": (green_algorithmic_bytes(dims), kern["z_green_pass"]["avg_ms"], 1)}
+              "z_green_pass": (green_bytes, kern["z_green_pass"]["avg_ms"], 1)}
     out = {"unit": "GB/s", "peak": peak, "per_pass": {}}
     tot_b, tot_ms = 0.0, 0.0
     for name, (b, ms, count) in passes.items():
@@ -172,6 +174,7 @@ def sweep_hbm(dims, kern, peak):
         tot_b += count * b
         tot_ms += count * ms
     out["algorithmic_bytes_per_sweep"] = tot_b
+    out["bytes_per_voxel_iter"] = tot_b / float(nx * ny * nz)
     out["achieved"] = tot_b / (tot_ms / 1e3) / 1e9
     out["frac"] = out["achieved"] / peak
     return out
@@ -344,7 +347,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    plan = api.Plan(p.dims, "mixed", autotune=True)   # FP32 sweeps + FP64 defect correction
+    # FP32 sweeps + FP64 defect correction; residual of Eq. 5.11 on predicted sweeps only
+    plan = api.Plan(p.dims, "mixed", autotune=True, sparse_resid=True)
     stream = plan.stream
     eps = torch.empty((6, nz, ny, nx), dtype=torch.float64, device=dev)
     sig = torch.empty_like(eps)
@@ -381,6 +385,7 @@ def run_ours(args):
     clocks.stop()
     launches = api.kernel_launches() - launches0
     g_launches, g_ms = plan.profile_read()
+    g_reads, g_writes = plan.profile_green_io()
     plan.profile(0)
     ms = e0.elapsed_time(e1)
     t = torch.tensor([ms / 1e3, float(nvox) * sweeps, float(args.steps)], dtype=torch.float64, device=dev)
@@ -494,7 +499,8 @@ def run_ours(args):
 
     hbm, peak_kind = peaks()
     g_avg_ms = g_ms / max(g_launches, 1)
-    alg = green_algorithmic_bytes(p.dims)
+    frac_r, frac_w = g_reads / max(g_launches, 1), g_writes / max(g_launches, 1)
+    alg = green_algorithmic_bytes(p.dims, d_reads=frac_r, d_writes=frac_w)
     achieved = alg / (g_avg_ms / 1e3) / 1e9
     traffic = traffic_record(p.dims)
     cpu = None
@@ -527,6 +533,7 @@ def run_ours(args):
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg, "avg_launch_ms": g_avg_ms,
+                     "launches_reading_d_prev": g_reads, "launches_writing_d": g_writes,
                      "launches_timed": g_launches, "timed_launches_from": "last timed step"},
         "kernels_ms_per_launch": kern,
         "sweep_ms": kern["x_pass_polarization"]["avg_ms"] + 2 * kern["y_passes"]["avg_ms"]
@@ -534,8 +541,7 @@ def run_ours(args):
         "non_sweep_ms_per_solve": secs * 1e3 / args.steps - (sweeps / args.steps) * (
             kern["x_pass_polarization"]["avg_ms"] + 2 * kern["y_passes"]["avg_ms"]
             + kern["z_green_pass"]["avg_ms"]),
-        "bytes_per_voxel_iter_design": 230.6,
-        "sweep_hbm": sweep_hbm(p.dims, kern, hbm),
+        "sweep_hbm": sweep_hbm(p.dims, kern, hbm, alg),
         "clocks": clocks.summary(),
         "e2e": e2e,
         "gpu_launches": launches,
@@ -662,7 +668,52 @@ def measure_extras(api, torch):
         "tuning": [pl.tuning()["variant"] for pl, _, _ in groups]}
     for pl, _, _ in groups:
         pl.close()
+    out["cufft_comparison"] = libfft_comparison(api, torch)
     return out
+
+
+def libfft_comparison(api, torch, sweeps=20):
+    """The fused FP32 sweep against sweeps assembled around torch.fft's cuFFT
+    transforms with the library's own polarization and Green-step kernels
+    (libfft_sweeps), on the benchmarked 256^3 problem: ms per sweep of each, both
+    by CUDA events over `sweeps` sweeps after warm-up, and the strain of the two
+    after the same number of sweeps."""
+    from paper_2601_00822_gb300 import workloads as W
+    from paper_2601_00822_gb300.libfft_sweeps import LibFftSweeps
+    p = W.config_c2(contrast=10.0, seed=1)
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp32")
+    with api.Plan(p.dims, "fp32", autotune=True) as plan:
+        st = plan.stream
+        s = LibFftSweeps(plan, ph, p.phases, p.c0, b)
+        for _ in range(3):
+            s.sweep()
+        s = LibFftSweeps(plan, ph, p.phases, p.c0, b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(sweeps):
+            s.sweep()
+        e1.record(st)
+        torch.cuda.synchronize()
+        lib_ms = e0.elapsed_time(e1) / sweeps
+        # fused: a fixed-sweep solve of sweeps and of 2 x sweeps; the difference is sweeps sweeps
+        times = []
+        for k in (sweeps, 2 * sweeps):
+            plan.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=k, want_sig=False, want_u=False)
+            torch.cuda.synchronize()
+            e0.record(st)
+            eps, _, _, _ = plan.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=k, want_sig=False, want_u=False)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        fused_ms = (times[1] - times[0]) / sweeps
+        eps20, _, _, _ = plan.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=sweeps, want_sig=False, want_u=False)
+        err = float(torch.linalg.vector_norm(s.eps - eps20) / torch.linalg.vector_norm(eps20))
+    return {"workload": "256^3 bench problem, FP32, Algorithm-1 sweeps: fused passes vs cuFFT (torch.fft rfftn / "
+                        "irfftn, strain kept in real space) around bfcs_polarize and bfcs_green_apply",
+            "ms_per_sweep_fused": fused_ms, "ms_per_sweep_cufft": lib_ms, "speedup_fused": lib_ms / fused_ms,
+            "eps_rel_l2_after_same_sweeps": err, "sweeps": sweeps}
 
 
 def run_precision_study(args):
