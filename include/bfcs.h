@@ -141,13 +141,15 @@ int bfcs_body_force(int nx, int ny, int nz, double cx, double cy, double cz, dou
  * a time-critical loop).  It makes no cudaMalloc/cudaMallocAsync/cudaFree call
  * and uses no allocating library routine.  The paper has no counterpart: this
  * is an allocation-free way to produce the load of Eq. 2.5.
- *  Scratch: a fixed 16 KiB FP64 array inside the library (2048 partial sums +
- *           the mean), held on every GPU that loads the library until exit.
- *  Limit:   nx*ny*nz <= 134217728 voxels (2048 blocks of 65536); larger grids
- *           return BFCS_ERR_INVALID_ARG before any device work.
- *  Set-up:  the first call on each device looks up the array's device address
- *           (cudaGetSymbolAddress) with that device current; make that first
- *           call before any stream capture on the device.
+ *  Scratch: a fixed 16 KiB FP64 array inside the library (up to 2048 partial
+ *           sums + the mean), held on every GPU that loads the library until exit.
+ *  Limit:   nx*ny*nz <= 134217728 voxels (a 512^3 grid), the stated maximum of
+ *           this entry point; larger grids return BFCS_ERR_INVALID_ARG before
+ *           any device work.
+ *  Set-up:  the first call on each device (and the first in each new context
+ *           of it, e.g. after cudaDeviceReset) looks up the array's device
+ *           address (cudaGetSymbolAddress) with that device current; make that
+ *           first call before any stream capture on the device.
  *  Sharing: every call uses the same array, which keeps the last call's
  *           contents; each call writes every slot it reads before reading it,
  *           so nothing needs clearing.  Calls whose work overlaps on the GPU
@@ -412,7 +414,10 @@ int bfcs_net_create(bfcs_net* out, int nx, int ny, int nz, int max_batch, int fl
 int bfcs_net_destroy(bfcs_net net);
 
 /* Waits for the context's stream and reports whether any network kernel gave
- * up a bounded wait (BFCS_ERR_TIMEOUT; its outputs are then unspecified). */
+ * up a bounded wait (BFCS_ERR_TIMEOUT; its outputs are then unspecified).  The
+ * condition is sticky: once set, the context's tensor-core convolutions return
+ * without work and every later status call reports it; destroy and re-create
+ * the context to continue. */
 int bfcs_net_status(bfcs_net net);
 
 /* Network input of one sample: x_out (dev, 4 x N float) from the body force b

@@ -378,6 +378,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_conv3_tc(ConvArgs a, int* err
   const int tiles_ps = ntx * nty * a.v.nz;
   const int total = tiles_ps * a.batch;
   const int G = gridDim.x;
+  // a network whose tensor-core wait once expired launches no more tensor-core
+  // work: the flag is sticky until the context is destroyed (see the exit below)
+  // (one thread reads it, so every thread of the block takes the same branch)
+  if (__syncthreads_or(tid == 0 && *(volatile int*)err != 0)) return;
 
   if (warp == 0) {   // tensor memory: 2 accumulators of N FP32 columns x 128 lanes
     const unsigned dst = (unsigned)__cvta_generic_to_shared(&tmem_base_s);
@@ -526,6 +530,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_conv3_tc(ConvArgs a, int* err
     wait_mma(k - 1);
     if (ok) epilogue(prev, (k - 1) & 1);
   }
+  // After an expired wait (ok == false) the MMAs of the last commit may still be
+  // in flight when the columns are released below: the contents of this CTA's
+  // TMEM columns are then undefined, and so would be a later CTA's accumulator
+  // placed in them.  The error flag is set before this point and is sticky, so
+  // no later tensor-core launch of this network runs and bfcs_net_status
+  // reports BFCS_ERR_TIMEOUT for every result from then on.
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
