@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--contrast", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-error", action="store_true",
+                    help="skip the all-FP64 reference solve that states the headline result's error")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the translated-averaging and mixed-grid group measurements")
     ap.add_argument("--no-warm-start", action="store_true",
@@ -411,7 +413,7 @@ def run_ours(args):
     # error of the headline result against FP64: the last timed step's fields
     # against an all-FP64 GPU solve of the same problem converged to 1e-10 (untimed)
     fp64_error = None
-    if rank == 0:
+    if rank == 0 and not args.no_fp64_error:
         with api.Plan(p.dims, "fp64") as p64:
             ph64 = api.voxelize(p.dims, p.cell, p.spheres, device=dev)
             b64 = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64", device=dev)
@@ -790,21 +792,38 @@ def run_precision_study(args):
 
 
 def run_sweeps_only(args):
-    """One FP32 solve with a fixed number of sweeps (tol = 0) on the bench workload;
-    used as the command under ncu (no clocks, no oracle, no end-to-end pass)."""
+    """One FP32 solve with a fixed number of sweeps (tol = 0) on the bench workload,
+    with the bench plan's sweep options (autotuned y passes, sparse residual
+    evaluation: with tol = 0 the residual of sweeps 0, 8, ... only); used as the
+    command under ncu (no clocks, no oracle, no end-to-end pass)."""
     import torch
     from paper_2601_00822_gb300 import api
     p = workload(args, 0)
     ph = api.voxelize(p.dims, p.cell, p.spheres)
     b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp32")
-    with api.Plan(p.dims, "fp32") as plan:
+    with api.Plan(p.dims, "fp32", autotune=True, sparse_resid=True) as plan:
         _, _, _, info = plan.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=args.sweeps_only)
     torch.cuda.synchronize()
     print(json.dumps({"sweeps": info.iters, "resid": info.resid, "grid": list(p.dims)}))
 
 
+def torchrun_argv(gpus, argv, port):
+    """Command that relaunches this script with one process per GPU (the launch
+    `bench.py --gpus N` gets when it is not already under a launcher)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        import socket
+        s = socket.socket()
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+        s.close()
+        cmd = torchrun_argv(args.gpus, sys.argv[1:], port)
+        os.execv(cmd[0], cmd)
     if args.sweeps_only > 0:
         run_sweeps_only(args)
         return

@@ -58,6 +58,7 @@ extern "C" {
 #define BFCS_MIXED 2                  /* FP32 sweeps with float-float defect correction; FP64 fields */
 #define BFCS_AUTOTUNE 4               /* OR-ed with FP32 or MIXED: time the y-pass variants at plan creation */
 #define BFCS_CG 8                     /* OR-ed with any precision: conjugate gradients (Algorithm 2) */
+#define BFCS_SPARSE_RESID 16          /* OR-ed with any precision: residual (Eq. 5.11) on predicted sweeps only */
 
 #define BFCS_MAX_PHASES 16
 
@@ -101,7 +102,16 @@ typedef struct {
  *             rounds of CG to 0.1 tol, 0.01 tol, ... relative to their start
  *             in the C0-weighted norm, each verified by two sweeps of the
  *             residual of Eq. 5.11; info.iters counts operator applications;
- *             allocates four more strain spectra per member).  BFCS_MIXED runs the sweeps in FP32 and
+ *             allocates four more strain spectra per member) and
+ *             BFCS_SPARSE_RESID (the residual of Eq. 5.11 is evaluated on
+ *             the first two sweeps and then on the sweep where the observed
+ *             contraction rate predicts r <= tol, at most 8 sweeps apart;
+ *             with tol = 0 on every 8th sweep from the first; the other sweeps neither read nor
+ *             write the previous polarization's divergence, which saves 48 of
+ *             the fused z pass's 168 bytes per mode; the fields of every
+ *             sweep are the same as without the flag, the stopping sweep can
+ *             only come later, and the history holds NaN on sweeps without a
+ *             residual).  BFCS_MIXED runs the sweeps in FP32 and
  *             corrects them with defects evaluated in float-float
  *             arithmetic (below); its fields at the API (b, eps,
  *             sigma, u, eps_init, fft3d data) are double.
@@ -466,6 +476,44 @@ int bfcs_surrogate_infer(bfcs_plan plan, const void* weights, const void* b, con
                          int nphases, const bfcs_lame* phases, void* eps_pred);
 
 /*
+ * Two steps of a sweep on their own, so that a sweep can be assembled around
+ * transforms made elsewhere (e.g. a library FFT, kept as a comparison of the
+ * fused passes).  Both run asynchronously on the plan's stream, in the plan's
+ * real type (float for BFCS_FP32, double otherwise).
+ *
+ * bfcs_polarize - the polarization of Eq. 5.7, tau = (L(x) - L0) : eps, pointwise.
+ *  phase:  dev, N int8 phase ids in [0, nphases) (ids outside the table read
+ *          phase 0's moduli); phases, C0 as in bfcs_solve.
+ *  eps:    dev, 6 x N (xx yy zz yz xz xy, tensorial shears); tau: dev, 6 x N
+ *          (may alias eps).  C0 = {0, 0} is rejected; for sigma = L eps use
+ *          bfcs_solve's outputs.
+ *  Errors: INVALID_ARG (null pointers, invalid moduli), CUDA.
+ *
+ * bfcs_green_apply - the Green step of Algorithm 1 (Eq. 5.9 with U0 of Eqs.
+ *  2.16-2.18 and the reference strain of Eqs. 2.8-2.9) on a dense half
+ *  spectrum: complex values [c][z][y][kx], kx in [0, nx/2], rows of nx/2 + 1
+ *  (the layout of a real-to-complex 3D transform), unnormalised (Eq. 4.3).
+ *  spec:   dev, 6 components: tau_hat on entry, eps_hat^{s+1} on exit =
+ *          U0 tau_hat + eps_hat^{b(0)} on modes with xi != 0 (reading R1 of xi),
+ *          N E at k = 0, 0 on the other modes with xi = 0; unnormalised (an
+ *          inverse transform that divides by N gives eps^{s+1}).
+ *  b_hat:  dev, 3 components of the same layout: the transformed body force.
+ *  E:      host, 6: prescribed mean strain.
+ *  d_prev: dev, 3 components, or NULL: on entry xi . tau_hat of the previous
+ *          sweep (zeros before the first), on exit that of this sweep;
+ *  num_out: dev, 1 double, or NULL (with d_prev): the residual numerator of
+ *          Eq. 5.11 (reading R4) of the strain whose polarization is on entry,
+ *          sum over modes with xi != 0 of w |xi.tau_hat - d_prev|^2 (w = 1 on
+ *          the kx = 0 and nx/2 planes, 2 elsewhere: the full spectrum's sum).
+ *  Errors: INVALID_ARG (null pointers, only one of d_prev / num_out, invalid
+ *          C0), CUDA.
+ */
+int bfcs_polarize(bfcs_plan plan, const int8_t* phase, int nphases, const bfcs_lame* phases, bfcs_lame C0,
+                  const void* eps, void* tau);
+int bfcs_green_apply(bfcs_plan plan, bfcs_lame C0, const double E[6], const void* b_hat, void* spec,
+                     void* d_prev, double* num_out);
+
+/*
  * bfcs_fft3d - the solver's 3D real transform on its own (Eqs. 4.3-4.4):
  *  direction -1: real (ncomp x N) -> half spectrum (ncomp x nz x ny x (nx/2+1)
  *  complex, unnormalised, Eq. 4.3); +1: half spectrum -> real with the 1/|N| of
@@ -481,10 +529,16 @@ int bfcs_fft3d(bfcs_plan plan, int direction, int ncomp, const void* in, void* o
  *   z/Green pass.  While on, every launch of that kind inside an executed sweep
  *   of a solve on this plan is bracketed by CUDA events on the plan's stream.
  * bfcs_profile_read: launches timed and their summed duration (ms) since the
- *   last read; resets the totals.  Both return a status. */
+ *   last read; resets the totals.  Both return a status.
+ * bfcs_profile_green_io: with kind 3, how many of the timed z/Green launches
+ *   (summed over members) read the previous sweep's divergence d_prev (3
+ *   complex values per mode) and how many wrote d (the same size); every
+ *   launch also reads and writes the 6-component spectrum and reads b_hat.
+ *   Waits for the plan's stream; resets the counts. */
 long long bfcs_kernel_launches(void);
 int bfcs_profile_kernel(bfcs_plan plan, int kind);
 int bfcs_profile_read(bfcs_plan plan, long long* launches, double* total_ms);
+int bfcs_profile_green_io(bfcs_plan plan, long long* d_reads, long long* d_writes);
 
 /* bfcs_plan_tuning - the plan's choice for the y passes of its FP32 sweeps
  * (project feature, not in the paper): variant 0..5 = column tile of 16, 8 or

@@ -26,6 +26,7 @@ FP64 = 1
 MIXED = 2
 AUTOTUNE = 4
 CG = 8
+SPARSE_RESID = 16
 
 # every symbol declared in include/bfcs.h
 EXPORTS = (
@@ -36,7 +37,7 @@ EXPORTS = (
     "bfcs_net_destroy", "bfcs_net_prepare", "bfcs_net_forward", "bfcs_net_grad", "bfcs_net_adam",
     "bfcs_net_train_step", "bfcs_net_predict", "bfcs_plan_tuning", "bfcs_solve_group", "bfcs_net_status",
     "bfcs_effective_stiffness", "bfcs_ensemble_average", "bfcs_radial_profile", "bfcs_rve_size",
-    "bfcs_kernel_fit", "bfcs_kernel_apply",
+    "bfcs_kernel_fit", "bfcs_kernel_apply", "bfcs_polarize", "bfcs_green_apply", "bfcs_profile_green_io",
 )
 NET_PARAMS = 523654
 NET_TRAIN = 1
@@ -84,10 +85,13 @@ def _declare(lib):
                                            d, i, vp, vp, C.POINTER(Info)]
     lib.bfcs_surrogate_infer.argtypes = [vp, vp, vp, vp, i, C.POINTER(Lame), vp]
     lib.bfcs_fft3d.argtypes = [vp, i, i, vp, vp]
+    lib.bfcs_polarize.argtypes = [vp, vp, i, C.POINTER(Lame), Lame, vp, vp]
+    lib.bfcs_green_apply.argtypes = [vp, Lame, C.POINTER(d), vp, vp, vp, vp]
     lib.bfcs_last_history.argtypes = [vp, C.POINTER(d), i]
     lib.bfcs_kernel_launches.argtypes = []
     lib.bfcs_profile_kernel.argtypes = [vp, i]
     lib.bfcs_profile_read.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(d)]
+    lib.bfcs_profile_green_io.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     ll, f = C.c_longlong, C.c_float
     lib.bfcs_net_param_count.argtypes = []
     lib.bfcs_net_create.argtypes = [C.POINTER(vp), i, i, i, i, i, vp]

@@ -88,7 +88,8 @@ def body_force(dims, centre, a, precision="fp32", device="cuda", stream=None) ->
 class Plan:
     """bfcs_plan_create / bfcs_plan_destroy with the solver calls as methods."""
 
-    def __init__(self, dims, precision="fp32", max_batch=1, stream=None, autotune=False, cg=False):
+    def __init__(self, dims, precision="fp32", max_batch=1, stream=None, autotune=False, cg=False,
+                 sparse_resid=False):
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.precision = precision
@@ -100,6 +101,8 @@ class Plan:
             flag |= _lib.AUTOTUNE
         if cg:
             flag |= _lib.CG
+        if sparse_resid:
+            flag |= _lib.SPARSE_RESID
         nx, ny, nz = self.dims
         _lib.check(self.lib.bfcs_plan_create(C.byref(h), nx, ny, nz, int(max_batch), flag,
                                              _stream_ptr(self.stream)), "bfcs_plan_create")
@@ -287,6 +290,32 @@ class Plan:
         _lib.check(code, "bfcs_effective_stiffness", allow)
         return ls.reshape(6, 6), as_.reshape(6, 6), [SolveInfo.of(infos[m]) for m in range(6)]
 
+    def polarize(self, phase, phases, c0, eps, tau=None):
+        """bfcs_polarize: tau = (L(x) - L0) : eps (Eq. 5.7); returns tau (6 x N)."""
+        _check_tensor(eps, self._shape(6), self.dtype, "eps")
+        tau = tau if tau is not None else self._alloc(6)
+        _check_tensor(tau, self._shape(6), self.dtype, "tau")
+        nx, ny, nz = self.dims
+        _check_tensor(phase, (nz, ny, nx), torch.int8, "phase")
+        _lib.check(self.lib.bfcs_polarize(self.handle, _ptr(phase), len(phases), _lames(phases), _lib.Lame(*c0),
+                                          _ptr(eps), _ptr(tau)), "bfcs_polarize")
+        return tau
+
+    def green_apply(self, c0, b_hat, spec, E=(0.0,) * 6, d_prev=None, num_out=None):
+        """bfcs_green_apply on a dense half spectrum (ncomp, nz, ny, nx//2 + 1),
+        complex, in place: tau_hat -> eps_hat^{s+1} (unnormalised); with d_prev
+        (3 components) and num_out (one float64) also the residual numerator."""
+        nx, ny, nz = self.dims
+        cdt = torch.complex64 if self.dtype == torch.float32 else torch.complex128
+        _check_tensor(spec, (6, nz, ny, nx // 2 + 1), cdt, "spec")
+        _check_tensor(b_hat, (3, nz, ny, nx // 2 + 1), cdt, "b_hat")
+        _check_tensor(d_prev, (3, nz, ny, nx // 2 + 1), cdt, "d_prev")
+        _check_tensor(num_out, (1,), torch.float64, "num_out")
+        e = (C.c_double * 6)(*[float(v) for v in E])
+        _lib.check(self.lib.bfcs_green_apply(self.handle, _lib.Lame(*c0), e, _ptr(b_hat), _ptr(spec), _ptr(d_prev),
+                                             _ptr(num_out)), "bfcs_green_apply")
+        return spec
+
     def fft3d(self, x, direction=-1):
         """bfcs_fft3d: forward real (c, nz, ny, nx) -> complex (c, nz, ny, nx/2+1) or back
         (inverse without the 1/N factor)."""
@@ -313,6 +342,13 @@ class Plan:
         ms = C.c_double()
         _lib.check(self.lib.bfcs_profile_read(self.handle, C.byref(n), C.byref(ms)), "bfcs_profile_read")
         return n.value, ms.value
+
+    def profile_green_io(self):
+        """bfcs_profile_green_io: (d_prev reads, d writes) of the timed z/Green launches."""
+        r = C.c_longlong()
+        w = C.c_longlong()
+        _lib.check(self.lib.bfcs_profile_green_io(self.handle, C.byref(r), C.byref(w)), "bfcs_profile_green_io")
+        return r.value, w.value
 
     def history(self, cap=1 << 16):
         """bfcs_last_history: residuals r(eps^s) of the last solve."""

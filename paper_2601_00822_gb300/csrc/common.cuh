@@ -450,7 +450,9 @@ struct IterState {
   int diverged;      // NaN/Inf seen
   int stalled;       // no 10% drop of the residual over the stall window
   int stall_at;      // sweep of the last stall checkpoint
-  int pad;
+  int next_check;    // sweep whose residual is evaluated next (sparse evaluation; else every sweep)
+  int last_check;    // sweep of resid_last (valid once checks > 0)
+  int checks;        // residual evaluations so far in this solve
   double stall_ref;  // residual at that checkpoint (0 = none yet)
   double resid_last;
   double bden;       // sqrt(sum |b_hat|^2) over modes with xi != 0

@@ -61,7 +61,11 @@ __device__ __forceinline__ void g0_apply(const C2<R> g[3], const R xi[3], R q, R
 // thread's share of the residual numerator sum.
 template <typename R, int L>
 __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>* pre, int col0, int ky, int mode,
-                                        C2<R>* dprev, IterState* stm, const R* Em) {
+                                        C2<R>* dprev, IterState* stm, const R* Em, bool rd = true,
+                                        bool wr = true) {
+  // GM_SWEEP: rd = this sweep forms the residual (d_prev staged), wr = it stores d
+  const bool rd_d = mode == GM_FINAL || (mode == GM_SWEEP && rd);
+  const bool wr_d = mode == GM_INIT || (mode == GM_SWEEP && wr);
   constexpr int T = kGreenT;
   constexpr int NCOL = GCfg<L>::NCOL;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -100,7 +104,7 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
 #pragma unroll
         for (int q = 0; q < 6; ++q) stm->tau0[q] = (double)M(q).x;
       }
-      if (mode == GM_SWEEP || mode == GM_INIT) {
+      if (wr_d) {
         dprev[gi] = mk<R>(0, 0); dprev[cs + gi] = mk<R>(0, 0); dprev[2 * cs + gi] = mk<R>(0, 0);
       }
 #pragma unroll
@@ -112,7 +116,7 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
     C2<R> bh0 = mk<R>(0, 0), bh1 = mk<R>(0, 0), bh2 = mk<R>(0, 0);
     C2<R> dp[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
     if (load) { bh0 = pm[0]; bh1 = pm[L * T]; bh2 = pm[2 * L * T]; }
-    if (mode == GM_SWEEP || mode == GM_FINAL) { dp[0] = pm[3 * L * T]; dp[1] = pm[4 * L * T]; dp[2] = pm[5 * L * T]; }
+    if (rd_d) { dp[0] = pm[3 * L * T]; dp[1] = pm[4 * L * T]; dp[2] = pm[5 * L * T]; }
 
     C2<R> d[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
     if (mode != GM_INIT) {
@@ -127,10 +131,10 @@ __device__ __forceinline__ R green_tile(const GArgs<R>& a, C2<R>* s, const C2<R>
         const R ex = d[i].x - dp[i].x, ey = d[i].y - dp[i].y;
         r2 += ex * ex + ey * ey;
       }
-      if (mode != GM_APPLY) acc += wgt * r2;
+      if (rd_d) acc += wgt * r2;
       if (mode == GM_FINAL) { d[0] = dp[0]; d[1] = dp[1]; d[2] = dp[2]; }
     }
-    if (mode == GM_SWEEP || mode == GM_INIT) {
+    if (wr_d) {
       dprev[gi] = d[0]; dprev[cs + gi] = d[1]; dprev[2 * cs + gi] = d[2];
     }
     // w = d - i b_hat
@@ -191,6 +195,15 @@ __global__ void __launch_bounds__(GCfg<L>::BLOCK, sizeof(R) == 4 ? 2 : 1) k_zgre
   const long long zs = (long long)ny * p;          // z stride
   const long long rowbase = (long long)ky * p;
   const int mode = a.mode;
+  // sparse residual evaluation (GM_SWEEP): read d_prev and form the residual only
+  // on the member's next check sweep; store d on that sweep, the one before it
+  // and the last sweep of the call (the final step reads it)
+  bool rd = true, wr = true;
+  if (mode == GM_SWEEP && a.sparse) {
+    const int sw = stm->iters, nc = stm->next_check;
+    rd = sw == nc;
+    wr = rd || sw + 1 == nc || sw + 1 >= a.maxit;
+  }
   // element z of line column c at column(c)[z * zs]
   auto column = [&](int c) { const int q = c / T; return spec + q * cs + rowbase + col0 + (c - q * T); };
 
@@ -198,7 +211,7 @@ __global__ void __launch_bounds__(GCfg<L>::BLOCK, sizeof(R) == 4 ? 2 : 1) k_zgre
   {
     constexpr int PER = 16 / sizeof(C2<R>);          // complex values per 16-byte copy
     constexpr int CPR = T / PER;                     // copies per row of the tile
-    const int narr = mode == GM_INIT ? 3 : mode == GM_APPLY ? 0 : 6;
+    const int narr = mode == GM_INIT ? 3 : mode == GM_APPLY ? 0 : (rd ? 6 : 3);
     for (int idx = tid; idx < narr * L * CPR; idx += nthr) {
       const int part = idx % CPR, n = (idx / CPR) % L, arr = idx / (CPR * L);
       const C2<R>* src = (arr < 3 ? bhat + arr * cs : dprev + (arr - 3) * cs) + n * zs + rowbase +
@@ -242,10 +255,10 @@ __global__ void __launch_bounds__(GCfg<L>::BLOCK, sizeof(R) == 4 ? 2 : 1) k_zgre
   __syncthreads();
 
   // ---- Green operators per mode
-  R acc = green_tile<R, L>(a, s, pre, col0, ky, mode, dprev, stm, Em);
+  R acc = green_tile<R, L>(a, s, pre, col0, ky, mode, dprev, stm, Em, rd, wr);
 
   // ---- residual partial of this block in FP64 (fixed order: deterministic)
-  const bool resid = mode == GM_SWEEP || mode == GM_FINAL;
+  const bool resid = (mode == GM_SWEEP && rd) || mode == GM_FINAL;
   if (resid) {
     double accd = (double)acc;
     for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
@@ -599,6 +612,126 @@ cudaError_t launch_symgrad(C2<R>* spec, long long ms, const Geo& g, const Member
 }
 
 
+// ---- Green step on a dense half spectrum, for transforms made outside the fused
+// passes (a library real-to-complex 3D FFT: rows of nx/2 + 1 modes, g.p = g.mx).
+// Per mode with xi != 0: d = tau_hat . xi, w = d - i b_hat, v = G0(xi) w and
+// eps_hat^{s+1} = -sym(xi (x) v), which is U0 tau_hat + eps_hat^{b(0)} (Eqs.
+// 5.9, 2.16-2.18, 2.8-2.9) in the factored form of the fused pass; the k = 0
+// mode takes N E (the DFT of the prescribed mean strain), the other modes with
+// xi = 0 take 0.  The result is unnormalised (an inverse transform that
+// divides by N follows).  With dprev, the residual numerator of Eq. 5.11
+// (reading R4) accumulates w_kx |d - d_prev|^2 per block into part[blockIdx.x]
+// and d is stored for the next sweep.
+template <typename R> struct E6 { R e[6]; };
+
+template <typename R>
+__global__ void k_green_dense(C2<R>* spec, const C2<R>* bhat, C2<R>* dprev, Geo g, R lam0, R mu0, E6<R> E,
+                              ResidSlot* part) {
+  __shared__ double red[32];
+  const long long modes = (long long)g.nz * g.ny * g.mx;
+  const R two_pi = R(6.283185307179586);
+  const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(g.nz);
+  const R inv_mu0 = R(1) / mu0, c0 = (lam0 + mu0) / (lam0 + R(2) * mu0);
+  const R nn = R((double)g.n);
+  R acc = R(0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.mx);
+    const long long r = i / g.mx;
+    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
+    C2<R>* sp = spec + r * g.p + kx;
+    const long long gi = r * g.p + kx;
+    R xi[3];
+    xi[0] = dk0 * R(signed_k(kx, g.nx));
+    xi[1] = dk1 * R(signed_k(ky, g.ny));
+    xi[2] = dk2 * R(signed_k(kz, g.nz));
+    const R qq = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    if (qq == R(0)) {
+      const bool k0 = kx == 0 && ky == 0 && kz == 0;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sp[c * g.cs] = mk<R>(k0 ? nn * E.e[c] : R(0), R(0));
+      if (dprev != nullptr) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dprev[c * g.cs + gi] = mk<R>(0, 0);
+      }
+      continue;
+    }
+    const C2<R> t0 = sp[0], t1 = sp[g.cs], t2 = sp[2 * g.cs], t3 = sp[3 * g.cs], t4 = sp[4 * g.cs],
+                t5 = sp[5 * g.cs];
+    C2<R> d[3];
+    d[0] = scale(t0, xi[0]) + scale(t5, xi[1]) + scale(t4, xi[2]);
+    d[1] = scale(t5, xi[0]) + scale(t1, xi[1]) + scale(t3, xi[2]);
+    d[2] = scale(t4, xi[0]) + scale(t3, xi[1]) + scale(t2, xi[2]);
+    if (dprev != nullptr) {
+      R r2 = R(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const C2<R> dp = dprev[c * g.cs + gi];
+        const R ex = d[c].x - dp.x, ey = d[c].y - dp.y;
+        r2 += ex * ex + ey * ey;
+        dprev[c * g.cs + gi] = d[c];
+      }
+      acc += ((kx == 0 || 2 * kx == g.nx) ? R(1) : R(2)) * r2;
+    }
+    C2<R> w[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const C2<R> b = bhat[c * g.cs + gi];
+      w[c] = mk<R>(d[c].x + b.y, d[c].y - b.x);
+    }
+    C2<R> v[3];
+    g0_apply<R>(w, xi, qq, inv_mu0, c0, v);
+    const R h = R(-0.5);
+    sp[0] = scale(v[0], -xi[0]);
+    sp[g.cs] = scale(v[1], -xi[1]);
+    sp[2 * g.cs] = scale(v[2], -xi[2]);
+    sp[3 * g.cs] = scale(scale(v[2], xi[1]) + scale(v[1], xi[2]), h);
+    sp[4 * g.cs] = scale(scale(v[2], xi[0]) + scale(v[0], xi[2]), h);
+    sp[5 * g.cs] = scale(scale(v[1], xi[0]) + scale(v[0], xi[1]), h);
+  }
+  if (part == nullptr) return;
+  double accd = (double)acc;
+  for (int off = 16; off > 0; off >>= 1) accd += __shfl_down_sync(0xffffffffu, accd, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = accd;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) t += red[k];
+    part[blockIdx.x].num = t;
+  }
+}
+
+// sum of the block partials in block order (deterministic) into *out
+static __global__ void k_sum_slots(const ResidSlot* part, int n, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i].num;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) t += red[k];
+    *out = t;
+  }
+}
+
+template <typename R>
+cudaError_t launch_green_dense(C2<R>* spec, const C2<R>* bhat, C2<R>* dprev, const Geo& g, double lam0,
+                               double mu0, const double* E, ResidSlot* part, int nblocks, double* num_out,
+                               cudaStream_t st) {
+  E6<R> e{};
+  for (int c = 0; c < 6; ++c) e.e[c] = (R)E[c];
+  const bool resid = dprev != nullptr && num_out != nullptr;
+  k_green_dense<R><<<nblocks, 256, 0, st>>>(spec, bhat, dprev, g, (R)lam0, (R)mu0, e, resid ? part : nullptr);
+  count_launches(1);
+  if (resid) {
+    k_sum_slots<<<1, 1024, 0, st>>>(part, nblocks, num_out);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
 template <typename R>
 int green_nparts(const Geo& g) {
   return ((g.mx + kGreenT - 1) / kGreenT) * g.ny;
@@ -638,7 +771,7 @@ template <typename R>
 cudaError_t launch_zgreen_b(const GArgs<R>& a, int batch, cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     const int pb = green_persistent_blocks<R>(a.g);
-    if (pb > 0 && a.mode == GM_SWEEP && a.skip_done && GPCfg<256>::SMEM <= 227 * 1024) {
+    if (pb > 0 && a.mode == GM_SWEEP && a.skip_done && !a.sparse && GPCfg<256>::SMEM <= 227 * 1024) {
       switch (a.g.nz) {
 #define BFCS_GP(L) case L: return zgreen_p_L<L>(a, batch, pb, st);
         BFCS_GP(32) BFCS_GP(48) BFCS_GP(64) BFCS_GP(96) BFCS_GP(128) BFCS_GP(192) BFCS_GP(256)
@@ -664,6 +797,8 @@ template cudaError_t launch_zgreen<BFCS_R>(const GArgs<BFCS_R>&, cudaStream_t);
 template cudaError_t launch_zgreen_b<BFCS_R>(const GArgs<BFCS_R>&, int, cudaStream_t);
 template int green_nparts<BFCS_R>(const Geo&);
 template int green_sweep_parts<BFCS_R>(const Geo&);
+template cudaError_t launch_green_dense<BFCS_R>(C2<BFCS_R>*, const C2<BFCS_R>*, C2<BFCS_R>*, const Geo&, double,
+                                                double, const double*, ResidSlot*, int, double*, cudaStream_t);
 #endif
 template cudaError_t launch_defect<BFCS_R>(const DArgs<BFCS_R>&, int, int, cudaStream_t);
 template cudaError_t launch_symgrad<BFCS_R>(C2<BFCS_R>*, long long, const Geo&, const Member*, int, cudaStream_t);

@@ -195,6 +195,33 @@ cudaError_t launch_body_force_blocks(R* b, int nx, int ny, int nz, double cx, do
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- polarization (Eq. 5.7)
+template <typename R>
+__global__ void k_polarize(R* tau, const R* eps, const int8_t* phase, PhaseTab<R> tab, long long n) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    int ph = phase[v];
+    ph = (ph >= 0 && ph < kMaxPhases) ? ph : 0;
+    const R l1 = tab.lam1[ph], m2 = R(2) * tab.mu1[ph];
+    R e[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = eps[c * n + v];
+    const R lt = l1 * (e[0] + e[1] + e[2]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tau[c * n + v] = m2 * e[c] + (c < 3 ? lt : R(0));
+  }
+}
+
+template <typename R>
+cudaError_t launch_polarize(R* tau, const R* eps, const int8_t* phase, const PhaseTab<R>& tab, long long n,
+                            cudaStream_t s) {
+  const long long want = (n + kRedThreads - 1) / kRedThreads;
+  const int blocks = (int)std::min<long long>(want, 8LL * 152);
+  k_polarize<R><<<std::max(blocks, 1), kRedThreads, 0, s>>>(tau, eps, phase, tab, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- validation
 constexpr int kValBlocks = 512;
 
@@ -319,11 +346,34 @@ cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterSt
 __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* sts, const Member* mem,
                                double* hist, int hist_cap, double tol, double lam0, double mu0, double E0,
                                double E1, double E2, double E3, double E4, double E5, double n, int maxdim,
-                               int mode, int warm_all, int stall_window) {
+                               int mode, int warm_all, int stall_window, int check_max, int maxit,
+                               unsigned long long* io) {
   __shared__ double red[32];
   const int m = blockIdx.x;
   IterState* st = sts + m;
   if (mode == GM_SWEEP && st->done) return;
+  __shared__ int no_check;   // decided by one thread: thread 0 advances st->iters below
+  if (threadIdx.x == 0) {
+    const int sw = st->iters, nc = st->next_check;
+    no_check = mode == GM_SWEEP && check_max > 1 && sw != nc;
+    if (io != nullptr && mode == GM_SWEEP) {
+      // what the Green pass of this sweep moved besides its fixed traffic: d_prev read, d written
+      const bool rd = check_max <= 1 || sw == nc;
+      const bool wr = check_max <= 1 || rd || sw + 1 == nc || sw + 1 >= maxit;
+      atomicAdd(io, (unsigned long long)rd);
+      atomicAdd(io + 1, (unsigned long long)wr);
+    }
+  }
+  __syncthreads();
+  if (no_check) {
+    // no residual on this sweep (the Green pass wrote no partials)
+    if (threadIdx.x == 0) {
+      const int sweep = st->iters;
+      if (sweep < hist_cap && hist != nullptr) hist[(long long)m * hist_cap + sweep] = NAN;
+      st->iters = sweep + 1;
+    }
+    return;
+  }
   part += m * nparts;
   double acc = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i].num;
@@ -350,6 +400,24 @@ __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* sts
   const bool skip_check = warm && sweep == 0;
   if (skip_check) r = INFINITY;
   if (sweep < hist_cap && hist != nullptr) hist[(long long)m * hist_cap + sweep] = r;
+  // sweep of the next evaluation: with sparse evaluation, where the contraction
+  // rate between the last two evaluations predicts r <= tol (at most check_max
+  // sweeps ahead; every check_max sweeps when tol = 0), else the next sweep
+  int gap = 1;
+  if (check_max > 1 && !skip_check) {
+    if (!(tol > 0.0)) {
+      gap = check_max;
+    } else if (st->checks > 0 && sweep > st->last_check && r > tol && r < st->resid_last && r > 0.0) {
+      const double rate = pow(r / st->resid_last, 1.0 / (double)(sweep - st->last_check));
+      const double need = ceil(log(tol / r) / log(rate));
+      gap = (int)fmin(fmax(need, 1.0), (double)check_max);
+    }
+  }
+  st->next_check = sweep + gap;
+  if (!skip_check) {
+    st->last_check = sweep;
+    st->checks += 1;
+  }
   st->resid_last = r;
   st->iters = sweep + 1;
   if (skip_check) return;
@@ -368,10 +436,11 @@ __global__ void k_resid_reduce(const ResidSlot* part, int nparts, IterState* sts
 cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, const Member* mem,
                                 double* hist, int hist_cap, double tol, double lam0, double mu0,
                                 const double* E, long long n, int maxdim, int mode, int warm_all,
-                                int stall_window, int batch, cudaStream_t s) {
+                                int stall_window, int check_max, int maxit, unsigned long long* io, int batch,
+                                cudaStream_t s) {
   k_resid_reduce<<<batch, 1024, 0, s>>>(part, nparts, st, mem, hist, hist_cap, tol, lam0, mu0, E[0], E[1],
                                         E[2], E[3], E[4], E[5], (double)n, maxdim, mode, warm_all,
-                                        stall_window);
+                                        stall_window, check_max, maxit, io);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -679,6 +748,8 @@ cudaError_t launch_stress(double* sig, const double* eps, const int8_t* phase, c
 #define BFCS_INST(R)                                                                              \
   template cudaError_t launch_body_force<R>(R*, int, int, int, double, double, double, double,     \
                                             double*, cudaStream_t);                               \
+  template cudaError_t launch_polarize<R>(R*, const R*, const int8_t*, const PhaseTab<R>&, long long,  \
+                                          cudaStream_t);                                          \
   template cudaError_t launch_body_force_blocks<R>(R*, int, int, int, double, double, double,      \
                                                    double, int, double*, cudaStream_t);           \
   template cudaError_t launch_validate<R>(const int8_t*, const R*, long long, int*, double*,       \

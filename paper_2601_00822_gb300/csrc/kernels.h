@@ -130,6 +130,11 @@ template <typename R> struct GArgs {
   int skip_done;          // 1: members with st[m].done skip the launch
   int use_me;             // 1: member m takes its mean strain from mE[m]
   int mode;
+  // GM_SWEEP with sparse residual evaluation: sweep s = st[m].iters reads d_prev
+  // and forms the residual only when s == st[m].next_check, and writes d only on
+  // that sweep, the one before it and the last sweep (s + 1 == maxit)
+  int sparse;
+  int maxit;
   R mE[kMaxBatch][6];
 };
 
@@ -155,6 +160,20 @@ template <typename R> struct DArgs {
 // components 0..5 out, in place.
 template <typename R> cudaError_t launch_symgrad(C2<R>* spec, long long ms, const Geo& g, const Member* mem, int batch,
                                                  cudaStream_t s);
+
+// Green step on a dense half spectrum (row pitch g.p = g.mx, component stride
+// g.cs): spec holds tau_hat on entry and eps_hat^{s+1} (unnormalised) on exit;
+// with dprev and num_out, the residual numerator of Eq. 5.11 from |d - d_prev|
+// goes to *num_out (block partials in part, nblocks slots) and d to dprev.
+template <typename R>
+cudaError_t launch_green_dense(C2<R>* spec, const C2<R>* bhat, C2<R>* dprev, const Geo& g, double lam0,
+                               double mu0, const double* E, ResidSlot* part, int nblocks, double* num_out,
+                               cudaStream_t st);
+// tau = (L(x) - L0) : eps pointwise (table lam1 / mu1; phase ids outside the
+// table read entry 0)
+template <typename R>
+cudaError_t launch_polarize(R* tau, const R* eps, const int8_t* phase, const PhaseTab<R>& tab, long long n,
+                            cudaStream_t s);
 
 template <typename R> cudaError_t launch_xpass(const XArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_defect(const DArgs<R>& a, int blocks, int batch, cudaStream_t s);
@@ -230,11 +249,18 @@ cudaError_t launch_bden(const C2<R>* bhat, const Geo& g, ResidSlot* part, IterSt
 // kReduceDefect.  One block per member: member m reduces part[m * nparts ...],
 // updates st[m] and writes hist[m * hist_cap + sweep]; its E and warm flag
 // come from mem[m] when mem is given, else from E / warm_all.  In GM_SWEEP the
-// sweep index is the device counter st[m].iters.
+// sweep index is the device counter st[m].iters.  check_max > 1: sparse
+// evaluation, only sweeps s == st[m].next_check carry a residual (others
+// record NaN in hist); after each evaluation the next one is placed at the
+// sweep where the observed contraction rate predicts r <= tol, at most
+// check_max sweeps ahead (every check_max sweeps when tol = 0).  io (nullable):
+// two counters that GM_SWEEP adds to, per member, whether the sweep's Green
+// pass read d_prev and whether it wrote d (maxit: the call's sweep limit).
 cudaError_t launch_resid_reduce(const ResidSlot* part, int nparts, IterState* st, const Member* mem,
                                 double* hist, int hist_cap, double tol, double c0_lam, double c0_mu,
                                 const double* E, long long n, int maxdim, int mode, int warm_all,
-                                int stall_window, int batch, cudaStream_t s);
+                                int stall_window, int check_max, int maxit, unsigned long long* io, int batch,
+                                cudaStream_t s);
 // mode for launch_resid_reduce: tau0 already holds sigma_hat(0) (defect evaluation)
 constexpr int kReduceDefect = 7;
 

@@ -35,6 +35,8 @@ struct bfcs_plan_s {
   Member* mem_dev = nullptr;       // max_batch member descriptors
   Member* mem_host = nullptr;      // pinned staging of the descriptors
   int graph_sweeps = 8;            // sweeps per captured graph (0: no graphs)
+  int resid_max = 1;               // BFCS_SPARSE_RESID: most sweeps between residual evaluations (1: every sweep)
+  unsigned long long* io_dev = nullptr;   // profiled z/Green launches: d_prev reads, d writes
   cudaStream_t loop_st = nullptr;  // private stream of the sweep loop (capturable), ordered with st
   cudaEvent_t order_ev[2];
   cudaEvent_t ev[2];
@@ -84,6 +86,7 @@ namespace {
 int severity(int s) { return s < 0 ? 1000 - s : s; }
 
 constexpr int kHistCap = 1 << 14;   // residual history entries kept per member
+constexpr int kSparseResidMax = 8;  // BFCS_SPARSE_RESID: most sweeps between residual evaluations
 
 double wait_limit_s() {
   const char* e = std::getenv("BFCS_WAIT_TIMEOUT_S");
@@ -158,7 +161,7 @@ void free_plan(bfcs_plan P) {
   if (P == nullptr) return;
   cudaFree(P->spec); cudaFree(P->bhat); cudaFree(P->dprev);
   for (int i = 0; i < 3; ++i) cudaFree(P->tw[i]);
-  cudaFree(P->part); cudaFree(P->ist); cudaFree(P->hist); cudaFree(P->mem_dev);
+  cudaFree(P->part); cudaFree(P->ist); cudaFree(P->hist); cudaFree(P->mem_dev); cudaFree(P->io_dev);
   if (P->mem_host) cudaFreeHost(P->mem_host);
   cudaFree(P->ival); cudaFree(P->dval); cudaFree(P->dscratch);
   cudaFree(P->tmp); cudaFree(P->tmp_hits); cudaFree(P->mod_buf); cudaFree(P->prof_buf);
@@ -397,6 +400,8 @@ struct SweepSet {
     ga.use_me = 1;
     for (int m = 0; m < B; ++m)
       for (int c = 0; c < 6; ++c) ga.mE[m][c] = (R)P->mem_host[m].E[c];
+    ga.sparse = P->resid_max > 1 ? 1 : 0;
+    ga.maxit = 0;                  // set by run_sets for its call
     ga.spec_ms = sms;
     ga.b_ms = 3 * g.cs;
     ga.d_ms = 3 * g.cs;
@@ -473,8 +478,11 @@ struct SweepSet {
     ga.skip_done = 1;
     CK(timed(3, [&] { return launch_zgreen_b<R>(ga, B, q); }));
     CK(timed(2, [&] { return launch_colpass_b<R>(cy, +1, B, q); }));
-    CK(launch_resid_reduce(P->part, green_sweep_parts<R>(P->g), P->ist, P->mem_dev, P->hist, P->hist_cap, tol,
-                           C0.lambda, C0.mu, E0, P->g.n, maxdim, GM_SWEEP, 0, P->stall_window, B, q));
+    // (the persistent form of the z pass does not run with sparse evaluation)
+    const int nparts = ga.sparse ? green_nparts<R>(P->g) : green_sweep_parts<R>(P->g);
+    unsigned long long* io = (P->prof_kind == 3 && sweep >= 0) ? P->io_dev : nullptr;
+    CK(launch_resid_reduce(P->part, nparts, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda, C0.mu, E0,
+                           P->g.n, maxdim, GM_SWEEP, 0, P->stall_window, P->resid_max, ga.maxit, io, B, q));
     return BFCS_OK;
   }
 
@@ -494,7 +502,7 @@ struct SweepSet {
     ga.skip_done = 0;
     CK(launch_zgreen_b<R>(ga, B, st));
     CK(launch_resid_reduce(P->part, P->ngreen, P->ist, P->mem_dev, P->hist, P->hist_cap, tol, C0.lambda, C0.mu,
-                           E0, P->g.n, maxdim, GM_FINAL, 0, 0, B, st));
+                           E0, P->g.n, maxdim, GM_FINAL, 0, 0, P->resid_max, 0, nullptr, B, st));
     cy.ncomp = 3;
     CK(launch_colpass_b<R>(cy, +1, B, st));
     XArgs<R> xu{};
@@ -603,6 +611,7 @@ int run_sets(std::vector<SweepSet<R>*>& sets, int maxit) {
     return BFCS_OK;
   };
 
+  for (auto* ss : sets) ss->ga.maxit = maxit;     // the last sweep of this call stores d for the final step
   bool profiling = false;
   for (auto* ss : sets) profiling = profiling || ss->P->prof_kind != 0;
   const int G = profiling ? 0 : P0->graph_sweeps;
@@ -651,16 +660,18 @@ int run_sets(std::vector<SweepSet<R>*>& sets, int maxit) {
       const SweepSet<R>& ss = *sets[i];
       for (int m = 0; m < ss.B; ++m, ++gm) {
         if (h[m].done) continue;
+        // the residual observed is of sweep last_check (every sweep's, unless sparse)
         const double r = h[m].resid_last;
+        const int at = h[m].last_check;
         const double tl = ss.P->mem_host[m].tol >= 0 ? ss.P->mem_host[m].tol : ss.tol;
-        if (!(tl > 0) || !(h[m].iters > 0) || !std::isfinite(r) || !(r > 0) || obs_it[gm] < 0 ||
-            !(h[m].iters > obs_it[gm]) || !(r < obs_r[gm])) {
+        if (!(tl > 0) || !(h[m].checks > 0) || !std::isfinite(r) || !(r > 0) || obs_it[gm] < 0 ||
+            !(at > obs_it[gm]) || !(r < obs_r[gm])) {
           known = false;
         } else {
-          const double rate = std::pow(r / obs_r[gm], 1.0 / (h[m].iters - obs_it[gm]));
-          worst = std::max(worst, std::log(tl / r) / std::log(rate));
+          const double rate = std::pow(r / obs_r[gm], 1.0 / (at - obs_it[gm]));
+          worst = std::max(worst, std::log(tl / r) / std::log(rate) - (h[m].iters - 1 - at));
         }
-        if (std::isfinite(r) && r > 0) { obs_it[gm] = h[m].iters; obs_r[gm] = r; }
+        if (h[m].checks > 0 && std::isfinite(r) && r > 0) { obs_it[gm] = at; obs_r[gm] = r; }
       }
     }
     return known ? worst : -1.0;
@@ -1528,7 +1539,7 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   const int prec = flags & 3;
   if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz) || max_batch < 1 || max_batch > kMaxBatch ||
       (prec != BFCS_FP32 && prec != BFCS_FP64 && prec != BFCS_MIXED) ||
-      (flags & ~(3 | BFCS_AUTOTUNE | BFCS_CG)) != 0)
+      (flags & ~(3 | BFCS_AUTOTUNE | BFCS_CG | BFCS_SPARSE_RESID)) != 0)
     return BFCS_ERR_INVALID_ARG;
   bfcs_plan P = new bfcs_plan_s();
   P->nx = nx; P->ny = ny; P->nz = nz;
@@ -1561,6 +1572,7 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
        cudaMalloc(&P->dprev, MB * 3 * cs * P->csz) == cudaSuccess &&
        cudaMalloc(&P->part, MB * P->npart * sizeof(ResidSlot)) == cudaSuccess &&
        cudaMalloc(&P->ist, MB * sizeof(IterState)) == cudaSuccess &&
+       cudaMalloc(&P->io_dev, 2 * sizeof(unsigned long long)) == cudaSuccess &&
        cudaMalloc(&P->hist, MB * kHistCap * sizeof(double)) == cudaSuccess &&
        cudaMalloc(&P->mem_dev, MB * sizeof(Member)) == cudaSuccess &&
        cudaMallocHost(&P->mem_host, MB * sizeof(Member)) == cudaSuccess &&
@@ -1600,8 +1612,16 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
          cudaMallocHost(&P->cg_host, MB * sizeof(CgState)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
   }
-  if (cudaMemset(P->ist, 0, MB * sizeof(IterState)) != cudaSuccess) { free_plan(P); return BFCS_ERR_CUDA; }
+  if (cudaMemset(P->ist, 0, MB * sizeof(IterState)) != cudaSuccess ||
+      cudaMemset(P->io_dev, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    free_plan(P);
+    return BFCS_ERR_CUDA;
+  }
   if (const char* gs = std::getenv("BFCS_GRAPH_SWEEPS")) P->graph_sweeps = std::max(0, std::atoi(gs));
+  if (flags & BFCS_SPARSE_RESID) {
+    P->resid_max = kSparseResidMax;
+    if (const char* ri = std::getenv("BFCS_RESID_INTERVAL")) P->resid_max = std::max(1, std::min(64, std::atoi(ri)));
+  }
   if (!P->fp64) {
     const char* cv = std::getenv("BFCS_COL_VARIANT");
     if (cv != nullptr) {
@@ -2016,6 +2036,39 @@ int bfcs_kernel_apply(bfcs_plan P, int degree, const double* coef, double delta,
   return sync_stream(P);
 }
 
+int bfcs_polarize(bfcs_plan P, const int8_t* phase, int nph, const bfcs_lame* phases, bfcs_lame C0,
+                  const void* eps, void* tau) {
+  if (P == nullptr || phase == nullptr || eps == nullptr || tau == nullptr) return BFCS_ERR_INVALID_ARG;
+  const int cm = check_material(nph, phases, C0);
+  if (cm != BFCS_OK) return cm;
+  if (P->fp64 || P->mixed)
+    CK(launch_polarize<double>((double*)tau, (const double*)eps, phase, make_tab<double>(nph, phases, C0), P->g.n,
+                               P->st));
+  else
+    CK(launch_polarize<float>((float*)tau, (const float*)eps, phase, make_tab<float>(nph, phases, C0), P->g.n,
+                              P->st));
+  return BFCS_OK;
+}
+
+int bfcs_green_apply(bfcs_plan P, bfcs_lame C0, const double E[6], const void* b_hat, void* spec, void* d_prev,
+                     double* num_out) {
+  if (P == nullptr || E == nullptr || b_hat == nullptr || spec == nullptr || (d_prev == nullptr) != (num_out == nullptr))
+    return BFCS_ERR_INVALID_ARG;
+  if (!(std::isfinite(C0.lambda) && std::isfinite(C0.mu) && C0.mu > 0 && C0.lambda + 2 * C0.mu > 0))
+    return BFCS_ERR_INVALID_ARG;
+  Geo g = P->g;                       // dense rows: nx/2 + 1 modes each
+  g.p = g.mx;
+  g.cs = (long long)g.nz * g.ny * g.mx;
+  const int blocks = std::max(1, std::min(P->npart, 4 * 152));
+  if (P->fp64 || P->mixed)
+    CK(launch_green_dense<double>((C2<double>*)spec, (const C2<double>*)b_hat, (C2<double>*)d_prev, g, C0.lambda,
+                                  C0.mu, E, P->part, blocks, num_out, P->st));
+  else
+    CK(launch_green_dense<float>((C2<float>*)spec, (const C2<float>*)b_hat, (C2<float>*)d_prev, g, C0.lambda,
+                                 C0.mu, E, P->part, blocks, num_out, P->st));
+  return BFCS_OK;
+}
+
 int bfcs_fft3d(bfcs_plan P, int direction, int ncomp, const void* in, void* out) {
   if (P == nullptr || in == nullptr || out == nullptr || ncomp < 1 || ncomp > 6 ||
       (direction != -1 && direction != 1))
@@ -2039,6 +2092,19 @@ int bfcs_profile_kernel(bfcs_plan P, int kind) {
   P->prof_kind = kind;
   P->prof_launches = 0;
   P->prof_ms = 0.0;
+  CK(cudaMemsetAsync(P->io_dev, 0, 2 * sizeof(unsigned long long), P->st));
+  return BFCS_OK;
+}
+
+int bfcs_profile_green_io(bfcs_plan P, long long* d_reads, long long* d_writes) {
+  if (P == nullptr || d_reads == nullptr || d_writes == nullptr) return BFCS_ERR_INVALID_ARG;
+  unsigned long long h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, P->io_dev, sizeof(h), cudaMemcpyDeviceToHost, P->st));
+  const int w = sync_stream(P);
+  if (w != BFCS_OK) return w;
+  *d_reads = (long long)h[0];
+  *d_writes = (long long)h[1];
+  CK(cudaMemsetAsync(P->io_dev, 0, sizeof(h), P->st));
   return BFCS_OK;
 }
 

@@ -55,9 +55,19 @@ def test_invalid_plan_rejected_before_any_device_work():
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 31, 1, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 0, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_plan_create(None, 32, 32, 32, 1, 0, None) == _lib.ERR_INVALID_ARG
-    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 16, None) == _lib.ERR_INVALID_ARG  # unknown flag
+    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 32, None) == _lib.ERR_INVALID_ARG  # unknown flag
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 3, None) == _lib.ERR_INVALID_ARG  # no precision 3
     assert lib.bfcs_plan_tuning(None, None, None, None, None) == _lib.ERR_INVALID_ARG
+
+
+def test_sweep_step_entry_points_reject_bad_arguments():
+    lib = _lib.load()
+    lame = (_lib.Lame * 1)(_lib.Lame(1.0, 0.5))
+    E = (ctypes.c_double * 6)()
+    n = ctypes.c_longlong()
+    assert lib.bfcs_polarize(None, None, 1, lame, _lib.Lame(1.0, 0.5), None, None) == _lib.ERR_INVALID_ARG
+    assert lib.bfcs_green_apply(None, _lib.Lame(1.0, 0.5), E, None, None, None, None) == _lib.ERR_INVALID_ARG
+    assert lib.bfcs_profile_green_io(None, ctypes.byref(n), ctypes.byref(n)) == _lib.ERR_INVALID_ARG
 
 
 def test_network_parameter_count_and_invalid_contexts():

@@ -163,3 +163,19 @@ def test_a_rank_that_leaves_gives_an_error_not_a_hang(tmp_path):
         assert time.monotonic() - t0 < 120, "rank 0 did not return"
     outcome, secs = open(path).read().split()
     assert outcome != "returned" and float(secs) < 60.0, (outcome, secs)
+
+
+def test_bench_relaunches_itself_with_one_process_per_gpu():
+    """bench.py --gpus N outside a launcher re-executes itself under
+    torch.distributed.run with N processes on 127.0.0.1 and the same arguments."""
+    import importlib.util
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    cmd = bench.torchrun_argv(4, ["--gpus", "4", "--steps", "3"], 29511)
+    assert cmd[:3] == [sys.executable, "-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[cmd.index("--master-port") + 1] == "29511"
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "3"] and cmd[-5].endswith("bench.py")

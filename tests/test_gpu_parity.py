@@ -604,3 +604,75 @@ def test_phase_map_at_an_unaligned_address(precision):
     ph_o, b_o = oracle_inputs(p)
     ref = O.solve(ph_o, p.phases, p.c0, b_o, tol=0, maxit=6)
     assert rel(e1.cpu().numpy(), ref["eps"]) < TOL[precision] * 10
+
+
+# ---------------------------------------------------------------- sparse residual evaluation
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["c1_32cubed", "ragged_48x24x96"])
+def test_sparse_residual_same_fields_fixed_sweeps(name, precision):
+    """With BFCS_SPARSE_RESID every sweep computes the same fields (the residual
+    does not enter the iteration) and the residuals it does evaluate (every 8th
+    sweep with tol = 0) are those of the dense evaluation; the final residual
+    and the oracle's fields after the same sweeps agree."""
+    p = CASES[name]
+    ph, b = gpu_inputs(p, precision)
+    sweeps = 20
+    out = {}
+    for sparse in (False, True):
+        with api.Plan(p.dims, precision, sparse_resid=sparse) as plan:
+            eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, p.mean_strain, tol=0.0, maxit=sweeps)
+            out[sparse] = (eps.clone(), sig.clone(), u.clone(), info, plan.history())
+    e0, s0, u0, i0, h0 = out[False]
+    e1, s1, u1, i1, h1 = out[True]
+    assert torch.equal(e0, e1) and torch.equal(s0, s1) and torch.equal(u0, u1)
+    assert i1.iters == i0.iters == sweeps and i1.resid == i0.resid
+    evaluated = ~np.isnan(h1)
+    assert list(np.nonzero(evaluated)[0]) == [0, 8, 16]
+    assert np.array_equal(h1[evaluated], h0[evaluated])
+    ph_o, b_o = oracle_inputs(p)
+    ref = O.solve(ph_o, p.phases, p.c0, b_o, p.mean_strain, tol=0.0, maxit=sweeps)
+    assert rel(e1.cpu().numpy(), ref["eps"]) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_sparse_residual_converged_solve(precision, tol):
+    """A converged solve with sparse evaluation meets the tolerance, stops at
+    most two sweeps after the dense evaluation would, and its fields equal the
+    oracle's after the same number of sweeps (batched members with different
+    shifts, mean strains and a warm start included)."""
+    p = CASES["ragged_48x24x96"]
+    ph, b = gpu_inputs(p, precision)
+    ph_o, b_o = oracle_inputs(p)
+    init_ref = O.solve(ph_o, p.phases, p.c0, b_o, tol=0, maxit=3)["eps"]
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    init = torch.tensor(init_ref, dtype=dt, device="cuda")
+    specs = [((0, 0, 0), (0,) * 6, None), ((5, 3, 11), (0.01, 0, 0, 0, 0, 0.002), None),
+             ((47, 23, 95), (0,) * 6, init)]
+    res = {}
+    for sparse in (False, True):
+        with api.Plan(p.dims, precision, max_batch=3, sparse_resid=sparse) as plan:
+            members = [dict(phase=ph, b=b, E=E, shift=sh, eps_init=ei) for sh, E, ei in specs]
+            members, infos = plan.solve_batched(members, p.phases, p.c0, tol=tol, maxit=4000)
+        res[sparse] = (members, infos)
+    for k, (sh, E, ei) in enumerate(specs):
+        dense, sparse = res[False][1][k], res[True][1][k]
+        assert sparse.status == _lib.OK and sparse.resid <= tol
+        assert dense.iters <= sparse.iters <= dense.iters + 2, (k, dense.iters, sparse.iters)
+        ref = O.solve(O.translate(ph_o, sh), p.phases, p.c0, b_o, E, tol=0.0, maxit=sparse.iters,
+                      eps_init=init_ref if ei is not None else None)
+        for key, k2 in (("eps_out", "eps"), ("sig_out", "sig"), ("u_out", "u")):
+            assert rel(res[True][0][k][key].cpu().numpy(), ref[k2]) < TOL[precision], (k, key)
+
+
+def test_sparse_residual_in_the_mixed_ladder():
+    """The bench's configuration (mixed ladder, autotuned, sparse evaluation) on C1
+    reaches 1e-9 by the oracle's own residual of the returned field."""
+    p = W.config_c1()
+    ph_o, b_o = oracle_inputs(p)
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    with api.Plan(p.dims, "mixed", autotune=True, sparse_resid=True) as plan:
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-9, maxit=4000)
+    assert info.status == _lib.OK and info.resid <= 1e-9
+    r = O.residual(ph_o, p.phases, eps.cpu().numpy(), O.fft3(b_o), O.wavevectors(p.dims))
+    assert r <= 2e-9, r
