@@ -182,9 +182,12 @@ def sweep_hbm(dims, kern, peak, green_bytes):
     return out
 
 
-def traffic_record(dims):
+def traffic_record(dims, frac_r, frac_w):
     """dram bytes per launch of the Green pass from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+    when the kernel source changed since the counters were taken.  The summary holds
+    one launch of each kind (neither d_prev read nor d written, d written only, both);
+    they are combined with the fractions of the timed launches that read d_prev
+    (frac_r) and wrote d (frac_w); every launch that reads also writes."""
     path = os.path.join(ROOT, "profiles", "zgreen_traffic.json")
     try:
         with open(path) as f:
@@ -199,7 +202,9 @@ def traffic_record(dims):
         return None
     nx, ny, nz = dims
     scale = (nz * ny * (nx // 2 + 1)) / float(rec["modes"])
-    return rec["dram_bytes_per_launch"] * scale
+    per = rec["dram_bytes_per_launch"]
+    plain, w, rw = per["neither"], per["write_d"], per["read_and_write_d"]
+    return (plain + frac_w * (w - plain) + frac_r * (rw - w)) * scale
 
 
 # ------------------------------------------------------------------ CPU oracle arm
@@ -504,7 +509,7 @@ def run_ours(args):
     frac_r, frac_w = g_reads / max(g_launches, 1), g_writes / max(g_launches, 1)
     alg = green_algorithmic_bytes(p.dims, d_reads=frac_r, d_writes=frac_w)
     achieved = alg / (g_avg_ms / 1e3) / 1e9
-    traffic = traffic_record(p.dims)
+    traffic = traffic_record(p.dims, frac_r, frac_w)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(p, fp64_error["sweeps_to_tol"] if fp64_error else None)
