@@ -84,3 +84,33 @@ def test_largest_grid_two_members_batched_equals_individual():
             (one,), _ = plan.solve_batched([dict(phase=ph, b=b, E=E, shift=sh, sig_out=None, u_out=None)],
                                            p.phases, p.c0, tol=0, maxit=12)
             assert torch.equal(one["eps_out"], m["eps_out"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_largest_batch_and_more_members_than_the_batch(precision):
+    """64 members (the most one launch carries) and 70 members on a plan of
+    max_batch 64 (run as groups of at most 64): every member equals its own
+    solve, and sampled members match the oracle at the same sweep count."""
+    dims = (16, 16, 16)
+    p = W.Problem(name="b64", dims=dims, cell=(8, 8, 8), spheres=np.asarray([[8, 8, 8, 30, 1]], np.int32),
+                  phases=[(1.0, 0.5), (6.0, 3.0)], c0=(3.5, 1.75), bf_centre=(8.0, 8.0, 8.0), bf_radius=4.0)
+    ph = api.voxelize(dims, p.cell, p.spheres)
+    b = api.body_force(dims, p.bf_centre, p.bf_radius, precision)
+    shifts = [(k % 16, (3 * k) % 16, (7 * k) % 16) for k in range(70)]
+    sweeps = 6
+    with api.Plan(dims, precision, max_batch=64, sparse_resid=True) as plan:
+        for count in (64, 70):
+            members = [dict(phase=ph, b=b, shift=s, sig_out=None, u_out=None) for s in shifts[:count]]
+            members, infos = plan.solve_batched(members, p.phases, p.c0, tol=0, maxit=sweeps)
+            assert len(infos) == count and all(i.iters == sweeps for i in infos)
+            with api.Plan(dims, precision, sparse_resid=True) as one:
+                for k in (0, 31, count - 1):
+                    (m1,), _ = one.solve_batched([dict(phase=ph, b=b, shift=shifts[k], sig_out=None, u_out=None)],
+                                                 p.phases, p.c0, tol=0, maxit=sweeps)
+                    assert torch.equal(m1["eps_out"], members[k]["eps_out"]), (count, k)
+    ph_o = O.phase_map(dims, p.cell, p.spheres)
+    b_o = O.body_force(dims, p.bf_centre, p.bf_radius)
+    bar = 1e-10 if precision == "fp64" else 1e-5
+    for k in (5, 63):
+        ref = O.solve(O.translate(ph_o, shifts[k]), p.phases, p.c0, b_o, tol=0, maxit=sweeps)
+        assert rel(members[k]["eps_out"].cpu().numpy(), ref["eps"]) < bar, k

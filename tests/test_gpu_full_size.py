@@ -8,7 +8,7 @@ seeded input; the GPU path must match it field by field at the same sweep
 count (relative L2 <= 1e-10 in FP64, <= 1e-5 in FP32) and reproduce its
 residual history of Eq. 5.11 (reading R4).
 
-The converged results are judged against an all-FP64 GPU solve of the same
+The converged results are compared with an all-FP64 GPU solve of the same
 problem, itself checked by the oracle's own residual of the returned field.
 """
 import os
