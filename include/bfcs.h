@@ -543,10 +543,13 @@ int bfcs_profile_green_io(bfcs_plan plan, long long* d_reads, long long* d_write
 /* bfcs_plan_tuning - the plan's choice for the y passes of its FP32 sweeps
  * (project feature, not in the paper): variant 0..5 = column tile of 16, 8 or
  * 32 kx columns per block, then the same three with the two radices of the
- * line length ny = R1 R2 in the other order.  With BFCS_AUTOTUNE the plan
- * timed every variant valid for ny on its own buffers and kept the fastest
- * (variant_ms: 6 doubles, ms per y forward + inverse pair, 0 = not timed);
- * without it the variant is 0.  Any output pointer may be NULL. */
+ * line length ny = R1 R2 in the other order; 6 and 7 = tiles of 8 and 16
+ * columns brought into shared memory by one tensor-memory-access copy per
+ * block (when the driver provides the tensor-map encoder).  With
+ * BFCS_AUTOTUNE the plan timed every variant valid for ny on its own buffers
+ * and kept the fastest (variant_ms: 8 doubles, ms per y forward + inverse
+ * pair, 0 = not timed); without it the variant is 0.  Any output pointer may
+ * be NULL. */
 int bfcs_plan_tuning(bfcs_plan plan, int* col_variant, int* col_tile, int* col_swap, double* variant_ms);
 
 /* Residual history of the last solve on the plan: copies min(cap, iters)

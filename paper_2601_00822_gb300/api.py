@@ -361,7 +361,7 @@ class Plan:
     def tuning(self):
         """bfcs_plan_tuning: dict(variant, tile, swap, variant_ms)."""
         v, t, sw = C.c_int(), C.c_int(), C.c_int()
-        ms = (C.c_double * 6)()
+        ms = (C.c_double * 8)()
         _lib.check(self.lib.bfcs_plan_tuning(self.handle, C.byref(v), C.byref(t), C.byref(sw), ms),
                    "bfcs_plan_tuning")
         return {"variant": v.value, "tile": t.value, "swap": bool(sw.value), "variant_ms": list(ms)}

@@ -447,7 +447,7 @@ struct Member {
 struct IterState {
   int done;          // 1 once r <= tol, the iteration stalled or diverged (later sweeps are no-ops)
   int iters;         // sweeps executed
-  int diverged;      // NaN/Inf seen
+  int diverged;      // 1: NaN/Inf seen; 2: a bounded device wait of one of its passes expired
   int stalled;       // no 10% drop of the residual over the stall window
   int stall_at;      // sweep of the last stall checkpoint
   int next_check;    // sweep whose residual is evaluated next (sparse evaluation; else every sweep)

@@ -8,6 +8,8 @@
 // (float-float arithmetic on FP64 fields, for the precision ladder).
 #include "kernels.h"
 
+#include <cuda.h>
+
 #ifndef BFCS_R
 #define BFCS_R float
 #endif
@@ -312,6 +314,103 @@ __global__ void __launch_bounds__(CCfg<L, T, SW>::THREADS, col_min_blocks<R, T>(
   }
 }
 
+// Column FFT along y with the tile loaded by the tensor memory accelerator: one
+// bulk tensor copy per block brings the T x L tile (T kx columns, all ny rows of
+// one (component, z) plane) into shared memory, completing on an mbarrier;
+// stage 1 then reads its rows there (in place, one barrier between the reads
+// and the writes) and stage 2 writes straight to global memory as k_colpass.
+// The tensor map (a 3D view of the 6-component spectra: floats along kx with
+// extent 2 mx, rows of pitch p, planes (member, component, z)) is built by the
+// plan; columns past mx read as zeros (out-of-bounds fill) and are not stored.
+// The wait is bounded: a copy that does not complete sets the member's fault
+// flag (IterState.diverged = 2, reported as a timeout) and the block returns.
+constexpr unsigned kTmaSpinLimit = 1u << 26;
+
+template <int L, int DIR, int T>
+__global__ void __launch_bounds__(CCfg<L, T, false>::THREADS, T == 8 ? 6 : 3)
+    k_colpass_tma(CArgs<float> a, const __grid_constant__ CUtensorMap tm) {
+  using R = float;
+  const int m = blockIdx.z;
+  if (a.st != nullptr && a.st[m].done) return;   // a member that has converged skips
+  constexpr int R1 = CCfg<L, T, false>::F1, R2 = CCfg<L, T, false>::F2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C2<R>* s = reinterpret_cast<C2<R>*>(smem_raw);   // [row][T], as the copy lands
+  __shared__ __align__(8) unsigned long long bar;
+  const int tid = threadIdx.x;
+  const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
+  const int plane = m * 6 * a.g.nz + blockIdx.y;   // (member, component, z) with blockIdx.y = comp * nz + z
+  const int kx0 = blockIdx.x * T;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar_a),
+                 "r"((unsigned)(L * T * sizeof(C2<R>)))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(2 * kx0), "r"(0), "r"(plane), "r"(bar_a)
+        : "memory");
+  }
+  unsigned done = 0, spins = 0;
+  while (!done) {
+    asm volatile(
+        "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(bar_a)
+        : "memory");
+    if (!done && ++spins > kTmaSpinLimit) break;
+  }
+  if (__syncthreads_or(!done)) {
+    // give the copy in flight a second bounded wait before the block leaves its buffer
+    for (unsigned k = 0; !done && k < kTmaSpinLimit; ++k)
+      asm volatile(
+          "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\nselp.u32 %0, 1, 0, q;\n}\n"
+          : "=r"(done)
+          : "r"(bar_a)
+          : "memory");
+    if (tid == 0 && a.st != nullptr) {
+      IterState* st = const_cast<IterState*>(a.st) + m;
+      atomicExch(&st->diverged, 2);
+      atomicExch(&st->done, 1);
+    }
+    return;
+  }
+  const int c = tid % T, j = tid / T;
+  const int kx = kx0 + c;
+  const bool valid = kx < a.g.mx;
+  const int ny = a.g.ny, p = a.g.p;
+  C2<R>* col = a.data + m * a.ms + (long long)blockIdx.y * ny * p + kx;
+  // stage 1 from the landed tile, in place: thread (c, j) owns rows R2 n1 + j
+  C2<R> x[R1];
+  if (j < R2) {
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) x[n1] = s[(R2 * n1 + j) * T + c];
+    stage1f<R, L, R1, DIR>(x, j, a.tw);
+  }
+  __syncthreads();
+  if (j < R2) {
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) s[(j * R1 + k1) * T + c] = x[k1];
+  }
+  __syncthreads();
+  // stage 2, outputs straight to global: thread (c, j) owns rows j + R1 k2
+  if (j < R1) {
+    C2<R> y[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) y[n2] = s[(n2 * R1 + j) * T + c];
+    stage2f<R, R2, DIR>(y);
+    if (valid) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) col[(long long)(j + R1 * k2) * p] = y[k2];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- dispatch
 template <typename R, int L>
 static cudaError_t xpass_L(const XArgs<R>& a, int batch, cudaStream_t st) {
@@ -367,8 +466,29 @@ static cudaError_t colpass_LT(const CArgs<R>& a, int batch, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int L, int DIR, int T>
+static cudaError_t colpass_tma_LT(const CArgs<float>& a, int batch, cudaStream_t st) {
+  dim3 grid((a.g.mx + T - 1) / T, a.g.nz * 6, batch);
+  const size_t smem = sizeof(C2<float>) * (size_t)L * T;
+  cudaError_t e = cudaFuncSetAttribute(k_colpass_tma<L, DIR, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_colpass_tma<L, DIR, T><<<grid, CCfg<L, T, false>::THREADS, smem, st>>>(
+      a, reinterpret_cast<const CUtensorMap*>(a.tmap)[T == 8 ? 0 : 1]);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template <typename R, int L, int DIR>
 static cudaError_t colpass_L(const CArgs<R>& a, int batch, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4 && L >= 32) {
+    // tensor-map tiles: only the sweep's y passes over 6-component spectra carry a map
+    if (col_variant_tma(a.variant)) {
+      const bool map = a.tmap != nullptr && a.axis == 1 && a.ncomp == 6 && a.ms == 6 * a.g.cs;
+      if (a.variant == 6) return map ? colpass_tma_LT<L, DIR, 8>(a, batch, st) : colpass_LT<R, L, DIR, 8, false>(a, batch, st);
+      return map ? colpass_tma_LT<L, DIR, 16>(a, batch, st) : colpass_LT<R, L, DIR, 16, false>(a, batch, st);
+    }
+  }
   if constexpr (sizeof(R) == 4 && L >= 32 && Fac<L>::R1 != Fac<L>::R2) {
     switch (a.variant) {
       case 1: return colpass_LT<R, L, DIR, 8, false>(a, batch, st);

@@ -475,6 +475,7 @@ cudaError_t launch_defect_final(const ResidSlot* part, int nparts, IterState* st
 bool col_variant_valid(int v, int n) {
   if (v == 0) return true;
   if (v < 0 || v >= kColVariants || n < 32 || !supported_len(n)) return false;
+  if (col_variant_tma(v)) return n <= 256;   // one box of n rows (a box edge is at most 256)
   if (!col_variant_swap(v)) return true;
   return n != 64 && n != 256;   // 64 = 8 x 8 and 256 = 16 x 16 have one order only
 }

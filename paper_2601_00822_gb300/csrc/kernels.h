@@ -67,13 +67,18 @@ template <typename R> struct CArgs {
   const IterState* st;    // nullable: member m = blockIdx.z skips once st[m].done
   long long ms;           // data stride between members (complex elements)
   int variant;            // FP32 only: column tile and factor order (kColVariants; 0 = default)
+  const void* tmap;       // host array of the two tensor maps (8, 16 columns) of a y pass over 6-component spectra, or null
 };
 
 // Column-pass variants an autotuner can pick from (FP32): tile width in kx
-// columns and the order of the two radices of the line length.
-constexpr int kColVariants = 6;
-constexpr int col_variant_tile(int v) { return v % 3 == 0 ? 16 : v % 3 == 1 ? 8 : 32; }
-constexpr bool col_variant_swap(int v) { return v >= 3; }
+// columns, the order of the two radices of the line length, and (6, 7) tiles
+// loaded by one tensor-memory-access copy per block (y passes of the sweep).
+constexpr int kColVariants = 8;
+constexpr int col_variant_tile(int v) {
+  return v == 6 ? 8 : v == 7 ? 16 : v % 3 == 0 ? 16 : v % 3 == 1 ? 8 : 32;
+}
+constexpr bool col_variant_swap(int v) { return v >= 3 && v < 6; }
+constexpr bool col_variant_tma(int v) { return v >= 6; }
 // whether variant v exists for line length n (only lengths with two different
 // radices have a swapped order; the tunable lengths are 32..256)
 bool col_variant_valid(int v, int n);

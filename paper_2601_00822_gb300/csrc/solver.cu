@@ -1,6 +1,7 @@
 // Host side of the C ABI: plans, the sweep driver of the modified basic scheme
 // (Algorithm 1) with device-side convergence flags and bounded host waits, the
 // batched and translated-averaging drivers (Eqs. 3.3-3.6) and the utilities.
+#include <cuda.h>
 #include "bfcs.h"
 #include "kernels.h"
 
@@ -78,7 +79,9 @@ struct bfcs_plan_s {
   IterState* cg_skip = nullptr;    // max_batch done flags for the FFT passes of A p
   CgState* cg_host = nullptr;      // pinned copy
   int col_variant = 0;             // y-pass tile / factor order of the FP32 sweeps (autotuned or default)
-  double col_variant_ms[kColVariants] = {0, 0, 0, 0, 0, 0};   // tuning times (ms per y forward+inverse pair)
+  double col_variant_ms[kColVariants] = {};   // tuning times (ms per y forward+inverse pair)
+  CUtensorMap tmap_y[2];           // FP32 spectra as a 3D tensor for the tensor-copy y passes (8, 16 columns)
+  bool tmap_ok = false;
 };
 
 namespace {
@@ -182,6 +185,40 @@ void free_plan(bfcs_plan P) {
   delete P;
 }
 
+// Tensor map of the plan's FP32 spectra for the tensor-copy y passes: floats
+// along kx (extent 2 mx: columns past mx read as zeros), rows of pitch p (ny),
+// planes (member, component, z) of ny p complex values; one box is 2T floats x
+// ny rows x 1 plane (T = 8 or 16 columns: 64 or 128 bytes, 16-byte multiples;
+// every tile starts at a multiple of 16 floats).  The encoder is reached through
+// the runtime, so the library does not link the driver library.  Returns false
+// (no tensor-copy variants) when it is unavailable or rejects the layout.
+bool encode_spectrum_map(bfcs_plan P) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  const Geo& g = P->g;
+  if (g.ny > 256 || g.ny < 32) return false;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    cudaGetLastError();
+    return false;
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * g.mx), (cuuint64_t)g.ny, (cuuint64_t)P->max_batch * 6 * g.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.p * sizeof(C2<float>), (cuuint64_t)g.ny * g.p * sizeof(C2<float>)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int k = 0; k < 2; ++k) {       // box widths of the two tile variants: 8 and 16 columns
+    const cuuint32_t box[3] = {k == 0 ? 16u : 32u, (cuuint32_t)g.ny, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(&P->tmap_y[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, P->spec, dims,
+                                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  return true;
+}
+
 // Autotuner of the FP32 sweep's y passes: every valid column-pass variant
 // (tile width, factor order) runs a y forward + inverse pair over the plan's
 // own spectrum buffer (max_batch members, zeroed), CUDA events on the plan's
@@ -201,11 +238,12 @@ int autotune(bfcs_plan P) {
   ca.ncomp = 6;
   ca.tw = (const C2<float>*)P->tw[1];
   ca.ms = 6 * P->g.cs;
+  ca.tmap = P->tmap_ok ? P->tmap_y : nullptr;
   double best = INFINITY;
   int bestv = 0, status = BFCS_OK;
   for (int v = 0; v < kColVariants && status == BFCS_OK; ++v) {
     P->col_variant_ms[v] = 0.0;
-    if (!col_variant_valid(v, P->g.ny)) continue;
+    if (!col_variant_valid(v, P->g.ny) || (col_variant_tma(v) && !P->tmap_ok)) continue;
     ca.variant = v;
     bool ok = true;
     for (int k = 0; k < 7 && ok; ++k) {
@@ -413,6 +451,7 @@ struct SweepSet {
     cy.axis = 1;
     cy.tw = (const C2<R>*)P->tw[1];
     cy.variant = P->col_variant;
+    cy.tmap = P->tmap_ok ? P->tmap_y : nullptr;
     xa.g = g;
     xa.spec_in = (C2<R>*)P->spec;
     xa.spec_out = (C2<R>*)P->spec;
@@ -533,7 +572,8 @@ struct SweepSet {
     for (int m = 0; m < B; ++m) {
       const IterState& h = hf[m];
       int status = BFCS_OK;
-      if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
+      if (h.diverged == 2) status = BFCS_ERR_TIMEOUT;     // a bounded device wait expired
+      else if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
       else if (tol > 0 && (!h.done || h.stalled)) status = BFCS_NOT_CONVERGED;
       if (infos != nullptr) {
         infos[m].iters = h.iters;
@@ -1622,11 +1662,12 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
     P->resid_max = kSparseResidMax;
     if (const char* ri = std::getenv("BFCS_RESID_INTERVAL")) P->resid_max = std::max(1, std::min(64, std::atoi(ri)));
   }
+  if (!P->fp64) P->tmap_ok = encode_spectrum_map(P);
   if (!P->fp64) {
     const char* cv = std::getenv("BFCS_COL_VARIANT");
     if (cv != nullptr) {
       const int v = std::atoi(cv);
-      P->col_variant = col_variant_valid(v, ny) ? v : 0;
+      P->col_variant = col_variant_valid(v, ny) && (!col_variant_tma(v) || P->tmap_ok) ? v : 0;
     } else if (flags & BFCS_AUTOTUNE) {
       const int e = autotune(P);
       if (e != BFCS_OK) { free_plan(P); return e; }
