@@ -202,6 +202,11 @@ int bfcs_body_force_noalloc(int nx, int ny, int nz, double cx, double cy, double
  * transform, R_hat = i xi.sigma_hat + b_hat), and while it exceeds tol an FP32 solve with load R
  * and E = 0 gives a correction added to the FP64 strain and displacement
  * (at most 8 rounds; maxit bounds the FP32 sweeps of all rounds together).
+ * The first round forms the FP64 strain as E + sym grad u from the FP64
+ * displacement.  With tol >= 1e-9 the later rounds evaluate the defect of the
+ * FP64 strain carried forward by adding each correction's FP32 strain (which
+ * keeps it equal to E + sym grad u to ~1e-10 of its norm); with tol < 1e-9
+ * every round re-forms it from the displacement.
  * info.resid is then that residual of the returned FP64 strain, and an
  * eps_init skips the first FP32 phase.  The FP32-only path cannot go below
  * its rounding floor (~1e-7 times the load's length scale in voxels).

@@ -89,6 +89,7 @@ namespace {
 int severity(int s) { return s < 0 ? 1000 - s : s; }
 
 constexpr int kHistCap = 1 << 14;   // residual history entries kept per member
+constexpr double kIncStrainTol = 1e-9;   // ladder: strain increments at or above this tolerance
 constexpr int kSparseResidMax = 8;  // BFCS_SPARSE_RESID: most sweeps between residual evaluations
 
 double wait_limit_s() {
@@ -1103,7 +1104,8 @@ int solve_group_impl(int n, const bfcs_group_item* items, int nph, const bfcs_la
 }
 
 // FP64 strain and defect from the FP64 displacements (precision ladder) of k
-// members in one launch per pass.  The passes compute in float-float (about
+// members in one launch per pass (from_eps: from the FP64 strains instead, see
+// below).  The passes compute in float-float (about
 // 48 bits, on the FP32 pipes) with float-float spectra; the real fields (u64
 // in, eps64 out) are FP64.  Slot j holds member idx[j]; dm[j] (host)
 // carries its phase, shift, E, the displacement u64 (as `b`, the real input
@@ -1113,13 +1115,41 @@ int solve_group_impl(int n, const bfcs_group_item* items, int nph, const bfcs_la
 // ist64[m].resid_final, and R_hat rounded to complex64 into the member's FP32
 // load spectrum (slot m of the plan's b_hat: the load of its correction
 // problem, already transformed).  eps64 goes to eps_out.
-int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTab<ff>& tab) {
+// from_eps: eps64 is already in dm[j].eps_init (FP64), the strain a previous
+// round returned plus the FP32 strain of the correction added since; sigma =
+// L eps64 and its transform are formed from it directly (the displacement
+// transforms, the symmetric gradient and their inverse are skipped) and no
+// strain is written.
+int defect_spectrum(bfcs_plan P, int k, const int* idx);
+int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTab<ff>& tab, bool from_eps) {
   const Geo g = P->g;
   cudaStream_t st = P->st;
   const long long sms = 6 * g.cs;
   C2<ff>* spec = (C2<ff>*)P->spec64;
   int e = upload_members(P, k, dm);
   if (e != BFCS_OK) return e;
+  CArgs<ff> ca{};
+  ca.data = spec;
+  ca.ms = sms;
+  ca.g = g;
+  if (from_eps) {
+    XArgs<ff> xs{};                                              // sigma = L eps64, R2C
+    xs.g = g;
+    xs.spec_out = spec;
+    xs.spec_ms = sms;
+    fill_xm(xs, dm, k, XIN_EPS_INIT, 0);
+    xs.tab = tab;
+    xs.tw = (const C2<ff>*)P->twff[0];
+    xs.ncomp = 6;
+    xs.mode = XM_REALSIG;
+    CK(launch_xpass_b<ff>(xs, k, st));
+    ca.ncomp = 6;
+    ca.axis = 1; ca.tw = (const C2<ff>*)P->twff[1];
+    CK(launch_colpass_b<ff>(ca, -1, k, st));                    // y forward
+    ca.axis = 2; ca.tw = (const C2<ff>*)P->twff[2];
+    CK(launch_colpass_b<ff>(ca, -1, k, st));                    // z forward
+    return defect_spectrum(P, k, idx);
+  }
   XArgs<ff> xa{};                                                // u_hat, x direction
   xa.g = g;
   xa.spec_out = spec;
@@ -1129,10 +1159,6 @@ int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTa
   xa.mode = XM_R2C;
   xa.tw = (const C2<ff>*)P->twff[0];
   CK(launch_xpass_b<ff>(xa, k, st));
-  CArgs<ff> ca{};
-  ca.data = spec;
-  ca.ms = sms;
-  ca.g = g;
   ca.ncomp = 3;
   ca.axis = 1; ca.tw = (const C2<ff>*)P->twff[1];
   CK(launch_colpass_b<ff>(ca, -1, k, st));
@@ -1157,6 +1183,17 @@ int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTa
   CK(launch_colpass_b<ff>(ca, -1, k, st));                      // y forward
   ca.axis = 2; ca.tw = (const C2<ff>*)P->twff[2];
   CK(launch_colpass_b<ff>(ca, -1, k, st));                      // z forward
+  return defect_spectrum(P, k, idx);
+}
+
+// R_hat = i xi . sigma_hat + b_hat64 of slot j's member idx[j] from the float-float
+// stress spectra in spec64 (slot-major), its residual into ist64, R_hat as complex64
+// into the member's slot of the plan's b_hat.
+int defect_spectrum(bfcs_plan P, int k, const int* idx) {
+  const Geo g = P->g;
+  cudaStream_t st = P->st;
+  const long long sms = 6 * g.cs;
+  C2<ff>* spec = (C2<ff>*)P->spec64;
   DArgs<ff> da{};
   da.spec = spec;
   da.spec_ms = sms;
@@ -1188,7 +1225,8 @@ int defect64(bfcs_plan P, int k, const Member* dm, const int* idx, const PhaseTa
 //  FP64 defect rounded to FP32, E = 0) together in one batched FP32 solve, each
 //  to its own relative tolerance 0.5 tol / r64 (at least switch_tol, so that no
 //  FP32 solve is asked to go near its rounding floor), and add the correction's
-//  displacement.
+//  displacement (and, at tol >= kIncStrainTol, its strain to eps64, from which
+//  the next round's defect is evaluated without re-forming eps64 from u64).
 int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_lame* phases, bfcs_lame C0,
                       double tol, int maxit, bfcs_info* infos) {
   int e = check_material(nph, phases, C0);
@@ -1220,6 +1258,11 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
   const PhaseTab<double> tab64 = make_tab<double>(nph, phases, C0);
   const PhaseTab<ff> tabff = make_tab<ff>(nph, phases, C0);
   const double zeroE[6] = {0, 0, 0, 0, 0, 0};
+  // Above kIncStrainTol the rounds after the first carry eps64 forward by adding
+  // each correction's FP32 strain (rounding ~6e-8 of an increment ~1e-3 of the
+  // strain, so eps64 stays compatible to ~1e-10) and evaluate the defect from it;
+  // below it every round re-forms eps64 = E + sym grad u64 exactly.
+  const bool inc_eps = tol >= kIncStrainTol;
   std::vector<int> sweeps(B, 0), stalled(B, 0), status(B, BFCS_OK);
   std::vector<double> r_last(B, INFINITY), r64(B, INFINITY);
   std::vector<char> fin(B, 0);
@@ -1286,12 +1329,16 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
       if (!fin[m]) act.push_back(m);
     if (act.empty()) break;
     mem.clear();
-    for (int m : act) {      // defect inputs: u64 as the real input, eps64 out
+    // defect inputs: u64 as the real input, eps64 out; after a correction with
+    // strain increments, eps64 (already updated) as the input
+    const bool from_eps = inc_eps && round > 0;
+    for (int m : act) {
       const auto sh = shift_of(m);
-      mem.push_back(make_member(in[m].phase, sh.data(), in[m].E, u64[m], nullptr,
-                                SolveOut{in[m].eps_out, nullptr, nullptr}));
+      mem.push_back(from_eps ? make_member(in[m].phase, sh.data(), in[m].E, nullptr, in[m].eps_out, SolveOut{})
+                             : make_member(in[m].phase, sh.data(), in[m].E, u64[m], nullptr,
+                                           SolveOut{in[m].eps_out, nullptr, nullptr}));
     }
-    e = defect64(P, (int)act.size(), mem.data(), act.data(), tabff);
+    e = defect64(P, (int)act.size(), mem.data(), act.data(), tabff, from_eps);
     if (e != BFCS_OK) return e;
     IterState* h64 = P->ist_host + 2 * P->max_batch;
     CK(read_small(h64, P->ist64, B * sizeof(IterState), st));
@@ -1315,7 +1362,8 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
         CK(cudaMemcpyAsync(bhat32 + (size_t)j * 3 * cs, bhat32 + (size_t)m * 3 * cs, 3 * cs * sizeof(C2<float>),
                            cudaMemcpyDeviceToDevice, st));
       const auto sh = shift_of(m);
-      Member c = make_member(in[m].phase, sh.data(), zeroE, nullptr, nullptr, SolveOut{nullptr, nullptr, u32(j)});
+      Member c = make_member(in[m].phase, sh.data(), zeroE, nullptr, nullptr,
+                             SolveOut{inc_eps ? eps32(j) : nullptr, nullptr, u32(j)});
       c.tol = std::min(0.5, std::max(0.5 * tol / r64[m], P->switch_tol));   // well above the FP32 floor
       mem.push_back(c);
       left = std::min(left, maxit - sweeps[m]);
@@ -1330,6 +1378,7 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
       sweeps[m] += inf[j].iters;
       stalled[m] = inf[j].stalled;
       CK(launch_add_f2d(u64[m], u32(j), 3 * n, st));
+      if (inc_eps) CK(launch_add_f2d((double*)in[m].eps_out, eps32(j), 6 * n, st));
     }
   }
   for (int m = 0; m < B; ++m)

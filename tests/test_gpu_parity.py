@@ -435,6 +435,33 @@ def test_mixed_ladder_defect_reaches_1e_12():
     assert r <= 2e-12, r
 
 
+@pytest.mark.parametrize("tol", [1e-6, 1e-9])
+@pytest.mark.parametrize("name", ["c1_32cubed", "aniso_12x32x24"])
+def test_mixed_strain_increments_keep_the_strain_compatible(name, tol):
+    """At tolerances of 1e-9 and above, the ladder's rounds after the first carry
+    the FP64 strain forward by each correction's FP32 strain instead of re-forming
+    it from the displacement.  The returned strain must still equal E + sym grad u
+    of the returned displacement (spectral, Eq. 2.3 with Eq. 4.8, through the
+    oracle's transforms) to 1e-9 of its norm.  It must meet the tolerance by the
+    oracle's own residual, and info.resid must be that residual (up to the
+    float-float arithmetic): the defect is still evaluated from the returned field."""
+    p = CASES[name]
+    ph_o, b_o = oracle_inputs(p)
+    ph, _ = gpu_inputs(p, "fp32")
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    with api.Plan(p.dims, "mixed") as plan:
+        eps, _, u, info = plan.solve(ph, p.phases, p.c0, b, E=p.mean_strain, tol=tol, maxit=6000)
+    assert info.status == _lib.OK and info.resid <= tol and info.precision_path == 2
+    e, uu = eps.cpu().numpy(), u.cpu().numpy()
+    xi = O.wavevectors(p.dims)
+    e_ref = np.real(O.ifft3(O.sym_grad_hat(O.fft3(uu), xi)))
+    e_ref += np.asarray(p.mean_strain, dtype=np.float64).reshape(6, 1, 1, 1)
+    assert rel(e, e_ref) < 1e-9, rel(e, e_ref)
+    r = O.residual(ph_o, p.phases, e, O.fft3(b_o), xi)
+    # float-float defect passes: ~48 bits relative to the stress scale, ~1e-15 of D absolute
+    assert r <= 1.05 * tol and abs(r - info.resid) <= 1e-4 * r + 1e-14, (r, info.resid)
+
+
 def test_mixed_batched_equals_individual_and_meets_tolerance():
     """The batched ladder (FP32 sweeps of all members in one launch per pass,
     FP64 defects per member) gives each member exactly the individual result;
