@@ -701,6 +701,60 @@ __global__ void k_green_dense(C2<R>* spec, const C2<R>* bhat, C2<R>* dprev, Geo 
   }
 }
 
+// Displacement of the last iterate without the final pass: eps^S = -Gamma0
+// tau^{S-1} + eps^{b(0)} has u_hat^S = i G0(xi) (d - i b_hat) / N with d = tau_hat^{S-1}
+// . xi, the d_prev the last sweep stored (Eqs. 2.9-2.10; 0 on the modes with xi = 0),
+// written into components 0..2 of the fully transformed spectrum.  Member
+// blockIdx.y at spec_ms, b_ms and d_ms; grid-stride over the stored modes.
+template <typename R>
+__global__ void k_uhat(GArgs<R> a) {
+  const int m = blockIdx.y;
+  const Geo g = a.g;
+  C2<R>* const spec = a.spec + m * a.spec_ms;
+  const C2<R>* const bhat = a.bhat + m * a.b_ms;
+  const C2<R>* const dprev = a.dprev + m * a.d_ms;
+  const R two_pi = R(6.283185307179586);
+  const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(g.nz);
+  const R inv_mu0 = recip(a.mu0), c0 = (a.lam0 + a.mu0) / (a.lam0 + R(2) * a.mu0);
+  const long long modes = (long long)g.nz * g.ny * g.mx;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < modes;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % g.mx);
+    const long long r = i / g.mx;
+    const int ky = (int)(r % g.ny), kz = (int)(r / g.ny);
+    const long long gi = r * g.p + kx;
+    R xi[3];
+    xi[0] = dk0 * R(signed_k(kx, g.nx));
+    xi[1] = dk1 * R(signed_k(ky, g.ny));
+    xi[2] = dk2 * R(signed_k(kz, g.nz));
+    const R qq = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    C2<R> u[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+    if (qq != R(0)) {
+      C2<R> w[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const C2<R> d = dprev[c * g.cs + gi], b = bhat[c * g.cs + gi];
+        w[c] = mk<R>(d.x + b.y, d.y - b.x);     // d - i b_hat
+      }
+      C2<R> v[3];
+      g0_apply<R>(w, xi, qq, inv_mu0, c0, v);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[c] = mk<R>(-v[c].y * a.inv_n, v[c].x * a.inv_n);   // i v / N
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) spec[c * g.cs + gi] = u[c];
+  }
+}
+
+template <typename R>
+cudaError_t launch_uhat(const GArgs<R>& a, int batch, cudaStream_t st) {
+  const long long modes = (long long)a.g.nz * a.g.ny * a.g.mx;
+  const int blocks = (int)std::min<long long>((modes + 255) / 256, 4 * 152);
+  k_uhat<R><<<dim3(blocks, batch), 256, 0, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // sum of the block partials in block order (deterministic) into *out
 static __global__ void k_sum_slots(const ResidSlot* part, int n, double* out) {
   __shared__ double red[32];
@@ -802,5 +856,6 @@ template cudaError_t launch_green_dense<BFCS_R>(C2<BFCS_R>*, const C2<BFCS_R>*, 
 #endif
 template cudaError_t launch_defect<BFCS_R>(const DArgs<BFCS_R>&, int, int, cudaStream_t);
 template cudaError_t launch_symgrad<BFCS_R>(C2<BFCS_R>*, long long, const Geo&, const Member*, int, cudaStream_t);
+template cudaError_t launch_uhat<BFCS_R>(const GArgs<BFCS_R>&, int, cudaStream_t);
 
 }  // namespace bfcs

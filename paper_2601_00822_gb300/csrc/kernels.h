@@ -195,6 +195,9 @@ template <typename R> int green_sweep_parts(const Geo& g);
 template <typename R> cudaError_t launch_xpass_b(const XArgs<R>& a, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_colpass_b(const CArgs<R>& a, int dir, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_zgreen_b(const GArgs<R>& a, int batch, cudaStream_t s);
+// u_hat^S = i G0(xi) (d_prev - i b_hat) / N into components 0..2 of a.spec for members
+// 0..batch-1 (the displacement of the last iterate from the d_prev its sweep stored)
+template <typename R> cudaError_t launch_uhat(const GArgs<R>& a, int batch, cudaStream_t s);
 
 // ---- nonlocal kernel regression (k_nonlocal.cu, FP64)
 constexpr int kNlMaxBasis = 8;      // Bernstein degree <= 7

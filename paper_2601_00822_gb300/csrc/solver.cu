@@ -528,9 +528,14 @@ struct SweepSet {
 
   // eps^S, sigma^S in real space; residual of eps^S; u^S; per-member infos.
   // On the plan's stream; ends with a bounded wait.
+  // u_only (no member wants sigma): eps^S by the x-direction C2R of the state and
+  // u^S from the d_prev of the last sweep (launch_uhat), without the final pass's
+  // forward transforms and residual; infos then report the last evaluated residual.
+  bool u_only = false;
   int finalize(bfcs_info* infos) {
     cudaStream_t st = P->st;
     const long long sms = 6 * P->g.cs;
+    if (u_only) return finalize_u(infos);
     xa.mode = XM_SWEEP;
     fill_xm(xa, P->mem_host, B, XIN_NONE, XOUT_EPS | XOUT_SIG);
     xa.st = nullptr;
@@ -554,6 +559,55 @@ struct SweepSet {
     xu.mode = XM_C2R;
     xu.tw = (const C2<R>*)P->tw[0];
     CK(launch_xpass_b<R>(xu, B, st));   // members without u_out write nothing
+    return report(infos);
+  }
+
+  int finalize_u(bfcs_info* infos) {
+    cudaStream_t st = P->st;
+    const long long sms = 6 * P->g.cs;
+    XArgs<R> xe{};
+    xe.g = P->g;
+    xe.spec_in = (C2<R>*)P->spec;
+    xe.spec_ms = sms;
+    xe.use_xm = 1;
+    bool any_eps = false;
+    for (int m = 0; m < B; ++m) {
+      XMember& x = xe.xm[m];
+      x.phase = P->mem_host[m].phase;
+      x.real_out = P->mem_host[m].eps_out;
+      any_eps = any_eps || x.real_out != nullptr;
+    }
+    xe.ncomp = 6;
+    xe.mode = XM_C2R;
+    xe.tw = (const C2<R>*)P->tw[0];
+    if (any_eps) CK(launch_xpass_b<R>(xe, B, st));      // eps^S, before u_hat overwrites the state
+    CK(launch_uhat<R>(ga, B, st));
+    CArgs<R> cz = cy;
+    cz.st = nullptr;
+    cz.axis = 2;
+    cz.ncomp = 3;
+    cz.tw = (const C2<R>*)P->tw[2];
+    cz.variant = 0;
+    cz.tmap = nullptr;
+    CK(launch_colpass_b<R>(cz, +1, B, st));             // z inverse
+    cy.st = nullptr;
+    cy.ncomp = 3;
+    CK(launch_colpass_b<R>(cy, +1, B, st));             // y inverse
+    XArgs<R> xu{};
+    xu.g = P->g;
+    xu.spec_in = (C2<R>*)P->spec;
+    xu.spec_ms = sms;
+    fill_xm(xu, P->mem_host, B, XIN_NONE, XOUT_U);
+    xu.ncomp = 3;
+    xu.mode = XM_C2R;
+    xu.tw = (const C2<R>*)P->tw[0];
+    CK(launch_xpass_b<R>(xu, B, st));
+    return report(infos);
+  }
+
+  // per-member infos from the device states (bounded wait)
+  int report(bfcs_info* infos) {
+    cudaStream_t st = P->st;
     IterState* hf = P->ist_host + 2 * P->max_batch;
     CK(read_small(hf, P->ist, B * sizeof(IterState), st));
     const int w = sync_stream(P);
@@ -573,13 +627,14 @@ struct SweepSet {
     for (int m = 0; m < B; ++m) {
       const IterState& h = hf[m];
       int status = BFCS_OK;
+      const double rf = u_only ? h.resid_last : h.resid_final;
       if (h.diverged == 2) status = BFCS_ERR_TIMEOUT;     // a bounded device wait expired
-      else if (h.diverged || !std::isfinite(h.resid_final)) status = BFCS_ERR_DIVERGED;
+      else if (h.diverged || (!u_only && !std::isfinite(rf))) status = BFCS_ERR_DIVERGED;
       else if (tol > 0 && (!h.done || h.stalled)) status = BFCS_NOT_CONVERGED;
       if (infos != nullptr) {
         infos[m].iters = h.iters;
         infos[m].status = status;
-        infos[m].resid = h.resid_final;
+        infos[m].resid = rf;
         infos[m].resid_prev = h.resid_last;
         infos[m].precision_path = sizeof(R) == 8 ? 1 : 0;
         infos[m].stalled = h.stalled;
@@ -890,9 +945,10 @@ int run_cg(SweepSet<R>& ss, std::vector<double>& req, int maxit, std::vector<int
 // halve the residual, then plain sweeps finish the job.
 template <typename R>
 int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const double* E0, double tol,
-              int maxit, bfcs_info* infos, bool any_warm) {
+              int maxit, bfcs_info* infos, bool any_warm, bool u_only = false) {
   SweepSet<R> ss;
   ss.prepare(P, B, tab, C0, E0, tol);
+  ss.u_only = u_only;
   int e = ss.init(any_warm);
   if (e != BFCS_OK) return e;
   std::vector<SweepSet<R>*> sets{&ss};
@@ -1314,8 +1370,9 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
   CK(launch_bden<float>(bhat32, g, P->part, P->ist, st, B, 3 * cs));
   e = upload_members(P, B, mem.data());
   if (e != BFCS_OK) return e;
+  // (the ladder's FP32 solves need the displacement and strain only: no final pass)
   const int s1 = run_batch<float>(P, B, tab32, C0, in[0].E, std::max(tol, P->switch_tol), maxit, inf.data(),
-                                  any_warm);
+                                  any_warm, true);
   if (s1 < 0) return s1;
   for (int m = 0; m < B; ++m) {
     sweeps[m] += inf[m].iters;
@@ -1371,7 +1428,7 @@ int solve_mixed_batch(bfcs_plan P, int B, const Member* in, int nph, const bfcs_
     CK(launch_bden<float>(bhat32, g, P->part, P->ist, st, k, 3 * cs));
     e = upload_members(P, k, mem.data());
     if (e != BFCS_OK) return e;
-    const int s2 = run_batch<float>(P, k, tab32, C0, zeroE, 0.5, std::max(left, 1), inf.data(), false);
+    const int s2 = run_batch<float>(P, k, tab32, C0, zeroE, 0.5, std::max(left, 1), inf.data(), false, true);
     if (s2 < 0) return s2;
     for (int j = 0; j < k; ++j) {
       const int m = next[j];
