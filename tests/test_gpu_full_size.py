@@ -1,4 +1,5 @@
-"""Parity at the benchmarked size: the 256^3 sweep kernels against the FP64 oracle.
+"""Parity at the benchmarked sizes: the 256^3 sweep kernels against the FP64 oracle,
+and the 128^3 batched translated averaging in its launch configuration.
 
 At 256^3 every line of the sweep has length 256, so these are the
 `k_xpass/k_colpass/k_zgreen<., 256>` instantiations in the launch configuration
@@ -143,3 +144,67 @@ def test_full_size_contrast_1000_converged_against_fp64():
     err_s = rel(sm.cpu().numpy(), s64.cpu().numpy())
     err_a = rel(am.cpu().numpy(), a64.cpu().numpy())
     assert max(err_e, err_s, err_a) < 1e-3, (err_e, err_s, err_a, im.iters, i64.iters)
+
+
+def test_full_size_translated_averaging_c3():
+    """C3 in the bench's launch configuration: 128^3 (8^3 cells of 16^3, one sphere
+    per cell, contrast 10), the 4^3 shift lattice in batches of 16 members.
+
+    (1) Three FP32 sweeps of a batch of 16 shifts: the first, a middle and the last
+        member against the oracle's Algorithm 1 (Eqs. 5.7-5.10) on the translated
+        phase map (Eq. 3.3) at the same sweep count.
+    (2) bfcs_translate_average over the same 16 shifts at the same sweep count
+        against the averages of Eqs. 3.4-3.6 written out here (FP64 sums of u, V u,
+        eps, V eps, sigma, V sigma over the members' fields from (1)) and the
+        inclusion hit counts.
+    (3) The bench's converged form (mixed ladder to 1e-6) of the average over the
+        first 16 shifts against an all-FP64 average to 1e-9: relative L2 below
+        contrast x tol = 1e-5 per field group."""
+    p = W.config_c3()
+    shifts = W.c3_shifts()[:16]
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    ph_o = O.phase_map(p.dims, p.cell, p.spheres)
+    assert np.array_equal(ph.cpu().numpy(), ph_o)
+    b32 = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp32")
+    b_o = O.body_force(p.dims, p.bf_centre, p.bf_radius)
+    with api.Plan(p.dims, "fp32", max_batch=16) as plan:
+        members = [dict(phase=ph, b=b32, shift=tuple(int(v) for v in chi)) for chi in shifts]
+        members, infos = plan.solve_batched(members, p.phases, p.c0, tol=0.0, maxit=SWEEPS)
+        assert all(i.iters == SWEEPS for i in infos)
+        avg, hits, _ = plan.translate_average(ph, p.phases, p.c0, b32, shifts, tol=0.0, maxit=SWEEPS)
+    for j in (0, 7, 15):
+        pj = O.translate(ph_o, shifts[j])
+        with sfft.set_workers(os.cpu_count() or 1):
+            ref = O.solve(pj, p.phases, p.c0, b_o, tol=0.0, maxit=SWEEPS)
+        for key, out in (("eps", "eps_out"), ("sig", "sig_out"), ("u", "u_out")):
+            err = rel(members[j][out].cpu().numpy(), ref[key])
+            assert err < TOL["fp32"], (j, key, err)
+    acc = np.zeros((30,) + ph_o.shape)
+    hit = np.zeros(ph_o.shape, dtype=np.int64)
+    for chi, m in zip(shifts, members):
+        v = (O.translate(ph_o, chi) != 0).astype(np.float64)
+        u, e, s = (m[k].cpu().numpy().astype(np.float64) for k in ("u_out", "eps_out", "sig_out"))
+        acc[0:3] += u
+        acc[3:6] += v * u
+        acc[6:12] += e
+        acc[12:18] += v * e
+        acc[18:24] += s
+        acc[24:30] += v * s
+        hit += v.astype(np.int64)
+    acc /= len(shifts)
+    assert np.array_equal(hits.cpu().numpy(), hit)
+    got = avg.cpu().numpy()
+    for lo, hi in ((0, 6), (6, 18), (18, 30)):
+        assert rel(got[lo:hi], acc[lo:hi]) < 1e-12, (lo, rel(got[lo:hi], acc[lo:hi]))
+    del members, avg, acc
+    b64 = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+    with api.Plan(p.dims, "fp64", max_batch=16) as plan:
+        a64, h64, i64 = plan.translate_average(ph, p.phases, p.c0, b64, shifts, tol=1e-9, maxit=20000)
+    assert all(i.status == _lib.OK for i in i64)
+    with api.Plan(p.dims, "mixed", max_batch=16) as plan:
+        am, hm, im = plan.translate_average(ph, p.phases, p.c0, b64, shifts, tol=p.tol, maxit=p.maxit)
+    assert all(i.status == _lib.OK and i.resid <= p.tol for i in im)
+    assert torch.equal(hm, h64)
+    a64, am = a64.cpu().numpy(), am.cpu().numpy()
+    for lo, hi in ((0, 6), (6, 18), (18, 30)):
+        assert rel(am[lo:hi], a64[lo:hi]) < 1e-5, (lo, rel(am[lo:hi], a64[lo:hi]))
