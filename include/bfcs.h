@@ -72,7 +72,7 @@ typedef struct {
   int status;           /* same value the call returned for this solve */
   double resid;         /* residual (Eq. 5.11 reading below) of the returned strain, FP64 */
   double resid_prev;    /* residual of the iterate that triggered the stop */
-  int precision_path;   /* 0 = FP32 sweeps, 1 = FP64 sweeps */
+  int precision_path;   /* 0 = FP32 sweeps, 1 = FP64 sweeps, 2 = BFCS_MIXED ladder (resid: float-float defect of the FP64 strain) */
   int stalled;          /* 1 if the residual did not drop by 10% over 100 sweeps (stops the solve) */
   double ms;            /* host wall time of the call, milliseconds */
 } bfcs_info;
