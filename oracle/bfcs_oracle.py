@@ -18,6 +18,8 @@ subjected to body force with compact support"):
     of the isotropic acoustic tensor.
   * Equilibrium residual, Eq. 5.11 (normalisation read as stated below).
   * Microstructure translation and translated averaging, Eqs. 3.3-3.7.
+  * Displacement-based conjugate gradients, Algorithm 3 (Eqs. 5.14-5.22), plain
+    as printed and with the reference medium's Green operator as preconditioner.
 
 Readings taken where the paper is silent or garbled (each is listed in the
 design notes of the repository):
@@ -35,6 +37,14 @@ design notes of the repository):
   R6  translated averages divide by the number of shifts (Eqs. 3.5-3.6 as
       printed), inclusion-weighted ones included; the hit count is returned.
   R7  translation: L(x, chi) = L0(x - chi) with b fixed (Eq. 3.3).
+  R18 Algorithm 3: the right-hand side of Eq. 5.14 is read with L1 = L - L0
+      (div L grad^s u1 = -div L1 eps^{b(0)}), the form that follows from Eqs.
+      2.10-2.13 and whose solution is that of Eq. 5.3 (with L it would drop the
+      body force); the operator is taken with the sign that makes it positive,
+      A(u) = -div L grad^s u, and b^A = div L1 eps^{b(0)}; the first iterate is
+      u1 = 0 (the printed u1 = b^A is a force, not a displacement); the CG
+      residual b^A - A(u1) is then exactly i xi . sigma_hat + b_hat, so the stop
+      test is the residual of Eq. 5.11 (reading R4), checked after each update.
 
 Loop convention shared with the GPU path: sweep s forms tau^s = L1 eps^s, its
 transform, the residual r(eps^s) and eps^{s+1}.  The solve stops after the
@@ -304,6 +314,86 @@ def solve(phase, table, c0, b, mean_strain=(0.0,) * 6, tol=1e-10, maxit=1000,
     sig = apply_local(phase, table, eps)
     u = displacement(eps, xi, lam0, mu0)
     out = dict(eps=eps, sig=sig, u=u, sweeps=sweeps, resid=r_final)
+    if history:
+        out["hist"] = hist
+    return out
+
+
+# ---------------------------------------------------------------- Algorithm 3
+def disp_operator(phase, table, u_hat, xi):
+    """A(u) = -i xi . F[L F^{-1}(sym(i xi (x) u_hat))]: the Fourier form of
+    -div L grad^s u (Eqs. 5.15-5.17, reading R18 for the sign); 3 components."""
+    eps = _real(sym_grad_hat(u_hat, xi), "A(u) strain")
+    return -div_hat(fft3(apply_local(phase, table, eps)), xi)
+
+
+def solve_cd(phase, table, c0, b, mean_strain=(0.0,) * 6, tol=1e-10, maxit=1000,
+             precondition=False, history=False):
+    """Displacement-based CG, Algorithm 3 (Eqs. 5.14-5.22), readings R18, R3, R4.
+
+    Unknown: the displacement fluctuation u1 of Eq. 2.10 (u = u^{b(0)} + u1) in
+    Fourier space; eps = eps^{b(0)} + grad^s u1, with the k = 0 mode of eps^{b(0)}
+    set to the mean strain E (R3).  Plain CG as printed; precondition=True applies
+    the reference medium's G0 (the inverse of -div L0 grad^s) to the residual.
+    Iteration j: alpha = (r.z)/(p.A p), u1 += alpha p, r -= alpha A p, z = M^-1 r,
+    beta = (r.z)_new/(r.z)_old, p = z + beta p; stop once r(eps^{j+1}) <= tol or
+    after maxit iterations.  Inner products over the full complex spectrum.
+    Returns dict(eps, sig, u, iters, resid, hist) like solve()."""
+    lam0, mu0 = c0
+    nz, ny, nx = phase.shape
+    dims = (nx, ny, nz)
+    n = nx * ny * nz
+    xi = wavevectors(dims)
+    b_hat = fft3(b)
+    eb0_hat = eps_b0_hat(b_hat, xi, lam0, mu0)
+    eb0_hat[:, 0, 0, 0] = n * np.asarray(mean_strain, dtype=float)   # reading R3
+    eb0 = _real(eb0_hat, "eps_b0")
+    table1 = [(l - lam0, m - mu0) for (l, m) in table]
+    bA = div_hat(fft3(apply_local(phase, table1, eb0)), xi)         # b^A = div L1 eps^{b(0)}
+
+    def precond(r):
+        return g0_apply(r, xi, lam0, mu0) if precondition else r
+
+    def dot(x, y):
+        return float(np.real(np.sum(np.conj(x) * y)))
+
+    def resid_of(r, u1_hat):
+        # Eq. 5.11 (reading R4): r = i xi . sigma_hat + b_hat on modes with xi != 0
+        q = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+        act = np.broadcast_to(q > 0, r.shape[1:])
+        num = np.sqrt(np.sum(np.abs(r[:, act]) ** 2))
+        eps = eb0 + _real(sym_grad_hat(u1_hat, xi), "eps")
+        s0 = fft3(apply_local(phase, table, eps))[:, 0, 0, 0]
+        s0n = np.sqrt(np.sum(np.abs(s0[:3]) ** 2) + 2.0 * np.sum(np.abs(s0[3:]) ** 2))
+        den = np.sqrt(np.sum(np.abs(b_hat[:, act]) ** 2)) + 2.0 * np.pi / max(dims) * s0n
+        return float(num / den) if den > 0 else float(num)
+
+    u1 = np.zeros_like(bA)                     # u1^[0] = 0 (reading R18)
+    r = bA.copy()                              # r^[0] = b^A - A(0)
+    z = precond(r)
+    p = z.copy()
+    rz = dot(r, z)
+    hist = [resid_of(r, u1)]
+    iters = 0
+    if hist[0] > tol:
+        for j in range(maxit):
+            q = disp_operator(phase, table, p, xi)
+            alpha = rz / dot(p, q)                                  # Eq. 5.18
+            u1 = u1 + alpha * p                                     # Eq. 5.19
+            r = r - alpha * q                                       # Eq. 5.20
+            z = precond(r)
+            rz_new = dot(r, z)
+            beta = rz_new / rz                                      # Eq. 5.21
+            p = z + beta * p                                        # Eq. 5.22
+            rz = rz_new
+            iters = j + 1
+            hist.append(resid_of(r, u1))
+            if hist[-1] <= tol:
+                break
+    eps = eb0 + _real(sym_grad_hat(u1, xi), "eps")
+    sig = apply_local(phase, table, eps)
+    u = displacement(eps, xi, lam0, mu0)
+    out = dict(eps=eps, sig=sig, u=u, iters=iters, resid=residual(phase, table, eps, b_hat, xi))
     if history:
         out["hist"] = hist
     return out

@@ -84,6 +84,16 @@ MUTATIONS = {
     "tikhonov_dropped": ("exact = np.linalg.solve(G + lam * np.eye(n), g)", "exact = np.linalg.solve(G, g)"),
     "stiffness_over_inclusions": ('Ls[:, J] = res["sig"].reshape(6, -1).mean(axis=1)',
                                   'Ls[:, J] = res["sig"][:, incl].mean(axis=1)'),
+    "cd_rhs_with_full_stiffness": ("bA = div_hat(fft3(apply_local(phase, table1, eb0)), xi)",
+                                   "bA = div_hat(fft3(apply_local(phase, table, eb0)), xi)"),
+    "cd_operator_sign": ("    return -div_hat(fft3(apply_local(phase, table, eps)), xi)",
+                         "    return div_hat(fft3(apply_local(phase, table, eps)), xi)"),
+    "cd_beta_of_old_residual": ("            beta = rz_new / rz                                      # Eq. 5.21",
+                                "            beta = rz / rz_new                                      # Eq. 5.21"),
+    "cd_residual_update_sign": ("            r = r - alpha * q                                       # Eq. 5.20",
+                                "            r = r + alpha * q                                       # Eq. 5.20"),
+    "cd_direction_from_unpreconditioned_residual": ("            p = z + beta * p                                        # Eq. 5.22",
+                                                    "            p = r + beta * p                                        # Eq. 5.22"),
 }
 
 

@@ -815,3 +815,153 @@ def test_kernel_fit_first_adam_step_is_minus_lr_sign_gradient():
     fit = O.kernel_fit([u], [gam], 2.0, 2, lam=0.5, iters=1, lr=0.1)
     grad0 = -2.0 * fit["g"]                                       # gradient at c = 0
     assert np.allclose(fit["coef"], -0.1 * np.sign(grad0), atol=1e-6)
+
+
+# ------------------------------------------------------------ Algorithm 3 (displacement-based CG)
+def test_cd_homogeneous_medium_is_the_reference_solution():
+    """L = L0 everywhere: b^A = div L1 eps^{b(0)} vanishes, so u1 = 0 and eps = eps^{b(0)}
+    (+ E) with no iteration, for the plain and the preconditioned forms."""
+    dims = (6, 8, 4)
+    nx, ny, nz = dims
+    c0 = (1.7, 0.9)
+    phase = RNG.integers(0, 2, size=(nz, ny, nx)).astype(np.int8)
+    b = drop_xi_zero(RNG.standard_normal((3, nz, ny, nx)))
+    E = tuple(0.01 * RNG.standard_normal(6))
+    xi = O.wavevectors(dims)
+    e0h = O.eps_b0_hat(O.fft3(b), xi, *c0)
+    e0h[:, 0, 0, 0] = nx * ny * nz * np.array(E)
+    for pc in (False, True):
+        res = O.solve_cd(phase, [c0, c0], c0, b, E, tol=1e-13, maxit=10, precondition=pc)
+        assert res["iters"] == 0 and res["resid"] < 1e-13
+        assert np.allclose(res["eps"], np.real(O.ifft3(e0h)), atol=1e-13)
+
+
+def test_cd_operator_on_a_plane_wave_is_the_navier_acoustic_tensor():
+    """Homogeneous (lam, mu): A(u) = -div L grad^s u of u = a cos(xi.x) is K(xi) a cos(xi.x)
+    with the acoustic tensor K_ik = mu |xi|^2 d_ik + (lam + mu) xi_i xi_k."""
+    dims = (8, 6, 4)
+    nx, ny, nz = dims
+    lam, mu = 1.3, 0.8
+    m = np.array([1, 2, 1])
+    xv = 2 * math.pi * m / np.array(dims)
+    a = np.array([0.4, -0.1, 0.7])
+    x = np.arange(nx)[None, None, :]
+    y = np.arange(ny)[None, :, None]
+    z = np.arange(nz)[:, None, None]
+    ph = xv[0] * x + xv[1] * y + xv[2] * z
+    u = np.stack([a[i] * np.cos(ph) for i in range(3)])
+    K = mu * (xv @ xv) * np.eye(3) + (lam + mu) * np.outer(xv, xv)
+    phase = np.zeros((nz, ny, nx), dtype=np.int8)
+    Au = np.real(O.ifft3(O.disp_operator(phase, [(lam, mu)], O.fft3(u), O.wavevectors(dims))))
+    Ka = K @ a
+    assert np.allclose(Au, np.stack([Ka[i] * np.cos(ph) for i in range(3)]), atol=1e-12)
+
+
+def _dense_system(dims, phase, table, c0, b, E):
+    """The displacement-based system of Algorithm 3 assembled from dense matrices of
+    the spectral gradient and divergence (unit-vector columns), independently of
+    the oracle's matrix-free operator: A = -Dv L Ds, u^b solving -Dv L0 Ds u^b = b,
+    eps^b = E + Ds u^b, b^A = Dv (L - L0) eps^b, and M = (-Dv L0 Ds)^+."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    Ds, Dv = _operators(dims)
+
+    def Lmat(lam, mu):
+        L = np.zeros((6 * n, 6 * n))
+        for c in range(6):
+            for p in range(n):
+                L[c * n + p, c * n + p] += 2 * mu[p]
+                if c < 3:
+                    for d in range(3):
+                        L[c * n + p, d * n + p] += lam[p]
+        return L
+
+    lam = np.array([t[0] for t in table])[phase].ravel()
+    mu = np.array([t[1] for t in table])[phase].ravel()
+    L = Lmat(lam, mu)
+    L0 = Lmat(np.full(n, c0[0]), np.full(n, c0[1]))
+    A = -Dv @ L @ Ds
+    A0 = -Dv @ L0 @ Ds
+    A0p = np.linalg.pinv(A0, rcond=1e-12)
+    ub = A0p @ b.ravel()
+    eb = np.concatenate([np.full(n, E[c]) for c in range(6)]) + Ds @ ub
+    bA = Dv @ ((L - L0) @ eb)
+    return A, A0p, bA, eb, Ds
+
+
+@pytest.mark.parametrize("precondition", [False, True])
+def test_cd_iterates_are_textbook_cg_on_the_dense_system(precondition):
+    """The oracle's Algorithm 3 after j iterations equals j steps of textbook (P)CG
+    from u1 = 0 on the dense system (the same inner product up to the DFT's factor
+    |N|, which cancels in alpha and beta): a wrong step length, sign, update order
+    or preconditioner changes the iterates at once."""
+    dims = (4, 4, 2)
+    nx, ny, nz = dims
+    r = np.random.default_rng(7)
+    phase = r.integers(0, 2, size=(nz, ny, nx)).astype(np.int8)
+    table = [(1.0, 0.5), (6.0, 3.0)]
+    c0 = (3.5, 1.75)
+    b = drop_xi_zero(r.standard_normal((3, nz, ny, nx)))
+    E = tuple(0.05 * r.standard_normal(6))
+    A, A0p, bA, eb, Ds = _dense_system(dims, phase, table, c0, b, E)
+    M = A0p if precondition else np.eye(A.shape[0])
+    u = np.zeros_like(bA)
+    res_ = bA.copy()
+    z = M @ res_
+    p = z.copy()
+    rz = res_ @ z
+    for j in range(1, 7):
+        q = A @ p
+        al = rz / (p @ q)
+        u = u + al * p
+        res_ = res_ - al * q
+        z = M @ res_
+        rz_new = res_ @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        got = O.solve_cd(phase, table, c0, b, E, tol=0.0, maxit=j, precondition=precondition)
+        assert got["iters"] == j
+        want = (eb + Ds @ u).reshape(6, nz, ny, nx)
+        assert np.allclose(got["eps"], want, atol=1e-10 * np.abs(want).max()), (j, precondition)
+
+
+@pytest.mark.parametrize("precondition", [False, True])
+def test_cd_converges_to_the_laminate_closed_form(precondition):
+    nx, ny, nz = 16, 2, 2
+    lam_ph = [1.0, 10.0]
+    mu_ph = [0.5, 5.0]
+    layers = np.array([0, 0, 1, 1, 1, 0, 0, 0, 1, 0, 1, 1, 0, 0, 1, 0], dtype=np.int8)
+    phase = np.broadcast_to(layers[None, None, :], (nz, ny, nx)).copy()
+    b1 = np.random.default_rng(3).standard_normal(nx)
+    bh = np.fft.fft(b1)
+    bh[0] = 0
+    bh[nx // 2] = 0
+    b1 = np.real(np.fft.ifft(bh))
+    b = np.zeros((3, nz, ny, nx))
+    b[0] = b1[None, None, :]
+    E = (0.02, 0, 0, 0, 0, 0)
+    table = list(zip(lam_ph, mu_ph))
+    res = O.solve_cd(phase, table, (5.5, 2.75), b, E, tol=1e-14, maxit=5000, precondition=precondition)
+    e11, s11 = laminate_exact(np.array(lam_ph)[layers], np.array(mu_ph)[layers], b1, E[0])
+    assert res["resid"] < 1e-13
+    assert np.allclose(res["eps"][0], e11[None, None, :], atol=1e-12)
+    assert np.allclose(res["eps"][1:], 0, atol=1e-12)
+    assert np.allclose(res["sig"][0], s11[None, None, :], atol=1e-11)
+
+
+def test_cd_residual_is_the_equilibrium_residual_and_matches_the_basic_scheme():
+    """The CG residual b^A - A(u1) is i xi . sigma_hat + b_hat (reading R18): its
+    history ends at the Eq. 5.11 residual of the returned field; both forms reach
+    the fixed point of Algorithm 1, the preconditioned one in far fewer iterations."""
+    dims, phase, table, c0 = _c1_small()
+    b = O.body_force(dims, (8.0, 8.0, 8.0), 5.0)
+    ref = O.solve(phase, table, c0, b, tol=1e-12, maxit=3000)
+    its = {}
+    for pc in (False, True):
+        res = O.solve_cd(phase, table, c0, b, tol=1e-12, maxit=5000, precondition=pc, history=True)
+        # (the recursive residual drifts from the true one by rounding: ~1e-16 of D per iteration)
+        assert res["resid"] <= 1.01e-12 and abs(res["hist"][-1] - res["resid"]) <= 1e-4 * res["resid"] + 1e-15
+        assert np.linalg.norm(res["eps"] - ref["eps"]) <= 1e-9 * np.linalg.norm(ref["eps"])
+        assert np.allclose(res["u"], ref["u"], atol=1e-9 * np.abs(ref["u"]).max())
+        its[pc] = res["iters"]
+    assert its[True] < ref["sweeps"] < its[False]
