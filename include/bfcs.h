@@ -59,6 +59,8 @@ extern "C" {
 #define BFCS_AUTOTUNE 4               /* OR-ed with FP32 or MIXED: time the y-pass variants at plan creation */
 #define BFCS_CG 8                     /* OR-ed with any precision: conjugate gradients (Algorithm 2) */
 #define BFCS_SPARSE_RESID 16          /* OR-ed with any precision: residual (Eq. 5.11) on predicted sweeps only */
+#define BFCS_CD 32                    /* OR-ed with any precision: displacement-based CG (Algorithm 3), as printed */
+#define BFCS_CD_PRECOND 64            /* as BFCS_CD, with the reference medium's G0 as preconditioner */
 
 #define BFCS_MAX_PHASES 16
 
@@ -103,6 +105,16 @@ typedef struct {
  *             in the C0-weighted norm, each verified by two sweeps of the
  *             residual of Eq. 5.11; info.iters counts operator applications;
  *             allocates four more strain spectra per member) and
+ *             BFCS_CD or BFCS_CD_PRECOND (the displacement-based conjugate
+ *             gradients of Algorithm 3, Eqs. 5.14-5.22, replace the sweeps:
+ *             the unknown is the displacement fluctuation u1 of Eq. 2.10 in
+ *             Fourier space, A(u1) = -div L grad^s u1 = div L1 eps^{b(0)}
+ *             (Eq. 5.14 read with L1 = L - L0 on the right), u1 starts at 0,
+ *             the CG residual is the equilibrium residual of Eq. 5.11, and
+ *             BFCS_CD_PRECOND applies the reference medium's G0 to it; info.iters
+ *             counts operator applications, info.resid is the residual of the
+ *             returned strain; an eps_init is rejected with INVALID_ARG; not
+ *             with BFCS_CG) and
  *             BFCS_SPARSE_RESID (the residual of Eq. 5.11 is evaluated on
  *             the first two sweeps and then on the sweep where the observed
  *             contraction rate predicts r <= tol, at most 8 sweeps apart;

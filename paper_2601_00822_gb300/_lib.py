@@ -27,6 +27,8 @@ MIXED = 2
 AUTOTUNE = 4
 CG = 8
 SPARSE_RESID = 16
+CD = 32
+CD_PRECOND = 64
 
 # every symbol declared in include/bfcs.h
 EXPORTS = (

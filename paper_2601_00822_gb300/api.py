@@ -89,7 +89,9 @@ class Plan:
     """bfcs_plan_create / bfcs_plan_destroy with the solver calls as methods."""
 
     def __init__(self, dims, precision="fp32", max_batch=1, stream=None, autotune=False, cg=False,
-                 sparse_resid=False):
+                 sparse_resid=False, cd=None):
+        """cd: None, or the displacement-based CG of Algorithm 3: "plain" (as printed,
+        BFCS_CD) or "g0" (preconditioned by the reference medium's G0, BFCS_CD_PRECOND)."""
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.precision = precision
@@ -103,6 +105,8 @@ class Plan:
             flag |= _lib.CG
         if sparse_resid:
             flag |= _lib.SPARSE_RESID
+        if cd is not None:
+            flag |= {"plain": _lib.CD, "g0": _lib.CD_PRECOND}[cd]
         nx, ny, nz = self.dims
         _lib.check(self.lib.bfcs_plan_create(C.byref(h), nx, ny, nz, int(max_batch), flag,
                                              _stream_ptr(self.stream)), "bfcs_plan_create")

@@ -34,6 +34,8 @@ UNITS = [
     ("k_green.cu", ["-DBFCS_R=ff", "-DBFCS_FF"], "k_green_ff.o"),
     ("k_cg.cu", ["-DBFCS_R=float"], "k_cg_f32.o"),
     ("k_cg.cu", ["-DBFCS_R=double"], "k_cg_f64.o"),
+    ("k_cd.cu", ["-DBFCS_R=float"], "k_cd_f32.o"),
+    ("k_cd.cu", ["-DBFCS_R=double"], "k_cd_f64.o"),
     ("k_misc.cu", [], "k_misc.o"),
     ("rve.cu", [], "rve.o"),
     ("k_nonlocal.cu", [], "k_nonlocal.o"),

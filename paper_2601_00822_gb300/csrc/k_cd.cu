@@ -1,0 +1,344 @@
+// Displacement-based conjugate gradients, Algorithm 3 (Eqs. 5.14-5.22): the
+// unknown is the displacement fluctuation u1 of Eq. 2.10 (u = u^{b(0)} + u1),
+// held as a fully transformed half spectrum of three components, and the system
+// is A(u1) = b^A with the positive operator A(u) = -i xi . F[L F^-1(sym(i xi (x)
+// u_hat))] and b^A = i xi . F[L1 eps^{b(0)}] (Eq. 5.14 with L1 = L - L0 on the
+// right, the form that follows from Eqs. 2.10-2.13).  The CG residual b^A - A(u1)
+// is then the equilibrium defect i xi . sigma_hat + b_hat of the strain
+// eps = eps^{b(0)} + grad^s u1, so the stop test is the residual of Eq. 5.11.
+// Optional preconditioner: the reference medium's G0 (the inverse of -div L0
+// grad^s), applied per mode.  Inner products run over the full spectrum: stored
+// modes weighted 1 at kx = 0 and kx = nx/2 and 2 elsewhere (Hermitian pairs);
+// per-mode products in the vectors' precision, sums in FP64.  Every kernel is
+// batched over members (blockIdx.y) and a finished member returns at entry; the
+// scalars alpha, beta, the residual and the stop test are formed on the device.
+#include "kernels.h"
+
+#ifndef BFCS_R
+#define BFCS_R float
+#endif
+
+namespace bfcs {
+
+constexpr int kCdThreads = 256;
+
+namespace {
+
+__device__ __forceinline__ double cd_reduce(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// v = G0(xi) w: the inverse of the isotropic acoustic tensor mu0 |xi|^2 I + (lam0 +
+// mu0) xi xi (Eqs. 2.6, 2.8), per mode
+template <typename R>
+__device__ __forceinline__ void cd_g0(const C2<R> (&w)[3], const R (&xi)[3], R qq, R lam0, R mu0, C2<R> (&v)[3]) {
+  const R iq = R(1) / qq;
+  const R c = (lam0 + mu0) / (lam0 + R(2) * mu0);
+  const C2<R> xw = scale(w[0], xi[0]) + scale(w[1], xi[1]) + scale(w[2], xi[2]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = scale(w[k] - scale(xw, c * xi[k] * iq), iq / mu0);
+}
+
+// sym(i xi (x) v) in 6-component storage (xx yy zz yz xz xy), times f
+template <typename R>
+__device__ __forceinline__ void cd_symgrad(const C2<R> (&v)[3], const R (&xi)[3], R f, C2<R> (&e)[6]) {
+  auto ih = [&](C2<R> a, R s) { return mk<R>(-a.y * s, a.x * s); };   // i a s
+  const R h = R(0.5) * f;
+  e[0] = ih(scale(v[0], xi[0]), f);
+  e[1] = ih(scale(v[1], xi[1]), f);
+  e[2] = ih(scale(v[2], xi[2]), f);
+  e[3] = ih(scale(v[2], xi[1]) + scale(v[1], xi[2]), h);
+  e[4] = ih(scale(v[2], xi[0]) + scale(v[0], xi[2]), h);
+  e[5] = ih(scale(v[1], xi[0]) + scale(v[0], xi[1]), h);
+}
+
+// i xi . s for a symmetric tensor s in 6-component storage
+template <typename R>
+__device__ __forceinline__ void cd_div(const C2<R> (&s)[6], const R (&xi)[3], C2<R> (&d)[3]) {
+  const C2<R> v0 = scale(s[0], xi[0]) + scale(s[5], xi[1]) + scale(s[4], xi[2]);
+  const C2<R> v1 = scale(s[5], xi[0]) + scale(s[1], xi[1]) + scale(s[3], xi[2]);
+  const C2<R> v2 = scale(s[4], xi[0]) + scale(s[3], xi[1]) + scale(s[2], xi[2]);
+  d[0] = mk<R>(-v0.y, v0.x);
+  d[1] = mk<R>(-v1.y, v1.x);
+  d[2] = mk<R>(-v2.y, v2.x);
+}
+
+template <typename R>
+__device__ __forceinline__ R cd_dot3(const C2<R> (&a)[3], const C2<R> (&b)[3]) {
+  R s = R(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s += a[k].x * b[k].x + a[k].y * b[k].y;
+  return s;
+}
+
+}  // namespace
+
+// Modes (CdMode):
+//  INIT:    r = b^A = i xi . s (s: F[L1 eps^{b(0)}], 6 components), u = 0, z = M r;
+//           partials <r, z>, <r, r>; the k = 0 thread stores s(0) in cd.s0b
+//  PQ:      q = -i xi . s (s: F[L grad^s p]); partial <p, q>; s(0) into cd.s0p
+//  UPDATE:  u += alpha p, r -= alpha q, z = M r; partials <r, z>, <r, r>
+//  DIR:     p = z + beta p, s = sym(i xi (x) p) / N (6 components; 0 where xi = 0)
+//  FINAL:   s = sym(i xi (x) (G0 b_hat + u)) / N, s(0) = E (the returned strain)
+//  FINAL_U: s = (G0 b_hat + u) / N in components 0..2 (the returned displacement)
+//  RESID:   partial |i xi . s + b_hat|^2 over xi != 0 (s: F[L eps]); s(0) into cd.s0u
+template <typename R>
+__global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
+  const int m = blockIdx.y;
+  const bool all = mode == CdMode::FINAL || mode == CdMode::FINAL_U || mode == CdMode::RESID;
+  if (!all && a.cd[m].done) return;
+  __shared__ double red[32];
+  const Geo g = a.g;
+  C2<R>* const u = a.u + m * a.ms;
+  C2<R>* const r = a.r + m * a.ms;
+  C2<R>* const z = a.z + m * a.ms;
+  C2<R>* const p = a.p + m * a.ms;
+  C2<R>* const q = a.q + m * a.ms;
+  C2<R>* const s = a.s + m * a.sms;
+  const C2<R>* const bh = a.bhat + m * a.b_ms;
+  const R alpha = (R)a.cd[m].alpha, beta = (R)a.cd[m].beta;
+  const R lam0 = (R)a.lam0, mu0 = (R)a.mu0;
+  const R inv_n = R(1.0 / (double)g.n);
+  const R two_pi = R(6.283185307179586);
+  const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(g.nz);
+  const long long modes = (long long)g.nz * g.ny * g.mx;
+  double acc1 = 0.0, acc2 = 0.0;
+  // 32-bit index arithmetic: a member's spectrum has at most 256 * 256 * 129 modes
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)modes; i += gridDim.x * blockDim.x) {
+    const int kx = i % g.mx;
+    const int rr = i / g.mx;
+    const int ky = rr % g.ny, kz = rr / g.ny;
+    const long long gi = (long long)rr * g.p + kx;
+    const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
+    R xi[3];
+    xi[0] = dk0 * R(signed_k(kx, g.nx));
+    xi[1] = dk1 * R(signed_k(ky, g.ny));
+    xi[2] = dk2 * R(signed_k(kz, g.nz));
+    const R qq = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    const bool nz = qq != R(0);
+    auto ld3 = [&](const C2<R>* v, C2<R> (&o)[3]) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o[k] = v[k * g.cs + gi];
+    };
+    auto st3 = [&](C2<R>* v, const C2<R> (&o)[3]) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[k * g.cs + gi] = o[k];
+    };
+    auto ld6 = [&](C2<R> (&o)[6]) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) o[k] = s[k * g.cs + gi];
+    };
+    auto precond = [&](const C2<R> (&x)[3], C2<R> (&y)[3]) {
+      if (a.precond && nz) {
+        cd_g0<R>(x, xi, qq, lam0, mu0, y);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) y[k] = a.precond ? mk<R>(0, 0) : x[k];
+      }
+    };
+    if (mode == CdMode::INIT) {
+      C2<R> t[6], rv[3], zv[3];
+      ld6(t);
+      if (i == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.cd[m].s0b[k] = (double)t[k].x;
+      }
+      cd_div<R>(t, xi, rv);
+      if (!nz) rv[0] = rv[1] = rv[2] = mk<R>(0, 0);
+      precond(rv, zv);
+      const C2<R> zero[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+      st3(r, rv);
+      st3(z, zv);
+      st3(p, zv);      // p = z (DIR then forms the operator input with beta = 0)
+      st3(u, zero);
+      acc1 += w * (double)cd_dot3<R>(rv, zv);
+      acc2 += w * (double)cd_dot3<R>(rv, rv);
+    } else if (mode == CdMode::PQ) {
+      C2<R> t[6], qv[3], pv[3];
+      ld6(t);
+      if (i == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.cd[m].s0p[k] = (double)t[k].x;
+      }
+      cd_div<R>(t, xi, qv);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) qv[k] = nz ? mk<R>(-qv[k].x, -qv[k].y) : mk<R>(0, 0);
+      st3(q, qv);
+      ld3(p, pv);
+      acc1 += w * (double)cd_dot3<R>(pv, qv);
+    } else if (mode == CdMode::UPDATE) {
+      C2<R> uv[3], pv[3], rv[3], qv[3], zv[3];
+      ld3(u, uv);
+      ld3(p, pv);
+      ld3(r, rv);
+      ld3(q, qv);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        uv[k] = uv[k] + scale(pv[k], alpha);
+        rv[k] = rv[k] - scale(qv[k], alpha);
+      }
+      precond(rv, zv);
+      st3(u, uv);
+      st3(r, rv);
+      st3(z, zv);
+      acc1 += w * (double)cd_dot3<R>(rv, zv);
+      acc2 += w * (double)cd_dot3<R>(rv, rv);
+    } else if (mode == CdMode::DIR) {
+      C2<R> pv[3], zv[3], e[6];
+      ld3(p, pv);
+      ld3(z, zv);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pv[k] = zv[k] + scale(pv[k], beta);
+      st3(p, pv);
+      cd_symgrad<R>(pv, xi, inv_n, e);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s[k * g.cs + gi] = nz ? e[k] : mk<R>(0, 0);
+    } else if (mode == CdMode::FINAL || mode == CdMode::FINAL_U) {
+      C2<R> uv[3], bv[3], gb[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+      ld3(u, uv);
+      ld3(bh, bv);
+      if (nz) cd_g0<R>(bv, xi, qq, lam0, mu0, gb);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) uv[k] = uv[k] + gb[k];      // u_hat = G0 b_hat + u1_hat (Eqs. 2.8, 2.10)
+      if (mode == CdMode::FINAL_U) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s[k * g.cs + gi] = nz ? scale(uv[k], inv_n) : mk<R>(0, 0);
+      } else {
+        C2<R> e[6];
+        cd_symgrad<R>(uv, xi, inv_n, e);
+        const double* E = a.mem[m].E;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          s[k * g.cs + gi] = nz ? e[k] : (i == 0 ? mk<R>((R)E[k], R(0)) : mk<R>(0, 0));
+      }
+    } else {   // RESID
+      C2<R> t[6], d[3], bv[3];
+      ld6(t);
+      if (i == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.cd[m].s0u[k] = (double)t[k].x;
+      }
+      if (nz) {
+        cd_div<R>(t, xi, d);
+        ld3(bh, bv);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = d[k] + bv[k];
+        acc1 += w * (double)cd_dot3<R>(d, d);
+      }
+    }
+  }
+  if (mode == CdMode::DIR || mode == CdMode::FINAL || mode == CdMode::FINAL_U) return;
+  const double t1 = cd_reduce(acc1, red);
+  const double t2 = cd_reduce(acc2, red);
+  if (threadIdx.x == 0) {
+    a.part[((long long)m * gridDim.x + blockIdx.x) * 2] = t1;
+    a.part[((long long)m * gridDim.x + blockIdx.x) * 2 + 1] = t2;
+  }
+}
+
+// |sigma_hat(0)|_F with shear components counted twice (Eq. 5.11 normaliser)
+__device__ __forceinline__ double cd_s0norm(const double (&s)[6]) {
+  return sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]));
+}
+
+// Per member: sums its partials in a fixed order and advances its scalars.
+//  INIT:   rz = <r, z>; residual of eps^{b(0)} (sigma_hat(0) = s0b + N L0 E); done at
+//          r <= tol or maxit = 0
+//  PQ:     alpha = rz / <p, A p> (a non-positive <p, A p> ends the member: breakdown)
+//  UPDATE: beta = <r, z>_new / rz; s0u += alpha s0p; iterations + 1; residual from
+//          <r, r>; done at r <= tol, NaN or the iteration limit
+//  RESID:  the residual of the returned strain into resid_final
+// The skip flags of the FFT passes follow done; the member's IterState receives the
+// iteration count, residuals and status fields read by the host.
+static __global__ void k_cd_scalar(const double* part, int nparts, CdState* cd, IterState* skip, IterState* ist,
+                                   const Member* mem, double lam0, double mu0, double n, int maxdim, int mode) {
+  __shared__ double red[32];
+  const int m = blockIdx.x;
+  CdState& S = cd[m];
+  if (mode != CdMode::RESID && S.done) return;
+  double a1 = 0.0, a2 = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    a1 += part[((long long)m * nparts + i) * 2];
+    a2 += part[((long long)m * nparts + i) * 2 + 1];
+  }
+  const double t1 = cd_reduce(a1, red);
+  const double t2 = cd_reduce(a2, red);
+  if (threadIdx.x != 0) return;
+  IterState& st = ist[m];
+  const double xmin = 6.283185307179586 / (double)maxdim;
+  auto resid = [&](const double (&s0)[6], double rr) {
+    const double den = st.bden + xmin * cd_s0norm(s0);
+    return den > 0.0 ? sqrt(rr) / den : sqrt(rr);
+  };
+  bool fin = false;
+  if (mode == CdMode::INIT) {
+    const double* E = mem[m].E;
+    const double trE = E[0] + E[1] + E[2];
+    for (int k = 0; k < 6; ++k) {
+      // sigma_hat(0) of L eps^{b(0)} = F[L1 eps^{b(0)}](0) + N L0 E
+      S.s0b[k] += n * ((k < 3 ? lam0 * trE : 0.0) + 2.0 * mu0 * E[k]);
+      S.s0u[k] = 0.0;
+    }
+    S.rz = t1;
+    S.iters = 0;
+    S.beta = 0.0;
+    S.resid = resid(S.s0b, t2);
+    st.resid_last = S.resid;
+    if (!(S.resid == S.resid)) { S.status = 3; fin = true; }
+    else if (S.resid <= S.tol) { S.status = 1; fin = true; }
+    else if (S.maxit <= 0) { S.status = 2; fin = true; }
+  } else if (mode == CdMode::PQ) {
+    if (t1 > 0.0 && t1 == t1) {
+      S.alpha = S.rz / t1;
+    } else {
+      S.status = 3;
+      fin = true;
+    }
+  } else if (mode == CdMode::UPDATE) {
+    S.beta = S.rz > 0.0 ? t1 / S.rz : 0.0;
+    S.rz = t1;
+    for (int k = 0; k < 6; ++k) S.s0u[k] += S.alpha * S.s0p[k];
+    S.iters += 1;
+    double s0[6];
+    for (int k = 0; k < 6; ++k) s0[k] = S.s0b[k] + S.s0u[k];
+    S.resid = resid(s0, t2);
+    st.resid_last = S.resid;
+    if (!(S.resid == S.resid)) { S.status = 3; fin = true; }
+    else if (S.resid <= S.tol) { S.status = 1; fin = true; }
+    else if (S.iters >= S.maxit) { S.status = 2; fin = true; }
+  } else {   // RESID: the true residual of the returned strain (s0u holds its sigma_hat(0))
+    st.resid_final = resid(S.s0u, t1);
+    st.iters = S.iters;
+    st.done = S.status == 1 ? 1 : 0;
+    st.diverged = S.status == 3 ? 1 : 0;
+    return;
+  }
+  if (fin) {
+    S.done = 1;
+    skip[m].done = 1;
+  }
+}
+
+template <typename R>
+cudaError_t launch_cd_vec(const CdArgs<R>& a, int mode, int batch, IterState* ist, const Member* mem, int maxdim,
+                          cudaStream_t st) {
+  k_cd_vec<R><<<dim3(kCdParts, batch), kCdThreads, 0, st>>>(a, mode);
+  count_launches(1);
+  if (mode == CdMode::DIR || mode == CdMode::FINAL || mode == CdMode::FINAL_U) return cudaGetLastError();
+  k_cd_scalar<<<batch, kCdThreads, 0, st>>>(a.part, kCdParts, a.cd, a.skip, ist, mem, a.lam0, a.mu0,
+                                            (double)a.g.n, maxdim, mode);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_cd_vec<BFCS_R>(const CdArgs<BFCS_R>&, int, int, IterState*, const Member*, int,
+                                           cudaStream_t);
+
+}  // namespace bfcs

@@ -111,6 +111,44 @@ template <typename R> struct CgArgs {
 // convergence), 3 DIR (p = r + beta p); the scalar step follows modes 0-2.
 template <typename R> cudaError_t launch_cg_vec(const CgArgs<R>& a, int mode, int batch, cudaStream_t st);
 
+// ---- displacement-based conjugate gradients, Algorithm 3 (k_cd.cu)
+struct CdMode { enum : int { INIT = 0, PQ = 1, UPDATE = 2, DIR = 3, FINAL = 4, FINAL_U = 5, RESID = 6 }; };
+struct CdState {
+  double rz;             // <r, z> (<r, r> without preconditioner)
+  double alpha, beta;
+  double s0b[6];         // sigma_hat(0) of L eps^{b(0)} (DFT scale)
+  double s0u[6];         // sigma_hat(0) of L grad^s u1 (after RESID: of the returned strain)
+  double s0p[6];         // sigma_hat(0) of L grad^s p (this iteration)
+  double tol;            // stop at residual <= tol (Eq. 5.11)
+  double resid;          // residual of the current iterate
+  int done, iters, maxit;
+  int status;            // 0 running, 1 converged, 2 iteration limit, 3 breakdown or NaN
+};
+constexpr int kCdParts = 512;       // partial sums (pairs) per member
+template <typename R> struct CdArgs {
+  C2<R>* u;              // u1_hat (3 components, fully transformed half spectrum)
+  C2<R>* r;              // residual b^A - A(u1)
+  C2<R>* z;              // preconditioned residual (r itself without preconditioner)
+  C2<R>* p;              // search direction
+  C2<R>* q;              // A p
+  C2<R>* s;              // 6-component work spectrum (operator input and output)
+  const C2<R>* bhat;     // body force spectrum (3 components)
+  long long ms, sms, b_ms;   // member strides of the vectors, of s and of bhat
+  Geo g;
+  double lam0, mu0;
+  double* part;          // 2 x kCdParts doubles per member
+  CdState* cd;
+  IterState* skip;       // done flags read by the FFT passes of A p
+  const Member* mem;     // per-member mean strain (FINAL)
+  int precond;           // 1: z = G0 r
+};
+// the vector step `mode` for members 0..batch-1, then (INIT, PQ, UPDATE, RESID)
+// the scalar step; ist: the members' IterState (bden read; iterations, residuals,
+// status written)
+template <typename R>
+cudaError_t launch_cd_vec(const CdArgs<R>& a, int mode, int batch, IterState* ist, const Member* mem, int maxdim,
+                          cudaStream_t st);
+
 // ---- fused z pass: forward z FFT -> Green operators -> residual -> inverse z FFT.
 enum GMode : int {
   GM_SWEEP = 0,   // eps_hat^{s+1} = -Gamma0 tau_hat^s + eps_hat^{b(0)}, k=0 <- E; residual of eps^s

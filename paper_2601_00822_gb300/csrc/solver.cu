@@ -73,6 +73,11 @@ struct bfcs_plan_s {
   double switch_tol = 1e-4;        // FP32 phase stops here (or at the stall)
   bfcs_net net = nullptr;          // inference context of bfcs_surrogate_infer (created on first use)
   bool use_cg = false;             // BFCS_CG: conjugate gradients (Algorithm 2) drive the sweeps
+  bool use_cd = false;             // BFCS_CD / BFCS_CD_PRECOND: displacement-based CG (Algorithm 3)
+  int cd_precond = 0;              // 1: G0 preconditioner (BFCS_CD_PRECOND)
+  double* cd_part = nullptr;       // 2 x kCdParts per member
+  CdState* cd_state = nullptr;     // max_batch
+  CdState* cd_host = nullptr;      // pinned
   void* cg_vec = nullptr;          // c, r, p, q: 4 x max_batch x 6 x cs complex (sweep precision)
   double* cg_part = nullptr;       // kCgParts per member
   CgState* cg_state = nullptr;     // max_batch
@@ -182,6 +187,8 @@ void free_plan(bfcs_plan P) {
   if (P->order_ev[1]) cudaEventDestroy(P->order_ev[1]);
   if (P->net) bfcs_net_destroy(P->net);
   cudaFree(P->cg_vec); cudaFree(P->cg_part); cudaFree(P->cg_state); cudaFree(P->cg_skip);
+  cudaFree(P->cd_part); cudaFree(P->cd_state);
+  if (P->cd_host) cudaFreeHost(P->cd_host);
   if (P->cg_host) cudaFreeHost(P->cg_host);
   delete P;
 }
@@ -936,6 +943,135 @@ int run_cg(SweepSet<R>& ss, std::vector<double>& req, int maxit, std::vector<int
   return BFCS_OK;
 }
 
+// Displacement-based CG (Algorithm 3) for the B members of ss, after its init()
+// (state: eps^{b(0)} + E, x transformed).  b^A = i xi . F[L1 eps^{b(0)}] comes from
+// one x pass (polarization) and the forward y and z passes; every iteration
+// applies the operator to p with the strain spectrum sym(i xi (x) p) / N (the
+// direction step writes it), the inverse z and y passes, the x pass that forms
+// sigma = L eps and transforms it forward, the forward y and z passes and the
+// divergence (PQ step), then updates u1, r and z (UPDATE) and p (DIR).  The host
+// reads the members' states after chunks of iterations.  Finally the strain
+// eps^{b(0)} + grad^s u1 and the displacement u^{b(0)} + u1 are transformed back
+// (with sigma = L eps when wanted) and the residual of Eq. 5.11 of the returned
+// strain is formed.  A warm start is not taken (Algorithm 3 starts from u1 = 0).
+template <typename R>
+int run_cd(SweepSet<R>& ss, int maxit, bfcs_info* infos) {
+  bfcs_plan P = ss.P;
+  const int B = ss.B;
+  cudaStream_t st = P->st;
+  const Geo g = P->g;
+  const long long vs = 3 * g.cs;
+  const long long vstride = (long long)P->max_batch * vs;
+  C2<R>* base = (C2<R>*)P->cg_vec;                 // 5 x max_batch x 3 cs of the 4 x max_batch x 6 cs
+  CdArgs<R> a{};
+  a.u = base;
+  a.r = base + vstride;
+  a.p = base + 2 * vstride;
+  a.q = base + 3 * vstride;
+  a.z = P->cd_precond ? base + 4 * vstride : a.r;
+  a.s = (C2<R>*)P->spec;
+  a.ms = vs;
+  a.sms = 6 * g.cs;
+  a.bhat = (const C2<R>*)P->bhat;
+  a.b_ms = 3 * g.cs;
+  a.g = g;
+  a.lam0 = ss.C0.lambda;
+  a.mu0 = ss.C0.mu;
+  a.part = P->cd_part;
+  a.cd = P->cd_state;
+  a.skip = P->cg_skip;
+  a.mem = P->mem_dev;
+  a.precond = P->cd_precond;
+  const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
+  for (int m = 0; m < B; ++m) {
+    CdState& h = P->cd_host[m];
+    h = CdState{};
+    h.tol = P->mem_host[m].tol >= 0 ? P->mem_host[m].tol : ss.tol;
+    h.maxit = maxit;
+  }
+  CK(cudaMemcpyAsync(P->cd_state, P->cd_host, B * sizeof(CdState), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(P->cg_skip, 0, B * sizeof(IterState), st));
+  // b^A from the state eps^{b(0)} (+ E): tau = L1 eps, forward x, y, z
+  XArgs<R> xa = ss.xa;
+  xa.mode = XM_SWEEP;
+  fill_xm(xa, P->mem_host, B, XIN_NONE, 0);
+  xa.st = nullptr;
+  CK(launch_xpass_b<R>(xa, B, st));
+  CArgs<R> cy = ss.cy;
+  cy.st = nullptr;
+  cy.ncomp = 6;
+  CArgs<R> cz = ss.cy;
+  cz.st = nullptr;
+  cz.axis = 2;
+  cz.ncomp = 6;
+  cz.tw = (const C2<R>*)P->tw[2];
+  cz.variant = 0;
+  cz.tmap = nullptr;
+  CK(launch_colpass_b<R>(cy, -1, B, st));
+  CK(launch_colpass_b<R>(cz, -1, B, st));
+  CK(launch_cd_vec<R>(a, CdMode::INIT, B, P->ist, P->mem_dev, maxdim, st));
+  CK(launch_cd_vec<R>(a, CdMode::DIR, B, P->ist, P->mem_dev, maxdim, st));
+  // iterations
+  XArgs<R> xs = ss.xa;
+  xs.mode = XM_SWEEPSIG;
+  fill_xm(xs, P->mem_host, B, XIN_NONE, 0);
+  xs.st = P->cg_skip;
+  cy.st = P->cg_skip;
+  cz.st = P->cg_skip;
+  int it = 0, chunk = 8;
+  while (it < maxit) {
+    const int c = std::min(chunk, maxit - it);
+    for (int k = 0; k < c; ++k) {
+      CK(launch_colpass_b<R>(cz, +1, B, st));
+      CK(launch_colpass_b<R>(cy, +1, B, st));
+      CK(launch_xpass_b<R>(xs, B, st));
+      CK(launch_colpass_b<R>(cy, -1, B, st));
+      CK(launch_colpass_b<R>(cz, -1, B, st));
+      CK(launch_cd_vec<R>(a, CdMode::PQ, B, P->ist, P->mem_dev, maxdim, st));
+      CK(launch_cd_vec<R>(a, CdMode::UPDATE, B, P->ist, P->mem_dev, maxdim, st));
+      CK(launch_cd_vec<R>(a, CdMode::DIR, B, P->ist, P->mem_dev, maxdim, st));
+    }
+    it += c;
+    chunk = std::min(chunk * 2, 64);
+    CK(read_small(P->cd_host, P->cd_state, B * sizeof(CdState), st));
+    const int w = sync_stream(P);
+    if (w != BFCS_OK) return w;
+    bool all = true;
+    for (int m = 0; m < B; ++m) all = all && P->cd_host[m].done;
+    if (all) break;
+  }
+  // the returned strain eps^{b(0)} + grad^s u1 (and sigma), its residual, the displacement
+  cy.st = nullptr;
+  cz.st = nullptr;
+  CK(launch_cd_vec<R>(a, CdMode::FINAL, B, P->ist, P->mem_dev, maxdim, st));
+  CK(launch_colpass_b<R>(cz, +1, B, st));
+  CK(launch_colpass_b<R>(cy, +1, B, st));
+  XArgs<R> xf = ss.xa;
+  xf.mode = XM_SWEEPSIG;
+  fill_xm(xf, P->mem_host, B, XIN_NONE, XOUT_EPS | XOUT_SIG);
+  xf.st = nullptr;
+  CK(launch_xpass_b<R>(xf, B, st));
+  CK(launch_colpass_b<R>(cy, -1, B, st));
+  CK(launch_colpass_b<R>(cz, -1, B, st));
+  CK(launch_cd_vec<R>(a, CdMode::RESID, B, P->ist, P->mem_dev, maxdim, st));
+  CK(launch_cd_vec<R>(a, CdMode::FINAL_U, B, P->ist, P->mem_dev, maxdim, st));
+  cz.ncomp = 3;
+  cy.ncomp = 3;
+  CK(launch_colpass_b<R>(cz, +1, B, st));
+  CK(launch_colpass_b<R>(cy, +1, B, st));
+  XArgs<R> xu{};
+  xu.g = P->g;
+  xu.spec_in = (C2<R>*)P->spec;
+  xu.spec_ms = 6 * g.cs;
+  fill_xm(xu, P->mem_host, B, XIN_NONE, XOUT_U);
+  xu.ncomp = 3;
+  xu.mode = XM_C2R;
+  xu.tw = (const C2<R>*)P->tw[0];
+  CK(launch_xpass_b<R>(xu, B, st));
+  ss.u_only = false;                               // the residual of the returned strain was formed
+  return ss.report(infos);
+}
+
 // Algorithm 1 for B members of one grid, advancing together: each sweep is
 // one launch per pass for all members; converged members skip on the device.
 // With BFCS_CG the sweeps are driven by conjugate gradients (Algorithm 2):
@@ -949,8 +1085,10 @@ int run_batch(bfcs_plan P, int B, const PhaseTab<R>& tab, bfcs_lame C0, const do
   SweepSet<R> ss;
   ss.prepare(P, B, tab, C0, E0, tol);
   ss.u_only = u_only;
+  if (P->use_cd && any_warm) return BFCS_ERR_INVALID_ARG;   // Algorithm 3 starts from u1 = 0
   int e = ss.init(any_warm);
   if (e != BFCS_OK) return e;
+  if (P->use_cd) return run_cd<R>(ss, maxit, infos);
   std::vector<SweepSet<R>*> sets{&ss};
   if (P->use_cg && tol > 0 && maxit > 2) {
     std::vector<int> applied(B, 0), verify(B, 0);
@@ -1685,7 +1823,8 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   const int prec = flags & 3;
   if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz) || max_batch < 1 || max_batch > kMaxBatch ||
       (prec != BFCS_FP32 && prec != BFCS_FP64 && prec != BFCS_MIXED) ||
-      (flags & ~(3 | BFCS_AUTOTUNE | BFCS_CG | BFCS_SPARSE_RESID)) != 0)
+      (flags & ~(3 | BFCS_AUTOTUNE | BFCS_CG | BFCS_SPARSE_RESID | BFCS_CD | BFCS_CD_PRECOND)) != 0 ||
+      ((flags & BFCS_CG) && (flags & (BFCS_CD | BFCS_CD_PRECOND))))
     return BFCS_ERR_INVALID_ARG;
   bfcs_plan P = new bfcs_plan_s();
   P->nx = nx; P->ny = ny; P->nz = nz;
@@ -1749,8 +1888,16 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
       if (P->tw64[a] == nullptr || P->twff[a] == nullptr) { free_plan(P); return BFCS_ERR_OOM; }
     }
   }
-  if (flags & BFCS_CG) {
-    P->use_cg = true;
+  if (flags & (BFCS_CD | BFCS_CD_PRECOND)) {   // u1, r, p, q (and z) vectors of 3 components in cg_vec
+    P->use_cd = true;
+    P->cd_precond = (flags & BFCS_CD_PRECOND) ? 1 : 0;
+    ok = cudaMalloc(&P->cd_part, MB * 2 * kCdParts * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&P->cd_state, MB * sizeof(CdState)) == cudaSuccess &&
+         cudaMallocHost(&P->cd_host, MB * sizeof(CdState)) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
+  }
+  if (flags & (BFCS_CG | BFCS_CD | BFCS_CD_PRECOND)) {
+    P->use_cg = (flags & BFCS_CG) != 0;
     ok = cudaMalloc(&P->cg_vec, 4 * MB * 6 * cs * P->csz) == cudaSuccess &&
          cudaMalloc(&P->cg_part, MB * kCgParts * sizeof(double)) == cudaSuccess &&
          cudaMalloc(&P->cg_state, MB * sizeof(CgState)) == cudaSuccess &&

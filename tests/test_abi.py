@@ -56,7 +56,9 @@ def test_invalid_plan_rejected_before_any_device_work():
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 0, 0, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 65, 0, None) == _lib.ERR_INVALID_ARG  # > 64 members
     assert lib.bfcs_plan_create(None, 32, 32, 32, 1, 0, None) == _lib.ERR_INVALID_ARG
-    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 32, None) == _lib.ERR_INVALID_ARG  # unknown flag
+    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 128, None) == _lib.ERR_INVALID_ARG  # unknown flag
+    # conjugate gradients of Algorithm 2 and of Algorithm 3 exclude each other
+    assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, _lib.CG | _lib.CD, None) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_plan_create(ctypes.byref(h), 32, 32, 32, 1, 3, None) == _lib.ERR_INVALID_ARG  # no precision 3
     assert lib.bfcs_plan_tuning(None, None, None, None, None) == _lib.ERR_INVALID_ARG
 

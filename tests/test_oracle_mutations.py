@@ -26,7 +26,10 @@ MUTATIONS = {
     "g0_coefficient": ("c = (lam0 + mu0) / (lam0 + 2.0 * mu0)\n    xv", "c = (lam0 + mu0) / (lam0 + 1.0 * mu0)\n    xv"),
     "sym_grad_sign": ("out[a] = 0.5j * (xi[j] * u_hat[i] + xi[i] * u_hat[j])",
                       "out[a] = -0.5j * (xi[j] * u_hat[i] + xi[i] * u_hat[j])"),
-    "mean_strain_dft_scale": ("eb0_hat[:, 0, 0, 0] = n * np.asarray", "eb0_hat[:, 0, 0, 0] = np.asarray"),
+    "mean_strain_dft_scale": ("eb0_hat[:, 0, 0, 0] = n * np.asarray(mean_strain, dtype=float)   # reading R3\n    table1",
+                              "eb0_hat[:, 0, 0, 0] = np.asarray(mean_strain, dtype=float)   # reading R3\n    table1"),
+    "cd_mean_strain_dft_scale": ("eb0_hat[:, 0, 0, 0] = n * np.asarray(mean_strain, dtype=float)   # reading R3\n    eb0",
+                                 "eb0_hat[:, 0, 0, 0] = np.asarray(mean_strain, dtype=float)   # reading R3\n    eb0"),
     "displacement_scale": ('return _real(-1j * g0_apply(v, xi, lam0, mu0), "displacement")',
                            'return _real(-2j * g0_apply(v, xi, lam0, mu0), "displacement")'),
     "translation_direction": ("np.roll(field, (sz, sy, sx)", "np.roll(field, (-sz, -sy, -sx)"),
@@ -39,8 +42,12 @@ MUTATIONS = {
     "body_force_power": ("-6.0 * x * s * s / (a * a)", "-6.0 * x * s / (a * a)"),
     "body_force_without_minimum_image": ("        return d - n * np.round(d / n)", "        return d"),
     "green_U1_coefficient": ("c1 = 1.0 / (4.0 * mu0)", "c1 = 1.0 / (2.0 * mu0)"),
-    "residual_normaliser_shear_once": ("2.0 * np.sum(np.abs(s0[3:]) ** 2)", "np.sum(np.abs(s0[3:]) ** 2)"),
-    "residual_xi_min_of_shortest_edge": ("2.0 * np.pi / max(dims) * s0n", "2.0 * np.pi / min(dims) * s0n"),
+    "residual_normaliser_shear_once": ("\n    s0n = np.sqrt(np.sum(np.abs(s0[:3]) ** 2) + 2.0 * np.sum(np.abs(s0[3:]) ** 2))",
+                                       "\n    s0n = np.sqrt(np.sum(np.abs(s0[:3]) ** 2) + np.sum(np.abs(s0[3:]) ** 2))"),
+    "cd_residual_normaliser_shear_once": ("        s0n = np.sqrt(np.sum(np.abs(s0[:3]) ** 2) + 2.0 * np.sum(np.abs(s0[3:]) ** 2))",
+                                          "        s0n = np.sqrt(np.sum(np.abs(s0[:3]) ** 2) + np.sum(np.abs(s0[3:]) ** 2))"),
+    "residual_xi_min_of_shortest_edge": ("\n    den = np.sqrt(np.sum(np.abs(b_hat[:, act]) ** 2)) + 2.0 * np.pi / max(dims) * s0n",
+                                         "\n    den = np.sqrt(np.sum(np.abs(b_hat[:, act]) ** 2)) + 2.0 * np.pi / min(dims) * s0n"),
     "wavevector_of_the_x_edge": ("        out.append(2.0 * np.pi * k / n)", "        out.append(2.0 * np.pi * k / dims[0])"),
     "phase_map_without_minimum_image": ("        return np.where(d >= n, d - 2 * n, d)", "        return d"),
     "initial_strain_zero": ('        eps = _real(eb0_hat, "eps0")', '        eps = np.zeros_like(_real(eb0_hat, "eps0"))'),
@@ -60,8 +67,8 @@ MUTATIONS = {
                                  "np.roll(field, (sx, sy, sz), axis=(-3, -2, -1))"),
     "residual_over_all_modes": ("act = np.broadcast_to(q > 0, sig_hat.shape[1:])",
                                 "act = np.broadcast_to(q >= 0, sig_hat.shape[1:])"),
-    "stress_of_the_reference_medium": ("    sig = apply_local(phase, table, eps)\n    u = displacement",
-                                       "    sig = apply_local(phase, [c0] * len(table), eps)\n    u = displacement"),
+    "stress_of_the_reference_medium": ("b_hat, xi)\n    sig = apply_local(phase, table, eps)\n    u = displacement",
+                                       "b_hat, xi)\n    sig = apply_local(phase, [c0] * len(table), eps)\n    u = displacement"),
     "sphere_boundary_exclusive": ("ph[d2 <= T] = p", "ph[d2 < T] = p"),
     "residual_misses_load": ("div = div_hat(sig_hat, xi) + b_hat", "div = div_hat(sig_hat, xi)"),
     "moduli_engineering_shear": ("    E[J] = 1.0\n", "    E[J] = 1.0 if J < 3 else 0.5\n"),

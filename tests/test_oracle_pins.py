@@ -965,3 +965,12 @@ def test_cd_residual_is_the_equilibrium_residual_and_matches_the_basic_scheme():
         assert np.allclose(res["u"], ref["u"], atol=1e-9 * np.abs(ref["u"]).max())
         its[pc] = res["iters"]
     assert its[True] < ref["sweeps"] < its[False]
+    # with a mean shear strain the normaliser's sigma_hat(0) has shear parts
+    r = np.random.default_rng(11)
+    dims = (8, 6, 4)
+    phase = r.integers(0, 2, size=(4, 6, 8)).astype(np.int8)
+    b = drop_xi_zero(r.standard_normal((3, 4, 6, 8)))
+    E = (0.01, -0.002, 0.0, 0.004, -0.003, 0.006)
+    res = O.solve_cd(phase, [(1.0, 0.5), (5.0, 2.5)], (3.0, 1.5), b, E, tol=1e-11, maxit=500, precondition=True,
+                     history=True)
+    assert res["resid"] <= 1.01e-11 and abs(res["hist"][-1] - res["resid"]) <= 1e-4 * res["resid"] + 1e-15
