@@ -609,9 +609,10 @@ def measure_extras(api, torch):
     q = W.config_c2(contrast=100.0, seed=1)
     phq = api.voxelize(q.dims, q.cell, q.spheres)
     bq = api.body_force(q.dims, q.bf_centre, q.bf_radius, "fp64")
-    c100 = {"workload": "C2 at contrast 100: 256^3, RSA vf 0.25 r 4-6, a = 24, mixed ladder to residual 1e-6"}
-    for label, cg in (("plain", False), ("cg", True)):
-        with api.Plan(q.dims, "mixed", autotune=True, cg=cg) as plan:
+    c100 = {"workload": "C2 at contrast 100: 256^3, RSA vf 0.25 r 4-6, a = 24, mixed ladder to residual 1e-6; "
+                        "plain: Algorithm 1 sweeps, cg: Algorithm 2, cd_g0: Algorithm 3 with the G0 preconditioner"}
+    for label, cg, cd in (("plain", False, None), ("cg", True, None), ("cd_g0", False, "g0")):
+        with api.Plan(q.dims, "mixed", autotune=True, cg=cg, cd=cd) as plan:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, _, _, info = plan.solve(phq, q.phases, q.c0, bq, tol=q.tol, maxit=q.maxit, want_sig=False,
@@ -620,6 +621,23 @@ def measure_extras(api, torch):
             c100[label] = {"seconds": time.perf_counter() - t0, "operator_applications": info.iters,
                            "resid": info.resid, "status": info.status}
     out["contrast_100"] = c100
+    # the bench workload itself (contrast 10) with the two Krylov forms
+    q = W.config_c2(contrast=10.0, seed=1)
+    phq = api.voxelize(q.dims, q.cell, q.spheres)
+    bq = api.body_force(q.dims, q.bf_centre, q.bf_radius, "fp64")
+    c10 = {"workload": "C2 at contrast 10 (the bench workload): mixed ladder to residual 1e-6; cg: Algorithm 2, "
+                       "cd_g0: Algorithm 3 with the G0 preconditioner (the sweeps of Algorithm 1 are the headline)"}
+    for label, cg, cd in (("cg", True, None), ("cd_g0", False, "g0")):
+        with api.Plan(q.dims, "mixed", autotune=True, cg=cg, cd=cd) as plan:
+            plan.solve(phq, q.phases, q.c0, bq, tol=q.tol, maxit=q.maxit, want_sig=False, want_u=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, _, info = plan.solve(phq, q.phases, q.c0, bq, tol=q.tol, maxit=q.maxit, want_sig=False,
+                                       want_u=False)
+            torch.cuda.synchronize()
+            c10[label] = {"seconds": time.perf_counter() - t0, "operator_applications": info.iters,
+                          "resid": info.resid, "status": info.status}
+    out["contrast_10_krylov"] = c10
     q = W.config_c2(contrast=10.0, seed=1)
     phq = api.voxelize(q.dims, q.cell, q.spheres)
     with api.Plan(q.dims, "mixed", max_batch=6, autotune=True) as plan:

@@ -144,6 +144,33 @@ def test_full_size_contrast_1000_converged_against_fp64():
     err_s = rel(sm.cpu().numpy(), s64.cpu().numpy())
     err_a = rel(am.cpu().numpy(), a64.cpu().numpy())
     assert max(err_e, err_s, err_a) < 1e-3, (err_e, err_s, err_a, im.iters, i64.iters)
+    # Algorithm 3 with the G0 preconditioner inside the mixed ladder, same bound
+    with api.Plan(p.dims, "mixed", cd="g0") as plan:
+        ec, sc, _, ic = plan.solve(ph, p.phases, p.c0, b, tol=1e-6, maxit=20000, want_u=False)
+    assert ic.status == _lib.OK and ic.resid <= 1e-6
+    err_e = rel(ec.cpu().numpy(), e64.cpu().numpy())
+    err_s = rel(sc.cpu().numpy(), s64.cpu().numpy())
+    assert max(err_e, err_s) < 1e-3, (err_e, err_s, ic.iters)
+
+
+def test_full_size_displacement_cg_iterates():
+    """Algorithm 3 (G0-preconditioned, FP32) at 256^3 on the bench problem: three
+    iterations against the oracle's iterates (strain, stress and displacement to
+    1e-5 in relative L2, the residual history's last value to 1e-3)."""
+    p = W.config_c2(contrast=10.0, seed=1)
+    ph_o = O.phase_map(p.dims, p.cell, p.spheres)
+    b_o = O.body_force(p.dims, p.bf_centre, p.bf_radius)
+    with sfft.set_workers(os.cpu_count() or 1):
+        ref = O.solve_cd(ph_o, p.phases, p.c0, b_o, tol=0.0, maxit=SWEEPS, precondition=True)
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp32")
+    with api.Plan(p.dims, "fp32", cd="g0") as plan:
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, tol=0.0, maxit=SWEEPS)
+    assert info.iters == ref["iters"] == SWEEPS
+    for got, key in ((eps, "eps"), (sig, "sig"), (u, "u")):
+        err = rel(got.cpu().numpy(), ref[key])
+        assert err < TOL["fp32"], (key, err)
+    assert abs(info.resid - ref["resid"]) <= 1e-3 * ref["resid"]
 
 
 def test_full_size_translated_averaging_c3():
