@@ -326,6 +326,196 @@ static __global__ void k_cd_scalar(const double* part, int nparts, CdState* cd, 
   }
 }
 
+// ---------------------------------------------------------------- fused z passes
+// The operator's z transforms fused with the pointwise CG steps next to them, in
+// the tile of the z/Green pass: a block holds T = 4 kx columns of one ky row for
+// all L z modes of the 6 components (24 line columns), its shared-memory slots
+// swizzled by row (components swap in every other pair of rows), and runs the
+// four-step line FFT in registers and shared memory.
+//  forward (ZFWD): stage 1 from global memory, stage 2, then per mode
+//     q = -i xi . sigma_hat (stored), the partial <p, q> and sigma_hat(0)  (PQ)
+//  inverse (ZINV): per mode p = z + beta p (stored) and sym(i xi (x) p) / N into the
+//     tile (DIR), then the inverse transform written to the work spectrum
+constexpr int kCdT = 4;
+constexpr int kCdNcol = 6 * kCdT;
+template <int L> struct ZCfg {
+  static constexpr int TASKS = kCdNcol * LineInfo<L>::RMAX;
+  static constexpr int BLOCK = (TASKS + 31) / 32 * 32;
+};
+__device__ __forceinline__ int cd_slot(int row, int c) { return c ^ (((row >> 1) & 1) << 2); }
+
+template <typename R, int L, bool FWD>
+__global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
+  const int m = blockIdx.z;
+  if (a.cd[m].done) return;
+  constexpr int T = kCdT, NCOL = kCdNcol;
+  constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
+  constexpr int TASKS = ZCfg<L>::TASKS;
+  extern __shared__ unsigned char smem_cd[];
+  C2<R>* const sm = reinterpret_cast<C2<R>*>(smem_cd);          // [n][slot]
+  __shared__ double red[32];
+  const Geo g = a.g;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int ky = blockIdx.y, col0 = blockIdx.x * T;
+  const long long zs = (long long)g.ny * g.p, rowbase = (long long)ky * g.p;
+  C2<R>* const s = a.s + m * a.sms;
+  const long long vo = m * a.ms;
+  auto column = [&](int c) { const int q = c / T; return s + q * g.cs + rowbase + col0 + (c - q * T); };
+  const R two_pi = R(6.283185307179586);
+  const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(L);
+  double acc = 0.0;
+  if (FWD) {
+    // ---- forward z transform of the 6 stress components
+    for (int task = tid; task < TASKS; task += nthr) {
+      const int c = task % NCOL, j = task / NCOL;
+      if (j >= R2) continue;
+      const bool cvalid = col0 + (c % T) < g.mx;
+      const C2<R>* gcol = column(c);
+      C2<R> x[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) x[n1] = cvalid ? gcol[(R2 * n1 + j) * zs] : mk<R>(0, 0);
+      stage1<R, L, -1>(x, j, a.tw);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) sm[(j * R1 + k1) * NCOL + cd_slot(j * R1 + k1, c)] = x[k1];
+    }
+    __syncthreads();
+    for (int task = tid; task < TASKS; task += nthr) {
+      const int c = task % NCOL, j = task / NCOL;
+      if (j >= R1) continue;
+      C2<R> y[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) y[n2] = sm[(n2 * R1 + j) * NCOL + cd_slot(n2 * R1 + j, c)];
+      stage2<R, L, -1>(y);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) sm[(j + R1 * k2) * NCOL + cd_slot(j + R1 * k2, c)] = y[k2];
+    }
+    __syncthreads();
+  }
+  // ---- per mode of the tile (column kx = col0 + col, z mode n)
+  for (int idx = tid; idx < T * L; idx += nthr) {
+    const int col = idx % T, n = idx / T;
+    const int kx = col0 + col;
+    C2<R>* const mrow = sm + n * NCOL + col;
+    const int qs = (n >> 1) & 1;
+    auto M = [&](int q) -> C2<R>& { return mrow[(q ^ qs) * T]; };
+    if (kx >= g.mx) {
+      if (!FWD) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) M(q) = mk<R>(0, 0);
+      }
+      continue;
+    }
+    const long long gi = n * zs + rowbase + kx;
+    R xi[3];
+    xi[0] = dk0 * R(signed_k(kx, g.nx));
+    xi[1] = dk1 * R(signed_k(ky, g.ny));
+    xi[2] = dk2 * R(signed_k(n, L));
+    const bool nz = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] != R(0);
+    if (FWD) {
+      C2<R> t[6], qv[3];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) t[q] = M(q);
+      if (kx == 0 && ky == 0 && n == 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) a.cd[m].s0p[q] = (double)t[q].x;
+      }
+      cd_div<R>(t, xi, qv);
+      R dot = R(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        qv[k] = nz ? mk<R>(-qv[k].x, -qv[k].y) : mk<R>(0, 0);
+        a.q[vo + k * g.cs + gi] = qv[k];
+        const C2<R> pk = a.p[vo + k * g.cs + gi];
+        dot += pk.x * qv[k].x + pk.y * qv[k].y;
+      }
+      acc += ((kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0) * (double)dot;
+    } else {
+      const R beta = (R)a.cd[m].beta;
+      const R inv_n = R(1.0 / (double)g.n);
+      C2<R> pv[3], e[6];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        pv[k] = a.z[vo + k * g.cs + gi] + scale(a.p[vo + k * g.cs + gi], beta);
+        a.p[vo + k * g.cs + gi] = pv[k];
+      }
+      cd_symgrad<R>(pv, xi, inv_n, e);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) M(q) = nz ? e[q] : mk<R>(0, 0);
+    }
+  }
+  if (FWD) {
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nthr / 32; ++w) t += red[w];
+      const long long slot = (long long)m * gridDim.x * gridDim.y + (long long)blockIdx.y * gridDim.x + blockIdx.x;
+      a.part[slot * 2] = t;
+      a.part[slot * 2 + 1] = 0.0;
+    }
+    return;
+  }
+  __syncthreads();
+  // ---- inverse z transform (four-step rule, decimation-in-frequency order) to the work spectrum
+  for (int task = tid; task < TASKS; task += nthr) {
+    const int c = task % NCOL, j = task / NCOL;
+    if (j >= R1) continue;
+    C2<R> y[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) y[k2] = sm[(j + R1 * k2) * NCOL + cd_slot(j + R1 * k2, c)];
+    Dft<R, R2, +1>::run(y);
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) sm[(j + R1 * n2) * NCOL + cd_slot(j + R1 * n2, c)] = y[n2];
+  }
+  __syncthreads();
+  for (int task = tid; task < TASKS; task += nthr) {
+    const int c = task % NCOL, j = task / NCOL;
+    if (j >= R2) continue;
+    C2<R> x[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) x[k1] = sm[(j * R1 + k1) * NCOL + cd_slot(j * R1 + k1, c)];
+    twiddle_then_dft<R, L, R1, +1>(x, j, a.tw);
+    if (col0 + (c % T) < g.mx) {
+      C2<R>* gcol = column(c);
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) gcol[(R2 * n1 + j) * zs] = x[n1];
+    }
+  }
+}
+
+template <typename R, int L>
+static cudaError_t zcd_L(const CdArgs<R>& a, bool fwd, int batch, cudaStream_t st) {
+  const dim3 grid((a.g.mx + kCdT - 1) / kCdT, a.g.ny, batch);
+  const size_t smem = sizeof(C2<R>) * (size_t)L * kCdNcol;
+  auto k = fwd ? k_zcd<R, L, true> : k_zcd<R, L, false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, ZCfg<L>::BLOCK, smem, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_zcd(const CdArgs<R>& a, bool fwd, int batch, IterState* ist, const Member* mem, int maxdim,
+                       cudaStream_t st) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (a.g.nz) {
+#define BFCS_ZCD(L) case L: e = zcd_L<R, L>(a, fwd, batch, st); break;
+    BFCS_ZCD(4) BFCS_ZCD(6) BFCS_ZCD(8) BFCS_ZCD(12) BFCS_ZCD(16) BFCS_ZCD(24) BFCS_ZCD(32) BFCS_ZCD(48)
+    BFCS_ZCD(64) BFCS_ZCD(96) BFCS_ZCD(128) BFCS_ZCD(192) BFCS_ZCD(256)
+#undef BFCS_ZCD
+    default: break;
+  }
+  if (e != cudaSuccess || !fwd) return e;
+  // alpha from <p, q>: one partial pair per tile
+  const int nparts = ((a.g.mx + kCdT - 1) / kCdT) * a.g.ny;
+  k_cd_scalar<<<batch, kCdThreads, 0, st>>>(a.part, nparts, a.cd, a.skip, ist, mem, a.lam0, a.mu0, (double)a.g.n,
+                                            maxdim, CdMode::PQ);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_cd_vec(const CdArgs<R>& a, int mode, int batch, IterState* ist, const Member* mem, int maxdim,
                           cudaStream_t st) {
@@ -340,5 +530,7 @@ cudaError_t launch_cd_vec(const CdArgs<R>& a, int mode, int batch, IterState* is
 
 template cudaError_t launch_cd_vec<BFCS_R>(const CdArgs<BFCS_R>&, int, int, IterState*, const Member*, int,
                                            cudaStream_t);
+template cudaError_t launch_zcd<BFCS_R>(const CdArgs<BFCS_R>&, bool, int, IterState*, const Member*, int,
+                                        cudaStream_t);
 
 }  // namespace bfcs

@@ -141,6 +141,7 @@ template <typename R> struct CdArgs {
   IterState* skip;       // done flags read by the FFT passes of A p
   const Member* mem;     // per-member mean strain (FINAL)
   int precond;           // 1: z = G0 r
+  const C2<R>* tw;       // z twiddles exp(-2 pi i j / nz) (fused z passes)
 };
 // the vector step `mode` for members 0..batch-1, then (INIT, PQ, UPDATE, RESID)
 // the scalar step; ist: the members' IterState (bden read; iterations, residuals,
@@ -148,6 +149,21 @@ template <typename R> struct CdArgs {
 template <typename R>
 cudaError_t launch_cd_vec(const CdArgs<R>& a, int mode, int batch, IterState* ist, const Member* mem, int maxdim,
                           cudaStream_t st);
+// the operator's z transforms fused with the CG steps beside them: fwd = the forward z
+// transform of the stress spectrum in a.s, then q = -i xi . sigma_hat, <p, q> and
+// alpha (replaces the forward z column pass and PQ); !fwd = p = z + beta p, the
+// strain spectrum sym(i xi (x) p) / N and its inverse z transform into a.s
+// (replaces DIR and the inverse z column pass).  a.tw: the z twiddles.  The <p, q>
+// partials take one pair per tile: a.part holds at least tiles x batch pairs.
+template <typename R>
+cudaError_t launch_zcd(const CdArgs<R>& a, bool fwd, int batch, IterState* ist, const Member* mem, int maxdim,
+                       cudaStream_t st);
+// partial pairs per member the Algorithm 3 kernels need (vector steps: kCdParts; fused
+// forward z pass: one per tile)
+inline int cd_parts(const Geo& g) {
+  const int tiles = (g.mx + 3) / 4 * g.ny;
+  return tiles > kCdParts ? tiles : kCdParts;
+}
 
 // ---- fused z pass: forward z FFT -> Green operators -> residual -> inverse z FFT.
 enum GMode : int {

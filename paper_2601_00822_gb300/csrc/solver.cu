@@ -982,6 +982,7 @@ int run_cd(SweepSet<R>& ss, int maxit, bfcs_info* infos) {
   a.skip = P->cg_skip;
   a.mem = P->mem_dev;
   a.precond = P->cd_precond;
+  a.tw = (const C2<R>*)P->tw[2];
   const int maxdim = std::max(g.nx, std::max(g.ny, g.nz));
   for (int m = 0; m < B; ++m) {
     CdState& h = P->cd_host[m];
@@ -1010,8 +1011,10 @@ int run_cd(SweepSet<R>& ss, int maxit, bfcs_info* infos) {
   CK(launch_colpass_b<R>(cy, -1, B, st));
   CK(launch_colpass_b<R>(cz, -1, B, st));
   CK(launch_cd_vec<R>(a, CdMode::INIT, B, P->ist, P->mem_dev, maxdim, st));
-  CK(launch_cd_vec<R>(a, CdMode::DIR, B, P->ist, P->mem_dev, maxdim, st));
-  // iterations
+  CK(launch_zcd<R>(a, false, B, P->ist, P->mem_dev, maxdim, st));      // p = z, its strain, inverse z
+  // iterations: inverse y, x (sigma = L eps), forward y, then the fused forward z
+  // pass with the divergence and <p, A p>, the update, and the fused direction step
+  // with the inverse z transform of the next operator input
   XArgs<R> xs = ss.xa;
   xs.mode = XM_SWEEPSIG;
   fill_xm(xs, P->mem_host, B, XIN_NONE, 0);
@@ -1022,14 +1025,12 @@ int run_cd(SweepSet<R>& ss, int maxit, bfcs_info* infos) {
   while (it < maxit) {
     const int c = std::min(chunk, maxit - it);
     for (int k = 0; k < c; ++k) {
-      CK(launch_colpass_b<R>(cz, +1, B, st));
       CK(launch_colpass_b<R>(cy, +1, B, st));
       CK(launch_xpass_b<R>(xs, B, st));
       CK(launch_colpass_b<R>(cy, -1, B, st));
-      CK(launch_colpass_b<R>(cz, -1, B, st));
-      CK(launch_cd_vec<R>(a, CdMode::PQ, B, P->ist, P->mem_dev, maxdim, st));
+      CK(launch_zcd<R>(a, true, B, P->ist, P->mem_dev, maxdim, st));
       CK(launch_cd_vec<R>(a, CdMode::UPDATE, B, P->ist, P->mem_dev, maxdim, st));
-      CK(launch_cd_vec<R>(a, CdMode::DIR, B, P->ist, P->mem_dev, maxdim, st));
+      CK(launch_zcd<R>(a, false, B, P->ist, P->mem_dev, maxdim, st));
     }
     it += c;
     chunk = std::min(chunk * 2, 64);
@@ -1891,7 +1892,7 @@ int bfcs_plan_create(bfcs_plan* out, int nx, int ny, int nz, int max_batch, int 
   if (flags & (BFCS_CD | BFCS_CD_PRECOND)) {   // u1, r, p, q (and z) vectors of 3 components in cg_vec
     P->use_cd = true;
     P->cd_precond = (flags & BFCS_CD_PRECOND) ? 1 : 0;
-    ok = cudaMalloc(&P->cd_part, MB * 2 * kCdParts * sizeof(double)) == cudaSuccess &&
+    ok = cudaMalloc(&P->cd_part, MB * 2 * (size_t)cd_parts(P->g) * sizeof(double)) == cudaSuccess &&
          cudaMalloc(&P->cd_state, MB * sizeof(CdState)) == cudaSuccess &&
          cudaMallocHost(&P->cd_host, MB * sizeof(CdState)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_plan(P); return BFCS_ERR_OOM; }
