@@ -81,11 +81,12 @@ __device__ __forceinline__ R cd_dot3(const C2<R> (&a)[3], const C2<R> (&b)[3]) {
 }  // namespace
 
 // Modes (CdMode):
-//  INIT:    r = b^A = i xi . s (s: F[L1 eps^{b(0)}], 6 components), u = 0, z = M r;
+//  INIT:    r = b^A = i xi . s (s: F[L1 eps^{b(0)}], 6 components), u = 0, p = z = M r;
 //           partials <r, z>, <r, r>; the k = 0 thread stores s(0) in cd.s0b
+//  (z = M r is never stored: every step that needs it forms it from r)
 //  PQ:      q = -i xi . s (s: F[L grad^s p]); partial <p, q>; s(0) into cd.s0p
-//  UPDATE:  u += alpha p, r -= alpha q, z = M r; partials <r, z>, <r, r>
-//  DIR:     p = z + beta p, s = sym(i xi (x) p) / N (6 components; 0 where xi = 0)
+//  UPDATE:  u += alpha p, r -= alpha q; partials <r, M r>, <r, r>
+//  DIR:     p = M r + beta p, s = sym(i xi (x) p) / N (6 components; 0 where xi = 0)
 //  FINAL:   s = sym(i xi (x) (G0 b_hat + u)) / N, s(0) = E (the returned strain)
 //  FINAL_U: s = (G0 b_hat + u) / N in components 0..2 (the returned displacement)
 //  RESID:   partial |i xi . s + b_hat|^2 over xi != 0 (s: F[L eps]); s(0) into cd.s0u
@@ -98,7 +99,6 @@ __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
   const Geo g = a.g;
   C2<R>* const u = a.u + m * a.ms;
   C2<R>* const r = a.r + m * a.ms;
-  C2<R>* const z = a.z + m * a.ms;
   C2<R>* const p = a.p + m * a.ms;
   C2<R>* const q = a.q + m * a.ms;
   C2<R>* const s = a.s + m * a.sms;
@@ -155,8 +155,7 @@ __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
       precond(rv, zv);
       const C2<R> zero[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
       st3(r, rv);
-      st3(z, zv);
-      st3(p, zv);      // p = z (DIR then forms the operator input with beta = 0)
+      st3(p, zv);      // p = z (the direction step then forms the operator input with beta = 0)
       st3(u, zero);
       acc1 += w * (double)cd_dot3<R>(rv, zv);
       acc2 += w * (double)cd_dot3<R>(rv, rv);
@@ -184,16 +183,16 @@ __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
         uv[k] = uv[k] + scale(pv[k], alpha);
         rv[k] = rv[k] - scale(qv[k], alpha);
       }
-      precond(rv, zv);
+      precond(rv, zv);                 // z = M r is formed where it is used, not stored
       st3(u, uv);
       st3(r, rv);
-      st3(z, zv);
       acc1 += w * (double)cd_dot3<R>(rv, zv);
       acc2 += w * (double)cd_dot3<R>(rv, rv);
     } else if (mode == CdMode::DIR) {
-      C2<R> pv[3], zv[3], e[6];
+      C2<R> pv[3], rv[3], zv[3], e[6];
       ld3(p, pv);
-      ld3(z, zv);
+      ld3(r, rv);
+      precond(rv, zv);
 #pragma unroll
       for (int k = 0; k < 3; ++k) pv[k] = zv[k] + scale(pv[k], beta);
       st3(p, pv);
@@ -334,7 +333,7 @@ static __global__ void k_cd_scalar(const double* part, int nparts, CdState* cd, 
 // four-step line FFT in registers and shared memory.
 //  forward (ZFWD): stage 1 from global memory, stage 2, then per mode
 //     q = -i xi . sigma_hat (stored), the partial <p, q> and sigma_hat(0)  (PQ)
-//  inverse (ZINV): per mode p = z + beta p (stored) and sym(i xi (x) p) / N into the
+//  inverse (ZINV): per mode p = M r + beta p (stored) and sym(i xi (x) p) / N into the
 //     tile (DIR), then the inverse transform written to the work spectrum
 constexpr int kCdT = 4;
 constexpr int kCdNcol = 6 * kCdT;
@@ -432,10 +431,18 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
     } else {
       const R beta = (R)a.cd[m].beta;
       const R inv_n = R(1.0 / (double)g.n);
-      C2<R> pv[3], e[6];
+      C2<R> pv[3], rv[3], zv[3], e[6];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) rv[k] = a.r[vo + k * g.cs + gi];
+      if (a.precond && nz) {                       // z = G0 r, formed here rather than stored
+        cd_g0<R>(rv, xi, xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2], (R)a.lam0, (R)a.mu0, zv);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) zv[k] = a.precond ? mk<R>(0, 0) : rv[k];
+      }
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        pv[k] = a.z[vo + k * g.cs + gi] + scale(a.p[vo + k * g.cs + gi], beta);
+        pv[k] = zv[k] + scale(a.p[vo + k * g.cs + gi], beta);
         a.p[vo + k * g.cs + gi] = pv[k];
       }
       cd_symgrad<R>(pv, xi, inv_n, e);

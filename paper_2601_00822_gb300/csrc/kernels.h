@@ -127,8 +127,7 @@ struct CdState {
 constexpr int kCdParts = 512;       // partial sums (pairs) per member
 template <typename R> struct CdArgs {
   C2<R>* u;              // u1_hat (3 components, fully transformed half spectrum)
-  C2<R>* r;              // residual b^A - A(u1)
-  C2<R>* z;              // preconditioned residual (r itself without preconditioner)
+  C2<R>* r;              // residual b^A - A(u1) (z = M r is formed where used)
   C2<R>* p;              // search direction
   C2<R>* q;              // A p
   C2<R>* s;              // 6-component work spectrum (operator input and output)
@@ -151,7 +150,7 @@ cudaError_t launch_cd_vec(const CdArgs<R>& a, int mode, int batch, IterState* is
                           cudaStream_t st);
 // the operator's z transforms fused with the CG steps beside them: fwd = the forward z
 // transform of the stress spectrum in a.s, then q = -i xi . sigma_hat, <p, q> and
-// alpha (replaces the forward z column pass and PQ); !fwd = p = z + beta p, the
+// alpha (replaces the forward z column pass and PQ); !fwd = p = M r + beta p, the
 // strain spectrum sym(i xi (x) p) / N and its inverse z transform into a.s
 // (replaces DIR and the inverse z column pass).  a.tw: the z twiddles.  The <p, q>
 // partials take one pair per tile: a.part holds at least tiles x batch pairs.

@@ -962,13 +962,12 @@ int run_cd(SweepSet<R>& ss, int maxit, bfcs_info* infos) {
   const Geo g = P->g;
   const long long vs = 3 * g.cs;
   const long long vstride = (long long)P->max_batch * vs;
-  C2<R>* base = (C2<R>*)P->cg_vec;                 // 5 x max_batch x 3 cs of the 4 x max_batch x 6 cs
+  C2<R>* base = (C2<R>*)P->cg_vec;                 // 4 x max_batch x 3 cs of the 4 x max_batch x 6 cs
   CdArgs<R> a{};
   a.u = base;
   a.r = base + vstride;
   a.p = base + 2 * vstride;
   a.q = base + 3 * vstride;
-  a.z = P->cd_precond ? base + 4 * vstride : a.r;
   a.s = (C2<R>*)P->spec;
   a.ms = vs;
   a.sms = 6 * g.cs;
