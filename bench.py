@@ -58,6 +58,9 @@ def parse():
                          "solve, errors and sweep counts; prints one JSON line and exits")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="profiling aid: run one FP32 solve of exactly this many sweeps and exit")
+    ap.add_argument("--krylov-only", choices=("cg", "cd"), default=None,
+                    help="profiling aid: one 256^3 contrast-100 solve (mixed ladder to 1e-6) with Algorithm 2 "
+                         "(cg) or the G0-preconditioned Algorithm 3 (cd) after one warm-up solve, then exit")
     return ap.parse_args()
 
 
@@ -830,6 +833,24 @@ def run_sweeps_only(args):
     print(json.dumps({"sweeps": info.iters, "resid": info.resid, "grid": list(p.dims)}))
 
 
+def run_krylov_only(args):
+    """The contrast-100 solve of the bench extras with one Krylov method, after a
+    warm-up solve on the same plan; used as the command under ncu."""
+    import torch
+    from paper_2601_00822_gb300 import api, workloads as W
+    q = W.config_c2(contrast=100.0, seed=1)
+    ph = api.voxelize(q.dims, q.cell, q.spheres)
+    b = api.body_force(q.dims, q.bf_centre, q.bf_radius, "fp64")
+    kw = dict(cg=True) if args.krylov_only == "cg" else dict(cd="g0")
+    with api.Plan(q.dims, "mixed", **kw) as plan:
+        for _ in range(2):
+            _, _, _, info = plan.solve(ph, q.phases, q.c0, b, tol=q.tol, maxit=q.maxit, want_sig=False,
+                                       want_u=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"method": args.krylov_only, "operator_applications": info.iters, "resid": info.resid,
+                      "status": info.status, "grid": list(q.dims)}))
+
+
 def torchrun_argv(gpus, argv, port):
     """Command that relaunches this script with one process per GPU (the launch
     `bench.py --gpus N` gets when it is not already under a launcher)."""
@@ -849,6 +870,9 @@ def main():
         os.execv(cmd[0], cmd)
     if args.sweeps_only > 0:
         run_sweeps_only(args)
+        return
+    if args.krylov_only is not None:
+        run_krylov_only(args)
         return
     if args.precision_study > 0:
         run_precision_study(args)
