@@ -350,8 +350,10 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
   constexpr int T = kCdT, NCOL = kCdNcol;
   constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
   constexpr int TASKS = ZCfg<L>::TASKS;
+  constexpr int MPT = (T * L + ZCfg<L>::BLOCK - 1) / ZCfg<L>::BLOCK;   // modes per thread
   extern __shared__ unsigned char smem_cd[];
-  C2<R>* const sm = reinterpret_cast<C2<R>*>(smem_cd);          // [n][slot]
+  C2<R>* const sm = reinterpret_cast<C2<R>*>(smem_cd);          // [n][slot], L x NCOL
+  C2<R>* const pre = sm + L * NCOL;                             // forward: p tile [arr][n][col]
   __shared__ double red[32];
   const Geo g = a.g;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -362,9 +364,19 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
   auto column = [&](int c) { const int q = c / T; return s + q * g.cs + rowbase + col0 + (c - q * T); };
   const R two_pi = R(6.283185307179586);
   const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(L);
+  // 16-byte copies of [arr][n][col] tiles of 3-component vectors (T columns of every row)
+  constexpr int PER = 16 / sizeof(C2<R>);
+  constexpr int CPR = T / PER;
+  auto stage = [&](C2<R>* dst, const C2<R>* v, int arr0) {
+    for (int idx = tid; idx < 3 * L * CPR; idx += nthr) {
+      const int part = idx % CPR, n = (idx / CPR) % L, arr = idx / (CPR * L);
+      cp_async16(dst + ((arr0 + arr) * L + n) * T + part * PER, v + vo + arr * g.cs + n * zs + rowbase + col0 + part * PER);
+    }
+  };
   double acc = 0.0;
   if (FWD) {
-    // ---- forward z transform of the 6 stress components
+    stage(pre, a.p, 0);                                         // p lands during the transform
+    cp_async_commit();
     for (int task = tid; task < TASKS; task += nthr) {
       const int c = task % NCOL, j = task / NCOL;
       if (j >= R2) continue;
@@ -388,80 +400,109 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) sm[(j + R1 * k2) * NCOL + cd_slot(j + R1 * k2, c)] = y[k2];
     }
+    cp_async_wait_all();
     __syncthreads();
+    for (int idx = tid; idx < T * L; idx += nthr) {
+      const int col = idx % T, n = idx / T;
+      const int kx = col0 + col;
+      if (kx >= g.mx) continue;
+      C2<R>* const mrow = sm + n * NCOL + col;
+      const int qs = (n >> 1) & 1;
+      C2<R> t[6], qv[3];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) t[q] = mrow[(q ^ qs) * T];
+      if (kx == 0 && ky == 0 && n == 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) a.cd[m].s0p[q] = (double)t[q].x;
+      }
+      R xi[3];
+      xi[0] = dk0 * R(signed_k(kx, g.nx));
+      xi[1] = dk1 * R(signed_k(ky, g.ny));
+      xi[2] = dk2 * R(signed_k(n, L));
+      const bool nz = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] != R(0);
+      cd_div<R>(t, xi, qv);
+      const long long gi = n * zs + rowbase + kx;
+      R dot = R(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        qv[k] = nz ? mk<R>(-qv[k].x, -qv[k].y) : mk<R>(0, 0);
+        a.q[vo + k * g.cs + gi] = qv[k];
+        const C2<R> pk = pre[(k * L + n) * T + col];
+        dot += pk.x * qv[k].x + pk.y * qv[k].y;
+      }
+      acc += ((kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0) * (double)dot;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double tsum = 0.0;
+      for (int w = 0; w < nthr / 32; ++w) tsum += red[w];
+      const long long slot = (long long)m * gridDim.x * gridDim.y + (long long)blockIdx.y * gridDim.x + blockIdx.x;
+      a.part[slot * 2] = tsum;
+      a.part[slot * 2 + 1] = 0.0;
+    }
+    return;
   }
-  // ---- per mode of the tile (column kx = col0 + col, z mode n)
-  for (int idx = tid; idx < T * L; idx += nthr) {
+  // ---- inverse: r and p tiles fill the transform tile ([arr][n][col], arrays 0-2 r,
+  // 3-5 p); each thread takes its modes into registers before the tile is rewritten
+  stage(sm, a.r, 0);
+  stage(sm, a.p, 3);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  C2<R> rv[MPT][3], pv[MPT][3];
+#pragma unroll
+  for (int k = 0; k < MPT; ++k) {
+    const int idx = tid + k * nthr;
+    if (idx < T * L) {
+      const int col = idx % T, n = idx / T;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rv[k][c] = sm[(c * L + n) * T + col];
+        pv[k][c] = sm[((3 + c) * L + n) * T + col];
+      }
+    }
+  }
+  __syncthreads();
+  const R beta = (R)a.cd[m].beta;
+  const R inv_n = R(1.0 / (double)g.n);
+#pragma unroll
+  for (int k = 0; k < MPT; ++k) {
+    const int idx = tid + k * nthr;
+    if (idx >= T * L) continue;
     const int col = idx % T, n = idx / T;
     const int kx = col0 + col;
     C2<R>* const mrow = sm + n * NCOL + col;
     const int qs = (n >> 1) & 1;
     auto M = [&](int q) -> C2<R>& { return mrow[(q ^ qs) * T]; };
     if (kx >= g.mx) {
-      if (!FWD) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) M(q) = mk<R>(0, 0);
-      }
+      for (int q = 0; q < 6; ++q) M(q) = mk<R>(0, 0);
       continue;
     }
-    const long long gi = n * zs + rowbase + kx;
     R xi[3];
     xi[0] = dk0 * R(signed_k(kx, g.nx));
     xi[1] = dk1 * R(signed_k(ky, g.ny));
     xi[2] = dk2 * R(signed_k(n, L));
-    const bool nz = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2] != R(0);
-    if (FWD) {
-      C2<R> t[6], qv[3];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) t[q] = M(q);
-      if (kx == 0 && ky == 0 && n == 0) {
-#pragma unroll
-        for (int q = 0; q < 6; ++q) a.cd[m].s0p[q] = (double)t[q].x;
-      }
-      cd_div<R>(t, xi, qv);
-      R dot = R(0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        qv[k] = nz ? mk<R>(-qv[k].x, -qv[k].y) : mk<R>(0, 0);
-        a.q[vo + k * g.cs + gi] = qv[k];
-        const C2<R> pk = a.p[vo + k * g.cs + gi];
-        dot += pk.x * qv[k].x + pk.y * qv[k].y;
-      }
-      acc += ((kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0) * (double)dot;
+    const R qq = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    const bool nz = qq != R(0);
+    C2<R> zv[3], e[6];
+    if (a.precond && nz) {                         // z = G0 r, formed here rather than stored
+      cd_g0<R>(rv[k], xi, qq, (R)a.lam0, (R)a.mu0, zv);
     } else {
-      const R beta = (R)a.cd[m].beta;
-      const R inv_n = R(1.0 / (double)g.n);
-      C2<R> pv[3], rv[3], zv[3], e[6];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) rv[k] = a.r[vo + k * g.cs + gi];
-      if (a.precond && nz) {                       // z = G0 r, formed here rather than stored
-        cd_g0<R>(rv, xi, xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2], (R)a.lam0, (R)a.mu0, zv);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) zv[k] = a.precond ? mk<R>(0, 0) : rv[k];
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        pv[k] = zv[k] + scale(a.p[vo + k * g.cs + gi], beta);
-        a.p[vo + k * g.cs + gi] = pv[k];
-      }
-      cd_symgrad<R>(pv, xi, inv_n, e);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) M(q) = nz ? e[q] : mk<R>(0, 0);
+      for (int c = 0; c < 3; ++c) zv[c] = a.precond ? mk<R>(0, 0) : rv[k][c];
     }
-  }
-  if (FWD) {
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nthr / 32; ++w) t += red[w];
-      const long long slot = (long long)m * gridDim.x * gridDim.y + (long long)blockIdx.y * gridDim.x + blockIdx.x;
-      a.part[slot * 2] = t;
-      a.part[slot * 2 + 1] = 0.0;
+    const long long gi = n * zs + rowbase + kx;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pv[k][c] = zv[c] + scale(pv[k][c], beta);
+      a.p[vo + c * g.cs + gi] = pv[k][c];
     }
-    return;
+    cd_symgrad<R>(pv[k], xi, inv_n, e);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) M(q) = nz ? e[q] : mk<R>(0, 0);
   }
   __syncthreads();
   // ---- inverse z transform (four-step rule, decimation-in-frequency order) to the work spectrum
@@ -494,7 +535,7 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
 template <typename R, int L>
 static cudaError_t zcd_L(const CdArgs<R>& a, bool fwd, int batch, cudaStream_t st) {
   const dim3 grid((a.g.mx + kCdT - 1) / kCdT, a.g.ny, batch);
-  const size_t smem = sizeof(C2<R>) * (size_t)L * kCdNcol;
+  const size_t smem = sizeof(C2<R>) * (size_t)L * (kCdNcol + (fwd ? 3 * kCdT : 0));   // + the p tile (forward)
   auto k = fwd ? k_zcd<R, L, true> : k_zcd<R, L, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
