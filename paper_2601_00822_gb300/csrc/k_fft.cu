@@ -482,9 +482,11 @@ static cudaError_t colpass_tma_LT(const CArgs<float>& a, int batch, cudaStream_t
 template <typename R, int L, int DIR>
 static cudaError_t colpass_L(const CArgs<R>& a, int batch, cudaStream_t st) {
   if constexpr (sizeof(R) == 4 && L >= 32) {
-    // tensor-map tiles: only the sweep's y passes over 6-component spectra carry a map
+    // tensor-map tiles: only the sweep's y passes over the 6-component spectra the map
+    // was encoded for; any other buffer (the CG vectors) takes the same tile with direct loads
     if (col_variant_tma(a.variant)) {
-      const bool map = a.tmap != nullptr && a.axis == 1 && a.ncomp == 6 && a.ms == 6 * a.g.cs;
+      const bool map = a.tmap != nullptr && a.data == a.tmap_data && a.axis == 1 && a.ncomp == 6 &&
+                       a.ms == 6 * a.g.cs;
       if (a.variant == 6) return map ? colpass_tma_LT<L, DIR, 8>(a, batch, st) : colpass_LT<R, L, DIR, 8, false>(a, batch, st);
       return map ? colpass_tma_LT<L, DIR, 16>(a, batch, st) : colpass_LT<R, L, DIR, 16, false>(a, batch, st);
     }

@@ -68,6 +68,7 @@ template <typename R> struct CArgs {
   long long ms;           // data stride between members (complex elements)
   int variant;            // FP32 only: column tile and factor order (kColVariants; 0 = default)
   const void* tmap;       // host array of the two tensor maps (8, 16 columns) of a y pass over 6-component spectra, or null
+  const void* tmap_data;  // the buffer the maps address: the tensor-copy tiles run only when data is this buffer
 };
 
 // Column-pass variants an autotuner can pick from (FP32): tile width in kx

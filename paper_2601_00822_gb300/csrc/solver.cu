@@ -247,6 +247,7 @@ int autotune(bfcs_plan P) {
   ca.tw = (const C2<float>*)P->tw[1];
   ca.ms = 6 * P->g.cs;
   ca.tmap = P->tmap_ok ? P->tmap_y : nullptr;
+  ca.tmap_data = P->spec;
   double best = INFINITY;
   int bestv = 0, status = BFCS_OK;
   for (int v = 0; v < kColVariants && status == BFCS_OK; ++v) {
@@ -460,6 +461,7 @@ struct SweepSet {
     cy.tw = (const C2<R>*)P->tw[1];
     cy.variant = P->col_variant;
     cy.tmap = P->tmap_ok ? P->tmap_y : nullptr;
+    cy.tmap_data = P->spec;
     xa.g = g;
     xa.spec_in = (C2<R>*)P->spec;
     xa.spec_out = (C2<R>*)P->spec;
@@ -904,7 +906,7 @@ int run_cg(SweepSet<R>& ss, std::vector<double>& req, int maxit, std::vector<int
   xa.spec_out = ca.q;
   xa.st = P->cg_skip;
   CArgs<R> cy = ss.cy;
-  cy.data = ca.q;
+  cy.data = ca.q;   // not the mapped spectrum: the same tile with direct loads (tmap_data != data)
   cy.st = P->cg_skip;
   cy.ncomp = 6;
   GArgs<R> ga = ss.ga;

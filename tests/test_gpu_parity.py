@@ -567,6 +567,29 @@ def test_cg_at_contrast_1000_against_plain_sweeps():
     assert i1.iters * 5 < i0.iters, (i1.iters, i0.iters)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 6, 7])
+def test_cg_operator_under_every_y_pass_variant(variant, monkeypatch):
+    """The operator's y passes run on the CG vectors, not on the plan's spectrum.
+    Under every y-pass variant (the tensor-copy tiles included, whose tensor maps
+    address the spectrum), a fixed number of operator applications (the first
+    sweep, 6 CG iterations, 2 verifying sweeps) gives the FP64 plan's iterate
+    (FP64 plans have no tensor-copy tiles)."""
+    p = W.config_c1()
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    monkeypatch.setenv("BFCS_COL_VARIANT", str(variant))
+    with api.Plan(p.dims, "fp32", cg=True) as plan:
+        assert plan.tuning()["variant"] == variant
+        b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp32")
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-12, maxit=8)
+    monkeypatch.delenv("BFCS_COL_VARIANT")
+    with api.Plan(p.dims, "fp64", cg=True) as plan:
+        b = api.body_force(p.dims, p.bf_centre, p.bf_radius, "fp64")
+        e64, s64, u64, i64 = plan.solve(ph, p.phases, p.c0, b, tol=1e-12, maxit=8)
+    assert info.iters == i64.iters == 9, (info.iters, i64.iters)
+    for a, r, key in ((eps, e64, "eps"), (sig, s64, "sig"), (u, u64, "u")):
+        assert rel(a.cpu().numpy(), r.cpu().numpy()) < 1e-4, (variant, key, rel(a.cpu().numpy(), r.cpu().numpy()))
+
+
 def test_cg_inside_the_mixed_ladder_and_batched_equals_individual():
     p = W.config_c1()
     ph_o, b_o = oracle_inputs(p)
