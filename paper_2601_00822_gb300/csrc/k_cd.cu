@@ -84,11 +84,13 @@ __device__ __forceinline__ R cd_dot3(const C2<R> (&a)[3], const C2<R> (&b)[3]) {
 //  INIT:    r = b^A = i xi . s (s: F[L1 eps^{b(0)}], 6 components), u = 0, p = z = M r;
 //           partials <r, z>, <r, r>; the k = 0 thread stores s(0) in cd.s0b
 //  (z = M r is never stored: every step that needs it forms it from r)
-//  PQ:      q = -i xi . s (s: F[L grad^s p]); partial <p, q>; s(0) into cd.s0p
-//  UPDATE:  u += alpha p, r -= alpha q; partials <r, M r>, <r, r>
-//  DIR:     p = M r + beta p, s = sym(i xi (x) p) / N (6 components; 0 where xi = 0)
+//  UPDATE:  r -= alpha q; partials <r, M r>, <r, r> (u += alpha p is taken by the
+//           direction step of the fused inverse z kernel, which reads p anyway)
 //  FINAL:   s = sym(i xi (x) (G0 b_hat + u)) / N, s(0) = E (the returned strain)
 //  FINAL_U: s = (G0 b_hat + u) / N in components 0..2 (the returned displacement)
+//  (FINAL and FINAL_U add the last alpha p first when an update step ended the member)
+// The products q = A p and <p, q> (PQ) and the direction step (DIR) run fused with
+// the z transforms, in k_zcd.
 //  RESID:   partial |i xi . s + b_hat|^2 over xi != 0 (s: F[L eps]); s(0) into cd.s0u
 template <typename R>
 __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
   C2<R>* const q = a.q + m * a.ms;
   C2<R>* const s = a.s + m * a.sms;
   const C2<R>* const bh = a.bhat + m * a.b_ms;
-  const R alpha = (R)a.cd[m].alpha, beta = (R)a.cd[m].beta;
+  const R alpha = (R)a.cd[m].alpha;
   const R lam0 = (R)a.lam0, mu0 = (R)a.mu0;
   const R inv_n = R(1.0 / (double)g.n);
   const R two_pi = R(6.283185307179586);
@@ -159,49 +161,26 @@ __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
       st3(u, zero);
       acc1 += w * (double)cd_dot3<R>(rv, zv);
       acc2 += w * (double)cd_dot3<R>(rv, rv);
-    } else if (mode == CdMode::PQ) {
-      C2<R> t[6], qv[3], pv[3];
-      ld6(t);
-      if (i == 0) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) a.cd[m].s0p[k] = (double)t[k].x;
-      }
-      cd_div<R>(t, xi, qv);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) qv[k] = nz ? mk<R>(-qv[k].x, -qv[k].y) : mk<R>(0, 0);
-      st3(q, qv);
-      ld3(p, pv);
-      acc1 += w * (double)cd_dot3<R>(pv, qv);
     } else if (mode == CdMode::UPDATE) {
-      C2<R> uv[3], pv[3], rv[3], qv[3], zv[3];
-      ld3(u, uv);
-      ld3(p, pv);
+      // r -= alpha q; u1 += alpha p follows in the direction step, which reads p anyway
+      C2<R> rv[3], qv[3], zv[3];
       ld3(r, rv);
       ld3(q, qv);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        uv[k] = uv[k] + scale(pv[k], alpha);
-        rv[k] = rv[k] - scale(qv[k], alpha);
-      }
+      for (int k = 0; k < 3; ++k) rv[k] = rv[k] - scale(qv[k], alpha);
       precond(rv, zv);                 // z = M r is formed where it is used, not stored
-      st3(u, uv);
       st3(r, rv);
       acc1 += w * (double)cd_dot3<R>(rv, zv);
       acc2 += w * (double)cd_dot3<R>(rv, rv);
-    } else if (mode == CdMode::DIR) {
-      C2<R> pv[3], rv[3], zv[3], e[6];
-      ld3(p, pv);
-      ld3(r, rv);
-      precond(rv, zv);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) pv[k] = zv[k] + scale(pv[k], beta);
-      st3(p, pv);
-      cd_symgrad<R>(pv, xi, inv_n, e);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) s[k * g.cs + gi] = nz ? e[k] : mk<R>(0, 0);
     } else if (mode == CdMode::FINAL || mode == CdMode::FINAL_U) {
       C2<R> uv[3], bv[3], gb[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
       ld3(u, uv);
+      if (a.cd[m].pend) {              // the last update's alpha p, not yet added by a direction step
+        C2<R> pv[3];
+        ld3(p, pv);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) uv[k] = uv[k] + scale(pv[k], alpha);
+      }
       ld3(bh, bv);
       if (nz) cd_g0<R>(bv, xi, qq, lam0, mu0, gb);
 #pragma unroll
@@ -233,7 +212,7 @@ __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
       }
     }
   }
-  if (mode == CdMode::DIR || mode == CdMode::FINAL || mode == CdMode::FINAL_U) return;
+  if (mode == CdMode::FINAL || mode == CdMode::FINAL_U) return;
   const double t1 = cd_reduce(acc1, red);
   const double t2 = cd_reduce(acc2, red);
   if (threadIdx.x == 0) {
@@ -287,6 +266,7 @@ static __global__ void k_cd_scalar(const double* part, int nparts, CdState* cd, 
     }
     S.rz = t1;
     S.iters = 0;
+    S.alpha = 0.0;     // the first direction step adds nothing to u = 0
     S.beta = 0.0;
     S.resid = resid(S.s0b, t2);
     st.resid_last = S.resid;
@@ -312,6 +292,7 @@ static __global__ void k_cd_scalar(const double* part, int nparts, CdState* cd, 
     if (!(S.resid == S.resid)) { S.status = 3; fin = true; }
     else if (S.resid <= S.tol) { S.status = 1; fin = true; }
     else if (S.iters >= S.maxit) { S.status = 2; fin = true; }
+    S.pend = fin ? 1 : 0;
   } else {   // RESID: the true residual of the returned strain (s0u holds its sigma_hat(0))
     st.resid_final = resid(S.s0u, t1);
     st.iters = S.iters;
@@ -333,8 +314,9 @@ static __global__ void k_cd_scalar(const double* part, int nparts, CdState* cd, 
 // four-step line FFT in registers and shared memory.
 //  forward (ZFWD): stage 1 from global memory, stage 2, then per mode
 //     q = -i xi . sigma_hat (stored), the partial <p, q> and sigma_hat(0)  (PQ)
-//  inverse (ZINV): per mode p = M r + beta p (stored) and sym(i xi (x) p) / N into the
-//     tile (DIR), then the inverse transform written to the work spectrum
+//  inverse (ZINV): per mode u += alpha p and p = M r + beta p (both stored) and
+//     sym(i xi (x) p) / N into the tile (DIR), then the inverse transform written to
+//     the work spectrum
 constexpr int kCdT = 4;
 constexpr int kCdNcol = 6 * kCdT;
 template <int L> struct ZCfg {
@@ -350,10 +332,9 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
   constexpr int T = kCdT, NCOL = kCdNcol;
   constexpr int R1 = LineInfo<L>::R1, R2 = LineInfo<L>::R2;
   constexpr int TASKS = ZCfg<L>::TASKS;
-  constexpr int MPT = (T * L + ZCfg<L>::BLOCK - 1) / ZCfg<L>::BLOCK;   // modes per thread
   extern __shared__ unsigned char smem_cd[];
   C2<R>* const sm = reinterpret_cast<C2<R>*>(smem_cd);          // [n][slot], L x NCOL
-  C2<R>* const pre = sm + L * NCOL;                             // forward: p tile [arr][n][col]
+  C2<R>* const pre = sm + L * NCOL;                             // p (forward) or u (inverse) tile [arr][n][col]
   __shared__ double red[32];
   const Geo g = a.g;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -444,33 +425,26 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
     }
     return;
   }
-  // ---- inverse: r and p tiles fill the transform tile ([arr][n][col], arrays 0-2 r,
-  // 3-5 p); each thread takes its modes into registers before the tile is rewritten
-  stage(sm, a.r, 0);
-  stage(sm, a.p, 3);
+  // ---- inverse: r (arrays 0-2) and p (3-5) of mode (n, col) land in the six tile slots
+  // its strain spectrum will take (row n, slots (q ^ qs) T + col), so each mode is read
+  // and rewritten by one thread; u lands in the extra tile
+  {
+    constexpr int PER = 16 / sizeof(C2<R>);
+    constexpr int CPR = T / PER;
+    for (int idx = tid; idx < 6 * L * CPR; idx += nthr) {
+      const int part = idx % CPR, n = (idx / CPR) % L, arr = idx / (CPR * L);
+      const C2<R>* v = arr < 3 ? a.r + arr * g.cs : a.p + (arr - 3) * g.cs;
+      const int qs = (n >> 1) & 1;
+      cp_async16(sm + n * NCOL + (arr ^ qs) * T + part * PER, v + vo + n * zs + rowbase + col0 + part * PER);
+    }
+  }
+  stage(pre, a.u, 0);
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
-  C2<R> rv[MPT][3], pv[MPT][3];
-#pragma unroll
-  for (int k = 0; k < MPT; ++k) {
-    const int idx = tid + k * nthr;
-    if (idx < T * L) {
-      const int col = idx % T, n = idx / T;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        rv[k][c] = sm[(c * L + n) * T + col];
-        pv[k][c] = sm[((3 + c) * L + n) * T + col];
-      }
-    }
-  }
-  __syncthreads();
-  const R beta = (R)a.cd[m].beta;
+  const R alpha = (R)a.cd[m].alpha, beta = (R)a.cd[m].beta;
   const R inv_n = R(1.0 / (double)g.n);
-#pragma unroll
-  for (int k = 0; k < MPT; ++k) {
-    const int idx = tid + k * nthr;
-    if (idx >= T * L) continue;
+  for (int idx = tid; idx < T * L; idx += nthr) {
     const int col = idx % T, n = idx / T;
     const int kx = col0 + col;
     C2<R>* const mrow = sm + n * NCOL + col;
@@ -481,6 +455,12 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
       for (int q = 0; q < 6; ++q) M(q) = mk<R>(0, 0);
       continue;
     }
+    C2<R> rv[3], pv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rv[c] = M(c);
+      pv[c] = M(3 + c);
+    }
     R xi[3];
     xi[0] = dk0 * R(signed_k(kx, g.nx));
     xi[1] = dk1 * R(signed_k(ky, g.ny));
@@ -489,18 +469,19 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
     const bool nz = qq != R(0);
     C2<R> zv[3], e[6];
     if (a.precond && nz) {                         // z = G0 r, formed here rather than stored
-      cd_g0<R>(rv[k], xi, qq, (R)a.lam0, (R)a.mu0, zv);
+      cd_g0<R>(rv, xi, qq, (R)a.lam0, (R)a.mu0, zv);
     } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) zv[c] = a.precond ? mk<R>(0, 0) : rv[k][c];
+      for (int c = 0; c < 3; ++c) zv[c] = a.precond ? mk<R>(0, 0) : rv[c];
     }
     const long long gi = n * zs + rowbase + kx;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      pv[k][c] = zv[c] + scale(pv[k][c], beta);
-      a.p[vo + c * g.cs + gi] = pv[k][c];
+      a.u[vo + c * g.cs + gi] = pre[(c * L + n) * T + col] + scale(pv[c], alpha);   // u1 += alpha p
+      pv[c] = zv[c] + scale(pv[c], beta);
+      a.p[vo + c * g.cs + gi] = pv[c];
     }
-    cd_symgrad<R>(pv[k], xi, inv_n, e);
+    cd_symgrad<R>(pv, xi, inv_n, e);
 #pragma unroll
     for (int q = 0; q < 6; ++q) M(q) = nz ? e[q] : mk<R>(0, 0);
   }
@@ -535,7 +516,7 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
 template <typename R, int L>
 static cudaError_t zcd_L(const CdArgs<R>& a, bool fwd, int batch, cudaStream_t st) {
   const dim3 grid((a.g.mx + kCdT - 1) / kCdT, a.g.ny, batch);
-  const size_t smem = sizeof(C2<R>) * (size_t)L * (kCdNcol + (fwd ? 3 * kCdT : 0));   // + the p tile (forward)
+  const size_t smem = sizeof(C2<R>) * (size_t)L * (kCdNcol + 3 * kCdT);   // + the p (forward) or u tile
   auto k = fwd ? k_zcd<R, L, true> : k_zcd<R, L, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -569,7 +550,7 @@ cudaError_t launch_cd_vec(const CdArgs<R>& a, int mode, int batch, IterState* is
                           cudaStream_t st) {
   k_cd_vec<R><<<dim3(kCdParts, batch), kCdThreads, 0, st>>>(a, mode);
   count_launches(1);
-  if (mode == CdMode::DIR || mode == CdMode::FINAL || mode == CdMode::FINAL_U) return cudaGetLastError();
+  if (mode == CdMode::FINAL || mode == CdMode::FINAL_U) return cudaGetLastError();
   k_cd_scalar<<<batch, kCdThreads, 0, st>>>(a.part, kCdParts, a.cd, a.skip, ist, mem, a.lam0, a.mu0,
                                             (double)a.g.n, maxdim, mode);
   count_launches(1);

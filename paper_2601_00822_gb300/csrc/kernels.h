@@ -113,7 +113,7 @@ template <typename R> struct CgArgs {
 template <typename R> cudaError_t launch_cg_vec(const CgArgs<R>& a, int mode, int batch, cudaStream_t st);
 
 // ---- displacement-based conjugate gradients, Algorithm 3 (k_cd.cu)
-struct CdMode { enum : int { INIT = 0, PQ = 1, UPDATE = 2, DIR = 3, FINAL = 4, FINAL_U = 5, RESID = 6 }; };
+struct CdMode { enum : int { INIT = 0, PQ = 1, UPDATE = 2, FINAL = 4, FINAL_U = 5, RESID = 6 }; };
 struct CdState {
   double rz;             // <r, z> (<r, r> without preconditioner)
   double alpha, beta;
@@ -124,6 +124,8 @@ struct CdState {
   double resid;          // residual of the current iterate
   int done, iters, maxit;
   int status;            // 0 running, 1 converged, 2 iteration limit, 3 breakdown or NaN
+  int pend;              // 1: an update step ended the member before its direction step
+                         // added alpha p to u1 (the final steps add it)
 };
 constexpr int kCdParts = 512;       // partial sums (pairs) per member
 template <typename R> struct CdArgs {

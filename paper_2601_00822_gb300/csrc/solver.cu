@@ -838,6 +838,24 @@ int run_sets(std::vector<SweepSet<R>*>& sets, int maxit) {
   return BFCS_OK;
 }
 
+// Chunk sizing of the Krylov loops, which read the members' device states after
+// each chunk of iterations (iterations enqueued past a member's stop are skipped
+// on the device but still cost their launches).  predict_left: from the residual r
+// at iteration `it` and the one observed before (r_obs at it_obs), the iterations
+// still needed to reach tol at the observed contraction rate, raised into `need`;
+// false when unknown (no earlier observation, no decrease, no tolerance).
+// next_chunk: that many plus one (2..64), else twice the last chunk.
+static bool predict_left(double r, double tol, int it, double r_obs, int it_obs, double& need) {
+  if (!(tol > 0) || !(r > 0) || !std::isfinite(r) || it_obs < 0 || it <= it_obs || !(r < r_obs)) return false;
+  const double rate = std::pow(r / r_obs, 1.0 / (it - it_obs));
+  need = std::max(need, std::log(tol / r) / std::log(rate));
+  return true;
+}
+static int next_chunk(bool known, double need, int chunk) {
+  if (!known) return std::min(chunk * 2, 64);
+  return std::max(2, std::min(64, (int)std::ceil(need) + 1));
+}
+
 // Conjugate gradients (Algorithm 2, operator of Eq. 5.13) from the current
 // state of every member of the set: c = the state, one standard sweep gives
 // s, r = p = s - c (the fixed-point residual is the CG residual), then
@@ -925,6 +943,8 @@ int run_cg(SweepSet<R>& ss, std::vector<double>& req, int maxit, std::vector<int
     return BFCS_OK;
   };
   int done_all = 0, it = 0, chunk = 8;
+  std::vector<double> obs_r(B, -1.0);
+  std::vector<int> obs_it(B, -1);
   while (!done_all && it < maxit) {
     const int c = std::min(chunk, maxit - it);
     for (int k = 0; k < c; ++k) {
@@ -932,12 +952,23 @@ int run_cg(SweepSet<R>& ss, std::vector<double>& req, int maxit, std::vector<int
       if (e != BFCS_OK) return e;
     }
     it += c;
-    chunk = std::min(chunk * 2, 64);
     CK(read_small(P->cg_host, P->cg_state, B * sizeof(CgState), st));
     const int w = sync_stream(P);
     if (w != BFCS_OK) return w;
     done_all = 1;
-    for (int m = 0; m < B; ++m) done_all = done_all && P->cg_host[m].done;
+    double need = 0.0;
+    bool known = true;
+    for (int m = 0; m < B; ++m) {
+      const CgState& h = P->cg_host[m];
+      if (h.done) continue;
+      done_all = 0;
+      // the stop test compares <r, r> with tol2 <r0, r0>: norms, squared
+      const double r = h.rr > 0 ? std::sqrt(h.rr) : -1.0;
+      known = known && predict_left(r, std::sqrt(h.tol2 * h.rr0), h.iters, obs_r[m], obs_it[m], need);
+      obs_r[m] = r;
+      obs_it[m] = h.iters;
+    }
+    chunk = next_chunk(known, need, chunk);
   }
   for (int m = 0; m < B; ++m)
     if (!finished[m]) applied[m] += 1 + P->cg_host[m].iters;   // finished members skipped both
@@ -1023,6 +1054,8 @@ int run_cd(SweepSet<R>& ss, int maxit, bfcs_info* infos) {
   cy.st = P->cg_skip;
   cz.st = P->cg_skip;
   int it = 0, chunk = 8;
+  std::vector<double> obs_r(B, -1.0);
+  std::vector<int> obs_it(B, -1);
   while (it < maxit) {
     const int c = std::min(chunk, maxit - it);
     for (int k = 0; k < c; ++k) {
@@ -1034,13 +1067,22 @@ int run_cd(SweepSet<R>& ss, int maxit, bfcs_info* infos) {
       CK(launch_zcd<R>(a, false, B, P->ist, P->mem_dev, maxdim, st));
     }
     it += c;
-    chunk = std::min(chunk * 2, 64);
     CK(read_small(P->cd_host, P->cd_state, B * sizeof(CdState), st));
     const int w = sync_stream(P);
     if (w != BFCS_OK) return w;
     bool all = true;
-    for (int m = 0; m < B; ++m) all = all && P->cd_host[m].done;
+    double need = 0.0;
+    bool known = true;
+    for (int m = 0; m < B; ++m) {
+      const CdState& h = P->cd_host[m];
+      if (h.done) continue;
+      all = false;
+      known = known && predict_left(h.resid, h.tol, h.iters, obs_r[m], obs_it[m], need);
+      obs_r[m] = h.resid;
+      obs_it[m] = h.iters;
+    }
     if (all) break;
+    chunk = next_chunk(known, need, chunk);
   }
   // the returned strain eps^{b(0)} + grad^s u1 (and sigma), its residual, the displacement
   cy.st = nullptr;
