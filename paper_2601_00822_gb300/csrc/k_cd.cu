@@ -36,15 +36,21 @@ __device__ __forceinline__ double cd_reduce(double v, double* red) {
 }
 
 // v = G0(xi) w: the inverse of the isotropic acoustic tensor mu0 |xi|^2 I + (lam0 +
-// mu0) xi xi (Eqs. 2.6, 2.8), per mode
+// mu0) xi xi (Eqs. 2.6, 2.8), per mode; g0c = {(lam0 + mu0) / (lam0 + 2 mu0), 1 / mu0}
+template <typename R> struct G0c { R c, inv_mu0; };
+template <typename R> __device__ __forceinline__ G0c<R> g0_consts(double lam0, double mu0) {
+  const R l = R(lam0), m = R(mu0);      // in R: no FP64 division on the device
+  return G0c<R>{(l + m) / (l + R(2) * m), R(1) / m};
+}
 template <typename R>
-__device__ __forceinline__ void cd_g0(const C2<R> (&w)[3], const R (&xi)[3], R qq, R lam0, R mu0, C2<R> (&v)[3]) {
+__device__ __forceinline__ void cd_g0(const C2<R> (&w)[3], const R (&xi)[3], R qq, G0c<R> g0c, C2<R> (&v)[3]) {
   const R iq = R(1) / qq;
-  const R c = (lam0 + mu0) / (lam0 + R(2) * mu0);
+  const R f = iq * g0c.inv_mu0;
   const C2<R> xw = scale(w[0], xi[0]) + scale(w[1], xi[1]) + scale(w[2], xi[2]);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) v[k] = scale(w[k] - scale(xw, c * xi[k] * iq), iq / mu0);
+  for (int k = 0; k < 3; ++k) v[k] = scale(w[k] - scale(xw, g0c.c * xi[k] * iq), f);
 }
+
 
 // sym(i xi (x) v) in 6-component storage (xx yy zz yz xz xy), times f
 template <typename R>
@@ -88,10 +94,10 @@ __device__ __forceinline__ R cd_dot3(const C2<R> (&a)[3], const C2<R> (&b)[3]) {
 //           direction step of the fused inverse z kernel, which reads p anyway)
 //  FINAL:   s = sym(i xi (x) (G0 b_hat + u)) / N, s(0) = E (the returned strain)
 //  FINAL_U: s = (G0 b_hat + u) / N in components 0..2 (the returned displacement)
+//  RESID:   partial |i xi . s + b_hat|^2 over xi != 0 (s: F[L eps]); s(0) into cd.s0u
 //  (FINAL and FINAL_U add the last alpha p first when an update step ended the member)
 // The products q = A p and <p, q> (PQ) and the direction step (DIR) run fused with
 // the z transforms, in k_zcd.
-//  RESID:   partial |i xi . s + b_hat|^2 over xi != 0 (s: F[L eps]); s(0) into cd.s0u
 template <typename R>
 __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
   const int m = blockIdx.y;
@@ -105,112 +111,132 @@ __global__ void __launch_bounds__(kCdThreads) k_cd_vec(CdArgs<R> a, int mode) {
   C2<R>* const q = a.q + m * a.ms;
   C2<R>* const s = a.s + m * a.sms;
   const C2<R>* const bh = a.bhat + m * a.b_ms;
-  const R alpha = (R)a.cd[m].alpha;
-  const R lam0 = (R)a.lam0, mu0 = (R)a.mu0;
-  const R inv_n = R(1.0 / (double)g.n);
+  __shared__ R cst[3];          // alpha and G0's constants, converted once per block
+  if (threadIdx.x == 0) {
+    const G0c<R> c = g0_consts<R>(a.lam0, a.mu0);
+    cst[0] = (R)a.cd[m].alpha;
+    cst[1] = c.c;
+    cst[2] = c.inv_mu0;
+  }
+  __syncthreads();
+  const R alpha = cst[0];
+  const G0c<R> g0c{cst[1], cst[2]};
+  const R inv_n = R(1) / R(g.n);
   const R two_pi = R(6.283185307179586);
   const R dk0 = two_pi / R(g.nx), dk1 = two_pi / R(g.ny), dk2 = two_pi / R(g.nz);
   const long long modes = (long long)g.nz * g.ny * g.mx;
+  // partial sums: 16 grid-stride modes in R (their products are R), then one FP64 add,
+  // so few FP64 instructions run (GB300 issues FP64 at a small fraction of the FP32 rate)
   double acc1 = 0.0, acc2 = 0.0;
+  const int stride = gridDim.x * blockDim.x;
   // 32-bit index arithmetic: a member's spectrum has at most 256 * 256 * 129 modes
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)modes; i += gridDim.x * blockDim.x) {
-    const int kx = i % g.mx;
-    const int rr = i / g.mx;
-    const int ky = rr % g.ny, kz = rr / g.ny;
-    const long long gi = (long long)rr * g.p + kx;
-    const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
-    R xi[3];
-    xi[0] = dk0 * R(signed_k(kx, g.nx));
-    xi[1] = dk1 * R(signed_k(ky, g.ny));
-    xi[2] = dk2 * R(signed_k(kz, g.nz));
-    const R qq = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
-    const bool nz = qq != R(0);
-    auto ld3 = [&](const C2<R>* v, C2<R> (&o)[3]) {
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (int)modes; i0 += 16 * stride) {
+    R p1 = R(0), p2 = R(0);
+    for (int j = 0; j < 16; ++j) {
+      const int i = i0 + j * stride;
+      if (i >= (int)modes) break;
+      const int kx = i % g.mx;
+      const int rr = i / g.mx;
+      const int ky = rr % g.ny, kz = rr / g.ny;
+      const long long gi = (long long)rr * g.p + kx;
+      const R w = (kx == 0 || 2 * kx == g.nx) ? R(1) : R(2);
+      R xi[3];
+      xi[0] = dk0 * R(signed_k(kx, g.nx));
+      xi[1] = dk1 * R(signed_k(ky, g.ny));
+      xi[2] = dk2 * R(signed_k(kz, g.nz));
+      const R qq = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+      const bool nz = qq != R(0);
+      auto ld3 = [&](const C2<R>* v, C2<R> (&o)[3]) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) o[k] = v[k * g.cs + gi];
-    };
-    auto st3 = [&](C2<R>* v, const C2<R> (&o)[3]) {
+        for (int k = 0; k < 3; ++k) o[k] = v[k * g.cs + gi];
+      };
+      auto st3 = [&](C2<R>* v, const C2<R> (&o)[3]) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) v[k * g.cs + gi] = o[k];
-    };
-    auto ld6 = [&](C2<R> (&o)[6]) {
+        for (int k = 0; k < 3; ++k) v[k * g.cs + gi] = o[k];
+      };
+      auto ld6 = [&](C2<R> (&o)[6]) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) o[k] = s[k * g.cs + gi];
-    };
-    auto precond = [&](const C2<R> (&x)[3], C2<R> (&y)[3]) {
-      if (a.precond && nz) {
-        cd_g0<R>(x, xi, qq, lam0, mu0, y);
-      } else {
+        for (int k = 0; k < 6; ++k) o[k] = s[k * g.cs + gi];
+      };
+      auto precond = [&](const C2<R> (&x)[3], C2<R> (&y)[3]) {
+        if (a.precond && nz) {
+          cd_g0<R>(x, xi, qq, g0c, y);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) y[k] = a.precond ? mk<R>(0, 0) : x[k];
-      }
-    };
-    if (mode == CdMode::INIT) {
-      C2<R> t[6], rv[3], zv[3];
-      ld6(t);
-      if (i == 0) {
+          for (int k = 0; k < 3; ++k) y[k] = a.precond ? mk<R>(0, 0) : x[k];
+        }
+      };
+      if (mode == CdMode::INIT) {
+        C2<R> t[6], rv[3], zv[3];
+        ld6(t);
+        if (i == 0) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) a.cd[m].s0b[k] = (double)t[k].x;
-      }
-      cd_div<R>(t, xi, rv);
-      if (!nz) rv[0] = rv[1] = rv[2] = mk<R>(0, 0);
-      precond(rv, zv);
-      const C2<R> zero[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
-      st3(r, rv);
-      st3(p, zv);      // p = z (the direction step then forms the operator input with beta = 0)
-      st3(u, zero);
-      acc1 += w * (double)cd_dot3<R>(rv, zv);
-      acc2 += w * (double)cd_dot3<R>(rv, rv);
-    } else if (mode == CdMode::UPDATE) {
-      // r -= alpha q; u1 += alpha p follows in the direction step, which reads p anyway
-      C2<R> rv[3], qv[3], zv[3];
-      ld3(r, rv);
-      ld3(q, qv);
+          for (int k = 0; k < 6; ++k) a.cd[m].s0b[k] = (double)t[k].x;
+        }
+        cd_div<R>(t, xi, rv);
+        if (!nz) rv[0] = rv[1] = rv[2] = mk<R>(0, 0);
+        precond(rv, zv);
+        const C2<R> zero[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+        st3(r, rv);
+        st3(p, zv);      // p = z (the direction step then forms the operator input with beta = 0)
+        st3(u, zero);
+        p1 += w * cd_dot3<R>(rv, zv);
+        p2 += w * cd_dot3<R>(rv, rv);
+      } else if (mode == CdMode::UPDATE) {
+        // r -= alpha q; u1 += alpha p follows in the direction step, which reads p anyway
+        C2<R> rv[3], qv[3], zv[3];
+        ld3(r, rv);
+        ld3(q, qv);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) rv[k] = rv[k] - scale(qv[k], alpha);
-      precond(rv, zv);                 // z = M r is formed where it is used, not stored
-      st3(r, rv);
-      acc1 += w * (double)cd_dot3<R>(rv, zv);
-      acc2 += w * (double)cd_dot3<R>(rv, rv);
-    } else if (mode == CdMode::FINAL || mode == CdMode::FINAL_U) {
-      C2<R> uv[3], bv[3], gb[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
-      ld3(u, uv);
-      if (a.cd[m].pend) {              // the last update's alpha p, not yet added by a direction step
-        C2<R> pv[3];
-        ld3(p, pv);
+        for (int k = 0; k < 3; ++k) rv[k] = rv[k] - scale(qv[k], alpha);
+        precond(rv, zv);                 // z = M r is formed where it is used, not stored
+        st3(r, rv);
+        p1 += w * cd_dot3<R>(rv, zv);
+        p2 += w * cd_dot3<R>(rv, rv);
+      } else if (mode == CdMode::FINAL || mode == CdMode::FINAL_U) {
+        C2<R> uv[3], bv[3], gb[3] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
+        ld3(u, uv);
+        if (a.cd[m].pend) {              // the last update's alpha p, not yet added by a direction step
+          C2<R> pv[3];
+          ld3(p, pv);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) uv[k] = uv[k] + scale(pv[k], alpha);
-      }
-      ld3(bh, bv);
-      if (nz) cd_g0<R>(bv, xi, qq, lam0, mu0, gb);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) uv[k] = uv[k] + gb[k];      // u_hat = G0 b_hat + u1_hat (Eqs. 2.8, 2.10)
-      if (mode == CdMode::FINAL_U) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) s[k * g.cs + gi] = nz ? scale(uv[k], inv_n) : mk<R>(0, 0);
-      } else {
-        C2<R> e[6];
-        cd_symgrad<R>(uv, xi, inv_n, e);
-        const double* E = a.mem[m].E;
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-          s[k * g.cs + gi] = nz ? e[k] : (i == 0 ? mk<R>((R)E[k], R(0)) : mk<R>(0, 0));
-      }
-    } else {   // RESID
-      C2<R> t[6], d[3], bv[3];
-      ld6(t);
-      if (i == 0) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) a.cd[m].s0u[k] = (double)t[k].x;
-      }
-      if (nz) {
-        cd_div<R>(t, xi, d);
+          for (int k = 0; k < 3; ++k) uv[k] = uv[k] + scale(pv[k], alpha);
+        }
         ld3(bh, bv);
+        if (nz) cd_g0<R>(bv, xi, qq, g0c, gb);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] = d[k] + bv[k];
-        acc1 += w * (double)cd_dot3<R>(d, d);
+        for (int k = 0; k < 3; ++k) uv[k] = uv[k] + gb[k];      // u_hat = G0 b_hat + u1_hat (Eqs. 2.8, 2.10)
+        if (mode == CdMode::FINAL_U) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) s[k * g.cs + gi] = nz ? scale(uv[k], inv_n) : mk<R>(0, 0);
+        } else {
+          C2<R> e[6];
+          cd_symgrad<R>(uv, xi, inv_n, e);
+          const double* E = a.mem[m].E;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) s[k * g.cs + gi] = nz ? e[k] : mk<R>(0, 0);
+          if (i == 0)                  // xi = 0: the prescribed mean strain
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s[k * g.cs + gi] = mk<R>((R)E[k], R(0));
+        }
+      } else {   // RESID
+        C2<R> t[6], d[3], bv[3];
+        ld6(t);
+        if (i == 0) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) a.cd[m].s0u[k] = (double)t[k].x;
+        }
+        if (nz) {
+          cd_div<R>(t, xi, d);
+          ld3(bh, bv);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) d[k] = d[k] + bv[k];
+          p1 += w * cd_dot3<R>(d, d);
+        }
       }
     }
+    acc1 += (double)p1;
+    acc2 += (double)p2;
   }
   if (mode == CdMode::FINAL || mode == CdMode::FINAL_U) return;
   const double t1 = cd_reduce(acc1, red);
@@ -354,7 +380,7 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
       cp_async16(dst + ((arr0 + arr) * L + n) * T + part * PER, v + vo + arr * g.cs + n * zs + rowbase + col0 + part * PER);
     }
   };
-  double acc = 0.0;
+  R acc = R(0);                 // this thread's <p, q> share (at most a few modes)
   if (FWD) {
     stage(pre, a.p, 0);                                         // p lands during the transform
     cp_async_commit();
@@ -411,10 +437,11 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
         const C2<R> pk = pre[(k * L + n) * T + col];
         dot += pk.x * qv[k].x + pk.y * qv[k].y;
       }
-      acc += ((kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0) * (double)dot;
+      acc += ((kx == 0 || 2 * kx == g.nx) ? R(1) : R(2)) * dot;
     }
+    // the warp's 32 shares in R (the products themselves are R), warps in FP64
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    if ((tid & 31) == 0) red[tid >> 5] = (double)acc;
     __syncthreads();
     if (tid == 0) {
       double tsum = 0.0;
@@ -440,10 +467,19 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
   }
   stage(pre, a.u, 0);
   cp_async_commit();
+  __shared__ R cst[4];          // alpha, beta and G0's constants, converted once per block
+  if (tid == 0) {
+    const G0c<R> g0c = g0_consts<R>(a.lam0, a.mu0);
+    cst[0] = (R)a.cd[m].alpha;
+    cst[1] = (R)a.cd[m].beta;
+    cst[2] = g0c.c;
+    cst[3] = g0c.inv_mu0;
+  }
   cp_async_wait_all();
   __syncthreads();
-  const R alpha = (R)a.cd[m].alpha, beta = (R)a.cd[m].beta;
-  const R inv_n = R(1.0 / (double)g.n);
+  const R alpha = cst[0], beta = cst[1];
+  const G0c<R> g0c{cst[2], cst[3]};
+  const R inv_n = R(1) / R(g.n);
   for (int idx = tid; idx < T * L; idx += nthr) {
     const int col = idx % T, n = idx / T;
     const int kx = col0 + col;
@@ -469,7 +505,7 @@ __global__ void __launch_bounds__(ZCfg<L>::BLOCK) k_zcd(CdArgs<R> a) {
     const bool nz = qq != R(0);
     C2<R> zv[3], e[6];
     if (a.precond && nz) {                         // z = G0 r, formed here rather than stored
-      cd_g0<R>(rv, xi, qq, (R)a.lam0, (R)a.mu0, zv);
+      cd_g0<R>(rv, xi, qq, g0c, zv);
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c) zv[c] = a.precond ? mk<R>(0, 0) : rv[c];

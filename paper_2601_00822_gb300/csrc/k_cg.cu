@@ -21,10 +21,10 @@ namespace bfcs {
 constexpr int kCgThreads = 256;
 
 // Re(a : C0 : conj b) for the 6 tensorial components (xx yy zz yz xz xy), in the
-// vectors' precision (FP32 vectors: FP32 per mode, the caller sums modes in FP64;
-// GB300's FP64 pipe would otherwise bound the vector kernels)
+// vectors' precision (FP32 vectors: FP32 per mode; the caller sums 16 modes in R
+// and then adds in FP64: GB300's FP64 pipe would otherwise bound the vector kernels)
 template <typename R>
-__device__ __forceinline__ double c0dot(const C2<R> (&a)[6], const C2<R> (&b)[6], double lam0, double mu0) {
+__device__ __forceinline__ R c0dot(const C2<R> (&a)[6], const C2<R> (&b)[6], R lam0, R mu0) {
   const R ta_r = a[0].x + a[1].x + a[2].x, ta_i = a[0].y + a[1].y + a[2].y;
   const R tb_r = b[0].x + b[1].x + b[2].x, tb_i = b[0].y + b[1].y + b[2].y;
   R s = R(0);
@@ -33,7 +33,7 @@ __device__ __forceinline__ double c0dot(const C2<R> (&a)[6], const C2<R> (&b)[6]
     const R w = c < 3 ? R(1) : R(2);
     s += w * (a[c].x * b[c].x + a[c].y * b[c].y);
   }
-  return (double)((R)lam0 * (ta_r * tb_r + ta_i * tb_i) + R(2) * (R)mu0 * s);
+  return lam0 * (ta_r * tb_r + ta_i * tb_i) + R(2) * mu0 * s;
 }
 
 __device__ __forceinline__ double block_reduce(double v, double* red) {
@@ -64,44 +64,60 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_vec(CgArgs<R> a, int mode) {
   C2<R>* p = a.p + off;
   C2<R>* q = a.q + off;
   const C2<R>* s = a.s != nullptr ? a.s + off : nullptr;
-  const R alpha = (R)a.cg[m].alpha, beta = (R)a.cg[m].beta;
+  __shared__ R cst[4];          // alpha, beta, lam0, mu0, converted once per block
+  if (threadIdx.x == 0) {
+    cst[0] = (R)a.cg[m].alpha;
+    cst[1] = (R)a.cg[m].beta;
+    cst[2] = (R)a.lam0;
+    cst[3] = (R)a.mu0;
+  }
+  __syncthreads();
+  const R alpha = cst[0], beta = cst[1], lam0 = cst[2], mu0 = cst[3];
   const long long modes = (long long)g.nz * g.ny * g.mx;
+  // partial sums: 16 grid-stride modes in R (their products are R), then one FP64 add
   double acc = 0.0;
+  const int stride = gridDim.x * blockDim.x;
   // 32-bit index arithmetic: a member's spectrum has at most 256 * 256 * 129 modes
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)modes; i += gridDim.x * blockDim.x) {
-    const int kx = i % g.mx;
-    const long long gi = (long long)(i / g.mx) * g.p + kx;
-    const double w = (kx == 0 || 2 * kx == g.nx) ? 1.0 : 2.0;
-    C2<R> u[6], v[6];
-    if (mode == CgMode::INIT) {
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (int)modes; i0 += 16 * stride) {
+    R part = R(0);
+    for (int j = 0; j < 16; ++j) {
+      const int i = i0 + j * stride;
+      if (i >= (int)modes) break;
+      const int kx = i % g.mx;
+      const long long gi = (long long)(i / g.mx) * g.p + kx;
+      const R w = (kx == 0 || 2 * kx == g.nx) ? R(1) : R(2);
+      C2<R> u[6], v[6];
+      if (mode == CgMode::INIT) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const C2<R> x = s[k * g.cs + gi] - c[k * g.cs + gi];
-        r[k * g.cs + gi] = x;
-        p[k * g.cs + gi] = x;
-        u[k] = x;
+        for (int k = 0; k < 6; ++k) {
+          const C2<R> x = s[k * g.cs + gi] - c[k * g.cs + gi];
+          r[k * g.cs + gi] = x;
+          p[k * g.cs + gi] = x;
+          u[k] = x;
+        }
+        part += w * c0dot<R>(u, u, lam0, mu0);
+      } else if (mode == CgMode::PQ) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          u[k] = p[k * g.cs + gi];
+          v[k] = u[k] - q[k * g.cs + gi];
+          q[k * g.cs + gi] = v[k];
+        }
+        part += w * c0dot<R>(u, v, lam0, mu0);
+      } else if (mode == CgMode::UPDATE) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          c[k * g.cs + gi] = c[k * g.cs + gi] + scale(p[k * g.cs + gi], alpha);
+          u[k] = r[k * g.cs + gi] - scale(q[k * g.cs + gi], alpha);
+          r[k * g.cs + gi] = u[k];
+        }
+        part += w * c0dot<R>(u, u, lam0, mu0);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k * g.cs + gi] = r[k * g.cs + gi] + scale(p[k * g.cs + gi], beta);
       }
-      acc += w * c0dot<R>(u, u, a.lam0, a.mu0);
-    } else if (mode == CgMode::PQ) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        u[k] = p[k * g.cs + gi];
-        v[k] = u[k] - q[k * g.cs + gi];
-        q[k * g.cs + gi] = v[k];
-      }
-      acc += w * c0dot<R>(u, v, a.lam0, a.mu0);
-    } else if (mode == CgMode::UPDATE) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        c[k * g.cs + gi] = c[k * g.cs + gi] + scale(p[k * g.cs + gi], alpha);
-        u[k] = r[k * g.cs + gi] - scale(q[k * g.cs + gi], alpha);
-        r[k * g.cs + gi] = u[k];
-      }
-      acc += w * c0dot<R>(u, u, a.lam0, a.mu0);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) p[k * g.cs + gi] = r[k * g.cs + gi] + scale(p[k * g.cs + gi], beta);
     }
+    acc += (double)part;
   }
   if (mode == CgMode::DIR) return;
   const double t = block_reduce(acc, red);
