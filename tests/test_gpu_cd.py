@@ -121,3 +121,77 @@ def test_cd_rejects_a_warm_start():
         eps, _, _, _ = plan.solve(ph, p.phases, p.c0, b, tol=1e-3, maxit=100)
         with pytest.raises(_lib.BfcsError):
             plan.solve(ph, p.phases, p.c0, b, tol=1e-3, maxit=100, eps_init=eps.clone())
+
+
+# ---------------------------------------------------------------- degenerate cases
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "mixed"])
+@pytest.mark.parametrize("cd", ["plain", "g0"])
+def test_cd_no_load_and_no_mean_strain_give_the_zero_field(cd, precision):
+    """b = 0 and E = 0: the right-hand side b^A vanishes, so the member stops at
+    the initial step (no iteration) and every returned field is zero."""
+    p = W.config_c1()
+    ph = api.voxelize(p.dims, p.cell, p.spheres)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    b = torch.zeros((3,) + ph.shape, dtype=dt, device="cuda")
+    with api.Plan(p.dims, precision, cd=cd) as plan:
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, tol=1e-8, maxit=100)
+    assert info.status == _lib.OK and info.iters == 0
+    assert float(eps.abs().max()) == 0.0 and float(sig.abs().max()) == 0.0 and float(u.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("cd", ["plain", "g0"])
+def test_cd_homogeneous_medium_stops_at_the_reference_strain(cd):
+    """Every voxel of one phase and C0 equal to it: L1 = 0, so b^A = 0 and the
+    returned strain is the reference strain eps^{b(0)} + E of Eq. 2.8 itself, the
+    oracle's converged field of the basic scheme, without an iteration."""
+    dims = (16, 16, 16)
+    phases = [(1.0, 0.5), (3.0, 1.2)]
+    E = (0.004, -0.001, 0.002, 0.0, 0.001, -0.003)
+    ph_o = np.ones(dims, dtype=np.int8)
+    b_o = O.body_force(dims, (8.0, 8.0, 8.0), 4.0)
+    ref = O.solve(ph_o, phases, phases[1], b_o, E, tol=1e-13, maxit=50)
+    ph = torch.ones(dims, dtype=torch.int8, device="cuda")
+    b = api.body_force(dims, (8.0, 8.0, 8.0), 4.0, "fp64")
+    with api.Plan(dims, "fp64", cd=cd) as plan:
+        eps, sig, u, info = plan.solve(ph, phases, phases[1], b, E=E, tol=1e-12, maxit=50)
+    assert info.status == _lib.OK and info.iters == 0 and info.resid <= 1e-12
+    for got, key in ((eps, "eps"), (sig, "sig"), (u, "u")):
+        assert rel(got.cpu().numpy(), ref[key]) < 1e-12, (key, rel(got.cpu().numpy(), ref[key]))
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("cd", ["plain", "g0"])
+def test_cd_smallest_grid_against_the_oracle(cd, precision, bar):
+    """The 4^3 grid (lines of 4 points on every axis, one 4-column tile) with a
+    mean strain: three iterations against the oracle's Algorithm 3."""
+    p = W.Problem(name="4cubed", dims=(4, 4, 4), cell=(4, 4, 4), spheres=np.asarray([[4, 4, 4, 4, 1]], np.int32),
+                  phases=[(1.0, 0.5), (6.0, 3.0)], c0=(3.5, 1.75), bf_centre=(2.0, 2.0, 2.0), bf_radius=1.8,
+                  mean_strain=(0.01, 0.0, -0.005, 0.0, 0.002, 0.0))
+    ph_o, b_o = oracle_inputs(p)
+    ref = O.solve_cd(ph_o, p.phases, p.c0, b_o, p.mean_strain, tol=0.0, maxit=3, precondition=cd == "g0")
+    ph, b = inputs(p, precision)
+    assert np.array_equal(ph.cpu().numpy(), ph_o)
+    with api.Plan(p.dims, precision, cd=cd) as plan:
+        eps, sig, u, info = plan.solve(ph, p.phases, p.c0, b, E=p.mean_strain, tol=0.0, maxit=3)
+    assert info.iters == ref["iters"] >= 1, (info.iters, ref["iters"])
+    for got, key in ((eps, "eps"), (sig, "sig"), (u, "u")):
+        assert rel(got.cpu().numpy(), ref[key]) < bar, (key, rel(got.cpu().numpy(), ref[key]))
+
+
+def test_cd_batch_with_a_member_that_stops_at_the_start():
+    """One member without load or mean strain (done at the initial step, skipped by
+    every later kernel) next to members that iterate: each equals its own solve."""
+    p = problem("aniso_12x32x24")
+    ph, b = inputs(p, "fp32")
+    zero = torch.zeros_like(b)
+    specs = [dict(phase=ph, b=b, E=p.mean_strain, shift=(0, 0, 0)),
+             dict(phase=ph, b=zero, E=(0.0,) * 6, shift=(3, 5, 7)),
+             dict(phase=ph, b=b, E=(0.0,) * 6, shift=(11, 2, 9))]
+    with api.Plan(p.dims, "fp32", max_batch=3, cd="g0") as plan, api.Plan(p.dims, "fp32", cd="g0") as one:
+        members, infos = plan.solve_batched([dict(s) for s in specs], p.phases, p.c0, tol=1e-5, maxit=500)
+        assert infos[1].iters == 0 and float(members[1]["eps_out"].abs().max()) == 0.0
+        for m, s, info in zip(members, specs, infos):
+            (mo,), (io,) = one.solve_batched([dict(s)], p.phases, p.c0, tol=1e-5, maxit=500)
+            assert info.status == io.status == _lib.OK and info.iters == io.iters
+            for key in ("eps_out", "sig_out", "u_out"):
+                assert torch.equal(m[key], mo[key]), (s["shift"], key)
