@@ -40,6 +40,7 @@ EXPORTS = (
     "bfcs_net_train_step", "bfcs_net_predict", "bfcs_plan_tuning", "bfcs_solve_group", "bfcs_net_status",
     "bfcs_effective_stiffness", "bfcs_ensemble_average", "bfcs_radial_profile", "bfcs_rve_size",
     "bfcs_kernel_fit", "bfcs_kernel_apply", "bfcs_polarize", "bfcs_green_apply", "bfcs_profile_green_io",
+    "bfcs_twiddles",
 )
 NET_PARAMS = 523654
 NET_TRAIN = 1
@@ -90,6 +91,7 @@ def _declare(lib):
     lib.bfcs_polarize.argtypes = [vp, vp, i, C.POINTER(Lame), Lame, vp, vp]
     lib.bfcs_green_apply.argtypes = [vp, Lame, C.POINTER(d), vp, vp, vp, vp]
     lib.bfcs_last_history.argtypes = [vp, C.POINTER(d), i]
+    lib.bfcs_twiddles.argtypes = [i, i, vp, i]
     lib.bfcs_kernel_launches.argtypes = []
     lib.bfcs_profile_kernel.argtypes = [vp, i]
     lib.bfcs_profile_read.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(d)]

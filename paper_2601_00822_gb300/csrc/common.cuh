@@ -259,6 +259,20 @@ template <int L> struct LineInfo {
   static constexpr int RMAX = R1 > R2 ? R1 : R2;
 };
 
+// Factored stage-1 twiddles.  With the first radix R1 (R1 % 4 == 0, R1 >= 8) a
+// stage-1 thread n2 needs W^(n2 b) (b = 1..3) and W^(4 n2 a) (a = 1..R1/4-1); the
+// twiddle table of a line of length L holds them after its L entries W^j, laid
+// out [entry][n2] so that the threads of consecutive n2 read consecutive values
+// (one 128-byte line per warp load, where the strided W^((4 n2 a) mod L) spans up
+// to 12).  The values equal the entries W^((n2 b) mod L), W^((4 n2 a) mod L).
+// One block per eligible radix of the line (Fac<L>::R1, then Fac<L>::R2 if it
+// differs); float and double tables only (float-float keeps the plain table).
+constexpr bool tw_factored(int r1) { return r1 % 4 == 0 && r1 >= 8; }
+constexpr int tw_block(int L, int r1) { return tw_factored(r1) ? (r1 / 4 + 2) * (L / r1) : 0; }
+template <int L, int R1> constexpr int tw_offset() {
+  return L + (R1 == Fac<L>::R1 ? 0 : tw_block(L, Fac<L>::R1));
+}
+
 // Shared-memory four-step FFT over NCOL independent lines of length L stored
 // column-wise: element n of line f at s[n * NCOL + f].  Needs at least
 // NCOL * RMAX threads (one task per thread per stage so it can run in place);
@@ -324,12 +338,13 @@ __device__ __forceinline__ void stage1f(C2<R>* x, int n2, const C2<R>* __restric
     // W^(n2 k1) with k1 = 4 a + b as W^(4 n2 a) W^(n2 b): R1/4 - 1 + 3 table loads
     // and (R1/4 - 1) * 3 products instead of R1 - 1 loads (each product adds about
     // one rounding; float-float keeps the table, where a product costs more than a load)
-    constexpr int A = R1 / 4;
+    constexpr int A = R1 / 4, N2 = L / R1;
+    const C2<R>* const f = tw + tw_offset<L, R1>() + n2;   // factored table, [entry][n2]
     C2<R> wb[4], wa[A];
 #pragma unroll
-    for (int b = 1; b < 4; ++b) wb[b] = tw[(n2 * b) % L];
+    for (int b = 1; b < 4; ++b) wb[b] = f[(b - 1) * N2];
 #pragma unroll
-    for (int a = 1; a < A; ++a) wa[a] = tw[(n2 * 4 * a) % L];
+    for (int a = 1; a < A; ++a) wa[a] = f[(a + 2) * N2];
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) {
       const int a = k1 / 4, b = k1 % 4;
@@ -354,12 +369,13 @@ __device__ __forceinline__ void stage1f(C2<R>* x, int n2, const C2<R>* __restric
 template <typename R, int L, int R1, int DIR>
 __device__ __forceinline__ void twiddle_then_dft(C2<R>* x, int n2, const C2<R>* __restrict__ tw) {
   if constexpr (R1 % 4 == 0 && R1 >= 8 && sizeof(R) <= 8 && !std::is_same<R, ff>::value) {
-    constexpr int A = R1 / 4;
+    constexpr int A = R1 / 4, N2 = L / R1;
+    const C2<R>* const f = tw + tw_offset<L, R1>() + n2;   // factored table, [entry][n2]
     C2<R> wb[4], wa[A];
 #pragma unroll
-    for (int b = 1; b < 4; ++b) wb[b] = tw[(n2 * b) % L];
+    for (int b = 1; b < 4; ++b) wb[b] = f[(b - 1) * N2];
 #pragma unroll
-    for (int a = 1; a < A; ++a) wa[a] = tw[(n2 * 4 * a) % L];
+    for (int a = 1; a < A; ++a) wa[a] = f[(a + 2) * N2];
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) {
       const int a = k1 / 4, b = k1 % 4;

@@ -149,17 +149,56 @@ cudaError_t read_small(void* host, const void* dev, size_t bytes, cudaStream_t s
   return cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st);
 }
 
+// The radices (R1, R2) of Fac<n>, on the host.
+static void line_radices(int n, int& r1, int& r2) {
+  switch (n) {
+    case 4: r1 = 2; r2 = 2; break;    case 6: r1 = 3; r2 = 2; break;    case 8: r1 = 4; r2 = 2; break;
+    case 12: r1 = 4; r2 = 3; break;   case 16: r1 = 4; r2 = 4; break;   case 24: r1 = 8; r2 = 3; break;
+    case 32: r1 = 8; r2 = 4; break;   case 48: r1 = 8; r2 = 6; break;   case 64: r1 = 8; r2 = 8; break;
+    case 96: r1 = 16; r2 = 6; break;  case 128: r1 = 16; r2 = 8; break; case 192: r1 = 16; r2 = 12; break;
+    case 256: r1 = 16; r2 = 16; break;
+    default: r1 = r2 = 0; break;
+  }
+}
+
+// Twiddles W^j = exp(-2 pi i j / n), j < n, then (FP32 and FP64 tables) the
+// factored stage-1 blocks that tw_offset / stage1f read: for each eligible
+// first radix r (Fac<n>::R1, then Fac<n>::R2 if it differs), entries
+// [b - 1][n2] = W^((n2 b) mod n), b = 1..3, and [a + 2][n2] = W^((4 n2 a) mod n),
+// a = 1..r/4-1, for n2 < n / r.
+template <typename R>
+std::vector<C2<R>> twiddle_table(int n) {
+  auto w = [&](long long j) {
+    const double t = 2.0 * 3.14159265358979323846 * (double)(j % n) / n;
+    C2<R> c;
+    c.x = (R)std::cos(t);
+    c.y = (R)(-std::sin(t));
+    return c;
+  };
+  std::vector<C2<R>> h(n);
+  for (int j = 0; j < n; ++j) h[j] = w(j);
+  if (!std::is_same<R, ff>::value) {
+    int r1 = 0, r2 = 0;
+    line_radices(n, r1, r2);
+    for (int k = 0; k < 2; ++k) {
+      const int r = k == 0 ? r1 : r2;
+      if (!tw_factored(r) || (k == 1 && r2 == r1)) continue;   // one block per distinct radix
+      const int n2s = n / r;
+      for (int b = 1; b < 4; ++b)
+        for (int n2 = 0; n2 < n2s; ++n2) h.push_back(w((long long)n2 * b));
+      for (int a = 1; a < r / 4; ++a)
+        for (int n2 = 0; n2 < n2s; ++n2) h.push_back(w(4LL * n2 * a));
+    }
+  }
+  return h;
+}
+
 template <typename R>
 void* make_twiddles(int n) {
-  std::vector<C2<R>> h(n);
-  for (int j = 0; j < n; ++j) {
-    const double t = 2.0 * 3.14159265358979323846 * j / n;
-    h[j].x = (R)std::cos(t);
-    h[j].y = (R)(-std::sin(t));
-  }
+  const std::vector<C2<R>> h = twiddle_table<R>(n);
   void* d = nullptr;
-  if (cudaMalloc(&d, sizeof(C2<R>) * n) != cudaSuccess) return nullptr;
-  if (cudaMemcpy(d, h.data(), sizeof(C2<R>) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMalloc(&d, sizeof(C2<R>) * h.size()) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, h.data(), sizeof(C2<R>) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(d);
     return nullptr;
   }
@@ -2453,6 +2492,20 @@ int bfcs_profile_read(bfcs_plan P, long long* launches, double* total_ms) {
   P->prof_launches = 0;
   P->prof_ms = 0.0;
   return BFCS_OK;
+}
+
+int bfcs_twiddles(int n, int precision, void* out, int cap) {
+  int r1 = 0, r2 = 0;
+  line_radices(n, r1, r2);
+  if (r1 == 0 || (precision != BFCS_FP32 && precision != BFCS_FP64) || cap < 0) return BFCS_ERR_INVALID_ARG;
+  if (precision == BFCS_FP32) {
+    const std::vector<C2<float>> h = twiddle_table<float>(n);
+    if (out != nullptr && (int)h.size() <= cap) std::memcpy(out, h.data(), h.size() * sizeof(C2<float>));
+    return (int)h.size();
+  }
+  const std::vector<C2<double>> h = twiddle_table<double>(n);
+  if (out != nullptr && (int)h.size() <= cap) std::memcpy(out, h.data(), h.size() * sizeof(C2<double>));
+  return (int)h.size();
 }
 
 int bfcs_last_history(bfcs_plan P, double* hist, int cap) {

@@ -108,3 +108,46 @@ def test_new_entry_points_reject_bad_arguments_before_device_work():
     for a, tol_f in ((0.0, 0.05), (3.0, 0.0), (-1.0, 0.05)):  # support radius and field tolerance must be positive
         assert lib.bfcs_rve_size(8, 8, 8, 1, sph, 2, lame, c0, a, 2, sizes_ok, 0, 1e-6, 100, tol_f, rec, None,
                                  ctypes.byref(acc), None) == _lib.ERR_INVALID_ARG
+
+
+# the four-step split L = R1 R2 of every supported line length (the first radix
+# runs first; the y passes' swapped variants run R2 first)
+SPLITS = {4: (2, 2), 6: (3, 2), 8: (4, 2), 12: (4, 3), 16: (4, 4), 24: (8, 3), 32: (8, 4), 48: (8, 6),
+          64: (8, 8), 96: (16, 6), 128: (16, 8), 192: (16, 12), 256: (16, 16)}
+
+
+def test_twiddle_tables_hold_the_factored_stage_one_blocks():
+    """The table a plan uploads (host-only call): W^j for j < n, then one block per
+    distinct first radix r (r % 4 == 0, r >= 8) read by the transform's first step
+    as block[entry][n2]: every value read there, at the offset the device computes,
+    is inside the table and equals W^((n2 b) mod n) or W^((4 n2 a) mod n) bit for
+    bit (the same entries of the plain table)."""
+    import numpy as np
+    lib = _lib.load()
+    for n, (r1, r2) in SPLITS.items():
+        for prec, dt, tol in ((_lib.FP32, np.float32, 2e-7), (_lib.FP64, np.float64, 2e-15)):
+            cnt = lib.bfcs_twiddles(n, prec, None, 0)
+            buf = np.zeros(2 * cnt, dtype=dt)
+            assert lib.bfcs_twiddles(n, prec, buf.ctypes.data, cnt) == cnt
+            tab = buf[0::2].astype(np.float64) + 1j * buf[1::2].astype(np.float64)
+            j = np.arange(n)
+            assert np.abs(tab[:n] - np.exp(-2j * np.pi * j / n)).max() <= tol, (n, prec)
+
+            def block(r):
+                return (r // 4 + 2) * (n // r) if r % 4 == 0 and r >= 8 else 0
+
+            expect = n + block(r1) + (block(r2) if r2 != r1 else 0)
+            assert cnt == expect, (n, prec, cnt, expect)
+            for r in (r1, r2):
+                if block(r) == 0:
+                    continue
+                off = n + (0 if r == r1 else block(r1))            # the device's offset rule
+                n2s = n // r
+                assert off + block(r) <= cnt, (n, r)
+                for n2 in range(n2s):
+                    for b in (1, 2, 3):
+                        assert tab[off + (b - 1) * n2s + n2] == tab[(n2 * b) % n], (n, r, n2, b)
+                    for a in range(1, r // 4):
+                        assert tab[off + (a + 2) * n2s + n2] == tab[(4 * n2 * a) % n], (n, r, n2, a)
+    assert lib.bfcs_twiddles(10, _lib.FP32, None, 0) == _lib.ERR_INVALID_ARG
+    assert lib.bfcs_twiddles(256, 7, None, 0) == _lib.ERR_INVALID_ARG
