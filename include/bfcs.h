@@ -575,16 +575,20 @@ int bfcs_last_history(bfcs_plan plan, double* hist, int cap);
 
 /* bfcs_twiddles - host-only diagnostic (no device work): the twiddle table a
  * plan uploads for a line of length n (one of the grid sizes above) in
- * precision BFCS_FP32 (float pairs) or BFCS_FP64 (double pairs), written to
- * host memory `out` as interleaved (re, im) values.  Entries 0..n-1 are
+ * precision BFCS_FP32 (float pairs), BFCS_FP64 (double pairs) or BFCS_MIXED
+ * (the ladder's float-float table: per entry the float pairs (hi, lo) of the
+ * real part, then of the imaginary part), written to host memory `out` as
+ * interleaved (re, im) values.  Entries 0..n-1 are
  * W^j = exp(-2 pi i j / n), the factors of the forward transform of Eq. 4.3.
  * Then, for each distinct first radix r of the line's four-step split that is
  * a multiple of 4 and at least 8 (the split's first radix, then its second),
  * a block [entry][n2] of (r/4 + 2) * (n/r) values: W^((n2 b) mod n) for
  * b = 1..3, then W^((4 n2 a) mod n) for a = 1..r/4-1, n2 < n/r; the
  * transform's first step reads them with consecutive n2 in consecutive
- * threads.  Returns the number of complex entries (a NULL out or a too small
- * cap only returns the count) or BFCS_ERR_INVALID_ARG. */
+ * threads.  A float-float table holds instead one block [k1 - 1][n2] =
+ * W^((n2 k1) mod n), k1 = 1..r1-1, n2 < n/r1, for the split's first radix r1.
+ * Returns the number of complex entries (a NULL out or a too small cap only
+ * returns the count) or BFCS_ERR_INVALID_ARG. */
 int bfcs_twiddles(int n, int precision, void* out, int cap);
 
 const char* bfcs_status_string(int status);

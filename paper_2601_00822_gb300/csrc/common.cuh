@@ -266,7 +266,9 @@ template <int L> struct LineInfo {
 // (one 128-byte line per warp load, where the strided W^((4 n2 a) mod L) spans up
 // to 12).  The values equal the entries W^((n2 b) mod L), W^((4 n2 a) mod L).
 // One block per eligible radix of the line (Fac<L>::R1, then Fac<L>::R2 if it
-// differs); float and double tables only (float-float keeps the plain table).
+// differs) in float and double tables.  Float-float tables, where a product costs
+// more than a load, hold instead the block [k1 - 1][n2] = W^((n2 k1) mod L),
+// k1 = 1..R1-1, n2 < L/R1, for R1 = Fac<L>::R1.
 constexpr bool tw_factored(int r1) { return r1 % 4 == 0 && r1 >= 8; }
 constexpr int tw_block(int L, int r1) { return tw_factored(r1) ? (r1 / 4 + 2) * (L / r1) : 0; }
 template <int L, int R1> constexpr int tw_offset() {
@@ -349,6 +351,18 @@ __device__ __forceinline__ void stage1f(C2<R>* x, int n2, const C2<R>* __restric
     for (int k1 = 1; k1 < R1; ++k1) {
       const int a = k1 / 4, b = k1 % 4;
       C2<R> w = a == 0 ? wb[b] : b == 0 ? wa[a] : cmul(wa[a], wb[b]);
+      if (DIR > 0) w.y = -w.y;
+      x[k1] = cmul(x[k1], w);
+    }
+  } else if constexpr (std::is_same<R, ff>::value && R1 == Fac<L>::R1) {
+    // float-float: W^((n2 k1) mod L) from the table's block [k1 - 1][n2] after its
+    // L entries (consecutive threads read consecutive values; the strided look-ups
+    // of 16-byte entries spanned up to 29 lines per warp load)
+    constexpr int N2 = L / R1;
+    const C2<R>* const f = tw + L + n2;
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      C2<R> w = f[(k1 - 1) * N2];
       if (DIR > 0) w.y = -w.y;
       x[k1] = cmul(x[k1], w);
     }

@@ -165,7 +165,8 @@ static void line_radices(int n, int& r1, int& r2) {
 // factored stage-1 blocks that tw_offset / stage1f read: for each eligible
 // first radix r (Fac<n>::R1, then Fac<n>::R2 if it differs), entries
 // [b - 1][n2] = W^((n2 b) mod n), b = 1..3, and [a + 2][n2] = W^((4 n2 a) mod n),
-// a = 1..r/4-1, for n2 < n / r.
+// a = 1..r/4-1, for n2 < n / r; float-float tables instead [k1 - 1][n2] =
+// W^((n2 k1) mod n), k1 = 1..r1-1, for the first radix r1.
 template <typename R>
 std::vector<C2<R>> twiddle_table(int n) {
   auto w = [&](long long j) {
@@ -177,7 +178,12 @@ std::vector<C2<R>> twiddle_table(int n) {
   };
   std::vector<C2<R>> h(n);
   for (int j = 0; j < n; ++j) h[j] = w(j);
-  if (!std::is_same<R, ff>::value) {
+  if (std::is_same<R, ff>::value) {     // float-float: [k1 - 1][n2] = W^(n2 k1), k1 < r1
+    int r1 = 0, r2 = 0;
+    line_radices(n, r1, r2);
+    for (int k1 = 1; k1 < r1; ++k1)
+      for (int n2 = 0; n2 < n / r1; ++n2) h.push_back(w((long long)n2 * k1));
+  } else {
     int r1 = 0, r2 = 0;
     line_radices(n, r1, r2);
     for (int k = 0; k < 2; ++k) {
@@ -2497,7 +2503,13 @@ int bfcs_profile_read(bfcs_plan P, long long* launches, double* total_ms) {
 int bfcs_twiddles(int n, int precision, void* out, int cap) {
   int r1 = 0, r2 = 0;
   line_radices(n, r1, r2);
-  if (r1 == 0 || (precision != BFCS_FP32 && precision != BFCS_FP64) || cap < 0) return BFCS_ERR_INVALID_ARG;
+  if (r1 == 0 || (precision != BFCS_FP32 && precision != BFCS_FP64 && precision != BFCS_MIXED) || cap < 0)
+    return BFCS_ERR_INVALID_ARG;
+  if (precision == BFCS_MIXED) {
+    const std::vector<C2<ff>> h = twiddle_table<ff>(n);
+    if (out != nullptr && (int)h.size() <= cap) std::memcpy(out, h.data(), h.size() * sizeof(C2<ff>));
+    return (int)h.size();
+  }
   if (precision == BFCS_FP32) {
     const std::vector<C2<float>> h = twiddle_table<float>(n);
     if (out != nullptr && (int)h.size() <= cap) std::memcpy(out, h.data(), h.size() * sizeof(C2<float>));

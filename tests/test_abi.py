@@ -151,3 +151,25 @@ def test_twiddle_tables_hold_the_factored_stage_one_blocks():
                         assert tab[off + (a + 2) * n2s + n2] == tab[(4 * n2 * a) % n], (n, r, n2, a)
     assert lib.bfcs_twiddles(10, _lib.FP32, None, 0) == _lib.ERR_INVALID_ARG
     assert lib.bfcs_twiddles(256, 7, None, 0) == _lib.ERR_INVALID_ARG
+
+
+def test_float_float_twiddle_tables_hold_the_stage_one_block():
+    """The ladder's float-float table (host-only call): W^j for j < n to float-float
+    accuracy, then the block [k1 - 1][n2] that the transform's first step reads, at
+    the offset n, equal bit for bit to the plain entries W^((n2 k1) mod n)."""
+    import numpy as np
+    lib = _lib.load()
+    for n, (r1, _) in SPLITS.items():
+        cnt = lib.bfcs_twiddles(n, _lib.MIXED, None, 0)
+        assert cnt == n + (r1 - 1) * (n // r1), (n, cnt)
+        buf = np.zeros(4 * cnt, dtype=np.float32)
+        assert lib.bfcs_twiddles(n, _lib.MIXED, buf.ctypes.data, cnt) == cnt
+        q = buf.reshape(cnt, 4).astype(np.float64)
+        tab = (q[:, 0] + q[:, 1]) + 1j * (q[:, 2] + q[:, 3])
+        j = np.arange(n)
+        assert np.abs(tab[:n] - np.exp(-2j * np.pi * j / n)).max() <= 1e-14, n
+        raw = buf.reshape(cnt, 4)
+        n2s = n // r1
+        for k1 in range(1, r1):
+            for n2 in range(n2s):
+                assert np.array_equal(raw[n + (k1 - 1) * n2s + n2], raw[(n2 * k1) % n]), (n, k1, n2)
