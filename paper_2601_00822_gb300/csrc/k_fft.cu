@@ -341,6 +341,9 @@ __global__ void __launch_bounds__(CCfg<L, T, false>::THREADS, T == 8 ? 6 : 3)
   const int plane = m * 6 * a.g.nz + blockIdx.y;   // (member, component, z) with blockIdx.y = comp * nz + z
   const int kx0 = blockIdx.x * T;
   if (tid == 0) {
+    // fetch the tensor map while the barrier is set up: between y passes other
+    // kernels run, so the block's one copy would otherwise wait for it
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<unsigned long long>(&tm)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
