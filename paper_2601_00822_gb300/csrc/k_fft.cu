@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(XCfg<L>::THREADS, xpass_min_blocks<R>()) k_xpa
   if (staged) {
     const XMember& M = a.xm[m];
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    constexpr int CH = L / 16;                     // 16-byte pieces per row
+    constexpr int CH = kPhaseStaged ? L / 16 : 1;  // 16-byte pieces per row
     for (int q = tid; q < LPB * CH; q += blockDim.x) {
       const int i = q / CH, ch = q - i * CH;
       const long long ln = line0 + i;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(CCfg<L, T, SW>::THREADS, col_min_blocks<R, T>(
 // plan; columns past mx read as zeros (out-of-bounds fill) and are not stored.
 // The wait is bounded: a copy that does not complete sets the member's fault
 // flag (IterState.diverged = 2, reported as a timeout) and the block returns.
-constexpr unsigned kTmaSpinLimit = 1u << 26;
+[[maybe_unused]] constexpr unsigned kTmaSpinLimit = 1u << 26;   // (FP32 builds only use it)
 
 template <int L, int DIR, int T>
 __global__ void __launch_bounds__(CCfg<L, T, false>::THREADS, T == 8 ? 6 : 3)
