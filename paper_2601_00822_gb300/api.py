@@ -92,13 +92,20 @@ class Plan:
                  sparse_resid=False, cd=None):
         """cd: None, or the displacement-based CG of Algorithm 3: "plain" (as printed,
         BFCS_CD) or "g0" (preconditioned by the reference medium's G0, BFCS_CD_PRECOND)."""
+        precisions = {"fp32": _lib.FP32, "fp64": _lib.FP64, "mixed": _lib.MIXED}
+        if precision not in precisions:
+            raise ValueError(f"precision must be one of {sorted(precisions)}, not {precision!r}")
+        if cd not in (None, "plain", "g0"):
+            raise ValueError(f"cd must be None, 'plain' or 'g0', not {cd!r}")
+        if cd is not None and cg:
+            raise ValueError("cg (Algorithm 2) and cd (Algorithm 3) exclude each other")
         self.lib = _lib.load()
         self.dims = tuple(int(d) for d in dims)
         self.precision = precision
         self.dtype = torch.float32 if precision == "fp32" else torch.float64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
-        flag = {"fp32": _lib.FP32, "fp64": _lib.FP64, "mixed": _lib.MIXED}[precision]
+        flag = precisions[precision]
         if autotune:
             flag |= _lib.AUTOTUNE
         if cg:

@@ -173,3 +173,17 @@ def test_float_float_twiddle_tables_hold_the_stage_one_block():
         for k1 in range(1, r1):
             for n2 in range(n2s):
                 assert np.array_equal(raw[n + (k1 - 1) * n2s + n2], raw[(n2 * k1) % n]), (n, k1, n2)
+
+
+def test_plan_options_are_checked_before_any_device_work():
+    """Unknown precisions and Krylov options, and CG together with Algorithm 3
+    (the library rejects BFCS_CG | BFCS_CD too), fail in the binding with a
+    ValueError before a stream or a device is touched."""
+    import pytest
+    from paper_2601_00822_gb300 import api
+    with pytest.raises(ValueError):
+        api.Plan((16, 16, 16), "fp16")
+    with pytest.raises(ValueError):
+        api.Plan((16, 16, 16), "fp32", cd="jacobi")
+    with pytest.raises(ValueError):
+        api.Plan((16, 16, 16), "fp32", cg=True, cd="g0")
